@@ -1,0 +1,256 @@
+"""FP64 CPU oracle of the pixel-track hot path (TEST INFRASTRUCTURE ONLY).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg import this package.  The
+product library never loads it.  It shares no code with the CUDA path; the only common input is
+the synthetic event generator.
+
+`build()` compiles `pxr_oracle.c` with gcc (`-O2 -ffp-contract=off`: no fused multiply-add, so that
+every cut quantity is the exact IEEE operation sequence written in the C source).  The functions
+below are thin ctypes wrappers; all arithmetic lives in the C file.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pxr_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liborc.so")
+MAXH = 8
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liborc.so (seconds)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-Wall", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class OrcParams(C.Structure):
+    _fields_ = [("n_layers", C.c_uint32), ("layer_is_disk", C.c_uint8 * 16),
+                ("n_pairs", C.c_uint32), ("pair_inner", C.c_uint8 * 32),
+                ("pair_outer", C.c_uint8 * 32), ("root_mask", C.c_uint32),
+                ("drop_suffixes", C.c_uint32), ("min_hits", C.c_uint32),
+                ("max_hits", C.c_uint32), ("cos_phi_window", C.c_double),
+                ("theta_cut", C.c_double), ("dca_cut", C.c_double), ("bfield", C.c_double),
+                ("sigma_rphi", C.c_double), ("sigma_z", C.c_double), ("x_over_x0", C.c_double)]
+
+
+class OrcTrack(C.Structure):
+    _fields_ = [("pt", C.c_double), ("phi", C.c_double), ("cot_theta", C.c_double),
+                ("dxy", C.c_double), ("dz", C.c_double), ("chi2", C.c_double),
+                ("charge", C.c_int32), ("status", C.c_int32)]
+
+
+class OrcResult(C.Structure):
+    _fields_ = [("n_hits", C.c_uint32), ("n_cells", C.c_uint32),
+                ("cell_in", C.POINTER(C.c_uint32)), ("cell_out", C.POINTER(C.c_uint32)),
+                ("n_edges", C.c_uint32), ("edge_a", C.POINTER(C.c_uint32)),
+                ("edge_b", C.POINTER(C.c_uint32)), ("n_tuples", C.c_uint32),
+                ("tup_n", C.POINTER(C.c_uint8)), ("tup_hits", C.POINTER(C.c_uint32)),
+                ("fit", C.POINTER(OrcTrack))]
+
+
+TRACK_DTYPE = np.dtype([("pt", "f8"), ("phi", "f8"), ("cot_theta", "f8"), ("dxy", "f8"),
+                        ("dz", "f8"), ("chi2", "f8"), ("charge", "i4"), ("status", "i4")])
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB_PATH)
+            d = C.c_double
+            L.orc_radius.restype = d
+            L.orc_radius.argtypes = [d, d]
+            L.orc_doublet_pass.restype = C.c_int
+            L.orc_doublet_pass.argtypes = [d] * 5
+            L.orc_theta_pass.restype = C.c_int
+            L.orc_theta_pass.argtypes = [d] * 7
+            L.orc_dca.restype = d
+            L.orc_dca.argtypes = [d] * 6
+            L.orc_dca_pass.restype = C.c_int
+            L.orc_dca_pass.argtypes = [d] * 7
+            dp = C.POINTER(C.c_double)
+            L.orc_bl_solve.restype = C.c_int
+            L.orc_bl_solve.argtypes = [C.c_int, dp, dp, dp, dp, C.c_int, dp, dp]
+            L.orc_fit_one.restype = C.c_int
+            L.orc_fit_one.argtypes = [C.c_int, dp, dp, dp, C.POINTER(C.c_uint16),
+                                      C.POINTER(OrcParams), C.POINTER(OrcTrack)]
+            L.orc_fit_batch.restype = None
+            L.orc_fit_batch.argtypes = [C.c_uint32, C.POINTER(C.c_uint8), dp, dp, dp,
+                                        C.POINTER(C.c_uint16), C.c_uint32,
+                                        C.POINTER(OrcParams), C.POINTER(OrcTrack)]
+            L.orc_reconstruct.restype = C.POINTER(OrcResult)
+            L.orc_reconstruct.argtypes = [C.c_uint32, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                          C.POINTER(C.c_float), C.POINTER(C.c_uint16),
+                                          C.POINTER(OrcParams), C.c_int]
+            L.orc_free.restype = None
+            L.orc_free.argtypes = [C.POINTER(OrcResult)]
+            _lib = L
+    return _lib
+
+
+def make_params(p) -> OrcParams:
+    """Marshal any object with the workload fields (geometry, pairs, cuts, fit constants)."""
+    o = OrcParams()
+    o.n_layers = p.n_layers
+    for i, v in enumerate(p.layer_is_disk):
+        o.layer_is_disk[i] = int(v)
+    o.n_pairs = len(p.pairs)
+    for i, (a, b) in enumerate(p.pairs):
+        o.pair_inner[i] = a
+        o.pair_outer[i] = b
+    o.root_mask = p.root_mask
+    o.drop_suffixes = 1 if p.drop_suffixes else 0
+    o.min_hits = p.min_hits
+    o.max_hits = p.max_hits
+    o.cos_phi_window = p.cos_phi_window
+    o.theta_cut = p.theta_cut
+    o.dca_cut = p.dca_cut
+    o.bfield = p.bfield
+    o.sigma_rphi = p.sigma_rphi
+    o.sigma_z = p.sigma_z
+    o.x_over_x0 = p.x_over_x0
+    return o
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+# -- single quantities -----------------------------------------------------------------------
+def radius(x, y):
+    return lib().orc_radius(float(x), float(y))
+
+
+def doublet_pass(xi, yi, xo, yo, cw) -> bool:
+    return bool(lib().orc_doublet_pass(xi, yi, xo, yo, cw))
+
+
+def theta_pass(ri, zi, rj, zj, rk, zk, t) -> bool:
+    return bool(lib().orc_theta_pass(ri, zi, rj, zj, rk, zk, t))
+
+
+def dca(xi, yi, xj, yj, xk, yk) -> float:
+    return lib().orc_dca(xi, yi, xj, yj, xk, yk)
+
+
+def bl_solve(s, meas, w, kvar, curv: bool):
+    """Broken-line normal-equation solve; returns (solution, chi2) or None on failure."""
+    n = len(s)
+    s = np.ascontiguousarray(s, np.float64)
+    meas = np.ascontiguousarray(meas, np.float64)
+    w = np.ascontiguousarray(w, np.float64)
+    kvar = np.ascontiguousarray(kvar, np.float64)
+    x = np.zeros(n + 1, np.float64)
+    chi2 = C.c_double(0.0)
+    rc = lib().orc_bl_solve(n, _ptr(s, C.c_double), _ptr(meas, C.c_double), _ptr(w, C.c_double),
+                            _ptr(kvar, C.c_double), 1 if curv else 0, _ptr(x, C.c_double),
+                            C.byref(chi2))
+    if rc != 0:
+        return None
+    return (x if curv else x[:n]), chi2.value
+
+
+# -- fits ------------------------------------------------------------------------------------
+def fit_one(X, Y, Z, layers, params) -> np.void:
+    n = len(X)
+    X = np.ascontiguousarray(X, np.float64)
+    Y = np.ascontiguousarray(Y, np.float64)
+    Z = np.ascontiguousarray(Z, np.float64)
+    L = np.ascontiguousarray(layers, np.uint16)
+    P = make_params(params)
+    out = OrcTrack()
+    lib().orc_fit_one(n, _ptr(X, C.c_double), _ptr(Y, C.c_double), _ptr(Z, C.c_double),
+                      _ptr(L, C.c_uint16), C.byref(P), C.byref(out))
+    rec = np.zeros((), TRACK_DTYPE)
+    for k in TRACK_DTYPE.names:
+        rec[k] = getattr(out, k)
+    return rec
+
+
+def fit_batch(nh, X, Y, Z, layers, params) -> np.ndarray:
+    """Fit m ntuplets; X, Y, Z, layers are [m, k] arrays (k <= 8), nh the hit counts."""
+    nh = np.ascontiguousarray(nh, np.uint8)
+    m, k = np.shape(X)
+    X = np.ascontiguousarray(X, np.float64)
+    Y = np.ascontiguousarray(Y, np.float64)
+    Z = np.ascontiguousarray(Z, np.float64)
+    L = np.ascontiguousarray(layers, np.uint16)
+    P = make_params(params)
+    out = np.zeros(m, TRACK_DTYPE)
+    lib().orc_fit_batch(m, _ptr(nh, C.c_uint8), _ptr(X, C.c_double), _ptr(Y, C.c_double),
+                        _ptr(Z, C.c_double), _ptr(L, C.c_uint16), k, C.byref(P),
+                        out.ctypes.data_as(C.POINTER(OrcTrack)))
+    return out
+
+
+# -- whole event -----------------------------------------------------------------------------
+def reconstruct(x, y, z, layer, params, stage: int = 4) -> dict:
+    """Doublets, CA edges, ntuplets and fits of one event (caller hit order).
+
+    Returns a dict with 'cells' [nc, 2] (inner, outer hit), 'edges' [ne, 2] (cell A, cell B),
+    'tuples' [nt, 8] (hits, 0xFFFFFFFF padded), 'tuple_n' [nt], 'fits' (structured [nt]).
+    """
+    x = np.ascontiguousarray(x, np.float32)
+    y = np.ascontiguousarray(y, np.float32)
+    z = np.ascontiguousarray(z, np.float32)
+    layer = np.ascontiguousarray(layer, np.uint16)
+    P = make_params(params)
+    L = lib()
+    rp = L.orc_reconstruct(len(x), _ptr(x, C.c_float), _ptr(y, C.c_float), _ptr(z, C.c_float),
+                           _ptr(layer, C.c_uint16), C.byref(P), stage)
+    if not rp:
+        raise ValueError("oracle rejected the input (layer id, limits) or ran out of memory")
+    try:
+        r = rp.contents
+        out = {}
+        nc = r.n_cells
+        cells = np.zeros((nc, 2), np.uint32)
+        if nc:
+            cells[:, 0] = np.ctypeslib.as_array(r.cell_in, (nc,))
+            cells[:, 1] = np.ctypeslib.as_array(r.cell_out, (nc,))
+        out["cells"] = cells
+        if stage >= 2:
+            ne = r.n_edges
+            edges = np.zeros((ne, 2), np.uint32)
+            if ne:
+                edges[:, 0] = np.ctypeslib.as_array(r.edge_a, (ne,))
+                edges[:, 1] = np.ctypeslib.as_array(r.edge_b, (ne,))
+            out["edges"] = edges
+        if stage >= 3:
+            nt = r.n_tuples
+            tup = np.full((nt, MAXH), 0xFFFFFFFF, np.uint32)
+            tn = np.zeros(nt, np.uint8)
+            if nt:
+                tup[:] = np.ctypeslib.as_array(r.tup_hits, (nt * MAXH,)).reshape(nt, MAXH)
+                tn[:] = np.ctypeslib.as_array(r.tup_n, (nt,))
+            out["tuples"] = tup
+            out["tuple_n"] = tn
+        if stage >= 4:
+            nt = r.n_tuples
+            fits = np.zeros(nt, TRACK_DTYPE)
+            if nt:
+                raw = np.ctypeslib.as_array(C.cast(r.fit, C.POINTER(C.c_uint8)),
+                                            (nt * C.sizeof(OrcTrack),))
+                fits[:] = np.frombuffer(raw.tobytes(), TRACK_DTYPE)
+            out["fits"] = fits
+        return out
+    finally:
+        L.orc_free(rp)
