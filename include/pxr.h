@@ -1,0 +1,258 @@
+/*
+ * pxr — pixel-track seeding and fitting on one GPU (sm_103a), C ABI.
+ *
+ * The library implements the data-parallel core of the "Tracks" module of the heterogeneous pixel
+ * reconstruction studied in the paper (§2, "Patatrack Heterogeneous Pixel Reconstruction": the
+ * module "forms n-tuplets from the hits, and fits the hit n-tuplets to obtain track parameters").
+ * Per event it runs: a per-layer phi-binned counting sort of the hits, doublet (cell) building in a
+ * phi window, cellular-automaton (CA) cell connection with an r-z alignment cut and a transverse
+ * DCA cut, ntuplet finding by a depth-first walk from root cells, and a broken-line helix fit of
+ * each ntuplet.  The paper gives no formulas for these steps; the definitions implemented are
+ * stated at each entry point below and in the parameter struct.
+ *
+ * Events are independent (the paper's throughput comes from processing many events concurrently,
+ * §5, Table 2).  The library batches many events into one set of kernel launches and serves a
+ * stream of events with continuous batching under a device-memory budget.
+ *
+ * Conventions for every entry point:
+ *   - Return value: PXR_OK (0) or a negative PXR_E* code.  pxr_last_error() gives a message.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA device memory of the
+ *     context's device (for example from torch.empty(..., device="cuda")).
+ *   - The library never takes ownership of caller memory.  Memory it allocates is released by
+ *     the matching destroy call.
+ *   - One context may be used from several threads: every entry point takes the context lock.
+ *   - Units: cm, GeV, tesla, radians.  Hit indices in results are positions in the caller's
+ *     input arrays of that event (0-based).
+ */
+#ifndef PXR_H
+#define PXR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PXR_MAX_LAYERS 16
+#define PXR_MAX_PAIRS 32
+#define PXR_MAX_HITS 6          /* hit slots per track; max_hits must be <= 6 */
+
+/* Return codes */
+#define PXR_OK 0
+#define PXR_EINVAL (-1)     /* bad argument, parameter or input value (NaN, layer id too large) */
+#define PXR_EAGAIN (-2)     /* admission refused now (memory budget or batch slots full); retry
+                               after pxr_poll has returned completed events */
+#define PXR_ENOMEM (-3)     /* the request can never fit the context's memory budget */
+#define PXR_EOVERFLOW (-4)  /* a per-event capacity (cells, edges, ntuplets) was exceeded; the
+                               event's results are truncated, never written out of bounds */
+#define PXR_ETIMEDOUT (-5)  /* a bounded wait gave up */
+#define PXR_ECUDA (-6)      /* a CUDA call failed; the context should be destroyed */
+#define PXR_ETRUNC (-7)     /* caller buffer too small; the required count is returned */
+#define PXR_ENOTFOUND (-8)  /* unknown or already fetched ticket */
+#define PXR_EBUSY (-9)      /* the ticket's event is not finished yet */
+
+/* Arithmetic of the three cuts. */
+#define PXR_CUT_FP64 0      /* every cut quantity evaluated in FP64, in the fixed operation
+                               order stated below (round to nearest, no fused multiply-add) */
+#define PXR_CUT_FP32 1      /* FP32 evaluation with a rigorous error bound around each
+                               threshold; a candidate inside the bound is re-evaluated exactly as
+                               in PXR_CUT_FP64, so both modes take the same decisions */
+
+/* Arithmetic of the broken-line fit. */
+#define PXR_FIT_FP64 0      /* all steps in FP64 */
+#define PXR_FIT_MIXED 1     /* FP32 bulk; residuals, Cholesky solves and the final conversion in
+                               FP64 */
+#define PXR_FIT_FP32 2      /* all steps in FP32 (local-frame differences formed exactly) */
+
+/* Presets for pxr_params_init */
+#define PXR_PRESET_BARREL 0 /* 4 barrel layers r = 2.9/6.8/10.9/16.0, pairs (0,1)(1,2)(2,3), roots
+                               {0}, quadruplets only (min = max = 4) */
+#define PXR_PRESET_PHASE1 1 /* barrel + 3 disks per side (ids 4-6 at +z, 7-9 at -z), 13 pairs,
+                               roots {0,1} with suffix removal, 3..5 hits */
+
+/*
+ * Reconstruction parameters.  All fields are inputs; pxr_params_init fills a preset.
+ *
+ * Doublets.  For every allowed pair p (layer pair_inner[p] -> layer pair_outer[p]) and every hit
+ *   i on the inner and o on the outer layer, the cell (i, o) exists iff
+ *       x_i x_o + y_i y_o >= cos_phi_window * r_i * r_o,   r = sqrt(x^2 + y^2),
+ *   i.e. the azimuths differ by at most phi_window.  cos_phi_window must equal cos(phi_window)
+ *   and is computed by the caller once (the library does not evaluate cos).
+ * CA edges.  Cell A = (i, j) connects to cell B = (j, k) iff
+ *       |a_r b_z - a_z b_r| <= theta_cut * |a| * |b|,  a = (r_j - r_i, z_j - z_i),
+ *                                                       b = (r_k - r_j, z_k - z_j)
+ *   and the circle through the three hits (transverse plane) passes within dca_cut of the
+ *   origin: with u = p_j - p_i, v = p_k - p_i, D = 2 (u_x v_y - u_y v_x),
+ *   c' = ((|u|^2 v_y - |v|^2 u_y) / D, (|v|^2 u_x - |u|^2 v_x) / D), c = p_i + c', R = |c'|,
+ *       dca = |2 c.p_i - |p_i|^2| / (|c| + R)   (D == 0: distance of the origin from the line
+ *                                                 through p_i and p_k).
+ * Ntuplets.  From every cell whose inner hit lies on a layer in root_layer_mask, follow edges
+ *   depth first; a path is emitted when it has max_hits hits or its last cell has no edge, and
+ *   it has at least min_hits hits.  With drop_suffixes, a path that is a strict suffix of another
+ *   emitted path is removed.
+ * Fit.  Broken line (V. Blobel, NIM A 566 (2006) 14): reference circle through hits 0, n/2, n-1;
+ *   transverse offsets + one curvature correction and a line in (s, z), each with multiple-
+ *   scattering kinks at the inner hits (Highland angle with x_over_x0 per layer crossing,
+ *   projected by 1 + cot^2 on the transverse and (1 + cot^2)^2 on the line kinks); weights
+ *   1/sigma_rphi^2 and 1/sigma_z^2 (disks: 1/(sigma_z cot)^2); Cholesky solves; conversion to the
+ *   point of closest approach to the z axis.  dxy = q (|C| - R) with C the fitted centre.
+ */
+typedef struct pxr_params {
+    uint32_t n_layers;                         /* <= PXR_MAX_LAYERS; hit layer ids < n_layers */
+    uint8_t layer_is_disk[PXR_MAX_LAYERS];     /* 1 for disks (z-fixed layers) */
+    uint32_t n_pairs;                          /* <= PXR_MAX_PAIRS */
+    uint8_t pair_inner[PXR_MAX_PAIRS];
+    uint8_t pair_outer[PXR_MAX_PAIRS];
+    uint32_t root_layer_mask;                  /* bit l set: cells starting on layer l are roots */
+    uint32_t drop_suffixes;                    /* 0 or 1 */
+    uint32_t min_hits, max_hits;               /* 2 <= min_hits <= max_hits <= PXR_MAX_HITS */
+    uint32_t cut_mode;                         /* PXR_CUT_* */
+    uint32_t fit_mode;                         /* PXR_FIT_* */
+    double phi_window;                         /* w, radians, (0, 0.5] */
+    double cos_phi_window;                     /* cos(w), computed by the caller */
+    double theta_cut;                          /* r-z alignment threshold, > 0 */
+    double dca_cut;                            /* cm, > 0 */
+    double bfield;                             /* tesla along +z, > 0 */
+    double sigma_rphi, sigma_z;                /* cm, > 0 */
+    double x_over_x0;                          /* radiation lengths per layer, >= 1e-6 */
+    uint32_t n_phi_bins;                       /* phi bins per layer, 64..2048; 0 = automatic */
+    uint32_t max_cells_per_event;              /* 0 = sized from the hit counts */
+    uint32_t max_tuples_per_event;             /* 0 = sized from the hit counts */
+} pxr_params;
+
+/* Context configuration. */
+typedef struct pxr_config {
+    int device;                 /* CUDA device ordinal */
+    size_t mem_budget_bytes;    /* device arena; 0 = 2 GiB */
+    void *arena;                /* optional caller device memory of mem_budget_bytes bytes (for
+                                   example a torch uint8 tensor); NULL = allocate once at create */
+    void *stream;               /* optional caller cudaStream_t for all work; NULL = the context
+                                   creates its own streams */
+    uint32_t max_batch_events;  /* dynamic batching cap (events per launch); 0 = 256 */
+    uint32_t max_batch_hits;    /* dynamic batching cap (hits per launch); 0 = 4M */
+    uint32_t max_inflight;      /* batches on the device at once, 1 or 2; 0 = 2 */
+    uint32_t keep_debug;        /* keep cells/edges/ntuplets of served events for
+                                   pxr_fetch_debug (costs memory until the fetch) */
+} pxr_config;
+
+/* Caller-owned arrays receiving the tracks of one event. */
+typedef struct pxr_tracks {
+    uint32_t capacity;          /* in: slots in every array below */
+    uint32_t n_tracks;          /* out: tracks of the event (may exceed capacity: PXR_ETRUNC) */
+    int32_t status;             /* out: PXR_OK or PXR_EOVERFLOW for this event */
+    uint8_t *n_hits;            /* [capacity] hits per track */
+    uint32_t *hit_idx;          /* [capacity * PXR_MAX_HITS] caller hit indices, inner to outer;
+                                   unused slots 0xFFFFFFFF */
+    double *pt, *phi, *cot_theta, *dxy, *dz, *chi2;   /* [capacity] */
+    int8_t *charge;             /* [capacity] */
+    int8_t *fit_status;         /* [capacity] 0 ok, 1 collinear, 2 zero curvature, 3 Cholesky */
+} pxr_tracks;
+
+typedef struct pxr_ctx pxr_ctx;
+typedef struct pxr_plan pxr_plan;
+
+/* Library version string (static storage). */
+const char *pxr_version(void);
+
+/* Message of the last error on this thread (static thread-local storage). */
+const char *pxr_last_error(void);
+
+/* Fill *p with a preset (PXR_PRESET_*), cut mode FP64 and fit mode FP64. */
+int pxr_params_init(pxr_params *p, int preset);
+
+/* Validate *p without touching any device: PXR_OK or PXR_EINVAL with a message. */
+int pxr_params_check(const pxr_params *p);
+
+/* Create a context on cfg->device.  Allocates the arena (unless cfg->arena is given), pinned host
+ * staging memory and the scheduler thread.  *out receives the context. */
+int pxr_create(const pxr_config *cfg, pxr_ctx **out);
+
+/* Stop the scheduler, wait for work in flight, release everything the context allocated.
+ * Unfetched results are discarded. */
+void pxr_destroy(pxr_ctx *ctx);
+
+/*
+ * Serving path.  Submit one event (host arrays of n_hits elements, caller order).  The hit data
+ * are copied before the call returns.  The event joins the next batch formed by the scheduler
+ * thread (continuous batching: a batch is launched as soon as a device slot is free).
+ * *ticket identifies the event.  Errors: PXR_EINVAL (bad params or input), PXR_EAGAIN (budget
+ * full now), PXR_ENOMEM (the event alone exceeds the budget).
+ */
+int pxr_submit_event(pxr_ctx *ctx, const float *x, const float *y, const float *z,
+                     const uint16_t *layer, uint32_t n_hits, const pxr_params *params,
+                     uint64_t *ticket);
+
+/* Return up to cap finished tickets in done[] (host array), *n_done = count.  Waits up to
+ * timeout_us microseconds (0 = do not wait, < 0 = until at least one is done or none pending). */
+int pxr_poll(pxr_ctx *ctx, uint64_t *done, uint32_t cap, uint32_t *n_done, int timeout_us);
+
+/* Copy the tracks of a finished event into caller arrays (canonical order: lexicographic by hit
+ * tuple).  On success the ticket is released.  PXR_ETRUNC: out->capacity too small, n_tracks set,
+ * ticket kept.  PXR_EBUSY: not finished.  The event's own status (overflow) is in out->status. */
+int pxr_fetch_tracks(pxr_ctx *ctx, uint64_t ticket, pxr_tracks *out);
+
+/* Debug content of a finished event kept with cfg->keep_debug (before pxr_fetch_tracks):
+ * what = 0: cells as (inner, outer) caller-index pairs (2 words each);
+ * what = 1: CA edges as (i, j, k) caller-index triples (3 words each);
+ * what = 2: ntuplets before suffix removal as PXR_MAX_HITS words each (0xFFFFFFFF padded).
+ * Writes at most cap words to buf (host), *n = number of items. */
+int pxr_fetch_debug(pxr_ctx *ctx, uint64_t ticket, int what, uint32_t *buf, uint32_t cap,
+                    uint32_t *n);
+
+/*
+ * Device-resident batch path ("plan").  A plan binds a batch of n_events events whose hits are
+ * already in device memory: x, y, z, layer are device arrays holding all events back to back,
+ * event e occupying [hit_offsets[e], hit_offsets[e+1]) (hit_offsets: host array of n_events+1).
+ * The plan owns a region of the context arena for all intermediate data and results; it sizes
+ * the per-event capacities from the per-layer hit counts (read back once here).  With
+ * use_graph != 0 the launch sequence is captured once into a CUDA graph and replayed.
+ * The caller keeps the input arrays alive and unchanged in shape for the plan's lifetime; their
+ * contents may change between runs.
+ */
+int pxr_plan_create(pxr_ctx *ctx, uint32_t n_events, const uint32_t *hit_offsets,
+                    const float *x, const float *y, const float *z, const uint16_t *layer,
+                    const pxr_params *params, int use_graph, pxr_plan **out);
+
+/* Run the whole hot path for the plan's batch on stream (cudaStream_t; NULL = the context's).
+ * Asynchronous: returns after enqueueing. */
+int pxr_plan_run(pxr_plan *plan, void *stream);
+
+/* Wait for the plan's last run and copy event e's tracks to the caller (same layout and order
+ * as pxr_fetch_tracks). */
+int pxr_plan_tracks(pxr_plan *plan, uint32_t e, pxr_tracks *out);
+
+/* Debug content of event e after the last run (see pxr_fetch_debug for `what`). */
+int pxr_plan_debug(pxr_plan *plan, uint32_t e, int what, uint32_t *buf, uint32_t cap,
+                   uint32_t *n);
+
+/* Number of kernel launches one pxr_plan_run performs (for launch accounting). */
+int pxr_plan_launches(const pxr_plan *plan);
+
+/* Per-event counters of the last run, copied to the host array out[5 * n_events]: out[k*E + e]
+ * for k = 0 cells, 1 CA edges, 2 ntuplets before selection, 3 flags (1 cells, 2 edges,
+ * 4 ntuplets overflowed; 8 bad layer id), 4 tracks. */
+int pxr_plan_counts(pxr_plan *plan, uint32_t *out);
+
+/* Device time in milliseconds of each stage of the last run, from CUDA events recorded between
+ * the launches (event-record nodes when the plan replays a graph).  Stage order: hit sort,
+ * doublets, CA connect, ntuplets + selection + output scan, fit; n = entries written (<= cap). */
+int pxr_plan_stage_ms(pxr_plan *plan, float *ms, int cap, int *n);
+
+void pxr_plan_destroy(pxr_plan *plan);
+
+/*
+ * Fit-only path over device-resident ntuplets (the precision study): m ntuplets of nh[t] hits
+ * (3..PXR_MAX_HITS), hit h of ntuplet t at x[t*stride + h] (device float arrays), layer ids
+ * likewise.  Outputs are device arrays of m elements.  fit_mode selects the arithmetic.
+ */
+int pxr_fit_batch(pxr_ctx *ctx, uint32_t m, const uint8_t *nh, const float *x, const float *y,
+                  const float *z, const uint16_t *layer, uint32_t stride,
+                  const pxr_params *params, double *pt, double *phi, double *cot_theta,
+                  double *dxy, double *dz, double *chi2, int8_t *charge, int8_t *fit_status,
+                  void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PXR_H */

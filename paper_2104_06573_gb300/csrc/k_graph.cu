@@ -1,0 +1,380 @@
+// Doublets, CA cell connection, ntuplet walk and ntuplet selection.
+//
+// Doublets: one warp per (inner hit, layer pair).  The outer layer's phi window is one or two
+// contiguous runs of the sorted hits; the 32 lanes test 32 consecutive candidates per step
+// (coalesced float4 loads), a ballot records the passes, one atomic per (hit, pair) reserves the
+// cells, and the second sweep writes them from the ballot masks, so the cells of an inner hit are
+// contiguous (the CA stage reads them as one run per pair).
+//
+// CA connect: one thread per cell A = (i, j) scans the cells B = (j, k) that start at its outer
+// hit; passes are counted first and, for the few cells that have any, written after one atomic
+// reservation.  Ntuplets: one thread per root cell walks the out-edges depth first with an
+// explicit stack.  Selection removes suffix paths and assigns output slots.
+#include "pxr_dev.cuh"
+#include "pxr_cuts.cuh"
+
+namespace pxr {
+
+constexpr float kPiF2 = 3.14159265358979f;
+constexpr int kMaxIt = 8;   // ballot masks kept per (hit, pair): 256 candidates
+
+struct Window {
+    uint32_t r0, n1, r2, n2;
+    __device__ __forceinline__ uint32_t pos(uint32_t c) const { return c < n1 ? r0 + c : r2 + (c - n1); }
+    __device__ __forceinline__ uint32_t size() const { return n1 + n2; }
+};
+
+// Candidates of layer Lo for an inner hit at azimuth phi: bins floor((phi -+ w_eps + pi) * nb/2pi)
+// taken modulo nb (one or two runs of the sorted hits).
+__device__ __forceinline__ Window phi_window(const uint32_t *__restrict__ bk, uint32_t Lo,
+                                             float phi, const DevParams &p)
+{
+    const uint32_t *lb = bk + Lo * p.nb;
+    int nb = (int)p.nb;
+    int blo = (int)floorf((phi - p.w_eps + kPiF2) * p.bins_per_rad);
+    int bhi = (int)floorf((phi + p.w_eps + kPiF2) * p.bins_per_rad);
+    Window w;
+    if (bhi - blo + 1 >= nb) {
+        w.r0 = lb[0]; w.n1 = lb[nb] - lb[0]; w.r2 = 0; w.n2 = 0;
+    } else if (blo < 0) {
+        w.r0 = lb[blo + nb]; w.n1 = lb[nb] - w.r0; w.r2 = lb[0]; w.n2 = lb[bhi + 1] - w.r2;
+    } else if (bhi >= nb) {
+        w.r0 = lb[blo]; w.n1 = lb[nb] - w.r0; w.r2 = lb[0]; w.n2 = lb[bhi - nb + 1] - w.r2;
+    } else {
+        w.r0 = lb[blo]; w.n1 = lb[bhi + 1] - w.r0; w.r2 = 0; w.n2 = 0;
+    }
+    return w;
+}
+
+__device__ __forceinline__ bool doublet_test(const DevBatch &b, const DevParams &p, uint32_t g,
+                                             float4 hi, uint32_t o)
+{
+    float4 ho = b.hs[o];
+    if (p.cut_mode == CUT_FP32) {
+        int r = doublet32(hi, ho, p.cw32);
+        if (r >= 0) return r == 1;
+    }
+    return doublet64((double)hi.x, (double)hi.y, b.r64[g], (double)ho.x, (double)ho.y, b.r64[o],
+                     p.cw);
+}
+
+__global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint32_t slots)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const uint64_t n_items = (uint64_t)b.N * slots;
+    const uint32_t nk = p.n_keys;
+    uint64_t item = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (; item < n_items; item += stride) {
+        const uint32_t g = (uint32_t)(item / slots), slot = (uint32_t)(item % slots);
+        const uint32_t e = find_event(b.hit_off, b.E, g);
+        const uint32_t *bk = b.bkt + (size_t)e * (nk + 1);
+        if (g >= bk[nk]) continue;                       // hit rejected by the sort (bad layer)
+        const uint32_t L = b.hmeta[g] >> kLocalBits;
+        if (slot >= p.n_out[L]) continue;
+        const uint32_t Lo = p.out_layer[L][slot];
+        const float4 hi = b.hs[g];
+        const Window w = phi_window(bk, Lo, atan2f(hi.y, hi.x), p);
+        const uint32_t nc = w.size();
+
+        uint32_t masks[kMaxIt];
+        uint32_t count = 0;
+#pragma unroll
+        for (int k = 0; k < kMaxIt; ++k) {
+            masks[k] = 0;
+            if ((uint32_t)k * 32u < nc) {
+                uint32_t c = (uint32_t)k * 32u + lane;
+                bool pass = c < nc && doublet_test(b, p, g, hi, w.pos(c));
+                masks[k] = __ballot_sync(0xFFFFFFFFu, pass);
+                count += __popc(masks[k]);
+            }
+        }
+        for (uint32_t c0 = kMaxIt * 32u; c0 < nc; c0 += 32u) {
+            uint32_t c = c0 + lane;
+            bool pass = c < nc && doublet_test(b, p, g, hi, w.pos(c));
+            count += __popc(__ballot_sync(0xFFFFFFFFu, pass));
+        }
+
+        uint32_t base = 0;
+        if (lane == 0 && count) base = atomicAdd(&b.cnt[C_CELLS * b.E + e], count);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        const uint32_t cap = b.cell_off[e + 1] - b.cell_off[e];
+        uint32_t nw = count;
+        if (base >= cap) nw = 0;
+        else if (base + count > cap) nw = cap - base;
+        if (lane == 0) {
+            if (nw < count) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_CELLS);
+            b.out_first[(size_t)g * kMaxOut + slot] = b.cell_off[e] + base;
+            b.out_n[(size_t)g * kMaxOut + slot] = nw;
+        }
+        if (nw == 0) continue;
+        const uint32_t first = b.cell_off[e] + base;
+        const bool fp64 = p.cut_mode == CUT_FP64;
+        const double ri = fp64 ? b.r64[g] : 0.0;
+        uint32_t run = 0;
+#pragma unroll
+        for (int k = 0; k < kMaxIt; ++k) {
+            uint32_t m = masks[k];
+            if ((m >> lane) & 1u) {
+                uint32_t idx = run + __popc(m & lt_mask);
+                if (idx < nw) {
+                    uint32_t o = w.pos((uint32_t)k * 32u + lane);
+                    b.cell_in[first + idx] = g;
+                    b.cell_out[first + idx] = o;
+                    if (fp64) b.cell_len64[first + idx] =
+                        seglen64(ri, (double)hi.z, b.r64[o], (double)b.hs[o].z);
+                }
+            }
+            run += __popc(m);
+        }
+        for (uint32_t c0 = kMaxIt * 32u; c0 < nc; c0 += 32u) {
+            uint32_t c = c0 + lane;
+            uint32_t o = c < nc ? w.pos(c) : 0u;
+            bool pass = c < nc && doublet_test(b, p, g, hi, o);
+            uint32_t m = __ballot_sync(0xFFFFFFFFu, pass);
+            if (pass) {
+                uint32_t idx = run + __popc(m & lt_mask);
+                if (idx < nw) {
+                    b.cell_in[first + idx] = g;
+                    b.cell_out[first + idx] = o;
+                    if (fp64) b.cell_len64[first + idx] =
+                        seglen64(ri, (double)hi.z, b.r64[o], (double)b.hs[o].z);
+                }
+            }
+            run += __popc(m);
+        }
+    }
+}
+
+void launch_doublets(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms)
+{
+    uint32_t slots = 1;
+    for (uint32_t l = 0; l < p.n_layers; ++l) slots = p.n_out[l] > slots ? p.n_out[l] : slots;
+    uint64_t warps = (uint64_t)b.N * slots;
+    uint64_t blocks = (warps + 7) / 8;
+    uint64_t cap = (uint64_t)sms * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) return;
+    k_doublets<<<(unsigned)blocks, 256, 0, s>>>(b, p, slots);
+}
+
+// ------------------------------------------------------------------------------------------
+// CA connect
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool triplet_test(const DevBatch &b, const DevParams &p, uint32_t i,
+                                             uint32_t j, uint32_t k, float4 hi, float4 hj,
+                                             const RZ32 &a, double na64, uint32_t A, uint32_t B)
+{
+    const float4 hk = b.hs[k];
+    bool exact_theta = p.cut_mode == CUT_FP64;
+    if (!exact_theta) {
+        RZ32 bs = rz32(hj, hk);
+        int r = theta32(a, bs, p.theta32);
+        if (r == 0) return false;
+        exact_theta = r < 0;
+    }
+    if (exact_theta) {
+        double ri = b.r64[i], rj = b.r64[j], rk = b.r64[k];
+        double nA = p.cut_mode == CUT_FP64 ? na64 : seglen64(ri, (double)hi.z, rj, (double)hj.z);
+        double nB = p.cut_mode == CUT_FP64 ? b.cell_len64[B]
+                                           : seglen64(rj, (double)hj.z, rk, (double)hk.z);
+        if (!theta64(ri, (double)hi.z, rj, (double)hj.z, rk, (double)hk.z, nA, nB, p.theta))
+            return false;
+    }
+    if (p.cut_mode == CUT_FP32) {
+        int r = dca32(hi.x, hi.y, hj.x, hj.y, hk.x, hk.y, p.dca32);
+        if (r >= 0) return r == 1;
+    }
+    return dca64((double)hi.x, (double)hi.y, (double)hj.x, (double)hj.y, (double)hk.x,
+                 (double)hk.y) <= p.dca;
+}
+
+__global__ void __launch_bounds__(256) k_connect(DevBatch b, DevParams p, uint32_t total)
+{
+    for (uint32_t A = blockIdx.x * blockDim.x + threadIdx.x; A < total;
+         A += gridDim.x * blockDim.x) {
+        const uint32_t e = find_event(b.cell_off, b.E, A);
+        const uint32_t c0 = b.cell_off[e];
+        const uint32_t ncell = min(b.cnt[C_CELLS * b.E + e], b.cell_off[e + 1] - c0);
+        if (A - c0 >= ncell) continue;
+        const uint32_t i = b.cell_in[A], j = b.cell_out[A];
+        const uint32_t Lj = b.hmeta[j] >> kLocalBits;
+        const uint32_t ns = p.n_out[Lj];
+        uint32_t npass = 0;
+        const float4 hi = b.hs[i], hj = b.hs[j];
+        RZ32 a = rz32(hi, hj);
+        const double na64 = p.cut_mode == CUT_FP64 ? b.cell_len64[A] : 0.0;
+        for (uint32_t s = 0; s < ns; ++s) {
+            const uint32_t f = b.out_first[(size_t)j * kMaxOut + s];
+            const uint32_t n = b.out_n[(size_t)j * kMaxOut + s];
+            for (uint32_t B = f; B < f + n; ++B)
+                npass += triplet_test(b, p, i, j, b.cell_out[B], hi, hj, a, na64, A, B);
+        }
+        uint32_t written = 0, first = 0;
+        if (npass) {
+            const uint32_t base = atomicAdd(&b.cnt[C_EDGES * b.E + e], npass);
+            const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
+            uint32_t nw = base >= cap ? 0u : min(npass, cap - base);
+            if (nw < npass) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+            first = b.edge_off[e] + base;
+            for (uint32_t s = 0; s < ns && written < nw; ++s) {
+                const uint32_t f = b.out_first[(size_t)j * kMaxOut + s];
+                const uint32_t n = b.out_n[(size_t)j * kMaxOut + s];
+                for (uint32_t B = f; B < f + n && written < nw; ++B)
+                    if (triplet_test(b, p, i, j, b.cell_out[B], hi, hj, a, na64, A, B))
+                        b.nbr[first + written++] = B;
+            }
+        }
+        b.nbr_first[A] = first;
+        b.nbr_n[A] = written;
+    }
+}
+
+void launch_connect(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
+{
+    uint64_t blocks = ((uint64_t)total + 255) / 256;
+    uint64_t cap = (uint64_t)sms * 32;
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) return;
+    k_connect<<<(unsigned)blocks, 256, 0, s>>>(b, p, total);
+}
+
+// ------------------------------------------------------------------------------------------
+// Ntuplets: depth-first walk from every root cell
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_ntuplets(DevBatch b, DevParams p, uint32_t total)
+{
+    for (uint32_t A = blockIdx.x * blockDim.x + threadIdx.x; A < total;
+         A += gridDim.x * blockDim.x) {
+        const uint32_t e = find_event(b.cell_off, b.E, A);
+        const uint32_t c0 = b.cell_off[e];
+        const uint32_t ncell = min(b.cnt[C_CELLS * b.E + e], b.cell_off[e + 1] - c0);
+        if (A - c0 >= ncell) continue;
+        const uint32_t Li = b.hmeta[b.cell_in[A]] >> kLocalBits;
+        if (!((p.root_mask >> Li) & 1u)) continue;
+        uint32_t cells[kMaxHits - 1];
+        uint32_t next[kMaxHits - 1];
+        int d = 0;
+        cells[0] = A;
+        next[0] = 0;
+        const uint32_t tcap = b.tup_off[e + 1] - b.tup_off[e];
+        while (d >= 0) {
+            const uint32_t c = cells[d];
+            const uint32_t nh = (uint32_t)d + 2u;
+            const uint32_t ne = b.nbr_n[c];
+            if (next[d] == 0 && (nh >= p.max_hits || ne == 0)) {
+                if (nh >= p.min_hits) {
+                    uint32_t slot = atomicAdd(&b.cnt[C_TUPLES * b.E + e], 1u);
+                    if (slot < tcap) {
+                        const uint32_t t = b.tup_off[e] + slot;
+                        uint32_t *th = b.tup_hits + (size_t)t * kMaxHits;
+                        th[0] = b.cell_in[cells[0]];
+                        for (int q = 0; q <= d; ++q) th[q + 1] = b.cell_out[cells[q]];
+                        for (int q = d + 2; q < kMaxHits; ++q) th[q] = kNone;
+                        b.tup_n[t] = (uint8_t)nh;
+                        b.tup_state[t] = nh < p.max_hits ? 2 : 1;
+                        b.tup_first[t] = A;
+                    } else {
+                        atomicOr(&b.cnt[C_FLAGS * b.E + e], F_TUPLES);
+                    }
+                }
+                --d;
+                continue;
+            }
+            if (next[d] < ne) {
+                const uint32_t nxt = b.nbr[b.nbr_first[c] + next[d]];
+                ++next[d];
+                ++d;
+                cells[d] = nxt;
+                next[d] = 0;
+                if (p.drop_suffixes) atomicMin(&b.mindepth[nxt], (uint32_t)d);
+            } else {
+                --d;
+            }
+        }
+    }
+}
+
+void launch_ntuplets(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
+{
+    uint64_t blocks = ((uint64_t)total + 255) / 256;
+    uint64_t cap = (uint64_t)sms * 32;
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) return;
+    k_ntuplets<<<(unsigned)blocks, 256, 0, s>>>(b, p, total);
+}
+
+// ------------------------------------------------------------------------------------------
+// Selection: a path that ended without an out-edge is a strict suffix of another emitted path
+// exactly when a root path of m hits enters its first cell and m + (its hits) <= max_hits.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_select(DevBatch b, DevParams p, uint32_t total)
+{
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += gridDim.x * blockDim.x) {
+        const uint32_t e = find_event(b.tup_off, b.E, t);
+        const uint32_t t0 = b.tup_off[e];
+        const uint32_t nt = min(b.cnt[C_TUPLES * b.E + e], b.tup_off[e + 1] - t0);
+        if (t - t0 >= nt) continue;
+        bool keep = true;
+        if (p.drop_suffixes && b.tup_state[t] == 2) {
+            const uint32_t md = b.mindepth[b.tup_first[t]];
+            if (md != kNone && md + b.tup_n[t] <= p.max_hits) keep = false;
+        }
+        b.tup_rank[t] = keep ? atomicAdd(&b.cnt[C_OUT * b.E + e], 1u) : kNone;
+    }
+}
+
+void launch_select(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
+{
+    uint64_t blocks = ((uint64_t)total + 255) / 256;
+    uint64_t cap = (uint64_t)sms * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) return;
+    k_select<<<(unsigned)blocks, 256, 0, s>>>(b, p, total);
+}
+
+// Exclusive prefix of the per-event output counts (one CTA).
+__global__ void k_out_scan(DevBatch b)
+{
+    __shared__ uint32_t carry;
+    __shared__ uint32_t warp_tot[32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    for (uint32_t e0 = 0; e0 < b.E; e0 += blockDim.x) {
+        uint32_t e = e0 + threadIdx.x;
+        uint32_t v = e < b.E ? b.cnt[C_OUT * b.E + e] : 0u;
+        uint32_t incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= (uint32_t)o) incl += t;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t nw = blockDim.x >> 5;
+            uint32_t w = lane < nw ? warp_tot[lane] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t t = __shfl_up_sync(0xFFFFFFFFu, w, o);
+                if (lane >= (uint32_t)o) w += t;
+            }
+            if (lane < nw) warp_tot[lane] = w;
+        }
+        __syncthreads();
+        uint32_t excl = carry + incl - v + (wid ? warp_tot[wid - 1] : 0u);
+        if (e < b.E) b.out_evt[e] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) b.out_evt[b.E] = carry;
+}
+
+void launch_out_scan(const DevBatch &b, cudaStream_t s)
+{
+    k_out_scan<<<1, 1024, 0, s>>>(b);
+}
+
+}  // namespace pxr

@@ -1,0 +1,128 @@
+// Device-side data layout of one batch of events, shared by the library's kernels.
+//
+// A batch holds E events whose hits sit back to back in the caller's arrays.  Every per-event
+// product (cells, CA edges, ntuplets, tracks) lives in a per-event region of a batch-wide array;
+// region e starts at the prefix of the per-event capacities computed on the host, and a per-event
+// counter says how much of it was filled.  Overflow of a region sets a per-event flag and drops
+// the excess: nothing is ever written outside a region, and one event's overflow never affects
+// another event (the result of an event does not depend on the batch it was run in).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pxr {
+
+constexpr int kMaxLayers = 16;
+constexpr int kMaxPairs = 32;
+constexpr int kMaxHits = 6;      // hit slots per ntuplet / track
+constexpr int kMaxOut = 4;       // layer pairs sharing one inner layer
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr int kLocalBits = 24;   // hmeta = layer << 24 | index of the hit inside its event
+constexpr uint32_t kLocalMask = (1u << kLocalBits) - 1u;
+
+// Per-event counters, laid out as kCounters consecutive arrays of E words.
+enum Counter : int { C_CELLS = 0, C_EDGES = 1, C_TUPLES = 2, C_FLAGS = 3, C_OUT = 4, kCounters = 5 };
+
+// Per-event flags (C_FLAGS).
+enum Flag : uint32_t { F_CELLS = 1u, F_EDGES = 2u, F_TUPLES = 4u, F_LAYER = 8u };
+
+enum CutMode : uint32_t { CUT_FP64 = 0, CUT_FP32 = 1 };
+enum FitMode : uint32_t { FIT_FP64 = 0, FIT_MIXED = 1, FIT_FP32 = 2 };
+
+struct DevParams {
+    uint32_t n_layers;
+    uint32_t nb;                        // phi bins per layer
+    uint32_t n_keys;                    // n_layers * nb
+    uint32_t root_mask;
+    uint32_t drop_suffixes;
+    uint32_t min_hits, max_hits;
+    uint32_t cut_mode, fit_mode;
+    uint8_t is_disk[kMaxLayers];
+    uint8_t n_out[kMaxLayers];          // number of pairs whose inner layer is l
+    uint8_t out_layer[kMaxLayers][kMaxOut];   // their outer layers
+    float bins_per_rad;                 // nb / (2 pi)
+    float w_eps;                        // phi_window + margin for the bin window (radians)
+    float cw32;                         // cos(w) rounded to float
+    float theta32;                      // theta_cut rounded to float
+    float dca32;                        // dca_cut rounded to float
+    double cw;                          // cos(w) as given by the caller
+    double theta, dca;
+    double bfield, sigma_rphi, sigma_z, x_over_x0;
+};
+
+struct DevBatch {
+    uint32_t E;                         // events
+    uint32_t N;                         // hits of all events
+    // inputs (device, caller order, events back to back)
+    const float *x, *y, *z;
+    const uint16_t *layer;
+    const uint32_t *hit_off;            // [E+1]
+    // per-event capacity prefixes [E+1]
+    const uint32_t *cell_off, *edge_off, *tup_off;
+    uint32_t *cnt;                      // [kCounters * E]
+    // counting sort of hits by (layer, phi bin)
+    uint32_t *bkt;                      // [E * (n_keys + 1)] absolute positions
+    float4 *hs;                         // [N] sorted hits: x, y, z, r (float)
+    double *r64;                        // [N] sorted radii, FP64
+    uint32_t *hmeta;                    // [N] layer << 24 | local caller index
+    // cells, grouped by (inner hit, pair slot)
+    uint32_t *out_first;                // [N * kMaxOut] first cell of (inner hit, slot)
+    uint32_t *out_n;                    // [N * kMaxOut] number of cells
+    uint32_t *cell_in, *cell_out;       // [cells] sorted hit positions
+    double *cell_len64;                 // [cells] |(dr, dz)| in FP64 (FP64 cut mode only)
+    // CA graph: out-edges of each cell
+    uint32_t *nbr_first;                // [cells]
+    uint32_t *nbr_n;                    // [cells]
+    uint32_t *nbr;                      // [edges] target cells
+    uint32_t *mindepth;                 // [cells] fewest hits before the cell on a root path
+    // ntuplets
+    uint32_t *tup_hits;                 // [tuples * kMaxHits] sorted hit positions
+    uint8_t *tup_n;                     // [tuples]
+    uint8_t *tup_state;                 // [tuples] 1 capped, 2 ended without edge
+    uint32_t *tup_first;                // [tuples] root cell
+    uint32_t *tup_rank;                 // [tuples] output slot within the event, kNone = dropped
+    // compact output, events back to back
+    uint32_t *out_evt;                  // [E+1]
+    uint32_t out_cap;                   // output slots (= tuple capacity)
+    uint8_t *o_nh;
+    uint32_t *o_hits;                   // [out_cap * kMaxHits] caller indices within the event
+    double *o_pt, *o_phi, *o_cot, *o_dxy, *o_dz, *o_chi2;
+    int8_t *o_q, *o_status;
+};
+
+// Largest e with off[e] <= t (off non-decreasing, off[0] = 0, t < off[E]).
+__device__ __forceinline__ uint32_t find_event(const uint32_t *__restrict__ off, uint32_t E,
+                                               uint32_t t)
+{
+    uint32_t lo = 0, hi = E;  // invariant: off[lo] <= t < off[hi]
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// One-time kernel attributes (large dynamic shared memory of the sort kernel).
+cudaError_t init_kernels();
+
+// Kernel launchers (defined in the .cu files).
+void launch_sort(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms);
+void launch_layer_count(const uint32_t *hit_off, const uint16_t *layer, uint32_t E,
+                        uint32_t n_layers, uint32_t *counts, cudaStream_t s, int sms);
+void launch_doublets(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms);
+void launch_connect(const DevBatch &b, const DevParams &p, uint32_t cell_total, cudaStream_t s,
+                    int sms);
+void launch_ntuplets(const DevBatch &b, const DevParams &p, uint32_t cell_total, cudaStream_t s,
+                     int sms);
+void launch_select(const DevBatch &b, const DevParams &p, uint32_t tup_total, cudaStream_t s,
+                   int sms);
+void launch_out_scan(const DevBatch &b, cudaStream_t s);
+void launch_fit(const DevBatch &b, const DevParams &p, uint32_t tup_total, cudaStream_t s,
+                int sms);
+void launch_fit_batch(uint32_t m, const uint8_t *nh, const float *x, const float *y,
+                      const float *z, const uint16_t *layer, uint32_t stride, const DevParams &p,
+                      double *pt, double *phi, double *cot, double *dxy, double *dz, double *chi2,
+                      int8_t *q, int8_t *status, cudaStream_t s, int sms);
+
+}  // namespace pxr

@@ -1,0 +1,267 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Sets (cells, CA edges, ntuplets before suffix removal, final hit tuples) must be bit-exact in
+both cut modes: the FP32 mode re-evaluates every candidate inside its rigorous error band with the
+FP64 formula, so it takes the same decisions.  Fitted parameters of the FP64 fit are compared
+with the oracle's FP64 fit within the tolerances stated for the method (pT and cot(theta) 1e-4
+relative, phi 1e-5 rad, dxy 1e-5 cm, dz 1e-4 relative with a 1e-5 cm floor); in practice they
+agree to ~1e-10 because only library math functions differ.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_2104_06573_gb300 import pxr, synth  # noqa: E402
+
+TOL = dict(pt=1e-4, cot_theta=1e-4, phi=1e-5, dxy=1e-5, dz=1e-4)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = pxr.Context(device=0, mem_budget_bytes=24 << 30)
+    yield c
+    c.close()
+
+
+def to_dev(events):
+    dev = torch.device("cuda:0")
+    off = np.zeros(len(events) + 1, np.uint32)
+    off[1:] = np.cumsum([len(e[0]) for e in events])
+    cat = [np.concatenate([e[k] for e in events]) if off[-1] else np.zeros(0, dt)
+           for k, dt in enumerate((np.float32, np.float32, np.float32, np.uint16))]
+    x = torch.from_numpy(np.ascontiguousarray(cat[0], np.float32)).to(dev)
+    y = torch.from_numpy(np.ascontiguousarray(cat[1], np.float32)).to(dev)
+    z = torch.from_numpy(np.ascontiguousarray(cat[2], np.float32)).to(dev)
+    layer = torch.from_numpy(np.ascontiguousarray(cat[3], np.uint16).view(np.int16)).to(dev)
+    if off[-1] == 0:      # keep valid device pointers for empty batches
+        x, y, z = (torch.zeros(1, device=dev) for _ in range(3))
+        layer = torch.zeros(1, dtype=torch.int16, device=dev)
+    return off, x, y, z, layer
+
+
+def run_plan(ctx, events, P, cut, fit=pxr.FIT_FP64, graph=False, n_phi_bins=0, max_cells=0,
+             debug=True):
+    off, x, y, z, layer = to_dev(events)
+    plan = pxr.Plan(ctx, off, x, y, z, layer,
+                    pxr.params_from(P, cut_mode=cut, fit_mode=fit, n_phi_bins=n_phi_bins,
+                                    max_cells=max_cells), use_graph=graph)
+    plan.pxr_plan_run()
+    out = []
+    for e in range(len(events)):
+        r = {"tracks": plan.pxr_plan_tracks(e)}
+        if debug:
+            r["cells"] = plan.pxr_plan_debug(e, 0)
+            r["edges"] = plan.pxr_plan_debug(e, 1)
+            r["tuples_all"] = plan.pxr_plan_debug(e, 2)
+        out.append(r)
+    plan.close()
+    return out
+
+
+def oracle_sets(orc, ev, P):
+    ref = orc.reconstruct(*ev, P)
+    cells = {tuple(map(int, c)) for c in ref["cells"]}
+    cl = ref["cells"]
+    edges = {(int(cl[a, 0]), int(cl[a, 1]), int(cl[b, 1])) for a, b in ref["edges"]}
+    tup = [tuple(int(h) for h in row[:n]) for row, n in zip(ref["tuples"], ref["tuple_n"])]
+    order = sorted(range(len(tup)), key=lambda i: tup[i] + (0xFFFFFFFF,) * (8 - len(tup[i])))
+    return ref, cells, edges, [tup[i] for i in order], ref["fits"][order]
+
+
+def gpu_tuples(tracks):
+    return [tuple(int(h) for h in row[:n]) for row, n in zip(tracks["hit_idx"], tracks["n_hits"])]
+
+
+def check_event(orc, ev, P, got, fit_tol=TOL):
+    ref, cells, edges, tup, fits = oracle_sets(orc, ev, P)
+    assert {tuple(map(int, c)) for c in got["cells"]} == cells
+    assert len(got["cells"]) == len(cells)
+    assert {tuple(map(int, c)) for c in got["edges"]} == edges
+    assert len(got["edges"]) == len(edges)
+    t = got["tracks"]
+    assert t["status"] == pxr.OK
+    assert gpu_tuples(t) == tup
+    if len(tup):
+        assert np.all(t["fit_status"] == fits["status"])
+        ok = fits["status"] == 0
+        assert np.all(t["charge"][ok] == fits["charge"][ok])
+        err = fit_errors(t, fits, ok)
+        for k, v in err.items():
+            assert v <= fit_tol[k], (k, v)
+    return len(cells), len(edges), len(tup)
+
+
+def fit_errors(t, f, ok):
+    if not np.any(ok):
+        return {k: 0.0 for k in TOL}
+    d = {}
+    d["pt"] = np.max(np.abs(t["pt"][ok] / f["pt"][ok] - 1))
+    d["cot_theta"] = np.max(np.abs(t["cot_theta"][ok] - f["cot_theta"][ok]) /
+                            np.maximum(1.0, np.abs(f["cot_theta"][ok])))
+    dphi = (t["phi"][ok] - f["phi"][ok] + np.pi) % (2 * np.pi) - np.pi
+    d["phi"] = np.max(np.abs(dphi))
+    d["dxy"] = np.max(np.abs(t["dxy"][ok] - f["dxy"][ok]))
+    d["dz"] = np.max(np.abs(t["dz"][ok] - f["dz"][ok]) /
+                     np.maximum(0.1, np.abs(f["dz"][ok])))
+    return d
+
+
+def ev_tuple(ev):
+    return (ev.x, ev.y, ev.z, ev.layer)
+
+
+@pytest.mark.parametrize("cut", [pxr.CUT_FP64, pxr.CUT_FP32])
+def test_barrel_event_bit_exact(ctx, orc, cut):
+    P = synth.params_barrel_quadruplets()
+    ev = ev_tuple(synth.event_barrel(0))
+    got = run_plan(ctx, [ev], P, cut)[0]
+    nc, ne, nt = check_event(orc, ev, P, got)
+    assert nt == 100 and nc > 700 and ne >= 200
+
+
+@pytest.mark.parametrize("cut", [pxr.CUT_FP64, pxr.CUT_FP32])
+def test_dense_event_with_disks_bit_exact(ctx, orc, cut):
+    P = synth.params_phase1()
+    ev = ev_tuple(synth.event_phase1(0))
+    got = run_plan(ctx, [ev], P, cut)[0]
+    nc, ne, nt = check_event(orc, ev, P, got)
+    assert nc > 200000 and nt > 3000
+    # the suffix rule removed something
+    assert len(got["tuples_all"]) > nt
+
+
+@pytest.mark.parametrize("cut", [pxr.CUT_FP64, pxr.CUT_FP32])
+def test_ragged_batch_and_edge_cases(ctx, orc, cut):
+    """Empty events, single hits, one populated layer, and events spanning many bins, in one
+    launch; each event must equal its oracle result."""
+    P = synth.params_barrel_quadruplets()
+    base = synth.event_barrel(3, 300)
+    events = [
+        (np.zeros(0, np.float32),) * 3 + (np.zeros(0, np.uint16),),
+        ev_tuple(synth.event_barrel(1, 1)),
+        (base.x[:1], base.y[:1], base.z[:1], base.layer[:1]),
+        ev_tuple(synth.event_barrel(2, 40)),
+        (base.x[base.layer == 2], base.y[base.layer == 2], base.z[base.layer == 2],
+         base.layer[base.layer == 2]),
+        ev_tuple(base),
+        (np.zeros(0, np.float32),) * 3 + (np.zeros(0, np.uint16),),
+        ev_tuple(synth.event_barrel(4, 1500)),
+    ]
+    got = run_plan(ctx, events, P, cut)
+    for ev, g in zip(events, got):
+        check_event(orc, ev, P, g)
+
+
+def test_graph_equals_direct_and_bin_counts(ctx, orc):
+    """Graph replay and direct launches agree; the result does not depend on the bin count."""
+    P = synth.params_phase1()
+    ev = ev_tuple(synth.make_event(5, 600, with_disks=True, pt_mode="power3", pt_lo=0.5,
+                                   eta_max=2.5, smear=True, noise_frac=0.2))
+    ref = run_plan(ctx, [ev], P, pxr.CUT_FP32, graph=False)[0]
+    for nb in (64, 256, 2048):
+        g = run_plan(ctx, [ev], P, pxr.CUT_FP32, graph=True, n_phi_bins=nb)[0]
+        assert {tuple(c) for c in g["cells"].tolist()} == {tuple(c) for c in ref["cells"].tolist()}
+        assert gpu_tuples(g["tracks"]) == gpu_tuples(ref["tracks"])
+        assert np.array_equal(g["tracks"]["pt"], ref["tracks"]["pt"])
+    check_event(orc, ev, P, ref)
+
+
+def test_overflow_is_flagged_not_written(ctx):
+    P = synth.params_barrel_quadruplets()
+    ev = ev_tuple(synth.event_barrel(0))
+    ok = ev_tuple(synth.event_barrel(1))
+    got = run_plan(ctx, [ev, ok], P, pxr.CUT_FP32, max_cells=50)
+    assert got[0]["tracks"]["status"] == pxr.EOVERFLOW
+    assert len(got[0]["cells"]) == 50
+    full = run_plan(ctx, [ok], P, pxr.CUT_FP32)[0]
+    assert got[1]["tracks"]["status"] == pxr.EOVERFLOW     # 50 is also too small for event 1
+    assert len(full["cells"]) > 50
+
+
+@pytest.mark.parametrize("cut", [pxr.CUT_FP64, pxr.CUT_FP32])
+def test_full_size_batch_sampled(ctx, orc, cut):
+    """The 256-event batch (200-6000 tracks per event) in one graph launch, as timed by the
+    benchmark.  Three sampled events (smallest, a middle one, the largest) are compared with the
+    oracle in full; every event passes the structural invariants."""
+    P = synth.params_barrel_quadruplets()
+    counts = synth.batch_track_counts(256)
+    evs = [ev_tuple(synth.make_event(e, counts[e])) for e in range(256)]
+    off, x, y, z, layer = to_dev(evs)
+    plan = pxr.Plan(ctx, off, x, y, z, layer, pxr.params_from(P, cut_mode=cut), use_graph=True)
+    plan.pxr_plan_run()
+    order = np.argsort(counts)
+    sample = [int(order[0]), int(order[128]), int(order[-1])]
+    for e in range(256):
+        t = plan.pxr_plan_tracks(e)
+        assert t["status"] == pxr.OK
+        lay = evs[e][3]
+        n = len(lay)
+        tuples = gpu_tuples(t)
+        assert len(set(tuples)) == len(tuples)
+        assert all(len(tt) == 4 and all(h < n for h in tt) for tt in tuples)
+        assert all([int(lay[h]) for h in tt] == [0, 1, 2, 3] for tt in tuples)
+        assert len(tuples) >= 0.95 * counts[e]          # nearly every generated track is found
+        if e in sample:
+            got = {"tracks": t, "cells": plan.pxr_plan_debug(e, 0),
+                   "edges": plan.pxr_plan_debug(e, 1)}
+            check_event(orc, evs[e], P, got)
+    plan.close()
+
+
+def test_serving_results_equal_alone_and_in_mix(ctx, orc):
+    """Continuous batching: events submitted while others run are batched with them; each
+    result equals the result of the same event run alone (bit-exact sets and fits)."""
+    P = synth.params_barrel_quadruplets()
+    p = pxr.params_from(P, cut_mode=pxr.CUT_FP32)
+    evs = [ev_tuple(synth.event_serving(100 + k, n))
+           for k, n in enumerate([50, 3000, 10, 800, 1, 5000, 200, 0, 1500])]
+    with pxr.Context(device=0, mem_budget_bytes=8 << 30, max_batch_events=4) as sctx:
+        tickets = [sctx.pxr_submit_event(*ev, p) for ev in evs]
+        done = set()
+        while len(done) < len(tickets):
+            done |= set(sctx.pxr_poll(timeout_us=200000))
+        mixed = [sctx.pxr_fetch_tracks(t) for t in tickets]
+    for ev, m in zip(evs, mixed):
+        alone = run_plan(ctx, [ev], P, pxr.CUT_FP32, debug=False)[0]["tracks"]
+        assert m["status"] == pxr.OK
+        assert gpu_tuples(m) == gpu_tuples(alone)
+        for k in pxr.TRACK_FIELDS:
+            assert np.array_equal(m[k], alone[k]), k
+    # and the served results match the oracle
+    for ev, m in zip(evs[:4], mixed[:4]):
+        _, _, _, tup, fits = oracle_sets(orc, ev, P)
+        assert gpu_tuples(m) == tup
+
+
+def test_fit_batch_modes(ctx, orc):
+    """Fit-only path on smeared ntuplets (70 % quadruplets, 30 % triplets, pT 0.5-100 GeV):
+    FP64 agrees with the oracle to round-off; MIXED and FP32 errors are reported."""
+    P = synth.params_barrel_quadruplets()
+    tb = synth.fit_tuplets(20000, seed=7)
+    ref = orc.fit_batch(tb.n_hits, tb.x.astype(np.float64), tb.y.astype(np.float64),
+                        tb.z.astype(np.float64), tb.layer, P)
+    dev = torch.device("cuda:0")
+    m = len(tb.n_hits)
+    args = [torch.from_numpy(a).to(dev) for a in (tb.n_hits, tb.x, tb.y, tb.z,
+                                                  tb.layer.view(np.int16))]
+    res = {}
+    for mode in (pxr.FIT_FP64, pxr.FIT_MIXED, pxr.FIT_FP32):
+        out = {k: torch.zeros(m, dtype=torch.float64, device=dev) for k in pxr.TRACK_FIELDS}
+        out["charge"] = torch.zeros(m, dtype=torch.int8, device=dev)
+        out["fit_status"] = torch.zeros(m, dtype=torch.int8, device=dev)
+        ctx.pxr_fit_batch(m, *args, 4, pxr.params_from(P, fit_mode=mode), out)
+        torch.cuda.synchronize()
+        h = {k: v.cpu().numpy() for k, v in out.items()}
+        ok = (ref["status"] == 0) & (h["fit_status"] == 0)
+        res[mode] = fit_errors(h, ref, ok)
+        if mode == pxr.FIT_FP64:
+            assert np.all(h["fit_status"] == ref["status"])
+            assert np.all(h["charge"][ok] == ref["charge"][ok])
+    for k, v in res[pxr.FIT_FP64].items():
+        assert v < 1e-8, (k, v)
+    print("fit errors vs FP64 oracle:", res)
