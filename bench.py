@@ -265,6 +265,7 @@ def run_pxr(args, rank, world, local):
     assert not cnt["flags"].any(), "capacity overflow in the timed batch"
     cells = int(cnt["cells"].sum())
     n_tracks = int(cnt["tracks"].sum())
+    layer_counts = [[int(v) for v in lc] for lc in layer_counts]
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -299,7 +300,7 @@ def run_pxr(args, rank, world, local):
     plan.close()
     ctx.close()
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(line, default=float), flush=True)
     if world > 1:
         dist.destroy_process_group()
 

@@ -61,9 +61,10 @@ extern "C" {
 
 /* Arithmetic of the broken-line fit. */
 #define PXR_FIT_FP64 0      /* all steps in FP64 */
-#define PXR_FIT_MIXED 1     /* FP32 bulk; residuals, Cholesky solves and the final conversion in
-                               FP64 */
-#define PXR_FIT_FP32 2      /* all steps in FP32 (local-frame differences formed exactly) */
+#define PXR_FIT_MIXED 1     /* FP64 arithmetic with FP32 transcendentals (atan2, log, cos, sin):
+                               the normal matrices need FP64 (kink weights up to ~1e14 next to
+                               measurement weights ~1e6) */
+#define PXR_FIT_FP32 2      /* all steps in FP32; errors against FP64 are reported, not bounded */
 
 /* Presets for pxr_params_init */
 #define PXR_PRESET_BARREL 0 /* 4 barrel layers r = 2.9/6.8/10.9/16.0, pairs (0,1)(1,2)(2,3), roots

@@ -288,7 +288,6 @@ int orc_fit_one(int n, const double *X, const double *Y, const double *Z, const 
     double Cy = (vv * ux - uu * vx) / D;
     double R0 = sqrt(Cx * Cx + Cy * Cy);
     double sgn = D > 0.0 ? 1.0 : -1.0;
-    int q = D > 0.0 ? -1 : 1;
 
     /* 2. path lengths and residuals */
     double ax = -Cx, ay = -Cy;

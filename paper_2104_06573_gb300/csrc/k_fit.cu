@@ -10,8 +10,9 @@
 //  4. transverse broken line (offsets u_i + curvature correction delta) and line broken line
 //     (z_i), normal equations solved by Cholesky;
 //  5. fitted circle at hit 0 and its point of closest approach to the z axis.
-// Precision modes: FP64 (all steps double), MIXED (steps 1-2 and 4-5 double, step 3 and the
-// normal-matrix assembly float), FP32 (all float).
+// Precision modes: FP64 (all steps double), MIXED (arithmetic double, transcendentals float:
+// the normal matrices mix kink weights up to ~1e14 with measurement weights ~1e6, which float
+// assembly cannot hold), FP32 (all float).
 #include "pxr_dev.cuh"
 
 namespace pxr {
@@ -107,8 +108,19 @@ struct FitOut {
     int8_t q, status;
 };
 
-// TC: prefit + residuals; TB: scattering + assembly; TS: solves + conversion.
-template <typename TC, typename TB, typename TS>
+// Transcendentals in float (FT = true) or in the argument's own type.
+template <bool FT, typename T>
+__device__ __forceinline__ T atan2_t(T y, T x) { return FT ? T(atan2f(float(y), float(x))) : atan2(y, x); }
+template <bool FT, typename T>
+__device__ __forceinline__ T log_t(T v) { return FT ? T(logf(float(v))) : log(v); }
+template <bool FT, typename T>
+__device__ __forceinline__ T cos_t(T v) { return FT ? T(cosf(float(v))) : cos(v); }
+template <bool FT, typename T>
+__device__ __forceinline__ T sin_t(T v) { return FT ? T(sinf(float(v))) : sin(v); }
+
+// TC: prefit + residuals; TB: scattering + assembly; TS: solves + conversion; FT: float
+// transcendentals (angles and logarithms need ~1e-7 relative, far inside the tolerances).
+template <typename TC, typename TB, typename TS, bool FT>
 __device__ void fit_track(int n, const float *X, const float *Y, const float *Z,
                           const uint8_t *L, const DevParams &p, FitOut &o)
 {
@@ -133,7 +145,7 @@ __device__ void fit_track(int n, const float *X, const float *Y, const float *Z,
         yr[i] = TB(pw / (sqrt_t(dx * dx + dy * dy) + R0));
         const TC cr = -Cx * dy + Cy * dx;
         const TC dt = -Cx * dx - Cy * dy;
-        s[i] = TB(R0 * atan2(sgn * cr, dt));
+        s[i] = TB(R0 * atan2_t<FT>(sgn * cr, dt));
         z[i] = TB(Z[i]);
     }
 
@@ -158,7 +170,7 @@ __device__ void fit_track(int n, const float *X, const float *Y, const float *Z,
     for (int j = 1; j + 1 < n; ++j) {
         const TB path = p.is_disk[L[j]] ? sqrt_t(sec2) / fabs(cot0) : sqrt_t(sec2);
         const TB xx = TB(p.x_over_x0) * path;
-        const TB th0 = (TB(0.0136) / pmom) * sqrt_t(xx) * (TB(1) + TB(0.038) * log(xx));
+        const TB th0 = (TB(0.0136) / pmom) * sqrt_t(xx) * (TB(1) + TB(0.038) * log_t<FT>(xx));
         const TB th2 = th0 * th0;
         kvT[j] = th2 * sec2;
         kvL[j] = th2 * sec2 * sec2;
@@ -185,7 +197,7 @@ __device__ void fit_track(int n, const float *X, const float *Y, const float *Z,
     const TS alpha = (xT[1] - xT[0]) / ds0 + TS(0.5) * delta * ds0;
     const TS nx = -TS(Cx) / R0s, ny = -TS(Cy) / R0s;
     const TS tx = -sgs * ny, ty = sgs * nx;
-    const TS ca = cos(alpha), sa = sin(alpha);
+    const TS ca = cos_t<FT>(alpha), sa = sin_t<FT>(alpha);
     const TS n2x = nx * ca - tx * sa, n2y = ny * ca - ty * sa;
     const TS P0x = xT[0] * nx, P0y = xT[0] * ny;
     const TS Fx = P0x - n2x / kappa, Fy = P0y - n2y / kappa;
@@ -195,10 +207,10 @@ __device__ void fit_track(int n, const float *X, const float *Y, const float *Z,
     const TS ex = wx / dist, ey = wy / dist;
     const TS tpx = -sgf * ey, tpy = sgf * ex;
     const TS cot = (xL[1] - xL[0]) / ds0;
-    const TS psi = atan2(sgf * (ex * ry - ey * rx), ex * rx + ey * ry);
+    const TS psi = atan2_t<FT>(sgf * (ex * ry - ey * rx), ex * rx + ey * ry);
     const int qf = sgf > TS(0) ? -1 : 1;
     o.pt = double(TS(kKpt * p.bfield) * R);
-    o.phi = double(atan2(tpy, tpx));
+    o.phi = double(atan2_t<FT>(tpy, tpx));
     o.cot = double(cot);
     o.dxy = double(TS(qf) * (dist - R));
     o.dz = double(xL[0] - cot * (R * psi));
@@ -211,9 +223,9 @@ __device__ __forceinline__ void fit_dispatch(int n, const float *X, const float 
                                              const float *Z, const uint8_t *L,
                                              const DevParams &p, FitOut &o)
 {
-    if (p.fit_mode == FIT_MIXED) fit_track<double, float, double>(n, X, Y, Z, L, p, o);
-    else if (p.fit_mode == FIT_FP32) fit_track<float, float, float>(n, X, Y, Z, L, p, o);
-    else fit_track<double, double, double>(n, X, Y, Z, L, p, o);
+    if (p.fit_mode == FIT_MIXED) fit_track<double, double, double, true>(n, X, Y, Z, L, p, o);
+    else if (p.fit_mode == FIT_FP32) fit_track<float, float, float, false>(n, X, Y, Z, L, p, o);
+    else fit_track<double, double, double, false>(n, X, Y, Z, L, p, o);
 }
 
 __global__ void __launch_bounds__(128) k_fit(DevBatch b, DevParams p, uint32_t total)
