@@ -253,6 +253,33 @@ int pxr_fit_batch(pxr_ctx *ctx, uint32_t m, const uint8_t *nh, const float *x, c
                   double *dxy, double *dz, double *chi2, int8_t *charge, int8_t *fit_status,
                   void *stream);
 
+/*
+ * Allocation-free doublet building for one event.  The paper has no counterpart: this entry
+ * point exists for callers that cannot let a library allocate device memory, such as serving
+ * loops that must not call cudaMalloc after start-up (it synchronises the device and stalls the
+ * other streams) and applications whose device memory is owned entirely by their own pool.
+ * It runs the hit sort and the doublet stage of the other entry points (same cells, same
+ * arithmetic) with all scratch in one fixed array in device global memory that the library
+ * holds on every GPU that loads it (about 12.6 MB) until the process exits; it calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Inputs (device): x, y, z, layer of n_hits hits (n_hits <= 65536).  Outputs (device):
+ * cells_inner[cap], cells_outer[cap] receive the cells as caller hit indices (cap <= 1048576),
+ * *n_cells the number of cells found (may exceed cap: then only cap are written), *flags
+ * (optional, may be NULL) the overflow flag word (1 = more cells than cap).  stream: cudaStream_t
+ * or NULL.  Asynchronous: results are valid once the stream reaches them.
+ * The first call on each device resolves the scratch array's device address and sets kernel
+ * attributes (with that device current); make that first call before any stream capture.
+ * Every call shares the scratch array and it keeps the last call's contents: calls whose work
+ * overlaps on the GPU race on it and must be ordered by the caller (one stream, or events).
+ * Errors: PXR_EINVAL for sizes beyond the limits or bad parameters (nothing is launched),
+ * PXR_ECUDA for a failed launch.
+ */
+int pxr_doublets_noalloc(const float *x, const float *y, const float *z, const uint16_t *layer,
+                         uint32_t n_hits, const pxr_params *params, uint32_t *cells_inner,
+                         uint32_t *cells_outer, uint32_t cap, uint32_t *n_cells,
+                         uint32_t *flags, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1260,3 +1260,9 @@ extern "C" int pxr_fetch_debug(pxr_ctx *ctx, uint64_t ticket, int what, uint32_t
     if (rc) return rc;
     return region_debug(t->batch->plan, t->index, what, buf, cap, n);
 }
+
+// Shared with the allocation-free doublet entry point (noalloc.cu).
+namespace pxr {
+int dev_params(const pxr_params *p, DevParams *d) { return check_params(p, d); }
+int set_error(int code, const char *msg) { return fail(code, msg); }
+}  // namespace pxr

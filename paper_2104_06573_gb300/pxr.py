@@ -108,6 +108,8 @@ def load(build_if_missing: bool = False):
             "pxr_plan_destroy": (None, [vp]),
             "pxr_fit_batch": (i32, [vp, u32, vp, vp, vp, vp, vp, u32, P(pxr_params), vp, vp, vp,
                                     vp, vp, vp, vp, vp, vp]),
+            "pxr_doublets_noalloc": (i32, [vp, vp, vp, vp, u32, P(pxr_params), vp, vp, u32, vp,
+                                           vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -366,6 +368,14 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def pxr_doublets_noalloc(x, y, z, layer, n_hits, params, cells_inner, cells_outer, cap, n_cells,
+                         flags=None, stream=None):
+    """Allocation-free doublets of one event (all arrays device tensors or pointers)."""
+    _check(load().pxr_doublets_noalloc(ptr(x), ptr(y), ptr(z), ptr(layer), n_hits,
+                                       C.byref(params), ptr(cells_inner), ptr(cells_outer), cap,
+                                       ptr(n_cells), ptr(flags), ptr(stream)))
 
 
 def pxr_version() -> str:
