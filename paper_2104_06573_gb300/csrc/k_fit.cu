@@ -113,10 +113,6 @@ template <bool FT, typename T>
 __device__ __forceinline__ T atan2_t(T y, T x) { return FT ? T(atan2f(float(y), float(x))) : atan2(y, x); }
 template <bool FT, typename T>
 __device__ __forceinline__ T log_t(T v) { return FT ? T(logf(float(v))) : log(v); }
-template <bool FT, typename T>
-__device__ __forceinline__ T cos_t(T v) { return FT ? T(cosf(float(v))) : cos(v); }
-template <bool FT, typename T>
-__device__ __forceinline__ T sin_t(T v) { return FT ? T(sinf(float(v))) : sin(v); }
 
 // TC: prefit + residuals; TB: scattering + assembly; TS: solves + conversion; FT: float
 // transcendentals (angles and logarithms need ~1e-7 relative, far inside the tolerances).
@@ -197,7 +193,16 @@ __device__ void fit_track(int n, const float *X, const float *Y, const float *Z,
     const TS alpha = (xT[1] - xT[0]) / ds0 + TS(0.5) * delta * ds0;
     const TS nx = -TS(Cx) / R0s, ny = -TS(Cy) / R0s;
     const TS tx = -sgs * ny, ty = sgs * nx;
-    const TS ca = cos_t<FT>(alpha), sa = sin_t<FT>(alpha);
+    TS ca, sa;
+    if constexpr (FT) {
+        // cos of a small angle rounds to 1 in float; 1 - 2 sin^2(a/2) keeps its deviation
+        const TS sh = TS(sinf(float(alpha * TS(0.5))));
+        ca = TS(1) - TS(2) * sh * sh;
+        sa = TS(sinf(float(alpha)));
+    } else {
+        ca = cos(alpha);
+        sa = sin(alpha);
+    }
     const TS n2x = nx * ca - tx * sa, n2y = ny * ca - ty * sa;
     const TS P0x = xT[0] * nx, P0y = xT[0] * ny;
     const TS Fx = P0x - n2x / kappa, Fy = P0y - n2y / kappa;

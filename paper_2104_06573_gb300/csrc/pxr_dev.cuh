@@ -41,11 +41,15 @@ struct DevParams {
     uint8_t is_disk[kMaxLayers];
     uint8_t n_out[kMaxLayers];          // number of pairs whose inner layer is l
     uint8_t out_layer[kMaxLayers][kMaxOut];   // their outer layers
+    uint8_t n_in[kMaxLayers];           // number of pairs whose outer layer is l
+    uint8_t in_layer[kMaxLayers][kMaxOut];    // their inner layers
+    uint8_t in_slot[kMaxLayers][kMaxOut];     // slot of l among the inner layer's outer layers
     float bins_per_rad;                 // nb / (2 pi)
     float w_eps;                        // phi_window + margin for the bin window (radians)
     float cw32;                         // cos(w) rounded to float
     float theta32;                      // theta_cut rounded to float
     float dca32;                        // dca_cut rounded to float
+    float key_halfwin;                  // r-z direction-key window: asin(theta_cut) + margin
     double cw;                          // cos(w) as given by the caller
     double theta, dca;
     double bfield, sigma_rphi, sigma_z, x_over_x0;

@@ -135,6 +135,9 @@ static int check_params(const pxr_params *p, DevParams *d)
         for (uint32_t s = 0; s < d->n_out[a]; ++s)
             if (d->out_layer[a][s] == b) return fail(PXR_EINVAL, "duplicate layer pair");
         if (d->n_out[a] >= kMaxOut) return fail(PXR_EINVAL, "more than 4 pairs share an inner layer");
+        if (d->n_in[b] >= kMaxOut) return fail(PXR_EINVAL, "more than 4 pairs share an outer layer");
+        d->in_layer[b][d->n_in[b]] = (uint8_t)a;
+        d->in_slot[b][d->n_in[b]++] = d->n_out[a];
         d->out_layer[a][d->n_out[a]++] = (uint8_t)b;
     }
     d->bins_per_rad = (float)(d->nb / (2.0 * M_PI));
@@ -142,6 +145,10 @@ static int check_params(const pxr_params *p, DevParams *d)
     d->cw32 = (float)p->cos_phi_window;
     d->theta32 = (float)p->theta_cut;
     d->dca32 = (float)p->dca_cut;
+    // |sin(angle)| <= t  <=>  the r-z directions differ by at most asin(t) modulo pi; the key
+    // below never changes faster than the angle, so this (plus a margin far above the float
+    // error of the key) is a conservative window.  t >= 1 keeps every candidate.
+    d->key_halfwin = p->theta_cut < 1.0 ? (float)(std::asin(p->theta_cut) + 1e-4) : 4.0f;
     d->cw = p->cos_phi_window;
     d->theta = p->theta_cut;
     d->dca = p->dca_cut;
@@ -454,6 +461,7 @@ static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
     if (t) CK(stage_mark(P->ev_stage[0], s, capturing));
     CK(cudaMemsetAsync(r + P->off.cnt, 0, 4 * (size_t)kCounters * P->E, s));
     if (p.drop_suffixes) CK(cudaMemsetAsync(r + P->off.mindepth, 0xFF, 4 * P->C, s));
+    CK(cudaMemsetAsync(r + P->off.nbr_n, 0, 4 * P->C, s));   // cells without edges stay at 0
     launch_sort(b, p, s, sms);
     if (t) CK(stage_mark(P->ev_stage[1], s, capturing));
     launch_doublets(b, p, s, sms);
