@@ -6,11 +6,11 @@
 // cells, and the second sweep writes them from the ballot masks, so the cells of an inner hit are
 // contiguous (the CA stage reads them as one run per pair).
 //
-// CA connect: one warp per junction hit j.  Its out-cells (j, k) are staged in shared memory and
-// sorted by the direction of (k - j) in the r-z plane; each in-cell (i, j) tests only the
-// out-cells whose direction lies within asin(theta_cut) of its own (modulo pi), a conservative
-// window in which the exact cuts decide.  Passes are counted first; the cells that have any
-// reserve their edge list with one atomic.  Ntuplets: one thread per root cell walks the
+// CA connect: one thread per cell A = (i, j).  The out-cells (j, k) that can pass the r-z
+// alignment cut have k inside a cone of directions around A's direction; a second index of the
+// hits (a per-layer grid over the free coordinate and phi) turns that cone into a few grid rows,
+// a conservative window in which the exact cuts decide.  Passes are counted first; the cells
+// that have any reserve their edge list with one atomic.  Ntuplets: one thread per root cell walks the
 // out-edges depth first with an explicit stack.  Selection removes suffix paths and assigns
 // output slots.
 #include "pxr_dev.cuh"
@@ -165,85 +165,32 @@ void launch_doublets(const DevBatch &b, const DevParams &p, cudaStream_t s, int 
 // ------------------------------------------------------------------------------------------
 // CA connect
 // ------------------------------------------------------------------------------------------
+// Exact decision for the triplet (i, j, k): r-z alignment, then DCA.  FP32 mode decides in float
+// when outside the guard band and falls back to the FP64 formulas otherwise.
 __device__ __forceinline__ bool triplet_test(const DevBatch &b, const DevParams &p, uint32_t i,
                                              uint32_t j, uint32_t k, float4 hi, float4 hj,
-                                             const RZ32 &a, double na64, uint32_t A, uint32_t B)
+                                             float4 hk, const RZ32 &a, double na64)
 {
-    const float4 hk = b.hs[k];
     bool exact_theta = p.cut_mode == CUT_FP64;
     if (!exact_theta) {
-        RZ32 bs = rz32(hj, hk);
-        int r = theta32(a, bs, p.theta32);
+        const RZ32 bs = rz32(hj, hk);
+        const int r = theta32(a, bs, p.theta32);
         if (r == 0) return false;
         exact_theta = r < 0;
     }
     if (exact_theta) {
-        double ri = b.r64[i], rj = b.r64[j], rk = b.r64[k];
-        double nA = p.cut_mode == CUT_FP64 ? na64 : seglen64(ri, (double)hi.z, rj, (double)hj.z);
-        double nB = p.cut_mode == CUT_FP64 ? b.cell_len64[B]
-                                           : seglen64(rj, (double)hj.z, rk, (double)hk.z);
+        const double ri = b.r64[i], rj = b.r64[j], rk = b.r64[k];
+        const double nA = p.cut_mode == CUT_FP64 ? na64 : seglen64(ri, (double)hi.z, rj, (double)hj.z);
+        const double nB = seglen64(rj, (double)hj.z, rk, (double)hk.z);
         if (!theta64(ri, (double)hi.z, rj, (double)hj.z, rk, (double)hk.z, nA, nB, p.theta))
             return false;
     }
     if (p.cut_mode == CUT_FP32) {
-        int r = dca32(hi.x, hi.y, hj.x, hj.y, hk.x, hk.y, p.dca32);
+        const int r = dca32(hi.x, hi.y, hj.x, hj.y, hk.x, hk.y, p.dca32);
         if (r >= 0) return r == 1;
     }
     return dca64((double)hi.x, (double)hi.y, (double)hj.x, (double)hj.y, (double)hk.x,
                  (double)hk.y) <= p.dca;
-}
-
-// Direction key of an r-z segment folded modulo pi: 1 - dr / (|dr| + dz) after turning the
-// segment into the upper half plane.  It increases with the direction angle on [0, pi), and its
-// derivative with respect to the angle lies in [1/2, 1], so two directions whose angles differ by
-// d (modulo pi) have keys that differ by at most d (modulo 2).  Zero-length segments get -1.
-__device__ __forceinline__ float dir_key(float dr, float dz)
-{
-    if (dz < 0.f || (dz == 0.f && dr < 0.f)) {
-        dr = -dr;
-        dz = -dz;
-    }
-    const float s = fabsf(dr) + dz;
-    return s > 0.f ? 1.f - __fdiv_rn(dr, s) : -1.f;
-}
-
-constexpr int kStage = 256;      // out-cells of one junction hit sorted in shared memory
-constexpr float kKeyPad = 3.0e38f;
-
-// Bitonic sort of n (power of two) entries by key, one warp.
-__device__ __forceinline__ void warp_bitonic(float *key, uint32_t *v1, uint32_t *v2, uint32_t n,
-                                             uint32_t lane)
-{
-    for (uint32_t k = 2; k <= n; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = lane; i < n; i += 32) {
-                const uint32_t ixj = i ^ j;
-                if (ixj > i) {
-                    const bool up = (i & k) == 0;
-                    const float a = key[i], c = key[ixj];
-                    if ((a > c) == up) {
-                        key[i] = c;
-                        key[ixj] = a;
-                        uint32_t t = v1[i]; v1[i] = v1[ixj]; v1[ixj] = t;
-                        t = v2[i]; v2[i] = v2[ixj]; v2[ixj] = t;
-                    }
-                }
-            }
-            __syncwarp();
-        }
-    }
-}
-
-// First index in [lo, hi) whose key is >= v (strict: > v).
-__device__ __forceinline__ uint32_t key_bound(const float *key, uint32_t lo, uint32_t hi, float v,
-                                              bool strict)
-{
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        const bool left = strict ? key[mid] <= v : key[mid] < v;
-        if (left) lo = mid + 1; else hi = mid;
-    }
-    return lo;
 }
 
 // Index of the cell (i, j): i's cells toward layer Lj are stored in the candidate order of i's
@@ -257,192 +204,154 @@ __device__ __forceinline__ uint32_t find_cell(const DevBatch &b, const DevParams
         return (pos >= w.r0 && pos < w.r0 + w.n1) ? pos - w.r0 : w.n1 + (pos - w.r2);
     };
     const uint32_t f = b.out_first[(size_t)i * kMaxOut + slot];
-    uint32_t lo = 0, hi_ = b.out_n[(size_t)i * kMaxOut + slot];
+    const uint32_t n = b.out_n[(size_t)i * kMaxOut + slot];
     const uint32_t want = rank(j);
+    uint32_t lo = 0, hi_ = n;
     while (lo < hi_) {
         const uint32_t mid = (lo + hi_) >> 1;
-        const uint32_t r = rank(b.cell_out[f + mid]);
-        if (r < want) lo = mid + 1; else hi_ = mid;
+        if (rank(b.cell_out[f + mid]) < want) lo = mid + 1; else hi_ = mid;
     }
-    if (lo < b.out_n[(size_t)i * kMaxOut + slot] && b.cell_out[f + lo] == j) return f + lo;
+    if (lo < n && b.cell_out[f + lo] == j) return f + lo;
     return kNone;   // dropped by a cell overflow
 }
 
-// Candidate out-cells of one in-cell: up to three ranges of the sorted stage.
-struct Ranges {
-    uint32_t a0, a1, b0, b1, c0, c1;
-};
-
-__device__ __forceinline__ Ranges key_ranges(const float *key, uint32_t nzero, uint32_t cnt,
-                                             float kA, float hw)
+// Conservative interval of the free coordinate (z on a barrel layer, r on a disk) reachable from
+// hit j along r-z directions within asin(theta_cut) of a = (ar, az), modulo pi.  With m the slope
+// of a against the layer's fixed coordinate and T = tan(asin(theta_cut)), the allowed slopes are
+// [(m - T)/(1 + mT), (m + T)/(1 - mT)] unless the cone contains the direction along the layer
+// (then everything is reachable); the offsets along the fixed coordinate span the layer's range.
+// Returns false when the whole free range must be scanned.
+__device__ __forceinline__ bool cone_window(float ar, float az, float rj, float zj, bool disk,
+                                            const float *lr, float T, float &lo, float &hi)
 {
-    Ranges r{0, nzero, 0, 0, 0, 0};              // zero-length out-cells always
-    if (kA < 0.f || hw >= 1.f) {
-        r.b0 = nzero;
-        r.b1 = cnt;
-        return r;
-    }
-    const float lo = kA - hw, hi = kA + hw;
-    if (lo < 0.f) {
-        r.b0 = key_bound(key, nzero, cnt, lo + 2.f, false);
-        r.b1 = cnt;
-        r.c0 = nzero;
-        r.c1 = key_bound(key, nzero, cnt, hi, true);
-    } else if (hi >= 2.f) {
-        r.b0 = key_bound(key, nzero, cnt, lo, false);
-        r.b1 = cnt;
-        r.c0 = nzero;
-        r.c1 = key_bound(key, nzero, cnt, hi - 2.f, true);
-    } else {
-        r.b0 = key_bound(key, nzero, cnt, lo, false);
-        r.b1 = key_bound(key, nzero, cnt, hi, true);
-    }
-    return r;
+    const float u = disk ? az : ar, v = disk ? ar : az;
+    const float base = disk ? rj : zj;
+    float dlo = disk ? lr[2] - zj : lr[0] - rj;
+    float dhi = disk ? lr[3] - zj : lr[1] - rj;
+    dlo -= 1e-4f + 1e-5f * fabsf(dlo);
+    dhi += 1e-4f + 1e-5f * fabsf(dhi);
+    if (!(fabsf(u) > 1e-20f) || !(T < 1e30f)) return false;
+    const float m = v / u;
+    const float den_hi = 1.f - m * T, den_lo = 1.f + m * T;
+    if (!(den_hi > 1e-4f) || !(den_lo > 1e-4f)) return false;
+    const float s_hi = (m + T) / den_hi, s_lo = (m - T) / den_lo;
+    const float c1 = dlo * s_lo, c2 = dlo * s_hi, c3 = dhi * s_lo, c4 = dhi * s_hi;
+    lo = base + fminf(fminf(c1, c2), fminf(c3, c4));
+    hi = base + fmaxf(fmaxf(c1, c2), fmaxf(c3, c4));
+    const float smax = fmaxf(fabsf(s_lo), fabsf(s_hi));
+    const float margin = 2e-3f + 1e-4f * (fabsf(lo) + fabsf(hi)) +
+                         1e-5f * fmaxf(fabsf(dlo), fabsf(dhi)) * (1.f + smax * smax);
+    lo -= margin;
+    hi += margin;
+    return true;
 }
 
-// Write the out-edges of cell A (npass of them) after one atomic reservation.
-template <typename Visit>
-__device__ __forceinline__ void emit_edges(const DevBatch &b, uint32_t e, uint32_t A,
-                                           uint32_t npass, Visit &&visit)
+__device__ __forceinline__ uint32_t free_bin(float v, float lo, float hi, uint32_t nf)
 {
-    const uint32_t base = atomicAdd(&b.cnt[C_EDGES * b.E + e], npass);
-    const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
-    const uint32_t nw = base >= cap ? 0u : min(npass, cap - base);
-    if (nw < npass) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
-    const uint32_t first = b.edge_off[e] + base;
-    uint32_t written = 0;
-    visit([&](uint32_t B) {
-        if (written < nw) b.nbr[first + written++] = B;
-    });
-    b.nbr_first[A] = first;
-    b.nbr_n[A] = written;
+    if (!(hi > lo)) return 0;
+    const float t = floorf((v - lo) * ((float)nf / (hi - lo)));
+    const int b = (int)t;
+    return (uint32_t)(b < 0 ? 0 : (b >= (int)nf ? (int)nf - 1 : b));
 }
 
-// One warp per junction hit j: its out-cells (j, k) are staged in shared memory sorted by the
-// direction key of (k - j) in r-z; each in-cell (i, j), found by scanning i over j's phi window
-// on the inner layer with the doublet cut, tests only the out-cells inside its key window.
-__global__ void __launch_bounds__(256) k_connect(DevBatch b, DevParams p)
+// Visit every hit k of the grid rows of layer Lk that the in-cell's cone can reach, inside hit
+// j's phi window (coarse grid bins; the doublet cut decides).
+template <typename F>
+__device__ __forceinline__ void visit_cone(const DevBatch &b, const DevParams &p, uint32_t e,
+                                           uint32_t Lk, const RZ32 &a, float4 hj, float phij,
+                                           F &&f)
 {
-    __shared__ float s_key[8][kStage];
-    __shared__ uint32_t s_B[8][kStage];
-    __shared__ uint32_t s_k[8][kStage];
-    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-    float *key = s_key[wid];
-    uint32_t *sB = s_B[wid], *sK = s_k[wid];
-    const uint32_t nk = p.n_keys;
-    const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t jj = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; jj < b.N;
-         jj += stride) {
-        const uint32_t j = (uint32_t)jj;
-        const uint32_t e = find_event(b.hit_off, b.E, j);
-        const uint32_t *bk = b.bkt + (size_t)e * (nk + 1);
-        if (j >= bk[nk]) continue;
+    const float *lr = b.lrange + ((size_t)e * p.n_layers + Lk) * 4;
+    const bool disk = p.is_disk[Lk];
+    const float flo = disk ? lr[0] : lr[2], fhi = disk ? lr[1] : lr[3];
+    if (!(fhi >= flo)) return;                               // no hit on this layer
+    float lo = flo, hi = fhi;
+    if (cone_window(a.ar, a.az, hj.w, hj.z, disk, lr, p.tan_win, lo, hi)) {
+        lo = fmaxf(lo, flo);
+        hi = fminf(hi, fhi);
+        if (lo > hi) return;
+    }
+    const uint32_t fb0 = free_bin(lo, flo, fhi, p.nf), fb1 = free_bin(hi, flo, fhi, p.nf);
+    const int np2 = (int)p.np2;
+    const int pb0 = (int)floorf((phij - p.w_eps + kPiF2) * p.bins2_per_rad);
+    const int pb1 = (int)floorf((phij + p.w_eps + kPiF2) * p.bins2_per_rad);
+    const uint32_t *b2 = b.bkt2 + (size_t)e * (p.n_keys2 + 1);
+    for (uint32_t fb = fb0; fb <= fb1; ++fb) {
+        const uint32_t row = (Lk * p.nf + fb) * p.np2;
+        uint32_t r[4];
+        int nr;
+        if (pb1 - pb0 + 1 >= np2) {
+            r[0] = row; r[1] = row + np2; nr = 1;
+        } else if (pb0 < 0) {
+            r[0] = row + pb0 + np2; r[1] = row + np2; r[2] = row; r[3] = row + pb1 + 1; nr = 2;
+        } else if (pb1 >= np2) {
+            r[0] = row + pb0; r[1] = row + np2; r[2] = row; r[3] = row + pb1 - np2 + 1; nr = 2;
+        } else {
+            r[0] = row + pb0; r[1] = row + pb1 + 1; nr = 1;
+        }
+        for (int q = 0; q < nr; ++q)
+            for (uint32_t t = b2[r[2 * q]]; t < b2[r[2 * q + 1]]; ++t) f(b.zs[t]);
+    }
+}
+
+// One thread per cell A = (i, j): the out-cells (j, k) it can connect to have their outer hit k
+// inside the cone of r-z directions around A's direction, which the grid turns into a few rows.
+// Passes are counted first; cells with passes reserve their edge list with one atomic and look
+// up each out-cell's index (binary search among j's cells).
+__global__ void __launch_bounds__(256) k_connect(DevBatch b, DevParams p, uint32_t total)
+{
+    for (uint32_t A = blockIdx.x * blockDim.x + threadIdx.x; A < total;
+         A += gridDim.x * blockDim.x) {
+        const uint32_t e = find_event(b.cell_off, b.E, A);
+        const uint32_t c0 = b.cell_off[e];
+        const uint32_t ncell = min(b.cnt[C_CELLS * b.E + e], b.cell_off[e + 1] - c0);
+        if (A - c0 >= ncell) continue;
+        const uint32_t j = b.cell_out[A];
         const uint32_t Lj = b.hmeta[j] >> kLocalBits;
-        const uint32_t nin = p.n_in[Lj], nout = p.n_out[Lj];
-        if (nin == 0 || nout == 0) continue;
-        uint32_t sf[kMaxOut], sn[kMaxOut], nB = 0;
-        for (uint32_t s = 0; s < kMaxOut; ++s) {
-            sf[s] = s < nout ? b.out_first[(size_t)j * kMaxOut + s] : 0u;
-            sn[s] = s < nout ? b.out_n[(size_t)j * kMaxOut + s] : 0u;
-            nB += sn[s];
-        }
-        if (nB == 0) continue;
-        const float4 hj = b.hs[j];
+        const uint32_t nout = p.n_out[Lj];
+        if (nout == 0) continue;
+        const uint32_t i = b.cell_in[A];
+        const float4 hi = b.hs[i], hj = b.hs[j];
+        const RZ32 a = rz32(hi, hj);
+        const double na64 = p.cut_mode == CUT_FP64 ? b.cell_len64[A] : 0.0;
         const float phij = atan2f(hj.y, hj.x);
-        const bool staged = nB <= (uint32_t)kStage;
-        uint32_t n = 32, nzero = 0;
-        if (staged) {
-            while (n < nB) n <<= 1;
-            for (uint32_t t = lane; t < n; t += 32) {
-                if (t < nB) {
-                    uint32_t q = t, s = 0;
-                    while (q >= sn[s]) { q -= sn[s]; ++s; }
-                    const uint32_t B = sf[s] + q;
-                    const uint32_t k = b.cell_out[B];
-                    const float4 hk = b.hs[k];
-                    key[t] = dir_key(__fsub_rn(hk.w, hj.w), __fsub_rn(hk.z, hj.z));
-                    sB[t] = B;
-                    sK[t] = k;
-                } else {
-                    key[t] = kKeyPad;
-                    sB[t] = kNone;
-                    sK[t] = 0;
+        auto pass = [&](uint32_t k) {
+            const float4 hk = b.hs[k];
+            return doublet_test(b, p, j, hj, k) && triplet_test(b, p, i, j, k, hi, hj, hk, a, na64);
+        };
+        uint32_t npass = 0;
+        for (uint32_t s = 0; s < nout; ++s)
+            visit_cone(b, p, e, p.out_layer[Lj][s], a, hj, phij,
+                       [&](uint32_t k) { npass += pass(k); });
+        if (!npass) continue;
+        const uint32_t *bk = b.bkt + (size_t)e * (p.n_keys + 1);
+        const uint32_t base = atomicAdd(&b.cnt[C_EDGES * b.E + e], npass);
+        const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
+        const uint32_t nw = base >= cap ? 0u : min(npass, cap - base);
+        if (nw < npass) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+        const uint32_t first = b.edge_off[e] + base;
+        uint32_t written = 0;
+        for (uint32_t s = 0; s < nout; ++s) {
+            const uint32_t Lk = p.out_layer[Lj][s];
+            visit_cone(b, p, e, Lk, a, hj, phij, [&](uint32_t k) {
+                if (written < nw && pass(k)) {
+                    const uint32_t B = find_cell(b, p, bk, j, hj, s, Lk, k);
+                    if (B != kNone) b.nbr[first + written++] = B;
                 }
-            }
-            __syncwarp();
-            warp_bitonic(key, sB, sK, n, lane);
-            nzero = key_bound(key, 0, nB, -0.5f, false);
+            });
         }
-        for (uint32_t si = 0; si < nin; ++si) {
-            const uint32_t Li = p.in_layer[Lj][si];
-            const uint32_t slot_i = p.in_slot[Lj][si];
-            const Window w = phi_window(bk, Li, phij, p);
-            const uint32_t nc = w.size();
-            for (uint32_t c0 = 0; c0 < nc; c0 += 32) {
-                const uint32_t c = c0 + lane;
-                if (c >= nc) continue;
-                const uint32_t i = w.pos(c);
-                const float4 hi = b.hs[i];
-                if (!doublet_test(b, p, i, hi, j)) continue;
-                const RZ32 a = rz32(hi, hj);
-                const double na64 = p.cut_mode == CUT_FP64
-                                        ? seglen64(b.r64[i], (double)hi.z, b.r64[j], (double)hj.z)
-                                        : 0.0;
-                if (staged) {
-                    const float kA = dir_key(__fsub_rn(hj.w, hi.w), __fsub_rn(hj.z, hi.z));
-                    const Ranges R = key_ranges(key, nzero, nB, kA, p.key_halfwin);
-                    auto each = [&](auto &&f) {
-                        for (uint32_t q = R.a0; q < R.a1; ++q) f(q);
-                        for (uint32_t q = R.b0; q < R.b1; ++q) f(q);
-                        for (uint32_t q = R.c0; q < R.c1; ++q) f(q);
-                    };
-                    uint32_t npass = 0;
-                    each([&](uint32_t q) {
-                        npass += triplet_test(b, p, i, j, sK[q], hi, hj, a, na64, 0, sB[q]);
-                    });
-                    if (!npass) continue;
-                    const uint32_t A = find_cell(b, p, bk, i, hi, slot_i, Lj, j);
-                    if (A == kNone) continue;
-                    emit_edges(b, e, A, npass, [&](auto &&put) {
-                        each([&](uint32_t q) {
-                            if (triplet_test(b, p, i, j, sK[q], hi, hj, a, na64, A, sB[q]))
-                                put(sB[q]);
-                        });
-                    });
-                } else {
-                    // more out-cells than the stage holds: test them all from global memory
-                    auto each = [&](auto &&f) {
-                        for (uint32_t s = 0; s < nout; ++s)
-                            for (uint32_t B = sf[s]; B < sf[s] + sn[s]; ++B) f(B);
-                    };
-                    uint32_t npass = 0;
-                    each([&](uint32_t B) {
-                        npass += triplet_test(b, p, i, j, b.cell_out[B], hi, hj, a, na64, 0, B);
-                    });
-                    if (!npass) continue;
-                    const uint32_t A = find_cell(b, p, bk, i, hi, slot_i, Lj, j);
-                    if (A == kNone) continue;
-                    emit_edges(b, e, A, npass, [&](auto &&put) {
-                        each([&](uint32_t B) {
-                            if (triplet_test(b, p, i, j, b.cell_out[B], hi, hj, a, na64, A, B))
-                                put(B);
-                        });
-                    });
-                }
-            }
-        }
-        __syncwarp();
+        b.nbr_first[A] = first;
+        b.nbr_n[A] = written;
     }
 }
 
 void launch_connect(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
 {
-    (void)total;
-    uint64_t blocks = ((uint64_t)b.N + 7) / 8;
-    uint64_t cap = (uint64_t)sms * 8;
+    uint64_t blocks = ((uint64_t)total + 255) / 256;
+    uint64_t cap = (uint64_t)sms * 32;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
-    k_connect<<<(unsigned)blocks, 256, 0, s>>>(b, p);
+    k_connect<<<(unsigned)blocks, 256, 0, s>>>(b, p, total);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -50,6 +50,11 @@ struct DevParams {
     float theta32;                      // theta_cut rounded to float
     float dca32;                        // dca_cut rounded to float
     float key_halfwin;                  // r-z direction-key window: asin(theta_cut) + margin
+    float tan_win;                      // tan(asin(theta_cut)) (inf when theta_cut >= 1)
+    uint32_t nf;                        // grid bins along the free coordinate (z barrel, r disk)
+    uint32_t np2;                       // grid bins in phi
+    uint32_t n_keys2;                   // n_layers * nf * np2
+    float bins2_per_rad;                // np2 / (2 pi)
     double cw;                          // cos(w) as given by the caller
     double theta, dca;
     double bfield, sigma_rphi, sigma_z, x_over_x0;
@@ -70,6 +75,10 @@ struct DevBatch {
     float4 *hs;                         // [N] sorted hits: x, y, z, r (float)
     double *r64;                        // [N] sorted radii, FP64
     uint32_t *hmeta;                    // [N] layer << 24 | local caller index
+    // second index of the sorted hits: per layer, a grid over (free coordinate, phi)
+    float *lrange;                      // [E * n_layers * 4] r min, r max, z min, z max
+    uint32_t *bkt2;                     // [E * (n_keys2 + 1)] grid bucket starts
+    uint32_t *zs;                       // [N] grid order -> position in the phi order
     // cells, grouped by (inner hit, pair slot)
     uint32_t *out_first;                // [N * kMaxOut] first cell of (inner hit, slot)
     uint32_t *out_n;                    // [N * kMaxOut] number of cells
@@ -112,6 +121,7 @@ cudaError_t init_kernels();
 
 // Kernel launchers (defined in the .cu files).
 void launch_sort(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms);
+void launch_grid(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms);
 void launch_layer_count(const uint32_t *hit_off, const uint16_t *layer, uint32_t E,
                         uint32_t n_layers, uint32_t *counts, cudaStream_t s, int sms);
 void launch_doublets(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms);

@@ -149,6 +149,14 @@ static int check_params(const pxr_params *p, DevParams *d)
     // below never changes faster than the angle, so this (plus a margin far above the float
     // error of the key) is a conservative window.  t >= 1 keeps every candidate.
     d->key_halfwin = p->theta_cut < 1.0 ? (float)(std::asin(p->theta_cut) + 1e-4) : 4.0f;
+    d->tan_win = p->theta_cut < 0.99 ? (float)std::tan(std::asin(p->theta_cut) + 1e-5)
+                                     : INFINITY;
+    // grid of the second hit index: phi bins about the window width, free-coordinate bins so
+    // that the grid counters fit 32768 entries
+    d->np2 = 128;
+    d->nf = std::max(8u, std::min(64u, 32768u / (d->n_layers * d->np2)));
+    d->n_keys2 = d->n_layers * d->nf * d->np2;
+    d->bins2_per_rad = (float)(d->np2 / (2.0 * M_PI));
     d->cw = p->cos_phi_window;
     d->theta = p->theta_cut;
     d->dca = p->dca_cut;
@@ -208,14 +216,15 @@ struct Layout {
 struct PlanOffsets {
     // inputs (serving plans only) and small host-filled arrays come first: one H2D copy
     size_t x, y, z, layer, hit_off, cell_off, edge_off, tup_off, head_end;
-    size_t cnt, bkt, hs, r64, hmeta, out_first, out_n, cell_in, cell_out, cell_len64, nbr_first,
+    size_t cnt, bkt, hs, r64, hmeta, lrange, bkt2, zs, out_first, out_n, cell_in, cell_out,
+        cell_len64, nbr_first,
         nbr_n, nbr, mindepth, tup_hits, tup_n, tup_state, tup_first, tup_rank, out_evt, o_nh,
         o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status;
     size_t total;
 };
 
 static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, uint64_t T,
-                               uint32_t nk, bool with_inputs, bool fp64_cells)
+                               const DevParams &dp, bool with_inputs, bool fp64_cells)
 {
     Layout L;
     PlanOffsets o{};
@@ -230,10 +239,13 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.tup_off = L.add(4 * (E + 1));
     o.head_end = L.total;
     o.cnt = L.add(4 * (size_t)kCounters * E);
-    o.bkt = L.add(4 * (size_t)E * (nk + 1));
+    o.bkt = L.add(4 * (size_t)E * (dp.n_keys + 1));
     o.hs = L.add(16 * N);
     o.r64 = L.add(8 * N);
     o.hmeta = L.add(4 * N);
+    o.lrange = L.add(4 * (size_t)E * dp.n_layers * 4);
+    o.bkt2 = L.add(4 * (size_t)E * (dp.n_keys2 + 1));
+    o.zs = L.add(4 * N);
     o.out_first = L.add(4 * N * kMaxOut);
     o.out_n = L.add(4 * N * kMaxOut);
     o.cell_in = L.add(4 * C);
@@ -388,6 +400,9 @@ static void plan_bind(pxr_plan *P)
     b.hs = (float4 *)(r + o.hs);
     b.r64 = (double *)(r + o.r64);
     b.hmeta = (uint32_t *)(r + o.hmeta);
+    b.lrange = (float *)(r + o.lrange);
+    b.bkt2 = (uint32_t *)(r + o.bkt2);
+    b.zs = (uint32_t *)(r + o.zs);
     b.out_first = (uint32_t *)(r + o.out_first);
     b.out_n = (uint32_t *)(r + o.out_n);
     b.cell_in = (uint32_t *)(r + o.cell_in);
@@ -439,8 +454,7 @@ static int plan_size(pxr_plan *P, const uint32_t *lcount, bool with_inputs)
     P->C = C;
     P->G = G;
     P->T = T;
-    P->off = plan_layout(E, P->N, C, G, T, P->dp.n_keys, with_inputs,
-                         P->dp.cut_mode == CUT_FP64);
+    P->off = plan_layout(E, P->N, C, G, T, P->dp, with_inputs, P->dp.cut_mode == CUT_FP64);
     return PXR_OK;
 }
 
@@ -463,6 +477,7 @@ static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
     if (p.drop_suffixes) CK(cudaMemsetAsync(r + P->off.mindepth, 0xFF, 4 * P->C, s));
     CK(cudaMemsetAsync(r + P->off.nbr_n, 0, 4 * P->C, s));   // cells without edges stay at 0
     launch_sort(b, p, s, sms);
+    launch_grid(b, p, s, sms);
     if (t) CK(stage_mark(P->ev_stage[1], s, capturing));
     launch_doublets(b, p, s, sms);
     if (t) CK(stage_mark(P->ev_stage[2], s, capturing));
@@ -478,7 +493,7 @@ static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
     return PXR_OK;
 }
 
-static int plan_launches(const pxr_plan *) { return 7; }
+static int plan_launches(const pxr_plan *) { return 8; }
 
 static void plan_free(pxr_plan *P)
 {
@@ -886,7 +901,7 @@ static size_t event_bytes(const pxr_params &p, const DevParams &dp, const uint32
                           uint32_t n)
 {
     EventCaps c = event_caps(p, lcount, n);
-    PlanOffsets o = plan_layout(1, n, c.cells, c.edges, c.tuples, dp.n_keys, true,
+    PlanOffsets o = plan_layout(1, n, c.cells, c.edges, c.tuples, dp, true,
                                 p.cut_mode == PXR_CUT_FP64);
     return o.total + 64 * 256;  // alignment slack of the shared batch layout
 }
