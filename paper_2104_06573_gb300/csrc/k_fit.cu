@@ -233,11 +233,12 @@ __device__ __forceinline__ void fit_dispatch(int n, const float *X, const float 
     else fit_track<double, double, double, false>(n, X, Y, Z, L, p, o);
 }
 
-__global__ void __launch_bounds__(128) k_fit(DevBatch b, DevParams p, uint32_t total)
+__global__ void __launch_bounds__(256) k_fit(DevBatch b, DevParams p, uint32_t total)
 {
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += gridDim.x * blockDim.x) {
-        const uint32_t e = find_event(b.tup_off, b.E, t);
+    const uint32_t n_chunks = total / kChunk;
+    for (uint32_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+        const uint32_t t = ch * kChunk + threadIdx.x;
+        const uint32_t e = b.tup_chunk[ch];
         const uint32_t t0 = b.tup_off[e];
         const uint32_t nt = min(b.cnt[C_TUPLES * b.E + e], b.tup_off[e + 1] - t0);
         if (t - t0 >= nt) continue;
@@ -270,11 +271,11 @@ __global__ void __launch_bounds__(128) k_fit(DevBatch b, DevParams p, uint32_t t
 
 void launch_fit(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
 {
-    uint64_t blocks = ((uint64_t)total + 127) / 128;
+    uint64_t blocks = total / kChunk;
     uint64_t cap = (uint64_t)sms * 16;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
-    k_fit<<<(unsigned)blocks, 128, 0, s>>>(b, p, total);
+    k_fit<<<(unsigned)blocks, kChunk, 0, s>>>(b, p, total);
 }
 
 // Fit-only path: m ntuplets given directly.

@@ -71,14 +71,14 @@ __global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint3
     const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (; item < n_items; item += stride) {
         const uint32_t g = (uint32_t)(item / slots), slot = (uint32_t)(item % slots);
-        const uint32_t e = find_event(b.hit_off, b.E, g);
+        const uint32_t e = hit_event(b, g);
         const uint32_t *bk = b.bkt + (size_t)e * (nk + 1);
         if (g >= bk[nk]) continue;                       // hit rejected by the sort (bad layer)
         const uint32_t L = b.hmeta[g] >> kLocalBits;
         if (slot >= p.n_out[L]) continue;
         const uint32_t Lo = p.out_layer[L][slot];
         const float4 hi = b.hs[g];
-        const Window w = phi_window(bk, Lo, atan2f(hi.y, hi.x), p);
+        const Window w = phi_window(bk, Lo, b.hphi[g], p);
         const uint32_t nc = w.size();
 
         uint32_t masks[kMaxIt];
@@ -199,7 +199,7 @@ __device__ __forceinline__ uint32_t find_cell(const DevBatch &b, const DevParams
                                               const uint32_t *bk, uint32_t i, float4 hi,
                                               uint32_t slot, uint32_t Lj, uint32_t j)
 {
-    const Window w = phi_window(bk, Lj, atan2f(hi.y, hi.x), p);
+    const Window w = phi_window(bk, Lj, b.hphi[i], p);
     auto rank = [&](uint32_t pos) {
         return (pos >= w.r0 && pos < w.r0 + w.n1) ? pos - w.r0 : w.n1 + (pos - w.r2);
     };
@@ -231,10 +231,11 @@ __device__ __forceinline__ bool cone_window(float ar, float az, float rj, float 
     dlo -= 1e-4f + 1e-5f * fabsf(dlo);
     dhi += 1e-4f + 1e-5f * fabsf(dhi);
     if (!(fabsf(u) > 1e-20f) || !(T < 1e30f)) return false;
-    const float m = v / u;
+    // approximate divisions: their ~2 ulp errors are far inside the margin below
+    const float m = __fdividef(v, u);
     const float den_hi = 1.f - m * T, den_lo = 1.f + m * T;
     if (!(den_hi > 1e-4f) || !(den_lo > 1e-4f)) return false;
-    const float s_hi = (m + T) / den_hi, s_lo = (m - T) / den_lo;
+    const float s_hi = __fdividef(m + T, den_hi), s_lo = __fdividef(m - T, den_lo);
     const float c1 = dlo * s_lo, c2 = dlo * s_hi, c3 = dhi * s_lo, c4 = dhi * s_hi;
     lo = base + fminf(fminf(c1, c2), fminf(c3, c4));
     hi = base + fmaxf(fmaxf(c1, c2), fmaxf(c3, c4));
@@ -246,11 +247,10 @@ __device__ __forceinline__ bool cone_window(float ar, float az, float rj, float 
     return true;
 }
 
-__device__ __forceinline__ uint32_t free_bin(float v, float lo, float hi, uint32_t nf)
+// The grid's bin of a free-coordinate value (the same expression the grid was built with).
+__device__ __forceinline__ uint32_t free_bin(float v, float lo, float scale, uint32_t nf)
 {
-    if (!(hi > lo)) return 0;
-    const float t = floorf((v - lo) * ((float)nf / (hi - lo)));
-    const int b = (int)t;
+    const int b = (int)floorf((v - lo) * scale);
     return (uint32_t)(b < 0 ? 0 : (b >= (int)nf ? (int)nf - 1 : b));
 }
 
@@ -261,7 +261,7 @@ __device__ __forceinline__ void visit_cone(const DevBatch &b, const DevParams &p
                                            uint32_t Lk, const RZ32 &a, float4 hj, float phij,
                                            F &&f)
 {
-    const float *lr = b.lrange + ((size_t)e * p.n_layers + Lk) * 4;
+    const float *lr = b.lrange + ((size_t)e * p.n_layers + Lk) * kLr;
     const bool disk = p.is_disk[Lk];
     const float flo = disk ? lr[0] : lr[2], fhi = disk ? lr[1] : lr[3];
     if (!(fhi >= flo)) return;                               // no hit on this layer
@@ -271,7 +271,7 @@ __device__ __forceinline__ void visit_cone(const DevBatch &b, const DevParams &p
         hi = fminf(hi, fhi);
         if (lo > hi) return;
     }
-    const uint32_t fb0 = free_bin(lo, flo, fhi, p.nf), fb1 = free_bin(hi, flo, fhi, p.nf);
+    const uint32_t fb0 = free_bin(lo, lr[4], lr[5], p.nf), fb1 = free_bin(hi, lr[4], lr[5], p.nf);
     const int np2 = (int)p.np2;
     const int pb0 = (int)floorf((phij - p.w_eps + kPiF2) * p.bins2_per_rad);
     const int pb1 = (int)floorf((phij + p.w_eps + kPiF2) * p.bins2_per_rad);
@@ -298,11 +298,12 @@ __device__ __forceinline__ void visit_cone(const DevBatch &b, const DevParams &p
 // inside the cone of r-z directions around A's direction, which the grid turns into a few rows.
 // Passes are counted first; cells with passes reserve their edge list with one atomic and look
 // up each out-cell's index (binary search among j's cells).
-__global__ void __launch_bounds__(256) k_connect(DevBatch b, DevParams p, uint32_t total)
+__global__ void __launch_bounds__(256, 3) k_connect(DevBatch b, DevParams p, uint32_t total)
 {
-    for (uint32_t A = blockIdx.x * blockDim.x + threadIdx.x; A < total;
-         A += gridDim.x * blockDim.x) {
-        const uint32_t e = find_event(b.cell_off, b.E, A);
+    const uint32_t n_chunks = total / kChunk;
+    for (uint32_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+        const uint32_t A = ch * kChunk + threadIdx.x;
+        const uint32_t e = b.cell_chunk[ch];
         const uint32_t c0 = b.cell_off[e];
         const uint32_t ncell = min(b.cnt[C_CELLS * b.E + e], b.cell_off[e + 1] - c0);
         if (A - c0 >= ncell) continue;
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(256) k_connect(DevBatch b, DevParams p, uint32
         const float4 hi = b.hs[i], hj = b.hs[j];
         const RZ32 a = rz32(hi, hj);
         const double na64 = p.cut_mode == CUT_FP64 ? b.cell_len64[A] : 0.0;
-        const float phij = atan2f(hj.y, hj.x);
+        const float phij = b.hphi[j];
         auto pass = [&](uint32_t k) {
             const float4 hk = b.hs[k];
             return doublet_test(b, p, j, hj, k) && triplet_test(b, p, i, j, k, hi, hj, hk, a, na64);
@@ -347,8 +348,8 @@ __global__ void __launch_bounds__(256) k_connect(DevBatch b, DevParams p, uint32
 
 void launch_connect(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
 {
-    uint64_t blocks = ((uint64_t)total + 255) / 256;
-    uint64_t cap = (uint64_t)sms * 32;
+    uint64_t blocks = total / kChunk;
+    uint64_t cap = (uint64_t)sms * 24;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
     k_connect<<<(unsigned)blocks, 256, 0, s>>>(b, p, total);
@@ -359,9 +360,10 @@ void launch_connect(const DevBatch &b, const DevParams &p, uint32_t total, cudaS
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_ntuplets(DevBatch b, DevParams p, uint32_t total)
 {
-    for (uint32_t A = blockIdx.x * blockDim.x + threadIdx.x; A < total;
-         A += gridDim.x * blockDim.x) {
-        const uint32_t e = find_event(b.cell_off, b.E, A);
+    const uint32_t n_chunks = total / kChunk;
+    for (uint32_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+        const uint32_t A = ch * kChunk + threadIdx.x;
+        const uint32_t e = b.cell_chunk[ch];
         const uint32_t c0 = b.cell_off[e];
         const uint32_t ncell = min(b.cnt[C_CELLS * b.E + e], b.cell_off[e + 1] - c0);
         if (A - c0 >= ncell) continue;
@@ -412,7 +414,7 @@ __global__ void __launch_bounds__(256) k_ntuplets(DevBatch b, DevParams p, uint3
 
 void launch_ntuplets(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
 {
-    uint64_t blocks = ((uint64_t)total + 255) / 256;
+    uint64_t blocks = total / kChunk;
     uint64_t cap = (uint64_t)sms * 32;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
@@ -425,9 +427,10 @@ void launch_ntuplets(const DevBatch &b, const DevParams &p, uint32_t total, cuda
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_select(DevBatch b, DevParams p, uint32_t total)
 {
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += gridDim.x * blockDim.x) {
-        const uint32_t e = find_event(b.tup_off, b.E, t);
+    const uint32_t n_chunks = total / kChunk;
+    for (uint32_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+        const uint32_t t = ch * kChunk + threadIdx.x;
+        const uint32_t e = b.tup_chunk[ch];
         const uint32_t t0 = b.tup_off[e];
         const uint32_t nt = min(b.cnt[C_TUPLES * b.E + e], b.tup_off[e + 1] - t0);
         if (t - t0 >= nt) continue;
@@ -442,7 +445,7 @@ __global__ void __launch_bounds__(256) k_select(DevBatch b, DevParams p, uint32_
 
 void launch_select(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
 {
-    uint64_t blocks = ((uint64_t)total + 255) / 256;
+    uint64_t blocks = total / kChunk;
     uint64_t cap = (uint64_t)sms * 16;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;

@@ -14,9 +14,9 @@ namespace pxr {
 
 constexpr float kPiF = 3.14159265358979f;
 
-__device__ __forceinline__ uint32_t phi_bin(float x, float y, const DevParams &p)
+__device__ __forceinline__ uint32_t phi_bin(float phi, const DevParams &p)
 {
-    float t = floorf((atan2f(y, x) + kPiF) * p.bins_per_rad);
+    float t = floorf((phi + kPiF) * p.bins_per_rad);
     int b = (int)t;
     b = b < 0 ? 0 : b;
     return (uint32_t)(b >= (int)p.nb ? (int)p.nb - 1 : b);
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(512) k_sort(DevBatch b, DevParams p)
             uint32_t g = h0 + h;
             uint32_t L = b.layer[g];
             if (L >= p.n_layers) { bad = true; continue; }
-            atomicAdd(&s_cnt[L * p.nb + phi_bin(b.x[g], b.y[g], p)], 1u);
+            atomicAdd(&s_cnt[L * p.nb + phi_bin(atan2f(b.y[g], b.x[g]), p)], 1u);
         }
         if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_LAYER);
         uint32_t total = block_exclusive_scan(s_cnt, nk, s_warp);
@@ -88,11 +88,13 @@ __global__ void __launch_bounds__(512) k_sort(DevBatch b, DevParams p)
             uint32_t L = b.layer[g];
             if (L >= p.n_layers) continue;
             float x = b.x[g], y = b.y[g], z = b.z[g];
-            uint32_t pos = h0 + atomicAdd(&s_cnt[L * p.nb + phi_bin(x, y, p)], 1u);
+            const float phi = atan2f(y, x);
+            uint32_t pos = h0 + atomicAdd(&s_cnt[L * p.nb + phi_bin(phi, p)], 1u);
             double r = radius64((double)x, (double)y);
             b.hs[pos] = make_float4(x, y, z, __double2float_rn(r));
             b.r64[pos] = r;
             b.hmeta[pos] = (L << kLocalBits) | h;
+            b.hphi[pos] = phi;
         }
         __syncthreads();
     }
@@ -110,21 +112,18 @@ __device__ __forceinline__ float o2f(int i) { return __int_as_float(i >= 0 ? i :
 // the free coordinate is z on barrel layers and r on disks, binned over the layer's actual range
 // in this event.  zs lists, bucket by bucket, the positions of the hits in the phi order.  The CA
 // stage looks up the few grid rows that an in-cell's r-z direction can reach.
-__device__ __forceinline__ uint32_t grid_bin_free(float v, float lo, float hi, uint32_t nf)
+__device__ __forceinline__ uint32_t grid_bin_free(float v, float lo, float scale, uint32_t nf)
 {
-    if (!(hi > lo)) return 0;
-    const float t = floorf((v - lo) * ((float)nf / (hi - lo)));
-    const int b = (int)t;
+    const int b = (int)floorf((v - lo) * scale);
     return (uint32_t)(b < 0 ? 0 : (b >= (int)nf ? (int)nf - 1 : b));
 }
 
-__device__ __forceinline__ uint32_t grid_key(float4 h, uint32_t L, const float *lr,
+__device__ __forceinline__ uint32_t grid_key(float4 h, float phi, uint32_t L, const float *lr,
                                              const DevParams &p)
 {
     const bool disk = p.is_disk[L];
-    const uint32_t fb = grid_bin_free(disk ? h.w : h.z, lr[L * 4 + (disk ? 0 : 2)],
-                                      lr[L * 4 + (disk ? 1 : 3)], p.nf);
-    int pb = (int)floorf((atan2f(h.y, h.x) + kPiF) * p.bins2_per_rad);
+    const uint32_t fb = grid_bin_free(disk ? h.w : h.z, lr[L * kLr + 4], lr[L * kLr + 5], p.nf);
+    int pb = (int)floorf((phi + kPiF) * p.bins2_per_rad);
     pb = pb < 0 ? 0 : (pb >= (int)p.np2 ? (int)p.np2 - 1 : pb);
     return (L * p.nf + fb) * p.np2 + (uint32_t)pb;
 }
@@ -133,7 +132,7 @@ __global__ void __launch_bounds__(512) k_grid(DevBatch b, DevParams p)
 {
     extern __shared__ uint32_t s_c2[];
     __shared__ int s_rng[kMaxLayers * 4];
-    __shared__ float s_lr[kMaxLayers * 4];
+    __shared__ float s_lr[kMaxLayers * kLr];
     __shared__ uint32_t s_warp[32];
     const uint32_t nk = p.n_keys, nk2 = p.n_keys2, nl = p.n_layers;
     for (uint32_t e = blockIdx.x; e < b.E; e += gridDim.x) {
@@ -152,13 +151,19 @@ __global__ void __launch_bounds__(512) k_grid(DevBatch b, DevParams p)
             atomicMax(&s_rng[L * 4 + 3], f2o(h.z));
         }
         __syncthreads();
-        for (uint32_t k = threadIdx.x; k < nl * 4; k += blockDim.x) {
-            s_lr[k] = o2f(s_rng[k]);
-            b.lrange[(size_t)e * nl * 4 + k] = s_lr[k];
+        for (uint32_t L = threadIdx.x; L < nl; L += blockDim.x) {
+            float *o = s_lr + L * kLr;
+            for (int k = 0; k < 4; ++k) o[k] = o2f(s_rng[L * 4 + k]);
+            // free coordinate: r on disks, z on barrel layers
+            const float lo = p.is_disk[L] ? o[0] : o[2], hi = p.is_disk[L] ? o[1] : o[3];
+            o[4] = lo;
+            o[5] = hi > lo ? (float)p.nf / (hi - lo) : 0.f;
+            for (int k = 0; k < kLr; ++k) b.lrange[((size_t)e * nl + L) * kLr + k] = o[k];
         }
         __syncthreads();
         for (uint32_t pos = h0 + threadIdx.x; pos < hend; pos += blockDim.x)
-            atomicAdd(&s_c2[grid_key(b.hs[pos], b.hmeta[pos] >> kLocalBits, s_lr, p)], 1u);
+            atomicAdd(&s_c2[grid_key(b.hs[pos], b.hphi[pos], b.hmeta[pos] >> kLocalBits, s_lr, p)],
+                      1u);
         __syncthreads();
         const uint32_t total = block_exclusive_scan(s_c2, nk2, s_warp);
         uint32_t *b2 = b.bkt2 + (size_t)e * (nk2 + 1);
@@ -166,7 +171,8 @@ __global__ void __launch_bounds__(512) k_grid(DevBatch b, DevParams p)
         if (threadIdx.x == 0) b2[nk2] = h0 + total;
         __syncthreads();
         for (uint32_t pos = h0 + threadIdx.x; pos < hend; pos += blockDim.x) {
-            const uint32_t key = grid_key(b.hs[pos], b.hmeta[pos] >> kLocalBits, s_lr, p);
+            const uint32_t key =
+                grid_key(b.hs[pos], b.hphi[pos], b.hmeta[pos] >> kLocalBits, s_lr, p);
             b.zs[h0 + atomicAdd(&s_c2[key], 1u)] = pos;
         }
         __syncthreads();

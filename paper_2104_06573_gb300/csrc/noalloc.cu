@@ -35,7 +35,9 @@ constexpr size_t kNaMeta = na_align(kNaR64 + 8 * (size_t)kNaMaxHits);    // hits
 constexpr size_t kNaFirst = na_align(kNaMeta + 4 * (size_t)kNaMaxHits);  // hits x 4 x u32
 constexpr size_t kNaN = na_align(kNaFirst + 16 * (size_t)kNaMaxHits);    // hits x 4 x u32
 constexpr size_t kNaLen = na_align(kNaN + 16 * (size_t)kNaMaxHits);      // cells x double
-constexpr size_t kNaBytes = na_align(kNaLen + 8 * (size_t)kNaMaxCells);  // ~12.6 MB
+constexpr size_t kNaPhi = na_align(kNaLen + 8 * (size_t)kNaMaxCells);    // hits x float
+constexpr size_t kNaHitChunk = na_align(kNaPhi + 4 * (size_t)kNaMaxHits); // hit chunks x u32
+constexpr size_t kNaBytes = na_align(kNaHitChunk + 4 * (size_t)(kNaMaxHits / kHitChunk));  // ~13 MB
 
 static __device__ __align__(256) unsigned char g_scratch[kNaBytes];
 
@@ -66,6 +68,9 @@ __global__ void k_na_init(uint32_t n_hits, uint32_t cap)
         cell_off[1] = cap;
     }
     if (threadIdx.x < kCounters) cnt[threadIdx.x] = 0;
+    // one event: every hit chunk belongs to event 0
+    uint32_t *hc = reinterpret_cast<uint32_t *>(g_scratch + kNaHitChunk);
+    for (uint32_t c = threadIdx.x; c < kNaMaxHits / kHitChunk; c += blockDim.x) hc[c] = 0;
 }
 
 // Copy the cell count (and the overflow flag) to the caller.
@@ -148,6 +153,8 @@ extern "C" int pxr_doublets_noalloc(const float *x, const float *y, const float 
     b.cell_in = cells_inner;
     b.cell_out = cells_outer;
     b.cell_len64 = reinterpret_cast<double *>(base + kNaLen);
+    b.hphi = reinterpret_cast<float *>(base + kNaPhi);
+    b.hit_chunk = reinterpret_cast<const uint32_t *>(base + kNaHitChunk);
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     k_na_init<<<1, 32, 0, s>>>(n_hits, cap);

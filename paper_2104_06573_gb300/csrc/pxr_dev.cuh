@@ -20,6 +20,9 @@ constexpr int kMaxOut = 4;       // layer pairs sharing one inner layer
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr int kLocalBits = 24;   // hmeta = layer << 24 | index of the hit inside its event
 constexpr uint32_t kLocalMask = (1u << kLocalBits) - 1u;
+constexpr uint32_t kChunk = 256;     // per-event cell / ntuplet capacities are multiples of this
+constexpr uint32_t kHitChunk = 32;   // granularity of the hit -> event table
+constexpr int kLr = 6;               // per-layer range record: r min/max, z min/max, free lo/scale
 
 // Per-event counters, laid out as kCounters consecutive arrays of E words.
 enum Counter : int { C_CELLS = 0, C_EDGES = 1, C_TUPLES = 2, C_FLAGS = 3, C_OUT = 4, kCounters = 5 };
@@ -75,8 +78,12 @@ struct DevBatch {
     float4 *hs;                         // [N] sorted hits: x, y, z, r (float)
     double *r64;                        // [N] sorted radii, FP64
     uint32_t *hmeta;                    // [N] layer << 24 | local caller index
+    float *hphi;                        // [N] atan2f(y, x) of the sorted hits (the binned value)
+    // event of a work chunk: cells and ntuplets by 256-entry chunk, hits by 32-hit chunk (first
+    // event of the chunk)
+    const uint32_t *cell_chunk, *tup_chunk, *hit_chunk;
     // second index of the sorted hits: per layer, a grid over (free coordinate, phi)
-    float *lrange;                      // [E * n_layers * 4] r min, r max, z min, z max
+    float *lrange;                      // [E * n_layers * kLr] r min/max, z min/max, free lo/scale
     uint32_t *bkt2;                     // [E * (n_keys2 + 1)] grid bucket starts
     uint32_t *zs;                       // [N] grid order -> position in the phi order
     // cells, grouped by (inner hit, pair slot)
@@ -103,6 +110,14 @@ struct DevBatch {
     double *o_pt, *o_phi, *o_cot, *o_dxy, *o_dz, *o_chi2;
     int8_t *o_q, *o_status;
 };
+
+// Event of hit g: the chunk table gives the event of the chunk's first hit.
+__device__ __forceinline__ uint32_t hit_event(const DevBatch &b, uint32_t g)
+{
+    uint32_t e = b.hit_chunk[g / kHitChunk];
+    while (e + 1 < b.E && g >= b.hit_off[e + 1]) ++e;
+    return e;
+}
 
 // Largest e with off[e] <= t (off non-decreasing, off[0] = 0, t < off[E]).
 __device__ __forceinline__ uint32_t find_event(const uint32_t *__restrict__ off, uint32_t E,

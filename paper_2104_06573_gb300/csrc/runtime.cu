@@ -196,8 +196,9 @@ static EventCaps event_caps(const pxr_params &p, const uint32_t *lcount, uint32_
     double edges = std::ceil(0.08 * cells) + 4.0 * n + 256.0;
     double tuples = p.max_tuples_per_event ? (double)p.max_tuples_per_event
                                            : std::ceil(0.5 * edges) + 2.0 * n + 256.0;
-    return EventCaps{(uint32_t)cells, (uint32_t)std::min(edges, 1.0e9),
-                     (uint32_t)std::min(tuples, 1.0e9)};
+    // cells and ntuplets in whole chunks: every chunk of the work loops belongs to one event
+    auto up = [](double v) { return (uint32_t)(std::ceil(v / kChunk) * kChunk); };
+    return EventCaps{up(cells), (uint32_t)std::min(edges, 1.0e9), up(std::min(tuples, 1.0e9))};
 }
 
 // ------------------------------------------------------------------------------------------
@@ -215,8 +216,9 @@ struct Layout {
 
 struct PlanOffsets {
     // inputs (serving plans only) and small host-filled arrays come first: one H2D copy
-    size_t x, y, z, layer, hit_off, cell_off, edge_off, tup_off, head_end;
-    size_t cnt, bkt, hs, r64, hmeta, lrange, bkt2, zs, out_first, out_n, cell_in, cell_out,
+    size_t x, y, z, layer, hit_off, cell_off, edge_off, tup_off, cell_chunk, tup_chunk, hit_chunk,
+        head_end;
+    size_t cnt, bkt, hs, r64, hmeta, hphi, lrange, bkt2, zs, out_first, out_n, cell_in, cell_out,
         cell_len64, nbr_first,
         nbr_n, nbr, mindepth, tup_hits, tup_n, tup_state, tup_first, tup_rank, out_evt, o_nh,
         o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status;
@@ -237,13 +239,17 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.cell_off = L.add(4 * (E + 1));
     o.edge_off = L.add(4 * (E + 1));
     o.tup_off = L.add(4 * (E + 1));
+    o.cell_chunk = L.add(4 * (C / kChunk));
+    o.tup_chunk = L.add(4 * (T / kChunk));
+    o.hit_chunk = L.add(4 * ((N + kHitChunk - 1) / kHitChunk));
     o.head_end = L.total;
     o.cnt = L.add(4 * (size_t)kCounters * E);
     o.bkt = L.add(4 * (size_t)E * (dp.n_keys + 1));
     o.hs = L.add(16 * N);
     o.r64 = L.add(8 * N);
     o.hmeta = L.add(4 * N);
-    o.lrange = L.add(4 * (size_t)E * dp.n_layers * 4);
+    o.hphi = L.add(4 * N);
+    o.lrange = L.add(4 * (size_t)E * dp.n_layers * kLr);
     o.bkt2 = L.add(4 * (size_t)E * (dp.n_keys2 + 1));
     o.zs = L.add(4 * N);
     o.out_first = L.add(4 * N * kMaxOut);
@@ -365,6 +371,7 @@ struct pxr_plan {
     uint32_t E = 0;
     uint64_t N = 0, C = 0, G = 0, T = 0;
     std::vector<uint32_t> hit_off, cell_off, edge_off, tup_off;
+    std::vector<uint32_t> cell_chunk, tup_chunk, hit_chunk;   // event of each work chunk
     PlanOffsets off{};
     char *region = nullptr;
     DevBatch db{};
@@ -400,6 +407,10 @@ static void plan_bind(pxr_plan *P)
     b.hs = (float4 *)(r + o.hs);
     b.r64 = (double *)(r + o.r64);
     b.hmeta = (uint32_t *)(r + o.hmeta);
+    b.hphi = (float *)(r + o.hphi);
+    b.cell_chunk = (const uint32_t *)(r + o.cell_chunk);
+    b.tup_chunk = (const uint32_t *)(r + o.tup_chunk);
+    b.hit_chunk = (const uint32_t *)(r + o.hit_chunk);
     b.lrange = (float *)(r + o.lrange);
     b.bkt2 = (uint32_t *)(r + o.bkt2);
     b.zs = (uint32_t *)(r + o.zs);
@@ -454,6 +465,20 @@ static int plan_size(pxr_plan *P, const uint32_t *lcount, bool with_inputs)
     P->C = C;
     P->G = G;
     P->T = T;
+    P->cell_chunk.assign(C / kChunk, 0);
+    P->tup_chunk.assign(T / kChunk, 0);
+    P->hit_chunk.assign((P->N + kHitChunk - 1) / kHitChunk, 0);
+    for (uint32_t e = 0; e < E; ++e) {
+        for (uint32_t c = P->cell_off[e] / kChunk; c < P->cell_off[e + 1] / kChunk; ++c)
+            P->cell_chunk[c] = e;
+        for (uint32_t c = P->tup_off[e] / kChunk; c < P->tup_off[e + 1] / kChunk; ++c)
+            P->tup_chunk[c] = e;
+    }
+    for (size_t c = 0, e = 0; c < P->hit_chunk.size(); ++c) {
+        const uint64_t g = (uint64_t)c * kHitChunk;
+        while (e + 1 < E && g >= P->hit_off[e + 1]) ++e;
+        P->hit_chunk[c] = (uint32_t)e;
+    }
     P->off = plan_layout(E, P->N, C, G, T, P->dp, with_inputs, P->dp.cut_mode == CUT_FP64);
     return PXR_OK;
 }
@@ -463,6 +488,14 @@ static cudaError_t stage_mark(cudaEvent_t ev, cudaStream_t s, bool capturing)
 {
     return capturing ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
                      : cudaEventRecord(ev, s);
+}
+
+// Copy the chunk tables into a host image of the plan's head region.
+static void fill_chunks(const pxr_plan *P, char *head)
+{
+    std::memcpy(head + P->off.cell_chunk, P->cell_chunk.data(), 4 * P->cell_chunk.size());
+    std::memcpy(head + P->off.tup_chunk, P->tup_chunk.data(), 4 * P->tup_chunk.size());
+    std::memcpy(head + P->off.hit_chunk, P->hit_chunk.data(), 4 * P->hit_chunk.size());
 }
 
 static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
@@ -584,6 +617,7 @@ extern "C" int pxr_plan_create(pxr_ctx *ctx, uint32_t n_events, const uint32_t *
         std::memcpy(head.data() + P->off.cell_off, P->cell_off.data(), e1);
         std::memcpy(head.data() + P->off.edge_off, P->edge_off.data(), e1);
         std::memcpy(head.data() + P->off.tup_off, P->tup_off.data(), e1);
+        fill_chunks(P.get(), head.data());
         size_t a = P->off.hit_off;
         CK(cudaMemcpyAsync(P->region + a, head.data() + a, P->off.head_end - a,
                            cudaMemcpyHostToDevice, s));
@@ -961,6 +995,7 @@ static int launch_batch(pxr_ctx *ctx, std::vector<std::shared_ptr<Ticket>> &item
     std::memcpy(h + P->off.cell_off, P->cell_off.data(), e1);
     std::memcpy(h + P->off.edge_off, P->edge_off.data(), e1);
     std::memcpy(h + P->off.tup_off, P->tup_off.data(), e1);
+    fill_chunks(P, h);
     cudaStream_t s = slot_stream(ctx, slot);
     B->stream = s;
     CK(cudaMemcpyAsync(P->region, h, P->off.head_end, cudaMemcpyHostToDevice, s));
