@@ -118,8 +118,10 @@ typedef struct pxr_params {
     double sigma_rphi, sigma_z;                /* cm, > 0 */
     double x_over_x0;                          /* radiation lengths per layer, >= 1e-6 */
     uint32_t n_phi_bins;                       /* phi bins per layer, 64..2048; 0 = automatic */
-    uint32_t max_cells_per_event;              /* 0 = sized from the hit counts */
-    uint32_t max_tuples_per_event;             /* 0 = sized from the hit counts */
+    uint32_t max_cells_per_event;              /* 0 = sized from the hit counts; rounded up to a
+                                                  multiple of 256 */
+    uint32_t max_tuples_per_event;             /* 0 = sized from the hit counts; rounded up to a
+                                                  multiple of 256 */
 } pxr_params;
 
 /* Context configuration. */

@@ -175,12 +175,15 @@ def test_overflow_is_flagged_not_written(ctx):
     P = synth.params_barrel_quadruplets()
     ev = ev_tuple(synth.event_barrel(0))
     ok = ev_tuple(synth.event_barrel(1))
+    # capacities are whole 256-cell chunks: 50 becomes 256, still below the ~770 cells
     got = run_plan(ctx, [ev, ok], P, pxr.CUT_FP32, max_cells=50)
     assert got[0]["tracks"]["status"] == pxr.EOVERFLOW
-    assert len(got[0]["cells"]) == 50
+    assert len(got[0]["cells"]) == 256
     full = run_plan(ctx, [ok], P, pxr.CUT_FP32)[0]
-    assert got[1]["tracks"]["status"] == pxr.EOVERFLOW     # 50 is also too small for event 1
-    assert len(full["cells"]) > 50
+    assert got[1]["tracks"]["status"] == pxr.EOVERFLOW     # also too small for event 1
+    assert len(full["cells"]) > 256
+    # the truncated cells are a subset of the full set
+    assert {tuple(c) for c in got[1]["cells"].tolist()} <= {tuple(c) for c in full["cells"].tolist()}
 
 
 @pytest.mark.parametrize("cut", [pxr.CUT_FP64, pxr.CUT_FP32])
