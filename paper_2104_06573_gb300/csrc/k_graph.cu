@@ -294,52 +294,203 @@ __device__ __forceinline__ void visit_cone(const DevBatch &b, const DevParams &p
     }
 }
 
-// One thread per cell A = (i, j): the out-cells (j, k) it can connect to have their outer hit k
-// inside the cone of r-z directions around A's direction, which the grid turns into a few rows.
-// Passes are counted first; cells with passes reserve their edge list with one atomic and look
-// up each out-cell's index (binary search among j's cells).
-__global__ void __launch_bounds__(256, 3) k_connect(DevBatch b, DevParams p, uint32_t total)
+// Grid ranges of one in-cell's cone: for every out-layer slot, the grid rows the cone reaches
+// and the one or two phi runs of each row.  Calls f(slot, first, count) for each non-empty range.
+template <typename F>
+__device__ __forceinline__ void cone_ranges(const DevBatch &b, const DevParams &p, uint32_t e,
+                                            uint32_t Lj, const RZ32 &a, float4 hj, float phij,
+                                            F &&f)
 {
+    const uint32_t *b2 = b.bkt2 + (size_t)e * (p.n_keys2 + 1);
+    const int np2 = (int)p.np2;
+    const int pb0 = (int)floorf((phij - p.w_eps + kPiF2) * p.bins2_per_rad);
+    const int pb1 = (int)floorf((phij + p.w_eps + kPiF2) * p.bins2_per_rad);
+    for (uint32_t s = 0; s < p.n_out[Lj]; ++s) {
+        const uint32_t Lk = p.out_layer[Lj][s];
+        const float *lr = b.lrange + ((size_t)e * p.n_layers + Lk) * kLr;
+        const bool disk = p.is_disk[Lk];
+        const float flo = disk ? lr[0] : lr[2], fhi = disk ? lr[1] : lr[3];
+        if (!(fhi >= flo)) continue;                             // no hit on this layer
+        float lo = flo, hi = fhi;
+        if (cone_window(a.ar, a.az, hj.w, hj.z, disk, lr, p.tan_win, lo, hi)) {
+            lo = fmaxf(lo, flo);
+            hi = fminf(hi, fhi);
+            if (lo > hi) continue;
+        }
+        const uint32_t fb0 = free_bin(lo, lr[4], lr[5], p.nf), fb1 = free_bin(hi, lr[4], lr[5], p.nf);
+        for (uint32_t fb = fb0; fb <= fb1; ++fb) {
+            const uint32_t row = (Lk * p.nf + fb) * p.np2;
+            uint32_t r[4];
+            int nr;
+            if (pb1 - pb0 + 1 >= np2) {
+                r[0] = row; r[1] = row + np2; nr = 1;
+            } else if (pb0 < 0) {
+                r[0] = row + pb0 + np2; r[1] = row + np2; r[2] = row; r[3] = row + pb1 + 1; nr = 2;
+            } else if (pb1 >= np2) {
+                r[0] = row + pb0; r[1] = row + np2; r[2] = row; r[3] = row + pb1 - np2 + 1; nr = 2;
+            } else {
+                r[0] = row + pb0; r[1] = row + pb1 + 1; nr = 1;
+            }
+            for (int q = 0; q < nr; ++q) {
+                const uint32_t t0 = b2[r[2 * q]], t1 = b2[r[2 * q + 1]];
+                if (t1 > t0) f(s, t0, t1 - t0);
+            }
+        }
+    }
+}
+
+constexpr int kConnWarps = 8;
+constexpr int kMaxR = 6;       // candidate ranges kept per in-cell (more: sequential path)
+constexpr int kPass = 96;      // passing triplets kept per warp round (more: sequential path)
+
+// One warp per 32 consecutive cells A = (i, j).  Each lane sets up its cell and collects the
+// grid ranges its cone reaches; the warp then tests all lanes' candidates together, 32 at a
+// time, so that lanes with many and lanes with no candidates do not diverge.  Passing triplets
+// go to a per-warp list; every cell with passes reserves its edge list with one atomic and looks
+// up each out-cell's index.  Cells whose cone needs more than kMaxR ranges, or whose passes do
+// not fit the list, take the sequential path.
+__global__ void __launch_bounds__(256, 2) k_connect(DevBatch b, DevParams p, uint32_t total)
+{
+    struct Lane {
+        float4 hi, hj;
+        RZ32 a;
+        double na64;
+        uint32_t i, j, pre, cnt, nr, npass;
+        uint32_t rs[kMaxR], rn[kMaxR];
+        uint8_t rslot[kMaxR];
+        uint8_t seq;
+    };
+    __shared__ Lane s_lane[kConnWarps][32];
+    __shared__ uint32_t s_pk[kConnWarps][kPass];
+    __shared__ uint8_t s_pown[kConnWarps][kPass], s_pslot[kConnWarps][kPass];
+    __shared__ uint32_t s_np[kConnWarps];
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    Lane *L = s_lane[wid];
+    Lane &me = L[lane];
     const uint32_t n_chunks = total / kChunk;
     for (uint32_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
         const uint32_t A = ch * kChunk + threadIdx.x;
         const uint32_t e = b.cell_chunk[ch];
         const uint32_t c0 = b.cell_off[e];
         const uint32_t ncell = min(b.cnt[C_CELLS * b.E + e], b.cell_off[e + 1] - c0);
-        if (A - c0 >= ncell) continue;
-        const uint32_t j = b.cell_out[A];
-        const uint32_t Lj = b.hmeta[j] >> kLocalBits;
-        const uint32_t nout = p.n_out[Lj];
-        if (nout == 0) continue;
-        const uint32_t i = b.cell_in[A];
-        const float4 hi = b.hs[i], hj = b.hs[j];
-        const RZ32 a = rz32(hi, hj);
-        const double na64 = p.cut_mode == CUT_FP64 ? b.cell_len64[A] : 0.0;
-        const float phij = b.hphi[j];
-        auto pass = [&](uint32_t k) {
-            const float4 hk = b.hs[k];
-            return doublet_test(b, p, j, hj, k) && triplet_test(b, p, i, j, k, hi, hj, hk, a, na64);
-        };
-        uint32_t npass = 0;
-        for (uint32_t s = 0; s < nout; ++s)
-            visit_cone(b, p, e, p.out_layer[Lj][s], a, hj, phij,
-                       [&](uint32_t k) { npass += pass(k); });
-        if (!npass) continue;
+        // ---- per-lane set-up -----------------------------------------------------------------
+        me.cnt = 0;
+        me.nr = 0;
+        me.npass = 0;
+        me.seq = 0;
+        uint32_t Lj = 0;
+        bool valid = A - c0 < ncell;
+        if (valid) {
+            me.j = b.cell_out[A];
+            Lj = b.hmeta[me.j] >> kLocalBits;
+            valid = p.n_out[Lj] != 0;
+        }
+        if (valid) {
+            me.i = b.cell_in[A];
+            me.hi = b.hs[me.i];
+            me.hj = b.hs[me.j];
+            me.a = rz32(me.hi, me.hj);
+            me.na64 = p.cut_mode == CUT_FP64 ? b.cell_len64[A] : 0.0;
+            cone_ranges(b, p, e, Lj, me.a, me.hj, b.hphi[me.j],
+                        [&](uint32_t s, uint32_t t0, uint32_t n) {
+                            if (me.nr < (uint32_t)kMaxR) {
+                                me.rs[me.nr] = t0;
+                                me.rn[me.nr] = n;
+                                me.rslot[me.nr] = (uint8_t)s;
+                                ++me.nr;
+                                me.cnt += n;
+                            } else {
+                                me.seq = 1;
+                            }
+                        });
+            if (me.seq) me.cnt = 0;
+        }
+        // ---- flatten the candidates of the warp --------------------------------------------
+        uint32_t incl = me.cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= (uint32_t)o) incl += t;
+        }
+        me.pre = incl - me.cnt;
+        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        if (lane == 0) s_np[wid] = 0;
+        __syncwarp();
+        for (uint32_t base = 0; base < tot; base += 32) {
+            const uint32_t t = base + lane;
+            if (t < tot) {
+                uint32_t lo = 0, hi_ = 31;                      // last lane with pre <= t
+                while (lo < hi_) {
+                    const uint32_t mid = (lo + hi_ + 1) >> 1;
+                    if (L[mid].pre <= t) lo = mid; else hi_ = mid - 1;
+                }
+                const Lane &ow = L[lo];
+                uint32_t loc = t - ow.pre, r = 0;
+                while (loc >= ow.rn[r]) { loc -= ow.rn[r]; ++r; }
+                const uint32_t k = b.zs[ow.rs[r] + loc];
+                const float4 hk = b.hs[k];
+                if (doublet_test(b, p, ow.j, ow.hj, k) &&
+                    triplet_test(b, p, ow.i, ow.j, k, ow.hi, ow.hj, hk, ow.a, ow.na64)) {
+                    const uint32_t q = atomicAdd(&s_np[wid], 1u);
+                    if (q < (uint32_t)kPass) {
+                        s_pk[wid][q] = k;
+                        s_pown[wid][q] = (uint8_t)lo;
+                        s_pslot[wid][q] = ow.rslot[r];
+                        atomicAdd(&L[lo].npass, 1u);
+                    } else {
+                        L[lo].seq = 1;                          // list full: redo this cell alone
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        // ---- edges -------------------------------------------------------------------------
+        if (!valid) continue;
         const uint32_t *bk = b.bkt + (size_t)e * (p.n_keys + 1);
+        const uint32_t np = min(s_np[wid], (uint32_t)kPass);
+        const uint32_t i = me.i, j = me.j;
+        auto pass = [&](uint32_t k) {
+            return doublet_test(b, p, j, me.hj, k) &&
+                   triplet_test(b, p, i, j, k, me.hi, me.hj, b.hs[k], me.a, me.na64);
+        };
+        if (me.seq) {
+            // sequential path: count, then write
+            uint32_t npass = 0;
+            for (uint32_t s = 0; s < p.n_out[Lj]; ++s)
+                visit_cone(b, p, e, p.out_layer[Lj][s], me.a, me.hj, b.hphi[j],
+                           [&](uint32_t k) { npass += pass(k); });
+            if (!npass) continue;
+            const uint32_t base = atomicAdd(&b.cnt[C_EDGES * b.E + e], npass);
+            const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
+            const uint32_t nw = base >= cap ? 0u : min(npass, cap - base);
+            if (nw < npass) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+            const uint32_t first = b.edge_off[e] + base;
+            uint32_t written = 0;
+            for (uint32_t s = 0; s < p.n_out[Lj]; ++s) {
+                const uint32_t Lk = p.out_layer[Lj][s];
+                visit_cone(b, p, e, Lk, me.a, me.hj, b.hphi[j], [&](uint32_t k) {
+                    if (written < nw && pass(k)) {
+                        const uint32_t B = find_cell(b, p, bk, j, me.hj, s, Lk, k);
+                        if (B != kNone) b.nbr[first + written++] = B;
+                    }
+                });
+            }
+            b.nbr_first[A] = first;
+            b.nbr_n[A] = written;
+            continue;
+        }
+        const uint32_t npass = me.npass;
+        if (!npass) continue;
         const uint32_t base = atomicAdd(&b.cnt[C_EDGES * b.E + e], npass);
         const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
         const uint32_t nw = base >= cap ? 0u : min(npass, cap - base);
         if (nw < npass) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
         const uint32_t first = b.edge_off[e] + base;
         uint32_t written = 0;
-        for (uint32_t s = 0; s < nout; ++s) {
-            const uint32_t Lk = p.out_layer[Lj][s];
-            visit_cone(b, p, e, Lk, a, hj, phij, [&](uint32_t k) {
-                if (written < nw && pass(k)) {
-                    const uint32_t B = find_cell(b, p, bk, j, hj, s, Lk, k);
-                    if (B != kNone) b.nbr[first + written++] = B;
-                }
-            });
+        for (uint32_t q = 0; q < np && written < nw; ++q) {
+            if (s_pown[wid][q] != lane) continue;
+            const uint32_t s = s_pslot[wid][q];
+            const uint32_t B = find_cell(b, p, bk, j, me.hj, s, p.out_layer[Lj][s], s_pk[wid][q]);
+            if (B != kNone) b.nbr[first + written++] = B;
         }
         b.nbr_first[A] = first;
         b.nbr_n[A] = written;
@@ -349,10 +500,10 @@ __global__ void __launch_bounds__(256, 3) k_connect(DevBatch b, DevParams p, uin
 void launch_connect(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
 {
     uint64_t blocks = total / kChunk;
-    uint64_t cap = (uint64_t)sms * 24;
+    uint64_t cap = (uint64_t)sms * 16;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
-    k_connect<<<(unsigned)blocks, 256, 0, s>>>(b, p, total);
+    k_connect<<<(unsigned)blocks, kConnWarps * 32, 0, s>>>(b, p, total);
 }
 
 // ------------------------------------------------------------------------------------------
