@@ -219,15 +219,12 @@ __device__ __forceinline__ uint32_t find_cell(const DevBatch &b, const DevParams
 // hit j along r-z directions within asin(theta_cut) of a = (ar, az), modulo pi.  With m the slope
 // of a against the layer's fixed coordinate and T = tan(asin(theta_cut)), the allowed slopes are
 // [(m - T)/(1 + mT), (m + T)/(1 - mT)] unless the cone contains the direction along the layer
-// (then everything is reachable); the offsets along the fixed coordinate span the layer's range.
+// (then everything is reachable); the offsets along the fixed coordinate span [dlo, dhi].
 // Returns false when the whole free range must be scanned.
-__device__ __forceinline__ bool cone_window(float ar, float az, float rj, float zj, bool disk,
-                                            const float *lr, float T, float &lo, float &hi)
+__device__ __forceinline__ bool cone_window(float ar, float az, float base, float dlo, float dhi,
+                                            bool disk, float T, float &lo, float &hi)
 {
     const float u = disk ? az : ar, v = disk ? ar : az;
-    const float base = disk ? rj : zj;
-    float dlo = disk ? lr[2] - zj : lr[0] - rj;
-    float dhi = disk ? lr[3] - zj : lr[1] - rj;
     dlo -= 1e-4f + 1e-5f * fabsf(dlo);
     dhi += 1e-4f + 1e-5f * fabsf(dhi);
     if (!(fabsf(u) > 1e-20f) || !(T < 1e30f)) return false;
@@ -247,263 +244,196 @@ __device__ __forceinline__ bool cone_window(float ar, float az, float rj, float 
     return true;
 }
 
-// The grid's bin of a free-coordinate value (the same expression the grid was built with).
-__device__ __forceinline__ uint32_t free_bin(float v, float lo, float scale, uint32_t nf)
-{
-    const int b = (int)floorf((v - lo) * scale);
-    return (uint32_t)(b < 0 ? 0 : (b >= (int)nf ? (int)nf - 1 : b));
-}
-
-// Visit every hit k of the grid rows of layer Lk that the in-cell's cone can reach, inside hit
-// j's phi window (coarse grid bins; the doublet cut decides).
-template <typename F>
-__device__ __forceinline__ void visit_cone(const DevBatch &b, const DevParams &p, uint32_t e,
-                                           uint32_t Lk, const RZ32 &a, float4 hj, float phij,
-                                           F &&f)
-{
-    const float *lr = b.lrange + ((size_t)e * p.n_layers + Lk) * kLr;
-    const bool disk = p.is_disk[Lk];
-    const float flo = disk ? lr[0] : lr[2], fhi = disk ? lr[1] : lr[3];
-    if (!(fhi >= flo)) return;                               // no hit on this layer
-    float lo = flo, hi = fhi;
-    if (cone_window(a.ar, a.az, hj.w, hj.z, disk, lr, p.tan_win, lo, hi)) {
-        lo = fmaxf(lo, flo);
-        hi = fminf(hi, fhi);
-        if (lo > hi) return;
-    }
-    const uint32_t fb0 = free_bin(lo, lr[4], lr[5], p.nf), fb1 = free_bin(hi, lr[4], lr[5], p.nf);
-    const int np2 = (int)p.np2;
-    const int pb0 = (int)floorf((phij - p.w_eps + kPiF2) * p.bins2_per_rad);
-    const int pb1 = (int)floorf((phij + p.w_eps + kPiF2) * p.bins2_per_rad);
-    const uint32_t *b2 = b.bkt2 + (size_t)e * (p.n_keys2 + 1);
-    for (uint32_t fb = fb0; fb <= fb1; ++fb) {
-        const uint32_t row = (Lk * p.nf + fb) * p.np2;
-        uint32_t r[4];
-        int nr;
-        if (pb1 - pb0 + 1 >= np2) {
-            r[0] = row; r[1] = row + np2; nr = 1;
-        } else if (pb0 < 0) {
-            r[0] = row + pb0 + np2; r[1] = row + np2; r[2] = row; r[3] = row + pb1 + 1; nr = 2;
-        } else if (pb1 >= np2) {
-            r[0] = row + pb0; r[1] = row + np2; r[2] = row; r[3] = row + pb1 - np2 + 1; nr = 2;
-        } else {
-            r[0] = row + pb0; r[1] = row + pb1 + 1; nr = 1;
-        }
-        for (int q = 0; q < nr; ++q)
-            for (uint32_t t = b2[r[2 * q]]; t < b2[r[2 * q + 1]]; ++t) f(b.zs[t]);
-    }
-}
-
-// Grid ranges of one in-cell's cone: for every out-layer slot, the grid rows the cone reaches
-// and the one or two phi runs of each row.  Calls f(slot, first, count) for each non-empty range.
-template <typename F>
-__device__ __forceinline__ void cone_ranges(const DevBatch &b, const DevParams &p, uint32_t e,
-                                            uint32_t Lj, const RZ32 &a, float4 hj, float phij,
-                                            F &&f)
-{
-    const uint32_t *b2 = b.bkt2 + (size_t)e * (p.n_keys2 + 1);
-    const int np2 = (int)p.np2;
-    const int pb0 = (int)floorf((phij - p.w_eps + kPiF2) * p.bins2_per_rad);
-    const int pb1 = (int)floorf((phij + p.w_eps + kPiF2) * p.bins2_per_rad);
-    for (uint32_t s = 0; s < p.n_out[Lj]; ++s) {
-        const uint32_t Lk = p.out_layer[Lj][s];
-        const float *lr = b.lrange + ((size_t)e * p.n_layers + Lk) * kLr;
-        const bool disk = p.is_disk[Lk];
-        const float flo = disk ? lr[0] : lr[2], fhi = disk ? lr[1] : lr[3];
-        if (!(fhi >= flo)) continue;                             // no hit on this layer
-        float lo = flo, hi = fhi;
-        if (cone_window(a.ar, a.az, hj.w, hj.z, disk, lr, p.tan_win, lo, hi)) {
-            lo = fmaxf(lo, flo);
-            hi = fminf(hi, fhi);
-            if (lo > hi) continue;
-        }
-        const uint32_t fb0 = free_bin(lo, lr[4], lr[5], p.nf), fb1 = free_bin(hi, lr[4], lr[5], p.nf);
-        for (uint32_t fb = fb0; fb <= fb1; ++fb) {
-            const uint32_t row = (Lk * p.nf + fb) * p.np2;
-            uint32_t r[4];
-            int nr;
-            if (pb1 - pb0 + 1 >= np2) {
-                r[0] = row; r[1] = row + np2; nr = 1;
-            } else if (pb0 < 0) {
-                r[0] = row + pb0 + np2; r[1] = row + np2; r[2] = row; r[3] = row + pb1 + 1; nr = 2;
-            } else if (pb1 >= np2) {
-                r[0] = row + pb0; r[1] = row + np2; r[2] = row; r[3] = row + pb1 - np2 + 1; nr = 2;
-            } else {
-                r[0] = row + pb0; r[1] = row + pb1 + 1; nr = 1;
-            }
-            for (int q = 0; q < nr; ++q) {
-                const uint32_t t0 = b2[r[2 * q]], t1 = b2[r[2 * q + 1]];
-                if (t1 > t0) f(s, t0, t1 - t0);
-            }
-        }
-    }
-}
-
 constexpr int kConnWarps = 8;
-constexpr int kMaxR = 6;       // candidate ranges kept per in-cell (more: sequential path)
-constexpr int kPass = 96;      // passing triplets kept per warp round (more: sequential path)
+constexpr int kStage = 256;     // out-cells of one junction staged per out-layer slot
+constexpr int kBins = 32;       // local bins of the free coordinate
 
-// One warp per 32 consecutive cells A = (i, j).  Each lane sets up its cell and collects the
-// grid ranges its cone reaches; the warp then tests all lanes' candidates together, 32 at a
-// time, so that lanes with many and lanes with no candidates do not diverge.  Passing triplets
-// go to a per-warp list; every cell with passes reserves its edge list with one atomic and looks
-// up each out-cell's index.  Cells whose cone needs more than kMaxR ranges, or whose passes do
-// not fit the list, take the sequential path.
-__global__ void __launch_bounds__(256, 2) k_connect(DevBatch b, DevParams p, uint32_t total)
+// Order-preserving int encoding of floats (shared-memory atomicMin / atomicMax).
+__device__ __forceinline__ int ford(float f)
 {
-    struct Lane {
-        float4 hi, hj;
-        RZ32 a;
-        double na64;
-        uint32_t i, j, pre, cnt, nr, npass;
-        uint32_t rs[kMaxR], rn[kMaxR];
-        uint8_t rslot[kMaxR];
-        uint8_t seq;
-    };
-    __shared__ Lane s_lane[kConnWarps][32];
-    __shared__ uint32_t s_pk[kConnWarps][kPass];
-    __shared__ uint8_t s_pown[kConnWarps][kPass], s_pslot[kConnWarps][kPass];
-    __shared__ uint32_t s_np[kConnWarps];
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float funord(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
+
+// One warp per junction hit j.  For each out-layer slot, j's out-cells (j, k) are staged in shared
+// memory and bucketed by the free coordinate of k (z on barrel layers, r on disks) over the
+// staged range.  Each in-cell (i, j), found by scanning i over j's phi window on the inner layer
+// with the doublet cut, computes the cone of r-z directions that can pass the alignment cut and
+// tests only the out-cells of the buckets that cone reaches (a conservative window: the exact
+// cuts decide).  In-cells with passes reserve their edge list with one atomic.  A slot with more
+// than kStage out-cells is tested against all of them from global memory.
+__global__ void __launch_bounds__(kConnWarps * 32, 2) k_connect(DevBatch b, DevParams p)
+{
+    __shared__ uint32_t s_B[kConnWarps][kStage], s_k[kConnWarps][kStage];
+    __shared__ float s_f[kConnWarps][kStage];
+    __shared__ uint32_t s_bin[kConnWarps][kBins + 1];
+    __shared__ int s_rng[kConnWarps][4];
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-    Lane *L = s_lane[wid];
-    Lane &me = L[lane];
-    const uint32_t n_chunks = total / kChunk;
-    for (uint32_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
-        const uint32_t A = ch * kChunk + threadIdx.x;
-        const uint32_t e = b.cell_chunk[ch];
-        const uint32_t c0 = b.cell_off[e];
-        const uint32_t ncell = min(b.cnt[C_CELLS * b.E + e], b.cell_off[e + 1] - c0);
-        // ---- per-lane set-up -----------------------------------------------------------------
-        me.cnt = 0;
-        me.nr = 0;
-        me.npass = 0;
-        me.seq = 0;
-        uint32_t Lj = 0;
-        bool valid = A - c0 < ncell;
-        if (valid) {
-            me.j = b.cell_out[A];
-            Lj = b.hmeta[me.j] >> kLocalBits;
-            valid = p.n_out[Lj] != 0;
-        }
-        if (valid) {
-            me.i = b.cell_in[A];
-            me.hi = b.hs[me.i];
-            me.hj = b.hs[me.j];
-            me.a = rz32(me.hi, me.hj);
-            me.na64 = p.cut_mode == CUT_FP64 ? b.cell_len64[A] : 0.0;
-            cone_ranges(b, p, e, Lj, me.a, me.hj, b.hphi[me.j],
-                        [&](uint32_t s, uint32_t t0, uint32_t n) {
-                            if (me.nr < (uint32_t)kMaxR) {
-                                me.rs[me.nr] = t0;
-                                me.rn[me.nr] = n;
-                                me.rslot[me.nr] = (uint8_t)s;
-                                ++me.nr;
-                                me.cnt += n;
-                            } else {
-                                me.seq = 1;
-                            }
-                        });
-            if (me.seq) me.cnt = 0;
-        }
-        // ---- flatten the candidates of the warp --------------------------------------------
-        uint32_t incl = me.cnt;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= (uint32_t)o) incl += t;
-        }
-        me.pre = incl - me.cnt;
-        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        if (lane == 0) s_np[wid] = 0;
-        __syncwarp();
-        for (uint32_t base = 0; base < tot; base += 32) {
-            const uint32_t t = base + lane;
-            if (t < tot) {
-                uint32_t lo = 0, hi_ = 31;                      // last lane with pre <= t
-                while (lo < hi_) {
-                    const uint32_t mid = (lo + hi_ + 1) >> 1;
-                    if (L[mid].pre <= t) lo = mid; else hi_ = mid - 1;
+    uint32_t *sB = s_B[wid], *sK = s_k[wid], *bin = s_bin[wid];
+    float *sF = s_f[wid];
+    int *rng = s_rng[wid];
+    const uint32_t nk = p.n_keys;
+    const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t jj = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; jj < b.N;
+         jj += stride) {
+        const uint32_t j = (uint32_t)jj;
+        const uint32_t e = hit_event(b, j);
+        const uint32_t *bk = b.bkt + (size_t)e * (nk + 1);
+        if (j >= bk[nk]) continue;
+        const uint32_t Lj = b.hmeta[j] >> kLocalBits;
+        const uint32_t nin = p.n_in[Lj], nout = p.n_out[Lj];
+        if (nin == 0 || nout == 0) continue;
+        const float4 hj = b.hs[j];
+        const float phij = b.hphi[j];
+        for (uint32_t s = 0; s < nout; ++s) {
+            const uint32_t Lk = p.out_layer[Lj][s];
+            const bool disk = p.is_disk[Lk];
+            const uint32_t f0 = b.out_first[(size_t)j * kMaxOut + s];
+            const uint32_t nB = b.out_n[(size_t)j * kMaxOut + s];
+            if (nB == 0) continue;
+            const bool staged = nB <= (uint32_t)kStage;
+            float flo = 0.f, fhi = 0.f, dlo = 0.f, dhi = 0.f, scale = 0.f;
+            if (staged) {
+                // stage: free coordinate and ranges of the out-cells
+                if (lane < 4) rng[lane] = (lane & 1) ? ford(-3.0e38f) : ford(3.0e38f);
+                __syncwarp();
+                for (uint32_t t = lane; t < nB; t += 32) {
+                    const uint32_t k = b.cell_out[f0 + t];
+                    const float4 hk = b.hs[k];
+                    const float fc = disk ? hk.w : hk.z, xc = disk ? hk.z : hk.w;
+                    sK[t] = k;
+                    sF[t] = fc;
+                    atomicMin(&rng[0], ford(fc));
+                    atomicMax(&rng[1], ford(fc));
+                    atomicMin(&rng[2], ford(xc));
+                    atomicMax(&rng[3], ford(xc));
                 }
-                const Lane &ow = L[lo];
-                uint32_t loc = t - ow.pre, r = 0;
-                while (loc >= ow.rn[r]) { loc -= ow.rn[r]; ++r; }
-                const uint32_t k = b.zs[ow.rs[r] + loc];
-                const float4 hk = b.hs[k];
-                if (doublet_test(b, p, ow.j, ow.hj, k) &&
-                    triplet_test(b, p, ow.i, ow.j, k, ow.hi, ow.hj, hk, ow.a, ow.na64)) {
-                    const uint32_t q = atomicAdd(&s_np[wid], 1u);
-                    if (q < (uint32_t)kPass) {
-                        s_pk[wid][q] = k;
-                        s_pown[wid][q] = (uint8_t)lo;
-                        s_pslot[wid][q] = ow.rslot[r];
-                        atomicAdd(&L[lo].npass, 1u);
+                __syncwarp();
+                flo = funord(rng[0]);
+                fhi = funord(rng[1]);
+                dlo = funord(rng[2]) - (disk ? hj.z : hj.w);
+                dhi = funord(rng[3]) - (disk ? hj.z : hj.w);
+                scale = fhi > flo ? (float)kBins / (fhi - flo) : 0.f;
+                // counting sort by local bin
+                for (uint32_t t = lane; t <= (uint32_t)kBins; t += 32) bin[t] = 0;
+                __syncwarp();
+                uint32_t mybin[kStage / 32];
+#pragma unroll
+                for (int q = 0; q < kStage / 32; ++q) {
+                    const uint32_t t = lane + 32u * q;
+                    if (t < nB) {
+                        int bb = (int)floorf((sF[t] - flo) * scale);
+                        bb = bb < 0 ? 0 : (bb >= kBins ? kBins - 1 : bb);
+                        mybin[q] = (uint32_t)bb;
+                        atomicAdd(&bin[bb + 1], 1u);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0)
+                    for (int t = 1; t <= kBins; ++t) bin[t] += bin[t - 1];
+                __syncwarp();
+                // scatter (B index, hit) into bin order; sF keeps the staged order, so read first
+                uint32_t myk[kStage / 32];
+#pragma unroll
+                for (int q = 0; q < kStage / 32; ++q) {
+                    const uint32_t t = lane + 32u * q;
+                    if (t < nB) myk[q] = sK[t];
+                }
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < kStage / 32; ++q) {
+                    const uint32_t t = lane + 32u * q;
+                    if (t < nB) {
+                        const uint32_t pos = atomicAdd(&bin[mybin[q]], 1u);
+                        sB[pos] = f0 + t;
+                        sK[pos] = myk[q];
+                    }
+                }
+                __syncwarp();
+                // bin[t] now holds the end of bin t; starts are bin[t - 1] (bin[-1] = 0)
+            }
+            for (uint32_t si = 0; si < nin; ++si) {
+                const uint32_t Li = p.in_layer[Lj][si];
+                const uint32_t slot_i = p.in_slot[Lj][si];
+                const Window w = phi_window(bk, Li, phij, p);
+                const uint32_t nc = w.size();
+                for (uint32_t c0 = 0; c0 < nc; c0 += 32) {
+                    const uint32_t c = c0 + lane;
+                    if (c >= nc) continue;
+                    const uint32_t i = w.pos(c);
+                    const float4 hi = b.hs[i];
+                    if (!doublet_test(b, p, i, hi, j)) continue;
+                    const RZ32 a = rz32(hi, hj);
+                    const double na64 = p.cut_mode == CUT_FP64
+                                            ? seglen64(b.r64[i], (double)hi.z, b.r64[j], (double)hj.z)
+                                            : 0.0;
+                    uint32_t q0 = 0, q1 = nB;
+                    if (staged) {
+                        float lo, hi_;
+                        if (cone_window(a.ar, a.az, disk ? hj.w : hj.z, dlo, dhi, disk, p.tan_win,
+                                        lo, hi_)) {
+                            if (hi_ < flo || lo > fhi) continue;
+                            int b0 = (int)floorf((lo - flo) * scale);
+                            int b1 = (int)floorf((hi_ - flo) * scale);
+                            b0 = b0 < 0 ? 0 : (b0 >= kBins ? kBins - 1 : b0);
+                            b1 = b1 < 0 ? 0 : (b1 >= kBins ? kBins - 1 : b1);
+                            q0 = b0 ? bin[b0 - 1] : 0u;
+                            q1 = bin[b1];
+                        }
+                    }
+                    auto pass = [&](uint32_t q, uint32_t &B) {
+                        uint32_t k;
+                        if (staged) { B = sB[q]; k = sK[q]; }
+                        else { B = f0 + q; k = b.cell_out[B]; }
+                        return triplet_test(b, p, i, j, k, hi, hj, b.hs[k], a, na64);
+                    };
+                    uint32_t npass = 0, B;
+                    for (uint32_t q = q0; q < q1; ++q) npass += pass(q, B);
+                    if (!npass) continue;
+                    const uint32_t A = find_cell(b, p, bk, i, hi, slot_i, Lj, j);
+                    if (A == kNone) continue;
+                    // an in-cell's edges over several out-layer slots: append to its list
+                    uint32_t have = s == 0 ? 0u : b.nbr_n[A];
+                    const uint32_t base = atomicAdd(&b.cnt[C_EDGES * b.E + e], npass);
+                    const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
+                    const uint32_t nw = base >= cap ? 0u : min(npass, cap - base);
+                    if (nw < npass) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+                    const uint32_t first = b.edge_off[e] + base;
+                    uint32_t written = 0;
+                    for (uint32_t q = q0; q < q1 && written < nw; ++q)
+                        if (pass(q, B)) b.nbr[first + written++] = B;
+                    if (have == 0) {
+                        b.nbr_first[A] = first;
+                        b.nbr_n[A] = written;
                     } else {
-                        L[lo].seq = 1;                          // list full: redo this cell alone
+                        // several slots: move the earlier edges next to the new ones
+                        const uint32_t old = b.nbr_first[A];
+                        const uint32_t base2 = atomicAdd(&b.cnt[C_EDGES * b.E + e], have + written);
+                        const uint32_t nw2 = base2 >= cap ? 0u : min(have + written, cap - base2);
+                        if (nw2 < have + written) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+                        const uint32_t f2 = b.edge_off[e] + base2;
+                        uint32_t w2 = 0;
+                        for (uint32_t t = 0; t < have && w2 < nw2; ++t) b.nbr[f2 + w2++] = b.nbr[old + t];
+                        for (uint32_t t = 0; t < written && w2 < nw2; ++t) b.nbr[f2 + w2++] = b.nbr[first + t];
+                        b.nbr_first[A] = f2;
+                        b.nbr_n[A] = w2;
                     }
                 }
             }
+            __syncwarp();
         }
-        __syncwarp();
-        // ---- edges -------------------------------------------------------------------------
-        if (!valid) continue;
-        const uint32_t *bk = b.bkt + (size_t)e * (p.n_keys + 1);
-        const uint32_t np = min(s_np[wid], (uint32_t)kPass);
-        const uint32_t i = me.i, j = me.j;
-        auto pass = [&](uint32_t k) {
-            return doublet_test(b, p, j, me.hj, k) &&
-                   triplet_test(b, p, i, j, k, me.hi, me.hj, b.hs[k], me.a, me.na64);
-        };
-        if (me.seq) {
-            // sequential path: count, then write
-            uint32_t npass = 0;
-            for (uint32_t s = 0; s < p.n_out[Lj]; ++s)
-                visit_cone(b, p, e, p.out_layer[Lj][s], me.a, me.hj, b.hphi[j],
-                           [&](uint32_t k) { npass += pass(k); });
-            if (!npass) continue;
-            const uint32_t base = atomicAdd(&b.cnt[C_EDGES * b.E + e], npass);
-            const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
-            const uint32_t nw = base >= cap ? 0u : min(npass, cap - base);
-            if (nw < npass) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
-            const uint32_t first = b.edge_off[e] + base;
-            uint32_t written = 0;
-            for (uint32_t s = 0; s < p.n_out[Lj]; ++s) {
-                const uint32_t Lk = p.out_layer[Lj][s];
-                visit_cone(b, p, e, Lk, me.a, me.hj, b.hphi[j], [&](uint32_t k) {
-                    if (written < nw && pass(k)) {
-                        const uint32_t B = find_cell(b, p, bk, j, me.hj, s, Lk, k);
-                        if (B != kNone) b.nbr[first + written++] = B;
-                    }
-                });
-            }
-            b.nbr_first[A] = first;
-            b.nbr_n[A] = written;
-            continue;
-        }
-        const uint32_t npass = me.npass;
-        if (!npass) continue;
-        const uint32_t base = atomicAdd(&b.cnt[C_EDGES * b.E + e], npass);
-        const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
-        const uint32_t nw = base >= cap ? 0u : min(npass, cap - base);
-        if (nw < npass) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
-        const uint32_t first = b.edge_off[e] + base;
-        uint32_t written = 0;
-        for (uint32_t q = 0; q < np && written < nw; ++q) {
-            if (s_pown[wid][q] != lane) continue;
-            const uint32_t s = s_pslot[wid][q];
-            const uint32_t B = find_cell(b, p, bk, j, me.hj, s, p.out_layer[Lj][s], s_pk[wid][q]);
-            if (B != kNone) b.nbr[first + written++] = B;
-        }
-        b.nbr_first[A] = first;
-        b.nbr_n[A] = written;
     }
 }
 
 void launch_connect(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
 {
-    uint64_t blocks = total / kChunk;
+    (void)total;
+    uint64_t blocks = ((uint64_t)b.N + kConnWarps - 1) / kConnWarps;
     uint64_t cap = (uint64_t)sms * 16;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
-    k_connect<<<(unsigned)blocks, kConnWarps * 32, 0, s>>>(b, p, total);
+    k_connect<<<(unsigned)blocks, kConnWarps * 32, 0, s>>>(b, p);
 }
 
 // ------------------------------------------------------------------------------------------
