@@ -6,11 +6,11 @@
 // cells, and the second sweep writes them from the ballot masks, so the cells of an inner hit are
 // contiguous (the CA stage reads them as one run per pair).
 //
-// CA connect: one thread per cell A = (i, j).  The out-cells (j, k) that can pass the r-z
-// alignment cut have k inside a cone of directions around A's direction; a second index of the
-// hits (a per-layer grid over the free coordinate and phi) turns that cone into a few grid rows,
-// a conservative window in which the exact cuts decide.  Passes are counted first; the cells
-// that have any reserve their edge list with one atomic.  Ntuplets: one thread per root cell walks the
+// CA connect: one warp per junction hit j.  j's out-cells (j, k) are staged in shared memory and
+// bucketed by the free coordinate of k (z on barrel layers, r on disks); each in-cell (i, j) tests
+// only the buckets reached by the cone of r-z directions within asin(theta_cut) of its own, a
+// conservative window in which the exact cuts decide.  Passes are counted first; in-cells with
+// passes reserve their edge list with one atomic.  Ntuplets: one thread per root cell walks the
 // out-edges depth first with an explicit stack.  Selection removes suffix paths and assigns
 // output slots.
 #include "pxr_dev.cuh"
@@ -268,11 +268,9 @@ __global__ void __launch_bounds__(kConnWarps * 32, 2) k_connect(DevBatch b, DevP
     __shared__ uint32_t s_B[kConnWarps][kStage], s_k[kConnWarps][kStage];
     __shared__ float s_f[kConnWarps][kStage];
     __shared__ uint32_t s_bin[kConnWarps][kBins + 1];
-    __shared__ int s_rng[kConnWarps][4];
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
     uint32_t *sB = s_B[wid], *sK = s_k[wid], *bin = s_bin[wid];
     float *sF = s_f[wid];
-    int *rng = s_rng[wid];
     const uint32_t nk = p.n_keys;
     const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t jj = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; jj < b.N;
@@ -295,25 +293,28 @@ __global__ void __launch_bounds__(kConnWarps * 32, 2) k_connect(DevBatch b, DevP
             const bool staged = nB <= (uint32_t)kStage;
             float flo = 0.f, fhi = 0.f, dlo = 0.f, dhi = 0.f, scale = 0.f;
             if (staged) {
-                // stage: free coordinate and ranges of the out-cells
-                if (lane < 4) rng[lane] = (lane & 1) ? ford(-3.0e38f) : ford(3.0e38f);
-                __syncwarp();
+                // stage: free coordinate and ranges of the out-cells (warp reductions)
+                int m0 = ford(3.0e38f), m1 = ford(-3.0e38f), m2 = m0, m3 = m1;
                 for (uint32_t t = lane; t < nB; t += 32) {
                     const uint32_t k = b.cell_out[f0 + t];
                     const float4 hk = b.hs[k];
                     const float fc = disk ? hk.w : hk.z, xc = disk ? hk.z : hk.w;
                     sK[t] = k;
                     sF[t] = fc;
-                    atomicMin(&rng[0], ford(fc));
-                    atomicMax(&rng[1], ford(fc));
-                    atomicMin(&rng[2], ford(xc));
-                    atomicMax(&rng[3], ford(xc));
+                    m0 = min(m0, ford(fc));
+                    m1 = max(m1, ford(fc));
+                    m2 = min(m2, ford(xc));
+                    m3 = max(m3, ford(xc));
                 }
+                m0 = __reduce_min_sync(0xFFFFFFFFu, m0);
+                m1 = __reduce_max_sync(0xFFFFFFFFu, m1);
+                m2 = __reduce_min_sync(0xFFFFFFFFu, m2);
+                m3 = __reduce_max_sync(0xFFFFFFFFu, m3);
                 __syncwarp();
-                flo = funord(rng[0]);
-                fhi = funord(rng[1]);
-                dlo = funord(rng[2]) - (disk ? hj.z : hj.w);
-                dhi = funord(rng[3]) - (disk ? hj.z : hj.w);
+                flo = funord(m0);
+                fhi = funord(m1);
+                dlo = funord(m2) - (disk ? hj.z : hj.w);
+                dhi = funord(m3) - (disk ? hj.z : hj.w);
                 scale = fhi > flo ? (float)kBins / (fhi - flo) : 0.f;
                 // counting sort by local bin
                 for (uint32_t t = lane; t <= (uint32_t)kBins; t += 32) bin[t] = 0;

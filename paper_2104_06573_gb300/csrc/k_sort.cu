@@ -100,100 +100,11 @@ __global__ void __launch_bounds__(512) k_sort(DevBatch b, DevParams p)
     }
 }
 
-// Order-preserving int encoding of floats (for shared-memory atomicMin / atomicMax).
-__device__ __forceinline__ int f2o(float f)
-{
-    const int i = __float_as_int(f);
-    return i >= 0 ? i : i ^ 0x7FFFFFFF;
-}
-__device__ __forceinline__ float o2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
-
-// Second index of each event's sorted hits: per layer, a grid over (free coordinate, phi), where
-// the free coordinate is z on barrel layers and r on disks, binned over the layer's actual range
-// in this event.  zs lists, bucket by bucket, the positions of the hits in the phi order.  The CA
-// stage looks up the few grid rows that an in-cell's r-z direction can reach.
-__device__ __forceinline__ uint32_t grid_bin_free(float v, float lo, float scale, uint32_t nf)
-{
-    const int b = (int)floorf((v - lo) * scale);
-    return (uint32_t)(b < 0 ? 0 : (b >= (int)nf ? (int)nf - 1 : b));
-}
-
-__device__ __forceinline__ uint32_t grid_key(float4 h, float phi, uint32_t L, const float *lr,
-                                             const DevParams &p)
-{
-    const bool disk = p.is_disk[L];
-    const uint32_t fb = grid_bin_free(disk ? h.w : h.z, lr[L * kLr + 4], lr[L * kLr + 5], p.nf);
-    int pb = (int)floorf((phi + kPiF) * p.bins2_per_rad);
-    pb = pb < 0 ? 0 : (pb >= (int)p.np2 ? (int)p.np2 - 1 : pb);
-    return (L * p.nf + fb) * p.np2 + (uint32_t)pb;
-}
-
-__global__ void __launch_bounds__(512) k_grid(DevBatch b, DevParams p)
-{
-    extern __shared__ uint32_t s_c2[];
-    __shared__ int s_rng[kMaxLayers * 4];
-    __shared__ float s_lr[kMaxLayers * kLr];
-    __shared__ uint32_t s_warp[32];
-    const uint32_t nk = p.n_keys, nk2 = p.n_keys2, nl = p.n_layers;
-    for (uint32_t e = blockIdx.x; e < b.E; e += gridDim.x) {
-        const uint32_t h0 = b.hit_off[e];
-        const uint32_t hend = b.bkt[(size_t)e * (nk + 1) + nk];
-        for (uint32_t k = threadIdx.x; k < nl * 4; k += blockDim.x)
-            s_rng[k] = (k & 1) ? f2o(-3.0e38f) : f2o(3.0e38f);
-        for (uint32_t k = threadIdx.x; k < nk2; k += blockDim.x) s_c2[k] = 0;
-        __syncthreads();
-        for (uint32_t pos = h0 + threadIdx.x; pos < hend; pos += blockDim.x) {
-            const float4 h = b.hs[pos];
-            const uint32_t L = b.hmeta[pos] >> kLocalBits;
-            atomicMin(&s_rng[L * 4 + 0], f2o(h.w));
-            atomicMax(&s_rng[L * 4 + 1], f2o(h.w));
-            atomicMin(&s_rng[L * 4 + 2], f2o(h.z));
-            atomicMax(&s_rng[L * 4 + 3], f2o(h.z));
-        }
-        __syncthreads();
-        for (uint32_t L = threadIdx.x; L < nl; L += blockDim.x) {
-            float *o = s_lr + L * kLr;
-            for (int k = 0; k < 4; ++k) o[k] = o2f(s_rng[L * 4 + k]);
-            // free coordinate: r on disks, z on barrel layers
-            const float lo = p.is_disk[L] ? o[0] : o[2], hi = p.is_disk[L] ? o[1] : o[3];
-            o[4] = lo;
-            o[5] = hi > lo ? (float)p.nf / (hi - lo) : 0.f;
-            for (int k = 0; k < kLr; ++k) b.lrange[((size_t)e * nl + L) * kLr + k] = o[k];
-        }
-        __syncthreads();
-        for (uint32_t pos = h0 + threadIdx.x; pos < hend; pos += blockDim.x)
-            atomicAdd(&s_c2[grid_key(b.hs[pos], b.hphi[pos], b.hmeta[pos] >> kLocalBits, s_lr, p)],
-                      1u);
-        __syncthreads();
-        const uint32_t total = block_exclusive_scan(s_c2, nk2, s_warp);
-        uint32_t *b2 = b.bkt2 + (size_t)e * (nk2 + 1);
-        for (uint32_t k = threadIdx.x; k < nk2; k += blockDim.x) b2[k] = h0 + s_c2[k];
-        if (threadIdx.x == 0) b2[nk2] = h0 + total;
-        __syncthreads();
-        for (uint32_t pos = h0 + threadIdx.x; pos < hend; pos += blockDim.x) {
-            const uint32_t key =
-                grid_key(b.hs[pos], b.hphi[pos], b.hmeta[pos] >> kLocalBits, s_lr, p);
-            b.zs[h0 + atomicAdd(&s_c2[key], 1u)] = pos;
-        }
-        __syncthreads();
-    }
-}
-
-void launch_grid(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms)
-{
-    uint32_t grid = b.E < (uint32_t)(sms * 4) ? b.E : (uint32_t)(sms * 4);
-    if (grid == 0) return;
-    k_grid<<<grid, 512, p.n_keys2 * sizeof(uint32_t), s>>>(b, p);
-}
-
 cudaError_t init_kernels()
 {
-    // up to 16 layers x 2048 bins of 4-byte counters (sort), 32768 grid buckets (grid)
-    cudaError_t e = cudaFuncSetAttribute(k_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kMaxLayers * 2048 * (int)sizeof(uint32_t));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                32768 * (int)sizeof(uint32_t));
+    // up to 16 layers x 2048 bins of 4-byte counters
+    return cudaFuncSetAttribute(k_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kMaxLayers * 2048 * (int)sizeof(uint32_t));
 }
 
 void launch_sort(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms)

@@ -22,7 +22,6 @@ constexpr int kLocalBits = 24;   // hmeta = layer << 24 | index of the hit insid
 constexpr uint32_t kLocalMask = (1u << kLocalBits) - 1u;
 constexpr uint32_t kChunk = 256;     // per-event cell / ntuplet capacities are multiples of this
 constexpr uint32_t kHitChunk = 32;   // granularity of the hit -> event table
-constexpr int kLr = 6;               // per-layer range record: r min/max, z min/max, free lo/scale
 
 // Per-event counters, laid out as kCounters consecutive arrays of E words.
 enum Counter : int { C_CELLS = 0, C_EDGES = 1, C_TUPLES = 2, C_FLAGS = 3, C_OUT = 4, kCounters = 5 };
@@ -52,12 +51,7 @@ struct DevParams {
     float cw32;                         // cos(w) rounded to float
     float theta32;                      // theta_cut rounded to float
     float dca32;                        // dca_cut rounded to float
-    float key_halfwin;                  // r-z direction-key window: asin(theta_cut) + margin
-    float tan_win;                      // tan(asin(theta_cut)) (inf when theta_cut >= 1)
-    uint32_t nf;                        // grid bins along the free coordinate (z barrel, r disk)
-    uint32_t np2;                       // grid bins in phi
-    uint32_t n_keys2;                   // n_layers * nf * np2
-    float bins2_per_rad;                // np2 / (2 pi)
+    float tan_win;                      // tan(asin(theta_cut) + margin); inf when theta_cut >= 1
     double cw;                          // cos(w) as given by the caller
     double theta, dca;
     double bfield, sigma_rphi, sigma_z, x_over_x0;
@@ -82,10 +76,6 @@ struct DevBatch {
     // event of a work chunk: cells and ntuplets by 256-entry chunk, hits by 32-hit chunk (first
     // event of the chunk)
     const uint32_t *cell_chunk, *tup_chunk, *hit_chunk;
-    // second index of the sorted hits: per layer, a grid over (free coordinate, phi)
-    float *lrange;                      // [E * n_layers * kLr] r min/max, z min/max, free lo/scale
-    uint32_t *bkt2;                     // [E * (n_keys2 + 1)] grid bucket starts
-    uint32_t *zs;                       // [N] grid order -> position in the phi order
     // cells, grouped by (inner hit, pair slot)
     uint32_t *out_first;                // [N * kMaxOut] first cell of (inner hit, slot)
     uint32_t *out_n;                    // [N * kMaxOut] number of cells
@@ -136,7 +126,6 @@ cudaError_t init_kernels();
 
 // Kernel launchers (defined in the .cu files).
 void launch_sort(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms);
-void launch_grid(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms);
 void launch_layer_count(const uint32_t *hit_off, const uint16_t *layer, uint32_t E,
                         uint32_t n_layers, uint32_t *counts, cudaStream_t s, int sms);
 void launch_doublets(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms);

@@ -145,18 +145,9 @@ static int check_params(const pxr_params *p, DevParams *d)
     d->cw32 = (float)p->cos_phi_window;
     d->theta32 = (float)p->theta_cut;
     d->dca32 = (float)p->dca_cut;
-    // |sin(angle)| <= t  <=>  the r-z directions differ by at most asin(t) modulo pi; the key
-    // below never changes faster than the angle, so this (plus a margin far above the float
-    // error of the key) is a conservative window.  t >= 1 keeps every candidate.
-    d->key_halfwin = p->theta_cut < 1.0 ? (float)(std::asin(p->theta_cut) + 1e-4) : 4.0f;
+    // |sin(angle)| <= t  <=>  the r-z directions differ by at most asin(t) modulo pi
     d->tan_win = p->theta_cut < 0.99 ? (float)std::tan(std::asin(p->theta_cut) + 1e-5)
                                      : INFINITY;
-    // grid of the second hit index: phi bins about the window width, free-coordinate bins so
-    // that the grid counters fit 32768 entries
-    d->np2 = 128;
-    d->nf = std::max(8u, std::min(64u, 32768u / (d->n_layers * d->np2)));
-    d->n_keys2 = d->n_layers * d->nf * d->np2;
-    d->bins2_per_rad = (float)(d->np2 / (2.0 * M_PI));
     d->cw = p->cos_phi_window;
     d->theta = p->theta_cut;
     d->dca = p->dca_cut;
@@ -218,7 +209,7 @@ struct PlanOffsets {
     // inputs (serving plans only) and small host-filled arrays come first: one H2D copy
     size_t x, y, z, layer, hit_off, cell_off, edge_off, tup_off, cell_chunk, tup_chunk, hit_chunk,
         head_end;
-    size_t cnt, bkt, hs, r64, hmeta, hphi, lrange, bkt2, zs, out_first, out_n, cell_in, cell_out,
+    size_t cnt, bkt, hs, r64, hmeta, hphi, out_first, out_n, cell_in, cell_out,
         cell_len64, nbr_first,
         nbr_n, nbr, mindepth, tup_hits, tup_n, tup_state, tup_first, tup_rank, out_evt, o_nh,
         o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status;
@@ -249,9 +240,7 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.r64 = L.add(8 * N);
     o.hmeta = L.add(4 * N);
     o.hphi = L.add(4 * N);
-    o.lrange = L.add(4 * (size_t)E * dp.n_layers * kLr);
-    o.bkt2 = L.add(4 * (size_t)E * (dp.n_keys2 + 1));
-    o.zs = L.add(4 * N);
+
     o.out_first = L.add(4 * N * kMaxOut);
     o.out_n = L.add(4 * N * kMaxOut);
     o.cell_in = L.add(4 * C);
@@ -411,9 +400,7 @@ static void plan_bind(pxr_plan *P)
     b.cell_chunk = (const uint32_t *)(r + o.cell_chunk);
     b.tup_chunk = (const uint32_t *)(r + o.tup_chunk);
     b.hit_chunk = (const uint32_t *)(r + o.hit_chunk);
-    b.lrange = (float *)(r + o.lrange);
-    b.bkt2 = (uint32_t *)(r + o.bkt2);
-    b.zs = (uint32_t *)(r + o.zs);
+
     b.out_first = (uint32_t *)(r + o.out_first);
     b.out_n = (uint32_t *)(r + o.out_n);
     b.cell_in = (uint32_t *)(r + o.cell_in);
@@ -510,7 +497,6 @@ static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
     if (p.drop_suffixes) CK(cudaMemsetAsync(r + P->off.mindepth, 0xFF, 4 * P->C, s));
     CK(cudaMemsetAsync(r + P->off.nbr_n, 0, 4 * P->C, s));   // cells without edges stay at 0
     launch_sort(b, p, s, sms);
-    launch_grid(b, p, s, sms);
     if (t) CK(stage_mark(P->ev_stage[1], s, capturing));
     launch_doublets(b, p, s, sms);
     if (t) CK(stage_mark(P->ev_stage[2], s, capturing));
@@ -526,7 +512,7 @@ static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
     return PXR_OK;
 }
 
-static int plan_launches(const pxr_plan *) { return 8; }
+static int plan_launches(const pxr_plan *) { return 7; }
 
 static void plan_free(pxr_plan *P)
 {
