@@ -247,8 +247,9 @@ __device__ __forceinline__ bool cone_window(float ar, float az, float base, floa
 constexpr int kConnWarps = 8;
 constexpr int kStage = 256;     // out-cells of one junction staged per out-layer slot
 constexpr int kBins = 32;       // local bins of the free coordinate
+constexpr int kPass = 64;       // passing triplets collected per round of 32 in-cells
 
-// Order-preserving int encoding of floats (shared-memory atomicMin / atomicMax).
+// Order-preserving int encoding of floats (for warp min / max reductions).
 __device__ __forceinline__ int ford(float f)
 {
     const int i = __float_as_int(f);
@@ -256,21 +257,56 @@ __device__ __forceinline__ int ford(float f)
 }
 __device__ __forceinline__ float funord(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
 
-// One warp per junction hit j.  For each out-layer slot, j's out-cells (j, k) are staged in shared
-// memory and bucketed by the free coordinate of k (z on barrel layers, r on disks) over the
-// staged range.  Each in-cell (i, j), found by scanning i over j's phi window on the inner layer
-// with the doublet cut, computes the cone of r-z directions that can pass the alignment cut and
-// tests only the out-cells of the buckets that cone reaches (a conservative window: the exact
-// cuts decide).  In-cells with passes reserve their edge list with one atomic.  A slot with more
-// than kStage out-cells is tested against all of them from global memory.
+// Append n out-edges of cell A (its list may already hold edges from an earlier out-layer slot).
+template <typename G>
+__device__ __forceinline__ void append_edges(const DevBatch &b, uint32_t e, uint32_t A, bool first_slot,
+                                             uint32_t n, G &&get)
+{
+    const uint32_t have = first_slot ? 0u : b.nbr_n[A];
+    const uint32_t old = b.nbr_first[A];
+    const uint32_t need = have + n;
+    const uint32_t base = atomicAdd(&b.cnt[C_EDGES * b.E + e], need);
+    const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
+    const uint32_t nw = base >= cap ? 0u : min(need, cap - base);
+    if (nw < need) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+    const uint32_t first = b.edge_off[e] + base;
+    uint32_t w = 0;
+    for (uint32_t t = 0; t < have && w < nw; ++t) b.nbr[first + w++] = b.nbr[old + t];
+    for (uint32_t t = 0; t < n && w < nw; ++t) b.nbr[first + w++] = get(t);
+    b.nbr_first[A] = first;
+    b.nbr_n[A] = w;
+}
+
+// One warp per junction hit j.  For each out-layer slot, j's out-cells (j, k) are staged in
+// shared memory and bucketed by the free coordinate of k (z on barrel layers, r on disks) over
+// the staged range.  The in-cells (i, j) are found 32 at a time by scanning i over j's phi window
+// on the inner layer with the doublet cut; each computes the cone of r-z directions that can pass
+// the alignment cut and the buckets it reaches (a conservative window: the exact cuts decide).
+// The warp then tests all 32 in-cells' candidates together, 32 at a time, collecting passes in a
+// shared list; each in-cell with passes finds its own index and appends its edge list.  A slot
+// with more than kStage out-cells is tested against all of them from global memory; an in-cell
+// whose passes overflow the list is redone alone.
 __global__ void __launch_bounds__(kConnWarps * 32, 2) k_connect(DevBatch b, DevParams p)
 {
+    struct Lane {
+        float4 hi;
+        RZ32 a;
+        double na64;
+        uint32_t i, q0, pre, npass;
+        uint32_t seq;
+    };
     __shared__ uint32_t s_B[kConnWarps][kStage], s_k[kConnWarps][kStage];
     __shared__ float s_f[kConnWarps][kStage];
     __shared__ uint32_t s_bin[kConnWarps][kBins + 1];
+    __shared__ Lane s_lane[kConnWarps][32];
+    __shared__ uint32_t s_pB[kConnWarps][kPass];
+    __shared__ uint8_t s_pown[kConnWarps][kPass];
+    __shared__ uint32_t s_np[kConnWarps];
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
     uint32_t *sB = s_B[wid], *sK = s_k[wid], *bin = s_bin[wid];
     float *sF = s_f[wid];
+    Lane *LL = s_lane[wid];
+    Lane &me = LL[lane];
     const uint32_t nk = p.n_keys;
     const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t jj = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; jj < b.N;
@@ -293,7 +329,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 2) k_connect(DevBatch b, DevP
             const bool staged = nB <= (uint32_t)kStage;
             float flo = 0.f, fhi = 0.f, dlo = 0.f, dhi = 0.f, scale = 0.f;
             if (staged) {
-                // stage: free coordinate and ranges of the out-cells (warp reductions)
+                // stage the out-cells: free coordinate and the ranges of both coordinates
                 int m0 = ford(3.0e38f), m1 = ford(-3.0e38f), m2 = m0, m3 = m1;
                 for (uint32_t t = lane; t < nB; t += 32) {
                     const uint32_t k = b.cell_out[f0 + t];
@@ -310,16 +346,15 @@ __global__ void __launch_bounds__(kConnWarps * 32, 2) k_connect(DevBatch b, DevP
                 m1 = __reduce_max_sync(0xFFFFFFFFu, m1);
                 m2 = __reduce_min_sync(0xFFFFFFFFu, m2);
                 m3 = __reduce_max_sync(0xFFFFFFFFu, m3);
-                __syncwarp();
                 flo = funord(m0);
                 fhi = funord(m1);
                 dlo = funord(m2) - (disk ? hj.z : hj.w);
                 dhi = funord(m3) - (disk ? hj.z : hj.w);
                 scale = fhi > flo ? (float)kBins / (fhi - flo) : 0.f;
-                // counting sort by local bin
-                for (uint32_t t = lane; t <= (uint32_t)kBins; t += 32) bin[t] = 0;
+                // counting sort by local bin: histogram, warp scan, scatter
+                if (lane < (uint32_t)kBins) bin[lane] = 0;
                 __syncwarp();
-                uint32_t mybin[kStage / 32];
+                uint32_t mybin[kStage / 32], myk[kStage / 32];
 #pragma unroll
                 for (int q = 0; q < kStage / 32; ++q) {
                     const uint32_t t = lane + 32u * q;
@@ -327,20 +362,19 @@ __global__ void __launch_bounds__(kConnWarps * 32, 2) k_connect(DevBatch b, DevP
                         int bb = (int)floorf((sF[t] - flo) * scale);
                         bb = bb < 0 ? 0 : (bb >= kBins ? kBins - 1 : bb);
                         mybin[q] = (uint32_t)bb;
-                        atomicAdd(&bin[bb + 1], 1u);
+                        myk[q] = sK[t];
+                        atomicAdd(&bin[bb], 1u);
                     }
                 }
                 __syncwarp();
-                if (lane == 0)
-                    for (int t = 1; t <= kBins; ++t) bin[t] += bin[t - 1];
-                __syncwarp();
-                // scatter (B index, hit) into bin order; sF keeps the staged order, so read first
-                uint32_t myk[kStage / 32];
-#pragma unroll
-                for (int q = 0; q < kStage / 32; ++q) {
-                    const uint32_t t = lane + 32u * q;
-                    if (t < nB) myk[q] = sK[t];
+                const uint32_t cnt = lane < (uint32_t)kBins ? bin[lane] : 0u;
+                uint32_t incl = cnt;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= (uint32_t)o) incl += t;
                 }
+                __syncwarp();
+                if (lane < (uint32_t)kBins) bin[lane] = incl - cnt;   // start of bin
                 __syncwarp();
 #pragma unroll
                 for (int q = 0; q < kStage / 32; ++q) {
@@ -352,7 +386,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 2) k_connect(DevBatch b, DevP
                     }
                 }
                 __syncwarp();
-                // bin[t] now holds the end of bin t; starts are bin[t - 1] (bin[-1] = 0)
+                // bin[t] is now the end of bin t; the start of bin t is bin[t - 1] (0 for t = 0)
             }
             for (uint32_t si = 0; si < nin; ++si) {
                 const uint32_t Li = p.in_layer[Lj][si];
@@ -360,66 +394,111 @@ __global__ void __launch_bounds__(kConnWarps * 32, 2) k_connect(DevBatch b, DevP
                 const Window w = phi_window(bk, Li, phij, p);
                 const uint32_t nc = w.size();
                 for (uint32_t c0 = 0; c0 < nc; c0 += 32) {
+                    // ---- set-up of one in-cell per lane ----
                     const uint32_t c = c0 + lane;
-                    if (c >= nc) continue;
-                    const uint32_t i = w.pos(c);
-                    const float4 hi = b.hs[i];
-                    if (!doublet_test(b, p, i, hi, j)) continue;
-                    const RZ32 a = rz32(hi, hj);
-                    const double na64 = p.cut_mode == CUT_FP64
-                                            ? seglen64(b.r64[i], (double)hi.z, b.r64[j], (double)hj.z)
-                                            : 0.0;
-                    uint32_t q0 = 0, q1 = nB;
-                    if (staged) {
-                        float lo, hi_;
-                        if (cone_window(a.ar, a.az, disk ? hj.w : hj.z, dlo, dhi, disk, p.tan_win,
-                                        lo, hi_)) {
-                            if (hi_ < flo || lo > fhi) continue;
-                            int b0 = (int)floorf((lo - flo) * scale);
-                            int b1 = (int)floorf((hi_ - flo) * scale);
-                            b0 = b0 < 0 ? 0 : (b0 >= kBins ? kBins - 1 : b0);
-                            b1 = b1 < 0 ? 0 : (b1 >= kBins ? kBins - 1 : b1);
-                            q0 = b0 ? bin[b0 - 1] : 0u;
-                            q1 = bin[b1];
+                    uint32_t q0 = 0, q1 = 0;
+                    me.npass = 0;
+                    me.seq = 0;
+                    bool valid = c < nc;
+                    if (valid) {
+                        const uint32_t i = w.pos(c);
+                        const float4 hi = b.hs[i];
+                        valid = doublet_test(b, p, i, hi, j);
+                        if (valid) {
+                            me.i = i;
+                            me.hi = hi;
+                            me.a = rz32(hi, hj);
+                            me.na64 = p.cut_mode == CUT_FP64
+                                          ? seglen64(b.r64[i], (double)hi.z, b.r64[j], (double)hj.z)
+                                          : 0.0;
+                            q1 = nB;
+                            float lo, hi_;
+                            if (staged && cone_window(me.a.ar, me.a.az, disk ? hj.w : hj.z, dlo,
+                                                      dhi, disk, p.tan_win, lo, hi_)) {
+                                if (hi_ < flo || lo > fhi) {
+                                    q1 = 0;
+                                } else {
+                                    int b0 = (int)floorf((lo - flo) * scale);
+                                    int b1 = (int)floorf((hi_ - flo) * scale);
+                                    b0 = b0 < 0 ? 0 : (b0 >= kBins ? kBins - 1 : b0);
+                                    b1 = b1 < 0 ? 0 : (b1 >= kBins ? kBins - 1 : b1);
+                                    q0 = b0 ? bin[b0 - 1] : 0u;
+                                    q1 = bin[b1];
+                                }
+                            }
                         }
                     }
-                    auto pass = [&](uint32_t q, uint32_t &B) {
-                        uint32_t k;
+                    const uint32_t cnt = q1 - q0;
+                    me.q0 = q0;
+                    uint32_t incl = cnt;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                        if (lane >= (uint32_t)o) incl += t;
+                    }
+                    me.pre = incl - cnt;
+                    const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                    if (lane == 0) s_np[wid] = 0;
+                    __syncwarp();
+                    // ---- the warp tests all candidates, 32 at a time ----
+                    for (uint32_t t0 = 0; t0 < tot; t0 += 32) {
+                        const uint32_t t = t0 + lane;
+                        if (t >= tot) continue;
+                        uint32_t lo = 0, hi_ = 31;              // last lane with pre <= t
+                        while (lo < hi_) {
+                            const uint32_t mid = (lo + hi_ + 1) >> 1;
+                            if (LL[mid].pre <= t) lo = mid; else hi_ = mid - 1;
+                        }
+                        const Lane &ow = LL[lo];
+                        const uint32_t q = ow.q0 + (t - ow.pre);
+                        uint32_t B, k;
                         if (staged) { B = sB[q]; k = sK[q]; }
                         else { B = f0 + q; k = b.cell_out[B]; }
-                        return triplet_test(b, p, i, j, k, hi, hj, b.hs[k], a, na64);
-                    };
-                    uint32_t npass = 0, B;
-                    for (uint32_t q = q0; q < q1; ++q) npass += pass(q, B);
-                    if (!npass) continue;
-                    const uint32_t A = find_cell(b, p, bk, i, hi, slot_i, Lj, j);
-                    if (A == kNone) continue;
-                    // an in-cell's edges over several out-layer slots: append to its list
-                    uint32_t have = s == 0 ? 0u : b.nbr_n[A];
-                    const uint32_t base = atomicAdd(&b.cnt[C_EDGES * b.E + e], npass);
-                    const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
-                    const uint32_t nw = base >= cap ? 0u : min(npass, cap - base);
-                    if (nw < npass) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
-                    const uint32_t first = b.edge_off[e] + base;
-                    uint32_t written = 0;
-                    for (uint32_t q = q0; q < q1 && written < nw; ++q)
-                        if (pass(q, B)) b.nbr[first + written++] = B;
-                    if (have == 0) {
-                        b.nbr_first[A] = first;
-                        b.nbr_n[A] = written;
-                    } else {
-                        // several slots: move the earlier edges next to the new ones
-                        const uint32_t old = b.nbr_first[A];
-                        const uint32_t base2 = atomicAdd(&b.cnt[C_EDGES * b.E + e], have + written);
-                        const uint32_t nw2 = base2 >= cap ? 0u : min(have + written, cap - base2);
-                        if (nw2 < have + written) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
-                        const uint32_t f2 = b.edge_off[e] + base2;
-                        uint32_t w2 = 0;
-                        for (uint32_t t = 0; t < have && w2 < nw2; ++t) b.nbr[f2 + w2++] = b.nbr[old + t];
-                        for (uint32_t t = 0; t < written && w2 < nw2; ++t) b.nbr[f2 + w2++] = b.nbr[first + t];
-                        b.nbr_first[A] = f2;
-                        b.nbr_n[A] = w2;
+                        if (triplet_test(b, p, ow.i, j, k, ow.hi, hj, b.hs[k], ow.a, ow.na64)) {
+                            const uint32_t slot = atomicAdd(&s_np[wid], 1u);
+                            if (slot < (uint32_t)kPass) {
+                                s_pB[wid][slot] = B;
+                                s_pown[wid][slot] = (uint8_t)lo;
+                                atomicAdd(&LL[lo].npass, 1u);
+                            } else {
+                                LL[lo].seq = 1;
+                            }
+                        }
                     }
+                    __syncwarp();
+                    // ---- in-cells with passes write their edges ----
+                    if (valid && (me.npass || me.seq)) {
+                        const uint32_t A = find_cell(b, p, bk, me.i, me.hi, slot_i, Lj, j);
+                        if (A != kNone) {
+                            if (me.seq) {
+                                uint32_t n = 0;
+                                for (uint32_t q = q0; q < q1; ++q) {
+                                    const uint32_t B = staged ? sB[q] : f0 + q;
+                                    const uint32_t k = staged ? sK[q] : b.cell_out[B];
+                                    n += triplet_test(b, p, me.i, j, k, me.hi, hj, b.hs[k], me.a, me.na64);
+                                }
+                                uint32_t q = q0;
+                                append_edges(b, e, A, s == 0, n, [&](uint32_t) {
+                                    for (;; ++q) {
+                                        const uint32_t B = staged ? sB[q] : f0 + q;
+                                        const uint32_t k = staged ? sK[q] : b.cell_out[B];
+                                        if (triplet_test(b, p, me.i, j, k, me.hi, hj, b.hs[k], me.a, me.na64)) {
+                                            ++q;
+                                            return B;
+                                        }
+                                    }
+                                });
+                            } else {
+                                const uint32_t np = min(s_np[wid], (uint32_t)kPass);
+                                uint32_t q = 0;
+                                append_edges(b, e, A, s == 0, me.npass, [&](uint32_t) {
+                                    while (s_pown[wid][q] != lane) ++q;
+                                    return s_pB[wid][q++];
+                                });
+                                (void)np;
+                            }
+                        }
+                    }
+                    __syncwarp();
                 }
             }
             __syncwarp();
