@@ -246,7 +246,7 @@ __device__ __forceinline__ bool cone_window(float ar, float az, float base, floa
 
 constexpr int kConnWarps = 8;
 constexpr int kStage = 256;     // out-cells of one junction staged per out-layer slot
-constexpr int kBins = 32;       // local bins of the free coordinate
+constexpr int kBins = 128;      // local bins of the free coordinate (multiple of 32)
 constexpr int kPass = 64;       // passing triplets collected per round of 32 in-cells
 
 // Order-preserving int encoding of floats (for warp min / max reductions).
@@ -288,25 +288,25 @@ __device__ __forceinline__ void append_edges(const DevBatch &b, uint32_t e, uint
 // whose passes overflow the list is redone alone.
 __global__ void __launch_bounds__(kConnWarps * 32, 2) k_connect(DevBatch b, DevParams p)
 {
-    struct Lane {
-        float4 hi;
-        RZ32 a;
-        double na64;
-        uint32_t i, q0, pre, npass;
-        uint32_t seq;
-    };
+    // per-warp staging and per-lane in-cell records (structure of arrays: lanes reading other
+    // lanes' records hit distinct banks)
     __shared__ uint32_t s_B[kConnWarps][kStage], s_k[kConnWarps][kStage];
     __shared__ float s_f[kConnWarps][kStage];
-    __shared__ uint32_t s_bin[kConnWarps][kBins + 1];
-    __shared__ Lane s_lane[kConnWarps][32];
+    __shared__ uint32_t s_bin[kConnWarps][kBins];
+    __shared__ float4 s_hi[kConnWarps][32], s_a[kConnWarps][32];
+    __shared__ double s_na[kConnWarps][32];
+    __shared__ uint32_t s_i[kConnWarps][32], s_q0[kConnWarps][32], s_pre[kConnWarps][32],
+        s_npass[kConnWarps][32], s_seq[kConnWarps][32];
     __shared__ uint32_t s_pB[kConnWarps][kPass];
     __shared__ uint8_t s_pown[kConnWarps][kPass];
     __shared__ uint32_t s_np[kConnWarps];
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
     uint32_t *sB = s_B[wid], *sK = s_k[wid], *bin = s_bin[wid];
     float *sF = s_f[wid];
-    Lane *LL = s_lane[wid];
-    Lane &me = LL[lane];
+    float4 *Hi = s_hi[wid], *Aa = s_a[wid];
+    double *Na = s_na[wid];
+    uint32_t *Ii = s_i[wid], *Q0 = s_q0[wid], *Pre = s_pre[wid], *Np = s_npass[wid],
+             *Seq = s_seq[wid];
     const uint32_t nk = p.n_keys;
     const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t jj = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; jj < b.N;
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 2) k_connect(DevBatch b, DevP
                 dhi = funord(m3) - (disk ? hj.z : hj.w);
                 scale = fhi > flo ? (float)kBins / (fhi - flo) : 0.f;
                 // counting sort by local bin: histogram, warp scan, scatter
-                if (lane < (uint32_t)kBins) bin[lane] = 0;
+                for (uint32_t t = lane; t < (uint32_t)kBins; t += 32) bin[t] = 0;
                 __syncwarp();
                 uint32_t mybin[kStage / 32], myk[kStage / 32];
 #pragma unroll
@@ -367,15 +367,23 @@ __global__ void __launch_bounds__(kConnWarps * 32, 2) k_connect(DevBatch b, DevP
                     }
                 }
                 __syncwarp();
-                const uint32_t cnt = lane < (uint32_t)kBins ? bin[lane] : 0u;
-                uint32_t incl = cnt;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                    if (lane >= (uint32_t)o) incl += t;
+                {
+                    // exclusive scan of the kBins counts: kBins / 32 consecutive bins per lane
+                    constexpr int per = kBins / 32;
+                    uint32_t v[per], sum = 0;
+#pragma unroll
+                    for (int q = 0; q < per; ++q) { v[q] = bin[lane * per + q]; sum += v[q]; }
+                    uint32_t incl = sum;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                        if (lane >= (uint32_t)o) incl += t;
+                    }
+                    uint32_t run = incl - sum;
+                    __syncwarp();
+#pragma unroll
+                    for (int q = 0; q < per; ++q) { bin[lane * per + q] = run; run += v[q]; }
+                    __syncwarp();
                 }
-                __syncwarp();
-                if (lane < (uint32_t)kBins) bin[lane] = incl - cnt;   // start of bin
-                __syncwarp();
 #pragma unroll
                 for (int q = 0; q < kStage / 32; ++q) {
                     const uint32_t t = lane + 32u * q;
@@ -396,24 +404,29 @@ __global__ void __launch_bounds__(kConnWarps * 32, 2) k_connect(DevBatch b, DevP
                 for (uint32_t c0 = 0; c0 < nc; c0 += 32) {
                     // ---- set-up of one in-cell per lane ----
                     const uint32_t c = c0 + lane;
-                    uint32_t q0 = 0, q1 = 0;
-                    me.npass = 0;
-                    me.seq = 0;
+                    uint32_t q0 = 0, q1 = 0, my_i = 0;
+                    float4 my_hi = make_float4(0.f, 0.f, 0.f, 0.f);
+                    RZ32 my_a{0.f, 0.f, 0.f, 0.f};
+                    double my_na = 0.0;
+                    Np[lane] = 0;
+                    Seq[lane] = 0;
                     bool valid = c < nc;
                     if (valid) {
-                        const uint32_t i = w.pos(c);
-                        const float4 hi = b.hs[i];
-                        valid = doublet_test(b, p, i, hi, j);
+                        my_i = w.pos(c);
+                        my_hi = b.hs[my_i];
+                        valid = doublet_test(b, p, my_i, my_hi, j);
                         if (valid) {
-                            me.i = i;
-                            me.hi = hi;
-                            me.a = rz32(hi, hj);
-                            me.na64 = p.cut_mode == CUT_FP64
-                                          ? seglen64(b.r64[i], (double)hi.z, b.r64[j], (double)hj.z)
-                                          : 0.0;
+                            my_a = rz32(my_hi, hj);
+                            my_na = p.cut_mode == CUT_FP64
+                                        ? seglen64(b.r64[my_i], (double)my_hi.z, b.r64[j], (double)hj.z)
+                                        : 0.0;
+                            Ii[lane] = my_i;
+                            Hi[lane] = my_hi;
+                            Aa[lane] = make_float4(my_a.ar, my_a.az, my_a.na, my_a.Ea);
+                            Na[lane] = my_na;
                             q1 = nB;
                             float lo, hi_;
-                            if (staged && cone_window(me.a.ar, me.a.az, disk ? hj.w : hj.z, dlo,
+                            if (staged && cone_window(my_a.ar, my_a.az, disk ? hj.w : hj.z, dlo,
                                                       dhi, disk, p.tan_win, lo, hi_)) {
                                 if (hi_ < flo || lo > fhi) {
                                     q1 = 0;
@@ -429,13 +442,13 @@ __global__ void __launch_bounds__(kConnWarps * 32, 2) k_connect(DevBatch b, DevP
                         }
                     }
                     const uint32_t cnt = q1 - q0;
-                    me.q0 = q0;
+                    Q0[lane] = q0;
                     uint32_t incl = cnt;
                     for (int o = 1; o < 32; o <<= 1) {
                         const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
                         if (lane >= (uint32_t)o) incl += t;
                     }
-                    me.pre = incl - cnt;
+                    Pre[lane] = incl - cnt;
                     const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
                     if (lane == 0) s_np[wid] = 0;
                     __syncwarp();
@@ -446,55 +459,55 @@ __global__ void __launch_bounds__(kConnWarps * 32, 2) k_connect(DevBatch b, DevP
                         uint32_t lo = 0, hi_ = 31;              // last lane with pre <= t
                         while (lo < hi_) {
                             const uint32_t mid = (lo + hi_ + 1) >> 1;
-                            if (LL[mid].pre <= t) lo = mid; else hi_ = mid - 1;
+                            if (Pre[mid] <= t) lo = mid; else hi_ = mid - 1;
                         }
-                        const Lane &ow = LL[lo];
-                        const uint32_t q = ow.q0 + (t - ow.pre);
+                        const uint32_t q = Q0[lo] + (t - Pre[lo]);
                         uint32_t B, k;
                         if (staged) { B = sB[q]; k = sK[q]; }
                         else { B = f0 + q; k = b.cell_out[B]; }
-                        if (triplet_test(b, p, ow.i, j, k, ow.hi, hj, b.hs[k], ow.a, ow.na64)) {
+                        const float4 av = Aa[lo];
+                        const RZ32 oa{av.x, av.y, av.z, av.w};
+                        if (triplet_test(b, p, Ii[lo], j, k, Hi[lo], hj, b.hs[k], oa, Na[lo])) {
                             const uint32_t slot = atomicAdd(&s_np[wid], 1u);
                             if (slot < (uint32_t)kPass) {
                                 s_pB[wid][slot] = B;
                                 s_pown[wid][slot] = (uint8_t)lo;
-                                atomicAdd(&LL[lo].npass, 1u);
+                                atomicAdd(&Np[lo], 1u);
                             } else {
-                                LL[lo].seq = 1;
+                                Seq[lo] = 1;
                             }
                         }
                     }
                     __syncwarp();
                     // ---- in-cells with passes write their edges ----
-                    if (valid && (me.npass || me.seq)) {
-                        const uint32_t A = find_cell(b, p, bk, me.i, me.hi, slot_i, Lj, j);
+                    const uint32_t my_np = Np[lane];
+                    if (valid && (my_np || Seq[lane])) {
+                        const uint32_t A = find_cell(b, p, bk, my_i, my_hi, slot_i, Lj, j);
                         if (A != kNone) {
-                            if (me.seq) {
+                            if (Seq[lane]) {
                                 uint32_t n = 0;
                                 for (uint32_t q = q0; q < q1; ++q) {
                                     const uint32_t B = staged ? sB[q] : f0 + q;
                                     const uint32_t k = staged ? sK[q] : b.cell_out[B];
-                                    n += triplet_test(b, p, me.i, j, k, me.hi, hj, b.hs[k], me.a, me.na64);
+                                    n += triplet_test(b, p, my_i, j, k, my_hi, hj, b.hs[k], my_a, my_na);
                                 }
                                 uint32_t q = q0;
                                 append_edges(b, e, A, s == 0, n, [&](uint32_t) {
                                     for (;; ++q) {
                                         const uint32_t B = staged ? sB[q] : f0 + q;
                                         const uint32_t k = staged ? sK[q] : b.cell_out[B];
-                                        if (triplet_test(b, p, me.i, j, k, me.hi, hj, b.hs[k], me.a, me.na64)) {
+                                        if (triplet_test(b, p, my_i, j, k, my_hi, hj, b.hs[k], my_a, my_na)) {
                                             ++q;
                                             return B;
                                         }
                                     }
                                 });
                             } else {
-                                const uint32_t np = min(s_np[wid], (uint32_t)kPass);
                                 uint32_t q = 0;
-                                append_edges(b, e, A, s == 0, me.npass, [&](uint32_t) {
+                                append_edges(b, e, A, s == 0, my_np, [&](uint32_t) {
                                     while (s_pown[wid][q] != lane) ++q;
                                     return s_pB[wid][q++];
                                 });
-                                (void)np;
                             }
                         }
                     }
