@@ -286,7 +286,7 @@ __device__ __forceinline__ void append_edges(const DevBatch &b, uint32_t e, uint
 // shared list; each in-cell with passes finds its own index and appends its edge list.  A slot
 // with more than kStage out-cells is tested against all of them from global memory; an in-cell
 // whose passes overflow the list is redone alone.
-__global__ void __launch_bounds__(kConnWarps * 32, 2) k_connect(DevBatch b, DevParams p)
+__global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevParams p)
 {
     // per-warp staging and per-lane in-cell records (structure of arrays: lanes reading other
     // lanes' records hit distinct banks)
