@@ -8,105 +8,23 @@
 //  3. Highland scattering angle from the reference momentum, kink variances projected by
 //     1 + cot^2 (transverse) and (1 + cot^2)^2 (line);
 //  4. transverse broken line (offsets u_i + curvature correction delta) and line broken line
-//     (z_i), normal equations solved by Cholesky;
+//     (z_i); the normal equations are a pentadiagonal block bordered (transverse) by the
+//     curvature row, solved by a banded Cholesky and the Schur complement of the border;
 //  5. fitted circle at hit 0 and its point of closest approach to the z axis.
 // Precision modes: FP64 (all steps double), MIXED (arithmetic double, transcendentals float:
 // the normal matrices mix kink weights up to ~1e14 with measurement weights ~1e6, which float
-// assembly cannot hold), FP32 (all float).
+// assembly cannot hold), FP32 (all float).  The hit count is a template parameter, so every
+// array lives in registers.
 #include "pxr_dev.cuh"
 
 namespace pxr {
 
 constexpr double kKpt = 0.299792458e-2;   // pT [GeV] = K B [T] R [cm]
-constexpr int kM = kMaxHits + 1;
 
 template <typename T>
 __device__ __forceinline__ T sqrt_t(T v) { return sqrt(v); }
 template <>
 __device__ __forceinline__ float sqrt_t<float>(float v) { return sqrtf(v); }
-
-// Dense Cholesky of the m x m SPD matrix A (row-major, m <= kM), then two triangular solves.
-template <typename T>
-__device__ __forceinline__ bool chol_solve(int m, T *A, const T *b, T *x)
-{
-    for (int j = 0; j < m; ++j) {
-        T s = A[j * kM + j];
-        for (int k = 0; k < j; ++k) s -= A[j * kM + k] * A[j * kM + k];
-        if (!(s > T(0))) return false;
-        const T d = sqrt_t(s);
-        A[j * kM + j] = d;
-        for (int i = j + 1; i < m; ++i) {
-            T t = A[i * kM + j];
-            for (int k = 0; k < j; ++k) t -= A[i * kM + k] * A[j * kM + k];
-            A[i * kM + j] = t / d;
-        }
-    }
-    T y[kM];
-    for (int i = 0; i < m; ++i) {
-        T t = b[i];
-        for (int k = 0; k < i; ++k) t -= A[i * kM + k] * y[k];
-        y[i] = t / A[i * kM + i];
-    }
-    for (int i = m - 1; i >= 0; --i) {
-        T t = y[i];
-        for (int k = i + 1; k < m; ++k) t -= A[k * kM + i] * x[k];
-        x[i] = t / A[i * kM + i];
-    }
-    return true;
-}
-
-// Normal equations of the broken line: measurements meas (weights w), kinks at inner points with
-// variance kv, optional curvature unknown at index n.  Assembled in TB, solved in TS.
-template <typename TB, typename TS>
-__device__ __forceinline__ bool broken_line(int n, const TB *s, const TB *meas, const TB *w,
-                                            const TB *kv, bool curv, TS *x, TS &chi2)
-{
-    const int m = n + (curv ? 1 : 0);
-    TB A[kM * kM];
-    TB bb[kM];
-    for (int r = 0; r < m; ++r) {
-        bb[r] = TB(0);
-        for (int c = 0; c < m; ++c) A[r * kM + c] = TB(0);
-    }
-    for (int i = 0; i < n; ++i) {
-        A[i * kM + i] += w[i];
-        bb[i] += w[i] * meas[i];
-    }
-    for (int j = 1; j + 1 < n; ++j) {
-        const TB ds0 = s[j] - s[j - 1], ds1 = s[j + 1] - s[j];
-        const TB wk = TB(1) / kv[j];
-        const int idx[4] = {j - 1, j, j + 1, n};
-        const TB g[4] = {TB(1) / ds0, -TB(1) / ds0 - TB(1) / ds1, TB(1) / ds1,
-                         curv ? TB(0.5) * (ds0 + ds1) : TB(0)};
-        const int q = curv ? 4 : 3;
-        for (int r = 0; r < q; ++r)
-            for (int c = 0; c < q; ++c) A[idx[r] * kM + idx[c]] += wk * g[r] * g[c];
-    }
-    TS As[kM * kM], bs[kM];
-    for (int r = 0; r < m; ++r) {
-        bs[r] = TS(bb[r]);
-        for (int c = 0; c < m; ++c) As[r * kM + c] = TS(A[r * kM + c]);
-    }
-    if (!chol_solve<TS>(m, As, bs, x)) return false;
-    TS c2 = TS(0);
-    for (int i = 0; i < n; ++i) {
-        const TS r = TS(meas[i]) - x[i];
-        c2 += TS(w[i]) * r * r;
-    }
-    for (int j = 1; j + 1 < n; ++j) {
-        const TS ds0 = TS(s[j]) - TS(s[j - 1]), ds1 = TS(s[j + 1]) - TS(s[j]);
-        TS beta = (x[j + 1] - x[j]) / ds1 - (x[j] - x[j - 1]) / ds0;
-        if (curv) beta += TS(0.5) * (ds0 + ds1) * x[n];
-        c2 += beta * beta / TS(kv[j]);
-    }
-    chi2 = c2;
-    return true;
-}
-
-struct FitOut {
-    double pt, phi, cot, dxy, dz, chi2;
-    int8_t q, status;
-};
 
 // Transcendentals in float (FT = true) or in the argument's own type.
 template <bool FT, typename T>
@@ -114,18 +32,143 @@ __device__ __forceinline__ T atan2_t(T y, T x) { return FT ? T(atan2f(float(y), 
 template <bool FT, typename T>
 __device__ __forceinline__ T log_t(T v) { return FT ? T(logf(float(v))) : log(v); }
 
-// TC: prefit + residuals; TB: scattering + assembly; TS: solves + conversion; FT: float
-// transcendentals (angles and logarithms need ~1e-7 relative, far inside the tolerances).
-template <typename TC, typename TB, typename TS, bool FT>
-__device__ void fit_track(int n, const float *X, const float *Y, const float *Z,
-                          const uint8_t *L, const DevParams &p, FitOut &o)
+struct FitOut {
+    double pt, phi, cot, dxy, dz, chi2;
+    int8_t q, status;
+};
+
+// Symmetric positive definite pentadiagonal matrix (diagonal d0, first and second
+// super-diagonals d1, d2) factored as L L^T in place (L's diagonal in d0, sub-diagonals in d1, d2).
+template <int N, typename T>
+__device__ __forceinline__ bool band_factor(T (&d0)[N], T (&d1)[N], T (&d2)[N])
+{
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        T s = d0[i];
+        if (i >= 1) s -= d1[i - 1] * d1[i - 1];
+        if (i >= 2) s -= d2[i - 2] * d2[i - 2];
+        if (!(s > T(0))) return false;
+        const T l = sqrt_t(s);
+        d0[i] = l;
+        if (i + 1 < N) {
+            T t = d1[i];
+            if (i >= 1) t -= d2[i - 1] * d1[i - 1];
+            d1[i] = t / l;
+        }
+        if (i + 2 < N) d2[i] = d2[i] / l;
+    }
+    return true;
+}
+
+// Solve (L L^T) x = b with the factor of band_factor.
+template <int N, typename T>
+__device__ __forceinline__ void band_solve(const T (&l0)[N], const T (&l1)[N], const T (&l2)[N],
+                                           const T (&b)[N], T (&x)[N])
+{
+    T y[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        T t = b[i];
+        if (i >= 1) t -= l1[i - 1] * y[i - 1];
+        if (i >= 2) t -= l2[i - 2] * y[i - 2];
+        y[i] = t / l0[i];
+    }
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+        T t = y[i];
+        if (i + 1 < N) t -= l1[i] * x[i + 1];
+        if (i + 2 < N) t -= l2[i] * x[i + 2];
+        x[i] = t / l0[i];
+    }
+}
+
+// Broken line over N points: measurements meas (weights w), kinks at the inner points with
+// variances kv, and (CURV) one curvature unknown.  Normal equations: a pentadiagonal block for
+// the offsets (each kink couples three neighbours) bordered by the curvature row; the border is
+// eliminated through the Schur complement.  Returns the offsets x, the curvature correction and
+// the chi2 at the minimum.
+template <int N, bool CURV, typename T>
+__device__ __forceinline__ bool broken_line_n(const T (&s)[N], const T (&meas)[N],
+                                              const T (&w)[N], const T (&kv)[N], T (&x)[N],
+                                              T &delta, T &chi2)
+{
+    T d0[N], d1[N], d2[N], c[N], b[N];
+    T dd = T(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        d0[i] = w[i];
+        d1[i] = T(0);
+        d2[i] = T(0);
+        c[i] = T(0);
+        b[i] = w[i] * meas[i];
+    }
+#pragma unroll
+    for (int j = 1; j + 1 < N; ++j) {
+        const T ds0 = s[j] - s[j - 1], ds1 = s[j + 1] - s[j];
+        const T wk = T(1) / kv[j];
+        const T g0 = T(1) / ds0, g2 = T(1) / ds1, g1 = -g0 - g2;
+        d0[j - 1] += wk * g0 * g0;
+        d0[j] += wk * g1 * g1;
+        d0[j + 1] += wk * g2 * g2;
+        d1[j - 1] += wk * g0 * g1;
+        d1[j] += wk * g1 * g2;
+        d2[j - 1] += wk * g0 * g2;
+        if (CURV) {
+            const T gd = T(0.5) * (ds0 + ds1);
+            c[j - 1] += wk * g0 * gd;
+            c[j] += wk * g1 * gd;
+            c[j + 1] += wk * g2 * gd;
+            dd += wk * gd * gd;
+        }
+    }
+    if (!band_factor<N, T>(d0, d1, d2)) return false;
+    band_solve<N, T>(d0, d1, d2, b, x);
+    delta = T(0);
+    if (CURV) {
+        T z[N];
+        band_solve<N, T>(d0, d1, d2, c, z);
+        T cy = T(0), cz = T(0);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            cy += c[i] * x[i];
+            cz += c[i] * z[i];
+        }
+        const T schur = dd - cz;
+        if (!(schur > T(0))) return false;
+        delta = -cy / schur;
+#pragma unroll
+        for (int i = 0; i < N; ++i) x[i] -= z[i] * delta;
+    }
+    T c2 = T(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const T r = meas[i] - x[i];
+        c2 += w[i] * r * r;
+    }
+#pragma unroll
+    for (int j = 1; j + 1 < N; ++j) {
+        const T ds0 = s[j] - s[j - 1], ds1 = s[j + 1] - s[j];
+        T beta = (x[j + 1] - x[j]) / ds1 - (x[j] - x[j - 1]) / ds0;
+        if (CURV) beta += T(0.5) * (ds0 + ds1) * delta;
+        c2 += beta * beta / kv[j];
+    }
+    chi2 = c2;
+    return true;
+}
+
+// TC: prefit + residuals + arc lengths; T: everything else (scattering, solves, conversion);
+// FT: float transcendentals (angles and logarithms need ~1e-7 relative, far inside the
+// tolerances).
+template <int N, typename TC, typename T, bool FT>
+__device__ void fit_n(const float *X, const float *Y, const float *Z, const uint8_t *L,
+                      const DevParams &p, FitOut &o)
 {
     o = FitOut{0, 0, 0, 0, 0, 0, 0, 0};
-    if (n < 3 || n > kMaxHits) { o.status = 4; return; }
-    TC px[kMaxHits], py[kMaxHits];
+    TC px[N], py[N];
     const TC x0 = TC(X[0]), y0 = TC(Y[0]);
-    for (int i = 0; i < n; ++i) { px[i] = TC(X[i]) - x0; py[i] = TC(Y[i]) - y0; }
-    const int ib = n / 2, ic = n - 1;
+#pragma unroll
+    for (int i = 0; i < N; ++i) { px[i] = TC(X[i]) - x0; py[i] = TC(Y[i]) - y0; }
+    constexpr int ib = N / 2, ic = N - 1;
     const TC ux = px[ib], uy = py[ib], vx = px[ic], vy = py[ic];
     const TC D = TC(2) * (ux * vy - uy * vx);
     if (D == TC(0)) { o.status = 1; return; }
@@ -134,103 +177,117 @@ __device__ void fit_track(int n, const float *X, const float *Y, const float *Z,
     const TC R0 = sqrt_t(Cx * Cx + Cy * Cy);
     const TC sgn = D > TC(0) ? TC(1) : TC(-1);
 
-    TB s[kMaxHits], yr[kMaxHits], z[kMaxHits];
-    for (int i = 0; i < n; ++i) {
+    T s[N], yr[N], z[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
         const TC dx = px[i] - Cx, dy = py[i] - Cy;
         const TC pw = (px[i] * px[i] + py[i] * py[i]) - TC(2) * (px[i] * Cx + py[i] * Cy);
-        yr[i] = TB(pw / (sqrt_t(dx * dx + dy * dy) + R0));
+        yr[i] = T(pw / (sqrt_t(dx * dx + dy * dy) + R0));
         const TC cr = -Cx * dy + Cy * dx;
         const TC dt = -Cx * dx - Cy * dy;
-        s[i] = TB(R0 * atan2_t<FT>(sgn * cr, dt));
-        z[i] = TB(Z[i]);
+        s[i] = T(R0 * atan2_t<FT>(sgn * cr, dt));
+        z[i] = T(Z[i]);
     }
 
     // multiple scattering
-    const TB cot0 = (z[ic] - z[0]) / (s[ic] - s[0]);
-    const TB sec2 = TB(1) + cot0 * cot0;
-    const TB pmom = TB(kKpt * p.bfield) * TB(R0) * sqrt_t(sec2);
-    TB kvT[kMaxHits], kvL[kMaxHits], wT[kMaxHits], wL[kMaxHits];
-    const TB wrphi = TB(1.0 / (p.sigma_rphi * p.sigma_rphi));
-    const TB wz = TB(1.0 / (p.sigma_z * p.sigma_z));
-    for (int i = 0; i < n; ++i) {
-        kvT[i] = TB(1);
-        kvL[i] = TB(1);
+    const T cot0 = (z[ic] - z[0]) / (s[ic] - s[0]);
+    const T sec2 = T(1) + cot0 * cot0;
+    const T pmom = T(kKpt * p.bfield) * T(R0) * sqrt_t(sec2);
+    T kvT[N], kvL[N], wT[N], wL[N];
+    const T wrphi = T(1.0 / (p.sigma_rphi * p.sigma_rphi));
+    const T wz = T(1.0 / (p.sigma_z * p.sigma_z));
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        kvT[i] = T(1);
+        kvL[i] = T(1);
         wT[i] = wrphi;
         if (p.is_disk[L[i]]) {
-            const TB sz = TB(p.sigma_z) * fabs(cot0);
-            wL[i] = TB(1) / (sz * sz);
+            const T sz = T(p.sigma_z) * fabs(cot0);
+            wL[i] = T(1) / (sz * sz);
         } else {
             wL[i] = wz;
         }
     }
-    for (int j = 1; j + 1 < n; ++j) {
-        const TB path = p.is_disk[L[j]] ? sqrt_t(sec2) / fabs(cot0) : sqrt_t(sec2);
-        const TB xx = TB(p.x_over_x0) * path;
-        const TB th0 = (TB(0.0136) / pmom) * sqrt_t(xx) * (TB(1) + TB(0.038) * log_t<FT>(xx));
-        const TB th2 = th0 * th0;
+#pragma unroll
+    for (int j = 1; j + 1 < N; ++j) {
+        const T path = p.is_disk[L[j]] ? sqrt_t(sec2) / fabs(cot0) : sqrt_t(sec2);
+        const T xx = T(p.x_over_x0) * path;
+        const T th0 = (T(0.0136) / pmom) * sqrt_t(xx) * (T(1) + T(0.038) * log_t<FT>(xx));
+        const T th2 = th0 * th0;
         kvT[j] = th2 * sec2;
         kvL[j] = th2 * sec2 * sec2;
-        if (!(kvT[j] > TB(0)) || !(kvL[j] > TB(0))) { o.status = 4; return; }
+        if (!(kvT[j] > T(0)) || !(kvL[j] > T(0))) { o.status = 4; return; }
     }
 
-    TS xT[kM], xL[kM];
-    TS chi2T, chi2L;
-    if (!broken_line<TB, TS>(n, s, yr, wT, kvT, true, xT, chi2T) ||
-        !broken_line<TB, TS>(n, s, z, wL, kvL, false, xL, chi2L)) {
+    T xT[N], xL[N], delta, dummy, chi2T, chi2L;
+    if (!broken_line_n<N, true, T>(s, yr, wT, kvT, xT, delta, chi2T) ||
+        !broken_line_n<N, false, T>(s, z, wL, kvL, xL, dummy, chi2L)) {
         o.status = 3;
         return;
     }
 
     // conversion to the point of closest approach
-    const TS delta = xT[n];
-    const TS R0s = TS(R0);
-    const TS kappa = TS(1) / R0s + delta;
-    if (kappa == TS(0) || !isfinite(kappa)) { o.status = 2; return; }
-    const TS R = TS(1) / fabs(kappa);
-    const TS sgs = TS(sgn);
-    const TS sgf = kappa > TS(0) ? sgs : -sgs;
-    const TS ds0 = TS(s[1]) - TS(s[0]);
-    const TS alpha = (xT[1] - xT[0]) / ds0 + TS(0.5) * delta * ds0;
-    const TS nx = -TS(Cx) / R0s, ny = -TS(Cy) / R0s;
-    const TS tx = -sgs * ny, ty = sgs * nx;
-    TS ca, sa;
+    const T R0s = T(R0);
+    const T kappa = T(1) / R0s + delta;
+    if (kappa == T(0) || !isfinite(kappa)) { o.status = 2; return; }
+    const T R = T(1) / fabs(kappa);
+    const T sgs = T(sgn);
+    const T sgf = kappa > T(0) ? sgs : -sgs;
+    const T ds0 = s[1] - s[0];
+    const T alpha = (xT[1] - xT[0]) / ds0 + T(0.5) * delta * ds0;
+    const T nx = -T(Cx) / R0s, ny = -T(Cy) / R0s;
+    const T tx = -sgs * ny, ty = sgs * nx;
+    T ca, sa;
     if constexpr (FT) {
         // cos of a small angle rounds to 1 in float; 1 - 2 sin^2(a/2) keeps its deviation
-        const TS sh = TS(sinf(float(alpha * TS(0.5))));
-        ca = TS(1) - TS(2) * sh * sh;
-        sa = TS(sinf(float(alpha)));
+        const T sh = T(sinf(float(alpha * T(0.5))));
+        ca = T(1) - T(2) * sh * sh;
+        sa = T(sinf(float(alpha)));
     } else {
         ca = cos(alpha);
         sa = sin(alpha);
     }
-    const TS n2x = nx * ca - tx * sa, n2y = ny * ca - ty * sa;
-    const TS P0x = xT[0] * nx, P0y = xT[0] * ny;
-    const TS Fx = P0x - n2x / kappa, Fy = P0y - n2y / kappa;
-    const TS rx = (P0x - Fx) * fabs(kappa), ry = (P0y - Fy) * fabs(kappa);
-    const TS wx = -TS(X[0]) - Fx, wy = -TS(Y[0]) - Fy;
-    const TS dist = sqrt_t(wx * wx + wy * wy);
-    const TS ex = wx / dist, ey = wy / dist;
-    const TS tpx = -sgf * ey, tpy = sgf * ex;
-    const TS cot = (xL[1] - xL[0]) / ds0;
-    const TS psi = atan2_t<FT>(sgf * (ex * ry - ey * rx), ex * rx + ey * ry);
-    const int qf = sgf > TS(0) ? -1 : 1;
-    o.pt = double(TS(kKpt * p.bfield) * R);
+    const T n2x = nx * ca - tx * sa, n2y = ny * ca - ty * sa;
+    const T P0x = xT[0] * nx, P0y = xT[0] * ny;
+    const T Fx = P0x - n2x / kappa, Fy = P0y - n2y / kappa;
+    const T rx = (P0x - Fx) * fabs(kappa), ry = (P0y - Fy) * fabs(kappa);
+    const T wx = -T(X[0]) - Fx, wy = -T(Y[0]) - Fy;
+    const T dist = sqrt_t(wx * wx + wy * wy);
+    const T ex = wx / dist, ey = wy / dist;
+    const T tpx = -sgf * ey, tpy = sgf * ex;
+    const T cot = (xL[1] - xL[0]) / ds0;
+    const T psi = atan2_t<FT>(sgf * (ex * ry - ey * rx), ex * rx + ey * ry);
+    const int qf = sgf > T(0) ? -1 : 1;
+    o.pt = double(T(kKpt * p.bfield) * R);
     o.phi = double(atan2_t<FT>(tpy, tpx));
     o.cot = double(cot);
-    o.dxy = double(TS(qf) * (dist - R));
+    o.dxy = double(T(qf) * (dist - R));
     o.dz = double(xL[0] - cot * (R * psi));
     o.chi2 = double(chi2T + chi2L);
     o.q = (int8_t)qf;
     o.status = 0;
 }
 
+template <typename TC, typename T, bool FT>
+__device__ __forceinline__ void fit_track(int n, const float *X, const float *Y, const float *Z,
+                                          const uint8_t *L, const DevParams &p, FitOut &o)
+{
+    switch (n) {
+    case 3: fit_n<3, TC, T, FT>(X, Y, Z, L, p, o); break;
+    case 4: fit_n<4, TC, T, FT>(X, Y, Z, L, p, o); break;
+    case 5: fit_n<5, TC, T, FT>(X, Y, Z, L, p, o); break;
+    case 6: fit_n<6, TC, T, FT>(X, Y, Z, L, p, o); break;
+    default: o = FitOut{0, 0, 0, 0, 0, 0, 0, 4};
+    }
+}
+
 __device__ __forceinline__ void fit_dispatch(int n, const float *X, const float *Y,
                                              const float *Z, const uint8_t *L,
                                              const DevParams &p, FitOut &o)
 {
-    if (p.fit_mode == FIT_MIXED) fit_track<double, double, double, true>(n, X, Y, Z, L, p, o);
-    else if (p.fit_mode == FIT_FP32) fit_track<float, float, float, false>(n, X, Y, Z, L, p, o);
-    else fit_track<double, double, double, false>(n, X, Y, Z, L, p, o);
+    if (p.fit_mode == FIT_MIXED) fit_track<double, double, true>(n, X, Y, Z, L, p, o);
+    else if (p.fit_mode == FIT_FP32) fit_track<float, float, false>(n, X, Y, Z, L, p, o);
+    else fit_track<double, double, false>(n, X, Y, Z, L, p, o);
 }
 
 __global__ void __launch_bounds__(256) k_fit(DevBatch b, DevParams p, uint32_t total)
