@@ -290,21 +290,19 @@ __device__ __forceinline__ void fit_dispatch(int n, const float *X, const float 
     else fit_track<double, double, false>(n, X, Y, Z, L, p, o);
 }
 
-__global__ void __launch_bounds__(256) k_fit(DevBatch b, DevParams p, uint32_t total)
+// One thread per output track: the kept ntuplets are listed per event in output order, and the
+// number of outputs is read on the device, so no thread is spent on unused capacity.
+__global__ void __launch_bounds__(256) k_fit(DevBatch b, DevParams p)
 {
-    const uint32_t n_chunks = total / kChunk;
-    for (uint32_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
-        const uint32_t t = ch * kChunk + threadIdx.x;
-        const uint32_t e = b.tup_chunk[ch];
-        const uint32_t t0 = b.tup_off[e];
-        const uint32_t nt = min(b.cnt[C_TUPLES * b.E + e], b.tup_off[e + 1] - t0);
-        if (t - t0 >= nt) continue;
-        const uint32_t rank = b.tup_rank[t];
-        if (rank == kNone) continue;
-        const uint32_t o = b.out_evt[e] + rank;
+    const uint32_t n_out = b.out_evt[b.E];
+    for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < n_out;
+         o += gridDim.x * blockDim.x) {
+        const uint32_t e = find_event(b.out_evt, b.E, o);
+        const uint32_t t = b.tup_list[b.tup_off[e] + (o - b.out_evt[e])];
         const int n = b.tup_n[t];
         float X[kMaxHits], Y[kMaxHits], Z[kMaxHits];
         uint8_t L[kMaxHits];
+#pragma unroll
         for (int h = 0; h < kMaxHits; ++h) {
             const uint32_t pos = b.tup_hits[(size_t)t * kMaxHits + h];
             if (h < n) {
@@ -314,6 +312,8 @@ __global__ void __launch_bounds__(256) k_fit(DevBatch b, DevParams p, uint32_t t
                 L[h] = (uint8_t)(meta >> kLocalBits);
                 b.o_hits[(size_t)o * kMaxHits + h] = meta & kLocalMask;
             } else {
+                X[h] = Y[h] = Z[h] = 0.f;
+                L[h] = 0;
                 b.o_hits[(size_t)o * kMaxHits + h] = kNone;
             }
         }
@@ -328,11 +328,11 @@ __global__ void __launch_bounds__(256) k_fit(DevBatch b, DevParams p, uint32_t t
 
 void launch_fit(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
 {
-    uint64_t blocks = total / kChunk;
-    uint64_t cap = (uint64_t)sms * 16;
+    uint64_t blocks = ((uint64_t)total + 255) / 256;
+    uint64_t cap = (uint64_t)sms * 8;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
-    k_fit<<<(unsigned)blocks, kChunk, 0, s>>>(b, p, total);
+    k_fit<<<(unsigned)blocks, 256, 0, s>>>(b, p);
 }
 
 // Fit-only path: m ntuplets given directly.

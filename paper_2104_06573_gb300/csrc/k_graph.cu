@@ -532,55 +532,73 @@ void launch_connect(const DevBatch &b, const DevParams &p, uint32_t total, cudaS
 // ------------------------------------------------------------------------------------------
 // Ntuplets: depth-first walk from every root cell
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_ntuplets(DevBatch b, DevParams p, uint32_t total)
+// Depth-first walk from one root cell A; emits every path that has max_hits hits or ends at a
+// cell without out-edges, if it has at least min_hits hits.
+__device__ __forceinline__ void walk_from(const DevBatch &b, const DevParams &p, uint32_t e,
+                                          uint32_t A)
 {
-    const uint32_t n_chunks = total / kChunk;
-    for (uint32_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
-        const uint32_t A = ch * kChunk + threadIdx.x;
-        const uint32_t e = b.cell_chunk[ch];
-        const uint32_t c0 = b.cell_off[e];
-        const uint32_t ncell = min(b.cnt[C_CELLS * b.E + e], b.cell_off[e + 1] - c0);
-        if (A - c0 >= ncell) continue;
-        const uint32_t Li = b.hmeta[b.cell_in[A]] >> kLocalBits;
-        if (!((p.root_mask >> Li) & 1u)) continue;
-        uint32_t cells[kMaxHits - 1];
-        uint32_t next[kMaxHits - 1];
-        int d = 0;
-        cells[0] = A;
-        next[0] = 0;
-        const uint32_t tcap = b.tup_off[e + 1] - b.tup_off[e];
-        while (d >= 0) {
-            const uint32_t c = cells[d];
-            const uint32_t nh = (uint32_t)d + 2u;
-            const uint32_t ne = b.nbr_n[c];
-            if (next[d] == 0 && (nh >= p.max_hits || ne == 0)) {
-                if (nh >= p.min_hits) {
-                    uint32_t slot = atomicAdd(&b.cnt[C_TUPLES * b.E + e], 1u);
-                    if (slot < tcap) {
-                        const uint32_t t = b.tup_off[e] + slot;
-                        uint32_t *th = b.tup_hits + (size_t)t * kMaxHits;
-                        th[0] = b.cell_in[cells[0]];
-                        for (int q = 0; q <= d; ++q) th[q + 1] = b.cell_out[cells[q]];
-                        for (int q = d + 2; q < kMaxHits; ++q) th[q] = kNone;
-                        b.tup_n[t] = (uint8_t)nh;
-                        b.tup_state[t] = nh < p.max_hits ? 2 : 1;
-                        b.tup_first[t] = A;
-                    } else {
-                        atomicOr(&b.cnt[C_FLAGS * b.E + e], F_TUPLES);
-                    }
+    uint32_t cells[kMaxHits - 1];
+    uint32_t next[kMaxHits - 1];
+    int d = 0;
+    cells[0] = A;
+    next[0] = 0;
+    const uint32_t tcap = b.tup_off[e + 1] - b.tup_off[e];
+    while (d >= 0) {
+        const uint32_t c = cells[d];
+        const uint32_t nh = (uint32_t)d + 2u;
+        const uint32_t ne = b.nbr_n[c];
+        if (next[d] == 0 && (nh >= p.max_hits || ne == 0)) {
+            if (nh >= p.min_hits) {
+                const uint32_t slot = atomicAdd(&b.cnt[C_TUPLES * b.E + e], 1u);
+                if (slot < tcap) {
+                    const uint32_t t = b.tup_off[e] + slot;
+                    uint32_t *th = b.tup_hits + (size_t)t * kMaxHits;
+                    th[0] = b.cell_in[cells[0]];
+                    for (int q = 0; q <= d; ++q) th[q + 1] = b.cell_out[cells[q]];
+                    for (int q = d + 2; q < kMaxHits; ++q) th[q] = kNone;
+                    b.tup_n[t] = (uint8_t)nh;
+                    b.tup_state[t] = nh < p.max_hits ? 2 : 1;
+                    b.tup_first[t] = A;
+                } else {
+                    atomicOr(&b.cnt[C_FLAGS * b.E + e], F_TUPLES);
                 }
-                --d;
-                continue;
             }
-            if (next[d] < ne) {
-                const uint32_t nxt = b.nbr[b.nbr_first[c] + next[d]];
-                ++next[d];
-                ++d;
-                cells[d] = nxt;
-                next[d] = 0;
-                if (p.drop_suffixes) atomicMin(&b.mindepth[nxt], (uint32_t)d);
-            } else {
-                --d;
+            --d;
+            continue;
+        }
+        if (next[d] < ne) {
+            const uint32_t nxt = b.nbr[b.nbr_first[c] + next[d]];
+            ++next[d];
+            ++d;
+            cells[d] = nxt;
+            next[d] = 0;
+            if (p.drop_suffixes) atomicMin(&b.mindepth[nxt], (uint32_t)d);
+        } else {
+            --d;
+        }
+    }
+}
+
+// One warp per root hit (a hit on a root layer); its lanes walk from the hit's cells.
+__global__ void __launch_bounds__(256) k_ntuplets(DevBatch b, DevParams p)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t nk = p.n_keys;
+    const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t gg = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gg < b.N;
+         gg += stride) {
+        const uint32_t g = (uint32_t)gg;
+        const uint32_t e = hit_event(b, g);
+        if (g >= b.bkt[(size_t)e * (nk + 1) + nk]) continue;
+        const uint32_t L = b.hmeta[g] >> kLocalBits;
+        if (!((p.root_mask >> L) & 1u)) continue;
+        for (uint32_t s = 0; s < p.n_out[L]; ++s) {
+            const uint32_t f = b.out_first[(size_t)g * kMaxOut + s];
+            const uint32_t n = b.out_n[(size_t)g * kMaxOut + s];
+            for (uint32_t c = lane; c < n; c += 32) {
+                const uint32_t A = f + c;
+                if (b.nbr_n[A] == 0 && p.min_hits > 2) continue;   // a 2-hit path is too short
+                walk_from(b, p, e, A);
             }
         }
     }
@@ -588,11 +606,12 @@ __global__ void __launch_bounds__(256) k_ntuplets(DevBatch b, DevParams p, uint3
 
 void launch_ntuplets(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
 {
-    uint64_t blocks = total / kChunk;
-    uint64_t cap = (uint64_t)sms * 32;
+    (void)total;
+    uint64_t blocks = ((uint64_t)b.N + 7) / 8;
+    uint64_t cap = (uint64_t)sms * 16;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
-    k_ntuplets<<<(unsigned)blocks, 256, 0, s>>>(b, p, total);
+    k_ntuplets<<<(unsigned)blocks, 256, 0, s>>>(b, p);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -613,7 +632,9 @@ __global__ void __launch_bounds__(256) k_select(DevBatch b, DevParams p, uint32_
             const uint32_t md = b.mindepth[b.tup_first[t]];
             if (md != kNone && md + b.tup_n[t] <= p.max_hits) keep = false;
         }
-        b.tup_rank[t] = keep ? atomicAdd(&b.cnt[C_OUT * b.E + e], 1u) : kNone;
+        const uint32_t rank = keep ? atomicAdd(&b.cnt[C_OUT * b.E + e], 1u) : kNone;
+        b.tup_rank[t] = rank;
+        if (keep) b.tup_list[t0 + rank] = t;
     }
 }
 

@@ -92,6 +92,7 @@ struct DevBatch {
     uint8_t *tup_state;                 // [tuples] 1 capped, 2 ended without edge
     uint32_t *tup_first;                // [tuples] root cell
     uint32_t *tup_rank;                 // [tuples] output slot within the event, kNone = dropped
+    uint32_t *tup_list;                 // [tuples] per event: kept ntuplets in output order
     // compact output, events back to back
     uint32_t *out_evt;                  // [E+1]
     uint32_t out_cap;                   // output slots (= tuple capacity)

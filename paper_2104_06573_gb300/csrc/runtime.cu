@@ -211,7 +211,7 @@ struct PlanOffsets {
         head_end;
     size_t cnt, bkt, hs, r64, hmeta, hphi, out_first, out_n, cell_in, cell_out,
         cell_len64, nbr_first,
-        nbr_n, nbr, mindepth, tup_hits, tup_n, tup_state, tup_first, tup_rank, out_evt, o_nh,
+        nbr_n, nbr, mindepth, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, out_evt, o_nh,
         o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status;
     size_t total;
 };
@@ -255,6 +255,7 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.tup_state = L.add(T);
     o.tup_first = L.add(4 * T);
     o.tup_rank = L.add(4 * T);
+    o.tup_list = L.add(4 * T);
     o.out_evt = L.add(4 * (E + 1));
     o.o_nh = L.add(T);
     o.o_hits = L.add(4 * T * kMaxHits);
@@ -415,6 +416,7 @@ static void plan_bind(pxr_plan *P)
     b.tup_state = (uint8_t *)(r + o.tup_state);
     b.tup_first = (uint32_t *)(r + o.tup_first);
     b.tup_rank = (uint32_t *)(r + o.tup_rank);
+    b.tup_list = (uint32_t *)(r + o.tup_list);
     b.out_evt = (uint32_t *)(r + o.out_evt);
     b.out_cap = (uint32_t)P->T;
     b.o_nh = (uint8_t *)(r + o.o_nh);
