@@ -117,8 +117,7 @@ typedef struct pxr_params {
     double bfield;                             /* tesla along +z, > 0 */
     double sigma_rphi, sigma_z;                /* cm, > 0 */
     double x_over_x0;                          /* radiation lengths per layer, >= 1e-6 */
-    uint32_t n_phi_bins;                       /* phi bins per layer, a multiple of 16 in
-                                                  64..2048; 0 = automatic */
+    uint32_t n_phi_bins;                       /* phi bins per layer, 64..2048; 0 = automatic */
     uint32_t max_cells_per_event;              /* 0 = sized from the hit counts; rounded up to a
                                                   multiple of 256 */
     uint32_t max_tuples_per_event;             /* 0 = sized from the hit counts; rounded up to a

@@ -61,260 +61,105 @@ __device__ __forceinline__ bool doublet_test(const DevBatch &b, const DevParams 
                      p.cw);
 }
 
-constexpr uint32_t kTileBins = 16;     // inner phi bins per tile (bin counts are multiples of 64)
-constexpr uint32_t kTileItems = 256;   // inner hits per pass of a tile
-constexpr uint32_t kStageHits = 2048;  // outer hits staged in shared memory
-constexpr uint32_t kMaxUnwrapped = 64; // unwrapped outer bins of a tile (+ 1 end)
-
-// One CTA per tile = (event, inner layer, layer pair, 16 consecutive inner phi bins).  The union
-// of the tile's outer phi windows is staged in shared memory with coalesced loads; each warp takes
-// one inner hit at a time and tests its window 32 candidates per step from the staged copy,
-// keeping the ballot masks in shared memory.  A block scan of the per-hit counts gives one atomic
-// per pass of the tile; the second sweep writes the cells from the masks.  Tiles whose windows do
-// not fit the stage read their candidates from global memory.
-__global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint32_t n_tiles)
+__global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint32_t slots)
 {
-    extern __shared__ float4 s_hs[];                       // [kStageHits]
-    __shared__ uint32_t s_pos[kStageHits];
-    __shared__ uint32_t s_mask[kTileItems * kMaxIt];
-    __shared__ uint32_t s_cnt[kTileItems];
-    __shared__ uint32_t s_so[kMaxUnwrapped + 1];           // staged offset of each unwrapped bin
-    __shared__ uint32_t s_ab[kMaxUnwrapped];               // absolute start of each unwrapped bin
-    __shared__ uint32_t s_warp[8];
-    __shared__ uint32_t s_base, s_total;
-    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t lane = threadIdx.x & 31u;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    const uint32_t nk = p.n_keys, nb = p.nb;
-    const uint32_t nchunk = nb / kTileBins, per_event = p.n_ls * nchunk;
-    const bool fp64 = p.cut_mode == CUT_FP64;
-    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const uint32_t e = tile / per_event, r = tile % per_event;
-        const uint32_t ls = r / nchunk, chunk = r % nchunk;
-        const uint32_t L = p.ls_layer[ls], slot = p.ls_slot[ls], Lo = p.out_layer[L][slot];
+    const uint64_t n_items = (uint64_t)b.N * slots;
+    const uint32_t nk = p.n_keys;
+    uint64_t item = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (; item < n_items; item += stride) {
+        const uint32_t g = (uint32_t)(item / slots), slot = (uint32_t)(item % slots);
+        const uint32_t e = hit_event(b, g);
         const uint32_t *bk = b.bkt + (size_t)e * (nk + 1);
-        const uint32_t b0 = chunk * kTileBins;
-        const uint32_t i0 = bk[L * nb + b0], i1 = bk[L * nb + b0 + kTileBins];
-        if (i0 == i1) continue;
-        const int W = (int)p.win_bins;
-        const int ulo = (int)b0 - W, uhi = (int)(b0 + kTileBins) - 1 + W;
-        const uint32_t nub = (uint32_t)(uhi - ulo + 1);
-        bool staged = nub < nb && nub <= kMaxUnwrapped;
-        const uint32_t *lb = bk + Lo * nb;
-        if (staged) {
-            // staged offsets of the unwrapped bins (warp 0 scans them)
-            if (wid == 0) {
-                uint32_t run = 0;
-                for (uint32_t u0 = 0; u0 < nub; u0 += 32) {
-                    const uint32_t u = u0 + lane;
-                    uint32_t c = 0;
-                    if (u < nub) {
-                        const uint32_t bin = (uint32_t)((ulo + (int)u + (int)nb) % (int)nb);
-                        s_ab[u] = lb[bin];
-                        c = lb[bin + 1] - lb[bin];
-                    }
-                    uint32_t incl = c;
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                        if (lane >= (uint32_t)o) incl += t;
-                    }
-                    if (u < nub) s_so[u] = run + incl - c;
-                    run += __shfl_sync(0xFFFFFFFFu, incl, 31);
-                }
-                if (lane == 0) s_so[nub] = run;
+        if (g >= bk[nk]) continue;                       // hit rejected by the sort (bad layer)
+        const uint32_t L = b.hmeta[g] >> kLocalBits;
+        if (slot >= p.n_out[L]) continue;
+        const uint32_t Lo = p.out_layer[L][slot];
+        const float4 hi = b.hs[g];
+        const Window w = phi_window(bk, Lo, b.hphi[g], p);
+        const uint32_t nc = w.size();
+
+        uint32_t masks[kMaxIt];
+        uint32_t count = 0;
+#pragma unroll
+        for (int k = 0; k < kMaxIt; ++k) {
+            masks[k] = 0;
+            if ((uint32_t)k * 32u < nc) {
+                uint32_t c = (uint32_t)k * 32u + lane;
+                bool pass = c < nc && doublet_test(b, p, g, hi, w.pos(c));
+                masks[k] = __ballot_sync(0xFFFFFFFFu, pass);
+                count += __popc(masks[k]);
             }
-            __syncthreads();
-            staged = s_so[nub] <= kStageHits;
-            if (staged) {
-                const uint32_t tot = s_so[nub];
-                for (uint32_t t = threadIdx.x; t < tot; t += blockDim.x) {
-                    uint32_t lo = 0, hi_ = nub - 1;        // last unwrapped bin with so <= t
-                    while (lo < hi_) {
-                        const uint32_t mid = (lo + hi_ + 1) >> 1;
-                        if (s_so[mid] <= t) lo = mid; else hi_ = mid - 1;
-                    }
-                    const uint32_t pos = s_ab[lo] + (t - s_so[lo]);
-                    s_pos[t] = pos;
-                    s_hs[t] = b.hs[pos];
-                }
-            }
-            __syncthreads();
         }
+        for (uint32_t c0 = kMaxIt * 32u; c0 < nc; c0 += 32u) {
+            uint32_t c = c0 + lane;
+            bool pass = c < nc && doublet_test(b, p, g, hi, w.pos(c));
+            count += __popc(__ballot_sync(0xFFFFFFFFu, pass));
+        }
+
+        uint32_t base = 0;
+        if (lane == 0 && count) base = atomicAdd(&b.cnt[C_CELLS * b.E + e], count);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
         const uint32_t cap = b.cell_off[e + 1] - b.cell_off[e];
-        for (uint32_t ib = i0; ib < i1; ib += kTileItems) {
-            const uint32_t n_items = min(kTileItems, i1 - ib);
-            // the candidates of one inner hit: a staged range or one/two global runs
-            auto window = [&](uint32_t g, float phi) {
-                Window w;
-                if (staged) {
-                    // the tile's union covers every window of its hits (win_bins includes one
-                    // bin of rounding slack); the clamps only guard the shared-memory index
-                    int blo = (int)floorf((phi - p.w_eps + kPiF2) * p.bins_per_rad);
-                    int bhi = (int)floorf((phi + p.w_eps + kPiF2) * p.bins_per_rad);
-                    blo = blo < ulo ? ulo : blo;
-                    bhi = bhi > uhi ? uhi : bhi;
-                    w.r0 = s_so[blo - ulo];
-                    w.n1 = s_so[bhi + 1 - ulo] - w.r0;
-                    w.r2 = 0;
-                    w.n2 = 0;
-                } else {
-                    w = phi_window(bk, Lo, phi, p);
-                }
-                return w;
-            };
-            auto cand = [&](const Window &w, uint32_t c, float4 &ho) {
-                const uint32_t q = w.pos(c);
-                if (staged) {
-                    ho = s_hs[q];
-                    return s_pos[q];
-                }
-                ho = b.hs[q];
-                return q;
-            };
-            auto test = [&](uint32_t g, float4 hi, uint32_t o, float4 ho) {
-                if (!fp64) {
-                    const int rr = doublet32(hi, ho, p.cw32);
-                    if (rr >= 0) return rr == 1;
-                }
-                return doublet64((double)hi.x, (double)hi.y, b.r64[g], (double)ho.x,
-                                 (double)ho.y, b.r64[o], p.cw);
-            };
-            // ---- pass 1: ballot masks and counts ----
-            for (uint32_t it = wid; it < n_items; it += nwarps) {
-                const uint32_t g = ib + it;
-                const float4 hi = b.hs[g];
-                const Window w = window(g, b.hphi[g]);
-                const uint32_t nc = w.size();
-                uint32_t count = 0;
+        uint32_t nw = count;
+        if (base >= cap) nw = 0;
+        else if (base + count > cap) nw = cap - base;
+        if (lane == 0) {
+            if (nw < count) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_CELLS);
+            b.out_first[(size_t)g * kMaxOut + slot] = b.cell_off[e] + base;
+            b.out_n[(size_t)g * kMaxOut + slot] = nw;
+        }
+        if (nw == 0) continue;
+        const uint32_t first = b.cell_off[e] + base;
+        const bool fp64 = p.cut_mode == CUT_FP64;
+        const double ri = fp64 ? b.r64[g] : 0.0;
+        uint32_t run = 0;
 #pragma unroll
-                for (int k = 0; k < kMaxIt; ++k) {
-                    uint32_t m = 0;
-                    if ((uint32_t)k * 32u < nc) {
-                        const uint32_t c = (uint32_t)k * 32u + lane;
-                        bool pass = false;
-                        if (c < nc) {
-                            float4 ho;
-                            const uint32_t o = cand(w, c, ho);
-                            pass = test(g, hi, o, ho);
-                        }
-                        m = __ballot_sync(0xFFFFFFFFu, pass);
-                        count += __popc(m);
-                    }
-                    if (lane == 0) s_mask[it * kMaxIt + k] = m;
-                }
-                for (uint32_t c0 = kMaxIt * 32u; c0 < nc; c0 += 32u) {
-                    const uint32_t c = c0 + lane;
-                    bool pass = false;
-                    if (c < nc) {
-                        float4 ho;
-                        const uint32_t o = cand(w, c, ho);
-                        pass = test(g, hi, o, ho);
-                    }
-                    count += __popc(__ballot_sync(0xFFFFFFFFu, pass));
-                }
-                if (lane == 0) s_cnt[it] = count;
-            }
-            __syncthreads();
-            // ---- block scan of the counts, one atomic per pass ----
-            {
-                const uint32_t v = threadIdx.x < n_items ? s_cnt[threadIdx.x] : 0u;
-                uint32_t incl = v;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                    if (lane >= (uint32_t)o) incl += t;
-                }
-                if (lane == 31) s_warp[wid] = incl;
-                __syncthreads();
-                uint32_t wpre = 0;
-                for (uint32_t q = 0; q < wid; ++q) wpre += s_warp[q];
-                if (threadIdx.x < n_items) s_cnt[threadIdx.x] = wpre + incl - v;   // exclusive
-                if (threadIdx.x == blockDim.x - 1) {
-                    const uint32_t total = wpre + incl;
-                    s_total = total;
-                    s_base = total ? atomicAdd(&b.cnt[C_CELLS * b.E + e], total) : 0u;
-                }
-                __syncthreads();
-            }
-            const uint32_t base = s_base;
-            // ---- pass 2: write the cells ----
-            for (uint32_t it = wid; it < n_items; it += nwarps) {
-                const uint32_t g = ib + it;
-                const uint32_t pre = s_cnt[it];
-                const uint32_t count =
-                    (it + 1 < n_items ? s_cnt[it + 1] : s_total) - pre;
-                const uint32_t at = base + pre;                  // within the event's region
-                uint32_t nw = count;
-                if (at >= cap) nw = 0;
-                else if (at + count > cap) nw = cap - at;
-                if (lane == 0) {
-                    if (nw < count) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_CELLS);
-                    b.out_first[(size_t)g * kMaxOut + slot] = b.cell_off[e] + at;
-                    b.out_n[(size_t)g * kMaxOut + slot] = nw;
-                }
-                if (nw == 0) continue;
-                const uint32_t first = b.cell_off[e] + at;
-                const float4 hi = b.hs[g];
-                const Window w = window(g, b.hphi[g]);
-                const uint32_t nc = w.size();
-                const double ri = fp64 ? b.r64[g] : 0.0;
-                uint32_t run = 0;
-#pragma unroll
-                for (int k = 0; k < kMaxIt; ++k) {
-                    if ((uint32_t)k * 32u >= nc) break;
-                    const uint32_t m = s_mask[it * kMaxIt + k];
-                    if ((m >> lane) & 1u) {
-                        const uint32_t idx = run + __popc(m & lt_mask);
-                        if (idx < nw) {
-                            float4 ho;
-                            const uint32_t o = cand(w, (uint32_t)k * 32u + lane, ho);
-                            b.cell_in[first + idx] = g;
-                            b.cell_out[first + idx] = o;
-                            if (fp64) b.cell_len64[first + idx] =
-                                seglen64(ri, (double)hi.z, b.r64[o], (double)ho.z);
-                        }
-                    }
-                    run += __popc(m);
-                }
-                for (uint32_t c0 = kMaxIt * 32u; c0 < nc; c0 += 32u) {
-                    const uint32_t c = c0 + lane;
-                    bool pass = false;
-                    uint32_t o = 0;
-                    float4 ho = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (c < nc) {
-                        o = cand(w, c, ho);
-                        pass = test(g, hi, o, ho);
-                    }
-                    const uint32_t m = __ballot_sync(0xFFFFFFFFu, pass);
-                    if (pass) {
-                        const uint32_t idx = run + __popc(m & lt_mask);
-                        if (idx < nw) {
-                            b.cell_in[first + idx] = g;
-                            b.cell_out[first + idx] = o;
-                            if (fp64) b.cell_len64[first + idx] =
-                                seglen64(ri, (double)hi.z, b.r64[o], (double)ho.z);
-                        }
-                    }
-                    run += __popc(m);
+        for (int k = 0; k < kMaxIt; ++k) {
+            uint32_t m = masks[k];
+            if ((m >> lane) & 1u) {
+                uint32_t idx = run + __popc(m & lt_mask);
+                if (idx < nw) {
+                    uint32_t o = w.pos((uint32_t)k * 32u + lane);
+                    b.cell_in[first + idx] = g;
+                    b.cell_out[first + idx] = o;
+                    if (fp64) b.cell_len64[first + idx] =
+                        seglen64(ri, (double)hi.z, b.r64[o], (double)b.hs[o].z);
                 }
             }
-            __syncthreads();
+            run += __popc(m);
+        }
+        for (uint32_t c0 = kMaxIt * 32u; c0 < nc; c0 += 32u) {
+            uint32_t c = c0 + lane;
+            uint32_t o = c < nc ? w.pos(c) : 0u;
+            bool pass = c < nc && doublet_test(b, p, g, hi, o);
+            uint32_t m = __ballot_sync(0xFFFFFFFFu, pass);
+            if (pass) {
+                uint32_t idx = run + __popc(m & lt_mask);
+                if (idx < nw) {
+                    b.cell_in[first + idx] = g;
+                    b.cell_out[first + idx] = o;
+                    if (fp64) b.cell_len64[first + idx] =
+                        seglen64(ri, (double)hi.z, b.r64[o], (double)b.hs[o].z);
+                }
+            }
+            run += __popc(m);
         }
     }
 }
 
-cudaError_t init_doublets()
-{
-    return cudaFuncSetAttribute(k_doublets, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kStageHits * (int)sizeof(float4));
-}
-
 void launch_doublets(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms)
 {
-    const uint64_t n_tiles = (uint64_t)b.E * p.n_ls * (p.nb / kTileBins);
-    uint64_t blocks = n_tiles;
-    const uint64_t cap = (uint64_t)sms * 4;
+    uint32_t slots = 1;
+    for (uint32_t l = 0; l < p.n_layers; ++l) slots = p.n_out[l] > slots ? p.n_out[l] : slots;
+    uint64_t warps = (uint64_t)b.N * slots;
+    uint64_t blocks = (warps + 7) / 8;
+    uint64_t cap = (uint64_t)sms * 16;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
-    k_doublets<<<(unsigned)blocks, 256, kStageHits * sizeof(float4), s>>>(b, p, (uint32_t)n_tiles);
+    k_doublets<<<(unsigned)blocks, 256, 0, s>>>(b, p, slots);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -127,7 +127,6 @@ extern "C" int pxr_doublets_noalloc(const float *x, const float *y, const float 
             cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
             if (e != cudaSuccess) return set_error(PXR_ECUDA, cudaGetErrorString(e));
             e = init_kernels();
-            if (e == cudaSuccess) e = init_doublets();
             if (e != cudaSuccess) return set_error(PXR_ECUDA, cudaGetErrorString(e));
             g_na_ptr[dev] = static_cast<unsigned char *>(p);
         }

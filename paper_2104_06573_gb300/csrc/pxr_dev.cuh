@@ -52,9 +52,6 @@ struct DevParams {
     float theta32;                      // theta_cut rounded to float
     float dca32;                        // dca_cut rounded to float
     float tan_win;                      // tan(asin(theta_cut) + margin); inf when theta_cut >= 1
-    uint32_t n_ls;                      // (inner layer, pair slot) combinations
-    uint8_t ls_layer[kMaxLayers * kMaxOut], ls_slot[kMaxLayers * kMaxOut];
-    uint32_t win_bins;                  // bins a phi window can reach beyond the hit's own bin
     double cw;                          // cos(w) as given by the caller
     double theta, dca;
     double bfield, sigma_rphi, sigma_z, x_over_x0;
@@ -133,7 +130,6 @@ void launch_sort(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms)
 void launch_layer_count(const uint32_t *hit_off, const uint16_t *layer, uint32_t E,
                         uint32_t n_layers, uint32_t *counts, cudaStream_t s, int sms);
 void launch_doublets(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms);
-cudaError_t init_doublets();
 void launch_connect(const DevBatch &b, const DevParams &p, uint32_t cell_total, cudaStream_t s,
                     int sms);
 void launch_ntuplets(const DevBatch &b, const DevParams &p, uint32_t cell_total, cudaStream_t s,

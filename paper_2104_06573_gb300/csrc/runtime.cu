@@ -114,8 +114,8 @@ static int check_params(const pxr_params *p, DevParams *d)
         !(p->sigma_rphi > 0.0) || !(p->sigma_z > 0.0) || !(p->x_over_x0 >= 1e-6) ||
         !std::isfinite(p->theta_cut) || !std::isfinite(p->dca_cut))
         return fail(PXR_EINVAL, "cuts, field, errors and material must be positive and finite");
-    if (p->n_phi_bins && (p->n_phi_bins < 64 || p->n_phi_bins > 2048 || p->n_phi_bins % 16))
-        return fail(PXR_EINVAL, "n_phi_bins must be 0 or a multiple of 16 in [64, 2048]");
+    if (p->n_phi_bins && (p->n_phi_bins < 64 || p->n_phi_bins > 2048))
+        return fail(PXR_EINVAL, "n_phi_bins must be 0 or in [64, 2048]");
     if (!d) return PXR_OK;
     std::memset(d, 0, sizeof(*d));
     d->n_layers = p->n_layers;
@@ -148,14 +148,6 @@ static int check_params(const pxr_params *p, DevParams *d)
     // |sin(angle)| <= t  <=>  the r-z directions differ by at most asin(t) modulo pi
     d->tan_win = p->theta_cut < 0.99 ? (float)std::tan(std::asin(p->theta_cut) + 1e-5)
                                      : INFINITY;
-    d->n_ls = 0;
-    for (uint32_t l = 0; l < d->n_layers; ++l)
-        for (uint32_t s = 0; s < d->n_out[l]; ++s) {
-            d->ls_layer[d->n_ls] = (uint8_t)l;
-            d->ls_slot[d->n_ls++] = (uint8_t)s;
-        }
-    // a hit's window spans its own bin +- ceil(w_eps nb / 2pi) bins, plus one for rounding
-    d->win_bins = (uint32_t)std::ceil((double)d->w_eps * d->nb / (2.0 * M_PI)) + 1;
     d->cw = p->cos_phi_window;
     d->theta = p->theta_cut;
     d->dca = p->dca_cut;
@@ -1191,7 +1183,6 @@ extern "C" int pxr_create(const pxr_config *cfg, pxr_ctx **out)
     for (auto &s : ctx->slot_stream) CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     for (auto &b : ctx->slot_buf) b.reset(new SlotBuffers());
     CK(init_kernels());
-    CK(init_doublets());
     pxr_ctx *c = ctx.get();
     ctx->sched = std::thread(scheduler, c);
     *out = ctx.release();
