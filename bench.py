@@ -178,6 +178,22 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def doublet_traffic(cells):
+    """DRAM bytes of one k_doublets launch from the committed ncu capture (scaled by cells, the
+    units the launch processes), or None when the kernel source changed since the capture."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "k_doublets_traffic.json")))
+        src = open(os.path.join(ROOT, "paper_2104_06573_gb300", "csrc", "k_graph.cu")).read()
+        a = src.index("__global__ void __launch_bounds__(256) k_doublets(")
+        b = src.index("void launch_doublets(")
+        if hashlib.sha256(src[a:b].encode()).hexdigest()[:16] != rec["source_sha16"]:
+            return None
+        return rec["dram_bytes_per_cell"] * cells
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def doublet_algorithmic_bytes(layer_counts, pairs, n_cells):
     """16 B per hit read per layer pair it takes part in, 8 B per inner hit and pair for the two
     bucket offsets of its window, 8 B per cell written."""
@@ -290,7 +306,7 @@ def run_pxr(args, rank, world, local):
                                   "fit+output"], [round(v, 4) for v in stage])),
             "roofline": {"kernel": "k_doublets", "bound": "hbm", "achieved": achieved,
                          "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                         "peak_source": peak_src, "traffic": None,
+                         "peak_source": peak_src, "traffic": doublet_traffic(cells),
                          "algorithmic_bytes": alg, "cells": cells},
             "clocks": clk, "tracks_per_step": n_tracks * world}
 

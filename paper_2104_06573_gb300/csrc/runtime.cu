@@ -699,7 +699,49 @@ struct HostTracks {
     }
 };
 
-// Copy tracks [a, b) of the source arrays into out in canonical order (lexicographic by hits).
+// Canonical order of n tracks (lexicographic by their hit tuples): LSD radix sort on the packed
+// first two hit indices (caller indices are < 2^24, so the key has 48 bits), then the rare runs
+// of equal first two hits are ordered by the remaining hits.
+static void canonical_order(const uint32_t *hits, size_t n, std::vector<uint32_t> &ord)
+{
+    std::vector<uint64_t> key(n), key2(n);
+    std::vector<uint32_t> tmp(n);
+    ord.resize(n);
+    for (size_t i = 0; i < n; ++i) {
+        const uint32_t *h = hits + i * kMaxHits;
+        key[i] = ((uint64_t)(h[0] & 0xFFFFFFu) << 24) | (uint64_t)(h[1] & 0xFFFFFFu);
+        ord[i] = (uint32_t)i;
+    }
+    size_t count[256];
+    for (int pass = 0; pass < 6; ++pass) {
+        const int sh = 8 * pass;
+        std::fill(count, count + 256, 0);
+        for (size_t i = 0; i < n; ++i) ++count[(key[i] >> sh) & 0xFF];
+        size_t run = 0;
+        for (int b = 0; b < 256; ++b) { const size_t c = count[b]; count[b] = run; run += c; }
+        for (size_t i = 0; i < n; ++i) {
+            const size_t d = count[(key[i] >> sh) & 0xFF]++;
+            key2[d] = key[i];
+            tmp[d] = ord[i];
+        }
+        key.swap(key2);
+        ord.swap(tmp);
+    }
+    for (size_t a = 0; a < n;) {
+        size_t b = a + 1;
+        while (b < n && key[b] == key[a]) ++b;
+        if (b - a > 1)
+            std::sort(ord.begin() + a, ord.begin() + b, [&](uint32_t x, uint32_t y) {
+                return std::lexicographical_compare(hits + (size_t)x * kMaxHits,
+                                                    hits + (size_t)x * kMaxHits + kMaxHits,
+                                                    hits + (size_t)y * kMaxHits,
+                                                    hits + (size_t)y * kMaxHits + kMaxHits);
+            });
+        a = b;
+    }
+}
+
+// Copy n tracks of the source arrays into out in canonical order.
 static int emit_tracks(const uint8_t *nh, const uint32_t *hits, const double *pt,
                        const double *phi, const double *cot, const double *dxy, const double *dz,
                        const double *chi2, const int8_t *q, const int8_t *st, size_t n,
@@ -708,14 +750,8 @@ static int emit_tracks(const uint8_t *nh, const uint32_t *hits, const double *pt
     out->n_tracks = (uint32_t)n;
     out->status = status;
     if (n > out->capacity) return fail(PXR_ETRUNC, "track capacity too small");
-    std::vector<uint32_t> ord(n);
-    std::iota(ord.begin(), ord.end(), 0u);
-    std::sort(ord.begin(), ord.end(), [&](uint32_t a, uint32_t b) {
-        return std::lexicographical_compare(hits + (size_t)a * kMaxHits,
-                                            hits + (size_t)a * kMaxHits + kMaxHits,
-                                            hits + (size_t)b * kMaxHits,
-                                            hits + (size_t)b * kMaxHits + kMaxHits);
-    });
+    std::vector<uint32_t> ord;
+    canonical_order(hits, n, ord);
     for (size_t k = 0; k < n; ++k) {
         uint32_t s = ord[k];
         if (out->n_hits) out->n_hits[k] = nh[s];

@@ -209,13 +209,15 @@ class TrackBuffer:
         return out
 
 
-def _read_tracks(call, cap_hint=4096) -> dict:
-    cap = cap_hint
+def _read_tracks(call, holder) -> dict:
+    """Fill a reusable TrackBuffer (grown on PXR_ETRUNC) and return copies of the results."""
     while True:
-        buf = TrackBuffer(cap)
+        buf = holder.get("buf")
+        if buf is None:
+            buf = holder["buf"] = TrackBuffer(8192)
         rc = call(buf.c)
         if rc == ETRUNC:
-            cap = buf.c.n_tracks + 16
+            holder["buf"] = TrackBuffer(max(2 * buf.capacity, buf.c.n_tracks + 16))
             continue
         _check(rc)
         return buf.result()
@@ -255,6 +257,7 @@ class Context:
         _check(L.pxr_create(C.byref(cfg), C.byref(h)))
         self.h = h
         self._arena_ref = arena          # keep caller memory alive
+        self._tracks = {}                # reusable host buffer for fetches
 
     def close(self):
         if self.h:
@@ -300,7 +303,8 @@ class Context:
         return [done[i] for i in range(n.value)]
 
     def pxr_fetch_tracks(self, ticket: int) -> dict:
-        return _read_tracks(lambda t: load().pxr_fetch_tracks(self.h, ticket, C.byref(t)))
+        return _read_tracks(lambda t: load().pxr_fetch_tracks(self.h, ticket, C.byref(t)),
+                            self._tracks)
 
     def pxr_fetch_debug(self, ticket: int, what: int) -> np.ndarray:
         return _read_debug(lambda b, cap, n: load().pxr_fetch_debug(self.h, ticket, what, b, cap,
@@ -330,13 +334,14 @@ class Plan:
         self.h = h
         self.ctx = ctx
         self.n_events = len(off) - 1
+        self._tracks = {}
         self._refs = (x, y, z, layer)      # the caller's device inputs stay alive
 
     def pxr_plan_run(self, stream=None):
         _check(load().pxr_plan_run(self.h, ptr(stream)))
 
     def pxr_plan_tracks(self, e: int) -> dict:
-        return _read_tracks(lambda t: load().pxr_plan_tracks(self.h, e, C.byref(t)))
+        return _read_tracks(lambda t: load().pxr_plan_tracks(self.h, e, C.byref(t)), self._tracks)
 
     def pxr_plan_debug(self, e: int, what: int) -> np.ndarray:
         return _read_debug(lambda b, cap, n: load().pxr_plan_debug(self.h, e, what, b, cap, n),
