@@ -207,23 +207,19 @@ def doublet_algorithmic_bytes(layer_counts, pairs, n_cells):
 def run_pxr(args, rank, world, local):
     import torch
     import torch.distributed as dist
-    from paper_2104_06573_gb300 import pxr, synth
+    from paper_2104_06573_gb300 import pxr, shard, synth
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
     cut = pxr.CUT_FP32 if args.cut == "fp32" else pxr.CUT_FP64
     fit = {"fp64": pxr.FIT_FP64, "mixed": pxr.FIT_MIXED, "fp32": pxr.FIT_FP32}[args.fit]
     P = synth.params_barrel_quadruplets()
     params = pxr.params_from(P, cut_mode=cut, fit_mode=fit)
     # each rank processes its own batch of events (event sharding, no collective)
-    counts, evs = make_batch(args.events, seed0=rank * 100000)
+    counts, evs = make_batch(args.events, seed0=shard.rank_seed0(rank))
     off = np.zeros(len(evs) + 1, np.uint32)
     off[1:] = np.cumsum([e.n for e in evs])
     cat = lambda k: np.concatenate([getattr(e, k) for e in evs])
@@ -254,7 +250,7 @@ def run_pxr(args, rank, world, local):
     ev = step_events(args.steps)
     clocks = Clocks(local)
     clocks.start()
-    barrier()
+    shard.barrier()
     torch.cuda.synchronize()
     stage = np.zeros(5)
     with torch.cuda.stream(stream):
@@ -266,14 +262,11 @@ def run_pxr(args, rank, world, local):
             stream.synchronize()
             stage += np.array(plan.pxr_plan_stage_ms())
     torch.cuda.synchronize()
-    barrier()
+    shard.barrier()
     clk = clocks.stop()
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
     total_ms = float(step_ms.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = shard.max_over_ranks(total_ms, device=dev)
     value = args.events * world * args.steps / (total_ms / 1e3)
     stage /= args.steps
 

@@ -271,3 +271,31 @@ def test_fit_batch_modes(ctx, orc):
     # still 1 % of the stated tolerance.
     for k, v in res[pxr.FIT_FP64].items():
         assert v < 0.01 * TOL[k], (k, v)
+
+
+def test_two_contexts_shard_events(ctx):
+    """Event sharding as the multi-GPU path does it, with two contexts standing in for two GPUs
+    on the one device: events dealt round-robin to the contexts give, event by event, the results
+    one context gives for the whole list (nothing crosses contexts)."""
+    from paper_2104_06573_gb300 import shard
+    P = synth.params_barrel_quadruplets()
+    p = pxr.params_from(P, cut_mode=pxr.CUT_FP32)
+    evs = [ev_tuple(synth.event_serving(300 + k, n)) for k, n in enumerate([40, 900, 0, 2500, 7])]
+    whole = [r["tracks"] for r in run_plan(ctx, evs, P, pxr.CUT_FP32, debug=False)]
+    got = {}
+    ctxs = [pxr.Context(device=0, mem_budget_bytes=2 << 30) for _ in range(2)]
+    try:
+        for r, c in enumerate(ctxs):
+            tickets = {int(e): c.pxr_submit_event(*evs[e], p) for e in shard.shard(len(evs), r, 2)}
+            done = set()
+            while len(done) < len(tickets):
+                done |= set(c.pxr_poll(timeout_us=200000))
+            got.update({e: c.pxr_fetch_tracks(t) for e, t in tickets.items()})
+    finally:
+        for c in ctxs:
+            c.close()
+    assert sorted(got) == list(range(len(evs)))
+    for e, w in enumerate(whole):
+        assert gpu_tuples(got[e]) == gpu_tuples(w)
+        for k in pxr.TRACK_FIELDS:
+            assert np.array_equal(got[e][k], w[k]), k
