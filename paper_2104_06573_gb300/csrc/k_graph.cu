@@ -7,12 +7,12 @@
 // contiguous (the CA stage reads them as one run per pair).
 //
 // CA connect: one warp per junction hit j.  j's out-cells (j, k) are staged in shared memory and
-// bucketed by the free coordinate of k (z on barrel layers, r on disks); each in-cell (i, j) tests
-// only the buckets reached by the cone of r-z directions within asin(theta_cut) of its own, a
-// conservative window in which the exact cuts decide.  Passes are counted first; in-cells with
-// passes reserve their edge list with one atomic.  Ntuplets: one thread per root cell walks the
-// out-edges depth first with an explicit stack.  Selection removes suffix paths and assigns
-// output slots.
+// counting-sorted by the free coordinate of k (z on barrel layers, r on disks); each in-cell
+// (i, j), one per lane, tests only the bins reached by the cone of r-z directions within
+// asin(theta_cut) of its own, a conservative window in which the exact cuts decide.  Lanes with
+// passes find their cell's index by a warp-wide search of a narrow range and append their edge
+// lists through one atomic per warp.  Ntuplets: one warp per root hit walks the out-edges of its
+// cells depth first.  Selection removes suffix paths and assigns output slots.
 #include "pxr_dev.cuh"
 #include "pxr_cuts.cuh"
 
@@ -50,9 +50,8 @@ __device__ __forceinline__ Window phi_window(const uint32_t *__restrict__ bk, ui
 }
 
 __device__ __forceinline__ bool doublet_test(const DevBatch &b, const DevParams &p, uint32_t g,
-                                             float4 hi, uint32_t o)
+                                             float4 hi, uint32_t o, float4 ho)
 {
-    float4 ho = b.hs[o];
     if (p.cut_mode == CUT_FP32) {
         int r = doublet32(hi, ho, p.cw32);
         if (r >= 0) return r == 1;
@@ -88,14 +87,16 @@ __global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint3
             masks[k] = 0;
             if ((uint32_t)k * 32u < nc) {
                 uint32_t c = (uint32_t)k * 32u + lane;
-                bool pass = c < nc && doublet_test(b, p, g, hi, w.pos(c));
+                bool pass = false;
+                if (c < nc) { const uint32_t o = w.pos(c); pass = doublet_test(b, p, g, hi, o, b.hs[o]); }
                 masks[k] = __ballot_sync(0xFFFFFFFFu, pass);
                 count += __popc(masks[k]);
             }
         }
         for (uint32_t c0 = kMaxIt * 32u; c0 < nc; c0 += 32u) {
             uint32_t c = c0 + lane;
-            bool pass = c < nc && doublet_test(b, p, g, hi, w.pos(c));
+            bool pass = false;
+                if (c < nc) { const uint32_t o = w.pos(c); pass = doublet_test(b, p, g, hi, o, b.hs[o]); }
             count += __popc(__ballot_sync(0xFFFFFFFFu, pass));
         }
 
@@ -113,8 +114,6 @@ __global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint3
         }
         if (nw == 0) continue;
         const uint32_t first = b.cell_off[e] + base;
-        const bool fp64 = p.cut_mode == CUT_FP64;
-        const double ri = fp64 ? b.r64[g] : 0.0;
         uint32_t run = 0;
 #pragma unroll
         for (int k = 0; k < kMaxIt; ++k) {
@@ -125,8 +124,6 @@ __global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint3
                     uint32_t o = w.pos((uint32_t)k * 32u + lane);
                     b.cell_in[first + idx] = g;
                     b.cell_out[first + idx] = o;
-                    if (fp64) b.cell_len64[first + idx] =
-                        seglen64(ri, (double)hi.z, b.r64[o], (double)b.hs[o].z);
                 }
             }
             run += __popc(m);
@@ -134,15 +131,13 @@ __global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint3
         for (uint32_t c0 = kMaxIt * 32u; c0 < nc; c0 += 32u) {
             uint32_t c = c0 + lane;
             uint32_t o = c < nc ? w.pos(c) : 0u;
-            bool pass = c < nc && doublet_test(b, p, g, hi, o);
+            bool pass = c < nc && doublet_test(b, p, g, hi, o, b.hs[o]);
             uint32_t m = __ballot_sync(0xFFFFFFFFu, pass);
             if (pass) {
                 uint32_t idx = run + __popc(m & lt_mask);
                 if (idx < nw) {
                     b.cell_in[first + idx] = g;
                     b.cell_out[first + idx] = o;
-                    if (fp64) b.cell_len64[first + idx] =
-                        seglen64(ri, (double)hi.z, b.r64[o], (double)b.hs[o].z);
                 }
             }
             run += __popc(m);
@@ -165,54 +160,33 @@ void launch_doublets(const DevBatch &b, const DevParams &p, cudaStream_t s, int 
 // ------------------------------------------------------------------------------------------
 // CA connect
 // ------------------------------------------------------------------------------------------
-// Exact decision for the triplet (i, j, k): r-z alignment, then DCA.  FP32 mode decides in float
-// when outside the guard band and falls back to the FP64 formulas otherwise.
+// Exact decision for the triplet (i, j, k), k the outer hit of the out-cell B = (j, k):
+// r-z alignment, then DCA.  FP32 mode decides in float when outside the guard band and falls
+// back to the FP64 formulas otherwise (the FP64 inputs are loaded only on that path).
 __device__ __forceinline__ bool triplet_test(const DevBatch &b, const DevParams &p, uint32_t i,
-                                             uint32_t j, uint32_t k, float4 hi, float4 hj,
-                                             float4 hk, const RZ32 &a, double na64)
+                                             uint32_t j, uint32_t B, float xi, float yi,
+                                             float4 hj, float4 hk, const RZ32 &a)
 {
     bool exact_theta = p.cut_mode == CUT_FP64;
     if (!exact_theta) {
-        const RZ32 bs = rz32(hj, hk);
-        const int r = theta32(a, bs, p.theta32);
+        const int r = theta32(a, rz32(hj, hk), p.theta32);
         if (r == 0) return false;
         exact_theta = r < 0;
     }
     if (exact_theta) {
+        const uint32_t k = b.cell_out[B];
+        const double zi = (double)b.hs[i].z, zj = (double)hj.z, zk = (double)hk.z;
         const double ri = b.r64[i], rj = b.r64[j], rk = b.r64[k];
-        const double nA = p.cut_mode == CUT_FP64 ? na64 : seglen64(ri, (double)hi.z, rj, (double)hj.z);
-        const double nB = seglen64(rj, (double)hj.z, rk, (double)hk.z);
-        if (!theta64(ri, (double)hi.z, rj, (double)hj.z, rk, (double)hk.z, nA, nB, p.theta))
-            return false;
+        const double nA = seglen64(ri, zi, rj, zj);
+        const double nB = seglen64(rj, zj, rk, zk);
+        if (!theta64(ri, zi, rj, zj, rk, zk, nA, nB, p.theta)) return false;
     }
     if (p.cut_mode == CUT_FP32) {
-        const int r = dca32(hi.x, hi.y, hj.x, hj.y, hk.x, hk.y, p.dca32);
+        const int r = dca32(xi, yi, hj.x, hj.y, hk.x, hk.y, p.dca32);
         if (r >= 0) return r == 1;
     }
-    return dca64((double)hi.x, (double)hi.y, (double)hj.x, (double)hj.y, (double)hk.x,
+    return dca64((double)xi, (double)yi, (double)hj.x, (double)hj.y, (double)hk.x,
                  (double)hk.y) <= p.dca;
-}
-
-// Index of the cell (i, j): i's cells toward layer Lj are stored in the candidate order of i's
-// phi window (run 1, then run 2), so their outer positions are increasing in that order.
-__device__ __forceinline__ uint32_t find_cell(const DevBatch &b, const DevParams &p,
-                                              const uint32_t *bk, uint32_t i, float4 hi,
-                                              uint32_t slot, uint32_t Lj, uint32_t j)
-{
-    const Window w = phi_window(bk, Lj, b.hphi[i], p);
-    auto rank = [&](uint32_t pos) {
-        return (pos >= w.r0 && pos < w.r0 + w.n1) ? pos - w.r0 : w.n1 + (pos - w.r2);
-    };
-    const uint32_t f = b.out_first[(size_t)i * kMaxOut + slot];
-    const uint32_t n = b.out_n[(size_t)i * kMaxOut + slot];
-    const uint32_t want = rank(j);
-    uint32_t lo = 0, hi_ = n;
-    while (lo < hi_) {
-        const uint32_t mid = (lo + hi_) >> 1;
-        if (rank(b.cell_out[f + mid]) < want) lo = mid + 1; else hi_ = mid;
-    }
-    if (lo < n && b.cell_out[f + lo] == j) return f + lo;
-    return kNone;   // dropped by a cell overflow
 }
 
 // Conservative interval of the free coordinate (z on a barrel layer, r on a disk) reachable from
@@ -247,7 +221,6 @@ __device__ __forceinline__ bool cone_window(float ar, float az, float base, floa
 constexpr int kConnWarps = 8;
 constexpr int kStage = 256;     // out-cells of one junction staged per out-layer slot
 constexpr int kBins = 128;      // local bins of the free coordinate (multiple of 32)
-constexpr int kPass = 64;       // passing triplets collected per round of 32 in-cells
 
 // Order-preserving int encoding of floats (for warp min / max reductions).
 __device__ __forceinline__ int ford(float f)
@@ -257,90 +230,99 @@ __device__ __forceinline__ int ford(float f)
 }
 __device__ __forceinline__ float funord(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
 
-// Append n out-edges of cell A (its list may already hold edges from an earlier out-layer slot).
-template <typename G>
-__device__ __forceinline__ void append_edges(const DevBatch &b, uint32_t e, uint32_t A, bool first_slot,
-                                             uint32_t n, G &&get)
+// Search range of the cell (i, j) in i's cell list toward layer Lj.  The list [f, f + n) holds
+// i's passing candidates on Lj in candidate order (phi window, run 1 then run 2); with c the rank
+// of j among the nc candidates, at most nc - n candidates failed, so the cell's offset lies in
+// [c - (nc - n), c].  Returns that range and the whole list.
+__device__ __forceinline__ void cell_range(const DevBatch &b, const DevParams &p,
+                                           const uint32_t *bk, uint32_t i, uint32_t slot,
+                                           uint32_t Lj, uint32_t j, uint32_t &lo, uint32_t &hi,
+                                           uint32_t &flo, uint32_t &fhi)
 {
-    const uint32_t have = first_slot ? 0u : b.nbr_n[A];
-    const uint32_t old = b.nbr_first[A];
-    const uint32_t need = have + n;
-    const uint32_t base = atomicAdd(&b.cnt[C_EDGES * b.E + e], need);
-    const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
-    const uint32_t nw = base >= cap ? 0u : min(need, cap - base);
-    if (nw < need) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
-    const uint32_t first = b.edge_off[e] + base;
-    uint32_t w = 0;
-    for (uint32_t t = 0; t < have && w < nw; ++t) b.nbr[first + w++] = b.nbr[old + t];
-    for (uint32_t t = 0; t < n && w < nw; ++t) b.nbr[first + w++] = get(t);
-    b.nbr_first[A] = first;
-    b.nbr_n[A] = w;
+    const uint32_t f = b.out_first[(size_t)i * kMaxOut + slot];
+    const uint32_t n = b.out_n[(size_t)i * kMaxOut + slot];
+    const Window w = phi_window(bk, Lj, b.hphi[i], p);
+    const uint32_t nc = w.size();
+    flo = f;
+    fhi = f + n;
+    const bool in1 = j >= w.r0 && j < w.r0 + w.n1, in2 = j >= w.r2 && j < w.r2 + w.n2;
+    if (n == 0 || !(in1 || in2) || n > nc) {
+        lo = flo;
+        hi = fhi;
+        return;
+    }
+    const uint32_t c = in1 ? j - w.r0 : w.n1 + (j - w.r2);
+    const uint32_t rej = nc - n;
+    lo = f + (c > rej ? c - rej : 0u);
+    hi = f + (c < n - 1 ? c : n - 1) + 1u;
 }
 
 // One warp per junction hit j.  For each out-layer slot, j's out-cells (j, k) are staged in
-// shared memory and bucketed by the free coordinate of k (z on barrel layers, r on disks) over
-// the staged range.  The in-cells (i, j) are found 32 at a time by scanning i over j's phi window
-// on the inner layer with the doublet cut; each computes the cone of r-z directions that can pass
-// the alignment cut and the buckets it reaches (a conservative window: the exact cuts decide).
-// The warp then tests all 32 in-cells' candidates together, 32 at a time, collecting passes in a
-// shared list; each in-cell with passes finds its own index and appends its edge list.  A slot
-// with more than kStage out-cells is tested against all of them from global memory; an in-cell
-// whose passes overflow the list is redone alone.
+// shared memory (k's coordinates) and counting-sorted by the free coordinate of k (z on barrel
+// layers, r on disks) into local bins over the staged range.  The in-cells (i, j) are found 32
+// at a time, one per lane, by scanning i over j's phi window on the inner layer with the doublet
+// cut; each lane computes the cone of r-z directions that can pass the alignment cut, the bins it
+// reaches (a conservative window: the exact cuts decide) and tests those out-cells itself.  Lanes
+// with passes locate their in-cell's index with warp-wide coalesced searches and append their
+// edges through one atomic per warp.  A slot with more than kStage out-cells is tested against all
+// of them from global memory.  Loads that do not depend on one another are issued together (the
+// junction's own records, its first out-cell list and inner window) so that a junction waits on
+// few memory round trips.
 __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevParams p)
 {
-    // per-warp staging and per-lane in-cell records (structure of arrays: lanes reading other
-    // lanes' records hit distinct banks)
-    __shared__ uint32_t s_B[kConnWarps][kStage], s_k[kConnWarps][kStage];
-    __shared__ float s_f[kConnWarps][kStage];
-    __shared__ uint32_t s_bin[kConnWarps][kBins];
-    __shared__ float4 s_hi[kConnWarps][32], s_a[kConnWarps][32];
-    __shared__ double s_na[kConnWarps][32];
-    __shared__ uint32_t s_i[kConnWarps][32], s_q0[kConnWarps][32], s_pre[kConnWarps][32],
-        s_npass[kConnWarps][32], s_seq[kConnWarps][32];
-    __shared__ uint32_t s_pB[kConnWarps][kPass];
-    __shared__ uint8_t s_pown[kConnWarps][kPass];
-    __shared__ uint32_t s_np[kConnWarps];
+    __shared__ float4 s_h[kConnWarps][kStage];      // staged out-cells' outer hits (list order)
+    __shared__ uint16_t s_t[kConnWarps][kStage];    // list positions sorted by local bin
+    __shared__ uint32_t s_bin[kConnWarps][kBins];   // bin ends after the scan
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-    uint32_t *sB = s_B[wid], *sK = s_k[wid], *bin = s_bin[wid];
-    float *sF = s_f[wid];
-    float4 *Hi = s_hi[wid], *Aa = s_a[wid];
-    double *Na = s_na[wid];
-    uint32_t *Ii = s_i[wid], *Q0 = s_q0[wid], *Pre = s_pre[wid], *Np = s_npass[wid],
-             *Seq = s_seq[wid];
+    float4 *sH = s_h[wid];
+    uint16_t *sT = s_t[wid];
+    uint32_t *bin = s_bin[wid];
     const uint32_t nk = p.n_keys;
     const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t jj = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; jj < b.N;
          jj += stride) {
         const uint32_t j = (uint32_t)jj;
-        const uint32_t e = hit_event(b, j);
-        const uint32_t *bk = b.bkt + (size_t)e * (nk + 1);
-        if (j >= bk[nk]) continue;
-        const uint32_t Lj = b.hmeta[j] >> kLocalBits;
-        const uint32_t nin = p.n_in[Lj], nout = p.n_out[Lj];
-        if (nin == 0 || nout == 0) continue;
+        // independent loads first (hits past an event's valid range carry layer 0xFF)
+        const uint32_t meta = b.hmeta[j];
         const float4 hj = b.hs[j];
         const float phij = b.hphi[j];
+        const uint32_t e = hit_event(b, j);
+        uint32_t f0 = b.out_first[(size_t)j * kMaxOut];
+        uint32_t nB = b.out_n[(size_t)j * kMaxOut];
+        const uint32_t Lj = meta >> kLocalBits;
+        if (Lj >= p.n_layers) continue;
+        const uint32_t nin = p.n_in[Lj], nout = p.n_out[Lj];
+        if (nin == 0 || nout == 0) continue;
+        const uint32_t *bk = b.bkt + (size_t)e * (nk + 1);
+        const Window w0 = phi_window(bk, p.in_layer[Lj][0], phij, p);
         for (uint32_t s = 0; s < nout; ++s) {
             const uint32_t Lk = p.out_layer[Lj][s];
             const bool disk = p.is_disk[Lk];
-            const uint32_t f0 = b.out_first[(size_t)j * kMaxOut + s];
-            const uint32_t nB = b.out_n[(size_t)j * kMaxOut + s];
+            if (s) {
+                f0 = b.out_first[(size_t)j * kMaxOut + s];
+                nB = b.out_n[(size_t)j * kMaxOut + s];
+            }
             if (nB == 0) continue;
             const bool staged = nB <= (uint32_t)kStage;
             float flo = 0.f, fhi = 0.f, dlo = 0.f, dhi = 0.f, scale = 0.f;
             if (staged) {
-                // stage the out-cells: free coordinate and the ranges of both coordinates
                 int m0 = ford(3.0e38f), m1 = ford(-3.0e38f), m2 = m0, m3 = m1;
-                for (uint32_t t = lane; t < nB; t += 32) {
-                    const uint32_t k = b.cell_out[f0 + t];
-                    const float4 hk = b.hs[k];
+                auto take = [&](uint32_t t, float4 hk) {
                     const float fc = disk ? hk.w : hk.z, xc = disk ? hk.z : hk.w;
-                    sK[t] = k;
-                    sF[t] = fc;
+                    sH[t] = hk;
                     m0 = min(m0, ford(fc));
                     m1 = max(m1, ford(fc));
                     m2 = min(m2, ford(xc));
                     m3 = max(m3, ford(xc));
+                };
+                for (uint32_t t0 = 0; t0 < nB; t0 += 64) {      // two loads in flight per lane
+                    const uint32_t ta = t0 + lane, tb = ta + 32u;
+                    const uint32_t ka = ta < nB ? b.cell_out[f0 + ta] : 0u;
+                    const uint32_t kb = tb < nB ? b.cell_out[f0 + tb] : 0u;
+                    const float4 ha = ta < nB ? b.hs[ka] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 hb = tb < nB ? b.hs[kb] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (ta < nB) take(ta, ha);
+                    if (tb < nB) take(tb, hb);
                 }
                 m0 = __reduce_min_sync(0xFFFFFFFFu, m0);
                 m1 = __reduce_max_sync(0xFFFFFFFFu, m1);
@@ -351,29 +333,24 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                 dlo = funord(m2) - (disk ? hj.z : hj.w);
                 dhi = funord(m3) - (disk ? hj.z : hj.w);
                 scale = fhi > flo ? (float)kBins / (fhi - flo) : 0.f;
-                // counting sort by local bin: histogram, warp scan, scatter
-                for (uint32_t t = lane; t < (uint32_t)kBins; t += 32) bin[t] = 0;
-                __syncwarp();
-                uint32_t mybin[kStage / 32], myk[kStage / 32];
+                // counting sort of the list positions by local bin: histogram, scan, scatter
 #pragma unroll
-                for (int q = 0; q < kStage / 32; ++q) {
-                    const uint32_t t = lane + 32u * q;
-                    if (t < nB) {
-                        int bb = (int)floorf((sF[t] - flo) * scale);
-                        bb = bb < 0 ? 0 : (bb >= kBins ? kBins - 1 : bb);
-                        mybin[q] = (uint32_t)bb;
-                        myk[q] = sK[t];
-                        atomicAdd(&bin[bb], 1u);
-                    }
-                }
+                for (int q = 0; q < kBins / 32; ++q) bin[lane + 32 * q] = 0;
+                __syncwarp();
+                auto local_bin = [&](uint32_t t) {
+                    const float4 hk = sH[t];
+                    const int bb = (int)floorf(((disk ? hk.w : hk.z) - flo) * scale);
+                    return bb < 0 ? 0u : (bb >= kBins ? (uint32_t)kBins - 1u : (uint32_t)bb);
+                };
+                for (uint32_t t = lane; t < nB; t += 32) atomicAdd(&bin[local_bin(t)], 1u);
                 __syncwarp();
                 {
-                    // exclusive scan of the kBins counts: kBins / 32 consecutive bins per lane
-                    constexpr int per = kBins / 32;
+                    constexpr int per = kBins / 32;      // consecutive bins per lane
                     uint32_t v[per], sum = 0;
 #pragma unroll
                     for (int q = 0; q < per; ++q) { v[q] = bin[lane * per + q]; sum += v[q]; }
                     uint32_t incl = sum;
+#pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
                         const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
                         if (lane >= (uint32_t)o) incl += t;
@@ -384,50 +361,31 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                     for (int q = 0; q < per; ++q) { bin[lane * per + q] = run; run += v[q]; }
                     __syncwarp();
                 }
-#pragma unroll
-                for (int q = 0; q < kStage / 32; ++q) {
-                    const uint32_t t = lane + 32u * q;
-                    if (t < nB) {
-                        const uint32_t pos = atomicAdd(&bin[mybin[q]], 1u);
-                        sB[pos] = f0 + t;
-                        sK[pos] = myk[q];
-                    }
-                }
+                for (uint32_t t = lane; t < nB; t += 32)
+                    sT[atomicAdd(&bin[local_bin(t)], 1u)] = (uint16_t)t;
                 __syncwarp();
                 // bin[t] is now the end of bin t; the start of bin t is bin[t - 1] (0 for t = 0)
             }
             for (uint32_t si = 0; si < nin; ++si) {
                 const uint32_t Li = p.in_layer[Lj][si];
                 const uint32_t slot_i = p.in_slot[Lj][si];
-                const Window w = phi_window(bk, Li, phij, p);
+                const Window w = si ? phi_window(bk, Li, phij, p) : w0;
                 const uint32_t nc = w.size();
                 for (uint32_t c0 = 0; c0 < nc; c0 += 32) {
-                    // ---- set-up of one in-cell per lane ----
+                    // ---- one in-cell candidate per lane ----
                     const uint32_t c = c0 + lane;
-                    uint32_t q0 = 0, q1 = 0, my_i = 0;
-                    float4 my_hi = make_float4(0.f, 0.f, 0.f, 0.f);
-                    RZ32 my_a{0.f, 0.f, 0.f, 0.f};
-                    double my_na = 0.0;
-                    Np[lane] = 0;
-                    Seq[lane] = 0;
-                    bool valid = c < nc;
-                    if (valid) {
-                        my_i = w.pos(c);
-                        my_hi = b.hs[my_i];
-                        valid = doublet_test(b, p, my_i, my_hi, j);
-                        if (valid) {
-                            my_a = rz32(my_hi, hj);
-                            my_na = p.cut_mode == CUT_FP64
-                                        ? seglen64(b.r64[my_i], (double)my_hi.z, b.r64[j], (double)hj.z)
-                                        : 0.0;
-                            Ii[lane] = my_i;
-                            Hi[lane] = my_hi;
-                            Aa[lane] = make_float4(my_a.ar, my_a.az, my_a.na, my_a.Ea);
-                            Na[lane] = my_na;
+                    uint32_t i = 0, q0 = 0, q1 = 0;
+                    float4 hi = make_float4(0.f, 0.f, 0.f, 0.f);
+                    RZ32 a{0.f, 0.f, 0.f, 0.f};
+                    if (c < nc) {
+                        i = w.pos(c);
+                        hi = b.hs[i];
+                        if (doublet_test(b, p, i, hi, j, hj)) {
+                            a = rz32(hi, hj);
                             q1 = nB;
                             float lo, hi_;
-                            if (staged && cone_window(my_a.ar, my_a.az, disk ? hj.w : hj.z, dlo,
-                                                      dhi, disk, p.tan_win, lo, hi_)) {
+                            if (staged && cone_window(a.ar, a.az, disk ? hj.w : hj.z, dlo, dhi,
+                                                      disk, p.tan_win, lo, hi_)) {
                                 if (hi_ < flo || lo > fhi) {
                                     q1 = 0;
                                 } else {
@@ -441,77 +399,88 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                             }
                         }
                     }
-                    const uint32_t cnt = q1 - q0;
-                    Q0[lane] = q0;
-                    uint32_t incl = cnt;
+                    // ---- each lane tests its own candidates ----
+                    uint32_t npass = 0, qf = 0, Bf = 0;
+                    for (uint32_t q = q0; q < q1; ++q) {
+                        uint32_t B;
+                        float4 hk;
+                        if (staged) {
+                            const uint32_t t = sT[q];
+                            B = f0 + t;
+                            hk = sH[t];
+                        } else {
+                            B = f0 + q;
+                            hk = b.hs[b.cell_out[B]];
+                        }
+                        if (triplet_test(b, p, i, j, B, hi.x, hi.y, hj, hk, a)) {
+                            if (npass == 0) { qf = q; Bf = B; }
+                            ++npass;
+                        }
+                    }
+                    const uint32_t pm = __ballot_sync(0xFFFFFFFFu, npass > 0);
+                    if (pm == 0) continue;
+                    // ---- index of each passing lane's in-cell (i, j) ----
+                    uint32_t lo = 0, hi_ = 0, flo_ = 0, fhi_ = 0;
+                    if (npass) cell_range(b, p, bk, i, slot_i, Lj, j, lo, hi_, flo_, fhi_);
+                    uint32_t A = kNone;
+                    for (uint32_t m = pm; m; m &= m - 1) {
+                        const int L = __ffs(m) - 1;
+                        const uint32_t r0 = __shfl_sync(0xFFFFFFFFu, lo, L);
+                        const uint32_t r1 = __shfl_sync(0xFFFFFFFFu, hi_, L);
+                        const uint32_t g0 = __shfl_sync(0xFFFFFFFFu, flo_, L);
+                        const uint32_t g1 = __shfl_sync(0xFFFFFFFFu, fhi_, L);
+                        uint32_t found = kNone;
+                        for (int pass = 0; pass < 2 && found == kNone; ++pass) {
+                            const uint32_t s0 = pass ? g0 : r0, s1 = pass ? g1 : r1;
+                            for (uint32_t q = s0; q < s1; q += 32) {
+                                const bool hit = q + lane < s1 && b.cell_out[q + lane] == j;
+                                const uint32_t bm = __ballot_sync(0xFFFFFFFFu, hit);
+                                if (bm) { found = q + (uint32_t)(__ffs(bm) - 1); break; }
+                            }
+                        }
+                        if (lane == (uint32_t)L) A = found;
+                    }
+                    // ---- append the edges: one atomic per warp reserves all lanes' lists ----
+                    const bool ok = npass && A != kNone;   // kNone: the cell was dropped (overflow)
+                    uint32_t have = 0, old = 0;
+                    if (ok && s > 0) { have = b.nbr_n[A]; old = b.nbr_first[A]; }
+                    const uint32_t need = ok ? have + npass : 0u;
+                    uint32_t incl = need;
+#pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
                         const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
                         if (lane >= (uint32_t)o) incl += t;
                     }
-                    Pre[lane] = incl - cnt;
                     const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-                    if (lane == 0) s_np[wid] = 0;
-                    __syncwarp();
-                    // ---- the warp tests all candidates, 32 at a time ----
-                    for (uint32_t t0 = 0; t0 < tot; t0 += 32) {
-                        const uint32_t t = t0 + lane;
-                        if (t >= tot) continue;
-                        uint32_t lo = 0, hi_ = 31;              // last lane with pre <= t
-                        while (lo < hi_) {
-                            const uint32_t mid = (lo + hi_ + 1) >> 1;
-                            if (Pre[mid] <= t) lo = mid; else hi_ = mid - 1;
-                        }
-                        const uint32_t q = Q0[lo] + (t - Pre[lo]);
-                        uint32_t B, k;
-                        if (staged) { B = sB[q]; k = sK[q]; }
-                        else { B = f0 + q; k = b.cell_out[B]; }
-                        const float4 av = Aa[lo];
-                        const RZ32 oa{av.x, av.y, av.z, av.w};
-                        if (triplet_test(b, p, Ii[lo], j, k, Hi[lo], hj, b.hs[k], oa, Na[lo])) {
-                            const uint32_t slot = atomicAdd(&s_np[wid], 1u);
-                            if (slot < (uint32_t)kPass) {
-                                s_pB[wid][slot] = B;
-                                s_pown[wid][slot] = (uint8_t)lo;
-                                atomicAdd(&Np[lo], 1u);
+                    uint32_t base = 0;
+                    if (lane == 0 && tot) base = atomicAdd(&b.cnt[C_EDGES * b.E + e], tot);
+                    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                    if (ok) {
+                        const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
+                        const uint32_t my0 = base + incl - need;
+                        const uint32_t nw = my0 >= cap ? 0u : min(need, cap - my0);
+                        if (nw < need) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+                        const uint32_t first = b.edge_off[e] + my0;
+                        uint32_t wr = 0;
+                        for (uint32_t t = 0; t < have && wr < nw; ++t) b.nbr[first + wr++] = b.nbr[old + t];
+                        if (wr < nw) b.nbr[first + wr++] = Bf;
+                        for (uint32_t q = qf + 1; q < q1 && wr < nw && npass > 1; ++q) {
+                            uint32_t B;
+                            float4 hk;
+                            if (staged) {
+                                const uint32_t t = sT[q];
+                                B = f0 + t;
+                                hk = sH[t];
                             } else {
-                                Seq[lo] = 1;
+                                B = f0 + q;
+                                hk = b.hs[b.cell_out[B]];
                             }
+                            if (triplet_test(b, p, i, j, B, hi.x, hi.y, hj, hk, a))
+                                b.nbr[first + wr++] = B;
                         }
+                        b.nbr_first[A] = first;
+                        b.nbr_n[A] = wr;
                     }
-                    __syncwarp();
-                    // ---- in-cells with passes write their edges ----
-                    const uint32_t my_np = Np[lane];
-                    if (valid && (my_np || Seq[lane])) {
-                        const uint32_t A = find_cell(b, p, bk, my_i, my_hi, slot_i, Lj, j);
-                        if (A != kNone) {
-                            if (Seq[lane]) {
-                                uint32_t n = 0;
-                                for (uint32_t q = q0; q < q1; ++q) {
-                                    const uint32_t B = staged ? sB[q] : f0 + q;
-                                    const uint32_t k = staged ? sK[q] : b.cell_out[B];
-                                    n += triplet_test(b, p, my_i, j, k, my_hi, hj, b.hs[k], my_a, my_na);
-                                }
-                                uint32_t q = q0;
-                                append_edges(b, e, A, s == 0, n, [&](uint32_t) {
-                                    for (;; ++q) {
-                                        const uint32_t B = staged ? sB[q] : f0 + q;
-                                        const uint32_t k = staged ? sK[q] : b.cell_out[B];
-                                        if (triplet_test(b, p, my_i, j, k, my_hi, hj, b.hs[k], my_a, my_na)) {
-                                            ++q;
-                                            return B;
-                                        }
-                                    }
-                                });
-                            } else {
-                                uint32_t q = 0;
-                                append_edges(b, e, A, s == 0, my_np, [&](uint32_t) {
-                                    while (s_pown[wid][q] != lane) ++q;
-                                    return s_pB[wid][q++];
-                                });
-                            }
-                        }
-                    }
-                    __syncwarp();
                 }
             }
             __syncwarp();

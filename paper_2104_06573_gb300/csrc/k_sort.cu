@@ -82,6 +82,8 @@ __global__ void __launch_bounds__(512) k_sort(DevBatch b, DevParams p)
         uint32_t *bk = b.bkt + (size_t)e * (nk + 1);
         for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) bk[k] = h0 + s_cnt[k];
         if (threadIdx.x == 0) bk[nk] = h0 + total;
+        // positions past the valid hits (inputs with a bad layer) get layer 0xFF in their record
+        for (uint32_t h = total + threadIdx.x; h < n; h += blockDim.x) b.hmeta[h0 + h] = 0xFFFFFFFFu;
         __syncthreads();
         for (uint32_t h = threadIdx.x; h < n; h += blockDim.x) {
             uint32_t g = h0 + h;

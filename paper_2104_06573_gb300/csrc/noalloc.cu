@@ -34,10 +34,9 @@ constexpr size_t kNaR64 = na_align(kNaHs + 16 * (size_t)kNaMaxHits);     // hits
 constexpr size_t kNaMeta = na_align(kNaR64 + 8 * (size_t)kNaMaxHits);    // hits x u32
 constexpr size_t kNaFirst = na_align(kNaMeta + 4 * (size_t)kNaMaxHits);  // hits x 4 x u32
 constexpr size_t kNaN = na_align(kNaFirst + 16 * (size_t)kNaMaxHits);    // hits x 4 x u32
-constexpr size_t kNaLen = na_align(kNaN + 16 * (size_t)kNaMaxHits);      // cells x double
-constexpr size_t kNaPhi = na_align(kNaLen + 8 * (size_t)kNaMaxCells);    // hits x float
+constexpr size_t kNaPhi = na_align(kNaN + 16 * (size_t)kNaMaxHits);      // hits x float
 constexpr size_t kNaHitChunk = na_align(kNaPhi + 4 * (size_t)kNaMaxHits); // hit chunks x u32
-constexpr size_t kNaBytes = na_align(kNaHitChunk + 4 * (size_t)(kNaMaxHits / kHitChunk));  // ~13 MB
+constexpr size_t kNaBytes = na_align(kNaHitChunk + 4 * (size_t)(kNaMaxHits / kHitChunk));  // ~4.5 MB
 
 static __device__ __align__(256) unsigned char g_scratch[kNaBytes];
 
@@ -152,7 +151,6 @@ extern "C" int pxr_doublets_noalloc(const float *x, const float *y, const float 
     b.out_n = reinterpret_cast<uint32_t *>(base + kNaN);
     b.cell_in = cells_inner;
     b.cell_out = cells_outer;
-    b.cell_len64 = reinterpret_cast<double *>(base + kNaLen);
     b.hphi = reinterpret_cast<float *>(base + kNaPhi);
     b.hit_chunk = reinterpret_cast<const uint32_t *>(base + kNaHitChunk);
     int sms = 152;

@@ -80,7 +80,6 @@ struct DevBatch {
     uint32_t *out_first;                // [N * kMaxOut] first cell of (inner hit, slot)
     uint32_t *out_n;                    // [N * kMaxOut] number of cells
     uint32_t *cell_in, *cell_out;       // [cells] sorted hit positions
-    double *cell_len64;                 // [cells] |(dr, dz)| in FP64 (FP64 cut mode only)
     // CA graph: out-edges of each cell
     uint32_t *nbr_first;                // [cells]
     uint32_t *nbr_n;                    // [cells]

@@ -210,14 +210,14 @@ struct PlanOffsets {
     size_t x, y, z, layer, hit_off, cell_off, edge_off, tup_off, cell_chunk, tup_chunk, hit_chunk,
         head_end;
     size_t cnt, bkt, hs, r64, hmeta, hphi, out_first, out_n, cell_in, cell_out,
-        cell_len64, nbr_first,
+        nbr_first,
         nbr_n, nbr, mindepth, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, out_evt, o_nh,
         o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status;
     size_t total;
 };
 
 static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, uint64_t T,
-                               const DevParams &dp, bool with_inputs, bool fp64_cells)
+                               const DevParams &dp, bool with_inputs)
 {
     Layout L;
     PlanOffsets o{};
@@ -245,7 +245,6 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.out_n = L.add(4 * N * kMaxOut);
     o.cell_in = L.add(4 * C);
     o.cell_out = L.add(4 * C);
-    o.cell_len64 = L.add(fp64_cells ? 8 * C : 0);
     o.nbr_first = L.add(4 * C);
     o.nbr_n = L.add(4 * C);
     o.nbr = L.add(4 * G);
@@ -406,7 +405,6 @@ static void plan_bind(pxr_plan *P)
     b.out_n = (uint32_t *)(r + o.out_n);
     b.cell_in = (uint32_t *)(r + o.cell_in);
     b.cell_out = (uint32_t *)(r + o.cell_out);
-    b.cell_len64 = (double *)(r + o.cell_len64);
     b.nbr_first = (uint32_t *)(r + o.nbr_first);
     b.nbr_n = (uint32_t *)(r + o.nbr_n);
     b.nbr = (uint32_t *)(r + o.nbr);
@@ -468,7 +466,7 @@ static int plan_size(pxr_plan *P, const uint32_t *lcount, bool with_inputs)
         while (e + 1 < E && g >= P->hit_off[e + 1]) ++e;
         P->hit_chunk[c] = (uint32_t)e;
     }
-    P->off = plan_layout(E, P->N, C, G, T, P->dp, with_inputs, P->dp.cut_mode == CUT_FP64);
+    P->off = plan_layout(E, P->N, C, G, T, P->dp, with_inputs);
     return PXR_OK;
 }
 
@@ -959,8 +957,7 @@ static size_t event_bytes(const pxr_params &p, const DevParams &dp, const uint32
                           uint32_t n)
 {
     EventCaps c = event_caps(p, lcount, n);
-    PlanOffsets o = plan_layout(1, n, c.cells, c.edges, c.tuples, dp, true,
-                                p.cut_mode == PXR_CUT_FP64);
+    PlanOffsets o = plan_layout(1, n, c.cells, c.edges, c.tuples, dp, true);
     return o.total + 64 * 256;  // alignment slack of the shared batch layout
 }
 
