@@ -70,14 +70,17 @@ __global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint3
     const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (; item < n_items; item += stride) {
         const uint32_t g = (uint32_t)(item / slots), slot = (uint32_t)(item % slots);
-        const uint32_t e = hit_event(b, g);
-        const uint32_t *bk = b.bkt + (size_t)e * (nk + 1);
-        if (g >= bk[nk]) continue;                       // hit rejected by the sort (bad layer)
-        const uint32_t L = b.hmeta[g] >> kLocalBits;
-        if (slot >= p.n_out[L]) continue;
-        const uint32_t Lo = p.out_layer[L][slot];
+        // independent loads first (hits past an event's valid range carry layer 0xFF)
+        const uint32_t meta = b.hmeta[g];
         const float4 hi = b.hs[g];
-        const Window w = phi_window(bk, Lo, b.hphi[g], p);
+        const float phig = b.hphi[g];
+        const uint32_t e = hit_event(b, g);
+        const uint32_t L = meta >> kLocalBits;
+        if (L >= p.n_layers || slot >= p.n_out[L]) continue;
+        const uint32_t *bk = b.bkt + (size_t)e * (nk + 1);
+        const uint32_t c_lo = b.cell_off[e], c_hi = b.cell_off[e + 1];
+        const uint32_t Lo = p.out_layer[L][slot];
+        const Window w = phi_window(bk, Lo, phig, p);
         const uint32_t nc = w.size();
 
         uint32_t masks[kMaxIt];
@@ -103,17 +106,17 @@ __global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint3
         uint32_t base = 0;
         if (lane == 0 && count) base = atomicAdd(&b.cnt[C_CELLS * b.E + e], count);
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
-        const uint32_t cap = b.cell_off[e + 1] - b.cell_off[e];
+        const uint32_t cap = c_hi - c_lo;
         uint32_t nw = count;
         if (base >= cap) nw = 0;
         else if (base + count > cap) nw = cap - base;
         if (lane == 0) {
             if (nw < count) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_CELLS);
-            b.out_first[(size_t)g * kMaxOut + slot] = b.cell_off[e] + base;
+            b.out_first[(size_t)g * kMaxOut + slot] = c_lo + base;
             b.out_n[(size_t)g * kMaxOut + slot] = nw;
         }
         if (nw == 0) continue;
-        const uint32_t first = b.cell_off[e] + base;
+        const uint32_t first = c_lo + base;
         uint32_t run = 0;
 #pragma unroll
         for (int k = 0; k < kMaxIt; ++k) {
@@ -455,10 +458,22 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                     uint32_t base = 0;
                     if (lane == 0 && tot) base = atomicAdd(&b.cnt[C_EDGES * b.E + e], tot);
                     base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                    const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
+                    const uint32_t my0 = base + incl - need;
+                    const uint32_t nw = !ok || my0 >= cap ? 0u : min(need, cap - my0);
+                    // root cells that get their first edges go to the event's root list
+                    if ((p.root_mask >> Li) & 1u) {
+                        const bool first = have == 0 && nw > 0;
+                        const uint32_t rm = __ballot_sync(0xFFFFFFFFu, first);
+                        uint32_t rbase = 0;
+                        if (lane == 0 && rm) rbase = atomicAdd(&b.cnt[C_ROOTS * b.E + e], __popc(rm));
+                        rbase = __shfl_sync(0xFFFFFFFFu, rbase, 0) + __popc(rm & ((1u << lane) - 1u));
+                        if (first) {
+                            if (rbase < cap) b.root_list[b.edge_off[e] + rbase] = A;
+                            else atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+                        }
+                    }
                     if (ok) {
-                        const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
-                        const uint32_t my0 = base + incl - need;
-                        const uint32_t nw = my0 >= cap ? 0u : min(need, cap - my0);
                         if (nw < need) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
                         const uint32_t first = b.edge_off[e] + my0;
                         uint32_t wr = 0;
@@ -549,33 +564,53 @@ __device__ __forceinline__ void walk_from(const DevBatch &b, const DevParams &p,
 }
 
 // One warp per root hit (a hit on a root layer); its lanes walk from the hit's cells.
+// Walk from every root cell: one warp per root hit, the lanes over its cells.  Used when 2-hit
+// paths count (min_hits <= 2), since then root cells without out-edges emit too.
 __global__ void __launch_bounds__(256) k_ntuplets(DevBatch b, DevParams p)
 {
     const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t nk = p.n_keys;
     const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t gg = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gg < b.N;
          gg += stride) {
         const uint32_t g = (uint32_t)gg;
-        const uint32_t e = hit_event(b, g);
-        if (g >= b.bkt[(size_t)e * (nk + 1) + nk]) continue;
+        // independent loads first (hits past an event's valid range carry layer 0xFF)
         const uint32_t L = b.hmeta[g] >> kLocalBits;
-        if (!((p.root_mask >> L) & 1u)) continue;
+        const uint32_t e = hit_event(b, g);
+        const uint32_t f_0 = b.out_first[(size_t)g * kMaxOut];
+        const uint32_t n_0 = b.out_n[(size_t)g * kMaxOut];
+        if (L >= p.n_layers || !((p.root_mask >> L) & 1u)) continue;
         for (uint32_t s = 0; s < p.n_out[L]; ++s) {
-            const uint32_t f = b.out_first[(size_t)g * kMaxOut + s];
-            const uint32_t n = b.out_n[(size_t)g * kMaxOut + s];
-            for (uint32_t c = lane; c < n; c += 32) {
-                const uint32_t A = f + c;
-                if (b.nbr_n[A] == 0 && p.min_hits > 2) continue;   // a 2-hit path is too short
-                walk_from(b, p, e, A);
-            }
+            const uint32_t f = s ? b.out_first[(size_t)g * kMaxOut + s] : f_0;
+            const uint32_t n = s ? b.out_n[(size_t)g * kMaxOut + s] : n_0;
+            for (uint32_t c = lane; c < n; c += 32) walk_from(b, p, e, f + c);
         }
     }
 }
 
-void launch_ntuplets(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
+// Walk from the root cells that have out-edges (listed per event by the CA stage): one thread
+// per listed cell.  Enough when paths need at least 3 hits.
+__global__ void __launch_bounds__(256) k_walk_roots(DevBatch b, DevParams p, uint32_t total)
 {
-    (void)total;
+    const uint32_t n_chunks = total / kChunk;
+    for (uint32_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+        const uint32_t x = ch * kChunk + threadIdx.x;
+        const uint32_t e = b.edge_chunk[ch];
+        const uint32_t x0 = b.edge_off[e];
+        const uint32_t n = min(b.cnt[C_ROOTS * b.E + e], b.edge_off[e + 1] - x0);
+        if (x - x0 < n) walk_from(b, p, e, b.root_list[x]);
+    }
+}
+
+void launch_ntuplets(const DevBatch &b, const DevParams &p, uint32_t edge_total, cudaStream_t s,
+                     int sms)
+{
+    if (p.min_hits > 2) {
+        const uint32_t chunks = edge_total / kChunk;
+        const uint32_t cap = (uint32_t)sms * 8;
+        if (chunks == 0) return;
+        k_walk_roots<<<chunks < cap ? chunks : cap, kChunk, 0, s>>>(b, p, edge_total);
+        return;
+    }
     uint64_t blocks = ((uint64_t)b.N + 7) / 8;
     uint64_t cap = (uint64_t)sms * 16;
     if (blocks > cap) blocks = cap;

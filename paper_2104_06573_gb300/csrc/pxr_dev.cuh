@@ -24,7 +24,12 @@ constexpr uint32_t kChunk = 256;     // per-event cell / ntuplet capacities are 
 constexpr uint32_t kHitChunk = 32;   // granularity of the hit -> event table
 
 // Per-event counters, laid out as kCounters consecutive arrays of E words.
-enum Counter : int { C_CELLS = 0, C_EDGES = 1, C_TUPLES = 2, C_FLAGS = 3, C_OUT = 4, kCounters = 5 };
+enum Counter : int {
+    C_CELLS = 0, C_EDGES = 1, C_TUPLES = 2, C_FLAGS = 3, C_OUT = 4,   // reported per event
+    C_ROOTS = 5,                                                       // internal
+    kCounters = 6
+};
+constexpr int kReportedCounters = 5;
 
 // Per-event flags (C_FLAGS).
 enum Flag : uint32_t { F_CELLS = 1u, F_EDGES = 2u, F_TUPLES = 4u, F_LAYER = 8u };
@@ -73,9 +78,9 @@ struct DevBatch {
     double *r64;                        // [N] sorted radii, FP64
     uint32_t *hmeta;                    // [N] layer << 24 | local caller index
     float *hphi;                        // [N] atan2f(y, x) of the sorted hits (the binned value)
-    // event of a work chunk: cells and ntuplets by 256-entry chunk, hits by 32-hit chunk (first
-    // event of the chunk)
-    const uint32_t *cell_chunk, *tup_chunk, *hit_chunk;
+    // event of a work chunk: cells, edges and ntuplets by 256-entry chunk; hits by 32-hit chunk
+    // (first event of the chunk, bit 31 set when the chunk holds the start of a later event)
+    const uint32_t *cell_chunk, *edge_chunk, *tup_chunk, *hit_chunk;
     // cells, grouped by (inner hit, pair slot)
     uint32_t *out_first;                // [N * kMaxOut] first cell of (inner hit, slot)
     uint32_t *out_n;                    // [N * kMaxOut] number of cells
@@ -85,6 +90,7 @@ struct DevBatch {
     uint32_t *nbr_n;                    // [cells]
     uint32_t *nbr;                      // [edges] target cells
     uint32_t *mindepth;                 // [cells] fewest hits before the cell on a root path
+    uint32_t *root_list;                // [edges] per event: root cells that have out-edges
     // ntuplets
     uint32_t *tup_hits;                 // [tuples * kMaxHits] sorted hit positions
     uint8_t *tup_n;                     // [tuples]
@@ -104,8 +110,10 @@ struct DevBatch {
 // Event of hit g: the chunk table gives the event of the chunk's first hit.
 __device__ __forceinline__ uint32_t hit_event(const DevBatch &b, uint32_t g)
 {
-    uint32_t e = b.hit_chunk[g / kHitChunk];
-    while (e + 1 < b.E && g >= b.hit_off[e + 1]) ++e;
+    const uint32_t v = b.hit_chunk[g / kHitChunk];
+    uint32_t e = v & 0x7FFFFFFFu;
+    if (v >> 31)
+        while (e + 1 < b.E && g >= b.hit_off[e + 1]) ++e;
     return e;
 }
 
@@ -131,7 +139,7 @@ void launch_layer_count(const uint32_t *hit_off, const uint16_t *layer, uint32_t
 void launch_doublets(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms);
 void launch_connect(const DevBatch &b, const DevParams &p, uint32_t cell_total, cudaStream_t s,
                     int sms);
-void launch_ntuplets(const DevBatch &b, const DevParams &p, uint32_t cell_total, cudaStream_t s,
+void launch_ntuplets(const DevBatch &b, const DevParams &p, uint32_t edge_total, cudaStream_t s,
                      int sms);
 void launch_select(const DevBatch &b, const DevParams &p, uint32_t tup_total, cudaStream_t s,
                    int sms);

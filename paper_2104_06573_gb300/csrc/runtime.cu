@@ -207,11 +207,12 @@ struct Layout {
 
 struct PlanOffsets {
     // inputs (serving plans only) and small host-filled arrays come first: one H2D copy
-    size_t x, y, z, layer, hit_off, cell_off, edge_off, tup_off, cell_chunk, tup_chunk, hit_chunk,
+    size_t x, y, z, layer, hit_off, cell_off, edge_off, tup_off, cell_chunk, edge_chunk, tup_chunk,
+        hit_chunk,
         head_end;
     size_t cnt, bkt, hs, r64, hmeta, hphi, out_first, out_n, cell_in, cell_out,
         nbr_first,
-        nbr_n, nbr, mindepth, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, out_evt, o_nh,
+        nbr_n, nbr, mindepth, root_list, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, out_evt, o_nh,
         o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status;
     size_t total;
 };
@@ -231,6 +232,7 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.edge_off = L.add(4 * (E + 1));
     o.tup_off = L.add(4 * (E + 1));
     o.cell_chunk = L.add(4 * (C / kChunk));
+    o.edge_chunk = L.add(4 * (G / kChunk));
     o.tup_chunk = L.add(4 * (T / kChunk));
     o.hit_chunk = L.add(4 * ((N + kHitChunk - 1) / kHitChunk));
     o.head_end = L.total;
@@ -249,6 +251,7 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.nbr_n = L.add(4 * C);
     o.nbr = L.add(4 * G);
     o.mindepth = L.add(4 * C);
+    o.root_list = L.add(4 * G);
     o.tup_hits = L.add(4 * T * kMaxHits);
     o.tup_n = L.add(T);
     o.tup_state = L.add(T);
@@ -360,7 +363,7 @@ struct pxr_plan {
     uint32_t E = 0;
     uint64_t N = 0, C = 0, G = 0, T = 0;
     std::vector<uint32_t> hit_off, cell_off, edge_off, tup_off;
-    std::vector<uint32_t> cell_chunk, tup_chunk, hit_chunk;   // event of each work chunk
+    std::vector<uint32_t> cell_chunk, edge_chunk, tup_chunk, hit_chunk;   // event of each chunk
     PlanOffsets off{};
     char *region = nullptr;
     DevBatch db{};
@@ -398,6 +401,7 @@ static void plan_bind(pxr_plan *P)
     b.hmeta = (uint32_t *)(r + o.hmeta);
     b.hphi = (float *)(r + o.hphi);
     b.cell_chunk = (const uint32_t *)(r + o.cell_chunk);
+    b.edge_chunk = (const uint32_t *)(r + o.edge_chunk);
     b.tup_chunk = (const uint32_t *)(r + o.tup_chunk);
     b.hit_chunk = (const uint32_t *)(r + o.hit_chunk);
 
@@ -409,6 +413,7 @@ static void plan_bind(pxr_plan *P)
     b.nbr_n = (uint32_t *)(r + o.nbr_n);
     b.nbr = (uint32_t *)(r + o.nbr);
     b.mindepth = (uint32_t *)(r + o.mindepth);
+    b.root_list = (uint32_t *)(r + o.root_list);
     b.tup_hits = (uint32_t *)(r + o.tup_hits);
     b.tup_n = (uint8_t *)(r + o.tup_n);
     b.tup_state = (uint8_t *)(r + o.tup_state);
@@ -453,18 +458,23 @@ static int plan_size(pxr_plan *P, const uint32_t *lcount, bool with_inputs)
     P->G = G;
     P->T = T;
     P->cell_chunk.assign(C / kChunk, 0);
+    P->edge_chunk.assign(G / kChunk, 0);
     P->tup_chunk.assign(T / kChunk, 0);
     P->hit_chunk.assign((P->N + kHitChunk - 1) / kHitChunk, 0);
     for (uint32_t e = 0; e < E; ++e) {
         for (uint32_t c = P->cell_off[e] / kChunk; c < P->cell_off[e + 1] / kChunk; ++c)
             P->cell_chunk[c] = e;
+        for (uint32_t c = P->edge_off[e] / kChunk; c < P->edge_off[e + 1] / kChunk; ++c)
+            P->edge_chunk[c] = e;
         for (uint32_t c = P->tup_off[e] / kChunk; c < P->tup_off[e + 1] / kChunk; ++c)
             P->tup_chunk[c] = e;
     }
     for (size_t c = 0, e = 0; c < P->hit_chunk.size(); ++c) {
         const uint64_t g = (uint64_t)c * kHitChunk;
         while (e + 1 < E && g >= P->hit_off[e + 1]) ++e;
-        P->hit_chunk[c] = (uint32_t)e;
+        // bit 31: a later event starts inside this chunk
+        const bool straddle = e + 1 < E && P->hit_off[e + 1] < g + kHitChunk;
+        P->hit_chunk[c] = (uint32_t)e | (straddle ? 0x80000000u : 0u);
     }
     P->off = plan_layout(E, P->N, C, G, T, P->dp, with_inputs);
     return PXR_OK;
@@ -481,6 +491,7 @@ static cudaError_t stage_mark(cudaEvent_t ev, cudaStream_t s, bool capturing)
 static void fill_chunks(const pxr_plan *P, char *head)
 {
     std::memcpy(head + P->off.cell_chunk, P->cell_chunk.data(), 4 * P->cell_chunk.size());
+    std::memcpy(head + P->off.edge_chunk, P->edge_chunk.data(), 4 * P->edge_chunk.size());
     std::memcpy(head + P->off.tup_chunk, P->tup_chunk.data(), 4 * P->tup_chunk.size());
     std::memcpy(head + P->off.hit_chunk, P->hit_chunk.data(), 4 * P->hit_chunk.size());
 }
@@ -502,7 +513,7 @@ static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
     if (t) CK(stage_mark(P->ev_stage[2], s, capturing));
     launch_connect(b, p, (uint32_t)P->C, s, sms);
     if (t) CK(stage_mark(P->ev_stage[3], s, capturing));
-    launch_ntuplets(b, p, (uint32_t)P->C, s, sms);
+    launch_ntuplets(b, p, (uint32_t)P->G, s, sms);
     launch_select(b, p, (uint32_t)P->T, s, sms);
     launch_out_scan(b, s);
     if (t) CK(stage_mark(P->ev_stage[4], s, capturing));
@@ -657,7 +668,7 @@ extern "C" int pxr_plan_counts(pxr_plan *P, uint32_t *out)
     int rc = set_device(P->ctx);
     if (rc) return rc;
     CK(cudaEventSynchronize(P->ev_done));
-    CK(cudaMemcpy(out, P->db.cnt, 4 * (size_t)kCounters * P->E, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(out, P->db.cnt, 4 * (size_t)kReportedCounters * P->E, cudaMemcpyDeviceToHost));
     return PXR_OK;
 }
 
