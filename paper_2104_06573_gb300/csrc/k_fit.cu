@@ -25,6 +25,10 @@ template <typename T>
 __device__ __forceinline__ T sqrt_t(T v) { return sqrt(v); }
 template <>
 __device__ __forceinline__ float sqrt_t<float>(float v) { return sqrtf(v); }
+template <typename T>
+__device__ __forceinline__ T rsqrt_t(T v) { return rsqrt(v); }
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
 
 // Transcendentals in float (FT = true) or in the argument's own type.
 template <bool FT, typename T>
@@ -38,7 +42,8 @@ struct FitOut {
 };
 
 // Symmetric positive definite pentadiagonal matrix (diagonal d0, first and second
-// super-diagonals d1, d2) factored as L L^T in place (L's diagonal in d0, sub-diagonals in d1, d2).
+// super-diagonals d1, d2) factored as L L^T in place: d1, d2 receive L's sub-diagonals and d0
+// the reciprocals of L's diagonal (so the solves multiply instead of divide).
 template <int N, typename T>
 __device__ __forceinline__ bool band_factor(T (&d0)[N], T (&d1)[N], T (&d2)[N])
 {
@@ -48,21 +53,21 @@ __device__ __forceinline__ bool band_factor(T (&d0)[N], T (&d1)[N], T (&d2)[N])
         if (i >= 1) s -= d1[i - 1] * d1[i - 1];
         if (i >= 2) s -= d2[i - 2] * d2[i - 2];
         if (!(s > T(0))) return false;
-        const T l = sqrt_t(s);
-        d0[i] = l;
+        const T il = rsqrt_t(s);
+        d0[i] = il;
         if (i + 1 < N) {
             T t = d1[i];
             if (i >= 1) t -= d2[i - 1] * d1[i - 1];
-            d1[i] = t / l;
+            d1[i] = t * il;
         }
-        if (i + 2 < N) d2[i] = d2[i] / l;
+        if (i + 2 < N) d2[i] = d2[i] * il;
     }
     return true;
 }
 
-// Solve (L L^T) x = b with the factor of band_factor.
+// Solve (L L^T) x = b with the factor of band_factor (il: reciprocal diagonal).
 template <int N, typename T>
-__device__ __forceinline__ void band_solve(const T (&l0)[N], const T (&l1)[N], const T (&l2)[N],
+__device__ __forceinline__ void band_solve(const T (&il)[N], const T (&l1)[N], const T (&l2)[N],
                                            const T (&b)[N], T (&x)[N])
 {
     T y[N];
@@ -71,25 +76,25 @@ __device__ __forceinline__ void band_solve(const T (&l0)[N], const T (&l1)[N], c
         T t = b[i];
         if (i >= 1) t -= l1[i - 1] * y[i - 1];
         if (i >= 2) t -= l2[i - 2] * y[i - 2];
-        y[i] = t / l0[i];
+        y[i] = t * il[i];
     }
 #pragma unroll
     for (int i = N - 1; i >= 0; --i) {
         T t = y[i];
         if (i + 1 < N) t -= l1[i] * x[i + 1];
         if (i + 2 < N) t -= l2[i] * x[i + 2];
-        x[i] = t / l0[i];
+        x[i] = t * il[i];
     }
 }
 
-// Broken line over N points: measurements meas (weights w), kinks at the inner points with
-// variances kv, and (CURV) one curvature unknown.  Normal equations: a pentadiagonal block for
-// the offsets (each kink couples three neighbours) bordered by the curvature row; the border is
-// eliminated through the Schur complement.  Returns the offsets x, the curvature correction and
-// the chi2 at the minimum.
+// Broken line over N points: measurements meas (weights w), kinks at the inner points j with
+// weights wk[j] (reciprocal variances), and (CURV) one curvature unknown.  g[i] = 1/(s[i+1]-s[i])
+// and h[i] = s[i+1]-s[i].  Normal equations: a pentadiagonal block for the offsets (each kink
+// couples three neighbours) bordered by the curvature row; the border is eliminated through the
+// Schur complement.  Returns the offsets x, the curvature correction and the chi2 at the minimum.
 template <int N, bool CURV, typename T>
-__device__ __forceinline__ bool broken_line_n(const T (&s)[N], const T (&meas)[N],
-                                              const T (&w)[N], const T (&kv)[N], T (&x)[N],
+__device__ __forceinline__ bool broken_line_n(const T (&g)[N], const T (&h)[N], const T (&meas)[N],
+                                              const T (&w)[N], const T (&wk)[N], T (&x)[N],
                                               T &delta, T &chi2)
 {
     T d0[N], d1[N], d2[N], c[N], b[N];
@@ -104,21 +109,20 @@ __device__ __forceinline__ bool broken_line_n(const T (&s)[N], const T (&meas)[N
     }
 #pragma unroll
     for (int j = 1; j + 1 < N; ++j) {
-        const T ds0 = s[j] - s[j - 1], ds1 = s[j + 1] - s[j];
-        const T wk = T(1) / kv[j];
-        const T g0 = T(1) / ds0, g2 = T(1) / ds1, g1 = -g0 - g2;
-        d0[j - 1] += wk * g0 * g0;
-        d0[j] += wk * g1 * g1;
-        d0[j + 1] += wk * g2 * g2;
-        d1[j - 1] += wk * g0 * g1;
-        d1[j] += wk * g1 * g2;
-        d2[j - 1] += wk * g0 * g2;
+        const T g0 = g[j - 1], g2 = g[j], g1 = -g0 - g2;
+        const T k = wk[j];
+        d0[j - 1] += k * g0 * g0;
+        d0[j] += k * g1 * g1;
+        d0[j + 1] += k * g2 * g2;
+        d1[j - 1] += k * g0 * g1;
+        d1[j] += k * g1 * g2;
+        d2[j - 1] += k * g0 * g2;
         if (CURV) {
-            const T gd = T(0.5) * (ds0 + ds1);
-            c[j - 1] += wk * g0 * gd;
-            c[j] += wk * g1 * gd;
-            c[j + 1] += wk * g2 * gd;
-            dd += wk * gd * gd;
+            const T gd = T(0.5) * (h[j - 1] + h[j]);
+            c[j - 1] += k * g0 * gd;
+            c[j] += k * g1 * gd;
+            c[j + 1] += k * g2 * gd;
+            dd += k * gd * gd;
         }
     }
     if (!band_factor<N, T>(d0, d1, d2)) return false;
@@ -147,10 +151,9 @@ __device__ __forceinline__ bool broken_line_n(const T (&s)[N], const T (&meas)[N
     }
 #pragma unroll
     for (int j = 1; j + 1 < N; ++j) {
-        const T ds0 = s[j] - s[j - 1], ds1 = s[j + 1] - s[j];
-        T beta = (x[j + 1] - x[j]) / ds1 - (x[j] - x[j - 1]) / ds0;
-        if (CURV) beta += T(0.5) * (ds0 + ds1) * delta;
-        c2 += beta * beta / kv[j];
+        T beta = (x[j + 1] - x[j]) * g[j] - (x[j] - x[j - 1]) * g[j - 1];
+        if (CURV) beta += T(0.5) * (h[j - 1] + h[j]) * delta;
+        c2 += beta * beta * wk[j];
     }
     chi2 = c2;
     return true;
@@ -158,7 +161,9 @@ __device__ __forceinline__ bool broken_line_n(const T (&s)[N], const T (&meas)[N
 
 // TC: prefit + residuals + arc lengths; T: everything else (scattering, solves, conversion);
 // FT: float transcendentals (angles and logarithms need ~1e-7 relative, far inside the
-// tolerances).
+// tolerances).  Divisions and square roots are shared where the method allows (one reciprocal
+// per arc-length step, one scattering angle per surface type, reciprocal Cholesky pivots): they
+// are the costly operations of the double-precision path.
 template <int N, typename TC, typename T, bool FT>
 __device__ void fit_n(const float *X, const float *Y, const float *Z, const uint8_t *L,
                       const DevParams &p, FitOut &o)
@@ -173,7 +178,8 @@ __device__ void fit_n(const float *X, const float *Y, const float *Z, const uint
     const TC D = TC(2) * (ux * vy - uy * vx);
     if (D == TC(0)) { o.status = 1; return; }
     const TC uu = ux * ux + uy * uy, vv = vx * vx + vy * vy;
-    const TC Cx = (uu * vy - vv * uy) / D, Cy = (vv * ux - uu * vx) / D;
+    const TC iD = TC(1) / D;
+    const TC Cx = (uu * vy - vv * uy) * iD, Cy = (vv * ux - uu * vx) * iD;
     const TC R0 = sqrt_t(Cx * Cx + Cy * Cy);
     const TC sgn = D > TC(0) ? TC(1) : TC(-1);
 
@@ -188,54 +194,72 @@ __device__ void fit_n(const float *X, const float *Y, const float *Z, const uint
         s[i] = T(R0 * atan2_t<FT>(sgn * cr, dt));
         z[i] = T(Z[i]);
     }
-
-    // multiple scattering
-    const T cot0 = (z[ic] - z[0]) / (s[ic] - s[0]);
-    const T sec2 = T(1) + cot0 * cot0;
-    const T pmom = T(kKpt * p.bfield) * T(R0) * sqrt_t(sec2);
-    T kvT[N], kvL[N], wT[N], wL[N];
-    const T wrphi = T(1.0 / (p.sigma_rphi * p.sigma_rphi));
-    const T wz = T(1.0 / (p.sigma_z * p.sigma_z));
+    T g[N], h[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        kvT[i] = T(1);
-        kvL[i] = T(1);
-        wT[i] = wrphi;
-        if (p.is_disk[L[i]]) {
-            const T sz = T(p.sigma_z) * fabs(cot0);
-            wL[i] = T(1) / (sz * sz);
-        } else {
-            wL[i] = wz;
-        }
-    }
-#pragma unroll
-    for (int j = 1; j + 1 < N; ++j) {
-        const T path = p.is_disk[L[j]] ? sqrt_t(sec2) / fabs(cot0) : sqrt_t(sec2);
-        const T xx = T(p.x_over_x0) * path;
-        const T th0 = (T(0.0136) / pmom) * sqrt_t(xx) * (T(1) + T(0.038) * log_t<FT>(xx));
-        const T th2 = th0 * th0;
-        kvT[j] = th2 * sec2;
-        kvL[j] = th2 * sec2 * sec2;
-        if (!(kvT[j] > T(0)) || !(kvL[j] > T(0))) { o.status = 4; return; }
+        h[i] = i + 1 < N ? s[i + 1] - s[i] : T(1);
+        g[i] = T(1) / h[i];
     }
 
+    // multiple scattering: one Highland angle per surface type (barrel, disk)
+    const T cot0 = (z[ic] - z[0]) / (s[ic] - s[0]);
+    const T sec2 = T(1) + cot0 * cot0;
+    const T isec2 = T(1) / sec2;
+    const T sec = sqrt_t(sec2);
+    const T pmom = T(kKpt * p.bfield) * T(R0) * sec;
+    const T a0 = T(0.0136) / pmom;
+    const T wrphi = T(1.0 / (p.sigma_rphi * p.sigma_rphi));
+    const T wz = T(1.0 / (p.sigma_z * p.sigma_z));
+    bool any_disk = false;
+#pragma unroll
+    for (int i = 0; i < N; ++i) any_disk |= p.is_disk[L[i]] != 0;
+    // reciprocal squared scattering angle on a surface crossed with path factor `path`
+    auto inv_th2 = [&](T path) {
+        const T xx = T(p.x_over_x0) * path;
+        const T th0 = a0 * sqrt_t(xx) * (T(1) + T(0.038) * log_t<FT>(xx));
+        return T(1) / (th0 * th0);
+    };
+    const T ib2 = inv_th2(sec);
+    T id2 = ib2, wdisk = wz;
+    if (any_disk) {
+        const T icot = T(1) / fabs(cot0);
+        id2 = inv_th2(sec * icot);
+        const T iz = T(1.0 / p.sigma_z) * icot;   // disk: sigma_r = sigma_z |cot|
+        wdisk = iz * iz;
+    }
+    T wkT[N], wkL[N], wT[N], wL[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const bool dk = p.is_disk[L[i]] != 0;
+        wT[i] = wrphi;
+        wL[i] = dk ? wdisk : wz;
+        const T it2 = dk ? id2 : ib2;
+        wkT[i] = it2 * isec2;            // kink variance th0^2 (1 + cot^2)
+        wkL[i] = it2 * isec2 * isec2;    // kink variance th0^2 (1 + cot^2)^2
+    }
+    // a kink variance that is zero or not a number (a weight that is not finite) is bad input
+#pragma unroll
+    for (int j = 1; j + 1 < N; ++j)
+        if (!isfinite(wkT[j]) || !isfinite(wkL[j])) { o.status = 4; return; }
+
     T xT[N], xL[N], delta, dummy, chi2T, chi2L;
-    if (!broken_line_n<N, true, T>(s, yr, wT, kvT, xT, delta, chi2T) ||
-        !broken_line_n<N, false, T>(s, z, wL, kvL, xL, dummy, chi2L)) {
+    if (!broken_line_n<N, true, T>(g, h, yr, wT, wkT, xT, delta, chi2T) ||
+        !broken_line_n<N, false, T>(g, h, z, wL, wkL, xL, dummy, chi2L)) {
         o.status = 3;
         return;
     }
 
     // conversion to the point of closest approach
     const T R0s = T(R0);
-    const T kappa = T(1) / R0s + delta;
+    const T iR0 = T(1) / R0s;
+    const T kappa = iR0 + delta;
     if (kappa == T(0) || !isfinite(kappa)) { o.status = 2; return; }
     const T R = T(1) / fabs(kappa);
     const T sgs = T(sgn);
     const T sgf = kappa > T(0) ? sgs : -sgs;
-    const T ds0 = s[1] - s[0];
-    const T alpha = (xT[1] - xT[0]) / ds0 + T(0.5) * delta * ds0;
-    const T nx = -T(Cx) / R0s, ny = -T(Cy) / R0s;
+    const T ds0 = h[0];
+    const T alpha = (xT[1] - xT[0]) * g[0] + T(0.5) * delta * ds0;
+    const T nx = -T(Cx) * iR0, ny = -T(Cy) * iR0;
     const T tx = -sgs * ny, ty = sgs * nx;
     T ca, sa;
     if constexpr (FT) {
@@ -249,13 +273,16 @@ __device__ void fit_n(const float *X, const float *Y, const float *Z, const uint
     }
     const T n2x = nx * ca - tx * sa, n2y = ny * ca - ty * sa;
     const T P0x = xT[0] * nx, P0y = xT[0] * ny;
-    const T Fx = P0x - n2x / kappa, Fy = P0y - n2y / kappa;
+    const T rk = kappa > T(0) ? R : -R;                  // 1 / kappa
+    const T Fx = P0x - n2x * rk, Fy = P0y - n2y * rk;
     const T rx = (P0x - Fx) * fabs(kappa), ry = (P0y - Fy) * fabs(kappa);
     const T wx = -T(X[0]) - Fx, wy = -T(Y[0]) - Fy;
-    const T dist = sqrt_t(wx * wx + wy * wy);
-    const T ex = wx / dist, ey = wy / dist;
+    const T d2 = wx * wx + wy * wy;
+    const T idist = rsqrt_t(d2);
+    const T dist = d2 * idist;
+    const T ex = wx * idist, ey = wy * idist;
     const T tpx = -sgf * ey, tpy = sgf * ex;
-    const T cot = (xL[1] - xL[0]) / ds0;
+    const T cot = (xL[1] - xL[0]) * g[0];
     const T psi = atan2_t<FT>(sgf * (ex * ry - ey * rx), ex * rx + ey * ry);
     const int qf = sgf > T(0) ? -1 : 1;
     o.pt = double(T(kKpt * p.bfield) * R);
@@ -292,7 +319,7 @@ __device__ __forceinline__ void fit_dispatch(int n, const float *X, const float 
 
 // One thread per output track: the kept ntuplets are listed per event in output order, and the
 // number of outputs is read on the device, so no thread is spent on unused capacity.
-__global__ void __launch_bounds__(256) k_fit(DevBatch b, DevParams p)
+__global__ void __launch_bounds__(256, 2) k_fit(DevBatch b, DevParams p)
 {
     const uint32_t n_out = b.out_evt[b.E];
     for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < n_out;
