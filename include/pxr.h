@@ -119,7 +119,9 @@ typedef struct pxr_params {
     double x_over_x0;                          /* radiation lengths per layer, >= 1e-6 */
     uint32_t n_phi_bins;                       /* phi bins per layer, 64..2048; 0 = automatic */
     uint32_t max_cells_per_event;              /* 0 = sized from the hit counts; rounded up to a
-                                                  multiple of 256 */
+                                                  multiple of 256.  Counts doublet candidates
+                                                  (pairs inside the phi window), a superset of
+                                                  the cells */
     uint32_t max_tuples_per_event;             /* 0 = sized from the hit counts; rounded up to a
                                                   multiple of 256 */
 } pxr_params;
@@ -172,7 +174,8 @@ int pxr_params_check(const pxr_params *p);
 int pxr_create(const pxr_config *cfg, pxr_ctx **out);
 
 /* Stop the scheduler, wait for work in flight, release everything the context allocated.
- * Unfetched results are discarded. */
+ * Unfetched results are discarded; plans of the context that are still alive are destroyed
+ * (their handles become invalid). */
 void pxr_destroy(pxr_ctx *ctx);
 
 /*
@@ -242,6 +245,8 @@ int pxr_plan_counts(pxr_plan *plan, uint32_t *out);
  * doublets, CA connect, ntuplets + selection + output scan, fit; n = entries written (<= cap). */
 int pxr_plan_stage_ms(pxr_plan *plan, float *ms, int cap, int *n);
 
+/* Wait for the plan's last run and release it.  Call before pxr_destroy of its context (which
+ * otherwise destroys it). */
 void pxr_plan_destroy(pxr_plan *plan);
 
 /*

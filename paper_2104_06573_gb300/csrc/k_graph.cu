@@ -1,17 +1,18 @@
 // Doublets, CA cell connection, ntuplet walk and ntuplet selection.
 //
 // Doublets: one warp per (inner hit, layer pair).  The outer layer's phi window is one or two
-// contiguous runs of the sorted hits; the 32 lanes test 32 consecutive candidates per step
-// (coalesced float4 loads), a ballot records the passes, one atomic per (hit, pair) reserves the
-// cells, and the second sweep writes them from the ballot masks, so the cells of an inner hit are
-// contiguous (the CA stage reads them as one run per pair).
+// contiguous runs of the sorted hits; the item reserves one entry per candidate with one atomic,
+// the 32 lanes test 32 consecutive candidates per step (coalesced float4 loads) and write the
+// outer hit, or kNone where the cut fails, to the candidate's entry.  The entries of an inner
+// hit are contiguous (the CA stage reads them as one run per pair) and the cell (i, o) is found
+// from o's position in i's window without a search.
 //
 // CA connect: one warp per junction hit j.  j's out-cells (j, k) are staged in shared memory and
 // counting-sorted by the free coordinate of k (z on barrel layers, r on disks); each in-cell
 // (i, j), one per lane, tests only the bins reached by the cone of r-z directions within
 // asin(theta_cut) of its own, a conservative window in which the exact cuts decide.  Lanes with
-// passes find their cell's index by a warp-wide search of a narrow range and append their edge
-// lists through one atomic per warp.  Ntuplets: one warp per root hit walks the out-edges of its
+// passes compute their cell's index from j's rank in i's window and append their edge lists
+// through one atomic per warp.  Ntuplets: one warp per root hit walks the out-edges of its
 // cells depth first.  Selection removes suffix paths and assigns output slots.
 #include "pxr_dev.cuh"
 #include "pxr_cuts.cuh"
@@ -60,7 +61,9 @@ __device__ __forceinline__ bool doublet_test(const DevBatch &b, const DevParams 
                      p.cw);
 }
 
-__global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint32_t slots)
+// Compact form (allocation-free entry point): passing pairs only, counted first, then written
+// from the ballot masks, so the cells of an inner hit are contiguous.
+__global__ void __launch_bounds__(256) k_doublets_compact(DevBatch b, DevParams p, uint32_t slots)
 {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -148,7 +151,146 @@ __global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint3
     }
 }
 
+// Plan form: one warp per block of 32 consecutive items (inner hit, layer pair), one lane per
+// item.  The lanes find their items' windows together (one round of dependent loads for 32
+// items); the warp reserves one entry per candidate for all its items with one atomic per event
+// present (usually one).  The items are then taken one at a time, their data broadcast from the
+// owning lane: the lanes test 64 consecutive candidates per step (coalesced float4 loads, two in
+// flight per lane) and write the outer hit, or kNone where the cut fails, to the candidate's
+// entry.
+
+__global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint32_t slots)
+{
+    const uint32_t FULL = 0xFFFFFFFFu;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t n_items = (uint64_t)b.N * slots;
+    const uint64_t n_blocks = (n_items + 31) / 32;
+    const uint32_t nk = p.n_keys;
+    const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t blk = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; blk < n_blocks;
+         blk += stride) {
+        // ---- one item per lane: its window on the outer layer ----
+        const uint64_t item = blk * 32 + lane;
+        uint32_t g = 0, slot = 0, e = 0, nc = 0, r0 = 0, n1 = 0, r2 = 0, c_lo = 0, cap = 0;
+        float4 hi = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool valid = false;
+        if (item < n_items) {
+            g = (uint32_t)(item / slots);
+            slot = (uint32_t)(item % slots);
+            // independent loads first (hits past an event's valid range carry layer 0xFF)
+            const uint32_t meta = b.hmeta[g];
+            hi = b.hs[g];
+            const float phig = b.hphi[g];
+            e = hit_event(b, g);
+            const uint32_t L = meta >> kLocalBits;
+            valid = L < p.n_layers && slot < p.n_out[L];
+            if (valid) {
+                c_lo = b.cell_off[e];
+                cap = b.cell_off[e + 1] - c_lo;
+                const Window w = phi_window(b.bkt + (size_t)e * (nk + 1), p.out_layer[L][slot],
+                                            phig, p);
+                r0 = w.r0;
+                n1 = w.n1;
+                r2 = w.r2;
+                nc = w.size();
+            }
+        }
+        // ---- reservation: one atomic per event among the lanes ----
+        uint32_t excl = nc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, excl, o);
+            if (lane >= (uint32_t)o) excl += t;
+        }
+        const uint32_t total = __shfl_sync(FULL, excl, 31);
+        excl -= nc;
+        uint32_t base = 0;
+        for (uint32_t rem = __ballot_sync(FULL, nc > 0); rem;) {
+            const int h = __ffs(rem) - 1;
+            const uint32_t eh = __shfl_sync(FULL, e, h);
+            const uint32_t seg = __ballot_sync(FULL, nc > 0 && e == eh);
+            const uint32_t v = (seg >> lane) & 1u ? nc : 0u;
+            uint32_t sc = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(FULL, sc, o);
+                if (lane >= (uint32_t)o) sc += t;
+            }
+            const uint32_t stot = __shfl_sync(FULL, sc, 31);
+            uint32_t sb = 0;
+            if (lane == (uint32_t)h) sb = atomicAdd(&b.cnt[C_SLOTS * b.E + eh], stot);
+            sb = __shfl_sync(FULL, sb, h);
+            if ((seg >> lane) & 1u) base = sb + sc - v;
+            rem &= ~seg;
+        }
+        const uint32_t nw = base >= cap ? 0u : min(nc, cap - base);
+        const uint32_t first = c_lo + base;
+        if (valid) {
+            if (nw < nc) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_CELLS);
+            const size_t oi = (size_t)g * kMaxOut + slot;
+            b.out_first[oi] = first;
+            b.out_n[oi] = nw;
+            b.out_r0[oi] = r0;
+            b.out_d2[oi] = n1 - r2;
+        }
+        // ---- candidates, item by item (the item's data broadcast once), 64 per step ----
+        uint32_t npass = 0;
+        for (uint32_t has = __ballot_sync(FULL, nw > 0); has; has &= has - 1) {
+            const int k = __ffs(has) - 1;
+            const uint32_t gk = __shfl_sync(FULL, g, k);
+            const float4 hk = make_float4(__shfl_sync(FULL, hi.x, k), __shfl_sync(FULL, hi.y, k),
+                                          0.f, __shfl_sync(FULL, hi.w, k));
+            const uint32_t a0 = __shfl_sync(FULL, r0, k), a1 = __shfl_sync(FULL, n1, k);
+            const uint32_t a2 = __shfl_sync(FULL, r2, k);
+            const uint32_t fk = __shfl_sync(FULL, first, k), wk = __shfl_sync(FULL, nw, k);
+            uint32_t np = 0;
+            for (uint32_t c0 = 0; c0 < wk; c0 += 64) {
+                const uint32_t ca = c0 + lane, cb = ca + 32u;
+                const uint32_t oa = ca < a1 ? a0 + ca : a2 + (ca - a1);
+                const uint32_t ob = cb < a1 ? a0 + cb : a2 + (cb - a1);
+                const float4 ha = ca < wk ? __ldg(&b.hs[oa]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 hb = cb < wk ? __ldg(&b.hs[ob]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (ca < wk) {
+                    const bool pass = doublet_test(b, p, gk, hk, oa, ha);
+                    b.cell_in[fk + ca] = gk;
+                    b.cell_out[fk + ca] = pass ? oa : kNone;
+                    np += pass;
+                }
+                if (cb < wk) {
+                    const bool pass = doublet_test(b, p, gk, hk, ob, hb);
+                    b.cell_in[fk + cb] = gk;
+                    b.cell_out[fk + cb] = pass ? ob : kNone;
+                    np += pass;
+                }
+            }
+            const uint32_t tot = __reduce_add_sync(FULL, np);
+            if (lane == (uint32_t)k) npass = tot;
+        }
+        // real cells per event: each item's count sits in its own lane
+        for (uint32_t rem = __ballot_sync(FULL, npass > 0); rem;) {
+            const int h = __ffs(rem) - 1;
+            const uint32_t eh = __shfl_sync(FULL, e, h);
+            const uint32_t seg = __ballot_sync(FULL, npass > 0 && e == eh);
+            const uint32_t tot = __reduce_add_sync(FULL, (seg >> lane) & 1u ? npass : 0u);
+            if (lane == (uint32_t)h) atomicAdd(&b.cnt[C_CELLS * b.E + eh], tot);
+            rem &= ~seg;
+        }
+    }
+}
+
 void launch_doublets(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms)
+{
+    uint32_t slots = 1;
+    for (uint32_t l = 0; l < p.n_layers; ++l) slots = p.n_out[l] > slots ? p.n_out[l] : slots;
+    const uint64_t warps = ((uint64_t)b.N * slots + 31) / 32;     // one warp per 32 items
+    uint64_t blocks = (warps + 7) / 8;
+    const uint64_t cap = (uint64_t)sms * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) return;
+    k_doublets<<<(unsigned)blocks, 256, 0, s>>>(b, p, slots);
+}
+
+void launch_doublets_compact(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms)
 {
     uint32_t slots = 1;
     for (uint32_t l = 0; l < p.n_layers; ++l) slots = p.n_out[l] > slots ? p.n_out[l] : slots;
@@ -157,7 +299,7 @@ void launch_doublets(const DevBatch &b, const DevParams &p, cudaStream_t s, int 
     uint64_t cap = (uint64_t)sms * 16;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
-    k_doublets<<<(unsigned)blocks, 256, 0, s>>>(b, p, slots);
+    k_doublets_compact<<<(unsigned)blocks, 256, 0, s>>>(b, p, slots);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -233,42 +375,15 @@ __device__ __forceinline__ int ford(float f)
 }
 __device__ __forceinline__ float funord(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
 
-// Search range of the cell (i, j) in i's cell list toward layer Lj.  The list [f, f + n) holds
-// i's passing candidates on Lj in candidate order (phi window, run 1 then run 2); with c the rank
-// of j among the nc candidates, at most nc - n candidates failed, so the cell's offset lies in
-// [c - (nc - n), c].  Returns that range and the whole list.
-__device__ __forceinline__ void cell_range(const DevBatch &b, const DevParams &p,
-                                           const uint32_t *bk, uint32_t i, uint32_t slot,
-                                           uint32_t Lj, uint32_t j, uint32_t &lo, uint32_t &hi,
-                                           uint32_t &flo, uint32_t &fhi)
-{
-    const uint32_t f = b.out_first[(size_t)i * kMaxOut + slot];
-    const uint32_t n = b.out_n[(size_t)i * kMaxOut + slot];
-    const Window w = phi_window(bk, Lj, b.hphi[i], p);
-    const uint32_t nc = w.size();
-    flo = f;
-    fhi = f + n;
-    const bool in1 = j >= w.r0 && j < w.r0 + w.n1, in2 = j >= w.r2 && j < w.r2 + w.n2;
-    if (n == 0 || !(in1 || in2) || n > nc) {
-        lo = flo;
-        hi = fhi;
-        return;
-    }
-    const uint32_t c = in1 ? j - w.r0 : w.n1 + (j - w.r2);
-    const uint32_t rej = nc - n;
-    lo = f + (c > rej ? c - rej : 0u);
-    hi = f + (c < n - 1 ? c : n - 1) + 1u;
-}
-
 // One warp per junction hit j.  For each out-layer slot, j's out-cells (j, k) are staged in
 // shared memory (k's coordinates) and counting-sorted by the free coordinate of k (z on barrel
 // layers, r on disks) into local bins over the staged range.  The in-cells (i, j) are found 32
 // at a time, one per lane, by scanning i over j's phi window on the inner layer with the doublet
 // cut; each lane computes the cone of r-z directions that can pass the alignment cut, the bins it
-// reaches (a conservative window: the exact cuts decide) and tests those out-cells itself.  Lanes
-// with passes locate their in-cell's index with warp-wide coalesced searches and append their
-// edges through one atomic per warp.  A slot with more than kStage out-cells is tested against all
-// of them from global memory.  Loads that do not depend on one another are issued together (the
+// reaches (a conservative window: the exact cuts decide) and tests those out-cells itself (j's
+// entries of failed candidates are skipped).  The in-cell's index is j's rank in i's window
+// (loaded alongside the tests); lanes with passes append their edges through one atomic per
+// warp.  A slot with more than kStage entries is tested from global memory.  Loads that do not depend on one another are issued together (the
 // junction's own records, its first out-cell list and inner window) so that a junction waits on
 // few memory round trips.
 __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevParams p)
@@ -307,10 +422,17 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
             }
             if (nB == 0) continue;
             const bool staged = nB <= (uint32_t)kStage;
+            // candidates of an in-cell are positions [q0, q1) of the bin-sorted passing entries
+            // (staged) or of j's entries (not staged, failed candidates skipped); nq of them
+            uint32_t nq = nB;
             float flo = 0.f, fhi = 0.f, dlo = 0.f, dhi = 0.f, scale = 0.f;
             if (staged) {
                 int m0 = ford(3.0e38f), m1 = ford(-3.0e38f), m2 = m0, m3 = m1;
-                auto take = [&](uint32_t t, float4 hk) {
+                auto take = [&](uint32_t t, uint32_t k, float4 hk) {
+                    if (k == kNone) {                       // candidate that failed the cut
+                        sH[t] = make_float4(__int_as_float(0x7FC00000), 0.f, 0.f, 0.f);
+                        return;
+                    }
                     const float fc = disk ? hk.w : hk.z, xc = disk ? hk.z : hk.w;
                     sH[t] = hk;
                     m0 = min(m0, ford(fc));
@@ -322,10 +444,10 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                     const uint32_t ta = t0 + lane, tb = ta + 32u;
                     const uint32_t ka = ta < nB ? b.cell_out[f0 + ta] : 0u;
                     const uint32_t kb = tb < nB ? b.cell_out[f0 + tb] : 0u;
-                    const float4 ha = ta < nB ? b.hs[ka] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const float4 hb = tb < nB ? b.hs[kb] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (ta < nB) take(ta, ha);
-                    if (tb < nB) take(tb, hb);
+                    const float4 ha = ta < nB && ka != kNone ? b.hs[ka] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 hb = tb < nB && kb != kNone ? b.hs[kb] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (ta < nB) take(ta, ka, ha);
+                    if (tb < nB) take(tb, kb, hb);
                 }
                 m0 = __reduce_min_sync(0xFFFFFFFFu, m0);
                 m1 = __reduce_max_sync(0xFFFFFFFFu, m1);
@@ -345,7 +467,9 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                     const int bb = (int)floorf(((disk ? hk.w : hk.z) - flo) * scale);
                     return bb < 0 ? 0u : (bb >= kBins ? (uint32_t)kBins - 1u : (uint32_t)bb);
                 };
-                for (uint32_t t = lane; t < nB; t += 32) atomicAdd(&bin[local_bin(t)], 1u);
+                // (entries of failed candidates carry x = NaN and are left out)
+                for (uint32_t t = lane; t < nB; t += 32)
+                    if (!isnan(sH[t].x)) atomicAdd(&bin[local_bin(t)], 1u);
                 __syncwarp();
                 {
                     constexpr int per = kBins / 32;      // consecutive bins per lane
@@ -365,9 +489,10 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                     __syncwarp();
                 }
                 for (uint32_t t = lane; t < nB; t += 32)
-                    sT[atomicAdd(&bin[local_bin(t)], 1u)] = (uint16_t)t;
+                    if (!isnan(sH[t].x)) sT[atomicAdd(&bin[local_bin(t)], 1u)] = (uint16_t)t;
                 __syncwarp();
                 // bin[t] is now the end of bin t; the start of bin t is bin[t - 1] (0 for t = 0)
+                nq = bin[kBins - 1];
             }
             for (uint32_t si = 0; si < nin; ++si) {
                 const uint32_t Li = p.in_layer[Lj][si];
@@ -385,7 +510,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                         hi = b.hs[i];
                         if (doublet_test(b, p, i, hi, j, hj)) {
                             a = rz32(hi, hj);
-                            q1 = nB;
+                            q1 = nq;
                             float lo, hi_;
                             if (staged && cone_window(a.ar, a.az, disk ? hj.w : hj.z, dlo, dhi,
                                                       disk, p.tan_win, lo, hi_)) {
@@ -402,6 +527,18 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                             }
                         }
                     }
+                    // ---- index of the in-cell (i, j): i's entry of rank(j) in its window ----
+                    uint32_t A = kNone, kA = kNone;
+                    if (q1 > q0) {
+                        const size_t it = (size_t)i * kMaxOut + slot_i;
+                        const uint32_t af = b.out_first[it], an = b.out_n[it];
+                        const uint32_t r0 = b.out_r0[it], d2 = b.out_d2[it];
+                        const uint32_t rank = j >= r0 ? j - r0 : j + d2;
+                        if (rank < an) {
+                            A = af + rank;
+                            kA = b.cell_out[A];                 // checked after the tests
+                        }
+                    }
                     // ---- each lane tests its own candidates ----
                     uint32_t npass = 0, qf = 0, Bf = 0;
                     for (uint32_t q = q0; q < q1; ++q) {
@@ -413,7 +550,9 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                             hk = sH[t];
                         } else {
                             B = f0 + q;
-                            hk = b.hs[b.cell_out[B]];
+                            const uint32_t k = b.cell_out[B];
+                            if (k == kNone) continue;
+                            hk = b.hs[k];
                         }
                         if (triplet_test(b, p, i, j, B, hi.x, hi.y, hj, hk, a)) {
                             if (npass == 0) { qf = q; Bf = B; }
@@ -422,27 +561,10 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                     }
                     const uint32_t pm = __ballot_sync(0xFFFFFFFFu, npass > 0);
                     if (pm == 0) continue;
-                    // ---- index of each passing lane's in-cell (i, j) ----
-                    uint32_t lo = 0, hi_ = 0, flo_ = 0, fhi_ = 0;
-                    if (npass) cell_range(b, p, bk, i, slot_i, Lj, j, lo, hi_, flo_, fhi_);
-                    uint32_t A = kNone;
-                    for (uint32_t m = pm; m; m &= m - 1) {
-                        const int L = __ffs(m) - 1;
-                        const uint32_t r0 = __shfl_sync(0xFFFFFFFFu, lo, L);
-                        const uint32_t r1 = __shfl_sync(0xFFFFFFFFu, hi_, L);
-                        const uint32_t g0 = __shfl_sync(0xFFFFFFFFu, flo_, L);
-                        const uint32_t g1 = __shfl_sync(0xFFFFFFFFu, fhi_, L);
-                        uint32_t found = kNone;
-                        for (int pass = 0; pass < 2 && found == kNone; ++pass) {
-                            const uint32_t s0 = pass ? g0 : r0, s1 = pass ? g1 : r1;
-                            for (uint32_t q = s0; q < s1; q += 32) {
-                                const bool hit = q + lane < s1 && b.cell_out[q + lane] == j;
-                                const uint32_t bm = __ballot_sync(0xFFFFFFFFu, hit);
-                                if (bm) { found = q + (uint32_t)(__ffs(bm) - 1); break; }
-                            }
-                        }
-                        if (lane == (uint32_t)L) A = found;
-                    }
+                    // the entry holds j unless the in-cell was dropped by a capacity overflow
+                    // (rank beyond the written entries); any other mismatch is flagged
+                    if (npass && A != kNone && kA != j) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_CELLS);
+                    if (kA != j) A = kNone;
                     // ---- append the edges: one atomic per warp reserves all lanes' lists ----
                     const bool ok = npass && A != kNone;   // kNone: the cell was dropped (overflow)
                     uint32_t have = 0, old = 0;
@@ -488,7 +610,9 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                                 hk = sH[t];
                             } else {
                                 B = f0 + q;
-                                hk = b.hs[b.cell_out[B]];
+                                const uint32_t k = b.cell_out[B];
+                                if (k == kNone) continue;
+                                hk = b.hs[k];
                             }
                             if (triplet_test(b, p, i, j, B, hi.x, hi.y, hj, hk, a))
                                 b.nbr[first + wr++] = B;
@@ -582,7 +706,8 @@ __global__ void __launch_bounds__(256) k_ntuplets(DevBatch b, DevParams p)
         for (uint32_t s = 0; s < p.n_out[L]; ++s) {
             const uint32_t f = s ? b.out_first[(size_t)g * kMaxOut + s] : f_0;
             const uint32_t n = s ? b.out_n[(size_t)g * kMaxOut + s] : n_0;
-            for (uint32_t c = lane; c < n; c += 32) walk_from(b, p, e, f + c);
+            for (uint32_t c = lane; c < n; c += 32)
+                if (b.cell_out[f + c] != kNone) walk_from(b, p, e, f + c);
         }
     }
 }

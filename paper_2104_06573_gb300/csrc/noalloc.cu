@@ -157,7 +157,7 @@ extern "C" int pxr_doublets_noalloc(const float *x, const float *y, const float 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     k_na_init<<<1, 32, 0, s>>>(n_hits, cap);
     launch_sort(b, dp, s, sms);
-    launch_doublets(b, dp, s, sms);
+    launch_doublets_compact(b, dp, s, sms);
     k_na_to_caller<<<sms * 4, 256, 0, s>>>(cells_inner, cells_outer, n_cells, cap);
     k_na_count<<<1, 32, 0, s>>>(n_cells, flags);
     cudaError_t e = cudaGetLastError();

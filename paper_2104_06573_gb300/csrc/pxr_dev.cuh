@@ -26,8 +26,8 @@ constexpr uint32_t kHitChunk = 32;   // granularity of the hit -> event table
 // Per-event counters, laid out as kCounters consecutive arrays of E words.
 enum Counter : int {
     C_CELLS = 0, C_EDGES = 1, C_TUPLES = 2, C_FLAGS = 3, C_OUT = 4,   // reported per event
-    C_ROOTS = 5,                                                       // internal
-    kCounters = 6
+    C_ROOTS = 5, C_SLOTS = 6,                                          // internal
+    kCounters = 7
 };
 constexpr int kReportedCounters = 5;
 
@@ -81,10 +81,16 @@ struct DevBatch {
     // event of a work chunk: cells, edges and ntuplets by 256-entry chunk; hits by 32-hit chunk
     // (first event of the chunk, bit 31 set when the chunk holds the start of a later event)
     const uint32_t *cell_chunk, *edge_chunk, *tup_chunk, *hit_chunk;
-    // cells, grouped by (inner hit, pair slot)
-    uint32_t *out_first;                // [N * kMaxOut] first cell of (inner hit, slot)
-    uint32_t *out_n;                    // [N * kMaxOut] number of cells
-    uint32_t *cell_in, *cell_out;       // [cells] sorted hit positions
+    // cells, grouped by (inner hit, pair slot).  The plan path keeps one entry per candidate of
+    // the inner hit's phi window on the outer layer, in window order (run 1, then run 2), with
+    // cell_out = kNone where the doublet cut failed: the cell (i, o) sits at out_first + rank,
+    // rank = o - out_r0 for o >= out_r0 (run 1) and o + out_d2 otherwise (run 2; unsigned
+    // arithmetic).  The allocation-free entry point writes passing pairs only.
+    uint32_t *out_first;                // [N * kMaxOut] first entry of (inner hit, slot)
+    uint32_t *out_n;                    // [N * kMaxOut] number of entries
+    uint32_t *out_r0;                   // [N * kMaxOut] first position of window run 1
+    uint32_t *out_d2;                   // [N * kMaxOut] (run 1 length) - (first position of run 2)
+    uint32_t *cell_in, *cell_out;       // [entries] sorted hit positions
     // CA graph: out-edges of each cell
     uint32_t *nbr_first;                // [cells]
     uint32_t *nbr_n;                    // [cells]
@@ -137,6 +143,7 @@ void launch_sort(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms)
 void launch_layer_count(const uint32_t *hit_off, const uint16_t *layer, uint32_t E,
                         uint32_t n_layers, uint32_t *counts, cudaStream_t s, int sms);
 void launch_doublets(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms);
+void launch_doublets_compact(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms);
 void launch_connect(const DevBatch &b, const DevParams &p, uint32_t cell_total, cudaStream_t s,
                     int sms);
 void launch_ntuplets(const DevBatch &b, const DevParams &p, uint32_t edge_total, cudaStream_t s,

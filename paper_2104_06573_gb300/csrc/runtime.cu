@@ -16,6 +16,7 @@
 #include <string>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/pxr.h"
@@ -210,7 +211,7 @@ struct PlanOffsets {
     size_t x, y, z, layer, hit_off, cell_off, edge_off, tup_off, cell_chunk, edge_chunk, tup_chunk,
         hit_chunk,
         head_end;
-    size_t cnt, bkt, hs, r64, hmeta, hphi, out_first, out_n, cell_in, cell_out,
+    size_t cnt, bkt, hs, r64, hmeta, hphi, out_first, out_n, out_r0, out_d2, cell_in, cell_out,
         nbr_first,
         nbr_n, nbr, mindepth, root_list, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, out_evt, o_nh,
         o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status;
@@ -245,6 +246,8 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
 
     o.out_first = L.add(4 * N * kMaxOut);
     o.out_n = L.add(4 * N * kMaxOut);
+    o.out_r0 = L.add(4 * N * kMaxOut);
+    o.out_d2 = L.add(4 * N * kMaxOut);
     o.cell_in = L.add(4 * C);
     o.cell_out = L.add(4 * C);
     o.nbr_first = L.add(4 * C);
@@ -341,6 +344,8 @@ struct pxr_ctx {
     bool own_arena = false;
     Arena arena;
     std::mutex api_mu;                  // serialises plan API calls
+    std::mutex plans_mu;
+    std::unordered_set<pxr_plan *> plans;   // live plans, destroyed with the context
     // serving
     std::mutex mu;
     std::condition_variable cv_sched, cv_done;
@@ -407,6 +412,8 @@ static void plan_bind(pxr_plan *P)
 
     b.out_first = (uint32_t *)(r + o.out_first);
     b.out_n = (uint32_t *)(r + o.out_n);
+    b.out_r0 = (uint32_t *)(r + o.out_r0);
+    b.out_d2 = (uint32_t *)(r + o.out_d2);
     b.cell_in = (uint32_t *)(r + o.cell_in);
     b.cell_out = (uint32_t *)(r + o.cell_out);
     b.nbr_first = (uint32_t *)(r + o.nbr_first);
@@ -638,6 +645,10 @@ extern "C" int pxr_plan_create(pxr_ctx *ctx, uint32_t n_events, const uint32_t *
         cudaGraphDestroy(g);
         CK(ce);
     }
+    {
+        std::lock_guard<std::mutex> g(ctx->plans_mu);
+        ctx->plans.insert(P.get());
+    }
     *out = P.release();
     return PXR_OK;
 }
@@ -690,6 +701,10 @@ extern "C" int pxr_plan_stage_ms(pxr_plan *P, float *ms, int cap, int *n)
 extern "C" void pxr_plan_destroy(pxr_plan *P)
 {
     if (!P) return;
+    {
+        std::lock_guard<std::mutex> g(P->ctx->plans_mu);
+        P->ctx->plans.erase(P);
+    }
     if (P->has_run) cudaEventSynchronize(P->ev_done);
     plan_free(P);
 }
@@ -826,13 +841,14 @@ static int region_debug(pxr_plan *P, uint32_t e, int what, uint32_t *buf, uint32
     if ((rc = d2h(meta, b.hmeta + h0, nh))) return rc;
     auto loc = [&](uint32_t pos) { return meta[pos - h0] & kLocalMask; };
     const uint32_t c0 = P->cell_off[e];
-    const uint32_t nc = std::min(cnt[C_CELLS], P->cell_off[e + 1] - c0);
+    const uint32_t nc = std::min(cnt[C_SLOTS], P->cell_off[e + 1] - c0);   // slots, holes included
     std::vector<uint32_t> out;
     if (what == 0 || what == 1) {
         std::vector<uint32_t> ci, co;
         if ((rc = d2h(ci, b.cell_in + c0, nc)) || (rc = d2h(co, b.cell_out + c0, nc))) return rc;
         if (what == 0) {
             for (uint32_t c = 0; c < nc; ++c) {
+                if (co[c] == kNone) continue;                   // candidate that failed the cut
                 out.push_back(loc(ci[c]));
                 out.push_back(loc(co[c]));
             }
@@ -1243,6 +1259,15 @@ extern "C" void pxr_destroy(pxr_ctx *ctx)
     }
     if (ctx->sched.joinable()) ctx->sched.join();
     cudaSetDevice(ctx->cfg.device);
+    {
+        // plans the caller did not destroy go with the context (their memory is in its arena)
+        std::lock_guard<std::mutex> g(ctx->plans_mu);
+        for (pxr_plan *P : ctx->plans) {
+            if (P->has_run) cudaEventSynchronize(P->ev_done);
+            plan_free(P);
+        }
+        ctx->plans.clear();
+    }
     ctx->tickets.clear();
     ctx->inflight.clear();
     for (auto &s : ctx->slot_stream)

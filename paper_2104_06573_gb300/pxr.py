@@ -365,7 +365,8 @@ class Plan:
 
     def close(self):
         if self.h:
-            load().pxr_plan_destroy(self.h)
+            if self.ctx.h:                 # a closed context has destroyed its plans already
+                load().pxr_plan_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -175,10 +175,11 @@ def test_overflow_is_flagged_not_written(ctx):
     P = synth.params_barrel_quadruplets()
     ev = ev_tuple(synth.event_barrel(0))
     ok = ev_tuple(synth.event_barrel(1))
-    # capacities are whole 256-cell chunks: 50 becomes 256, still below the ~770 cells
+    # capacities are whole 256-entry chunks: 50 becomes 256, still below the ~770 cells (each
+    # entry holds a window candidate, so at most 256 of the event's cells are kept)
     got = run_plan(ctx, [ev, ok], P, pxr.CUT_FP32, max_cells=50)
     assert got[0]["tracks"]["status"] == pxr.EOVERFLOW
-    assert len(got[0]["cells"]) == 256
+    assert 0 < len(got[0]["cells"]) <= 256
     full = run_plan(ctx, [ok], P, pxr.CUT_FP32)[0]
     assert got[1]["tracks"]["status"] == pxr.EOVERFLOW     # also too small for event 1
     assert len(full["cells"]) > 256
