@@ -267,7 +267,7 @@ int pxr_fit_batch(pxr_ctx *ctx, uint32_t m, const uint8_t *nh, const float *x, c
  * other streams) and applications whose device memory is owned entirely by their own pool.
  * It runs the hit sort and the doublet stage of the other entry points (same cells, same
  * arithmetic) with all scratch in one fixed array in device global memory that the library
- * holds on every GPU that loads it (about 4.5 MB) until the process exits; it calls no
+ * holds on every GPU that loads it (about 6.4 MB) until the process exits; it calls no
  * cudaMalloc, cudaFree or allocating library routine.
  *
  * Inputs (device): x, y, z, layer of n_hits hits (n_hits <= 65536).  Outputs (device):

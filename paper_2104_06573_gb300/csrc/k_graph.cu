@@ -115,8 +115,7 @@ __global__ void __launch_bounds__(256) k_doublets_compact(DevBatch b, DevParams 
         else if (base + count > cap) nw = cap - base;
         if (lane == 0) {
             if (nw < count) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_CELLS);
-            b.out_first[(size_t)g * kMaxOut + slot] = c_lo + base;
-            b.out_n[(size_t)g * kMaxOut + slot] = nw;
+            b.item[(size_t)g * kMaxOut + slot] = make_uint4(c_lo + base, nw, 0u, 0u);
         }
         if (nw == 0) continue;
         const uint32_t first = c_lo + base;
@@ -228,10 +227,7 @@ __global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint3
         if (valid) {
             if (nw < nc) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_CELLS);
             const size_t oi = (size_t)g * kMaxOut + slot;
-            b.out_first[oi] = first;
-            b.out_n[oi] = nw;
-            b.out_r0[oi] = r0;
-            b.out_d2[oi] = n1 - r2;
+            b.item[oi] = make_uint4(first, nw, r0, n1 - r2);
         }
         // ---- candidates, item by item (the item's data broadcast once), 64 per step ----
         uint32_t npass = 0;
@@ -405,8 +401,8 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
         const float4 hj = b.hs[j];
         const float phij = b.hphi[j];
         const uint32_t e = hit_event(b, j);
-        uint32_t f0 = b.out_first[(size_t)j * kMaxOut];
-        uint32_t nB = b.out_n[(size_t)j * kMaxOut];
+        const uint4 it0 = b.item[(size_t)j * kMaxOut];
+        uint32_t f0 = it0.x, nB = it0.y;
         const uint32_t Lj = meta >> kLocalBits;
         if (Lj >= p.n_layers) continue;
         const uint32_t nin = p.n_in[Lj], nout = p.n_out[Lj];
@@ -417,8 +413,9 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
             const uint32_t Lk = p.out_layer[Lj][s];
             const bool disk = p.is_disk[Lk];
             if (s) {
-                f0 = b.out_first[(size_t)j * kMaxOut + s];
-                nB = b.out_n[(size_t)j * kMaxOut + s];
+                const uint4 its = b.item[(size_t)j * kMaxOut + s];
+                f0 = its.x;
+                nB = its.y;
             }
             if (nB == 0) continue;
             const bool staged = nB <= (uint32_t)kStage;
@@ -503,11 +500,13 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                     // ---- one in-cell candidate per lane ----
                     const uint32_t c = c0 + lane;
                     uint32_t i = 0, q0 = 0, q1 = 0;
+                    uint4 itm = make_uint4(0u, 0u, 0u, 0u);
                     float4 hi = make_float4(0.f, 0.f, 0.f, 0.f);
                     RZ32 a{0.f, 0.f, 0.f, 0.f};
                     if (c < nc) {
                         i = w.pos(c);
                         hi = b.hs[i];
+                        itm = b.item[(size_t)i * kMaxOut + slot_i];   // with hs[i]: one round trip
                         if (doublet_test(b, p, i, hi, j, hj)) {
                             a = rz32(hi, hj);
                             q1 = nq;
@@ -530,12 +529,9 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                     // ---- index of the in-cell (i, j): i's entry of rank(j) in its window ----
                     uint32_t A = kNone, kA = kNone;
                     if (q1 > q0) {
-                        const size_t it = (size_t)i * kMaxOut + slot_i;
-                        const uint32_t af = b.out_first[it], an = b.out_n[it];
-                        const uint32_t r0 = b.out_r0[it], d2 = b.out_d2[it];
-                        const uint32_t rank = j >= r0 ? j - r0 : j + d2;
-                        if (rank < an) {
-                            A = af + rank;
+                        const uint32_t rank = j >= itm.z ? j - itm.z : j + itm.w;
+                        if (rank < itm.y) {
+                            A = itm.x + rank;
                             kA = b.cell_out[A];                 // checked after the tests
                         }
                     }
@@ -700,12 +696,11 @@ __global__ void __launch_bounds__(256) k_ntuplets(DevBatch b, DevParams p)
         // independent loads first (hits past an event's valid range carry layer 0xFF)
         const uint32_t L = b.hmeta[g] >> kLocalBits;
         const uint32_t e = hit_event(b, g);
-        const uint32_t f_0 = b.out_first[(size_t)g * kMaxOut];
-        const uint32_t n_0 = b.out_n[(size_t)g * kMaxOut];
+        const uint4 it0 = b.item[(size_t)g * kMaxOut];
         if (L >= p.n_layers || !((p.root_mask >> L) & 1u)) continue;
         for (uint32_t s = 0; s < p.n_out[L]; ++s) {
-            const uint32_t f = s ? b.out_first[(size_t)g * kMaxOut + s] : f_0;
-            const uint32_t n = s ? b.out_n[(size_t)g * kMaxOut + s] : n_0;
+            const uint4 its = s ? b.item[(size_t)g * kMaxOut + s] : it0;
+            const uint32_t f = its.x, n = its.y;
             for (uint32_t c = lane; c < n; c += 32)
                 if (b.cell_out[f + c] != kNone) walk_from(b, p, e, f + c);
         }

@@ -32,11 +32,10 @@ constexpr size_t kNaBkt = na_align(kNaCnt + 4 * kCounters);             // (keys
 constexpr size_t kNaHs = na_align(kNaBkt + 4 * (kNaMaxKeys + 1));       // hits x float4
 constexpr size_t kNaR64 = na_align(kNaHs + 16 * (size_t)kNaMaxHits);     // hits x double
 constexpr size_t kNaMeta = na_align(kNaR64 + 8 * (size_t)kNaMaxHits);    // hits x u32
-constexpr size_t kNaFirst = na_align(kNaMeta + 4 * (size_t)kNaMaxHits);  // hits x 4 x u32
-constexpr size_t kNaN = na_align(kNaFirst + 16 * (size_t)kNaMaxHits);    // hits x 4 x u32
-constexpr size_t kNaPhi = na_align(kNaN + 16 * (size_t)kNaMaxHits);      // hits x float
+constexpr size_t kNaItem = na_align(kNaMeta + 4 * (size_t)kNaMaxHits);   // hits x 4 x uint4
+constexpr size_t kNaPhi = na_align(kNaItem + 64 * (size_t)kNaMaxHits);    // hits x float
 constexpr size_t kNaHitChunk = na_align(kNaPhi + 4 * (size_t)kNaMaxHits); // hit chunks x u32
-constexpr size_t kNaBytes = na_align(kNaHitChunk + 4 * (size_t)(kNaMaxHits / kHitChunk));  // ~4.5 MB
+constexpr size_t kNaBytes = na_align(kNaHitChunk + 4 * (size_t)(kNaMaxHits / kHitChunk));  // ~6.4 MB
 
 static __device__ __align__(256) unsigned char g_scratch[kNaBytes];
 
@@ -147,8 +146,7 @@ extern "C" int pxr_doublets_noalloc(const float *x, const float *y, const float 
     b.hs = reinterpret_cast<float4 *>(base + kNaHs);
     b.r64 = reinterpret_cast<double *>(base + kNaR64);
     b.hmeta = reinterpret_cast<uint32_t *>(base + kNaMeta);
-    b.out_first = reinterpret_cast<uint32_t *>(base + kNaFirst);
-    b.out_n = reinterpret_cast<uint32_t *>(base + kNaN);
+    b.item = reinterpret_cast<uint4 *>(base + kNaItem);
     b.cell_in = cells_inner;
     b.cell_out = cells_outer;
     b.hphi = reinterpret_cast<float *>(base + kNaPhi);

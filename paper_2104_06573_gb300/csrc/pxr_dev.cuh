@@ -83,13 +83,11 @@ struct DevBatch {
     const uint32_t *cell_chunk, *edge_chunk, *tup_chunk, *hit_chunk;
     // cells, grouped by (inner hit, pair slot).  The plan path keeps one entry per candidate of
     // the inner hit's phi window on the outer layer, in window order (run 1, then run 2), with
-    // cell_out = kNone where the doublet cut failed: the cell (i, o) sits at out_first + rank,
-    // rank = o - out_r0 for o >= out_r0 (run 1) and o + out_d2 otherwise (run 2; unsigned
-    // arithmetic).  The allocation-free entry point writes passing pairs only.
-    uint32_t *out_first;                // [N * kMaxOut] first entry of (inner hit, slot)
-    uint32_t *out_n;                    // [N * kMaxOut] number of entries
-    uint32_t *out_r0;                   // [N * kMaxOut] first position of window run 1
-    uint32_t *out_d2;                   // [N * kMaxOut] (run 1 length) - (first position of run 2)
+    // cell_out = kNone where the doublet cut failed.  item[(i, slot)] = (first entry, entries,
+    // r0, d2): the cell (i, o) sits at first + rank, rank = o - r0 for o >= r0 (window run 1)
+    // and o + d2 otherwise (run 2; unsigned arithmetic, d2 = run-1 length - run-2 start).  The
+    // allocation-free entry point writes passing pairs only (z, w unused).
+    uint4 *item;                        // [N * kMaxOut]
     uint32_t *cell_in, *cell_out;       // [entries] sorted hit positions
     // CA graph: out-edges of each cell
     uint32_t *nbr_first;                // [cells]

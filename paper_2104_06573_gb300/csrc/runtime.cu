@@ -211,7 +211,7 @@ struct PlanOffsets {
     size_t x, y, z, layer, hit_off, cell_off, edge_off, tup_off, cell_chunk, edge_chunk, tup_chunk,
         hit_chunk,
         head_end;
-    size_t cnt, bkt, hs, r64, hmeta, hphi, out_first, out_n, out_r0, out_d2, cell_in, cell_out,
+    size_t cnt, bkt, hs, r64, hmeta, hphi, item, cell_in, cell_out,
         nbr_first,
         nbr_n, nbr, mindepth, root_list, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, out_evt, o_nh,
         o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status;
@@ -244,10 +244,7 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.hmeta = L.add(4 * N);
     o.hphi = L.add(4 * N);
 
-    o.out_first = L.add(4 * N * kMaxOut);
-    o.out_n = L.add(4 * N * kMaxOut);
-    o.out_r0 = L.add(4 * N * kMaxOut);
-    o.out_d2 = L.add(4 * N * kMaxOut);
+    o.item = L.add(16 * N * kMaxOut);
     o.cell_in = L.add(4 * C);
     o.cell_out = L.add(4 * C);
     o.nbr_first = L.add(4 * C);
@@ -410,10 +407,7 @@ static void plan_bind(pxr_plan *P)
     b.tup_chunk = (const uint32_t *)(r + o.tup_chunk);
     b.hit_chunk = (const uint32_t *)(r + o.hit_chunk);
 
-    b.out_first = (uint32_t *)(r + o.out_first);
-    b.out_n = (uint32_t *)(r + o.out_n);
-    b.out_r0 = (uint32_t *)(r + o.out_r0);
-    b.out_d2 = (uint32_t *)(r + o.out_d2);
+    b.item = (uint4 *)(r + o.item);
     b.cell_in = (uint32_t *)(r + o.cell_in);
     b.cell_out = (uint32_t *)(r + o.cell_out);
     b.nbr_first = (uint32_t *)(r + o.nbr_first);
