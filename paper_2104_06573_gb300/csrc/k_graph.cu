@@ -50,6 +50,14 @@ __device__ __forceinline__ Window phi_window(const uint32_t *__restrict__ bk, ui
     return w;
 }
 
+// FP64 decision of the doublet cut (every call in FP64 mode, the guard band in FP32 mode), kept
+// out of line so that its double-precision registers do not weigh on the callers' hot loops.
+__device__ __noinline__ bool doublet_exact(const double *r64, uint32_t g, uint32_t o, float xi,
+                                           float yi, float xo, float yo, double cw)
+{
+    return doublet64((double)xi, (double)yi, r64[g], (double)xo, (double)yo, r64[o], cw);
+}
+
 __device__ __forceinline__ bool doublet_test(const DevBatch &b, const DevParams &p, uint32_t g,
                                              float4 hi, uint32_t o, float4 ho)
 {
@@ -57,8 +65,7 @@ __device__ __forceinline__ bool doublet_test(const DevBatch &b, const DevParams 
         int r = doublet32(hi, ho, p.cw32);
         if (r >= 0) return r == 1;
     }
-    return doublet64((double)hi.x, (double)hi.y, b.r64[g], (double)ho.x, (double)ho.y, b.r64[o],
-                     p.cw);
+    return doublet_exact(b.r64, g, o, hi.x, hi.y, ho.x, ho.y, p.cw);
 }
 
 // Compact form (allocation-free entry point): passing pairs only, counted first, then written
@@ -301,33 +308,42 @@ void launch_doublets_compact(const DevBatch &b, const DevParams &p, cudaStream_t
 // ------------------------------------------------------------------------------------------
 // CA connect
 // ------------------------------------------------------------------------------------------
+// FP64 part of the triplet cut, out of line (see doublet_exact): the r-z alignment in FP64 when
+// need_theta, then the DCA, decided by the FP32 result dc (1 pass, 0 fail) or else in FP64.
+__device__ __noinline__ bool triplet_exact(const double *r64, const uint32_t *cell_out,
+                                           const float4 *hs, uint32_t i, uint32_t j, uint32_t B,
+                                           float xi, float yi, float4 hj, float4 hk,
+                                           bool need_theta, int dc, double theta, double dca)
+{
+    if (need_theta) {
+        const uint32_t k = cell_out[B];
+        const double zi = (double)hs[i].z, zj = (double)hj.z, zk = (double)hk.z;
+        const double ri = r64[i], rj = r64[j], rk = r64[k];
+        const double nA = seglen64(ri, zi, rj, zj);
+        const double nB = seglen64(rj, zj, rk, zk);
+        if (!theta64(ri, zi, rj, zj, rk, zk, nA, nB, theta)) return false;
+    }
+    if (dc >= 0) return dc == 1;
+    return dca64((double)xi, (double)yi, (double)hj.x, (double)hj.y, (double)hk.x,
+                 (double)hk.y) <= dca;
+}
+
 // Exact decision for the triplet (i, j, k), k the outer hit of the out-cell B = (j, k):
-// r-z alignment, then DCA.  FP32 mode decides in float when outside the guard band and falls
-// back to the FP64 formulas otherwise (the FP64 inputs are loaded only on that path).
+// r-z alignment, then DCA.  FP32 mode decides in float when outside the guard bands and takes
+// the FP64 formulas otherwise (FP64 mode always).
 __device__ __forceinline__ bool triplet_test(const DevBatch &b, const DevParams &p, uint32_t i,
                                              uint32_t j, uint32_t B, float xi, float yi,
                                              float4 hj, float4 hk, const RZ32 &a)
 {
-    bool exact_theta = p.cut_mode == CUT_FP64;
-    if (!exact_theta) {
-        const int r = theta32(a, rz32(hj, hk), p.theta32);
-        if (r == 0) return false;
-        exact_theta = r < 0;
-    }
-    if (exact_theta) {
-        const uint32_t k = b.cell_out[B];
-        const double zi = (double)b.hs[i].z, zj = (double)hj.z, zk = (double)hk.z;
-        const double ri = b.r64[i], rj = b.r64[j], rk = b.r64[k];
-        const double nA = seglen64(ri, zi, rj, zj);
-        const double nB = seglen64(rj, zj, rk, zk);
-        if (!theta64(ri, zi, rj, zj, rk, zk, nA, nB, p.theta)) return false;
-    }
+    int th = -1, dc = -1;
     if (p.cut_mode == CUT_FP32) {
-        const int r = dca32(xi, yi, hj.x, hj.y, hk.x, hk.y, p.dca32);
-        if (r >= 0) return r == 1;
+        th = theta32(a, rz32(hj, hk), p.theta32);
+        if (th == 0) return false;
+        dc = dca32(xi, yi, hj.x, hj.y, hk.x, hk.y, p.dca32);
+        if (th == 1 && dc >= 0) return dc == 1;
     }
-    return dca64((double)xi, (double)yi, (double)hj.x, (double)hj.y, (double)hk.x,
-                 (double)hk.y) <= p.dca;
+    return triplet_exact(b.r64, b.cell_out, b.hs, i, j, B, xi, yi, hj, hk, th < 0, dc, p.theta,
+                         p.dca);
 }
 
 // Conservative interval of the free coordinate (z on a barrel layer, r on a disk) reachable from
