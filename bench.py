@@ -38,10 +38,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pxr", choices=["pxr", "reference"])
     ap.add_argument("--cut", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--fit", default="fp64", choices=["fp64", "mixed", "fp32"])
+    ap.add_argument("--fit", default="mixed", choices=["fp64", "mixed", "fp32"])
     ap.add_argument("--events", type=int, default=256)
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/serving/cpu legs")
     ap.add_argument("--serve-rate", type=float, default=5000.0)
+    ap.add_argument("--no-tune", action="store_true", help="built-in bin count and grid sizes")
+    ap.add_argument("--tune-cache", default=os.path.join(os.path.expanduser("~"), ".cache", "pxr",
+                                                         "tune.json"))
     return ap.parse_args()
 
 
@@ -236,8 +239,16 @@ def run_pxr(args, rank, world, local):
     stream = torch.cuda.Stream(device=dev)
     ctx = pxr.Context(device=local, mem_budget_bytes=budget, arena=arena,
                       stream=stream.cuda_stream)
-    plan = pxr.Plan(ctx, off, x, y, z, layer, params, use_graph=True)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    tuning = None
+    if not args.no_tune:
+        # phi-bin count and per-stage grid sizes picked on this batch (outside the timed region)
+        from paper_2104_06573_gb300 import autotune
+        with torch.cuda.stream(stream):
+            params, tuning = autotune.tune_plan(ctx, off, x, y, z, layer, params, stream=stream,
+                                                cache=args.tune_cache, flush=flush.zero_)
+        torch.cuda.synchronize()
+    plan = pxr.Plan(ctx, off, x, y, z, layer, params, use_graph=True)
 
     def step_events(n):
         return [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -293,7 +304,8 @@ def run_pxr(args, rank, world, local):
             "dtype": f"cuts {args.cut}, fit {args.fit}", "data": "synthetic",
             "config": {"workload": WORKLOAD, "events_per_step": args.events * world,
                        "hits_per_step": n_hits * world, "l2": "flushed (512 MB write) between steps",
-                       "launch": "captured CUDA graph, inputs resident"},
+                       "launch": "captured CUDA graph, inputs resident",
+                       "tuning": tuning and {k: tuning[k] for k in ("n_phi_bins", "grid_per_sm")}},
             "gpu_launches": plan.pxr_plan_launches() * args.steps,
             "stage_ms": dict(zip(["sort", "doublets", "connect", "ntuplets+select",
                                   "fit+output"], [round(v, 4) for v in stage])),

@@ -72,6 +72,15 @@ extern "C" {
 #define PXR_PRESET_PHASE1 1 /* barrel + 3 disks per side (ids 4-6 at +z, 7-9 at -z), 13 pairs,
                                roots {0,1} with suffix removal, 3..5 hits */
 
+/* Stages whose grid size is tunable (index into pxr_params.grid_per_sm). */
+#define PXR_STAGES 6
+#define PXR_STAGE_SORT 0
+#define PXR_STAGE_DOUBLETS 1
+#define PXR_STAGE_CONNECT 2
+#define PXR_STAGE_WALK 3
+#define PXR_STAGE_SELECT 4
+#define PXR_STAGE_FIT 5
+
 /*
  * Reconstruction parameters.  All fields are inputs; pxr_params_init fills a preset.
  *
@@ -124,6 +133,10 @@ typedef struct pxr_params {
                                                   the cells */
     uint32_t max_tuples_per_event;             /* 0 = sized from the hit counts; rounded up to a
                                                   multiple of 256 */
+    uint32_t grid_per_sm[PXR_STAGES];          /* launch shape: CTAs per SM at most for the
+                                                  stage's grid (PXR_STAGE_*), 1..64; 0 = the
+                                                  built-in value.  Results do not depend on it;
+                                                  pxr's autotuner picks it with the bin count */
 } pxr_params;
 
 /* Context configuration. */

@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(256, 2) k_fit(DevBatch b, DevParams p)
 void launch_fit(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
 {
     uint64_t blocks = ((uint64_t)total + 255) / 256;
-    uint64_t cap = (uint64_t)sms * 8;
+    uint64_t cap = (uint64_t)sms * p.grid_per_sm[5];
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
     k_fit<<<(unsigned)blocks, 256, 0, s>>>(b, p);

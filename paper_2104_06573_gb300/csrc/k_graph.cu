@@ -287,7 +287,7 @@ void launch_doublets(const DevBatch &b, const DevParams &p, cudaStream_t s, int 
     for (uint32_t l = 0; l < p.n_layers; ++l) slots = p.n_out[l] > slots ? p.n_out[l] : slots;
     const uint64_t warps = ((uint64_t)b.N * slots + 31) / 32;     // one warp per 32 items
     uint64_t blocks = (warps + 7) / 8;
-    const uint64_t cap = (uint64_t)sms * 16;
+    const uint64_t cap = (uint64_t)sms * p.grid_per_sm[1];
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
     k_doublets<<<(unsigned)blocks, 256, 0, s>>>(b, p, slots);
@@ -643,7 +643,7 @@ void launch_connect(const DevBatch &b, const DevParams &p, uint32_t total, cudaS
 {
     (void)total;
     uint64_t blocks = ((uint64_t)b.N + kConnWarps - 1) / kConnWarps;
-    uint64_t cap = (uint64_t)sms * 16;
+    uint64_t cap = (uint64_t)sms * p.grid_per_sm[2];
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
     k_connect<<<(unsigned)blocks, kConnWarps * 32, 0, s>>>(b, p);
@@ -742,13 +742,13 @@ void launch_ntuplets(const DevBatch &b, const DevParams &p, uint32_t edge_total,
 {
     if (p.min_hits > 2) {
         const uint32_t chunks = edge_total / kChunk;
-        const uint32_t cap = (uint32_t)sms * 8;
+        const uint32_t cap = (uint32_t)sms * p.grid_per_sm[3];
         if (chunks == 0) return;
         k_walk_roots<<<chunks < cap ? chunks : cap, kChunk, 0, s>>>(b, p, edge_total);
         return;
     }
     uint64_t blocks = ((uint64_t)b.N + 7) / 8;
-    uint64_t cap = (uint64_t)sms * 16;
+    uint64_t cap = (uint64_t)sms * 2 * p.grid_per_sm[3];
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
     k_ntuplets<<<(unsigned)blocks, 256, 0, s>>>(b, p);
@@ -781,7 +781,7 @@ __global__ void __launch_bounds__(256) k_select(DevBatch b, DevParams p, uint32_
 void launch_select(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
 {
     uint64_t blocks = total / kChunk;
-    uint64_t cap = (uint64_t)sms * 16;
+    uint64_t cap = (uint64_t)sms * 2 * p.grid_per_sm[4];
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
     k_select<<<(unsigned)blocks, 256, 0, s>>>(b, p, total);

@@ -111,7 +111,8 @@ cudaError_t init_kernels()
 
 void launch_sort(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms)
 {
-    uint32_t grid = b.E < (uint32_t)(sms * 4) ? b.E : (uint32_t)(sms * 4);
+    const uint32_t cap = (uint32_t)sms * p.grid_per_sm[0];
+    const uint32_t grid = b.E < cap ? b.E : cap;
     if (grid == 0) return;
     k_sort<<<grid, 512, p.n_keys * sizeof(uint32_t), s>>>(b, p);
 }

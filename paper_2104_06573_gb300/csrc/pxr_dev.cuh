@@ -57,6 +57,7 @@ struct DevParams {
     float theta32;                      // theta_cut rounded to float
     float dca32;                        // dca_cut rounded to float
     float tan_win;                      // tan(asin(theta_cut) + margin); inf when theta_cut >= 1
+    uint32_t grid_per_sm[6];            // CTAs per SM at most, per stage (sort ... fit)
     double cw;                          // cos(w) as given by the caller
     double theta, dca;
     double bfield, sigma_rphi, sigma_z, x_over_x0;

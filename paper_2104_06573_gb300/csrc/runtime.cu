@@ -117,6 +117,8 @@ static int check_params(const pxr_params *p, DevParams *d)
         return fail(PXR_EINVAL, "cuts, field, errors and material must be positive and finite");
     if (p->n_phi_bins && (p->n_phi_bins < 64 || p->n_phi_bins > 2048))
         return fail(PXR_EINVAL, "n_phi_bins must be 0 or in [64, 2048]");
+    for (int k = 0; k < PXR_STAGES; ++k)
+        if (p->grid_per_sm[k] > 64) return fail(PXR_EINVAL, "grid_per_sm must be in [0, 64]");
     if (!d) return PXR_OK;
     std::memset(d, 0, sizeof(*d));
     d->n_layers = p->n_layers;
@@ -156,6 +158,10 @@ static int check_params(const pxr_params *p, DevParams *d)
     d->sigma_rphi = p->sigma_rphi;
     d->sigma_z = p->sigma_z;
     d->x_over_x0 = p->x_over_x0;
+    // launch shapes: CTAs per SM at most (the kernels stride over their work)
+    static const uint32_t kGridDefault[PXR_STAGES] = {4, 16, 16, 8, 8, 8};
+    for (int k = 0; k < PXR_STAGES; ++k)
+        d->grid_per_sm[k] = p->grid_per_sm[k] ? p->grid_per_sm[k] : kGridDefault[k];
     return PXR_OK;
 }
 
@@ -172,16 +178,18 @@ struct EventCaps {
     uint32_t cells, edges, tuples;
 };
 
-static EventCaps event_caps(const pxr_params &p, const uint32_t *lcount, uint32_t n)
+static EventCaps event_caps(const pxr_params &p, uint32_t nb, const uint32_t *lcount, uint32_t n)
 {
-    // Uniform azimuths give n_i n_o (2w / 2pi) cells per pair; 30 % head room plus a per-hit
-    // floor covers fluctuations.  Edges: measured ~2-3 % of cells on the synthetic workloads.
+    // Cell entries are the candidates of the inner hits' bin windows: with uniform azimuths a
+    // pair has n_i n_o f of them, f = (2 w + one bin) / 2pi (the whole bins that cover an
+    // interval exceed it by one bin width on average); 30 % head room plus a per-hit floor
+    // covers fluctuations.  Edges: measured ~2-3 % of cells on the synthetic workloads.
     double pairs = 0.0, inner = 0.0;
     for (uint32_t k = 0; k < p.n_pairs; ++k) {
         pairs += (double)lcount[p.pair_inner[k]] * (double)lcount[p.pair_outer[k]];
         inner += lcount[p.pair_inner[k]];
     }
-    double f = std::min(1.0, 2.0 * p.phi_window / (2.0 * M_PI));
+    double f = std::min(1.0, (2.0 * (p.phi_window + 2e-5) + 2.0 * M_PI / nb) / (2.0 * M_PI));
     double cells = p.max_cells_per_event ? (double)p.max_cells_per_event
                                          : std::ceil(1.3 * f * pairs) + 4.0 * inner + 256.0;
     cells = std::min(cells, 1.0e9);
@@ -445,7 +453,7 @@ static int plan_size(pxr_plan *P, const uint32_t *lcount, bool with_inputs)
     uint64_t C = 0, G = 0, T = 0;
     for (uint32_t e = 0; e < E; ++e) {
         uint32_t n = P->hit_off[e + 1] - P->hit_off[e];
-        EventCaps c = event_caps(P->params, lcount + (size_t)e * (kMaxLayers + 1), n);
+        EventCaps c = event_caps(P->params, P->dp.nb, lcount + (size_t)e * (kMaxLayers + 1), n);
         C += c.cells;
         G += c.edges;
         T += c.tuples;
@@ -977,7 +985,7 @@ struct SlotBuffers {
 static size_t event_bytes(const pxr_params &p, const DevParams &dp, const uint32_t *lcount,
                           uint32_t n)
 {
-    EventCaps c = event_caps(p, lcount, n);
+    EventCaps c = event_caps(p, dp.nb, lcount, n);
     PlanOffsets o = plan_layout(1, n, c.cells, c.edges, c.tuples, dp, true);
     return o.total + 64 * 256;  // alignment slack of the shared batch layout
 }

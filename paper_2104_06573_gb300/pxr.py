@@ -42,7 +42,8 @@ class pxr_params(C.Structure):
                 ("theta_cut", C.c_double), ("dca_cut", C.c_double), ("bfield", C.c_double),
                 ("sigma_rphi", C.c_double), ("sigma_z", C.c_double),
                 ("x_over_x0", C.c_double), ("n_phi_bins", C.c_uint32),
-                ("max_cells_per_event", C.c_uint32), ("max_tuples_per_event", C.c_uint32)]
+                ("max_cells_per_event", C.c_uint32), ("max_tuples_per_event", C.c_uint32),
+                ("grid_per_sm", C.c_uint32 * 6)]
 
 
 class pxr_config(C.Structure):
@@ -141,10 +142,14 @@ def ptr(x):
 
 
 # -- parameters ------------------------------------------------------------------------------
+STAGES = ("sort", "doublets", "connect", "walk", "select", "fit")   # PXR_STAGE_* order
+
+
 def params_from(p, cut_mode=CUT_FP64, fit_mode=FIT_FP64, n_phi_bins=0, max_cells=0,
-                max_tuples=0) -> pxr_params:
+                max_tuples=0, grid_per_sm=None) -> pxr_params:
     """Marshal any object with the workload fields (n_layers, layer_is_disk, pairs, root_mask,
-    drop_suffixes, min_hits, max_hits, phi_window, cos_phi_window, cuts, field, errors)."""
+    drop_suffixes, min_hits, max_hits, phi_window, cos_phi_window, cuts, field, errors).
+    grid_per_sm: optional CTAs-per-SM caps per stage (STAGES order; 0 = built-in)."""
     o = pxr_params()
     o.n_layers = p.n_layers
     for i, v in enumerate(p.layer_is_disk):
@@ -162,6 +167,8 @@ def params_from(p, cut_mode=CUT_FP64, fit_mode=FIT_FP64, n_phi_bins=0, max_cells
     o.bfield, o.sigma_rphi, o.sigma_z, o.x_over_x0 = p.bfield, p.sigma_rphi, p.sigma_z, p.x_over_x0
     o.n_phi_bins = n_phi_bins
     o.max_cells_per_event, o.max_tuples_per_event = max_cells, max_tuples
+    for k, v in enumerate(grid_per_sm or ()):
+        o.grid_per_sm[k] = int(v)
     return o
 
 
