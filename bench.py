@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/serving/cpu legs")
     ap.add_argument("--serve-rate", type=float, default=5000.0)
     ap.add_argument("--no-tune", action="store_true", help="built-in bin count and grid sizes")
+    ap.add_argument("--bins", type=int, default=0, help="phi bins per layer (skips tuning)")
+    ap.add_argument("--grid", default="", help="CTAs per SM per stage, 6 comma-separated values "
+                    "(sort,doublets,connect,walk,select,fit; skips tuning)")
     ap.add_argument("--tune-cache", default=os.path.join(os.path.expanduser("~"), ".cache", "pxr",
                                                          "tune.json"))
     return ap.parse_args()
@@ -181,9 +184,10 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def doublet_traffic(cells):
+def doublet_traffic(cells, n_phi_bins):
     """DRAM bytes of one k_doublets launch from the committed ncu capture (scaled by cells, the
-    units the launch processes), or None when the kernel source changed since the capture."""
+    units the launch processes), or None when the kernel source or the bin count (which sets the
+    candidates per cell) differs from the capture's."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "k_doublets_traffic.json")))
@@ -191,6 +195,8 @@ def doublet_traffic(cells):
         a = src.index("__global__ void __launch_bounds__(256) k_doublets(")
         b = src.index("void launch_doublets(")
         if hashlib.sha256(src[a:b].encode()).hexdigest()[:16] != rec["source_sha16"]:
+            return None
+        if int(rec.get("n_phi_bins", -1)) != int(n_phi_bins):
             return None
         return rec["dram_bytes_per_cell"] * cells
     except (OSError, ValueError, KeyError):
@@ -241,7 +247,12 @@ def run_pxr(args, rank, world, local):
                       stream=stream.cuda_stream)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     tuning = None
-    if not args.no_tune:
+    if args.bins or args.grid:
+        grid = [int(v) for v in args.grid.split(",")] if args.grid else [0] * 6
+        from paper_2104_06573_gb300 import autotune
+        params = autotune._with(params, args.bins or 0, grid)
+        tuning = {"n_phi_bins": args.bins, "grid_per_sm": grid}
+    elif not args.no_tune:
         # phi-bin count and per-stage grid sizes picked on this batch (outside the timed region)
         from paper_2104_06573_gb300 import autotune
         with torch.cuda.stream(stream):
@@ -311,7 +322,8 @@ def run_pxr(args, rank, world, local):
                                   "fit+output"], [round(v, 4) for v in stage])),
             "roofline": {"kernel": "k_doublets", "bound": "hbm", "achieved": achieved,
                          "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                         "peak_source": peak_src, "traffic": doublet_traffic(cells),
+                         "peak_source": peak_src,
+                         "traffic": doublet_traffic(cells, params.n_phi_bins),
                          "algorithmic_bytes": alg, "cells": cells},
             "clocks": clk, "tracks_per_step": n_tracks * world}
 
