@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/serving/cpu legs")
     ap.add_argument("--serve-rate", type=float, default=5000.0)
     ap.add_argument("--no-tune", action="store_true", help="built-in bin count and grid sizes")
+    ap.add_argument("--study", action="store_true",
+                    help="measure every workload configuration (one JSON document, not the "
+                         "benchmark line)")
+    ap.add_argument("--fit-n", type=int, default=1_000_000, help="ntuplets of the fit study")
     ap.add_argument("--bins", type=int, default=0, help="phi bins per layer (skips tuning)")
     ap.add_argument("--grid", default="", help="CTAs per SM per stage, 6 comma-separated values "
                     "(sort,doublets,connect,walk,select,fit; skips tuning)")
@@ -385,34 +389,12 @@ def extras(args, ctx, pxr, synth, P, params, evs, off, x, y, z, layer, dev, stre
                       "d2h_bytes_per_step": int(d2h),
                       "how": "pxr_submit_event x256 (host arrays) + pxr_poll + pxr_fetch_tracks"}
 
-        # Poisson arrivals: latency submit -> fetchable
-        rate = args.serve_rate
-        n_req = int(min(6000, max(500, rate * 1.5)))
-        arr, tcount = synth.serving_stream(rate, n_req, seed=1)
-        pool = [synth.event_serving(1000 + k, int(tcount[k])) for k in range(64)]
-        t_sub, t_done = {}, {}
-        start = time.perf_counter()
-        k = 0
-        pending = 0
-        while k < n_req or pending:
-            now = time.perf_counter() - start
-            while k < n_req and arr[k] <= now:
-                e = pool[k % len(pool)]
-                t = sctx.try_submit_event(e.x, e.y, e.z, e.layer, params)
-                if t is None:
-                    break
-                t_sub[t] = time.perf_counter()
-                k += 1
-                pending += 1
-            for t in sctx.pxr_poll(timeout_us=50 if k < n_req else 20000):
-                t_done[t] = time.perf_counter()
-                sctx.pxr_fetch_tracks(t)
-                pending -= 1
-        lat = np.array([t_done[t] - t_sub[t] for t in t_sub]) * 1e3
-        span = max(t_done.values()) - min(t_sub.values())
-        out["serving"] = {"rate_hz": rate, "events": n_req, "p50_ms": float(np.percentile(lat, 50)),
-                          "p99_ms": float(np.percentile(lat, 99)), "events_per_s": n_req / span,
-                          "tracks": "lognormal median 1500, sigma 0.8, cap 8000; smeared barrel"}
+    # Poisson arrivals, latency from arrival to fetchable, 8 GB budget, continuous batching
+    rate = args.serve_rate
+    sv = _serve(pxr, synth, params, dev, rate, int(min(6000, max(1000, rate * 1.5))), 8 << 30,
+                256)
+    sv["tracks"] = "lognormal median 1500, sigma 0.8, cap 8000; smeared barrel"
+    out["serving"] = sv
 
     # host-core oracle on a bounded sample of the same workload
     cores = os.cpu_count() or 1
@@ -424,11 +406,193 @@ def extras(args, ctx, pxr, synth, P, params, evs, off, x, y, z, layer, dev, stre
     return out
 
 
+# ---------------------------------------------------------------------------------------------
+# study: every workload configuration of the method, one JSON document (bench.py --study)
+# ---------------------------------------------------------------------------------------------
+def _gpu_event_rate(pxr, ctx, ev, params, dev, stream, reps):
+    """Events/s of one event through a plan without a graph (the plain path), inputs resident."""
+    import torch
+    x, y, z = (torch.from_numpy(getattr(ev, k)).to(dev) for k in "xyz")
+    layer = torch.from_numpy(ev.layer.view(np.int16)).to(dev)
+    plan = pxr.Plan(ctx, [0, ev.n], x, y, z, layer, params, use_graph=False)
+    for _ in range(5):
+        plan.pxr_plan_run(stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        plan.pxr_plan_run(stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    rate = reps / (a.elapsed_time(b) / 1e3)
+    tracks = plan.pxr_plan_tracks(0)
+    debug = {w: plan.pxr_plan_debug(0, w) for w in (0, 1)}
+    plan.close()
+    return rate, tracks, debug
+
+
+def _oracle_rate(oracle, ev, P, min_s=1.0):
+    n, t0 = 0, time.perf_counter()
+    while True:
+        r = oracle.reconstruct(ev.x, ev.y, ev.z, ev.layer, P)
+        n += 1
+        if time.perf_counter() - t0 >= min_s:
+            return n / (time.perf_counter() - t0), r
+
+
+def _set_mismatches(ref, tracks, debug):
+    cells = {tuple(map(int, c)) for c in ref["cells"]}
+    cl = ref["cells"]
+    edges = {(int(cl[a, 0]), int(cl[a, 1]), int(cl[b, 1])) for a, b in ref["edges"]}
+    tup = {tuple(int(h) for h in row[:n]) for row, n in zip(ref["tuples"], ref["tuple_n"])}
+    g_cells = {tuple(map(int, c)) for c in debug[0]}
+    g_edges = {tuple(map(int, c)) for c in debug[1]}
+    g_tup = {tuple(int(h) for h in row[:n]) for row, n in zip(tracks["hit_idx"],
+                                                                tracks["n_hits"])}
+    return {"cells": len(cells ^ g_cells), "edges": len(edges ^ g_edges),
+            "ntuplets": len(tup ^ g_tup), "n_cells": len(cells), "n_edges": len(edges),
+            "n_ntuplets": len(tup)}
+
+
+def _fit_errors(h, f, ok):
+    d = {}
+    rel = lambda a, b, floor: np.abs(a - b) / np.maximum(floor, np.abs(b))
+    dphi = np.abs((h["phi"][ok] - f["phi"][ok] + np.pi) % (2 * np.pi) - np.pi)
+    errs = {"pt": rel(h["pt"][ok], f["pt"][ok], 0.0), "phi": dphi,
+            "cot_theta": rel(h["cot_theta"][ok], f["cot_theta"][ok], 1.0),
+            "dxy": np.abs(h["dxy"][ok] - f["dxy"][ok]),
+            "dz": rel(h["dz"][ok], f["dz"][ok], 0.1)}
+    for k, v in errs.items():
+        d[k] = {"max": float(v.max()), "p99": float(np.percentile(v, 99))}
+    return d
+
+
+def _serve(pxr, synth, params, dev, rate, n_req, budget, max_batch_events):
+    """Poisson arrivals; latency from arrival to fetchable (time spent waiting for admission
+    counts)."""
+    arr, tcount = synth.serving_stream(rate, n_req, seed=1)
+    pool = [synth.event_serving(1000 + k, int(tcount[k])) for k in range(64)]
+    with pxr.Context(device=dev.index, mem_budget_bytes=budget,
+                     max_batch_events=max_batch_events) as sctx:
+        # warm-up
+        for e in pool[:4]:
+            t = sctx.pxr_submit_event(e.x, e.y, e.z, e.layer, params)
+            while t not in sctx.pxr_poll(timeout_us=100000):
+                pass
+            sctx.pxr_fetch_tracks(t)
+        t_arr, t_done = {}, {}
+        start = time.perf_counter()
+        k = pending = 0
+        while k < n_req or pending:
+            now = time.perf_counter() - start
+            while k < n_req and arr[k] <= now:
+                e = pool[k % len(pool)]
+                t = sctx.try_submit_event(e.x, e.y, e.z, e.layer, params)
+                if t is None:
+                    break
+                t_arr[t] = start + arr[k]
+                k += 1
+                pending += 1
+            for t in sctx.pxr_poll(timeout_us=50 if k < n_req else 20000):
+                t_done[t] = time.perf_counter()
+                sctx.pxr_fetch_tracks(t)
+                pending -= 1
+    lat = np.array([t_done[t] - t_arr[t] for t in t_arr]) * 1e3
+    span = max(t_done.values()) - start
+    return {"rate_hz": rate, "events": n_req, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "events_per_s": n_req / span}
+
+
+def study(args):
+    import torch
+    import oracle
+    from paper_2104_06573_gb300 import pxr, synth
+    oracle.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    out = {"host_cores": os.cpu_count()}
+    with pxr.Context(device=0, mem_budget_bytes=16 << 30, stream=stream.cuda_stream) as ctx:
+        # C1: one barrel event, quadruplets; FP64 cuts and FP32 cuts
+        ev = synth.event_barrel(0)
+        P = synth.params_barrel_quadruplets()
+        o_rate, ref = _oracle_rate(oracle, ev, P)
+        c1 = {"hits": int(ev.n), "oracle_1core_events_per_s": o_rate}
+        for name, cut in (("fp64", pxr.CUT_FP64), ("fp32", pxr.CUT_FP32)):
+            prm = pxr.params_from(P, cut_mode=cut, fit_mode=pxr.FIT_FP64)
+            rate, tr, dbg = _gpu_event_rate(pxr, ctx, ev, prm, dev, stream, 500)
+            c1["gpu_plain_events_per_s_" + name] = rate
+            c1["set_mismatches_" + name] = _set_mismatches(ref, tr, dbg)
+        out["C1_barrel_event"] = c1
+        # C2: dense event with disks, both cut modes
+        ev = synth.event_phase1(0)
+        P = synth.params_phase1()
+        o_rate, ref = _oracle_rate(oracle, ev, P, 3.0)
+        c2 = {"hits": int(ev.n), "oracle_1core_events_per_s": o_rate}
+        for name, cut in (("fp64", pxr.CUT_FP64), ("fp32", pxr.CUT_FP32)):
+            prm = pxr.params_from(P, cut_mode=cut, fit_mode=pxr.FIT_FP64)
+            rate, tr, dbg = _gpu_event_rate(pxr, ctx, ev, prm, dev, stream, 200)
+            c2["gpu_plain_events_per_s_" + name] = rate
+            c2["set_mismatches_" + name] = _set_mismatches(ref, tr, dbg)
+        out["C2_dense_event"] = c2
+        # C4: fit precision and throughput on 1e6 smeared ntuplets
+        P = synth.params_barrel_quadruplets()
+        tb = synth.fit_tuplets(args.fit_n, seed=3)
+        t0 = time.perf_counter()
+        ref = oracle.fit_batch(tb.n_hits, tb.x.astype(np.float64), tb.y.astype(np.float64),
+                               tb.z.astype(np.float64), tb.layer, P)
+        o_fit = len(ref) / (time.perf_counter() - t0)
+        m = len(tb.n_hits)
+        dargs = [torch.from_numpy(a).to(dev) for a in (tb.n_hits, tb.x, tb.y, tb.z,
+                                                       tb.layer.view(np.int16))]
+        c4 = {"ntuplets": m, "oracle_1core_fits_per_s": o_fit}
+        for name, mode in (("fp32", pxr.FIT_FP32), ("mixed", pxr.FIT_MIXED),
+                           ("fp64", pxr.FIT_FP64)):
+            res = {k: torch.zeros(m, dtype=torch.float64, device=dev) for k in pxr.TRACK_FIELDS}
+            res["charge"] = torch.zeros(m, dtype=torch.int8, device=dev)
+            res["fit_status"] = torch.zeros(m, dtype=torch.int8, device=dev)
+            prm = pxr.params_from(P, fit_mode=mode)
+            for _ in range(2):
+                ctx.pxr_fit_batch(m, *dargs, 4, prm, res, stream=stream)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(5):
+                ctx.pxr_fit_batch(m, *dargs, 4, prm, res, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            h = {k: v.cpu().numpy() for k, v in res.items()}
+            ok = (ref["status"] == 0) & (h["fit_status"] == 0)
+            c4[name] = {"fits_per_s": 5 * m / (a.elapsed_time(b) / 1e3),
+                        "status_agree": float(np.mean(h["fit_status"] == ref["status"])),
+                        "errors": _fit_errors(h, ref, ok)}
+        out["C4_fit_precision"] = c4
+    # C5: serving sweep, continuous batching vs one event per launch, 8 GB budget
+    P = synth.params_barrel_quadruplets()
+    prm = pxr.params_from(P, cut_mode=pxr.CUT_FP32, fit_mode=pxr.FIT_MIXED)
+    c5 = []
+    for rate in (500.0, 1000.0, 2000.0, 5000.0):
+        n = int(min(6000, max(1000, rate * 2)))
+        c5.append({"served": _serve(pxr, synth, prm, dev, rate, n, 8 << 30, 256),
+                   "plain": _serve(pxr, synth, prm, dev, rate, n, 8 << 30, 1)})
+    out["C5_serving"] = c5
+    # oracle on all host cores, one event per process, on a sample of the batch workload
+    cores = os.cpu_count() or 1
+    sample = oracle_sample(min(32, 2 * cores))
+    v, wall, _ = cpu_baseline(sample, cores)
+    out["C3_oracle_all_cores"] = {"events_per_s": v, "cores": cores, "sample_events": len(sample)}
+    print(json.dumps(out, indent=1, default=float), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.study:
+        if rank == 0:
+            study(args)
         return
     run_pxr(args, rank, world, local)
 

@@ -36,6 +36,30 @@ __device__ __forceinline__ T atan2_t(T y, T x) { return FT ? T(atan2f(float(y), 
 template <bool FT, typename T>
 __device__ __forceinline__ T log_t(T v) { return FT ? T(logf(float(v))) : log(v); }
 
+// Turning angle about the reference centre, for the arc lengths.  A float arctangent is good to
+// ~1e-7 relative, and a nearly straight fitted track (whose curvature is a small difference of
+// inverse radii) amplifies that in pT; so with float transcendentals the small angles, where
+// that happens (|angle| < 0.25 rad), come from the arctangent series in the working precision
+// (terms to t^17: truncation below 4e-13 relative), the larger ones from the float function.
+template <bool FT, typename T>
+__device__ __forceinline__ T arc_angle(T y, T x)
+{
+    if (FT && x > T(0) && fabs(y) < T(0.25) * x) {
+        const T t = y / x, t2 = t * t;
+        T p = T(1.0 / 17.0);
+        p = p * t2 - T(1.0 / 15.0);
+        p = p * t2 + T(1.0 / 13.0);
+        p = p * t2 - T(1.0 / 11.0);
+        p = p * t2 + T(1.0 / 9.0);
+        p = p * t2 - T(1.0 / 7.0);
+        p = p * t2 + T(1.0 / 5.0);
+        p = p * t2 - T(1.0 / 3.0);
+        p = p * t2 + T(1.0);
+        return t * p;
+    }
+    return atan2_t<FT>(y, x);
+}
+
 struct FitOut {
     double pt, phi, cot, dxy, dz, chi2;
     int8_t q, status;
@@ -191,7 +215,7 @@ __device__ void fit_n(const float *X, const float *Y, const float *Z, const uint
         yr[i] = T(pw / (sqrt_t(dx * dx + dy * dy) + R0));
         const TC cr = -Cx * dy + Cy * dx;
         const TC dt = -Cx * dx - Cy * dy;
-        s[i] = T(R0 * atan2_t<FT>(sgn * cr, dt));
+        s[i] = T(R0 * arc_angle<FT>(sgn * cr, dt));
         z[i] = T(Z[i]);
     }
     T g[N], h[N];

@@ -272,6 +272,19 @@ def test_fit_batch_modes(ctx, orc):
     # still 1 % of the stated tolerance.
     for k, v in res[pxr.FIT_FP64].items():
         assert v < 0.01 * TOL[k], (k, v)
+    # MIXED (double arithmetic, float transcendentals) stays inside the stated tolerances
+    for k, v in res[pxr.FIT_MIXED].items():
+        assert v <= TOL[k], (k, v)
+
+
+@pytest.mark.parametrize("cut", [pxr.CUT_FP32])
+def test_dense_event_mixed_fit_within_tolerance(ctx, orc, cut):
+    """The batch path with the MIXED fit (the benchmark's setting): sets bit-exact, fitted
+    parameters within the stated tolerances of the FP64 oracle."""
+    P = synth.params_phase1()
+    ev = ev_tuple(synth.event_phase1(4))
+    got = run_plan(ctx, [ev], P, cut, fit=pxr.FIT_MIXED)[0]
+    check_event(orc, ev, P, got, fit_tol=TOL)
 
 
 def test_two_contexts_shard_events(ctx):
