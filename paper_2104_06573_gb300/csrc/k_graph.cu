@@ -161,9 +161,8 @@ __global__ void __launch_bounds__(256) k_doublets_compact(DevBatch b, DevParams 
 // item.  The lanes find their items' windows together (one round of dependent loads for 32
 // items); the warp reserves one entry per candidate for all its items with one atomic per event
 // present (usually one).  The items are then taken one at a time, their data broadcast from the
-// owning lane: the lanes test 64 consecutive candidates per step (coalesced float4 loads, two in
-// flight per lane) and write the outer hit, or kNone where the cut fails, to the candidate's
-// entry.
+// owning lane: the lanes test 32 consecutive candidates per step (coalesced float4 loads) and
+// write the outer hit, or kNone where the cut fails, to the candidate's entry.
 
 __global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint32_t slots)
 {
@@ -236,48 +235,32 @@ __global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint3
             const size_t oi = (size_t)g * kMaxOut + slot;
             b.item[oi] = make_uint4(first, nw, r0, n1 - r2);
         }
-        // ---- candidates, item by item (the item's data broadcast once), 64 per step ----
-        uint32_t npass = 0;
-        for (uint32_t has = __ballot_sync(FULL, nw > 0); has; has &= has - 1) {
-            const int k = __ffs(has) - 1;
+        // ---- candidates, item by item (the item's data broadcast once), 32 per step ----
+        const uint32_t has = __ballot_sync(FULL, nw > 0);
+        const uint32_t e_main = __shfl_sync(FULL, e, has ? __ffs(has) - 1 : 0);
+        uint32_t npass = 0;                       // this lane's passes of the event e_main
+        for (uint32_t m = has; m; m &= m - 1) {
+            const int k = __ffs(m) - 1;
             const uint32_t gk = __shfl_sync(FULL, g, k);
             const float4 hk = make_float4(__shfl_sync(FULL, hi.x, k), __shfl_sync(FULL, hi.y, k),
                                           0.f, __shfl_sync(FULL, hi.w, k));
             const uint32_t a0 = __shfl_sync(FULL, r0, k), a1 = __shfl_sync(FULL, n1, k);
             const uint32_t a2 = __shfl_sync(FULL, r2, k);
             const uint32_t fk = __shfl_sync(FULL, first, k), wk = __shfl_sync(FULL, nw, k);
+            const uint32_t ek = __shfl_sync(FULL, e, k);
             uint32_t np = 0;
-            for (uint32_t c0 = 0; c0 < wk; c0 += 64) {
-                const uint32_t ca = c0 + lane, cb = ca + 32u;
-                const uint32_t oa = ca < a1 ? a0 + ca : a2 + (ca - a1);
-                const uint32_t ob = cb < a1 ? a0 + cb : a2 + (cb - a1);
-                const float4 ha = ca < wk ? __ldg(&b.hs[oa]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 hb = cb < wk ? __ldg(&b.hs[ob]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                if (ca < wk) {
-                    const bool pass = doublet_test(b, p, gk, hk, oa, ha);
-                    b.cell_in[fk + ca] = gk;
-                    b.cell_out[fk + ca] = pass ? oa : kNone;
-                    np += pass;
-                }
-                if (cb < wk) {
-                    const bool pass = doublet_test(b, p, gk, hk, ob, hb);
-                    b.cell_in[fk + cb] = gk;
-                    b.cell_out[fk + cb] = pass ? ob : kNone;
-                    np += pass;
-                }
+            for (uint32_t c = lane; c < wk; c += 32) {
+                const uint32_t o = c < a1 ? a0 + c : a2 + (c - a1);
+                const bool pass = doublet_test(b, p, gk, hk, o, __ldg(&b.hs[o]));
+                b.cell_in[fk + c] = gk;
+                b.cell_out[fk + c] = pass ? o : kNone;
+                np += pass;
             }
-            const uint32_t tot = __reduce_add_sync(FULL, np);
-            if (lane == (uint32_t)k) npass = tot;
+            if (ek == e_main) npass += np;
+            else if (np) atomicAdd(&b.cnt[C_CELLS * b.E + ek], np);   // block spans two events
         }
-        // real cells per event: each item's count sits in its own lane
-        for (uint32_t rem = __ballot_sync(FULL, npass > 0); rem;) {
-            const int h = __ffs(rem) - 1;
-            const uint32_t eh = __shfl_sync(FULL, e, h);
-            const uint32_t seg = __ballot_sync(FULL, npass > 0 && e == eh);
-            const uint32_t tot = __reduce_add_sync(FULL, (seg >> lane) & 1u ? npass : 0u);
-            if (lane == (uint32_t)h) atomicAdd(&b.cnt[C_CELLS * b.E + eh], tot);
-            rem &= ~seg;
-        }
+        npass = __reduce_add_sync(FULL, npass);
+        if (lane == 0 && npass) atomicAdd(&b.cnt[C_CELLS * b.E + e_main], npass);
     }
 }
 
