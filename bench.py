@@ -440,10 +440,24 @@ def _oracle_rate(oracle, ev, P, min_s=1.0):
             return n / (time.perf_counter() - t0), r
 
 
-def _set_mismatches(ref, tracks, debug):
+def _set_mismatches(ref, tracks, debug, layer, P):
+    """Symmetric differences against the oracle.  CA edges are compared on the cells that can lie
+    on a root path (root cells and, transitively, their edges' targets): the GPU builds the
+    out-edges of exactly those."""
     cells = {tuple(map(int, c)) for c in ref["cells"]}
     cl = ref["cells"]
-    edges = {(int(cl[a, 0]), int(cl[a, 1]), int(cl[b, 1])) for a, b in ref["edges"]}
+    out = {}
+    for a, b in ref["edges"]:
+        out.setdefault(int(a), []).append(int(b))
+    todo = [c for c in range(len(cl)) if (P.root_mask >> int(layer[cl[c, 0]])) & 1]
+    seen = set(todo)
+    while todo:
+        for b in out.get(todo.pop(), ()):
+            if b not in seen:
+                seen.add(b)
+                todo.append(b)
+    edges = {(int(cl[a, 0]), int(cl[a, 1]), int(cl[b, 1])) for a, b in ref["edges"]
+             if int(a) in seen}
     tup = {tuple(int(h) for h in row[:n]) for row, n in zip(ref["tuples"], ref["tuple_n"])}
     g_cells = {tuple(map(int, c)) for c in debug[0]}
     g_edges = {tuple(map(int, c)) for c in debug[1]}
@@ -522,7 +536,7 @@ def study(args):
             prm = pxr.params_from(P, cut_mode=cut, fit_mode=pxr.FIT_FP64)
             rate, tr, dbg = _gpu_event_rate(pxr, ctx, ev, prm, dev, stream, 500)
             c1["gpu_plain_events_per_s_" + name] = rate
-            c1["set_mismatches_" + name] = _set_mismatches(ref, tr, dbg)
+            c1["set_mismatches_" + name] = _set_mismatches(ref, tr, dbg, ev.layer, P)
         out["C1_barrel_event"] = c1
         # C2: dense event with disks, both cut modes
         ev = synth.event_phase1(0)
@@ -533,7 +547,7 @@ def study(args):
             prm = pxr.params_from(P, cut_mode=cut, fit_mode=pxr.FIT_FP64)
             rate, tr, dbg = _gpu_event_rate(pxr, ctx, ev, prm, dev, stream, 200)
             c2["gpu_plain_events_per_s_" + name] = rate
-            c2["set_mismatches_" + name] = _set_mismatches(ref, tr, dbg)
+            c2["set_mismatches_" + name] = _set_mismatches(ref, tr, dbg, ev.layer, P)
         out["C2_dense_event"] = c2
         # C4: fit precision and throughput on 1e6 smeared ntuplets
         P = synth.params_barrel_quadruplets()

@@ -84,7 +84,8 @@ extern "C" {
 /*
  * Reconstruction parameters.  All fields are inputs; pxr_params_init fills a preset.
  *
- * Doublets.  For every allowed pair p (layer pair_inner[p] -> layer pair_outer[p]) and every hit
+ * Doublets.  For every allowed pair p (layer pair_inner[p] -> layer pair_outer[p]; the pairs must
+ *   not form a cycle of layers, and at most 4 pairs may share an inner or an outer layer) and every hit
  *   i on the inner and o on the outer layer, the cell (i, o) exists iff
  *       x_i x_o + y_i y_o >= cos_phi_window * r_i * r_o,   r = sqrt(x^2 + y^2),
  *   i.e. the azimuths differ by at most phi_window.  cos_phi_window must equal cos(phi_window)
@@ -213,7 +214,9 @@ int pxr_fetch_tracks(pxr_ctx *ctx, uint64_t ticket, pxr_tracks *out);
 
 /* Debug content of a finished event kept with cfg->keep_debug (before pxr_fetch_tracks):
  * what = 0: cells as (inner, outer) caller-index pairs (2 words each);
- * what = 1: CA edges as (i, j, k) caller-index triples (3 words each);
+ * what = 1: CA edges as (i, j, k) caller-index triples (3 words each), for the cells that can
+ *           lie on a root path (root cells and, transitively, their edges' targets: the edges
+ *           of other cells cannot change a result and are not built);
  * what = 2: ntuplets before suffix removal as PXR_MAX_HITS words each (0xFFFFFFFF padded).
  * Writes at most cap words to buf (host), *n = number of items. */
 int pxr_fetch_debug(pxr_ctx *ctx, uint64_t ticket, int what, uint32_t *buf, uint32_t cap,

@@ -381,7 +381,20 @@ __device__ __forceinline__ float funord(int i) { return __int_as_float(i >= 0 ? 
 // warp.  A slot with more than kStage entries is tested from global memory.  Loads that do not depend on one another are issued together (the
 // junction's own records, its first out-cell list and inner window) so that a junction waits on
 // few memory round trips.
-__global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevParams p)
+// Mark cell C as reached (it has an in-edge); the first marker appends it to the event's frontier
+// list, the input of the sparse pass of C's outer layer.
+__device__ __forceinline__ void mark_reached(const DevBatch &b, uint32_t e, uint32_t C)
+{
+    const uint32_t bit = 1u << (C & 31u);
+    if (atomicOr(&b.live[C >> 5], bit) & bit) return;
+    const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
+    const uint32_t x = atomicAdd(&b.cnt[C_FRONT * b.E + e], 1u);
+    if (x < cap) b.front_list[b.edge_off[e] + x] = C;
+    else atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+}
+
+__global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevParams p,
+                                                                uint32_t layer_mask)
 {
     __shared__ float4 s_h[kConnWarps][kStage];      // staged out-cells' outer hits (list order)
     __shared__ uint16_t s_t[kConnWarps][kStage];    // list positions sorted by local bin
@@ -403,11 +416,13 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
         const uint4 it0 = b.item[(size_t)j * kMaxOut];
         uint32_t f0 = it0.x, nB = it0.y;
         const uint32_t Lj = meta >> kLocalBits;
-        if (Lj >= p.n_layers) continue;
+        if (Lj >= p.n_layers || !((layer_mask >> Lj) & 1u)) continue;
         const uint32_t nin = p.n_in[Lj], nout = p.n_out[Lj];
         if (nin == 0 || nout == 0) continue;
         const uint32_t *bk = b.bkt + (size_t)e * (nk + 1);
         const Window w0 = phi_window(bk, p.in_layer[Lj][0], phij, p);
+        // out-cells that start further pairs from a non-root inner layer go to the frontier
+        const bool j_root = (p.root_mask >> Lj) & 1u;
         for (uint32_t s = 0; s < nout; ++s) {
             const uint32_t Lk = p.out_layer[Lj][s];
             const bool disk = p.is_disk[Lk];
@@ -490,9 +505,12 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                 // bin[t] is now the end of bin t; the start of bin t is bin[t - 1] (0 for t = 0)
                 nq = bin[kBins - 1];
             }
+            const bool front = !j_root && p.n_out[Lk] > 0;
             for (uint32_t si = 0; si < nin; ++si) {
                 const uint32_t Li = p.in_layer[Lj][si];
                 const uint32_t slot_i = p.in_slot[Lj][si];
+                // this pass takes the root in-cells; reached non-root ones go to the sparse pass
+                if (!((p.root_mask >> Li) & 1u)) continue;
                 const Window w = si ? phi_window(bk, Li, phij, p) : w0;
                 const uint32_t nc = w.size();
                 for (uint32_t c0 = 0; c0 < nc; c0 += 32) {
@@ -595,7 +613,10 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                         const uint32_t first = b.edge_off[e] + my0;
                         uint32_t wr = 0;
                         for (uint32_t t = 0; t < have && wr < nw; ++t) b.nbr[first + wr++] = b.nbr[old + t];
-                        if (wr < nw) b.nbr[first + wr++] = Bf;
+                        if (wr < nw) {
+                            b.nbr[first + wr++] = Bf;
+                            if (front) mark_reached(b, e, Bf);
+                        }
                         for (uint32_t q = qf + 1; q < q1 && wr < nw && npass > 1; ++q) {
                             uint32_t B;
                             float4 hk;
@@ -609,8 +630,10 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                                 if (k == kNone) continue;
                                 hk = b.hs[k];
                             }
-                            if (triplet_test(b, p, i, j, B, hi.x, hi.y, hj, hk, a))
+                            if (triplet_test(b, p, i, j, B, hi.x, hi.y, hj, hk, a)) {
                                 b.nbr[first + wr++] = B;
+                                if (front) mark_reached(b, e, B);
+                            }
                         }
                         b.nbr_first[A] = first;
                         b.nbr_n[A] = wr;
@@ -622,14 +645,181 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
     }
 }
 
-void launch_connect(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
+void launch_connect(const DevBatch &b, const DevParams &p, uint32_t layer_mask, cudaStream_t s,
+                    int sms)
 {
-    (void)total;
     uint64_t blocks = ((uint64_t)b.N + kConnWarps - 1) / kConnWarps;
     uint64_t cap = (uint64_t)sms * p.grid_per_sm[2];
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
-    k_connect<<<(unsigned)blocks, kConnWarps * 32, 0, s>>>(b, p);
+    k_connect<<<(unsigned)blocks, kConnWarps * 32, 0, s>>>(b, p, layer_mask);
+}
+
+// Sparse CA pass over the frontier: cells B = (j, k) that were reached (have an in-edge), are not
+// root cells, and whose outer hit k lies on a layer of layer_mask.  Their out-edges go to the
+// out-cells C = (k, l) of every pair starting on k's layer that pass the triplet cut.  Each warp
+// takes 32 consecutive frontier entries (one chunk of 256 entries per CTA, all of one event): the
+// lanes load their cells' hits together, then the warp tests the cells' out-entries one cell at
+// a time, 32 entries per step (failed candidates skipped), collecting the passes in shared
+// memory grouped by cell; one atomic reserves the edge lists of all 32 cells, which are
+// contiguous and in the same order, so the warp copies them with coalesced stores.  A cell whose
+// passes do not fit the buffer is redone on its own.  Reached out-cells join the frontier.
+constexpr int kFrontBuf = 256;
+constexpr int kFrontU = 3;      // entries per lane whose loads are issued together
+
+__global__ void __launch_bounds__(256, 4) k_connect_front(DevBatch b, DevParams p, uint32_t total,
+                                                          uint32_t layer_mask)
+{
+    __shared__ uint32_t s_pass[8][kFrontBuf];
+    const uint32_t FULL = 0xFFFFFFFFu;
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, lt = (1u << lane) - 1u;
+    uint32_t *buf = s_pass[wid];
+    const uint32_t n_chunks = total / kChunk;
+    for (uint32_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+        const uint32_t e = b.edge_chunk[ch];
+        const uint32_t x0 = b.edge_off[e];
+        const uint32_t nf = min(b.front_snap[e], b.edge_off[e + 1] - x0);
+        if (ch * kChunk - x0 >= nf) continue;                      // uniform over the CTA
+        // ---- this warp's 32 entries, one cell per lane ----
+        const uint32_t x = ch * kChunk + wid * 32u + lane;
+        uint32_t B = 0, j = 0, k = 0, Lk = 0;
+        float4 hj = make_float4(0.f, 0.f, 0.f, 0.f), hk = hj;
+        uint4 it0 = make_uint4(0u, 0u, 0u, 0u);                    // k's first pair's entries
+        bool valid = x - x0 < nf;
+        if (valid) {
+            B = b.front_list[x];
+            j = b.cell_in[B];
+            k = b.cell_out[B];
+            hj = b.hs[j];
+            hk = b.hs[k];
+            it0 = b.item[(size_t)k * kMaxOut];
+            Lk = b.hmeta[k] >> kLocalBits;
+            valid = (layer_mask >> Lk) & 1u;
+        }
+        uint32_t my_cnt = 0, redo = 0;
+        uint32_t nbuf = 0;                                         // warp-uniform
+        for (uint32_t m = __ballot_sync(FULL, valid); m; m &= m - 1) {
+            const int q = __ffs(m) - 1;
+            const uint32_t jq = __shfl_sync(FULL, j, q), kq = __shfl_sync(FULL, k, q);
+            const uint32_t Lq = __shfl_sync(FULL, Lk, q);
+            const float4 hjq = make_float4(__shfl_sync(FULL, hj.x, q), __shfl_sync(FULL, hj.y, q),
+                                           __shfl_sync(FULL, hj.z, q), __shfl_sync(FULL, hj.w, q));
+            const float4 hkq = make_float4(__shfl_sync(FULL, hk.x, q), __shfl_sync(FULL, hk.y, q),
+                                           __shfl_sync(FULL, hk.z, q), __shfl_sync(FULL, hk.w, q));
+            const RZ32 a = rz32(hjq, hkq);
+            const bool k_root = (p.root_mask >> Lq) & 1u;
+            const uint32_t start = nbuf;
+            uint32_t cnt = 0;
+            bool fits = true;
+            for (uint32_t s = 0; s < p.n_out[Lq]; ++s) {
+                const uint4 it = s ? b.item[(size_t)kq * kMaxOut + s]
+                                   : make_uint4(__shfl_sync(FULL, it0.x, q),
+                                                __shfl_sync(FULL, it0.y, q), 0u, 0u);
+                const bool front = !k_root && p.n_out[p.out_layer[Lq][s]] > 0;
+                for (uint32_t c0 = 0; c0 < it.y; c0 += 32u * kFrontU) {
+                    // all loads of the step first: entries, then their outer hits
+                    uint32_t l[kFrontU];
+                    float4 hl[kFrontU];
+#pragma unroll
+                    for (int u = 0; u < kFrontU; ++u) {
+                        const uint32_t c = c0 + 32u * u + lane;
+                        l[u] = c < it.y ? b.cell_out[it.x + c] : kNone;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kFrontU; ++u)
+                        hl[u] = l[u] != kNone ? b.hs[l[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int u = 0; u < kFrontU; ++u) {
+                        if (c0 + 32u * u >= it.y) break;                   // uniform
+                        const uint32_t C = it.x + c0 + 32u * u + lane;
+                        const bool pass = l[u] != kNone &&
+                            triplet_test(b, p, jq, kq, C, hjq.x, hjq.y, hkq, hl[u], a);
+                        const uint32_t pm = __ballot_sync(FULL, pass);
+                        if (pass) {
+                            const uint32_t idx = start + cnt + __popc(pm & lt);
+                            if (idx < (uint32_t)kFrontBuf) buf[idx] = C;
+                            if (front) mark_reached(b, e, C);
+                        }
+                        cnt += __popc(pm);
+                    }
+                }
+            }
+            if (start + cnt > (uint32_t)kFrontBuf) fits = false;
+            if (lane == (uint32_t)q) {
+                my_cnt = fits ? cnt : 0u;
+                redo = fits ? 0u : cnt;
+            }
+            if (fits) nbuf += cnt;
+        }
+        // ---- one reservation for the buffered lists (in lane order = buffer order) ----
+        uint32_t incl = my_cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= (uint32_t)o) incl += t;
+        }
+        uint32_t base = 0;
+        if (lane == 0 && nbuf) base = atomicAdd(&b.cnt[C_EDGES * b.E + e], nbuf);
+        base = __shfl_sync(FULL, base, 0);
+        const uint32_t cap = b.edge_off[e + 1] - x0;
+        const uint32_t nw = base >= cap ? 0u : min(nbuf, cap - base);
+        if (nw < nbuf && lane == 0) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+        __syncwarp();
+        for (uint32_t t = lane; t < nw; t += 32) b.nbr[x0 + base + t] = buf[t];
+        if (my_cnt) {
+            const uint32_t o = incl - my_cnt;                      // offset in the warp's range
+            b.nbr_first[B] = x0 + base + o;
+            b.nbr_n[B] = o >= nw ? 0u : min(my_cnt, nw - o);
+        }
+        // ---- cells whose passes did not fit: their own reservation and a second sweep ----
+        for (uint32_t m = __ballot_sync(FULL, redo > 0); m; m &= m - 1) {
+            const int q = __ffs(m) - 1;
+            const uint32_t Bq = __shfl_sync(FULL, B, q), n = __shfl_sync(FULL, redo, q);
+            const uint32_t jq = __shfl_sync(FULL, j, q), kq = __shfl_sync(FULL, k, q);
+            const uint32_t Lq = __shfl_sync(FULL, Lk, q);
+            const float4 hjq = make_float4(__shfl_sync(FULL, hj.x, q), __shfl_sync(FULL, hj.y, q),
+                                           __shfl_sync(FULL, hj.z, q), __shfl_sync(FULL, hj.w, q));
+            const float4 hkq = make_float4(__shfl_sync(FULL, hk.x, q), __shfl_sync(FULL, hk.y, q),
+                                           __shfl_sync(FULL, hk.z, q), __shfl_sync(FULL, hk.w, q));
+            const RZ32 a = rz32(hjq, hkq);
+            uint32_t rb = 0;
+            if (lane == 0) rb = atomicAdd(&b.cnt[C_EDGES * b.E + e], n);
+            rb = __shfl_sync(FULL, rb, 0);
+            const uint32_t rw = rb >= cap ? 0u : min(n, cap - rb);
+            if (lane == 0) {
+                if (rw < n) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+                b.nbr_first[Bq] = x0 + rb;
+                b.nbr_n[Bq] = rw;
+            }
+            uint32_t run = 0;
+            for (uint32_t s = 0; s < p.n_out[Lq] && run < rw; ++s) {
+                const uint4 it = b.item[(size_t)kq * kMaxOut + s];
+                for (uint32_t c0 = 0; c0 < it.y && run < rw; c0 += 32) {
+                    const uint32_t C = it.x + c0 + lane;
+                    bool pass = false;
+                    if (c0 + lane < it.y) {
+                        const uint32_t l = b.cell_out[C];
+                        if (l != kNone)
+                            pass = triplet_test(b, p, jq, kq, C, hjq.x, hjq.y, hkq, b.hs[l], a);
+                    }
+                    const uint32_t pm = __ballot_sync(FULL, pass);
+                    const uint32_t idx = run + __popc(pm & lt);
+                    if (pass && idx < rw) b.nbr[x0 + rb + idx] = C;
+                    run += __popc(pm);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+void launch_connect_front(const DevBatch &b, const DevParams &p, uint32_t total,
+                          uint32_t layer_mask, cudaStream_t s, int sms)
+{
+    const uint32_t chunks = total / kChunk;
+    const uint32_t cap = (uint32_t)sms * p.grid_per_sm[2];
+    if (chunks == 0) return;
+    k_connect_front<<<chunks < cap ? chunks : cap, 256, 0, s>>>(b, p, total, layer_mask);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -26,8 +26,8 @@ constexpr uint32_t kHitChunk = 32;   // granularity of the hit -> event table
 // Per-event counters, laid out as kCounters consecutive arrays of E words.
 enum Counter : int {
     C_CELLS = 0, C_EDGES = 1, C_TUPLES = 2, C_FLAGS = 3, C_OUT = 4,   // reported per event
-    C_ROOTS = 5, C_SLOTS = 6,                                          // internal
-    kCounters = 7
+    C_ROOTS = 5, C_SLOTS = 6, C_FRONT = 7,                             // internal
+    kCounters = 8
 };
 constexpr int kReportedCounters = 5;
 
@@ -58,6 +58,11 @@ struct DevParams {
     float dca32;                        // dca_cut rounded to float
     float tan_win;                      // tan(asin(theta_cut) + margin); inf when theta_cut >= 1
     uint32_t grid_per_sm[6];            // CTAs per SM at most, per stage (sort ... fit)
+    // CA levels: junction layers (with in- and out-pairs) ordered so that every pair's inner
+    // layer comes first; per level the junction layers whose in-cells include root cells (dense
+    // pass) and those with in-cells from non-root layers (sparse pass over reached cells)
+    uint32_t n_levels;
+    uint32_t level_dense[kMaxLayers + 1], level_sparse[kMaxLayers + 1];   // layer bit masks
     double cw;                          // cos(w) as given by the caller
     double theta, dca;
     double bfield, sigma_rphi, sigma_z, x_over_x0;
@@ -96,6 +101,11 @@ struct DevBatch {
     uint32_t *nbr;                      // [edges] target cells
     uint32_t *mindepth;                 // [cells] fewest hits before the cell on a root path
     uint32_t *root_list;                // [edges] per event: root cells that have out-edges
+    uint32_t *live;                     // [entries / 32] bit per cell: has an in-edge
+    uint32_t *front_list;               // [edges] per event: non-root cells with in-edges whose
+                                        //   outer hit starts further pairs (the sparse CA input)
+    uint32_t *front_snap;               // [E] frontier lengths when a sparse pass starts (the pass
+                                        //   appends for later levels while it reads)
     // ntuplets
     uint32_t *tup_hits;                 // [tuples * kMaxHits] sorted hit positions
     uint8_t *tup_n;                     // [tuples]
@@ -143,7 +153,9 @@ void launch_layer_count(const uint32_t *hit_off, const uint16_t *layer, uint32_t
                         uint32_t n_layers, uint32_t *counts, cudaStream_t s, int sms);
 void launch_doublets(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms);
 void launch_doublets_compact(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms);
-void launch_connect(const DevBatch &b, const DevParams &p, uint32_t cell_total, cudaStream_t s,
+void launch_connect_front(const DevBatch &b, const DevParams &p, uint32_t edge_total,
+                          uint32_t layer_mask, cudaStream_t s, int sms);
+void launch_connect(const DevBatch &b, const DevParams &p, uint32_t layer_mask, cudaStream_t s,
                     int sms);
 void launch_ntuplets(const DevBatch &b, const DevParams &p, uint32_t edge_total, cudaStream_t s,
                      int sms);

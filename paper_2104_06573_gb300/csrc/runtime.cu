@@ -158,6 +158,29 @@ static int check_params(const pxr_params *p, DevParams *d)
     d->sigma_rphi = p->sigma_rphi;
     d->sigma_z = p->sigma_z;
     d->x_over_x0 = p->x_over_x0;
+    // CA levels: a layer's level is 1 + the highest level of its pairs' inner layers (0 without
+    // in-pairs); junction layers (in- and out-pairs) are processed level by level, so that every
+    // cell has all its in-edges before its own out-edges are built
+    uint32_t level[kMaxLayers] = {};
+    for (uint32_t pass = 0;; ++pass) {
+        bool changed = false;
+        for (uint32_t l = 0; l < p->n_layers; ++l)
+            for (uint32_t q = 0; q < d->n_in[l]; ++q)
+                if (level[d->in_layer[l][q]] + 1u > level[l]) {
+                    level[l] = level[d->in_layer[l][q]] + 1u;
+                    changed = true;
+                }
+        if (!changed) break;
+        if (pass >= p->n_layers) return fail(PXR_EINVAL, "layer pairs form a cycle");
+    }
+    for (uint32_t l = 0; l < p->n_layers; ++l) {
+        if (!d->n_in[l] || !d->n_out[l]) continue;
+        d->n_levels = std::max(d->n_levels, level[l]);
+        for (uint32_t q = 0; q < d->n_in[l]; ++q) {
+            if ((p->root_layer_mask >> d->in_layer[l][q]) & 1u) d->level_dense[level[l]] |= 1u << l;
+            else d->level_sparse[level[l]] |= 1u << l;
+        }
+    }
     // launch shapes: CTAs per SM at most (the kernels stride over their work)
     static const uint32_t kGridDefault[PXR_STAGES] = {4, 16, 16, 8, 8, 8};
     for (int k = 0; k < PXR_STAGES; ++k)
@@ -196,9 +219,9 @@ static EventCaps event_caps(const pxr_params &p, uint32_t nb, const uint32_t *lc
     double edges = std::ceil(0.08 * cells) + 4.0 * n + 256.0;
     double tuples = p.max_tuples_per_event ? (double)p.max_tuples_per_event
                                            : std::ceil(0.5 * edges) + 2.0 * n + 256.0;
-    // cells and ntuplets in whole chunks: every chunk of the work loops belongs to one event
+    // cells, edges and ntuplets in whole chunks: every chunk of the work loops belongs to one event
     auto up = [](double v) { return (uint32_t)(std::ceil(v / kChunk) * kChunk); };
-    return EventCaps{up(cells), (uint32_t)std::min(edges, 1.0e9), up(std::min(tuples, 1.0e9))};
+    return EventCaps{up(cells), up(std::min(edges, 1.0e9)), up(std::min(tuples, 1.0e9))};
 }
 
 // ------------------------------------------------------------------------------------------
@@ -221,7 +244,7 @@ struct PlanOffsets {
         head_end;
     size_t cnt, bkt, hs, r64, hmeta, hphi, item, cell_in, cell_out,
         nbr_first,
-        nbr_n, nbr, mindepth, root_list, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, out_evt, o_nh,
+        nbr_n, nbr, mindepth, root_list, live, front_list, front_snap, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, out_evt, o_nh,
         o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status;
     size_t total;
 };
@@ -260,6 +283,9 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.nbr = L.add(4 * G);
     o.mindepth = L.add(4 * C);
     o.root_list = L.add(4 * G);
+    o.live = L.add(4 * ((C + 31) / 32));
+    o.front_list = L.add(4 * G);
+    o.front_snap = L.add(4 * (size_t)E);
     o.tup_hits = L.add(4 * T * kMaxHits);
     o.tup_n = L.add(T);
     o.tup_state = L.add(T);
@@ -423,6 +449,9 @@ static void plan_bind(pxr_plan *P)
     b.nbr = (uint32_t *)(r + o.nbr);
     b.mindepth = (uint32_t *)(r + o.mindepth);
     b.root_list = (uint32_t *)(r + o.root_list);
+    b.live = (uint32_t *)(r + o.live);
+    b.front_list = (uint32_t *)(r + o.front_list);
+    b.front_snap = (uint32_t *)(r + o.front_snap);
     b.tup_hits = (uint32_t *)(r + o.tup_hits);
     b.tup_n = (uint8_t *)(r + o.tup_n);
     b.tup_state = (uint8_t *)(r + o.tup_state);
@@ -516,11 +545,19 @@ static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
     CK(cudaMemsetAsync(r + P->off.cnt, 0, 4 * (size_t)kCounters * P->E, s));
     if (p.drop_suffixes) CK(cudaMemsetAsync(r + P->off.mindepth, 0xFF, 4 * P->C, s));
     CK(cudaMemsetAsync(r + P->off.nbr_n, 0, 4 * P->C, s));   // cells without edges stay at 0
+    CK(cudaMemsetAsync(r + P->off.live, 0, 4 * ((P->C + 31) / 32), s));
     launch_sort(b, p, s, sms);
     if (t) CK(stage_mark(P->ev_stage[1], s, capturing));
     launch_doublets(b, p, s, sms);
     if (t) CK(stage_mark(P->ev_stage[2], s, capturing));
-    launch_connect(b, p, (uint32_t)P->C, s, sms);
+    for (uint32_t lv = 1; lv <= p.n_levels; ++lv) {
+        if (p.level_dense[lv]) launch_connect(b, p, p.level_dense[lv], s, sms);
+        if (p.level_sparse[lv]) {
+            CK(cudaMemcpyAsync(b.front_snap, b.cnt + (size_t)C_FRONT * P->E, 4 * (size_t)P->E,
+                               cudaMemcpyDeviceToDevice, s));
+            launch_connect_front(b, p, (uint32_t)P->G, p.level_sparse[lv], s, sms);
+        }
+    }
     if (t) CK(stage_mark(P->ev_stage[3], s, capturing));
     launch_ntuplets(b, p, (uint32_t)P->G, s, sms);
     launch_select(b, p, (uint32_t)P->T, s, sms);
@@ -532,7 +569,13 @@ static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
     return PXR_OK;
 }
 
-static int plan_launches(const pxr_plan *) { return 7; }
+static int plan_launches(const pxr_plan *P)
+{
+    int n = 6;                                  // sort, doublets, walk, select, scan, fit
+    for (uint32_t lv = 1; lv <= P->dp.n_levels; ++lv)
+        n += (P->dp.level_dense[lv] ? 1 : 0) + (P->dp.level_sparse[lv] ? 1 : 0);
+    return n;
+}
 
 static void plan_free(pxr_plan *P)
 {

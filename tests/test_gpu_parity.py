@@ -63,11 +63,29 @@ def run_plan(ctx, events, P, cut, fit=pxr.FIT_FP64, graph=False, n_phi_bins=0, m
     return out
 
 
+def reached_edges(ref, layer, P):
+    """The oracle's CA edges whose source cell can lie on a root path: root cells (inner hit on
+    a root layer) and, transitively, the targets of their edges.  The GPU builds the out-edges of
+    exactly these cells (no other cell can be part of an emitted ntuplet)."""
+    cl = ref["cells"]
+    out = {}
+    for a, b in ref["edges"]:
+        out.setdefault(int(a), []).append(int(b))
+    live = [c for c in range(len(cl)) if (P.root_mask >> int(layer[cl[c, 0]])) & 1]
+    seen = set(live)
+    while live:
+        a = live.pop()
+        for b in out.get(a, ()):
+            if b not in seen:
+                seen.add(b)
+                live.append(b)
+    return {(int(cl[a, 0]), int(cl[a, 1]), int(cl[b, 1])) for a, b in ref["edges"] if int(a) in seen}
+
+
 def oracle_sets(orc, ev, P):
     ref = orc.reconstruct(*ev, P)
     cells = {tuple(map(int, c)) for c in ref["cells"]}
-    cl = ref["cells"]
-    edges = {(int(cl[a, 0]), int(cl[a, 1]), int(cl[b, 1])) for a, b in ref["edges"]}
+    edges = reached_edges(ref, ev[3], P)
     tup = [tuple(int(h) for h in row[:n]) for row, n in zip(ref["tuples"], ref["tuple_n"])]
     order = sorted(range(len(tup)), key=lambda i: tup[i] + (0xFFFFFFFF,) * (8 - len(tup[i])))
     return ref, cells, edges, [tup[i] for i in order], ref["fits"][order]
