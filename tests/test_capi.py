@@ -90,6 +90,15 @@ def test_params_validation(lib):
     q = pxr.params_from(synth.params_phase1())
     q.pair_outer[0] = q.pair_inner[0]                    # inner == outer
     assert lib.pxr_params_check(C.byref(q)) == pxr.EINVAL
+    # layer pairs that form a cycle (3 -> 0 closes 0 -> 1 -> 2 -> 3) have no CA level order
+    q = pxr.params_from(synth.params_barrel_quadruplets())
+    q.pair_inner[q.n_pairs], q.pair_outer[q.n_pairs] = 3, 0
+    q.n_pairs += 1
+    assert lib.pxr_params_check(C.byref(q)) == pxr.EINVAL
+    for k, v in ((0, 65), (5, 100)):                     # grid caps above 64 CTAs per SM
+        q = pxr.params_from(synth.params_barrel_quadruplets())
+        q.grid_per_sm[k] = v
+        assert lib.pxr_params_check(C.byref(q)) == pxr.EINVAL
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
