@@ -381,12 +381,16 @@ __device__ __forceinline__ float funord(int i) { return __int_as_float(i >= 0 ? 
 // warp.  A slot with more than kStage entries is tested from global memory.  Loads that do not depend on one another are issued together (the
 // junction's own records, its first out-cell list and inner window) so that a junction waits on
 // few memory round trips.
-// Mark cell C as reached (it has an in-edge); the first marker appends it to the event's frontier
-// list, the input of the sparse pass of C's outer layer.
-__device__ __forceinline__ void mark_reached(const DevBatch &b, uint32_t e, uint32_t C)
+// Mark cell C as reached (it has an in-edge).  The first marker clears C's edge count (the walk
+// reads it; a later level writes the count if C gets out-edges) and, when C is `listed` (a
+// non-root cell whose outer hit starts further pairs), appends it to the event's frontier list,
+// the input of the sparse pass of C's outer layer.
+__device__ __forceinline__ void mark_reached(const DevBatch &b, uint32_t e, uint32_t C, bool listed)
 {
     const uint32_t bit = 1u << (C & 31u);
     if (atomicOr(&b.live[C >> 5], bit) & bit) return;
+    b.nbr_n[C] = 0u;
+    if (!listed) return;
     const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
     const uint32_t x = atomicAdd(&b.cnt[C_FRONT * b.E + e], 1u);
     if (x < cap) b.front_list[b.edge_off[e] + x] = C;
@@ -615,7 +619,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                         for (uint32_t t = 0; t < have && wr < nw; ++t) b.nbr[first + wr++] = b.nbr[old + t];
                         if (wr < nw) {
                             b.nbr[first + wr++] = Bf;
-                            if (front) mark_reached(b, e, Bf);
+                            mark_reached(b, e, Bf, front);
                         }
                         for (uint32_t q = qf + 1; q < q1 && wr < nw && npass > 1; ++q) {
                             uint32_t B;
@@ -632,7 +636,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                             }
                             if (triplet_test(b, p, i, j, B, hi.x, hi.y, hj, hk, a)) {
                                 b.nbr[first + wr++] = B;
-                                if (front) mark_reached(b, e, B);
+                                mark_reached(b, e, B, front);
                             }
                         }
                         b.nbr_first[A] = first;
@@ -738,7 +742,7 @@ __global__ void __launch_bounds__(256, 4) k_connect_front(DevBatch b, DevParams 
                         if (pass) {
                             const uint32_t idx = start + cnt + __popc(pm & lt);
                             if (idx < (uint32_t)kFrontBuf) buf[idx] = C;
-                            if (front) mark_reached(b, e, C);
+                            mark_reached(b, e, C, front);
                         }
                         cnt += __popc(pm);
                     }

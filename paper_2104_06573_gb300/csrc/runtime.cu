@@ -544,7 +544,12 @@ static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
     if (t) CK(stage_mark(P->ev_stage[0], s, capturing));
     CK(cudaMemsetAsync(r + P->off.cnt, 0, 4 * (size_t)kCounters * P->E, s));
     if (p.drop_suffixes) CK(cudaMemsetAsync(r + P->off.mindepth, 0xFF, 4 * P->C, s));
-    CK(cudaMemsetAsync(r + P->off.nbr_n, 0, 4 * P->C, s));   // cells without edges stay at 0
+    // edge counts are written for root cells with edges and for every reached cell (0 until it
+    // gets out-edges); two readers need the others cleared: the walk over all root cells (when
+    // 2-hit paths count) and a junction with several out-layers appending to an in-cell's list
+    bool multi_out = false;
+    for (uint32_t l = 0; l < p.n_layers; ++l) multi_out |= p.n_out[l] > 1;
+    if (p.min_hits <= 2 || multi_out) CK(cudaMemsetAsync(r + P->off.nbr_n, 0, 4 * P->C, s));
     CK(cudaMemsetAsync(r + P->off.live, 0, 4 * ((P->C + 31) / 32), s));
     launch_sort(b, p, s, sms);
     if (t) CK(stage_mark(P->ev_stage[1], s, capturing));
@@ -898,14 +903,22 @@ static int region_debug(pxr_plan *P, uint32_t e, int what, uint32_t *buf, uint32
                 out.push_back(loc(co[c]));
             }
         } else {
-            std::vector<uint32_t> nf, nn;
+            std::vector<uint32_t> nf, nn, live, roots;
             if ((rc = d2h(nf, b.nbr_first + c0, nc)) || (rc = d2h(nn, b.nbr_n + c0, nc))) return rc;
             const uint32_t g0 = P->edge_off[e];
             const uint32_t ng = std::min(cnt[C_EDGES], P->edge_off[e + 1] - g0);
             std::vector<uint32_t> nb;
             if ((rc = d2h(nb, b.nbr + g0, ng))) return rc;
+            // edge lists are valid for reached cells (live bit) and for root cells with edges
+            // (the root list); other counts are not cleared
+            if ((rc = d2h(live, b.live + c0 / 32, (nc + 31) / 32))) return rc;
+            const uint32_t nr = std::min(cnt[C_ROOTS], P->edge_off[e + 1] - g0);
+            if ((rc = d2h(roots, b.root_list + g0, nr))) return rc;
+            std::vector<uint8_t> valid(nc, 0);
+            for (uint32_t c = 0; c < nc; ++c) valid[c] = (live[c / 32] >> (c % 32)) & 1u;
+            for (uint32_t A : roots) valid[A - c0] = 1;
             for (uint32_t c = 0; c < nc; ++c)
-                for (uint32_t k = 0; k < nn[c]; ++k) {
+                for (uint32_t k = 0; valid[c] && k < nn[c]; ++k) {
                     uint32_t B = nb[nf[c] - g0 + k] - c0;
                     out.push_back(loc(ci[c]));
                     out.push_back(loc(co[c]));
