@@ -819,11 +819,27 @@ static void canonical_order(const uint32_t *hits, size_t n, std::vector<uint32_t
 static int emit_tracks(const uint8_t *nh, const uint32_t *hits, const double *pt,
                        const double *phi, const double *cot, const double *dxy, const double *dz,
                        const double *chi2, const int8_t *q, const int8_t *st, size_t n,
-                       int32_t status, pxr_tracks *out)
+                       int32_t status, pxr_tracks *out, bool in_order = false)
 {
     out->n_tracks = (uint32_t)n;
     out->status = status;
     if (n > out->capacity) return fail(PXR_ETRUNC, "track capacity too small");
+    if (in_order) {                          // already canonical: plain copies
+        auto cp = [n](void *dst, const void *src, size_t sz) {
+            if (dst && n) std::memcpy(dst, src, sz * n);
+        };
+        cp(out->n_hits, nh, 1);
+        cp(out->hit_idx, hits, 4 * kMaxHits);
+        cp(out->pt, pt, 8);
+        cp(out->phi, phi, 8);
+        cp(out->cot_theta, cot, 8);
+        cp(out->dxy, dxy, 8);
+        cp(out->dz, dz, 8);
+        cp(out->chi2, chi2, 8);
+        cp(out->charge, q, 1);
+        cp(out->fit_status, st, 1);
+        return PXR_OK;
+    }
     std::vector<uint32_t> ord;
     canonical_order(hits, n, ord);
     for (size_t k = 0; k < n; ++k) {
@@ -982,15 +998,21 @@ extern "C" int pxr_fit_batch(pxr_ctx *ctx, uint32_t m, const uint8_t *nh, const 
 struct Ticket {
     uint64_t id = 0;
     int state = 0;                       // 0 pending, 1 running, 2 done
-    std::vector<float> x, y, z;
-    std::vector<uint16_t> layer;
+    // the event's hits, copied at submission: x, y, z (float) then layer (uint16), n of each
+    std::unique_ptr<uint8_t[]> hits;
+    uint32_t n = 0;
+    const float *x() const { return reinterpret_cast<const float *>(hits.get()); }
+    const float *y() const { return x() + n; }
+    const float *z() const { return x() + 2 * (size_t)n; }
+    const uint16_t *layer() const { return reinterpret_cast<const uint16_t *>(x() + 3 * (size_t)n); }
     uint32_t lcount[kMaxLayers + 1] = {};
     pxr_params params{};
     size_t bytes = 0;
     std::shared_ptr<Batch> batch;        // kept for pxr_fetch_debug
     uint32_t index = 0;
     int32_t status = PXR_OK;
-    HostTracks res;                      // results, copied out of the slot's pinned buffer
+    HostTracks res;                      // results in canonical order (copied from the slot's
+                                         // pinned buffer by the scheduler thread)
 };
 
 // Pinned host buffers of one in-flight slot, grown on demand and reused.
@@ -1052,7 +1074,16 @@ static cudaStream_t slot_stream(pxr_ctx *ctx, int slot)
 }
 
 // Build and launch one batch (scheduler thread, ctx->mu held).
-static int launch_batch(pxr_ctx *ctx, std::vector<std::shared_ptr<Ticket>> &items, int slot,
+// Releases a held lock for the scope (the scheduler's host copies run without ctx->mu, so that
+// submissions and fetches proceed meanwhile).
+struct Unlocked {
+    std::unique_lock<std::mutex> &lk;
+    explicit Unlocked(std::unique_lock<std::mutex> &l) : lk(l) { lk.unlock(); }
+    ~Unlocked() { lk.lock(); }
+};
+
+static int launch_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
+                        std::vector<std::shared_ptr<Ticket>> &items, int slot,
                         std::shared_ptr<Batch> &out)
 {
     auto B = std::make_shared<Batch>();
@@ -1069,7 +1100,7 @@ static int launch_batch(pxr_ctx *ctx, std::vector<std::shared_ptr<Ticket>> &item
     P->hit_off.assign(E + 1, 0);
     std::vector<uint32_t> lcount((size_t)E * (kMaxLayers + 1));
     for (uint32_t e = 0; e < E; ++e) {
-        P->hit_off[e + 1] = P->hit_off[e] + (uint32_t)items[e]->x.size();
+        P->hit_off[e + 1] = P->hit_off[e] + items[e]->n;
         std::memcpy(&lcount[(size_t)e * (kMaxLayers + 1)], items[e]->lcount,
                     sizeof(items[e]->lcount));
         B->reserved += items[e]->bytes;
@@ -1087,14 +1118,28 @@ static int launch_batch(pxr_ctx *ctx, std::vector<std::shared_ptr<Ticket>> &item
     P->region = ctx->arena.alloc(P->off.total);
     if (!P->region) return fail(PXR_EAGAIN, "arena fragmented");
     plan_bind(P);
-    // pinned staging of the head (inputs + small arrays), one H2D copy
+    // pinned staging of the head (inputs + small arrays), one H2D copy; the batch's tickets are
+    // out of the pending queue and reach no other thread before the batch is published
+    {
+    Unlocked unlocked(lk);
     char *h = sb.head.p;
-    for (uint32_t e = 0; e < E; ++e) {
-        size_t a = P->hit_off[e], n = items[e]->x.size();
-        std::memcpy(h + P->off.x + 4 * a, items[e]->x.data(), 4 * n);
-        std::memcpy(h + P->off.y + 4 * a, items[e]->y.data(), 4 * n);
-        std::memcpy(h + P->off.z + 4 * a, items[e]->z.data(), 4 * n);
-        std::memcpy(h + P->off.layer + 2 * a, items[e]->layer.data(), 2 * n);
+    auto stage = [&](uint32_t e0, uint32_t step) {
+        for (uint32_t e = e0; e < E; e += step) {
+            size_t a = P->hit_off[e], n = items[e]->n;
+            std::memcpy(h + P->off.x + 4 * a, items[e]->x(), 4 * n);
+            std::memcpy(h + P->off.y + 4 * a, items[e]->y(), 4 * n);
+            std::memcpy(h + P->off.z + 4 * a, items[e]->z(), 4 * n);
+            std::memcpy(h + P->off.layer + 2 * a, items[e]->layer(), 2 * n);
+        }
+    };
+    {
+        // large batches are staged by a few host threads
+        const uint32_t nth = P->N > (1u << 20) ? std::min<uint32_t>(
+            E, std::max(1u, std::min(8u, std::thread::hardware_concurrency() / 2))) : 1u;
+        std::vector<std::thread> th;
+        for (uint32_t w = 1; w < nth; ++w) th.emplace_back(stage, w, nth);
+        stage(0, nth);
+        for (auto &x : th) x.join();
     }
     const size_t e1 = 4 * (E + 1);
     std::memcpy(h + P->off.hit_off, P->hit_off.data(), e1);
@@ -1113,21 +1158,20 @@ static int launch_batch(pxr_ctx *ctx, std::vector<std::shared_ptr<Ticket>> &item
     CK(cudaMemcpyAsync(hev, P->db.out_evt, e1, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(hev + E + 1, P->db.cnt + C_FLAGS * E, 4 * E, cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(B->ev_counts, s));
+    }
     B->state = 1;
     for (uint32_t e = 0; e < E; ++e) {
         items[e]->state = 1;
         items[e]->index = e;
-        std::vector<float>().swap(items[e]->x);
-        std::vector<float>().swap(items[e]->y);
-        std::vector<float>().swap(items[e]->z);
-        std::vector<uint16_t>().swap(items[e]->layer);
+        items[e]->hits.reset();
     }
     out = B;
     return PXR_OK;
 }
 
 // Advance one in-flight batch; returns true when it changed state.
-static bool progress_batch(pxr_ctx *ctx, const std::shared_ptr<Batch> &Bp)
+static bool progress_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
+                           const std::shared_ptr<Batch> &Bp)
 {
     Batch &B = *Bp;
     pxr_plan *P = B.plan;
@@ -1174,25 +1218,63 @@ static bool progress_batch(pxr_ctx *ctx, const std::shared_ptr<Batch> &Bp)
     }
     if (B.state == 2 && cudaEventQuery(B.ev_data) == cudaSuccess) {
         const char *ho = sb.out.p;
+        std::vector<std::shared_ptr<Ticket>> ts(E);
         for (uint32_t e = 0; e < E; ++e) {
             auto it = ctx->tickets.find(B.ids[e]);
-            if (it == ctx->tickets.end()) continue;
-            Ticket &t = *it->second;
+            if (it != ctx->tickets.end()) ts[e] = it->second;
+        }
+        {
+        // the results reach no other thread before the tickets are marked done (below)
+        Unlocked unlocked(lk);
+        // events in parallel (a few host threads): the ordering is the heaviest host work of a
+        // batch
+        auto work = [&](uint32_t e0, uint32_t step) {
+        std::vector<uint32_t> ord;
+        for (uint32_t e = e0; e < E; e += step) {
+            if (!ts[e]) continue;
+            Ticket &t = *ts[e];
             const uint32_t a = hev[e], n = hev[e + 1] - a;
             t.res.resize(n);
             if (n) {
-                std::memcpy(t.res.nh.data(), ho + B.o_nh + a, n);
-                std::memcpy(t.res.hits.data(), ho + B.o_hits + 4 * (size_t)a * kMaxHits,
-                            4 * (size_t)n * kMaxHits);
-                std::memcpy(t.res.pt.data(), ho + B.o_pt + 8 * (size_t)a, 8 * n);
-                std::memcpy(t.res.phi.data(), ho + B.o_phi + 8 * (size_t)a, 8 * n);
-                std::memcpy(t.res.cot.data(), ho + B.o_cot + 8 * (size_t)a, 8 * n);
-                std::memcpy(t.res.dxy.data(), ho + B.o_dxy + 8 * (size_t)a, 8 * n);
-                std::memcpy(t.res.dz.data(), ho + B.o_dz + 8 * (size_t)a, 8 * n);
-                std::memcpy(t.res.chi2.data(), ho + B.o_chi2 + 8 * (size_t)a, 8 * n);
-                std::memcpy(t.res.q.data(), ho + B.o_q + a, n);
-                std::memcpy(t.res.st.data(), ho + B.o_st + a, n);
+                // canonical order here, on the scheduler thread, so that a fetch only copies
+                auto hp = [&](size_t off) { return ho + off; };
+                const uint32_t *hits = (const uint32_t *)hp(B.o_hits + 4 * (size_t)a * kMaxHits);
+                canonical_order(hits, n, ord);
+                const uint8_t *nh = (const uint8_t *)hp(B.o_nh + a);
+                const double *pt = (const double *)hp(B.o_pt + 8 * (size_t)a);
+                const double *phi = (const double *)hp(B.o_phi + 8 * (size_t)a);
+                const double *cot = (const double *)hp(B.o_cot + 8 * (size_t)a);
+                const double *dxy = (const double *)hp(B.o_dxy + 8 * (size_t)a);
+                const double *dz = (const double *)hp(B.o_dz + 8 * (size_t)a);
+                const double *chi2 = (const double *)hp(B.o_chi2 + 8 * (size_t)a);
+                const int8_t *q = (const int8_t *)hp(B.o_q + a);
+                const int8_t *st = (const int8_t *)hp(B.o_st + a);
+                for (uint32_t k = 0; k < n; ++k) {
+                    const uint32_t s_ = ord[k];
+                    t.res.nh[k] = nh[s_];
+                    std::memcpy(&t.res.hits[(size_t)k * kMaxHits], hits + (size_t)s_ * kMaxHits,
+                                4 * kMaxHits);
+                    t.res.pt[k] = pt[s_];
+                    t.res.phi[k] = phi[s_];
+                    t.res.cot[k] = cot[s_];
+                    t.res.dxy[k] = dxy[s_];
+                    t.res.dz[k] = dz[s_];
+                    t.res.chi2[k] = chi2[s_];
+                    t.res.q[k] = q[s_];
+                    t.res.st[k] = st[s_];
+                }
             }
+        }
+        };
+        const uint32_t nth = std::min<uint32_t>(E, std::max(1u, std::min(8u, std::thread::hardware_concurrency() / 2)));
+        std::vector<std::thread> th;
+        for (uint32_t w = 1; w < nth; ++w) th.emplace_back(work, w, nth);
+        work(0, nth);
+        for (auto &x : th) x.join();
+        }
+        for (uint32_t e = 0; e < E; ++e) {
+            if (!ts[e]) continue;
+            Ticket &t = *ts[e];
             t.status = flags_status(hev[E + 1 + e]);
             t.state = 2;
             if (ctx->cfg.keep_debug) t.batch = Bp;
@@ -1217,7 +1299,7 @@ static void scheduler(pxr_ctx *ctx)
     while (true) {
         bool moved = false;
         for (size_t k = 0; k < ctx->inflight.size();) {
-            moved |= progress_batch(ctx, ctx->inflight[k]);
+            moved |= progress_batch(ctx, lk, ctx->inflight[k]);
             if (ctx->inflight[k]->state == 3) ctx->inflight.erase(ctx->inflight.begin() + k);
             else ++k;
         }
@@ -1230,8 +1312,8 @@ static void scheduler(pxr_ctx *ctx)
             while (!ctx->pending.empty() && items.size() < ctx->cfg.max_batch_events) {
                 auto &t = ctx->tickets[ctx->pending.front()];
                 if (std::memcmp(&t->params, &p0, sizeof(pxr_params)) != 0) break;
-                if (!items.empty() && hits + t->x.size() > ctx->cfg.max_batch_hits) break;
-                hits += t->x.size();
+                if (!items.empty() && hits + t->n > ctx->cfg.max_batch_hits) break;
+                hits += t->n;
                 items.push_back(t);
                 ctx->pending.pop_front();
             }
@@ -1239,7 +1321,7 @@ static void scheduler(pxr_ctx *ctx)
             for (auto &b : ctx->inflight)
                 if (b->slot == 0) slot = 1;
             std::shared_ptr<Batch> B;
-            int rc = launch_batch(ctx, items, slot, B);
+            int rc = launch_batch(ctx, lk, items, slot, B);
             if (rc == PXR_EAGAIN && !ctx->inflight.empty()) {
                 // arena fragmented by the batch in flight: retry after it completes
                 for (auto it = items.rbegin(); it != items.rend(); ++it)
@@ -1346,12 +1428,27 @@ extern "C" int pxr_submit_event(pxr_ctx *ctx, const float *x, const float *y, co
     if (rc) return rc;
     if (n_hits > kLocalMask) return fail(PXR_EINVAL, "too many hits in one event");
     auto t = std::make_shared<Ticket>();
+    // copy the hits into the ticket (uninitialised storage), then check them and count them per
+    // layer (four interleaved counter sets keep the increments independent)
+    t->n = n_hits;
+    t->hits.reset(new uint8_t[14 * (size_t)n_hits + 16]);
+    float *tx = const_cast<float *>(t->x());
+    std::memcpy(tx, x, 4 * (size_t)n_hits);
+    std::memcpy(tx + n_hits, y, 4 * (size_t)n_hits);
+    std::memcpy(tx + 2 * (size_t)n_hits, z, 4 * (size_t)n_hits);
+    std::memcpy(const_cast<uint16_t *>(t->layer()), layer, 2 * (size_t)n_hits);
+    bool finite = true;
+    uint32_t bad_layer = 0;
+    uint32_t lc[4][kMaxLayers + 1] = {};
     for (uint32_t h = 0; h < n_hits; ++h) {
-        if (!std::isfinite(x[h]) || !std::isfinite(y[h]) || !std::isfinite(z[h]))
-            return fail(PXR_EINVAL, "non-finite hit coordinate");
-        if (layer[h] >= params->n_layers) return fail(PXR_EINVAL, "hit layer id >= n_layers");
-        t->lcount[layer[h]]++;
+        finite &= std::isfinite(x[h]) & std::isfinite(y[h]) & std::isfinite(z[h]);
+        const uint16_t l = layer[h];
+        bad_layer |= l >= params->n_layers;
+        lc[h & 3][l < kMaxLayers ? l : kMaxLayers]++;
     }
+    if (!finite) return fail(PXR_EINVAL, "non-finite hit coordinate");
+    if (bad_layer) return fail(PXR_EINVAL, "hit layer id >= n_layers");
+    for (int l = 0; l <= kMaxLayers; ++l) t->lcount[l] = lc[0][l] + lc[1][l] + lc[2][l] + lc[3][l];
     t->params = *params;
     t->bytes = event_bytes(*params, dp, t->lcount, n_hits);
     if (t->bytes > ctx->arena.size) return fail(PXR_ENOMEM, "event exceeds the memory budget");
@@ -1361,10 +1458,6 @@ extern "C" int pxr_submit_event(pxr_ctx *ctx, const float *x, const float *y, co
         ctx->sched_error.clear();
     }
     if (ctx->reserved + t->bytes > ctx->arena.size) return fail(PXR_EAGAIN, "memory budget full");
-    t->x.assign(x, x + n_hits);
-    t->y.assign(y, y + n_hits);
-    t->z.assign(z, z + n_hits);
-    t->layer.assign(layer, layer + n_hits);
     t->id = ctx->next_ticket++;
     ctx->reserved += t->bytes;
     ctx->tickets[t->id] = t;
@@ -1408,7 +1501,7 @@ extern "C" int pxr_fetch_tracks(pxr_ctx *ctx, uint64_t ticket, pxr_tracks *out)
     const HostTracks &r = t->res;
     int rc = emit_tracks(r.nh.data(), r.hits.data(), r.pt.data(), r.phi.data(), r.cot.data(),
                          r.dxy.data(), r.dz.data(), r.chi2.data(), r.q.data(), r.st.data(),
-                         r.size(), t->status, out);
+                         r.size(), t->status, out, true);
     if (rc) return rc;
     std::lock_guard<std::mutex> g(ctx->mu);
     ctx->tickets.erase(ticket);

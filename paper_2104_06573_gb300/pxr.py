@@ -54,12 +54,12 @@ class pxr_config(C.Structure):
 
 
 class pxr_tracks(C.Structure):
+    # the array fields are raw addresses (the C struct's typed pointers have the same layout)
     _fields_ = [("capacity", C.c_uint32), ("n_tracks", C.c_uint32), ("status", C.c_int32),
-                ("n_hits", C.POINTER(C.c_uint8)), ("hit_idx", C.POINTER(C.c_uint32)),
-                ("pt", C.POINTER(C.c_double)), ("phi", C.POINTER(C.c_double)),
-                ("cot_theta", C.POINTER(C.c_double)), ("dxy", C.POINTER(C.c_double)),
-                ("dz", C.POINTER(C.c_double)), ("chi2", C.POINTER(C.c_double)),
-                ("charge", C.POINTER(C.c_int8)), ("fit_status", C.POINTER(C.c_int8))]
+                ("n_hits", C.c_void_p), ("hit_idx", C.c_void_p), ("pt", C.c_void_p),
+                ("phi", C.c_void_p), ("cot_theta", C.c_void_p), ("dxy", C.c_void_p),
+                ("dz", C.c_void_p), ("chi2", C.c_void_p), ("charge", C.c_void_p),
+                ("fit_status", C.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -186,48 +186,46 @@ def pxr_params_init(preset: int) -> pxr_params:
 TRACK_FIELDS = ("pt", "phi", "cot_theta", "dxy", "dz", "chi2")
 
 
-class TrackBuffer:
-    """Host arrays for one event's tracks."""
+# per-track record layout of one fetch: (field, numpy dtype, values per track)
+_TRACK_LAYOUT = (("n_hits", np.uint8, 1), ("hit_idx", np.uint32, MAX_HITS),
+                 ("pt", np.float64, 1), ("phi", np.float64, 1), ("cot_theta", np.float64, 1),
+                 ("dxy", np.float64, 1), ("dz", np.float64, 1), ("chi2", np.float64, 1),
+                 ("charge", np.int8, 1), ("fit_status", np.int8, 1))
 
-    def __init__(self, capacity: int):
-        self.capacity = capacity
-        self.n_hits = np.zeros(capacity, np.uint8)
-        self.hit_idx = np.zeros((capacity, MAX_HITS), np.uint32)
-        self.cols = {k: np.zeros(capacity, np.float64) for k in TRACK_FIELDS}
-        self.charge = np.zeros(capacity, np.int8)
-        self.fit_status = np.zeros(capacity, np.int8)
-        t = pxr_tracks()
-        t.capacity = capacity
-        t.n_hits = self.n_hits.ctypes.data_as(C.POINTER(C.c_uint8))
-        t.hit_idx = self.hit_idx.ctypes.data_as(C.POINTER(C.c_uint32))
-        for k in TRACK_FIELDS:
-            setattr(t, k, self.cols[k].ctypes.data_as(C.POINTER(C.c_double)))
-        t.charge = self.charge.ctypes.data_as(C.POINTER(C.c_int8))
-        t.fit_status = self.fit_status.ctypes.data_as(C.POINTER(C.c_int8))
-        self.c = t
 
-    def result(self) -> dict:
-        n = self.c.n_tracks
-        out = {"n": n, "status": self.c.status, "n_hits": self.n_hits[:n].copy(),
-               "hit_idx": self.hit_idx[:n].copy(), "charge": self.charge[:n].copy(),
-               "fit_status": self.fit_status[:n].copy()}
-        for k in TRACK_FIELDS:
-            out[k] = self.cols[k][:n].copy()
+def _read_tracks(call, holder=None) -> dict:
+    """Ask for the track count, then fill arrays of exactly that size (one allocation, the
+    library writes straight into it; nothing is copied afterwards)."""
+    t = pxr_tracks()
+    t.capacity = 0
+    rc = call(t)
+    if rc not in (OK, ETRUNC):
+        _check(rc)
+    n = t.n_tracks
+    if rc == OK:                                        # no tracks: the call is complete
+        out = {"n": 0, "status": t.status}
+        for name, dt, k in _TRACK_LAYOUT:
+            out[name] = np.zeros((0, k) if k > 1 else 0, dt)
         return out
-
-
-def _read_tracks(call, holder) -> dict:
-    """Fill a reusable TrackBuffer (grown on PXR_ETRUNC) and return copies of the results."""
     while True:
-        buf = holder.get("buf")
-        if buf is None:
-            buf = holder["buf"] = TrackBuffer(8192)
-        rc = call(buf.c)
-        if rc == ETRUNC:
-            holder["buf"] = TrackBuffer(max(2 * buf.capacity, buf.c.n_tracks + 16))
+        sizes = [np.dtype(dt).itemsize * k * max(n, 1) for _, dt, k in _TRACK_LAYOUT]
+        offs = np.concatenate([[0], np.cumsum([(z + 15) // 16 * 16 for z in sizes])])
+        buf = np.empty(int(offs[-1]), np.uint8)
+        base = buf.ctypes.data
+        t = pxr_tracks()
+        t.capacity = n
+        for (name, _, _), off in zip(_TRACK_LAYOUT, offs[:-1]):
+            setattr(t, name, base + int(off))
+        rc = call(t)
+        if rc == ETRUNC:                                # (the count cannot grow; defensive)
+            n = t.n_tracks
             continue
         _check(rc)
-        return buf.result()
+        out = {"n": n, "status": t.status}
+        for (name, dt, k), off in zip(_TRACK_LAYOUT, offs[:-1]):
+            a = np.frombuffer(buf, dt, n * k, int(off))
+            out[name] = a.reshape(n, k) if k > 1 else a
+        return out
 
 
 def _read_debug(call, what, cap_hint=1 << 16) -> np.ndarray:
@@ -264,7 +262,6 @@ class Context:
         _check(L.pxr_create(C.byref(cfg), C.byref(h)))
         self.h = h
         self._arena_ref = arena          # keep caller memory alive
-        self._tracks = {}                # reusable host buffer for fetches
 
     def close(self):
         if self.h:
@@ -310,8 +307,7 @@ class Context:
         return [done[i] for i in range(n.value)]
 
     def pxr_fetch_tracks(self, ticket: int) -> dict:
-        return _read_tracks(lambda t: load().pxr_fetch_tracks(self.h, ticket, C.byref(t)),
-                            self._tracks)
+        return _read_tracks(lambda t: load().pxr_fetch_tracks(self.h, ticket, C.byref(t)))
 
     def pxr_fetch_debug(self, ticket: int, what: int) -> np.ndarray:
         return _read_debug(lambda b, cap, n: load().pxr_fetch_debug(self.h, ticket, what, b, cap,
@@ -341,14 +337,13 @@ class Plan:
         self.h = h
         self.ctx = ctx
         self.n_events = len(off) - 1
-        self._tracks = {}
         self._refs = (x, y, z, layer)      # the caller's device inputs stay alive
 
     def pxr_plan_run(self, stream=None):
         _check(load().pxr_plan_run(self.h, ptr(stream)))
 
     def pxr_plan_tracks(self, e: int) -> dict:
-        return _read_tracks(lambda t: load().pxr_plan_tracks(self.h, e, C.byref(t)), self._tracks)
+        return _read_tracks(lambda t: load().pxr_plan_tracks(self.h, e, C.byref(t)))
 
     def pxr_plan_debug(self, e: int, what: int) -> np.ndarray:
         return _read_debug(lambda b, cap, n: load().pxr_plan_debug(self.h, e, what, b, cap, n),
