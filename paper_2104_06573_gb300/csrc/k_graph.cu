@@ -58,18 +58,28 @@ __device__ __noinline__ bool doublet_exact(const double *r64, uint32_t g, uint32
     return doublet64((double)xi, (double)yi, r64[g], (double)xo, (double)yo, r64[o], cw);
 }
 
+// The kernels are instantiated per cut mode.  F64 (FP64-cut mode): a candidate is accepted or
+// rejected by the FP64 formula, inline, except when the FP32 evaluation rejects it outside its
+// rigorous error band (the FP64 formula rejects it too; most candidates end there).  Otherwise
+// FP32 decides outside the band and the out-of-line FP64 formula inside it.
+template <bool F64>
 __device__ __forceinline__ bool doublet_test(const DevBatch &b, const DevParams &p, uint32_t g,
                                              float4 hi, uint32_t o, float4 ho)
 {
-    if (p.cut_mode == CUT_FP32) {
-        int r = doublet32(hi, ho, p.cw32);
+    if constexpr (F64) {
+        if (doublet32(hi, ho, p.cw32) == 0) return false;
+        return doublet64((double)hi.x, (double)hi.y, b.r64[g], (double)ho.x, (double)ho.y,
+                         b.r64[o], p.cw);
+    } else {
+        const int r = doublet32(hi, ho, p.cw32);
         if (r >= 0) return r == 1;
+        return doublet_exact(b.r64, g, o, hi.x, hi.y, ho.x, ho.y, p.cw);
     }
-    return doublet_exact(b.r64, g, o, hi.x, hi.y, ho.x, ho.y, p.cw);
 }
 
 // Compact form (allocation-free entry point): passing pairs only, counted first, then written
 // from the ballot masks, so the cells of an inner hit are contiguous.
+template <bool F64>
 __global__ void __launch_bounds__(256) k_doublets_compact(DevBatch b, DevParams p, uint32_t slots)
 {
     const uint32_t lane = threadIdx.x & 31u;
@@ -101,7 +111,7 @@ __global__ void __launch_bounds__(256) k_doublets_compact(DevBatch b, DevParams 
             if ((uint32_t)k * 32u < nc) {
                 uint32_t c = (uint32_t)k * 32u + lane;
                 bool pass = false;
-                if (c < nc) { const uint32_t o = w.pos(c); pass = doublet_test(b, p, g, hi, o, b.hs[o]); }
+                if (c < nc) { const uint32_t o = w.pos(c); pass = doublet_test<F64>(b, p, g, hi, o, b.hs[o]); }
                 masks[k] = __ballot_sync(0xFFFFFFFFu, pass);
                 count += __popc(masks[k]);
             }
@@ -109,7 +119,7 @@ __global__ void __launch_bounds__(256) k_doublets_compact(DevBatch b, DevParams 
         for (uint32_t c0 = kMaxIt * 32u; c0 < nc; c0 += 32u) {
             uint32_t c = c0 + lane;
             bool pass = false;
-                if (c < nc) { const uint32_t o = w.pos(c); pass = doublet_test(b, p, g, hi, o, b.hs[o]); }
+            if (c < nc) { const uint32_t o = w.pos(c); pass = doublet_test<F64>(b, p, g, hi, o, b.hs[o]); }
             count += __popc(__ballot_sync(0xFFFFFFFFu, pass));
         }
 
@@ -143,7 +153,7 @@ __global__ void __launch_bounds__(256) k_doublets_compact(DevBatch b, DevParams 
         for (uint32_t c0 = kMaxIt * 32u; c0 < nc; c0 += 32u) {
             uint32_t c = c0 + lane;
             uint32_t o = c < nc ? w.pos(c) : 0u;
-            bool pass = c < nc && doublet_test(b, p, g, hi, o, b.hs[o]);
+            bool pass = c < nc && doublet_test<F64>(b, p, g, hi, o, b.hs[o]);
             uint32_t m = __ballot_sync(0xFFFFFFFFu, pass);
             if (pass) {
                 uint32_t idx = run + __popc(m & lt_mask);
@@ -164,6 +174,7 @@ __global__ void __launch_bounds__(256) k_doublets_compact(DevBatch b, DevParams 
 // owning lane: the lanes test 32 consecutive candidates per step (coalesced float4 loads) and
 // write the outer hit, or kNone where the cut fails, to the candidate's entry.
 
+template <bool F64>
 __global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint32_t slots)
 {
     const uint32_t FULL = 0xFFFFFFFFu;
@@ -251,7 +262,7 @@ __global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint3
             uint32_t np = 0;
             for (uint32_t c = lane; c < wk; c += 32) {
                 const uint32_t o = c < a1 ? a0 + c : a2 + (c - a1);
-                const bool pass = doublet_test(b, p, gk, hk, o, __ldg(&b.hs[o]));
+                const bool pass = doublet_test<F64>(b, p, gk, hk, o, __ldg(&b.hs[o]));
                 b.cell_in[fk + c] = gk;
                 b.cell_out[fk + c] = pass ? o : kNone;
                 np += pass;
@@ -273,7 +284,10 @@ void launch_doublets(const DevBatch &b, const DevParams &p, cudaStream_t s, int 
     const uint64_t cap = (uint64_t)sms * p.grid_per_sm[1];
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
-    k_doublets<<<(unsigned)blocks, 256, 0, s>>>(b, p, slots);
+    if (p.cut_mode == CUT_FP64)
+        k_doublets<true><<<(unsigned)blocks, 256, 0, s>>>(b, p, slots);
+    else
+        k_doublets<false><<<(unsigned)blocks, 256, 0, s>>>(b, p, slots);
 }
 
 void launch_doublets_compact(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms)
@@ -285,7 +299,10 @@ void launch_doublets_compact(const DevBatch &b, const DevParams &p, cudaStream_t
     uint64_t cap = (uint64_t)sms * 16;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
-    k_doublets_compact<<<(unsigned)blocks, 256, 0, s>>>(b, p, slots);
+    if (p.cut_mode == CUT_FP64)
+        k_doublets_compact<true><<<(unsigned)blocks, 256, 0, s>>>(b, p, slots);
+    else
+        k_doublets_compact<false><<<(unsigned)blocks, 256, 0, s>>>(b, p, slots);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -314,19 +331,30 @@ __device__ __noinline__ bool triplet_exact(const double *r64, const uint32_t *ce
 // Exact decision for the triplet (i, j, k), k the outer hit of the out-cell B = (j, k):
 // r-z alignment, then DCA.  FP32 mode decides in float when outside the guard bands and takes
 // the FP64 formulas otherwise (FP64 mode always).
+template <bool F64>
 __device__ __forceinline__ bool triplet_test(const DevBatch &b, const DevParams &p, uint32_t i,
                                              uint32_t j, uint32_t B, float xi, float yi,
                                              float4 hj, float4 hk, const RZ32 &a)
 {
-    int th = -1, dc = -1;
-    if (p.cut_mode == CUT_FP32) {
-        th = theta32(a, rz32(hj, hk), p.theta32);
+    if constexpr (F64) {
+        if (theta32(a, rz32(hj, hk), p.theta32) == 0) return false;
+        const uint32_t k = b.cell_out[B];
+        const double zi = (double)b.hs[i].z, zj = (double)hj.z, zk = (double)hk.z;
+        const double ri = b.r64[i], rj = b.r64[j], rk = b.r64[k];
+        if (!theta64(ri, zi, rj, zj, rk, zk, seglen64(ri, zi, rj, zj), seglen64(rj, zj, rk, zk),
+                     p.theta))
+            return false;
+        if (dca32(xi, yi, hj.x, hj.y, hk.x, hk.y, p.dca32) == 0) return false;
+        return dca64((double)xi, (double)yi, (double)hj.x, (double)hj.y, (double)hk.x,
+                     (double)hk.y) <= p.dca;
+    } else {
+        const int th = theta32(a, rz32(hj, hk), p.theta32);
         if (th == 0) return false;
-        dc = dca32(xi, yi, hj.x, hj.y, hk.x, hk.y, p.dca32);
+        const int dc = dca32(xi, yi, hj.x, hj.y, hk.x, hk.y, p.dca32);
         if (th == 1 && dc >= 0) return dc == 1;
+        return triplet_exact(b.r64, b.cell_out, b.hs, i, j, B, xi, yi, hj, hk, th < 0, dc,
+                             p.theta, p.dca);
     }
-    return triplet_exact(b.r64, b.cell_out, b.hs, i, j, B, xi, yi, hj, hk, th < 0, dc, p.theta,
-                         p.dca);
 }
 
 // Conservative interval of the free coordinate (z on a barrel layer, r on a disk) reachable from
@@ -397,6 +425,7 @@ __device__ __forceinline__ void mark_reached(const DevBatch &b, uint32_t e, uint
     else atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
 }
 
+template <bool F64>
 __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevParams p,
                                                                 uint32_t layer_mask)
 {
@@ -528,7 +557,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                         i = w.pos(c);
                         hi = b.hs[i];
                         itm = b.item[(size_t)i * kMaxOut + slot_i];   // with hs[i]: one round trip
-                        if (doublet_test(b, p, i, hi, j, hj)) {
+                        if (doublet_test<F64>(b, p, i, hi, j, hj)) {
                             a = rz32(hi, hj);
                             q1 = nq;
                             float lo, hi_;
@@ -571,7 +600,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                             if (k == kNone) continue;
                             hk = b.hs[k];
                         }
-                        if (triplet_test(b, p, i, j, B, hi.x, hi.y, hj, hk, a)) {
+                        if (triplet_test<F64>(b, p, i, j, B, hi.x, hi.y, hj, hk, a)) {
                             if (npass == 0) { qf = q; Bf = B; }
                             ++npass;
                         }
@@ -634,7 +663,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                                 if (k == kNone) continue;
                                 hk = b.hs[k];
                             }
-                            if (triplet_test(b, p, i, j, B, hi.x, hi.y, hj, hk, a)) {
+                            if (triplet_test<F64>(b, p, i, j, B, hi.x, hi.y, hj, hk, a)) {
                                 b.nbr[first + wr++] = B;
                                 mark_reached(b, e, B, front);
                             }
@@ -656,7 +685,10 @@ void launch_connect(const DevBatch &b, const DevParams &p, uint32_t layer_mask, 
     uint64_t cap = (uint64_t)sms * p.grid_per_sm[2];
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
-    k_connect<<<(unsigned)blocks, kConnWarps * 32, 0, s>>>(b, p, layer_mask);
+    if (p.cut_mode == CUT_FP64)
+        k_connect<true><<<(unsigned)blocks, kConnWarps * 32, 0, s>>>(b, p, layer_mask);
+    else
+        k_connect<false><<<(unsigned)blocks, kConnWarps * 32, 0, s>>>(b, p, layer_mask);
 }
 
 // Sparse CA pass over the frontier: cells B = (j, k) that were reached (have an in-edge), are not
@@ -671,6 +703,7 @@ void launch_connect(const DevBatch &b, const DevParams &p, uint32_t layer_mask, 
 constexpr int kFrontBuf = 256;
 constexpr int kFrontU = 3;      // entries per lane whose loads are issued together
 
+template <bool F64>
 __global__ void __launch_bounds__(256, 4) k_connect_front(DevBatch b, DevParams p, uint32_t total,
                                                           uint32_t layer_mask)
 {
@@ -737,7 +770,7 @@ __global__ void __launch_bounds__(256, 4) k_connect_front(DevBatch b, DevParams 
                         if (c0 + 32u * u >= it.y) break;                   // uniform
                         const uint32_t C = it.x + c0 + 32u * u + lane;
                         const bool pass = l[u] != kNone &&
-                            triplet_test(b, p, jq, kq, C, hjq.x, hjq.y, hkq, hl[u], a);
+                            triplet_test<F64>(b, p, jq, kq, C, hjq.x, hjq.y, hkq, hl[u], a);
                         const uint32_t pm = __ballot_sync(FULL, pass);
                         if (pass) {
                             const uint32_t idx = start + cnt + __popc(pm & lt);
@@ -804,7 +837,7 @@ __global__ void __launch_bounds__(256, 4) k_connect_front(DevBatch b, DevParams 
                     if (c0 + lane < it.y) {
                         const uint32_t l = b.cell_out[C];
                         if (l != kNone)
-                            pass = triplet_test(b, p, jq, kq, C, hjq.x, hjq.y, hkq, b.hs[l], a);
+                            pass = triplet_test<F64>(b, p, jq, kq, C, hjq.x, hjq.y, hkq, b.hs[l], a);
                     }
                     const uint32_t pm = __ballot_sync(FULL, pass);
                     const uint32_t idx = run + __popc(pm & lt);
@@ -823,7 +856,11 @@ void launch_connect_front(const DevBatch &b, const DevParams &p, uint32_t total,
     const uint32_t chunks = total / kChunk;
     const uint32_t cap = (uint32_t)sms * p.grid_per_sm[2];
     if (chunks == 0) return;
-    k_connect_front<<<chunks < cap ? chunks : cap, 256, 0, s>>>(b, p, total, layer_mask);
+    const uint32_t grid = chunks < cap ? chunks : cap;
+    if (p.cut_mode == CUT_FP64)
+        k_connect_front<true><<<grid, 256, 0, s>>>(b, p, total, layer_mask);
+    else
+        k_connect_front<false><<<grid, 256, 0, s>>>(b, p, total, layer_mask);
 }
 
 // ------------------------------------------------------------------------------------------
