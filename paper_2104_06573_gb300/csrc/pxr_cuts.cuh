@@ -133,7 +133,8 @@ __device__ __forceinline__ int theta32(const RZ32 &a, const RZ32 &b, float t32)
 // (N = (|u|^2 v_y - |v|^2 u_y, |v|^2 u_x - |u|^2 v_x)), dca = |G| / H, so dca <= d iff
 // |G| <= d H.  Each of G and H is a polynomial of at most 14 rounded operations on inputs with
 // relative error u; its error is below gamma_16 times the same polynomial on absolute values
-// (Gabs, Habs).  The band takes twice that.
+// (Gabs, Habs).  The band takes twice that.  Habs bounds each square root of a sum of two
+// squares by the sum of the two absolute values (larger, so the band stays an upper bound).
 __device__ __forceinline__ int dca32(float xi, float yi, float xj, float yj, float xk, float yk,
                                      float d)
 {
@@ -155,7 +156,7 @@ __device__ __forceinline__ int dca32(float xi, float yi, float xj, float yj, flo
     float H = __fadd_rn(__fsqrt_rn(__fmaf_rn(qx, qx, __fmul_rn(qy, qy))),
                         __fsqrt_rn(__fmaf_rn(Nx, Nx, __fmul_rn(Ny, Ny))));
     float qxa = fabsf(xi) * Dabs + Nxa, qya = fabsf(yi) * Dabs + Nya;
-    float Habs = sqrtf(qxa * qxa + qya * qya) + sqrtf(Nxa * Nxa + Nya * Nya);
+    float Habs = qxa + qya + Nxa + Nya;
     float q = __fsub_rn(fabsf(G), __fmul_rn(d, H));
     float B = 2.0f * 16.0f * kU * (Gabs + d * Habs) * 1.01f;
     if (!(Gabs < 1e30f) || !(Habs < 1e30f)) return -1;
