@@ -398,17 +398,6 @@ __device__ __forceinline__ int ford(float f)
 }
 __device__ __forceinline__ float funord(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
 
-// One warp per junction hit j.  For each out-layer slot, j's out-cells (j, k) are staged in
-// shared memory (k's coordinates) and counting-sorted by the free coordinate of k (z on barrel
-// layers, r on disks) into local bins over the staged range.  The in-cells (i, j) are found 32
-// at a time, one per lane, by scanning i over j's phi window on the inner layer with the doublet
-// cut; each lane computes the cone of r-z directions that can pass the alignment cut, the bins it
-// reaches (a conservative window: the exact cuts decide) and tests those out-cells itself (j's
-// entries of failed candidates are skipped).  The in-cell's index is j's rank in i's window
-// (loaded alongside the tests); lanes with passes append their edges through one atomic per
-// warp.  A slot with more than kStage entries is tested from global memory.  Loads that do not depend on one another are issued together (the
-// junction's own records, its first out-cell list and inner window) so that a junction waits on
-// few memory round trips.
 // Mark cell C as reached (it has an in-edge).  The first marker clears C's edge count (the walk
 // reads it; a later level writes the count if C gets out-edges) and, when C is `listed` (a
 // non-root cell whose outer hit starts further pairs), appends it to the event's frontier list,
@@ -416,15 +405,34 @@ __device__ __forceinline__ float funord(int i) { return __int_as_float(i >= 0 ? 
 __device__ __forceinline__ void mark_reached(const DevBatch &b, uint32_t e, uint32_t C, bool listed)
 {
     const uint32_t bit = 1u << (C & 31u);
+    if (!listed) {
+        // nothing to append: the mark needs no answer, and clearing the count again is harmless
+        // (C's own edges are written by a later launch)
+        atomicOr(&b.live[C >> 5], bit);
+        b.nbr_n[C] = 0u;
+        return;
+    }
     if (atomicOr(&b.live[C >> 5], bit) & bit) return;
     b.nbr_n[C] = 0u;
-    if (!listed) return;
     const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
     const uint32_t x = atomicAdd(&b.cnt[C_FRONT * b.E + e], 1u);
     if (x < cap) b.front_list[b.edge_off[e] + x] = C;
     else atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
 }
 
+// One warp per junction hit j.  For each out-layer slot, j's out-cells (j, k) are staged in
+// shared memory (k's coordinates) and counting-sorted by the free coordinate of k (z on barrel
+// layers, r on disks) into local bins over the staged range.  The in-cells (i, j) are found 32
+// at a time, one per lane, by scanning i over j's phi window on the inner layer with the doublet
+// cut; each lane computes the cone of r-z directions that can pass the alignment cut, the bins it
+// reaches (a conservative window: the exact cuts decide) and tests those out-cells itself (j's
+// entries of failed candidates are skipped).  The in-cell's index is j's rank in i's window
+// (loaded alongside the tests).  Lanes with passes append their edges: the round's returning
+// atomics (edge and root-list reservations, frontier slots, reached marks) are issued together,
+// so a round waits on one atomic round trip.  A slot with more than kStage entries is tested
+// from global memory.  Loads that do not depend on one another are issued together (the
+// junction's own records, its first out-cell list and inner window) so that a junction waits on
+// few memory round trips.
 template <bool F64>
 __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevParams p,
                                                                 uint32_t layer_mask)
@@ -623,33 +631,45 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                         if (lane >= (uint32_t)o) incl += t;
                     }
                     const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-                    uint32_t base = 0;
+                    // the round's returning atomics are issued together: the edge reservation, the
+                    // root-list reservation (every in-cell of this pass is a root cell; it is listed
+                    // with its first edges) and the reached mark of each lane's first pass (set
+                    // before the capacity is known: under overflow, flagged, a marked cell may
+                    // lack its edge, which only costs work)
+                    const bool first_root = ok && have == 0;
+                    const uint32_t rm = __ballot_sync(0xFFFFFFFFu, first_root);
+                    const uint32_t fm = __ballot_sync(0xFFFFFFFFu, ok && front);
+                    uint32_t base = 0, rbase = 0, fbase = 0, was = 0;
+                    const uint32_t bit = 1u << (Bf & 31u);
                     if (lane == 0 && tot) base = atomicAdd(&b.cnt[C_EDGES * b.E + e], tot);
+                    if (lane == 0 && rm) rbase = atomicAdd(&b.cnt[C_ROOTS * b.E + e], __popc(rm));
+                    if (lane == 0 && fm) fbase = atomicAdd(&b.cnt[C_FRONT * b.E + e], __popc(fm));
+                    if (ok) was = atomicOr(&b.live[Bf >> 5], bit);
+                    const uint32_t lt = (1u << lane) - 1u;
                     base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                    rbase = __shfl_sync(0xFFFFFFFFu, rbase, 0) + __popc(rm & lt);
+                    fbase = __shfl_sync(0xFFFFFFFFu, fbase, 0) + __popc(fm & lt);
                     const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
                     const uint32_t my0 = base + incl - need;
                     const uint32_t nw = !ok || my0 >= cap ? 0u : min(need, cap - my0);
-                    // root cells that get their first edges go to the event's root list
-                    if ((p.root_mask >> Li) & 1u) {
-                        const bool first = have == 0 && nw > 0;
-                        const uint32_t rm = __ballot_sync(0xFFFFFFFFu, first);
-                        uint32_t rbase = 0;
-                        if (lane == 0 && rm) rbase = atomicAdd(&b.cnt[C_ROOTS * b.E + e], __popc(rm));
-                        rbase = __shfl_sync(0xFFFFFFFFu, rbase, 0) + __popc(rm & ((1u << lane) - 1u));
-                        if (first) {
-                            if (rbase < cap) b.root_list[b.edge_off[e] + rbase] = A;
-                            else atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
-                        }
+                    // a cell reached for the first time: its edge count cleared and, if its outer
+                    // hit starts further pairs, the frontier entry (one reservation per warp)
+                    const bool fresh = ok && !(was & bit);
+                    if (fresh) b.nbr_n[Bf] = 0u;
+                    if (ok && front) {
+                        if (fbase < cap) b.front_list[b.edge_off[e] + fbase] = fresh ? Bf : kNone;
+                        else atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+                    }
+                    if (first_root) {
+                        if (rbase < cap) b.root_list[b.edge_off[e] + rbase] = A;
+                        else atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
                     }
                     if (ok) {
                         if (nw < need) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
                         const uint32_t first = b.edge_off[e] + my0;
                         uint32_t wr = 0;
                         for (uint32_t t = 0; t < have && wr < nw; ++t) b.nbr[first + wr++] = b.nbr[old + t];
-                        if (wr < nw) {
-                            b.nbr[first + wr++] = Bf;
-                            mark_reached(b, e, Bf, front);
-                        }
+                        if (wr < nw) b.nbr[first + wr++] = Bf;
                         for (uint32_t q = qf + 1; q < q1 && wr < nw && npass > 1; ++q) {
                             uint32_t B;
                             float4 hk;
@@ -725,6 +745,9 @@ __global__ void __launch_bounds__(256, 4) k_connect_front(DevBatch b, DevParams 
         bool valid = x - x0 < nf;
         if (valid) {
             B = b.front_list[x];
+            valid = B != kNone;                                    // slot of a cell reached twice
+        }
+        if (valid) {
             j = b.cell_in[B];
             k = b.cell_out[B];
             hj = b.hs[j];

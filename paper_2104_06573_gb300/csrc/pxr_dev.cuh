@@ -103,7 +103,8 @@ struct DevBatch {
     uint32_t *root_list;                // [edges] per event: root cells that have out-edges
     uint32_t *live;                     // [entries / 32] bit per cell: has an in-edge
     uint32_t *front_list;               // [edges] per event: non-root cells with in-edges whose
-                                        //   outer hit starts further pairs (the sparse CA input)
+                                        //   outer hit starts further pairs (the sparse CA input;
+                                        //   kNone: a slot reserved for a cell already listed)
     uint32_t *front_snap;               // [E] frontier lengths when a sparse pass starts (the pass
                                         //   appends for later levels while it reads)
     // ntuplets
