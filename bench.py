@@ -120,7 +120,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -130,6 +130,12 @@ class Clocks:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def wait_first(self, timeout=3.0):
+        """Block until the sampler has printed its first line (it takes a moment to start)."""
+        t0 = time.time()
+        while self.proc and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.01)
 
     def stop(self):
         if not self.proc:
@@ -276,6 +282,7 @@ def run_pxr(args, rank, world, local):
     ev = step_events(args.steps)
     clocks = Clocks(local)
     clocks.start()
+    clocks.wait_first()
     shard.barrier()
     torch.cuda.synchronize()
     stage = np.zeros(5)

@@ -388,11 +388,15 @@ __global__ void __launch_bounds__(256, 2) k_fit(DevBatch b, DevParams p)
 
 void launch_fit(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
 {
-    uint64_t blocks = ((uint64_t)total + 255) / 256;
-    uint64_t cap = (uint64_t)sms * p.grid_per_sm[5];
+    // a few hundred fits are bound by the FP64 pipe of the SMs they run on: small batches take
+    // smaller blocks, so that their tracks spread over more SMs
+    uint32_t tpb = 32;
+    while (tpb < 256 && (uint64_t)tpb * sms < total) tpb *= 2;
+    uint64_t blocks = ((uint64_t)total + tpb - 1) / tpb;
+    uint64_t cap = (uint64_t)sms * p.grid_per_sm[5] * (256 / tpb);
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
-    k_fit<<<(unsigned)blocks, 256, 0, s>>>(b, p);
+    k_fit<<<(unsigned)blocks, tpb, 0, s>>>(b, p);
 }
 
 // Fit-only path: m ntuplets given directly.
