@@ -175,6 +175,45 @@ def test_ragged_batch_and_edge_cases(ctx, orc, cut):
         check_event(orc, ev, P, g)
 
 
+def degenerate_events():
+    """Inputs at the method's degenerate points: every hit given twice (identical cells and
+    triplets side by side); straight radial tracks exactly on the phi = +-pi seam (y = +0.0 and
+    y = -0.0 put the same direction in the last and the first azimuth bin) and at phi = 0, whose
+    hits are exactly collinear (the DCA's line branch; the fit reports no circle, status 1, on
+    both sides); and a barrel event rotated so that one track's hits straddle the seam."""
+    R = np.array(synth.BARREL_R, np.float64)
+    base = synth.event_barrel(7, 60)
+    dup = tuple(np.concatenate([a, a]) for a in ev_tuple(base))
+    xs, ys, zs, ls = [], [], [], []
+    for y0, x_sign, cot, z0 in [(0.0, -1.0, 0.3, 1.0), (-0.0, -1.0, -0.2, -2.0),
+                                (0.0, 1.0, 0.1, 0.5)]:
+        for lid, r in enumerate(R):
+            xs.append(x_sign * r); ys.append(y0); zs.append(z0 + cot * r); ls.append(lid)
+    straight = (np.array(xs, np.float32), np.array(ys, np.float32), np.array(zs, np.float32),
+                np.array(ls, np.uint16))
+    ev = synth.event_barrel(9, 80)
+    k = int(np.flatnonzero(ev.layer == 1)[0])
+    a = np.pi - np.arctan2(float(ev.y[k]), float(ev.x[k]))      # hit k onto phi = pi
+    c, sn = np.cos(a), np.sin(a)
+    x64, y64 = ev.x.astype(np.float64), ev.y.astype(np.float64)
+    seam = ((c * x64 - sn * y64).astype(np.float32), (sn * x64 + c * y64).astype(np.float32),
+            ev.z.copy(), ev.layer.copy())
+    return [dup, straight, seam]
+
+
+@pytest.mark.parametrize("cut", [pxr.CUT_FP64, pxr.CUT_FP32])
+def test_degenerate_inputs(ctx, orc, cut):
+    P = synth.params_barrel_quadruplets()
+    events = degenerate_events()
+    got = run_plan(ctx, events, P, cut)
+    for ev, g in zip(events, got):
+        check_event(orc, ev, P, g)
+    # the straight tracks are found on both sides of the seam, and the rotated event's tracks too
+    assert len(gpu_tuples(got[1]["tracks"])) >= 3
+    phi = np.arctan2(events[2][1], events[2][0])
+    assert np.any(np.abs(np.abs(phi) - np.pi) < 0.02)
+
+
 def test_graph_equals_direct_and_bin_counts(ctx, orc):
     """Graph replay and direct launches agree; the result does not depend on the bin count."""
     P = synth.params_phase1()
