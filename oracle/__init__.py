@@ -6,7 +6,8 @@ the synthetic event generator.
 
 `build()` compiles `pxr_oracle.c` with gcc (`-O2 -ffp-contract=off`: no fused multiply-add, so that
 every cut quantity is the exact IEEE operation sequence written in the C source).  The functions
-below are thin ctypes wrappers; all arithmetic lives in the C file.
+below are thin ctypes wrappers; all arithmetic lives in the C file, except the track selection
+(`select_tracks`), written here in plain Python from its definition.
 """
 from __future__ import annotations
 
@@ -254,3 +255,54 @@ def reconstruct(x, y, z, layer, params, stage: int = 4) -> dict:
         return out
     finally:
         L.orc_free(rp)
+
+
+# -- track selection -------------------------------------------------------------------------
+Q_GOOD, Q_KEPT = 1, 2
+
+
+def select_tracks(tuples, tuple_n, fits, pt_min=0.0, chi2_max=0.0, clean_shared=False):
+    """Quality bits of each fitted track (the selection step that follows the fit; the paper
+    names the Tracks product, §2, but defines no selection, so this is the library's reading).
+
+    GOOD: fit status 0, pT >= pt_min (no cut when pt_min is 0) and chi2/ndof <= chi2_max (no
+    cut when chi2_max is 0), with ndof = max(2 n - 5, 1) for n hits (two measurements per hit,
+    five helix parameters).
+    KEPT: GOOD and, with clean_shared, no other GOOD track that shares a hit with it ranks
+    strictly better; a track ranks better when it has more hits, or as many hits and a smaller
+    chi2/ndof.  One round: a track is dropped by a better one even when that one is dropped in
+    turn.  Without clean_shared, KEPT = GOOD.
+    """
+    nt = len(tuple_n)
+    good = [False] * nt
+    rank = [None] * nt
+    hits = []
+    for t in range(nt):
+        n = int(tuple_n[t])
+        hits.append([int(h) for h in tuples[t][:n]])
+        ndof = max(2 * n - 5, 1)
+        r = float(fits[t]["chi2"]) / ndof
+        ok = int(fits[t]["status"]) == 0
+        if ok and pt_min > 0:
+            ok = float(fits[t]["pt"]) >= pt_min
+        if ok and chi2_max > 0:
+            ok = r <= chi2_max
+        good[t] = ok
+        rank[t] = (-n, r)
+    users = {}
+    for t in range(nt):
+        if good[t]:
+            for h in hits[t]:
+                users.setdefault(h, []).append(t)
+    q = np.zeros(nt, np.uint8)
+    for t in range(nt):
+        if not good[t]:
+            continue
+        kept = True
+        if clean_shared:
+            for h in hits[t]:
+                for u in users[h]:
+                    if u != t and rank[u] < rank[t]:
+                        kept = False
+        q[t] = Q_GOOD | (Q_KEPT if kept else 0)
+    return q
