@@ -81,6 +81,11 @@ extern "C" {
 #define PXR_STAGE_SELECT 4
 #define PXR_STAGE_FIT 5
 
+/* Track quality bits (pxr_tracks.quality). */
+#define PXR_Q_GOOD 1u       /* fit status 0 and the selection cuts (pt_min, chi2_max) passed */
+#define PXR_Q_KEPT 2u       /* good, and (with clean_shared) no better-ranked good track shares a
+                               hit with it */
+
 /*
  * Reconstruction parameters.  All fields are inputs; pxr_params_init fills a preset.
  *
@@ -108,6 +113,12 @@ extern "C" {
  *   projected by 1 + cot^2 on the transverse and (1 + cot^2)^2 on the line kinks); weights
  *   1/sigma_rphi^2 and 1/sigma_z^2 (disks: 1/(sigma_z cot)^2); Cholesky solves; conversion to the
  *   point of closest approach to the z axis.  dxy = q (|C| - R) with C the fitted centre.
+ * Selection.  Every fitted track stays in the output with quality bits: PXR_Q_GOOD when its fit
+ *   status is 0, pT >= pt_min and chi2 / ndof <= chi2_max (ndof = max(2 n - 5, 1) for n hits; a
+ *   threshold of 0 is no cut); PXR_Q_KEPT when it is good and, with clean_shared, no other good
+ *   track of the event that shares a hit with it ranks strictly better (more hits, or as many and
+ *   a smaller chi2 / ndof).  One round: a track is dropped by a better one even if that one is
+ *   dropped in turn.  Without clean_shared, KEPT equals GOOD.
  */
 typedef struct pxr_params {
     uint32_t n_layers;                         /* <= PXR_MAX_LAYERS; hit layer ids < n_layers */
@@ -138,6 +149,10 @@ typedef struct pxr_params {
                                                   stage's grid (PXR_STAGE_*), 1..64; 0 = the
                                                   built-in value.  Results do not depend on it;
                                                   pxr's autotuner picks it with the bin count */
+    double pt_min;                             /* selection: GeV, >= 0; 0 = no cut */
+    double chi2_max;                           /* selection: chi2 per degree of freedom, >= 0;
+                                                  0 = no cut */
+    uint32_t clean_shared;                     /* selection: 0 or 1 (shared-hit cleaning) */
 } pxr_params;
 
 /* Context configuration. */
@@ -166,6 +181,7 @@ typedef struct pxr_tracks {
     double *pt, *phi, *cot_theta, *dxy, *dz, *chi2;   /* [capacity] */
     int8_t *charge;             /* [capacity] */
     int8_t *fit_status;         /* [capacity] 0 ok, 1 collinear, 2 zero curvature, 3 Cholesky */
+    uint8_t *quality;           /* [capacity] PXR_Q_* bits of the selection */
 } pxr_tracks;
 
 typedef struct pxr_ctx pxr_ctx;

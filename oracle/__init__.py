@@ -265,9 +265,9 @@ def select_tracks(tuples, tuple_n, fits, pt_min=0.0, chi2_max=0.0, clean_shared=
     """Quality bits of each fitted track (the selection step that follows the fit; the paper
     names the Tracks product, §2, but defines no selection, so this is the library's reading).
 
-    GOOD: fit status 0, pT >= pt_min (no cut when pt_min is 0) and chi2/ndof <= chi2_max (no
-    cut when chi2_max is 0), with ndof = max(2 n - 5, 1) for n hits (two measurements per hit,
-    five helix parameters).
+    GOOD: fit status 0, a finite chi2, pT >= pt_min (no cut when pt_min is 0) and chi2/ndof <=
+    chi2_max (no cut when chi2_max is 0), with ndof = max(2 n - 5, 1) for n hits (two
+    measurements per hit, five helix parameters).
     KEPT: GOOD and, with clean_shared, no other GOOD track that shares a hit with it ranks
     strictly better; a track ranks better when it has more hits, or as many hits and a smaller
     chi2/ndof.  One round: a track is dropped by a better one even when that one is dropped in
@@ -282,7 +282,7 @@ def select_tracks(tuples, tuple_n, fits, pt_min=0.0, chi2_max=0.0, clean_shared=
         hits.append([int(h) for h in tuples[t][:n]])
         ndof = max(2 * n - 5, 1)
         r = float(fits[t]["chi2"]) / ndof
-        ok = int(fits[t]["status"]) == 0
+        ok = int(fits[t]["status"]) == 0 and np.isfinite(r)
         if ok and pt_min > 0:
             ok = float(fits[t]["pt"]) >= pt_min
         if ok and chi2_max > 0:

@@ -350,8 +350,24 @@ __device__ __forceinline__ void fit_dispatch(int n, const float *X, const float 
     else fit_track<double, double, false>(n, X, Y, Z, L, p, o);
 }
 
+// Selection rank of a good track for shared-hit cleaning: more hits first, then smaller
+// chi2/ndof.  A 64-bit key ordered like that rank: 7 - n in the top bits, then the bits of the
+// non-negative double chi2/ndof (ordered like its value) without their last four.
+__device__ __forceinline__ unsigned long long rank_key(int n, double chi2_ndof)
+{
+    return ((unsigned long long)(7 - n) << 60) |
+           ((unsigned long long)__double_as_longlong(chi2_ndof) >> 4);
+}
+
+__device__ __forceinline__ double chi2_ndof(double chi2, int n)
+{
+    return chi2 / (double)(2 * n - 5 > 1 ? 2 * n - 5 : 1);
+}
+
 // One thread per output track: the kept ntuplets are listed per event in output order, and the
-// number of outputs is read on the device, so no thread is spent on unused capacity.
+// number of outputs is read on the device, so no thread is spent on unused capacity.  After the
+// fit, the selection cuts give the track's quality; with shared-hit cleaning a good track offers
+// its rank key to each of its hits (the smallest key of a hit wins, k_keep reads them).
 __global__ void __launch_bounds__(256, 2) k_fit(DevBatch b, DevParams p)
 {
     const uint32_t n_out = b.out_evt[b.E];
@@ -362,15 +378,18 @@ __global__ void __launch_bounds__(256, 2) k_fit(DevBatch b, DevParams p)
         const int n = b.tup_n[t];
         float X[kMaxHits], Y[kMaxHits], Z[kMaxHits];
         uint8_t L[kMaxHits];
+        uint32_t loc[kMaxHits];
 #pragma unroll
         for (int h = 0; h < kMaxHits; ++h) {
             const uint32_t pos = b.tup_hits[(size_t)t * kMaxHits + h];
+            loc[h] = 0;
             if (h < n) {
                 const float4 v = b.hs[pos];
                 const uint32_t meta = b.hmeta[pos];
                 X[h] = v.x; Y[h] = v.y; Z[h] = v.z;
                 L[h] = (uint8_t)(meta >> kLocalBits);
-                b.o_hits[(size_t)o * kMaxHits + h] = meta & kLocalMask;
+                loc[h] = meta & kLocalMask;
+                b.o_hits[(size_t)o * kMaxHits + h] = loc[h];
             } else {
                 X[h] = Y[h] = Z[h] = 0.f;
                 L[h] = 0;
@@ -383,6 +402,37 @@ __global__ void __launch_bounds__(256, 2) k_fit(DevBatch b, DevParams p)
         b.o_pt[o] = f.pt; b.o_phi[o] = f.phi; b.o_cot[o] = f.cot;
         b.o_dxy[o] = f.dxy; b.o_dz[o] = f.dz; b.o_chi2[o] = f.chi2;
         b.o_q[o] = f.q; b.o_status[o] = f.status;
+        const double r = chi2_ndof(f.chi2, n);
+        const bool good = f.status == 0 && isfinite(r) && (p.pt_min <= 0.0 || f.pt >= p.pt_min) &&
+                          (p.chi2_max <= 0.0 || r <= p.chi2_max);
+        b.o_ql[o] = good ? (uint8_t)(kQGood | (p.clean ? 0u : kQKept)) : (uint8_t)0;
+        if (good && p.clean) {
+            const unsigned long long key = rank_key(n, r);
+            const uint32_t h0 = b.hit_off[e];
+#pragma unroll
+            for (int h = 0; h < kMaxHits; ++h)
+                if (h < n) atomicMin(&b.best[h0 + loc[h]], key);
+        }
+    }
+}
+
+// Shared-hit cleaning, after every good track has offered its key: a good track is kept when no
+// hit of it carries a smaller key (a better-ranked good track sharing the hit).
+__global__ void __launch_bounds__(256) k_keep(DevBatch b)
+{
+    const uint32_t n_out = b.out_evt[b.E];
+    for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < n_out;
+         o += gridDim.x * blockDim.x) {
+        const uint8_t ql = b.o_ql[o];
+        if (!(ql & kQGood)) continue;
+        const uint32_t e = find_event(b.out_evt, b.E, o);
+        const int n = b.o_nh[o];
+        const unsigned long long key = rank_key(n, chi2_ndof(b.o_chi2[o], n));
+        const uint32_t h0 = b.hit_off[e];
+        bool kept = true;
+        for (int h = 0; h < n; ++h)
+            kept &= b.best[h0 + b.o_hits[(size_t)o * kMaxHits + h]] >= key;
+        if (kept) b.o_ql[o] = (uint8_t)(ql | kQKept);
     }
 }
 
@@ -397,6 +447,15 @@ void launch_fit(const DevBatch &b, const DevParams &p, uint32_t total, cudaStrea
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
     k_fit<<<(unsigned)blocks, tpb, 0, s>>>(b, p);
+}
+
+void launch_keep(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
+{
+    uint64_t blocks = ((uint64_t)total + 255) / 256;
+    const uint64_t cap = (uint64_t)sms * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) return;
+    k_keep<<<(unsigned)blocks, 256, 0, s>>>(b);
 }
 
 // Fit-only path: m ntuplets given directly.

@@ -31,6 +31,9 @@ enum Counter : int {
 };
 constexpr int kReportedCounters = 5;
 
+// Track quality bits (the header's PXR_Q_GOOD, PXR_Q_KEPT).
+constexpr uint8_t kQGood = 1u, kQKept = 2u;
+
 // Per-event flags (C_FLAGS).
 enum Flag : uint32_t { F_CELLS = 1u, F_EDGES = 2u, F_TUPLES = 4u, F_LAYER = 8u };
 
@@ -66,6 +69,8 @@ struct DevParams {
     double cw;                          // cos(w) as given by the caller
     double theta, dca;
     double bfield, sigma_rphi, sigma_z, x_over_x0;
+    double pt_min, chi2_max;            // track selection (0: no cut)
+    uint32_t clean;                     // shared-hit cleaning
 };
 
 struct DevBatch {
@@ -121,6 +126,9 @@ struct DevBatch {
     uint32_t *o_hits;                   // [out_cap * kMaxHits] caller indices within the event
     double *o_pt, *o_phi, *o_cot, *o_dxy, *o_dz, *o_chi2;
     int8_t *o_q, *o_status;
+    uint8_t *o_ql;                      // quality bits (PXR_Q_*)
+    unsigned long long *best;           // [N] shared-hit cleaning: best rank key per hit (caller
+                                        //   order, events back to back)
 };
 
 // Event of hit g: the chunk table gives the event of the chunk's first hit.
@@ -165,6 +173,8 @@ void launch_select(const DevBatch &b, const DevParams &p, uint32_t tup_total, cu
 void launch_out_scan(const DevBatch &b, cudaStream_t s);
 void launch_fit(const DevBatch &b, const DevParams &p, uint32_t tup_total, cudaStream_t s,
                 int sms);
+void launch_keep(const DevBatch &b, const DevParams &p, uint32_t tup_total, cudaStream_t s,
+                 int sms);
 void launch_fit_batch(uint32_t m, const uint8_t *nh, const float *x, const float *y,
                       const float *z, const uint16_t *layer, uint32_t stride, const DevParams &p,
                       double *pt, double *phi, double *cot, double *dxy, double *dz, double *chi2,

@@ -119,6 +119,9 @@ static int check_params(const pxr_params *p, DevParams *d)
         return fail(PXR_EINVAL, "n_phi_bins must be 0 or in [64, 2048]");
     for (int k = 0; k < PXR_STAGES; ++k)
         if (p->grid_per_sm[k] > 64) return fail(PXR_EINVAL, "grid_per_sm must be in [0, 64]");
+    if (!(p->pt_min >= 0.0) || !(p->chi2_max >= 0.0) || !std::isfinite(p->pt_min) ||
+        !std::isfinite(p->chi2_max) || p->clean_shared > 1)
+        return fail(PXR_EINVAL, "pt_min and chi2_max must be finite and >= 0, clean_shared 0 or 1");
     if (!d) return PXR_OK;
     std::memset(d, 0, sizeof(*d));
     d->n_layers = p->n_layers;
@@ -158,6 +161,9 @@ static int check_params(const pxr_params *p, DevParams *d)
     d->sigma_rphi = p->sigma_rphi;
     d->sigma_z = p->sigma_z;
     d->x_over_x0 = p->x_over_x0;
+    d->pt_min = p->pt_min;
+    d->chi2_max = p->chi2_max;
+    d->clean = p->clean_shared;
     // CA levels: a layer's level is 1 + the highest level of its pairs' inner layers (0 without
     // in-pairs); junction layers (in- and out-pairs) are processed level by level, so that every
     // cell has all its in-edges before its own out-edges are built
@@ -245,7 +251,7 @@ struct PlanOffsets {
     size_t cnt, bkt, hs, r64, hmeta, hphi, item, cell_in, cell_out,
         nbr_first,
         nbr_n, nbr, mindepth, root_list, live, front_list, front_snap, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, out_evt, o_nh,
-        o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status;
+        o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status, o_ql, best;
     size_t total;
 };
 
@@ -303,6 +309,8 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.o_chi2 = L.add(8 * T);
     o.o_q = L.add(T);
     o.o_status = L.add(T);
+    o.o_ql = L.add(T);
+    o.best = L.add(dp.clean ? 8 * N : 0);
     o.total = L.add(0);
     return o;
 }
@@ -470,6 +478,8 @@ static void plan_bind(pxr_plan *P)
     b.o_chi2 = (double *)(r + o.o_chi2);
     b.o_q = (int8_t *)(r + o.o_q);
     b.o_status = (int8_t *)(r + o.o_status);
+    b.o_ql = (uint8_t *)(r + o.o_ql);
+    b.best = (unsigned long long *)(r + o.best);
 }
 
 // Fill the per-event capacity prefixes from per-layer counts (lcount: E x (kMaxLayers+1)).
@@ -568,7 +578,10 @@ static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
     launch_select(b, p, (uint32_t)P->T, s, sms);
     launch_out_scan(b, s);
     if (t) CK(stage_mark(P->ev_stage[4], s, capturing));
+    // the selection's shared-hit ranks start at the largest key (no track)
+    if (p.clean) CK(cudaMemsetAsync(b.best, 0xFF, 8 * (size_t)P->N, s));
     launch_fit(b, p, (uint32_t)P->T, s, sms);
+    if (p.clean) launch_keep(b, p, (uint32_t)P->T, s, sms);
     if (t) CK(stage_mark(P->ev_stage[5], s, capturing));
     CK(cudaGetLastError());
     return PXR_OK;
@@ -576,7 +589,7 @@ static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
 
 static int plan_launches(const pxr_plan *P)
 {
-    int n = 6;                                  // sort, doublets, walk, select, scan, fit
+    int n = 6 + (P->dp.clean ? 1 : 0);          // sort, doublets, walk, select, scan, fit, keep
     for (uint32_t lv = 1; lv <= P->dp.n_levels; ++lv)
         n += (P->dp.level_dense[lv] ? 1 : 0) + (P->dp.level_sparse[lv] ? 1 : 0);
     return n;
@@ -765,11 +778,12 @@ struct HostTracks {
     std::vector<uint32_t> hits;
     std::vector<double> pt, phi, cot, dxy, dz, chi2;
     std::vector<int8_t> q, st;
+    std::vector<uint8_t> ql;
     size_t size() const { return nh.size(); }
     void resize(size_t n)
     {
         nh.resize(n); hits.resize(n * kMaxHits); pt.resize(n); phi.resize(n); cot.resize(n);
-        dxy.resize(n); dz.resize(n); chi2.resize(n); q.resize(n); st.resize(n);
+        dxy.resize(n); dz.resize(n); chi2.resize(n); q.resize(n); st.resize(n); ql.resize(n);
     }
 };
 
@@ -818,8 +832,8 @@ static void canonical_order(const uint32_t *hits, size_t n, std::vector<uint32_t
 // Copy n tracks of the source arrays into out in canonical order.
 static int emit_tracks(const uint8_t *nh, const uint32_t *hits, const double *pt,
                        const double *phi, const double *cot, const double *dxy, const double *dz,
-                       const double *chi2, const int8_t *q, const int8_t *st, size_t n,
-                       int32_t status, pxr_tracks *out, bool in_order = false)
+                       const double *chi2, const int8_t *q, const int8_t *st, const uint8_t *ql,
+                       size_t n, int32_t status, pxr_tracks *out, bool in_order = false)
 {
     out->n_tracks = (uint32_t)n;
     out->status = status;
@@ -838,6 +852,7 @@ static int emit_tracks(const uint8_t *nh, const uint32_t *hits, const double *pt
         cp(out->chi2, chi2, 8);
         cp(out->charge, q, 1);
         cp(out->fit_status, st, 1);
+        cp(out->quality, ql, 1);
         return PXR_OK;
     }
     std::vector<uint32_t> ord;
@@ -855,6 +870,7 @@ static int emit_tracks(const uint8_t *nh, const uint32_t *hits, const double *pt
         if (out->chi2) out->chi2[k] = chi2[s];
         if (out->charge) out->charge[k] = q[s];
         if (out->fit_status) out->fit_status[k] = st[s];
+        if (out->quality) out->quality[k] = ql[s];
     }
     return PXR_OK;
 }
@@ -885,11 +901,12 @@ extern "C" int pxr_plan_tracks(pxr_plan *P, uint32_t e, pxr_tracks *out)
         (rc = d2h(h.pt, P->db.o_pt + a, n)) || (rc = d2h(h.phi, P->db.o_phi + a, n)) ||
         (rc = d2h(h.cot, P->db.o_cot + a, n)) || (rc = d2h(h.dxy, P->db.o_dxy + a, n)) ||
         (rc = d2h(h.dz, P->db.o_dz + a, n)) || (rc = d2h(h.chi2, P->db.o_chi2 + a, n)) ||
-        (rc = d2h(h.q, P->db.o_q + a, n)) || (rc = d2h(h.st, P->db.o_status + a, n)))
+        (rc = d2h(h.q, P->db.o_q + a, n)) || (rc = d2h(h.st, P->db.o_status + a, n)) ||
+        (rc = d2h(h.ql, P->db.o_ql + a, n)))
         return rc;
     return emit_tracks(h.nh.data(), h.hits.data(), h.pt.data(), h.phi.data(), h.cot.data(),
-                       h.dxy.data(), h.dz.data(), h.chi2.data(), h.q.data(), h.st.data(), n,
-                       flags_status(flags), out);
+                       h.dxy.data(), h.dz.data(), h.chi2.data(), h.q.data(), h.st.data(),
+                       h.ql.data(), n, flags_status(flags), out);
 }
 
 // Debug content of one event of a plan region (also used by the serving path).
@@ -1047,7 +1064,7 @@ struct Batch {
     size_t reserved = 0;
     uint32_t total = 0;
     size_t o_nh = 0, o_hits = 0, o_pt = 0, o_phi = 0, o_cot = 0, o_dxy = 0, o_dz = 0,
-           o_chi2 = 0, o_q = 0, o_st = 0;
+           o_chi2 = 0, o_q = 0, o_st = 0, o_ql = 0;
     ~Batch()
     {
         if (ev_counts) cudaEventDestroy(ev_counts);
@@ -1193,6 +1210,7 @@ static bool progress_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
         B.o_chi2 = L.add(8 * T);
         B.o_q = L.add(T);
         B.o_st = L.add(T);
+        B.o_ql = L.add(T);
         bool ok = sb.out.reserve(L.add(0) + 256);
         const DevBatch &d = P->db;
         char *ho = sb.out.p;
@@ -1210,6 +1228,7 @@ static bool progress_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
             cp(B.o_chi2, d.o_chi2, 8 * T);
             cp(B.o_q, d.o_q, T);
             cp(B.o_st, d.o_status, T);
+            cp(B.o_ql, d.o_ql, T);
         }
         ok &= cudaEventRecord(B.ev_data, s) == cudaSuccess;
         if (!ok) ctx->sched_error = "device-to-host copy failed";
@@ -1249,6 +1268,7 @@ static bool progress_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
                 const double *chi2 = (const double *)hp(B.o_chi2 + 8 * (size_t)a);
                 const int8_t *q = (const int8_t *)hp(B.o_q + a);
                 const int8_t *st = (const int8_t *)hp(B.o_st + a);
+                const uint8_t *ql = (const uint8_t *)hp(B.o_ql + a);
                 for (uint32_t k = 0; k < n; ++k) {
                     const uint32_t s_ = ord[k];
                     t.res.nh[k] = nh[s_];
@@ -1262,6 +1282,7 @@ static bool progress_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
                     t.res.chi2[k] = chi2[s_];
                     t.res.q[k] = q[s_];
                     t.res.st[k] = st[s_];
+                    t.res.ql[k] = ql[s_];
                 }
             }
         }
@@ -1501,7 +1522,7 @@ extern "C" int pxr_fetch_tracks(pxr_ctx *ctx, uint64_t ticket, pxr_tracks *out)
     const HostTracks &r = t->res;
     int rc = emit_tracks(r.nh.data(), r.hits.data(), r.pt.data(), r.phi.data(), r.cot.data(),
                          r.dxy.data(), r.dz.data(), r.chi2.data(), r.q.data(), r.st.data(),
-                         r.size(), t->status, out, true);
+                         r.ql.data(), r.size(), t->status, out, true);
     if (rc) return rc;
     std::lock_guard<std::mutex> g(ctx->mu);
     ctx->tickets.erase(ticket);

@@ -45,11 +45,11 @@ def to_dev(events):
 
 
 def run_plan(ctx, events, P, cut, fit=pxr.FIT_FP64, graph=False, n_phi_bins=0, max_cells=0,
-             debug=True):
+             debug=True, **select):
     off, x, y, z, layer = to_dev(events)
     plan = pxr.Plan(ctx, off, x, y, z, layer,
                     pxr.params_from(P, cut_mode=cut, fit_mode=fit, n_phi_bins=n_phi_bins,
-                                    max_cells=max_cells), use_graph=graph)
+                                    max_cells=max_cells, **select), use_graph=graph)
     plan.pxr_plan_run()
     out = []
     for e in range(len(events)):
@@ -212,6 +212,64 @@ def test_degenerate_inputs(ctx, orc, cut):
     assert len(gpu_tuples(got[1]["tracks"])) >= 3
     phi = np.arctan2(events[2][1], events[2][0])
     assert np.any(np.abs(np.abs(phi) - np.pi) < 0.02)
+
+
+def ambiguous_selection(tup, n, fits, pt_min, chi2_max, clean, rel=1e-6):
+    """Tracks whose selection the two fits (GPU and oracle, both FP64 but in different operation
+    orders) may decide differently: a pT or chi2/ndof within `rel` of its cut, or a shared hit
+    with a track of equal length whose chi2/ndof is within `rel` of its own.  Returns a mask;
+    every other track must get the same bits."""
+    nt = len(n)
+    r = np.array([f["chi2"] / max(2 * int(k) - 5, 1) for f, k in zip(fits, n)], np.float64)
+    amb = np.zeros(nt, bool)
+    if pt_min > 0:
+        amb |= np.abs(fits["pt"] / pt_min - 1) <= 2e-4           # the fit tolerance on pT
+    if chi2_max > 0:
+        amb |= np.abs(r / chi2_max - 1) <= rel
+    if clean:
+        users = {}
+        for t in range(nt):
+            for h in tup[t][:n[t]]:
+                users.setdefault(int(h), []).append(t)
+        for lst in users.values():
+            for a in lst:
+                for c in lst:
+                    if a < c and n[a] == n[c] and abs(r[a] - r[c]) <= rel * max(r[a], r[c]):
+                        amb[a] = amb[c] = True
+    return amb
+
+
+@pytest.mark.parametrize("which", ["barrel_smeared", "dense"])
+def test_selection_matches_oracle(ctx, orc, which):
+    """Quality cuts and shared-hit cleaning on the GPU against the oracle's selection, track by
+    track (tracks matched by their hit tuples); near-threshold and near-tie tracks, where the two
+    FP64 fits may round to different sides, are only checked for consistency."""
+    if which == "dense":
+        P, ev = synth.params_phase1(), synth.event_phase1(3, 1200)
+        sel = dict(pt_min=0.6, chi2_max=20.0, clean_shared=True)
+    else:
+        P, ev = synth.params_barrel_quadruplets(), synth.make_event(11, 3000, smear=True)
+        sel = dict(pt_min=0.0, chi2_max=0.0, clean_shared=True)
+    e = ev_tuple(ev)
+    ref, _cells, _edges, tup, fits = oracle_sets(orc, e, P)
+    order_tup = np.array([list(t) + [0xFFFFFFFF] * (8 - len(t)) for t in tup], np.uint32) \
+        if tup else np.zeros((0, 8), np.uint32)
+    tn = np.array([len(t) for t in tup], np.uint8)
+    want = orc.select_tracks(order_tup, tn, fits, **sel)
+    got = run_plan(ctx, [e], P, pxr.CUT_FP32, debug=False, **sel)[0]["tracks"]
+    assert gpu_tuples(got) == tup
+    amb = ambiguous_selection(order_tup, tn, fits, sel["pt_min"], sel["chi2_max"], True)
+    q = got["quality"]
+    assert np.array_equal(q[~amb], want[~amb]), np.flatnonzero(q[~amb] != want[~amb])
+    assert not np.any(((q & pxr.Q_KEPT) != 0) & ((q & pxr.Q_GOOD) == 0))
+    kept, good = (want & pxr.Q_KEPT) != 0, (want & pxr.Q_GOOD) != 0
+    assert 0 < kept.sum() < good.sum()            # the cleaning acts
+    print(which, "good", good.sum(), "kept", kept.sum(), "ambiguous", amb.sum())
+    # without a selection every fitted track is good and kept
+    off = run_plan(ctx, [e], P, pxr.CUT_FP32, debug=False)[0]["tracks"]
+    ok = off["fit_status"] == 0
+    assert np.all(off["quality"][ok] == pxr.Q_GOOD | pxr.Q_KEPT)
+    assert np.all(off["quality"][~ok] == 0)
 
 
 def test_graph_equals_direct_and_bin_counts(ctx, orc):
