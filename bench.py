@@ -438,6 +438,67 @@ def _gpu_event_rate(pxr, ctx, ev, params, dev, stream, reps):
     return rate, tracks, debug
 
 
+def _selection_study(pxr, synth, ctx, dev, stream, n_events=256, reps=10):
+    """Track selection (shared-hit cleaning) on the batch workload with smeared hits: its cost
+    (step and fit+output stage time, selection off and on, L2 flushed between steps) and its
+    effect (fake fraction and the share of generated tracks kept, from the generator's truth)."""
+    import torch
+    counts = synth.batch_track_counts(n_events, 0)
+    evs = [synth.make_event(e, counts[e], smear=True) for e in range(n_events)]
+    off = np.zeros(n_events + 1, np.uint32)
+    off[1:] = np.cumsum([e.n for e in evs])
+    cat = lambda k: np.concatenate([getattr(e, k) for e in evs])
+    x, y, z = (torch.from_numpy(cat(k)).to(dev) for k in "xyz")
+    layer = torch.from_numpy(cat("layer").view(np.int16)).to(dev)
+    P = synth.params_barrel_quadruplets()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    res = {"events": n_events, "hits": int(off[-1])}
+    for name, clean in (("off", False), ("on", True)):
+        prm = pxr.params_from(P, cut_mode=pxr.CUT_FP32, fit_mode=pxr.FIT_MIXED, n_phi_bins=1024,
+                              clean_shared=clean)
+        plan = pxr.Plan(ctx, off, x, y, z, layer, prm, use_graph=True)
+        st = np.zeros(5)
+        with torch.cuda.stream(stream):
+            for r in range(reps + 2):
+                flush.zero_()
+                plan.pxr_plan_run(stream)
+                stream.synchronize()
+                if r >= 2:
+                    st += np.array(plan.pxr_plan_stage_ms())
+        st /= reps
+        res["step_ms_" + name] = float(st.sum())
+        res["fit_output_ms_" + name] = float(st[4])
+        if clean:
+            n_all = n_good = n_kept = fake_all = fake_kept = 0
+            found, kept_true, generated = set(), set(), 0
+            for e, ev in enumerate(evs):
+                t = plan.pxr_plan_tracks(e)
+                q = t["quality"]
+                generated += len(np.unique(ev.track[ev.track >= 0]))
+                for k in range(len(q)):
+                    h = t["hit_idx"][k, :t["n_hits"][k]]
+                    ids = ev.track[h]
+                    tid = int(ids[0]) if ids[0] >= 0 and np.all(ids == ids[0]) else -1
+                    n_all += 1
+                    fake_all += tid < 0
+                    if q[k] & pxr.Q_GOOD:
+                        n_good += 1
+                    if tid >= 0:
+                        found.add((e, tid))
+                    if q[k] & pxr.Q_KEPT:
+                        n_kept += 1
+                        fake_kept += tid < 0
+                        if tid >= 0:
+                            kept_true.add((e, tid))
+            res.update({"tracks": n_all, "good": n_good, "kept": n_kept,
+                        "fake_fraction_all": fake_all / max(n_all, 1),
+                        "fake_fraction_kept": fake_kept / max(n_kept, 1),
+                        "generated_tracks_found": len(found) / max(generated, 1),
+                        "generated_tracks_kept": len(kept_true) / max(generated, 1)})
+        plan.close()
+    return res
+
+
 def _oracle_rate(oracle, ev, P, min_s=1.0):
     n, t0 = 0, time.perf_counter()
     while True:
@@ -588,6 +649,8 @@ def study(args):
                         "status_agree": float(np.mean(h["fit_status"] == ref["status"])),
                         "errors": _fit_errors(h, ref, ok)}
         out["C4_fit_precision"] = c4
+        # next row N1: track selection (shared-hit cleaning) on the smeared batch
+        out["N1_selection"] = _selection_study(pxr, synth, ctx, dev, stream)
     # C5: serving sweep, continuous batching vs one event per launch, 8 GB budget
     P = synth.params_barrel_quadruplets()
     prm = pxr.params_from(P, cut_mode=pxr.CUT_FP32, fit_mode=pxr.FIT_MIXED)
