@@ -282,7 +282,7 @@ def select_tracks(tuples, tuple_n, fits, pt_min=0.0, chi2_max=0.0, clean_shared=
         hits.append([int(h) for h in tuples[t][:n]])
         ndof = max(2 * n - 5, 1)
         r = float(fits[t]["chi2"]) / ndof
-        ok = int(fits[t]["status"]) == 0 and np.isfinite(r)
+        ok = int(fits[t]["status"]) == 0 and np.isfinite(float(fits[t]["chi2"]))
         if ok and pt_min > 0:
             ok = float(fits[t]["pt"]) >= pt_min
         if ok and chi2_max > 0:

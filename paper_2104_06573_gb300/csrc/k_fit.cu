@@ -402,8 +402,11 @@ __global__ void __launch_bounds__(256, 2) k_fit(DevBatch b, DevParams p)
         b.o_pt[o] = f.pt; b.o_phi[o] = f.phi; b.o_cot[o] = f.cot;
         b.o_dxy[o] = f.dxy; b.o_dz[o] = f.dz; b.o_chi2[o] = f.chi2;
         b.o_q[o] = f.q; b.o_status[o] = f.status;
-        const double r = chi2_ndof(f.chi2, n);
-        const bool good = f.status == 0 && isfinite(r) && (p.pt_min <= 0.0 || f.pt >= p.pt_min) &&
+        // (the FP64 division only when a cut or the ranking needs chi2/ndof)
+        const bool need_r = p.chi2_max > 0.0 || p.clean;
+        const double r = need_r ? chi2_ndof(f.chi2, n) : 0.0;
+        const bool good = f.status == 0 && isfinite(f.chi2) &&
+                          (p.pt_min <= 0.0 || f.pt >= p.pt_min) &&
                           (p.chi2_max <= 0.0 || r <= p.chi2_max);
         b.o_ql[o] = good ? (uint8_t)(kQGood | (p.clean ? 0u : kQKept)) : (uint8_t)0;
         if (good && p.clean) {
