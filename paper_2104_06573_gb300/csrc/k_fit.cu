@@ -378,18 +378,15 @@ __global__ void __launch_bounds__(256, 2) k_fit(DevBatch b, DevParams p)
         const int n = b.tup_n[t];
         float X[kMaxHits], Y[kMaxHits], Z[kMaxHits];
         uint8_t L[kMaxHits];
-        uint32_t loc[kMaxHits];
 #pragma unroll
         for (int h = 0; h < kMaxHits; ++h) {
             const uint32_t pos = b.tup_hits[(size_t)t * kMaxHits + h];
-            loc[h] = 0;
             if (h < n) {
                 const float4 v = b.hs[pos];
                 const uint32_t meta = b.hmeta[pos];
                 X[h] = v.x; Y[h] = v.y; Z[h] = v.z;
                 L[h] = (uint8_t)(meta >> kLocalBits);
-                loc[h] = meta & kLocalMask;
-                b.o_hits[(size_t)o * kMaxHits + h] = loc[h];
+                b.o_hits[(size_t)o * kMaxHits + h] = meta & kLocalMask;
             } else {
                 X[h] = Y[h] = Z[h] = 0.f;
                 L[h] = 0;
@@ -412,9 +409,8 @@ __global__ void __launch_bounds__(256, 2) k_fit(DevBatch b, DevParams p)
         if (good && p.clean) {
             const unsigned long long key = rank_key(n, r);
             const uint32_t h0 = b.hit_off[e];
-#pragma unroll
-            for (int h = 0; h < kMaxHits; ++h)
-                if (h < n) atomicMin(&b.best[h0 + loc[h]], key);
+            for (int h = 0; h < n; ++h)          // (the hit indices this thread wrote above)
+                atomicMin(&b.best[h0 + b.o_hits[(size_t)o * kMaxHits + h]], key);
         }
     }
 }
