@@ -343,8 +343,11 @@ def run_pxr(args, rank, world, local):
     ca_ms = stage[2]
     ca_achieved = ca_alg / (ca_ms / 1e3) / 1e9
 
+    rates = args.events * world / (step_ms / 1e3)      # per-step spread (rank-local)
     line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "value_std": float(np.std(rates, ddof=1)) if len(rates) > 1 else 0.0,
+            "ms_per_step_min_max": [float(step_ms.min()), float(step_ms.max())],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": f"cuts {args.cut}, fit {args.fit}", "data": "synthetic",
             "config": {"workload": WORKLOAD, "events_per_step": args.events * world,

@@ -89,12 +89,13 @@ def store_cache(path: str, key: str, value: dict) -> None:
     os.replace(tmp, path)
 
 
-def tune_plan(ctx, hit_offsets, x, y, z, layer, params, stream=None, reps: int = 3,
+def tune_plan(ctx, hit_offsets, x, y, z, layer, params, stream=None, reps: int = 5,
               bins: Sequence[int] = BINS, grids: Sequence[int] = GRIDS, cache: str | None = None,
               flush=None):
     """Tune n_phi_bins and grid_per_sm of `params` on this batch (device inputs); returns a copy
     of params with the choice filled in and a dict describing it.  `flush()` (optional) runs
-    before every timed step (an L2 flush on the same stream)."""
+    before every timed step (an L2 flush on the same stream).  A setting's time is the fastest of
+    its `reps` steps: interference from other work on the device only ever adds time."""
     import numpy as np
 
     from . import pxr
@@ -120,7 +121,7 @@ def tune_plan(ctx, hit_offsets, x, y, z, layer, params, stream=None, reps: int =
                     times.append(sum(plan.pxr_plan_stage_ms()))
             if plan.pxr_plan_counts()["flags"].any():           # a capacity ran out: reject
                 return float("inf")
-            return float(np.median(times))
+            return float(np.min(times))
         finally:
             plan.close()
 

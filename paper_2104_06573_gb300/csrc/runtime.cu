@@ -7,6 +7,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -18,6 +19,8 @@
 #include <unordered_map>
 #include <unordered_set>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/pxr.h"
 #include "pxr_dev.cuh"
@@ -316,6 +319,27 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
 }
 
 // ------------------------------------------------------------------------------------------
+// tracing and host-side fault injection
+// ------------------------------------------------------------------------------------------
+// NVTX range over a host scope (what a timeline profiler shows next to the kernels it launches).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+
+// Test hook: with PXR_FAULT_ARENA=n in the environment, the n-th arena allocation of the process
+// (counting from 1) fails as if the arena were full.  Host-side only; nothing on the GPU fails.
+static bool arena_fault_now()
+{
+    static const long at = [] {
+        const char *v = std::getenv("PXR_FAULT_ARENA");
+        return v ? std::atol(v) : 0L;
+    }();
+    static std::atomic<long> calls{0};
+    return at > 0 && calls.fetch_add(1) + 1 == at;
+}
+
+// ------------------------------------------------------------------------------------------
 // arena: first-fit free list over one device allocation
 // ------------------------------------------------------------------------------------------
 struct Arena {
@@ -333,6 +357,7 @@ struct Arena {
     }
     char *alloc(size_t bytes)
     {
+        if (arena_fault_now()) return nullptr;
         std::lock_guard<std::mutex> g(mu);
         bytes = (bytes + 255) & ~size_t(255);
         if (bytes == 0) bytes = 256;
@@ -546,6 +571,7 @@ static void fill_chunks(const pxr_plan *P, char *head)
 
 static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
 {
+    Range range("pxr.enqueue");
     const DevBatch &b = P->db;
     const DevParams &p = P->dp;
     int sms = P->ctx->sms;
@@ -1103,6 +1129,7 @@ static int launch_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
                         std::vector<std::shared_ptr<Ticket>> &items, int slot,
                         std::shared_ptr<Batch> &out)
 {
+    Range range("pxr.batch.launch");
     auto B = std::make_shared<Batch>();
     B->ctx = ctx;
     B->slot = slot;
@@ -1245,6 +1272,7 @@ static bool progress_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
         {
         // the results reach no other thread before the tickets are marked done (below)
         Unlocked unlocked(lk);
+        Range range("pxr.batch.order");
         // events in parallel (a few host threads): the ordering is the heaviest host work of a
         // batch
         auto work = [&](uint32_t e0, uint32_t step) {
