@@ -93,6 +93,9 @@ def lib():
             L.orc_fit_one.restype = C.c_int
             L.orc_fit_one.argtypes = [C.c_int, dp, dp, dp, C.POINTER(C.c_uint16),
                                       C.POINTER(OrcParams), C.POINTER(OrcTrack)]
+            L.orc_fit_cov.restype = C.c_int
+            L.orc_fit_cov.argtypes = [C.c_int, dp, dp, dp, C.POINTER(C.c_uint16),
+                                      C.POINTER(OrcParams), C.POINTER(OrcTrack), dp]
             L.orc_fit_batch.restype = None
             L.orc_fit_batch.argtypes = [C.c_uint32, C.POINTER(C.c_uint8), dp, dp, dp,
                                         C.POINTER(C.c_uint16), C.c_uint32,
@@ -200,6 +203,50 @@ def fit_batch(nh, X, Y, Z, layers, params) -> np.ndarray:
                         _ptr(Z, C.c_double), _ptr(L, C.c_uint16), k, C.byref(P),
                         out.ctypes.data_as(C.POINTER(OrcTrack)))
     return out
+
+
+COV_PARAMS = ("qoverpt", "phi", "cot_theta", "dxy", "dz")
+
+
+def fit_cov_batch(nh, X, Y, Z, layers, params):
+    """Fits and covariances of (q/pT, phi, cot, dxy, dz) of m ntuplets ([m, k] arrays as for
+    fit_batch).  Returns (fits, cov [m, 15] upper triangles row by row; NaN where the fit or the
+    covariance failed).  The covariance is the fitted values' (the inverse normal matrices of the
+    two broken lines) propagated through the conversion linearised by central differences."""
+    nh = np.ascontiguousarray(nh, np.uint8)
+    m = len(nh)
+    X = np.ascontiguousarray(X, np.float64)
+    Y = np.ascontiguousarray(Y, np.float64)
+    Z = np.ascontiguousarray(Z, np.float64)
+    L = np.ascontiguousarray(layers, np.uint16)
+    P = make_params(params)
+    fits = np.zeros(m, TRACK_DTYPE)
+    cov = np.full((m, 15), np.nan)
+    out = OrcTrack()
+    c15 = (C.c_double * 15)()
+    lb = lib()
+    for t in range(m):
+        n = int(nh[t])
+        rc = lb.orc_fit_cov(n, _ptr(X[t], C.c_double), _ptr(Y[t], C.c_double),
+                            _ptr(Z[t], C.c_double), _ptr(L[t], C.c_uint16), C.byref(P),
+                            C.byref(out), c15)
+        for k in TRACK_DTYPE.names:
+            fits[t][k] = getattr(out, k)
+        if rc == 0:
+            cov[t] = np.frombuffer(c15, np.float64)
+    return fits, cov
+
+
+def cov_matrix(c15):
+    """Full symmetric 5 x 5 matrices from upper triangles ([..., 15] -> [..., 5, 5])."""
+    c15 = np.asarray(c15)
+    M = np.zeros(c15.shape[:-1] + (5, 5))
+    k = 0
+    for i in range(5):
+        for j in range(i, 5):
+            M[..., i, j] = M[..., j, i] = c15[..., k]
+            k += 1
+    return M
 
 
 # -- whole event -----------------------------------------------------------------------------

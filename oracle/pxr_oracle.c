@@ -39,6 +39,7 @@
 #define ORC_MAX_PAIRS 32
 #define ORC_MAXH 8                    /* hit slots per ntuplet */
 #define ORC_K_PT 0.299792458e-2       /* pT [GeV] = K B[T] R[cm] */
+#define ORC_TWO_PI 6.283185307179586476925286766559
 
 typedef struct {
     uint32_t n_layers;
@@ -198,8 +199,8 @@ static int chol_solve(int m, const double *A, const double *b, double *x)
  * derivative -x[n].  Minimises  sum w (meas - x)^2 + sum beta^2 / kvar  through the normal
  * equations.  Returns 0 on success and stores the minimum in *chi2.
  */
-int orc_bl_solve(int n, const double *s, const double *meas, const double *w, const double *kvar,
-                 int curv, double *x, double *chi2)
+static int bl_solve(int n, const double *s, const double *meas, const double *w,
+                    const double *kvar, int curv, double *x, double *chi2, double *Ainv)
 {
     int m = n + (curv ? 1 : 0);
     double A[ORC_MAXM * ORC_MAXM];
@@ -225,6 +226,16 @@ int orc_bl_solve(int n, const double *s, const double *meas, const double *w, co
             for (int c = 0; c < m; ++c) A[r * m + c] += wk * g[r] * g[c];
     }
     if (chol_solve(m, A, b, x) != 0) return -1;
+    /* covariance of the unknowns: the inverse of the normal matrix, column by column */
+    if (Ainv) {
+        for (int k = 0; k < m; ++k) {
+            double e[ORC_MAXM], col[ORC_MAXM];
+            memset(e, 0, sizeof(e));
+            e[k] = 1.0;
+            if (chol_solve(m, A, e, col) != 0) return -1;
+            for (int r = 0; r < m; ++r) Ainv[r * m + k] = col[r];
+        }
+    }
     double c2 = 0.0;
     for (int i = 0; i < n; ++i) c2 += w[i] * (meas[i] - x[i]) * (meas[i] - x[i]);
     for (int j = 1; j + 1 < n; ++j) {
@@ -236,6 +247,12 @@ int orc_bl_solve(int n, const double *s, const double *meas, const double *w, co
     }
     *chi2 = c2;
     return 0;
+}
+
+int orc_bl_solve(int n, const double *s, const double *meas, const double *w, const double *kvar,
+                 int curv, double *x, double *chi2)
+{
+    return bl_solve(n, s, meas, w, kvar, curv, x, chi2, NULL);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -266,8 +283,109 @@ int orc_bl_solve(int n, const double *s, const double *meas, const double *w, co
  *     phi = direction of motion at the PCA; pT = K B R; cot = (v_1 - v_0)/ds_0;
  *     dz = v_0 - cot * (arc length from the PCA to hit 0).
  */
-int orc_fit_one(int n, const double *X, const double *Y, const double *Z, const uint16_t *lay,
-                const orc_params *P, orc_track *out)
+/* Step 6 as a function of the fitted values q = (u_0, u_1, delta, v_0, v_1) and the reference
+ * circle's geometry (also evaluated around q for the covariance's Jacobian). */
+typedef struct {
+    double R0, Cx, Cy, sgn, x0, y0, ds0, kB;
+} conv_geom;
+
+static int bl_convert(const conv_geom *G, const double *q, orc_track *out)
+{
+    double delta = q[2];
+    double kappa = 1.0 / G->R0 + delta;               /* > 0: bends like the reference circle */
+    if (kappa == 0.0 || !isfinite(kappa)) return 2;
+    double R = 1.0 / fabs(kappa);
+    double sgn = G->sgn;
+    double sgf = kappa > 0.0 ? sgn : -sgn;            /* orientation about the fitted centre */
+    int qf = sgf > 0.0 ? -1 : 1;
+    double ds0 = G->ds0;
+    double alpha = (q[1] - q[0]) / ds0 + 0.5 * delta * ds0;
+    double nx = -G->Cx / G->R0, ny = -G->Cy / G->R0;  /* outward normal at hit 0 */
+    double tx = -sgn * ny, ty = sgn * nx;             /* direction of motion at hit 0 */
+    double ca = cos(alpha), sa = sin(alpha);
+    double n2x = nx * ca - tx * sa, n2y = ny * ca - ty * sa;
+    double P0x = q[0] * nx, P0y = q[0] * ny;
+    double Fx = P0x - n2x / kappa, Fy = P0y - n2y / kappa;   /* fitted centre */
+    double rx = (P0x - Fx) * fabs(kappa), ry = (P0y - Fy) * fabs(kappa); /* centre -> hit 0 */
+    double wx = -G->x0 - Fx, wy = -G->y0 - Fy;        /* centre -> transverse origin */
+    double dist = sqrt(wx * wx + wy * wy);
+    double ex = wx / dist, ey = wy / dist;
+    double tpx = -sgf * ey, tpy = sgf * ex;           /* direction of motion at the PCA */
+    double cot = (q[4] - q[3]) / ds0;
+    double psi = atan2(sgf * (ex * ry - ey * rx), ex * rx + ey * ry);
+    out->pt = G->kB * R;
+    out->phi = atan2(tpy, tpx);
+    out->cot_theta = cot;
+    out->dxy = qf * (dist - R);
+    out->dz = q[3] - cot * (R * psi);
+    out->charge = qf;
+    out->status = 0;
+    return 0;
+}
+
+/* The five parameters of the covariance: q/pT (charge over pT, 1/GeV), phi, cot, dxy, dz. */
+static void cov_params(const orc_track *t, double *v)
+{
+    v[0] = t->charge / t->pt;
+    v[1] = t->phi;
+    v[2] = t->cot_theta;
+    v[3] = t->dxy;
+    v[4] = t->dz;
+}
+
+/*
+ * Covariance of (q/pT, phi, cot, dxy, dz): the fitted values q have the covariance of the
+ * linear least-squares problems, the inverse normal matrices (u_0, u_1, delta from the
+ * transverse fit, v_0, v_1 from the line fit; the two fits are independent); the conversion is
+ * linearised around q by a five-point central difference in each q_k with step 1e-3 of its
+ * standard deviation.  cov15 receives the upper triangle row by row.
+ */
+static int bl_cov(const conv_geom *G, const double *q, const double *AT, int mT, int n,
+                  const double *AL, double *cov15)
+{
+    double C[5][5];
+    memset(C, 0, sizeof(C));
+    const int it[3] = {0, 1, n};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) C[a][b] = AT[it[a] * mT + it[b]];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) C[3 + a][3 + b] = AL[a * n + b];
+    double J[5][5];
+    for (int k = 0; k < 5; ++k) {
+        if (!(C[k][k] > 0.0)) return -1;
+        const double h = 1e-3 * sqrt(C[k][k]);
+        double v[4][5];
+        const double off[4] = {-2.0, -1.0, 1.0, 2.0};
+        for (int t = 0; t < 4; ++t) {
+            double qq[5];
+            orc_track tr;
+            for (int i = 0; i < 5; ++i) qq[i] = q[i];
+            qq[k] += off[t] * h;
+            if (bl_convert(G, qq, &tr) != 0) return -1;
+            cov_params(&tr, v[t]);
+        }
+        for (int i = 0; i < 5; ++i) {
+            double d1 = v[2][i] - v[1][i], d2 = v[3][i] - v[0][i];
+            if (i == 1) {                               /* azimuth differences modulo 2 pi */
+                d1 = remainder(d1, ORC_TWO_PI);
+                d2 = remainder(d2, ORC_TWO_PI);
+            }
+            J[i][k] = (8.0 * d1 - d2) / (12.0 * h);
+        }
+    }
+    int o = 0;
+    for (int i = 0; i < 5; ++i)
+        for (int j = i; j < 5; ++j) {
+            double acc = 0.0;
+            for (int a = 0; a < 5; ++a)
+                for (int b = 0; b < 5; ++b) acc += J[i][a] * C[a][b] * J[j][b];
+            cov15[o++] = acc;
+        }
+    return 0;
+}
+
+static int fit_core(int n, const double *X, const double *Y, const double *Z, const uint16_t *lay,
+                    const orc_params *P, orc_track *out, double *cov15)
 {
     double px[ORC_MAXH], py[ORC_MAXH], s[ORC_MAXH], yres[ORC_MAXH];
     double wT[ORC_MAXH], wL[ORC_MAXH], kvT[ORC_MAXH], kvL[ORC_MAXH];
@@ -328,41 +446,32 @@ int orc_fit_one(int n, const double *X, const double *Y, const double *Z, const 
         }
     }
 
-    /* 4-5. the two broken lines */
-    if (orc_bl_solve(n, s, yres, wT, kvT, 1, xT, &chi2T) != 0) { out->status = 3; return -1; }
-    if (orc_bl_solve(n, s, Z, wL, kvL, 0, xL, &chi2L) != 0) { out->status = 3; return -1; }
+    /* 4-5. the two broken lines (and, for the covariance, their inverse normal matrices) */
+    double AT[ORC_MAXM * ORC_MAXM], AL[ORC_MAXM * ORC_MAXM];
+    if (bl_solve(n, s, yres, wT, kvT, 1, xT, &chi2T, cov15 ? AT : NULL) != 0) { out->status = 3; return -1; }
+    if (bl_solve(n, s, Z, wL, kvL, 0, xL, &chi2L, cov15 ? AL : NULL) != 0) { out->status = 3; return -1; }
 
     /* 6. conversion */
-    double delta = xT[n];
-    double kappa = 1.0 / R0 + delta;                  /* > 0: bends like the reference circle */
-    if (kappa == 0.0 || !isfinite(kappa)) { out->status = 2; return -1; }
-    double R = 1.0 / fabs(kappa);
-    double sgf = kappa > 0.0 ? sgn : -sgn;            /* orientation about the fitted centre */
-    int qf = sgf > 0.0 ? -1 : 1;
-    double ds0 = s[1] - s[0];
-    double alpha = (xT[1] - xT[0]) / ds0 + 0.5 * delta * ds0;
-    double nx = -Cx / R0, ny = -Cy / R0;              /* outward normal at hit 0 */
-    double tx = -sgn * ny, ty = sgn * nx;             /* direction of motion at hit 0 */
-    double ca = cos(alpha), sa = sin(alpha);
-    double n2x = nx * ca - tx * sa, n2y = ny * ca - ty * sa;
-    double P0x = xT[0] * nx, P0y = xT[0] * ny;
-    double Fx = P0x - n2x / kappa, Fy = P0y - n2y / kappa;   /* fitted centre */
-    double rx = (P0x - Fx) * fabs(kappa), ry = (P0y - Fy) * fabs(kappa); /* centre -> hit 0 */
-    double wx = -x0 - Fx, wy = -y0 - Fy;              /* centre -> transverse origin */
-    double dist = sqrt(wx * wx + wy * wy);
-    double ex = wx / dist, ey = wy / dist;
-    double tpx = -sgf * ey, tpy = sgf * ex;           /* direction of motion at the PCA */
-    double cot = (xL[1] - xL[0]) / ds0;
-    double psi = atan2(sgf * (ex * ry - ey * rx), ex * rx + ey * ry);
-    out->pt = ORC_K_PT * P->bfield * R;
-    out->phi = atan2(tpy, tpx);
-    out->cot_theta = cot;
-    out->dxy = qf * (dist - R);
-    out->dz = xL[0] - cot * (R * psi);
+    conv_geom G = {R0, Cx, Cy, sgn, x0, y0, s[1] - s[0], ORC_K_PT * P->bfield};
+    const double q[5] = {xT[0], xT[1], xT[n], xL[0], xL[1]};
+    int st = bl_convert(&G, q, out);
+    if (st) { out->status = st; return -1; }
     out->chi2 = chi2T + chi2L;
-    out->charge = qf;
-    out->status = 0;
+    if (cov15 && bl_cov(&G, q, AT, n + 1, n, AL, cov15) != 0) { out->status = 5; return -1; }
     return 0;
+}
+
+int orc_fit_one(int n, const double *X, const double *Y, const double *Z, const uint16_t *lay,
+                const orc_params *P, orc_track *out)
+{
+    return fit_core(n, X, Y, Z, lay, P, out, NULL);
+}
+
+/* The fit and the covariance of (q/pT, phi, cot, dxy, dz) (15 doubles, upper triangle). */
+int orc_fit_cov(int n, const double *X, const double *Y, const double *Z, const uint16_t *lay,
+                const orc_params *P, orc_track *out, double *cov15)
+{
+    return fit_core(n, X, Y, Z, lay, P, out, cov15);
 }
 
 /* Fit m ntuplets given as padded rows of ORC_MAXH hits (FP64 coordinates). */
