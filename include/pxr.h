@@ -119,6 +119,11 @@ extern "C" {
  *   track of the event that shares a hit with it ranks strictly better (more hits, or as many and
  *   a smaller chi2 / ndof).  One round: a track is dropped by a better one even if that one is
  *   dropped in turn.  Without clean_shared, KEPT equals GOOD.
+ * Covariance (fit_cov).  The fitted offsets u_0, u_1 and curvature correction of the transverse
+ *   broken line and the line values v_0, v_1 have the covariance of the two linear least-squares
+ *   problems (the corresponding blocks of the inverse normal matrices; the two fits are
+ *   independent); it is propagated to (q/pT, phi, cot_theta, dxy, dz) through the conversion,
+ *   linearised around the solution by central differences in FP64.
  */
 typedef struct pxr_params {
     uint32_t n_layers;                         /* <= PXR_MAX_LAYERS; hit layer ids < n_layers */
@@ -153,6 +158,8 @@ typedef struct pxr_params {
     double chi2_max;                           /* selection: chi2 per degree of freedom, >= 0;
                                                   0 = no cut */
     uint32_t clean_shared;                     /* selection: 0 or 1 (shared-hit cleaning) */
+    uint32_t fit_cov;                          /* 1: compute each track's covariance
+                                                  (pxr_tracks.cov); 0: not computed */
 } pxr_params;
 
 /* Context configuration. */
@@ -182,6 +189,9 @@ typedef struct pxr_tracks {
     int8_t *charge;             /* [capacity] */
     int8_t *fit_status;         /* [capacity] 0 ok, 1 collinear, 2 zero curvature, 3 Cholesky */
     uint8_t *quality;           /* [capacity] PXR_Q_* bits of the selection */
+    double *cov;                /* [capacity * 15] covariance of (q/pT [1/GeV], phi, cot_theta,
+                                   dxy, dz), upper triangle row by row; NaN when fit_cov was 0
+                                   or the fit failed */
 } pxr_tracks;
 
 typedef struct pxr_ctx pxr_ctx;

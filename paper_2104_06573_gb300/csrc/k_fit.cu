@@ -115,11 +115,13 @@ __device__ __forceinline__ void band_solve(const T (&il)[N], const T (&l1)[N], c
 // weights wk[j] (reciprocal variances), and (CURV) one curvature unknown.  g[i] = 1/(s[i+1]-s[i])
 // and h[i] = s[i+1]-s[i].  Normal equations: a pentadiagonal block for the offsets (each kink
 // couples three neighbours) bordered by the curvature row; the border is eliminated through the
-// Schur complement.  Returns the offsets x, the curvature correction and the chi2 at the minimum.
-template <int N, bool CURV, typename T>
+// Schur complement.  Returns the offsets x, the curvature correction and the chi2 at the minimum;
+// with CV, also the covariance of (x_0, x_1[, delta]) (the corresponding block of the inverse
+// normal matrix: cv = c00, c01, c11 and, with CURV, c0d, c1d, cdd).
+template <int N, bool CURV, typename T, bool CV = false>
 __device__ __forceinline__ bool broken_line_n(const T (&g)[N], const T (&h)[N], const T (&meas)[N],
                                               const T (&w)[N], const T (&wk)[N], T (&x)[N],
-                                              T &delta, T &chi2)
+                                              T &delta, T &chi2, T *cv = nullptr)
 {
     T d0[N], d1[N], d2[N], c[N], b[N];
     T dd = T(0);
@@ -152,8 +154,8 @@ __device__ __forceinline__ bool broken_line_n(const T (&g)[N], const T (&h)[N], 
     if (!band_factor<N, T>(d0, d1, d2)) return false;
     band_solve<N, T>(d0, d1, d2, b, x);
     delta = T(0);
+    T z[N], schur = T(1);
     if (CURV) {
-        T z[N];
         band_solve<N, T>(d0, d1, d2, c, z);
         T cy = T(0), cz = T(0);
 #pragma unroll
@@ -161,11 +163,34 @@ __device__ __forceinline__ bool broken_line_n(const T (&g)[N], const T (&h)[N], 
             cy += c[i] * x[i];
             cz += c[i] * z[i];
         }
-        const T schur = dd - cz;
+        schur = dd - cz;
         if (!(schur > T(0))) return false;
         delta = -cy / schur;
 #pragma unroll
         for (int i = 0; i < N; ++i) x[i] -= z[i] * delta;
+    }
+    if constexpr (CV) {
+        // columns 0 and 1 of the inverse of the pentadiagonal block; the bordered inverse adds
+        // z z^T / S to it, with -z / S and 1 / S for the curvature (S the Schur complement)
+        T e[N], y0[N], y1[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) e[i] = i == 0 ? T(1) : T(0);
+        band_solve<N, T>(d0, d1, d2, e, y0);
+#pragma unroll
+        for (int i = 0; i < N; ++i) e[i] = i == 1 ? T(1) : T(0);
+        band_solve<N, T>(d0, d1, d2, e, y1);
+        cv[0] = y0[0];
+        cv[1] = y0[1];
+        cv[2] = y1[1];
+        if (CURV) {
+            const T is = T(1) / schur;
+            cv[0] += z[0] * z[0] * is;
+            cv[1] += z[0] * z[1] * is;
+            cv[2] += z[1] * z[1] * is;
+            cv[3] = -z[0] * is;
+            cv[4] = -z[1] * is;
+            cv[5] = is;
+        }
     }
     T c2 = T(0);
 #pragma unroll
@@ -183,14 +208,70 @@ __device__ __forceinline__ bool broken_line_n(const T (&g)[N], const T (&h)[N], 
     return true;
 }
 
+// Geometry of the conversion: the reference circle (reciprocal radius, centre, orientation) in
+// the frame of hit 0, the first arc-length step (and its reciprocal), hit 0, and K B.
+template <typename T>
+struct ConvGeom {
+    T iR0, Cx, Cy, sgs, g0, ds0, X0, Y0, kB;
+};
+
+// Conversion of the fitted offsets u_0, u_1, curvature correction delta and line values v_0, v_1
+// to the point of closest approach: curvature, direction at hit 0 turned by the fitted slope,
+// fitted centre, PCA; false when the fitted curvature vanishes.
+template <bool FT, typename T>
+__device__ __forceinline__ bool bl_convert(const ConvGeom<T> &G, T u0, T u1, T delta, T v0, T v1,
+                                           FitOut &o)
+{
+    const T kappa = G.iR0 + delta;
+    if (kappa == T(0) || !isfinite(kappa)) return false;
+    const T R = T(1) / fabs(kappa);
+    const T sgs = G.sgs;
+    const T sgf = kappa > T(0) ? sgs : -sgs;
+    const T ds0 = G.ds0;
+    const T alpha = (u1 - u0) * G.g0 + T(0.5) * delta * ds0;
+    const T nx = -G.Cx * G.iR0, ny = -G.Cy * G.iR0;
+    const T tx = -sgs * ny, ty = sgs * nx;
+    T ca, sa;
+    if constexpr (FT) {
+        // cos of a small angle rounds to 1 in float; 1 - 2 sin^2(a/2) keeps its deviation
+        const T sh = T(sinf(float(alpha * T(0.5))));
+        ca = T(1) - T(2) * sh * sh;
+        sa = T(sinf(float(alpha)));
+    } else {
+        ca = cos(alpha);
+        sa = sin(alpha);
+    }
+    const T n2x = nx * ca - tx * sa, n2y = ny * ca - ty * sa;
+    const T P0x = u0 * nx, P0y = u0 * ny;
+    const T rk = kappa > T(0) ? R : -R;                  // 1 / kappa
+    const T Fx = P0x - n2x * rk, Fy = P0y - n2y * rk;
+    const T rx = (P0x - Fx) * fabs(kappa), ry = (P0y - Fy) * fabs(kappa);
+    const T wx = -G.X0 - Fx, wy = -G.Y0 - Fy;
+    const T d2 = wx * wx + wy * wy;
+    const T idist = rsqrt_t(d2);
+    const T dist = d2 * idist;
+    const T ex = wx * idist, ey = wy * idist;
+    const T tpx = -sgf * ey, tpy = sgf * ex;
+    const T cot = (v1 - v0) * G.g0;
+    const T psi = atan2_t<FT>(sgf * (ex * ry - ey * rx), ex * rx + ey * ry);
+    const int qf = sgf > T(0) ? -1 : 1;
+    o.pt = double(G.kB * R);
+    o.phi = double(atan2_t<FT>(tpy, tpx));
+    o.cot = double(cot);
+    o.dxy = double(T(qf) * (dist - R));
+    o.dz = double(v0 - cot * (R * psi));
+    o.q = (int8_t)qf;
+    return true;
+}
+
 // TC: prefit + residuals + arc lengths; T: everything else (scattering, solves, conversion);
 // FT: float transcendentals (angles and logarithms need ~1e-7 relative, far inside the
 // tolerances).  Divisions and square roots are shared where the method allows (one reciprocal
 // per arc-length step, one scattering angle per surface type, reciprocal Cholesky pivots): they
 // are the costly operations of the double-precision path.
-template <int N, typename TC, typename T, bool FT>
+template <int N, typename TC, typename T, bool FT, bool COV>
 __device__ void fit_n(const float *X, const float *Y, const float *Z, const uint8_t *L,
-                      const DevParams &p, FitOut &o)
+                      const DevParams &p, FitOut &o, double *cov15)
 {
     o = FitOut{0, 0, 0, 0, 0, 0, 0, 0};
     TC px[N], py[N];
@@ -276,8 +357,9 @@ __device__ void fit_n(const float *X, const float *Y, const float *Z, const uint
         if (!isfinite(wkT[j]) || !isfinite(wkL[j])) { o.status = 4; return; }
 
     T xT[N], xL[N], delta, dummy, chi2T, chi2L;
-    if (!broken_line_n<N, true, T>(g, h, yr, wT, wkT, xT, delta, chi2T) ||
-        !broken_line_n<N, false, T>(g, h, z, wL, wkL, xL, dummy, chi2L)) {
+    T cvT[6], cvL[3];
+    if (!broken_line_n<N, true, T, COV>(g, h, yr, wT, wkT, xT, delta, chi2T, cvT) ||
+        !broken_line_n<N, false, T, COV>(g, h, z, wL, wkL, xL, dummy, chi2L, cvL)) {
         o.status = 3;
         return;
     }
@@ -285,69 +367,88 @@ __device__ void fit_n(const float *X, const float *Y, const float *Z, const uint
     // conversion to the point of closest approach
     const T R0s = T(R0);
     const T iR0 = T(1) / R0s;
-    const T kappa = iR0 + delta;
-    if (kappa == T(0) || !isfinite(kappa)) { o.status = 2; return; }
-    const T R = T(1) / fabs(kappa);
-    const T sgs = T(sgn);
-    const T sgf = kappa > T(0) ? sgs : -sgs;
-    const T ds0 = h[0];
-    const T alpha = (xT[1] - xT[0]) * g[0] + T(0.5) * delta * ds0;
-    const T nx = -T(Cx) * iR0, ny = -T(Cy) * iR0;
-    const T tx = -sgs * ny, ty = sgs * nx;
-    T ca, sa;
-    if constexpr (FT) {
-        // cos of a small angle rounds to 1 in float; 1 - 2 sin^2(a/2) keeps its deviation
-        const T sh = T(sinf(float(alpha * T(0.5))));
-        ca = T(1) - T(2) * sh * sh;
-        sa = T(sinf(float(alpha)));
-    } else {
-        ca = cos(alpha);
-        sa = sin(alpha);
-    }
-    const T n2x = nx * ca - tx * sa, n2y = ny * ca - ty * sa;
-    const T P0x = xT[0] * nx, P0y = xT[0] * ny;
-    const T rk = kappa > T(0) ? R : -R;                  // 1 / kappa
-    const T Fx = P0x - n2x * rk, Fy = P0y - n2y * rk;
-    const T rx = (P0x - Fx) * fabs(kappa), ry = (P0y - Fy) * fabs(kappa);
-    const T wx = -T(X[0]) - Fx, wy = -T(Y[0]) - Fy;
-    const T d2 = wx * wx + wy * wy;
-    const T idist = rsqrt_t(d2);
-    const T dist = d2 * idist;
-    const T ex = wx * idist, ey = wy * idist;
-    const T tpx = -sgf * ey, tpy = sgf * ex;
-    const T cot = (xL[1] - xL[0]) * g[0];
-    const T psi = atan2_t<FT>(sgf * (ex * ry - ey * rx), ex * rx + ey * ry);
-    const int qf = sgf > T(0) ? -1 : 1;
-    o.pt = double(T(kKpt * p.bfield) * R);
-    o.phi = double(atan2_t<FT>(tpy, tpx));
-    o.cot = double(cot);
-    o.dxy = double(T(qf) * (dist - R));
-    o.dz = double(xL[0] - cot * (R * psi));
+    const ConvGeom<T> G{iR0, T(Cx), T(Cy), T(sgn), g[0], h[0], T(X[0]), T(Y[0]),
+                        T(kKpt * p.bfield)};
+    if (!bl_convert<FT, T>(G, xT[0], xT[1], delta, xL[0], xL[1], o)) { o.status = 2; return; }
     o.chi2 = double(chi2T + chi2L);
-    o.q = (int8_t)qf;
     o.status = 0;
+    if constexpr (COV) {
+        // covariance of (q/pT, phi, cot, dxy, dz): the fitted values' covariance (the blocks of
+        // the inverse normal matrices; the two broken lines are independent) through the
+        // conversion, linearised by central differences in FP64 with steps of 1e-3 standard
+        // deviations
+        double C[5][5];
+#pragma unroll
+        for (int a = 0; a < 5; ++a)
+#pragma unroll
+            for (int c = 0; c < 5; ++c) C[a][c] = 0.0;
+        C[0][0] = cvT[0]; C[0][1] = C[1][0] = cvT[1]; C[1][1] = cvT[2];
+        C[0][2] = C[2][0] = cvT[3]; C[1][2] = C[2][1] = cvT[4]; C[2][2] = cvT[5];
+        C[3][3] = cvL[0]; C[3][4] = C[4][3] = cvL[1]; C[4][4] = cvL[2];
+        const ConvGeom<double> Gd{double(G.iR0), double(G.Cx), double(G.Cy), double(G.sgs),
+                                  double(G.g0), double(G.ds0), double(G.X0), double(G.Y0),
+                                  double(G.kB)};
+        const double q0[5] = {double(xT[0]), double(xT[1]), double(delta), double(xL[0]),
+                              double(xL[1])};
+        double J[5][5];
+        bool ok = true;
+        for (int k = 0; k < 5; ++k) {
+            const double st = 1e-3 * sqrt(C[k][k]);
+            ok &= st > 0.0;
+            double qp[5], qm[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) { qp[i] = q0[i]; qm[i] = q0[i]; }
+            qp[k] += st;
+            qm[k] -= st;
+            FitOut a, c;
+            ok &= bl_convert<false, double>(Gd, qp[0], qp[1], qp[2], qp[3], qp[4], a);
+            ok &= bl_convert<false, double>(Gd, qm[0], qm[1], qm[2], qm[3], qm[4], c);
+            const double va[5] = {a.q / a.pt, a.phi, a.cot, a.dxy, a.dz};
+            const double vc[5] = {c.q / c.pt, c.phi, c.cot, c.dxy, c.dz};
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                double d = va[i] - vc[i];
+                if (i == 1) d = remainder(d, 6.283185307179586);   // azimuths modulo 2 pi
+                J[i][k] = d / (2.0 * st);
+            }
+        }
+        int w = 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int j = i; j < 5; ++j) {
+                double acc = 0.0;
+#pragma unroll
+                for (int a = 0; a < 5; ++a)
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) acc += J[i][a] * C[a][c] * J[j][c];
+                cov15[w++] = ok ? acc : __longlong_as_double(0x7FF8000000000000LL);
+            }
+    }
 }
 
-template <typename TC, typename T, bool FT>
+template <typename TC, typename T, bool FT, bool COV>
 __device__ __forceinline__ void fit_track(int n, const float *X, const float *Y, const float *Z,
-                                          const uint8_t *L, const DevParams &p, FitOut &o)
+                                          const uint8_t *L, const DevParams &p, FitOut &o,
+                                          double *cov15)
 {
     switch (n) {
-    case 3: fit_n<3, TC, T, FT>(X, Y, Z, L, p, o); break;
-    case 4: fit_n<4, TC, T, FT>(X, Y, Z, L, p, o); break;
-    case 5: fit_n<5, TC, T, FT>(X, Y, Z, L, p, o); break;
-    case 6: fit_n<6, TC, T, FT>(X, Y, Z, L, p, o); break;
+    case 3: fit_n<3, TC, T, FT, COV>(X, Y, Z, L, p, o, cov15); break;
+    case 4: fit_n<4, TC, T, FT, COV>(X, Y, Z, L, p, o, cov15); break;
+    case 5: fit_n<5, TC, T, FT, COV>(X, Y, Z, L, p, o, cov15); break;
+    case 6: fit_n<6, TC, T, FT, COV>(X, Y, Z, L, p, o, cov15); break;
     default: o = FitOut{0, 0, 0, 0, 0, 0, 0, 4};
     }
 }
 
+template <bool COV>
 __device__ __forceinline__ void fit_dispatch(int n, const float *X, const float *Y,
                                              const float *Z, const uint8_t *L,
-                                             const DevParams &p, FitOut &o)
+                                             const DevParams &p, FitOut &o, double *cov15)
 {
-    if (p.fit_mode == FIT_MIXED) fit_track<double, double, true>(n, X, Y, Z, L, p, o);
-    else if (p.fit_mode == FIT_FP32) fit_track<float, float, false>(n, X, Y, Z, L, p, o);
-    else fit_track<double, double, false>(n, X, Y, Z, L, p, o);
+    if (p.fit_mode == FIT_MIXED) fit_track<double, double, true, COV>(n, X, Y, Z, L, p, o, cov15);
+    else if (p.fit_mode == FIT_FP32) fit_track<float, float, false, COV>(n, X, Y, Z, L, p, o, cov15);
+    else fit_track<double, double, false, COV>(n, X, Y, Z, L, p, o, cov15);
 }
 
 // Selection rank of a good track for shared-hit cleaning: more hits first, then smaller
@@ -368,6 +469,7 @@ __device__ __forceinline__ double chi2_ndof(double chi2, int n)
 // number of outputs is read on the device, so no thread is spent on unused capacity.  After the
 // fit, the selection cuts give the track's quality; with shared-hit cleaning a good track offers
 // its rank key to each of its hits (the smallest key of a hit wins, k_keep reads them).
+template <bool COV>
 __global__ void __launch_bounds__(256, 2) k_fit(DevBatch b, DevParams p)
 {
     const uint32_t n_out = b.out_evt[b.E];
@@ -394,7 +496,14 @@ __global__ void __launch_bounds__(256, 2) k_fit(DevBatch b, DevParams p)
             }
         }
         FitOut f;
-        fit_dispatch(n, X, Y, Z, L, p, f);
+        double cv[COV ? 15 : 1];
+        fit_dispatch<COV>(n, X, Y, Z, L, p, f, cv);
+        if constexpr (COV) {
+#pragma unroll
+            for (int k = 0; k < 15; ++k)
+                b.o_cov[(size_t)o * 15 + k] =
+                    f.status == 0 ? cv[k] : __longlong_as_double(0x7FF8000000000000LL);
+        }
         b.o_nh[o] = (uint8_t)n;
         b.o_pt[o] = f.pt; b.o_phi[o] = f.phi; b.o_cot[o] = f.cot;
         b.o_dxy[o] = f.dxy; b.o_dz[o] = f.dz; b.o_chi2[o] = f.chi2;
@@ -445,7 +554,8 @@ void launch_fit(const DevBatch &b, const DevParams &p, uint32_t total, cudaStrea
     uint64_t cap = (uint64_t)sms * p.grid_per_sm[5] * (256 / tpb);
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
-    k_fit<<<(unsigned)blocks, tpb, 0, s>>>(b, p);
+    if (p.cov) k_fit<true><<<(unsigned)blocks, tpb, 0, s>>>(b, p);
+    else k_fit<false><<<(unsigned)blocks, tpb, 0, s>>>(b, p);
 }
 
 void launch_keep(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
@@ -481,7 +591,7 @@ __global__ void __launch_bounds__(128) k_fit_batch(uint32_t m, const uint8_t *nh
             }
         }
         FitOut f;
-        fit_dispatch(n <= (int)stride ? n : 0, X, Y, Z, L, p, f);
+        fit_dispatch<false>(n <= (int)stride ? n : 0, X, Y, Z, L, p, f, nullptr);
         pt[t] = f.pt; phi[t] = f.phi; cot[t] = f.cot; dxy[t] = f.dxy; dz[t] = f.dz;
         chi2[t] = f.chi2; q[t] = f.q; status[t] = f.status;
     }

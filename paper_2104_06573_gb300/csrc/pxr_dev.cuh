@@ -71,6 +71,7 @@ struct DevParams {
     double bfield, sigma_rphi, sigma_z, x_over_x0;
     double pt_min, chi2_max;            // track selection (0: no cut)
     uint32_t clean;                     // shared-hit cleaning
+    uint32_t cov;                       // fit covariance wanted
 };
 
 struct DevBatch {
@@ -127,6 +128,7 @@ struct DevBatch {
     double *o_pt, *o_phi, *o_cot, *o_dxy, *o_dz, *o_chi2;
     int8_t *o_q, *o_status;
     uint8_t *o_ql;                      // quality bits (PXR_Q_*)
+    double *o_cov;                      // [out_cap * 15] covariances (only with the cov option)
     unsigned long long *best;           // [N] shared-hit cleaning: best rank key per hit (caller
                                         //   order, events back to back)
 };

@@ -125,6 +125,7 @@ static int check_params(const pxr_params *p, DevParams *d)
     if (!(p->pt_min >= 0.0) || !(p->chi2_max >= 0.0) || !std::isfinite(p->pt_min) ||
         !std::isfinite(p->chi2_max) || p->clean_shared > 1)
         return fail(PXR_EINVAL, "pt_min and chi2_max must be finite and >= 0, clean_shared 0 or 1");
+    if (p->fit_cov > 1) return fail(PXR_EINVAL, "fit_cov must be 0 or 1");
     if (!d) return PXR_OK;
     std::memset(d, 0, sizeof(*d));
     d->n_layers = p->n_layers;
@@ -167,6 +168,7 @@ static int check_params(const pxr_params *p, DevParams *d)
     d->pt_min = p->pt_min;
     d->chi2_max = p->chi2_max;
     d->clean = p->clean_shared;
+    d->cov = p->fit_cov;
     // CA levels: a layer's level is 1 + the highest level of its pairs' inner layers (0 without
     // in-pairs); junction layers (in- and out-pairs) are processed level by level, so that every
     // cell has all its in-edges before its own out-edges are built
@@ -254,7 +256,7 @@ struct PlanOffsets {
     size_t cnt, bkt, hs, r64, hmeta, hphi, item, cell_in, cell_out,
         nbr_first,
         nbr_n, nbr, mindepth, root_list, live, front_list, front_snap, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, out_evt, o_nh,
-        o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status, o_ql, best;
+        o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status, o_ql, best, o_cov;
     size_t total;
 };
 
@@ -314,6 +316,7 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.o_status = L.add(T);
     o.o_ql = L.add(T);
     o.best = L.add(dp.clean ? 8 * N : 0);
+    o.o_cov = L.add(dp.cov ? 8 * 15 * T : 0);
     o.total = L.add(0);
     return o;
 }
@@ -505,6 +508,7 @@ static void plan_bind(pxr_plan *P)
     b.o_status = (int8_t *)(r + o.o_status);
     b.o_ql = (uint8_t *)(r + o.o_ql);
     b.best = (unsigned long long *)(r + o.best);
+    b.o_cov = (double *)(r + o.o_cov);
 }
 
 // Fill the per-event capacity prefixes from per-layer counts (lcount: E x (kMaxLayers+1)).
@@ -805,11 +809,13 @@ struct HostTracks {
     std::vector<double> pt, phi, cot, dxy, dz, chi2;
     std::vector<int8_t> q, st;
     std::vector<uint8_t> ql;
+    std::vector<double> cov;             // 15 per track, or empty (covariance not computed)
     size_t size() const { return nh.size(); }
-    void resize(size_t n)
+    void resize(size_t n, bool with_cov = false)
     {
         nh.resize(n); hits.resize(n * kMaxHits); pt.resize(n); phi.resize(n); cot.resize(n);
         dxy.resize(n); dz.resize(n); chi2.resize(n); q.resize(n); st.resize(n); ql.resize(n);
+        cov.resize(with_cov ? 15 * n : 0);
     }
 };
 
@@ -855,48 +861,34 @@ static void canonical_order(const uint32_t *hits, size_t n, std::vector<uint32_t
     }
 }
 
-// Copy n tracks of the source arrays into out in canonical order.
-static int emit_tracks(const uint8_t *nh, const uint32_t *hits, const double *pt,
-                       const double *phi, const double *cot, const double *dxy, const double *dz,
-                       const double *chi2, const int8_t *q, const int8_t *st, const uint8_t *ql,
-                       size_t n, int32_t status, pxr_tracks *out, bool in_order = false)
+// Copy the tracks of h into out, in canonical order (in_order: h already is).  A covariance
+// that was not computed reads as NaN.
+static int emit_tracks(const HostTracks &h, int32_t status, pxr_tracks *out, bool in_order = false)
 {
+    const size_t n = h.size();
     out->n_tracks = (uint32_t)n;
     out->status = status;
     if (n > out->capacity) return fail(PXR_ETRUNC, "track capacity too small");
-    if (in_order) {                          // already canonical: plain copies
-        auto cp = [n](void *dst, const void *src, size_t sz) {
-            if (dst && n) std::memcpy(dst, src, sz * n);
-        };
-        cp(out->n_hits, nh, 1);
-        cp(out->hit_idx, hits, 4 * kMaxHits);
-        cp(out->pt, pt, 8);
-        cp(out->phi, phi, 8);
-        cp(out->cot_theta, cot, 8);
-        cp(out->dxy, dxy, 8);
-        cp(out->dz, dz, 8);
-        cp(out->chi2, chi2, 8);
-        cp(out->charge, q, 1);
-        cp(out->fit_status, st, 1);
-        cp(out->quality, ql, 1);
-        return PXR_OK;
-    }
     std::vector<uint32_t> ord;
-    canonical_order(hits, n, ord);
+    if (!in_order) canonical_order(h.hits.data(), n, ord);
     for (size_t k = 0; k < n; ++k) {
-        uint32_t s = ord[k];
-        if (out->n_hits) out->n_hits[k] = nh[s];
+        const size_t s = in_order ? k : ord[k];
+        if (out->n_hits) out->n_hits[k] = h.nh[s];
         if (out->hit_idx)
-            std::memcpy(out->hit_idx + k * kMaxHits, hits + (size_t)s * kMaxHits, 4 * kMaxHits);
-        if (out->pt) out->pt[k] = pt[s];
-        if (out->phi) out->phi[k] = phi[s];
-        if (out->cot_theta) out->cot_theta[k] = cot[s];
-        if (out->dxy) out->dxy[k] = dxy[s];
-        if (out->dz) out->dz[k] = dz[s];
-        if (out->chi2) out->chi2[k] = chi2[s];
-        if (out->charge) out->charge[k] = q[s];
-        if (out->fit_status) out->fit_status[k] = st[s];
-        if (out->quality) out->quality[k] = ql[s];
+            std::memcpy(out->hit_idx + k * kMaxHits, h.hits.data() + s * kMaxHits, 4 * kMaxHits);
+        if (out->pt) out->pt[k] = h.pt[s];
+        if (out->phi) out->phi[k] = h.phi[s];
+        if (out->cot_theta) out->cot_theta[k] = h.cot[s];
+        if (out->dxy) out->dxy[k] = h.dxy[s];
+        if (out->dz) out->dz[k] = h.dz[s];
+        if (out->chi2) out->chi2[k] = h.chi2[s];
+        if (out->charge) out->charge[k] = h.q[s];
+        if (out->fit_status) out->fit_status[k] = h.st[s];
+        if (out->quality) out->quality[k] = h.ql[s];
+        if (out->cov) {
+            if (h.cov.empty()) std::fill(out->cov + 15 * k, out->cov + 15 * k + 15, NAN);
+            else std::memcpy(out->cov + 15 * k, h.cov.data() + 15 * s, 15 * sizeof(double));
+        }
     }
     return PXR_OK;
 }
@@ -930,9 +922,8 @@ extern "C" int pxr_plan_tracks(pxr_plan *P, uint32_t e, pxr_tracks *out)
         (rc = d2h(h.q, P->db.o_q + a, n)) || (rc = d2h(h.st, P->db.o_status + a, n)) ||
         (rc = d2h(h.ql, P->db.o_ql + a, n)))
         return rc;
-    return emit_tracks(h.nh.data(), h.hits.data(), h.pt.data(), h.phi.data(), h.cot.data(),
-                       h.dxy.data(), h.dz.data(), h.chi2.data(), h.q.data(), h.st.data(),
-                       h.ql.data(), n, flags_status(flags), out);
+    if (P->dp.cov && (rc = d2h(h.cov, P->db.o_cov + 15 * a, 15 * n))) return rc;
+    return emit_tracks(h, flags_status(flags), out);
 }
 
 // Debug content of one event of a plan region (also used by the serving path).
@@ -1090,7 +1081,7 @@ struct Batch {
     size_t reserved = 0;
     uint32_t total = 0;
     size_t o_nh = 0, o_hits = 0, o_pt = 0, o_phi = 0, o_cot = 0, o_dxy = 0, o_dz = 0,
-           o_chi2 = 0, o_q = 0, o_st = 0, o_ql = 0;
+           o_chi2 = 0, o_q = 0, o_st = 0, o_ql = 0, o_cov = 0;
     ~Batch()
     {
         if (ev_counts) cudaEventDestroy(ev_counts);
@@ -1238,6 +1229,7 @@ static bool progress_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
         B.o_q = L.add(T);
         B.o_st = L.add(T);
         B.o_ql = L.add(T);
+        B.o_cov = L.add(P->dp.cov ? 8 * 15 * (size_t)T : 0);
         bool ok = sb.out.reserve(L.add(0) + 256);
         const DevBatch &d = P->db;
         char *ho = sb.out.p;
@@ -1256,6 +1248,7 @@ static bool progress_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
             cp(B.o_q, d.o_q, T);
             cp(B.o_st, d.o_status, T);
             cp(B.o_ql, d.o_ql, T);
+            if (P->dp.cov) cp(B.o_cov, d.o_cov, 8 * 15 * (size_t)T);
         }
         ok &= cudaEventRecord(B.ev_data, s) == cudaSuccess;
         if (!ok) ctx->sched_error = "device-to-host copy failed";
@@ -1281,7 +1274,7 @@ static bool progress_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
             if (!ts[e]) continue;
             Ticket &t = *ts[e];
             const uint32_t a = hev[e], n = hev[e + 1] - a;
-            t.res.resize(n);
+            t.res.resize(n, P->dp.cov != 0);
             if (n) {
                 // canonical order here, on the scheduler thread, so that a fetch only copies
                 auto hp = [&](size_t off) { return ho + off; };
@@ -1297,6 +1290,7 @@ static bool progress_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
                 const int8_t *q = (const int8_t *)hp(B.o_q + a);
                 const int8_t *st = (const int8_t *)hp(B.o_st + a);
                 const uint8_t *ql = (const uint8_t *)hp(B.o_ql + a);
+                const double *cv = (const double *)hp(B.o_cov + 8 * 15 * (size_t)a);
                 for (uint32_t k = 0; k < n; ++k) {
                     const uint32_t s_ = ord[k];
                     t.res.nh[k] = nh[s_];
@@ -1311,6 +1305,9 @@ static bool progress_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
                     t.res.q[k] = q[s_];
                     t.res.st[k] = st[s_];
                     t.res.ql[k] = ql[s_];
+                    if (P->dp.cov)
+                        std::memcpy(&t.res.cov[15 * (size_t)k], cv + 15 * (size_t)s_,
+                                    15 * sizeof(double));
                 }
             }
         }
@@ -1548,9 +1545,7 @@ extern "C" int pxr_fetch_tracks(pxr_ctx *ctx, uint64_t ticket, pxr_tracks *out)
         if (t->state != 2) return fail(PXR_EBUSY, "event not finished");
     }
     const HostTracks &r = t->res;
-    int rc = emit_tracks(r.nh.data(), r.hits.data(), r.pt.data(), r.phi.data(), r.cot.data(),
-                         r.dxy.data(), r.dz.data(), r.chi2.data(), r.q.data(), r.st.data(),
-                         r.ql.data(), r.size(), t->status, out, true);
+    int rc = emit_tracks(r, t->status, out, true);
     if (rc) return rc;
     std::lock_guard<std::mutex> g(ctx->mu);
     ctx->tickets.erase(ticket);

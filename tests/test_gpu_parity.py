@@ -272,6 +272,41 @@ def test_selection_matches_oracle(ctx, orc, which):
     assert np.all(off["quality"][~ok] == 0)
 
 
+@pytest.mark.parametrize("fit", [pxr.FIT_FP64, pxr.FIT_MIXED])
+def test_covariance_matches_oracle(ctx, orc, fit):
+    """Track covariances (q/pT, phi, cot, dxy, dz) of the served tracks against the oracle's,
+    element by element relative to sqrt(C_ii C_jj): both linearise the same conversion (central
+    differences of different orders), so they agree to far better than 1e-3."""
+    P = synth.params_barrel_quadruplets()
+    ev = synth.make_event(12, 800, smear=True)
+    e = ev_tuple(ev)
+    got = run_plan(ctx, [e], P, pxr.CUT_FP32, fit=fit, debug=False, fit_cov=True)[0]["tracks"]
+    off = run_plan(ctx, [e], P, pxr.CUT_FP32, fit=fit, debug=False)[0]["tracks"]
+    assert np.all(np.isnan(off["cov"]))                  # not computed unless asked
+    # asking does not change the fit beyond round-off (the two kernel instantiations may fuse
+    # multiply-adds differently)
+    assert gpu_tuples(off) == gpu_tuples(got)
+    for k in pxr.TRACK_FIELDS:
+        assert np.allclose(off[k], got[k], rtol=1e-12, atol=1e-15), k
+    tup = gpu_tuples(got)
+    nt = len(tup)
+    X = np.zeros((nt, 8)); Y = np.zeros((nt, 8)); Z = np.zeros((nt, 8))
+    L = np.zeros((nt, 8), np.uint16)
+    nh = np.array([len(t) for t in tup], np.uint8)
+    for t, hits in enumerate(tup):
+        h = np.array(hits)
+        X[t, :len(h)], Y[t, :len(h)], Z[t, :len(h)] = ev.x[h], ev.y[h], ev.z[h]
+        L[t, :len(h)] = ev.layer[h]
+    fits, cov = orc.fit_cov_batch(nh, X, Y, Z, L, P)
+    ok = (fits["status"] == 0) & (got["fit_status"] == 0)
+    assert ok.sum() > 0.9 * nt
+    A, B = orc.cov_matrix(got["cov"][ok]), orc.cov_matrix(cov[ok])
+    d = np.sqrt(np.diagonal(B, axis1=1, axis2=2))
+    rel = np.abs(A - B) / (d[:, :, None] * d[:, None, :])
+    print("fit mode", fit, "max relative covariance difference", rel.max())
+    assert rel.max() < 1e-3
+
+
 def test_graph_equals_direct_and_bin_counts(ctx, orc):
     """Graph replay and direct launches agree; the result does not depend on the bin count."""
     P = synth.params_phase1()
