@@ -474,7 +474,8 @@ def _gpu_event_rate(pxr, ctx, ev, params, dev, stream, reps):
 def _selection_study(pxr, synth, ctx, dev, stream, n_events=256, reps=10):
     """Track selection (shared-hit cleaning) on the batch workload with smeared hits: its cost
     (step and fit+output stage time, selection off and on, L2 flushed between steps) and its
-    effect (fake fraction and the share of generated tracks kept, from the generator's truth)."""
+    effect (fake fraction and the share of generated tracks kept, from the generator's truth);
+    and the cost of the track covariance (fit_cov, "cov")."""
     import torch
     counts = synth.batch_track_counts(n_events, 0)
     evs = [synth.make_event(e, counts[e], smear=True) for e in range(n_events)]
@@ -486,9 +487,9 @@ def _selection_study(pxr, synth, ctx, dev, stream, n_events=256, reps=10):
     P = synth.params_barrel_quadruplets()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     res = {"events": n_events, "hits": int(off[-1])}
-    for name, clean in (("off", False), ("on", True)):
+    for name, clean, cov in (("off", False, False), ("on", True, False), ("cov", False, True)):
         prm = pxr.params_from(P, cut_mode=pxr.CUT_FP32, fit_mode=pxr.FIT_MIXED, n_phi_bins=1024,
-                              clean_shared=clean)
+                              clean_shared=clean, fit_cov=cov)
         plan = pxr.Plan(ctx, off, x, y, z, layer, prm, use_graph=True)
         st = np.zeros(5)
         with torch.cuda.stream(stream):
@@ -501,6 +502,9 @@ def _selection_study(pxr, synth, ctx, dev, stream, n_events=256, reps=10):
         st /= reps
         res["step_ms_" + name] = float(st.sum())
         res["fit_output_ms_" + name] = float(st[4])
+        if cov:
+            t0 = plan.pxr_plan_tracks(0)
+            res["cov_finite_fraction_event0"] = float(np.mean(np.isfinite(t0["cov"][:, 0])))
         if clean:
             n_all = n_good = n_kept = fake_all = fake_kept = 0
             found, kept_true, generated = set(), set(), 0
