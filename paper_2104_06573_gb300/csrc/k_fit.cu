@@ -32,7 +32,11 @@ __device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
 
 // Transcendentals in float (FT = true) or in the argument's own type.
 template <bool FT, typename T>
-__device__ __forceinline__ T atan2_t(T y, T x) { return FT ? T(atan2f(float(y), float(x))) : atan2(y, x); }
+__device__ __forceinline__ T atan2_t(T y, T x)
+{
+    if constexpr (FT) return T(atan2f(float(y), float(x)));
+    else return atan2(y, x);
+}
 template <bool FT, typename T>
 __device__ __forceinline__ T log_t(T v) { return FT ? T(logf(float(v))) : log(v); }
 
@@ -215,21 +219,71 @@ struct ConvGeom {
     T iR0, Cx, Cy, sgs, g0, ds0, X0, Y0, kB;
 };
 
+// Forward-mode derivatives: a value and its derivatives with respect to the five fitted values
+// (u_0, u_1, delta, v_0, v_1).  The conversion below runs on it to give the exact Jacobian of
+// the track parameters (the chain rule of each operation, no difference quotients).
+struct D5 {
+    double v, d[5];
+    __device__ D5(double x = 0.0) : v(x) { for (int i = 0; i < 5; ++i) d[i] = 0.0; }
+    __device__ explicit operator double() const { return v; }
+};
+__device__ __forceinline__ D5 operator+(const D5 &a, const D5 &b)
+{ D5 r(a.v + b.v); for (int i = 0; i < 5; ++i) r.d[i] = a.d[i] + b.d[i]; return r; }
+__device__ __forceinline__ D5 operator-(const D5 &a, const D5 &b)
+{ D5 r(a.v - b.v); for (int i = 0; i < 5; ++i) r.d[i] = a.d[i] - b.d[i]; return r; }
+__device__ __forceinline__ D5 operator-(const D5 &a)
+{ D5 r(-a.v); for (int i = 0; i < 5; ++i) r.d[i] = -a.d[i]; return r; }
+__device__ __forceinline__ D5 operator*(const D5 &a, const D5 &b)
+{ D5 r(a.v * b.v); for (int i = 0; i < 5; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i]; return r; }
+__device__ __forceinline__ D5 operator/(const D5 &a, const D5 &b)
+{ D5 r(a.v / b.v); for (int i = 0; i < 5; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v; return r; }
+__device__ __forceinline__ bool operator>(const D5 &a, const D5 &b) { return a.v > b.v; }
+__device__ __forceinline__ bool operator==(const D5 &a, const D5 &b) { return a.v == b.v; }
+__device__ __forceinline__ bool isfinite(const D5 &a) { return ::isfinite(a.v); }
+__device__ __forceinline__ D5 fabs(const D5 &a) { return a.v < 0.0 ? -a : a; }
+__device__ __forceinline__ D5 sin(const D5 &a)
+{ D5 r(::sin(a.v)); const double c = ::cos(a.v); for (int i = 0; i < 5; ++i) r.d[i] = c * a.d[i]; return r; }
+__device__ __forceinline__ D5 cos(const D5 &a)
+{ D5 r(::cos(a.v)); const double s = -::sin(a.v); for (int i = 0; i < 5; ++i) r.d[i] = s * a.d[i]; return r; }
+__device__ __forceinline__ D5 atan2(const D5 &y, const D5 &x)
+{
+    D5 r(::atan2(y.v, x.v));
+    const double q = 1.0 / (x.v * x.v + y.v * y.v);
+    for (int i = 0; i < 5; ++i) r.d[i] = (x.v * y.d[i] - y.v * x.d[i]) * q;
+    return r;
+}
+template <>
+__device__ __forceinline__ D5 rsqrt_t<D5>(D5 a)
+{
+    D5 r(::rsqrt(a.v));
+    const double k = -0.5 * r.v * r.v * r.v;
+    for (int i = 0; i < 5; ++i) r.d[i] = k * a.d[i];
+    return r;
+}
+// the overloads above must not hide the plain floating-point functions inside this namespace
+using ::atan2;
+using ::cos;
+using ::fabs;
+using ::isfinite;
+using ::sin;
+
 // Conversion of the fitted offsets u_0, u_1, curvature correction delta and line values v_0, v_1
 // to the point of closest approach: curvature, direction at hit 0 turned by the fitted slope,
-// fitted centre, PCA; false when the fitted curvature vanishes.
-template <bool FT, typename T>
-__device__ __forceinline__ bool bl_convert(const ConvGeom<T> &G, T u0, T u1, T delta, T v0, T v1,
-                                           FitOut &o)
+// fitted centre, PCA; false when the fitted curvature vanishes.  T carries the fitted values (a
+// floating type, or D5 for their Jacobian); TG the geometry.
+template <bool FT, typename T, typename TG>
+__device__ __forceinline__ bool convert_core(const ConvGeom<TG> &G, T u0, T u1, T delta, T v0,
+                                             T v1, T &pt, T &phi, T &cot, T &dxy, T &dz,
+                                             int &qf)
 {
-    const T kappa = G.iR0 + delta;
+    const T kappa = T(G.iR0) + delta;
     if (kappa == T(0) || !isfinite(kappa)) return false;
     const T R = T(1) / fabs(kappa);
-    const T sgs = G.sgs;
+    const T sgs = T(G.sgs);
     const T sgf = kappa > T(0) ? sgs : -sgs;
-    const T ds0 = G.ds0;
-    const T alpha = (u1 - u0) * G.g0 + T(0.5) * delta * ds0;
-    const T nx = -G.Cx * G.iR0, ny = -G.Cy * G.iR0;
+    const T ds0 = T(G.ds0);
+    const T alpha = (u1 - u0) * T(G.g0) + T(0.5) * delta * ds0;
+    const T nx = -T(G.Cx) * T(G.iR0), ny = -T(G.Cy) * T(G.iR0);
     const T tx = -sgs * ny, ty = sgs * nx;
     T ca, sa;
     if constexpr (FT) {
@@ -246,20 +300,34 @@ __device__ __forceinline__ bool bl_convert(const ConvGeom<T> &G, T u0, T u1, T d
     const T rk = kappa > T(0) ? R : -R;                  // 1 / kappa
     const T Fx = P0x - n2x * rk, Fy = P0y - n2y * rk;
     const T rx = (P0x - Fx) * fabs(kappa), ry = (P0y - Fy) * fabs(kappa);
-    const T wx = -G.X0 - Fx, wy = -G.Y0 - Fy;
+    const T wx = -T(G.X0) - Fx, wy = -T(G.Y0) - Fy;
     const T d2 = wx * wx + wy * wy;
     const T idist = rsqrt_t(d2);
     const T dist = d2 * idist;
     const T ex = wx * idist, ey = wy * idist;
     const T tpx = -sgf * ey, tpy = sgf * ex;
-    const T cot = (v1 - v0) * G.g0;
+    cot = (v1 - v0) * T(G.g0);
     const T psi = atan2_t<FT>(sgf * (ex * ry - ey * rx), ex * rx + ey * ry);
-    const int qf = sgf > T(0) ? -1 : 1;
-    o.pt = double(G.kB * R);
-    o.phi = double(atan2_t<FT>(tpy, tpx));
+    qf = sgf > T(0) ? -1 : 1;
+    pt = T(G.kB) * R;
+    phi = atan2_t<FT>(tpy, tpx);
+    dxy = T(double(qf)) * (dist - R);
+    dz = v0 - cot * (R * psi);
+    return true;
+}
+
+template <bool FT, typename T>
+__device__ __forceinline__ bool bl_convert(const ConvGeom<T> &G, T u0, T u1, T delta, T v0, T v1,
+                                           FitOut &o)
+{
+    T pt, phi, cot, dxy, dz;
+    int qf;
+    if (!convert_core<FT, T, T>(G, u0, u1, delta, v0, v1, pt, phi, cot, dxy, dz, qf)) return false;
+    o.pt = double(pt);
+    o.phi = double(phi);
     o.cot = double(cot);
-    o.dxy = double(T(qf) * (dist - R));
-    o.dz = double(v0 - cot * (R * psi));
+    o.dxy = double(dxy);
+    o.dz = double(dz);
     o.q = (int8_t)qf;
     return true;
 }
@@ -375,8 +443,7 @@ __device__ void fit_n(const float *X, const float *Y, const float *Z, const uint
     if constexpr (COV) {
         // covariance of (q/pT, phi, cot, dxy, dz): the fitted values' covariance (the blocks of
         // the inverse normal matrices; the two broken lines are independent) through the
-        // conversion, linearised by central differences in FP64 with steps of 1e-3 standard
-        // deviations
+        // conversion's Jacobian (forward-mode derivatives in FP64)
         double C[5][5];
 #pragma unroll
         for (int a = 0; a < 5; ++a)
@@ -388,29 +455,27 @@ __device__ void fit_n(const float *X, const float *Y, const float *Z, const uint
         const ConvGeom<double> Gd{double(G.iR0), double(G.Cx), double(G.Cy), double(G.sgs),
                                   double(G.g0), double(G.ds0), double(G.X0), double(G.Y0),
                                   double(G.kB)};
-        const double q0[5] = {double(xT[0]), double(xT[1]), double(delta), double(xL[0]),
-                              double(xL[1])};
+        D5 q0[5];
+        q0[0] = D5(double(xT[0]));
+        q0[1] = D5(double(xT[1]));
+        q0[2] = D5(double(delta));
+        q0[3] = D5(double(xL[0]));
+        q0[4] = D5(double(xL[1]));
+#pragma unroll
+        for (int k = 0; k < 5; ++k) q0[k].d[k] = 1.0;
+        D5 pt, phi, cot, dxy, dz;
+        int qf;
+        const bool ok = convert_core<false, D5, double>(Gd, q0[0], q0[1], q0[2], q0[3], q0[4],
+                                                        pt, phi, cot, dxy, dz, qf);
+        const D5 qpt = D5(double(qf)) / pt;
         double J[5][5];
-        bool ok = true;
+#pragma unroll
         for (int k = 0; k < 5; ++k) {
-            const double st = 1e-3 * sqrt(C[k][k]);
-            ok &= st > 0.0;
-            double qp[5], qm[5];
-#pragma unroll
-            for (int i = 0; i < 5; ++i) { qp[i] = q0[i]; qm[i] = q0[i]; }
-            qp[k] += st;
-            qm[k] -= st;
-            FitOut a, c;
-            ok &= bl_convert<false, double>(Gd, qp[0], qp[1], qp[2], qp[3], qp[4], a);
-            ok &= bl_convert<false, double>(Gd, qm[0], qm[1], qm[2], qm[3], qm[4], c);
-            const double va[5] = {a.q / a.pt, a.phi, a.cot, a.dxy, a.dz};
-            const double vc[5] = {c.q / c.pt, c.phi, c.cot, c.dxy, c.dz};
-#pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                double d = va[i] - vc[i];
-                if (i == 1) d = remainder(d, 6.283185307179586);   // azimuths modulo 2 pi
-                J[i][k] = d / (2.0 * st);
-            }
+            J[0][k] = qpt.d[k];
+            J[1][k] = phi.d[k];
+            J[2][k] = cot.d[k];
+            J[3][k] = dxy.d[k];
+            J[4][k] = dz.d[k];
         }
         int w = 0;
 #pragma unroll
