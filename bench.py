@@ -416,7 +416,7 @@ def extras(args, ctx, pxr, synth, P, params, evs, off, x, y, z, layer, dev, stre
             d2h = 0
             for t in tickets:
                 r = sctx.pxr_fetch_tracks(t)
-                d2h += r["n"] * (1 + 4 * pxr.MAX_HITS + 6 * 8 + 2) + 8
+                d2h += r["n"] * (1 + 4 * pxr.MAX_HITS + 6 * 8 + 3) + 8
             return time.perf_counter() - t0, d2h
         serve_all()
         times = []

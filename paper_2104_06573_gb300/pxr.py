@@ -200,12 +200,15 @@ TRACK_FIELDS = ("pt", "phi", "cot_theta", "dxy", "dz", "chi2")
 _TRACK_LAYOUT = (("n_hits", np.uint8, 1), ("hit_idx", np.uint32, MAX_HITS),
                  ("pt", np.float64, 1), ("phi", np.float64, 1), ("cot_theta", np.float64, 1),
                  ("dxy", np.float64, 1), ("dz", np.float64, 1), ("chi2", np.float64, 1),
-                 ("charge", np.int8, 1), ("fit_status", np.int8, 1), ("quality", np.uint8, 1), ("cov", np.float64, 15))
+                 ("charge", np.int8, 1), ("fit_status", np.int8, 1), ("quality", np.uint8, 1),
+                 ("cov", np.float64, 15))
 
 
-def _read_tracks(call, holder=None) -> dict:
+def _read_tracks(call, cov=False) -> dict:
     """Ask for the track count, then fill arrays of exactly that size (one allocation, the
-    library writes straight into it; nothing is copied afterwards)."""
+    library writes straight into it; nothing is copied afterwards).  The covariance array is
+    requested only with cov (it holds NaN unless the covariance was computed)."""
+    layout = _TRACK_LAYOUT if cov else _TRACK_LAYOUT[:-1]
     t = pxr_tracks()
     t.capacity = 0
     rc = call(t)
@@ -214,17 +217,17 @@ def _read_tracks(call, holder=None) -> dict:
     n = t.n_tracks
     if rc == OK:                                        # no tracks: the call is complete
         out = {"n": 0, "status": t.status}
-        for name, dt, k in _TRACK_LAYOUT:
+        for name, dt, k in layout:
             out[name] = np.zeros((0, k) if k > 1 else 0, dt)
         return out
     while True:
-        sizes = [np.dtype(dt).itemsize * k * max(n, 1) for _, dt, k in _TRACK_LAYOUT]
+        sizes = [np.dtype(dt).itemsize * k * max(n, 1) for _, dt, k in layout]
         offs = np.concatenate([[0], np.cumsum([(z + 15) // 16 * 16 for z in sizes])])
         buf = np.empty(int(offs[-1]), np.uint8)
         base = buf.ctypes.data
         t = pxr_tracks()
         t.capacity = n
-        for (name, _, _), off in zip(_TRACK_LAYOUT, offs[:-1]):
+        for (name, _, _), off in zip(layout, offs[:-1]):
             setattr(t, name, base + int(off))
         rc = call(t)
         if rc == ETRUNC:                                # (the count cannot grow; defensive)
@@ -232,7 +235,7 @@ def _read_tracks(call, holder=None) -> dict:
             continue
         _check(rc)
         out = {"n": n, "status": t.status}
-        for (name, dt, k), off in zip(_TRACK_LAYOUT, offs[:-1]):
+        for (name, dt, k), off in zip(layout, offs[:-1]):
             a = np.frombuffer(buf, dt, n * k, int(off))
             out[name] = a.reshape(n, k) if k > 1 else a
         return out
@@ -316,8 +319,9 @@ class Context:
         _check(load().pxr_poll(self.h, done, cap, C.byref(n), timeout_us))
         return [done[i] for i in range(n.value)]
 
-    def pxr_fetch_tracks(self, ticket: int) -> dict:
-        return _read_tracks(lambda t: load().pxr_fetch_tracks(self.h, ticket, C.byref(t)))
+    def pxr_fetch_tracks(self, ticket: int, cov: bool = False) -> dict:
+        """Tracks of a finished event (cov: also the covariances, if they were computed)."""
+        return _read_tracks(lambda t: load().pxr_fetch_tracks(self.h, ticket, C.byref(t)), cov)
 
     def pxr_fetch_debug(self, ticket: int, what: int) -> np.ndarray:
         return _read_debug(lambda b, cap, n: load().pxr_fetch_debug(self.h, ticket, what, b, cap,
@@ -347,13 +351,17 @@ class Plan:
         self.h = h
         self.ctx = ctx
         self.n_events = len(off) - 1
+        self.with_cov = bool(params.fit_cov)
         self._refs = (x, y, z, layer)      # the caller's device inputs stay alive
 
     def pxr_plan_run(self, stream=None):
         _check(load().pxr_plan_run(self.h, ptr(stream)))
 
-    def pxr_plan_tracks(self, e: int) -> dict:
-        return _read_tracks(lambda t: load().pxr_plan_tracks(self.h, e, C.byref(t)))
+    def pxr_plan_tracks(self, e: int, cov=None) -> dict:
+        """Tracks of event e (cov: with the covariance array; default: when the plan's
+        parameters ask for covariances)."""
+        return _read_tracks(lambda t: load().pxr_plan_tracks(self.h, e, C.byref(t)),
+                            self.with_cov if cov is None else cov)
 
     def pxr_plan_debug(self, e: int, what: int) -> np.ndarray:
         return _read_debug(lambda b, cap, n: load().pxr_plan_debug(self.h, e, what, b, cap, n),

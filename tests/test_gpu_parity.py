@@ -282,7 +282,12 @@ def test_covariance_matches_oracle(ctx, orc, fit):
     e = ev_tuple(ev)
     got = run_plan(ctx, [e], P, pxr.CUT_FP32, fit=fit, debug=False, fit_cov=True)[0]["tracks"]
     off = run_plan(ctx, [e], P, pxr.CUT_FP32, fit=fit, debug=False)[0]["tracks"]
-    assert np.all(np.isnan(off["cov"]))                  # not computed unless asked
+    assert "cov" not in off                              # not fetched unless computed
+    off_p = pxr.Plan(ctx, [0, ev.n], *to_dev([e])[1:],
+                     pxr.params_from(P, cut_mode=pxr.CUT_FP32, fit_mode=fit))
+    off_p.pxr_plan_run()
+    assert np.all(np.isnan(off_p.pxr_plan_tracks(0, cov=True)["cov"]))   # NaN: not computed
+    off_p.close()
     # asking does not change the fit beyond round-off (the two kernel instantiations may fuse
     # multiply-adds differently)
     assert gpu_tuples(off) == gpu_tuples(got)
