@@ -869,10 +869,31 @@ static int emit_tracks(const HostTracks &h, int32_t status, pxr_tracks *out, boo
     out->n_tracks = (uint32_t)n;
     out->status = status;
     if (n > out->capacity) return fail(PXR_ETRUNC, "track capacity too small");
+    if (in_order) {                          // already canonical: one copy per array
+        auto cp = [n](void *dst, const void *src, size_t sz) {
+            if (dst && n) std::memcpy(dst, src, sz * n);
+        };
+        cp(out->n_hits, h.nh.data(), 1);
+        cp(out->hit_idx, h.hits.data(), 4 * kMaxHits);
+        cp(out->pt, h.pt.data(), 8);
+        cp(out->phi, h.phi.data(), 8);
+        cp(out->cot_theta, h.cot.data(), 8);
+        cp(out->dxy, h.dxy.data(), 8);
+        cp(out->dz, h.dz.data(), 8);
+        cp(out->chi2, h.chi2.data(), 8);
+        cp(out->charge, h.q.data(), 1);
+        cp(out->fit_status, h.st.data(), 1);
+        cp(out->quality, h.ql.data(), 1);
+        if (out->cov) {
+            if (h.cov.empty()) std::fill(out->cov, out->cov + 15 * n, NAN);
+            else cp(out->cov, h.cov.data(), 15 * sizeof(double));
+        }
+        return PXR_OK;
+    }
     std::vector<uint32_t> ord;
-    if (!in_order) canonical_order(h.hits.data(), n, ord);
+    canonical_order(h.hits.data(), n, ord);
     for (size_t k = 0; k < n; ++k) {
-        const size_t s = in_order ? k : ord[k];
+        const size_t s = ord[k];
         if (out->n_hits) out->n_hits[k] = h.nh[s];
         if (out->hit_idx)
             std::memcpy(out->hit_idx + k * kMaxHits, h.hits.data() + s * kMaxHits, 4 * kMaxHits);
