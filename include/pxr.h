@@ -65,6 +65,11 @@ extern "C" {
                                the normal matrices need FP64 (kink weights up to ~1e14 next to
                                measurement weights ~1e6) */
 #define PXR_FIT_FP32 2      /* all steps in FP32; errors against FP64 are reported, not bounded */
+#define PXR_FIT_RIEMANN 3   /* Riemann fit instead of the broken line, FP64: hits mapped to the
+                               paraboloid w = x^2 + y^2, the plane through them (smallest
+                               eigenvector of the weighted scatter matrix) gives the circle; a
+                               weighted straight line in (arc length, z); no multiple scattering.
+                               The track covariance is not computed for it (NaN) */
 
 /* Presets for pxr_params_init */
 #define PXR_PRESET_BARREL 0 /* 4 barrel layers r = 2.9/6.8/10.9/16.0, pairs (0,1)(1,2)(2,3), roots

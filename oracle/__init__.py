@@ -96,6 +96,10 @@ def lib():
             L.orc_fit_cov.restype = C.c_int
             L.orc_fit_cov.argtypes = [C.c_int, dp, dp, dp, C.POINTER(C.c_uint16),
                                       C.POINTER(OrcParams), C.POINTER(OrcTrack), dp]
+            L.orc_riemann_batch.restype = None
+            L.orc_riemann_batch.argtypes = [C.c_uint32, C.POINTER(C.c_uint8), dp, dp, dp,
+                                            C.POINTER(C.c_uint16), C.c_uint32,
+                                            C.POINTER(OrcParams), C.POINTER(OrcTrack)]
             L.orc_fit_batch.restype = None
             L.orc_fit_batch.argtypes = [C.c_uint32, C.POINTER(C.c_uint8), dp, dp, dp,
                                         C.POINTER(C.c_uint16), C.c_uint32,
@@ -202,6 +206,22 @@ def fit_batch(nh, X, Y, Z, layers, params) -> np.ndarray:
     lib().orc_fit_batch(m, _ptr(nh, C.c_uint8), _ptr(X, C.c_double), _ptr(Y, C.c_double),
                         _ptr(Z, C.c_double), _ptr(L, C.c_uint16), k, C.byref(P),
                         out.ctypes.data_as(C.POINTER(OrcTrack)))
+    return out
+
+
+def riemann_batch(nh, X, Y, Z, layers, params) -> np.ndarray:
+    """Riemann fits of m ntuplets ([m, k] arrays as for fit_batch)."""
+    nh = np.ascontiguousarray(nh, np.uint8)
+    m, k = np.shape(X)
+    X = np.ascontiguousarray(X, np.float64)
+    Y = np.ascontiguousarray(Y, np.float64)
+    Z = np.ascontiguousarray(Z, np.float64)
+    L = np.ascontiguousarray(layers, np.uint16)
+    P = make_params(params)
+    out = np.zeros(m, TRACK_DTYPE)
+    lib().orc_riemann_batch(m, _ptr(nh, C.c_uint8), _ptr(X, C.c_double), _ptr(Y, C.c_double),
+                            _ptr(Z, C.c_double), _ptr(L, C.c_uint16), k, C.byref(P),
+                            out.ctypes.data_as(C.POINTER(OrcTrack)))
     return out
 
 

@@ -484,6 +484,151 @@ void orc_fit_batch(uint32_t m, const uint8_t *nh, const double *X, const double 
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Riemann fit of one ntuplet                                                                  */
+/* ------------------------------------------------------------------------------------------ */
+/* Eigen-decomposition of a symmetric 3 x 3 matrix by cyclic Jacobi rotations (the textbook
+ * method: each rotation zeroes one off-diagonal element; sweeps until they vanish).  On return
+ * the diagonal of a holds the eigenvalues and the columns of v the eigenvectors. */
+static void jacobi3(double a[3][3], double v[3][3])
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) v[i][j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        double off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
+        double diag = fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2]);
+        if (off <= 1e-300 || off <= 1e-18 * diag) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (a[p][q] == 0.0) continue;
+                /* rotation angle that zeroes a[p][q]: tan(2 phi) = 2 a_pq / (a_qq - a_pp) */
+                double th = 0.5 * (a[q][q] - a[p][p]) / a[p][q];
+                double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < 3; ++k) {            /* a <- a J */
+                    double akp = a[k][p], akq = a[k][q];
+                    a[k][p] = c * akp - sn * akq;
+                    a[k][q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {            /* a <- J^T a */
+                    double apk = a[p][k], aqk = a[q][k];
+                    a[p][k] = c * apk - sn * aqk;
+                    a[q][k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {            /* v <- v J */
+                    double vkp = v[k][p], vkq = v[k][q];
+                    v[k][p] = c * vkp - sn * vkq;
+                    v[k][q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+}
+
+/*
+ * Riemann fit (reading of the circle fit on the Riemann paraboloid: Strandlie et al., Comput.
+ * Phys. Commun. 131 (2000) 95, in its fast plane-fit form):
+ *  1. map each hit (x, y) to (x, y, x^2 + y^2) in the transverse frame of the beam line; fit a
+ *     plane c + n.p = 0 (|n| = 1) minimising sum w_i (c + n.p_i)^2 with w_i = 1/sigma_rphi^2:
+ *     n is the eigenvector of the smallest eigenvalue of the weighted scatter matrix about the
+ *     weighted centroid, c = -n.centroid; the plane cuts the paraboloid in the circle with
+ *     centre (-n_x, -n_y) / (2 n_w) and radius^2 = (n_x^2 + n_y^2 - 4 c n_w) / (4 n_w^2);
+ *  2. orientation from the turn of hit n-1 relative to hit 0 about the centre (charge = -sgn);
+ *     arc lengths s_i from hit 0 along the motion; weighted straight line z = z_0 + cot s
+ *     (weights 1/sigma_z^2, disks 1/(sigma_z cot0)^2 as in the broken line);
+ *  3. point of closest approach of the circle to the beam line; dxy = q (|C| - R); phi the
+ *     direction of motion there; dz = z_0 + cot s_PCA; pT = K B R;
+ *     chi2 = sum ((|p_i - C| - R) / sigma_rphi)^2 + sum ((z_i - z_0 - cot s_i) / sigma_z,i)^2.
+ * No multiple scattering enters (the fast form).
+ */
+int orc_riemann_one(int n, const double *X, const double *Y, const double *Z, const uint16_t *lay,
+                    const orc_params *P, orc_track *out)
+{
+    memset(out, 0, sizeof(*out));
+    if (n < 3 || n > ORC_MAXH) { out->status = 4; return -1; }
+    double w = 1.0 / (P->sigma_rphi * P->sigma_rphi);
+    double sw = 0.0, m[3] = {0.0, 0.0, 0.0};
+    double pts[ORC_MAXH][3];
+    for (int i = 0; i < n; ++i) {
+        pts[i][0] = X[i];
+        pts[i][1] = Y[i];
+        pts[i][2] = X[i] * X[i] + Y[i] * Y[i];
+        for (int k = 0; k < 3; ++k) m[k] += w * pts[i][k];
+        sw += w;
+    }
+    for (int k = 0; k < 3; ++k) m[k] /= sw;
+    double A[3][3] = {{0}}, V[3][3];
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) A[a][b] += w * (pts[i][a] - m[a]) * (pts[i][b] - m[b]);
+    jacobi3(A, V);
+    int kmin = 0;
+    for (int k = 1; k < 3; ++k)
+        if (A[k][k] < A[kmin][kmin]) kmin = k;
+    double nx = V[0][kmin], ny = V[1][kmin], nw = V[2][kmin];
+    double c = -(nx * m[0] + ny * m[1] + nw * m[2]);
+    if (nw == 0.0) { out->status = 1; return -1; }
+    double Cx = -nx / (2.0 * nw), Cy = -ny / (2.0 * nw);
+    double R2 = (nx * nx + ny * ny - 4.0 * c * nw) / (4.0 * nw * nw);
+    if (!(R2 > 0.0) || !isfinite(R2)) { out->status = 2; return -1; }
+    double R = sqrt(R2);
+    /* orientation: the turn from hit 0 to hit n-1 about the centre */
+    double ax = X[0] - Cx, ay = Y[0] - Cy;
+    double bx = X[n - 1] - Cx, by = Y[n - 1] - Cy;
+    double sgn = (ax * by - ay * bx) > 0.0 ? 1.0 : -1.0;
+    int q = sgn > 0.0 ? -1 : 1;
+    double s[ORC_MAXH];
+    for (int i = 0; i < n; ++i) {
+        double dx = X[i] - Cx, dy = Y[i] - Cy;
+        s[i] = R * atan2(sgn * (ax * dy - ay * dx), ax * dx + ay * dy);
+    }
+    /* line */
+    double cot0 = (Z[n - 1] - Z[0]) / (s[n - 1] - s[0]);
+    double S0 = 0.0, S1 = 0.0, S2 = 0.0, T0 = 0.0, T1 = 0.0, wz[ORC_MAXH];
+    for (int i = 0; i < n; ++i) {
+        double sz = P->layer_is_disk[lay[i]] ? P->sigma_z * fabs(cot0) : P->sigma_z;
+        wz[i] = 1.0 / (sz * sz);
+        S0 += wz[i];
+        S1 += wz[i] * s[i];
+        S2 += wz[i] * s[i] * s[i];
+        T0 += wz[i] * Z[i];
+        T1 += wz[i] * s[i] * Z[i];
+    }
+    double det = S0 * S2 - S1 * S1;
+    if (!(det > 0.0)) { out->status = 3; return -1; }
+    double cot = (S0 * T1 - S1 * T0) / det;
+    double z0 = (S2 * T0 - S1 * T1) / det;
+    /* point of closest approach to the beam line */
+    double dC = sqrt(Cx * Cx + Cy * Cy);
+    double ux = -Cx / dC, uy = -Cy / dC;            /* from the centre towards the beam line */
+    double Px = Cx + R * ux, Py = Cy + R * uy;
+    double tpx = -sgn * (Py - Cy) / R, tpy = sgn * (Px - Cx) / R;
+    double s_pca = R * atan2(sgn * (ax * (Py - Cy) - ay * (Px - Cx)), ax * (Px - Cx) + ay * (Py - Cy));
+    double chi2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double d = sqrt((X[i] - Cx) * (X[i] - Cx) + (Y[i] - Cy) * (Y[i] - Cy)) - R;
+        double e = Z[i] - z0 - cot * s[i];
+        chi2 += w * d * d + wz[i] * e * e;
+    }
+    out->pt = ORC_K_PT * P->bfield * R;
+    out->phi = atan2(tpy, tpx);
+    out->cot_theta = cot;
+    out->dxy = q * (dC - R);
+    out->dz = z0 + cot * s_pca;
+    out->chi2 = chi2;
+    out->charge = q;
+    out->status = 0;
+    return 0;
+}
+
+void orc_riemann_batch(uint32_t m, const uint8_t *nh, const double *X, const double *Y,
+                       const double *Z, const uint16_t *lay, uint32_t stride, const orc_params *P,
+                       orc_track *out)
+{
+    for (uint32_t t = 0; t < m; ++t)
+        orc_riemann_one(nh[t], X + (size_t)t * stride, Y + (size_t)t * stride,
+                        Z + (size_t)t * stride, lay + (size_t)t * stride, P, &out[t]);
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Event reconstruction: doublets -> CA edges -> ntuplets -> fits                              */
 /* ------------------------------------------------------------------------------------------ */
 typedef struct {

@@ -506,11 +506,153 @@ __device__ __forceinline__ void fit_track(int n, const float *X, const float *Y,
     }
 }
 
+// ---- Riemann fit (FP64) ----
+// Smallest eigenpair of a symmetric 3 x 3 matrix: the eigenvalues in closed form (the
+// trigonometric solution of the characteristic cubic of A - tr(A)/3), the eigenvector as the
+// longest cross product of two rows of A - lambda I (orthogonal to both, so in the null space),
+// then once more with the Rayleigh quotient of that vector as lambda.
+__device__ __forceinline__ bool smallest_eigvec(const double (&A)[3][3], double (&v)[3])
+{
+    const double q = (A[0][0] + A[1][1] + A[2][2]) / 3.0;
+    const double b00 = A[0][0] - q, b11 = A[1][1] - q, b22 = A[2][2] - q;
+    const double p2 = b00 * b00 + b11 * b11 + b22 * b22 +
+                      2.0 * (A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2]);
+    const double p = sqrt(p2 / 6.0);
+    if (!(p > 0.0)) return false;
+    const double ip = 1.0 / p;
+    const double c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip;
+    const double c01 = A[0][1] * ip, c02 = A[0][2] * ip, c12 = A[1][2] * ip;
+    const double det = c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) +
+                       c02 * (c01 * c12 - c11 * c02);
+    const double r = fmin(1.0, fmax(-1.0, 0.5 * det));
+    const double phi = acos(r) / 3.0;
+    double lam = q + 2.0 * p * cos(phi + 2.0943951023931957);   // the smallest root
+    for (int it = 0; it < 2; ++it) {
+        const double r0[3] = {A[0][0] - lam, A[0][1], A[0][2]};
+        const double r1[3] = {A[1][0], A[1][1] - lam, A[1][2]};
+        const double r2[3] = {A[2][0], A[2][1], A[2][2] - lam};
+        auto cross = [](const double *a, const double *b, double *c) {
+            c[0] = a[1] * b[2] - a[2] * b[1];
+            c[1] = a[2] * b[0] - a[0] * b[2];
+            c[2] = a[0] * b[1] - a[1] * b[0];
+        };
+        double x01[3], x02[3], x12[3];
+        cross(r0, r1, x01);
+        cross(r0, r2, x02);
+        cross(r1, r2, x12);
+        const double n01 = x01[0] * x01[0] + x01[1] * x01[1] + x01[2] * x01[2];
+        const double n02 = x02[0] * x02[0] + x02[1] * x02[1] + x02[2] * x02[2];
+        const double n12 = x12[0] * x12[0] + x12[1] * x12[1] + x12[2] * x12[2];
+        const double *best = x01;
+        double nb = n01;
+        if (n02 > nb) { best = x02; nb = n02; }
+        if (n12 > nb) { best = x12; nb = n12; }
+        if (!(nb > 0.0)) return false;
+        const double inv = rsqrt(nb);
+        v[0] = best[0] * inv;
+        v[1] = best[1] * inv;
+        v[2] = best[2] * inv;
+        double Av[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) Av[i] = A[i][0] * v[0] + A[i][1] * v[1] + A[i][2] * v[2];
+        lam = v[0] * Av[0] + v[1] * Av[1] + v[2] * Av[2];
+    }
+    return true;
+}
+
+// Riemann fit of n hits (the same reading and output conventions as the broken line's
+// conversion: orientation sgn, charge -sgn, arc lengths from hit 0, dxy = q (|C| - R)).
+__device__ __noinline__ void riemann_fit(int n, const float *X, const float *Y, const float *Z,
+                            const uint8_t *L, const DevParams &p, FitOut &o)
+{
+    o = FitOut{0, 0, 0, 0, 0, 0, 0, 0};
+    if (n < 3 || n > kMaxHits) { o.status = 4; return; }
+    const double w = 1.0 / (p.sigma_rphi * p.sigma_rphi);
+    double P3[kMaxHits][3], m[3] = {0.0, 0.0, 0.0}, sw = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double x = X[i], y = Y[i];
+        P3[i][0] = x;
+        P3[i][1] = y;
+        P3[i][2] = x * x + y * y;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) m[k] += w * P3[i][k];
+        sw += w;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) m[k] /= sw;
+    double A[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    for (int i = 0; i < n; ++i) {
+        const double d0 = P3[i][0] - m[0], d1 = P3[i][1] - m[1], d2 = P3[i][2] - m[2];
+        A[0][0] += w * d0 * d0; A[0][1] += w * d0 * d1; A[0][2] += w * d0 * d2;
+        A[1][1] += w * d1 * d1; A[1][2] += w * d1 * d2; A[2][2] += w * d2 * d2;
+    }
+    A[1][0] = A[0][1]; A[2][0] = A[0][2]; A[2][1] = A[1][2];
+    double nv[3];
+    if (!smallest_eigvec(A, nv) || nv[2] == 0.0) { o.status = 1; return; }
+    const double c = -(nv[0] * m[0] + nv[1] * m[1] + nv[2] * m[2]);
+    const double Cx = -nv[0] / (2.0 * nv[2]), Cy = -nv[1] / (2.0 * nv[2]);
+    const double R2 = (nv[0] * nv[0] + nv[1] * nv[1] - 4.0 * c * nv[2]) / (4.0 * nv[2] * nv[2]);
+    if (!(R2 > 0.0) || !isfinite(R2)) { o.status = 2; return; }
+    const double R = sqrt(R2);
+    const double ax = X[0] - Cx, ay = Y[0] - Cy;
+    const double bx = X[n - 1] - Cx, by = Y[n - 1] - Cy;
+    const double sgn = ax * by - ay * bx > 0.0 ? 1.0 : -1.0;
+    const int q = sgn > 0.0 ? -1 : 1;
+    double s[kMaxHits], wz[kMaxHits];
+    for (int i = 0; i < n; ++i) {
+        const double dx = X[i] - Cx, dy = Y[i] - Cy;
+        s[i] = R * atan2(sgn * (ax * dy - ay * dx), ax * dx + ay * dy);
+    }
+    const double cot0 = (double(Z[n - 1]) - double(Z[0])) / (s[n - 1] - s[0]);
+    double S0 = 0.0, S1 = 0.0, S2 = 0.0, T0 = 0.0, T1 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double sz = p.is_disk[L[i]] ? p.sigma_z * fabs(cot0) : p.sigma_z;
+        wz[i] = 1.0 / (sz * sz);
+        S0 += wz[i];
+        S1 += wz[i] * s[i];
+        S2 += wz[i] * s[i] * s[i];
+        T0 += wz[i] * double(Z[i]);
+        T1 += wz[i] * s[i] * double(Z[i]);
+    }
+    const double det = S0 * S2 - S1 * S1;
+    if (!(det > 0.0)) { o.status = 3; return; }
+    const double cot = (S0 * T1 - S1 * T0) / det;
+    const double z0 = (S2 * T0 - S1 * T1) / det;
+    const double dC = sqrt(Cx * Cx + Cy * Cy);
+    const double Px = Cx - R * Cx / dC, Py = Cy - R * Cy / dC;   // closest approach
+    const double tpx = -sgn * (Py - Cy) / R, tpy = sgn * (Px - Cx) / R;
+    const double s_pca = R * atan2(sgn * (ax * (Py - Cy) - ay * (Px - Cx)),
+                                   ax * (Px - Cx) + ay * (Py - Cy));
+    double chi2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double dx = X[i] - Cx, dy = Y[i] - Cy;
+        const double d = sqrt(dx * dx + dy * dy) - R;
+        const double e = double(Z[i]) - z0 - cot * s[i];
+        chi2 += w * d * d + wz[i] * e * e;
+    }
+    o.pt = kKpt * p.bfield * R;
+    o.phi = atan2(tpy, tpx);
+    o.cot = cot;
+    o.dxy = q * (dC - R);
+    o.dz = z0 + cot * s_pca;
+    o.chi2 = chi2;
+    o.q = (int8_t)q;
+    o.status = 0;
+}
+
 template <bool COV>
 __device__ __forceinline__ void fit_dispatch(int n, const float *X, const float *Y,
                                              const float *Z, const uint8_t *L,
                                              const DevParams &p, FitOut &o, double *cov15)
 {
+    if (p.fit_mode == FIT_RIEMANN) {
+        riemann_fit(n, X, Y, Z, L, p, o);
+        if constexpr (COV) {
+#pragma unroll
+            for (int k = 0; k < 15; ++k) cov15[k] = __longlong_as_double(0x7FF8000000000000LL);
+        }
+        return;
+    }
     if (p.fit_mode == FIT_MIXED) fit_track<double, double, true, COV>(n, X, Y, Z, L, p, o, cov15);
     else if (p.fit_mode == FIT_FP32) fit_track<float, float, false, COV>(n, X, Y, Z, L, p, o, cov15);
     else fit_track<double, double, false, COV>(n, X, Y, Z, L, p, o, cov15);

@@ -38,7 +38,7 @@ constexpr uint8_t kQGood = 1u, kQKept = 2u;
 enum Flag : uint32_t { F_CELLS = 1u, F_EDGES = 2u, F_TUPLES = 4u, F_LAYER = 8u };
 
 enum CutMode : uint32_t { CUT_FP64 = 0, CUT_FP32 = 1 };
-enum FitMode : uint32_t { FIT_FP64 = 0, FIT_MIXED = 1, FIT_FP32 = 2 };
+enum FitMode : uint32_t { FIT_FP64 = 0, FIT_MIXED = 1, FIT_FP32 = 2, FIT_RIEMANN = 3 };
 
 struct DevParams {
     uint32_t n_layers;

@@ -110,7 +110,7 @@ static int check_params(const pxr_params *p, DevParams *d)
     if (p->min_hits < 2 || p->max_hits > PXR_MAX_HITS || p->min_hits > p->max_hits)
         return fail(PXR_EINVAL, "need 2 <= min_hits <= max_hits <= 6");
     if (p->cut_mode > PXR_CUT_FP32) return fail(PXR_EINVAL, "bad cut_mode");
-    if (p->fit_mode > PXR_FIT_FP32) return fail(PXR_EINVAL, "bad fit_mode");
+    if (p->fit_mode > PXR_FIT_RIEMANN) return fail(PXR_EINVAL, "bad fit_mode");
     if (!(p->phi_window > 0.0 && p->phi_window <= 0.5)) return fail(PXR_EINVAL, "phi_window must be in (0, 0.5]");
     if (!(std::fabs(p->cos_phi_window - std::cos(p->phi_window)) < 1e-12))
         return fail(PXR_EINVAL, "cos_phi_window must equal cos(phi_window)");

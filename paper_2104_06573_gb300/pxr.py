@@ -21,7 +21,7 @@ MAX_LAYERS, MAX_PAIRS, MAX_HITS = 16, 32, 6
 OK, EINVAL, EAGAIN, ENOMEM, EOVERFLOW, ETIMEDOUT, ECUDA, ETRUNC, ENOTFOUND, EBUSY = (
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9)
 CUT_FP64, CUT_FP32 = 0, 1
-FIT_FP64, FIT_MIXED, FIT_FP32 = 0, 1, 2
+FIT_FP64, FIT_MIXED, FIT_FP32, FIT_RIEMANN = 0, 1, 2, 3
 PRESET_BARREL, PRESET_PHASE1 = 0, 1
 NONE = 0xFFFFFFFF
 

@@ -432,6 +432,53 @@ def test_fit_batch_modes(ctx, orc):
         assert v <= TOL[k], (k, v)
 
 
+def test_riemann_fit_matches_oracle(ctx, orc):
+    """Riemann fit (FP64) through the fit-only path on smeared ntuplets and through the batch
+    path on a dense event with disks: statuses, charges and parameters against the oracle's
+    Riemann fit (closed-form eigenvalues and cross products on the GPU, Jacobi rotations in the
+    oracle)."""
+    P = synth.params_barrel_quadruplets()
+    tb = synth.fit_tuplets(20000, seed=17)
+    ref = orc.riemann_batch(tb.n_hits, tb.x.astype(np.float64), tb.y.astype(np.float64),
+                            tb.z.astype(np.float64), tb.layer, P)
+    dev = torch.device("cuda:0")
+    m = len(tb.n_hits)
+    args = [torch.from_numpy(a).to(dev) for a in (tb.n_hits, tb.x, tb.y, tb.z,
+                                                  tb.layer.view(np.int16))]
+    out = {k: torch.zeros(m, dtype=torch.float64, device=dev) for k in pxr.TRACK_FIELDS}
+    out["charge"] = torch.zeros(m, dtype=torch.int8, device=dev)
+    out["fit_status"] = torch.zeros(m, dtype=torch.int8, device=dev)
+    ctx.pxr_fit_batch(m, *args, 4, pxr.params_from(P, fit_mode=pxr.FIT_RIEMANN), out)
+    torch.cuda.synchronize()
+    h = {k: v.cpu().numpy() for k, v in out.items()}
+    assert np.all(h["fit_status"] == ref["status"])
+    ok = ref["status"] == 0
+    assert np.all(h["charge"][ok] == ref["charge"][ok])
+    err = fit_errors(h, ref, ok)
+    print("Riemann fit errors vs oracle:", err)
+    for k, v in err.items():
+        assert v < 0.01 * TOL[k], (k, v)
+    # batch path, dense event with disks
+    P2 = synth.params_phase1()
+    ev = ev_tuple(synth.event_phase1(6, 800))
+    got = run_plan(ctx, [ev], P2, pxr.CUT_FP32, fit=pxr.FIT_RIEMANN, debug=False)[0]["tracks"]
+    _, _, _, tup, _ = oracle_sets(orc, ev, P2)
+    assert gpu_tuples(got) == tup
+    nt = len(tup)
+    X = np.zeros((nt, 8)); Y = np.zeros((nt, 8)); Z = np.zeros((nt, 8))
+    L = np.zeros((nt, 8), np.uint16)
+    nh = np.array([len(t) for t in tup], np.uint8)
+    for t, hits in enumerate(tup):
+        hh = np.array(hits)
+        X[t, :len(hh)], Y[t, :len(hh)], Z[t, :len(hh)] = ev[0][hh], ev[1][hh], ev[2][hh]
+        L[t, :len(hh)] = ev[3][hh]
+    ref2 = orc.riemann_batch(nh, X, Y, Z, L, P2)
+    assert np.all(got["fit_status"] == ref2["status"])
+    ok2 = ref2["status"] == 0
+    for k, v in fit_errors(got, ref2, ok2).items():
+        assert v < 0.01 * TOL[k], (k, v)
+
+
 @pytest.mark.parametrize("cut", [pxr.CUT_FP32])
 def test_dense_event_mixed_fit_within_tolerance(ctx, orc, cut):
     """The batch path with the MIXED fit (the benchmark's setting): sets bit-exact, fitted
