@@ -685,6 +685,31 @@ def study(args):
             c4[name] = {"fits_per_s": 5 * m / (a.elapsed_time(b) / 1e3),
                         "status_agree": float(np.mean(h["fit_status"] == ref["status"])),
                         "errors": _fit_errors(h, ref, ok)}
+        # the Riemann fit (FP64) on the same ntuplets, against the oracle's Riemann fit
+        t0 = time.perf_counter()
+        ref_r = oracle.riemann_batch(tb.n_hits, tb.x.astype(np.float64), tb.y.astype(np.float64),
+                                     tb.z.astype(np.float64), tb.layer, P)
+        o_rm = len(ref_r) / (time.perf_counter() - t0)
+        res = {k: torch.zeros(m, dtype=torch.float64, device=dev) for k in pxr.TRACK_FIELDS}
+        res["charge"] = torch.zeros(m, dtype=torch.int8, device=dev)
+        res["fit_status"] = torch.zeros(m, dtype=torch.int8, device=dev)
+        prm = pxr.params_from(P, fit_mode=pxr.FIT_RIEMANN)
+        for _ in range(2):
+            ctx.pxr_fit_batch(m, *dargs, 4, prm, res, stream=stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(5):
+            ctx.pxr_fit_batch(m, *dargs, 4, prm, res, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        h = {k: v.cpu().numpy() for k, v in res.items()}
+        ok = (ref_r["status"] == 0) & (h["fit_status"] == 0)
+        c4["riemann"] = {"fits_per_s": 5 * m / (a.elapsed_time(b) / 1e3),
+                         "oracle_1core_fits_per_s": o_rm,
+                         "status_agree": float(np.mean(h["fit_status"] == ref_r["status"])),
+                         "errors_vs_oracle_riemann": _fit_errors(h, ref_r, ok),
+                         "errors_vs_oracle_broken_line": _fit_errors(h, ref, ok & (ref["status"] == 0))}
         out["C4_fit_precision"] = c4
         # next row N1: track selection (shared-hit cleaning) on the smeared batch
         out["N1_selection"] = _selection_study(pxr, synth, ctx, dev, stream)
