@@ -12,6 +12,7 @@ below are thin ctypes wrappers; all arithmetic lives in the C file, except the t
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -373,3 +374,46 @@ def select_tracks(tuples, tuple_n, fits, pt_min=0.0, chi2_max=0.0, clean_shared=
                         kept = False
         q[t] = Q_GOOD | (Q_KEPT if kept else 0)
     return q
+
+
+# -- primary vertices ------------------------------------------------------------------------
+def find_vertices(fits, quality, gap, min_tracks):
+    """Primary vertices of one event from its fitted tracks (the vertexing step that follows the
+    tracks, §2; the paper defines no algorithm, so this is the library's reading).
+
+    Tracks taken: the KEPT ones with a finite dz.  Sorted by dz (equal dz: the track order), a
+    track joins the cluster of the one before it when their dz differ by at most `gap` (cm).
+    Clusters of at least `min_tracks` tracks are vertices: z the mean dz, z_err the standard
+    error of the mean (sqrt(sum (dz - z)^2 / (n (n - 1)))), the track count and the sum of pT^2.
+    Vertices are ordered by sum pT^2, largest first (equal sums: smaller z first).
+    Returns (vertices: dict of arrays z, z_err, n_tracks, sum_pt2; per-track vertex index, -1
+    for tracks in no vertex)."""
+    nt = len(quality)
+    take = [t for t in range(nt) if (quality[t] & Q_KEPT) and np.isfinite(fits[t]["dz"])]
+    take.sort(key=lambda t: (float(fits[t]["dz"]), t))
+    clusters = []
+    for t in take:
+        if clusters and float(fits[t]["dz"]) - float(fits[clusters[-1][-1]]["dz"]) <= gap:
+            clusters[-1].append(t)
+        else:
+            clusters.append([t])
+    verts = []
+    for c in clusters:
+        n = len(c)
+        if n < min_tracks:
+            continue
+        dz = [float(fits[t]["dz"]) for t in c]
+        z = sum(dz) / n
+        ss = sum((v - z) ** 2 for v in dz)
+        err = math.sqrt(ss / (n * (n - 1))) if n > 1 else 0.0
+        pt2 = sum(float(fits[t]["pt"]) ** 2 for t in c)
+        verts.append((pt2, z, err, n, c))
+    verts.sort(key=lambda v: (-v[0], v[1]))
+    vid = np.full(nt, -1, np.int32)
+    for k, v in enumerate(verts):
+        for t in v[4]:
+            vid[t] = k
+    out = {"z": np.array([v[1] for v in verts]), "z_err": np.array([v[2] for v in verts]),
+           "n_tracks": np.array([v[3] for v in verts], np.uint32),
+           "sum_pt2": np.array([v[0] for v in verts])}
+    return out, vid

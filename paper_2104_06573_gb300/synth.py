@@ -261,9 +261,17 @@ def _noise(rng: Rng, layer_counts, n_noise):
 
 
 def make_event(seed: int, n_tracks: int, *, with_disks=False, pt_mode="uniform", pt_lo=1.0,
-               pt_hi=10.0, eta_max=1.0, smear=False, noise_frac=0.0, shuffle=True) -> Event:
+               pt_hi=10.0, eta_max=1.0, smear=False, noise_frac=0.0, shuffle=True,
+               n_vertices: int = 0) -> Event:
+    """n_vertices > 0: the tracks come from that many primary vertices (z ~ N(0, 5 cm)), each
+    track from a uniformly drawn one; otherwise every track has its own origin z ~ N(0, 5 cm)."""
     rng = Rng(seed, 1)
     tr = draw_tracks(rng, n_tracks, pt_mode, pt_lo, pt_hi, eta_max)
+    if n_vertices > 0:
+        vr = Rng(seed, 5)
+        vz = vr.normal(n_vertices, 5.0)
+        owner = np.minimum((vr.uniform(n_tracks) * n_vertices).astype(np.int64), n_vertices - 1)
+        tr = Tracks(tr.pt, tr.phi0, tr.cot, tr.q, vz[owner])
     tid, lay, _s, x, y, z = helix_points(tr, with_disks)
     if smear:
         x, y, z = _smear(Rng(seed, 2), lay, x, y, z, with_disks, 10e-4, 20e-4)
