@@ -128,7 +128,12 @@ extern "C" {
  *   broken line and the line values v_0, v_1 have the covariance of the two linear least-squares
  *   problems (the corresponding blocks of the inverse normal matrices; the two fits are
  *   independent); it is propagated to (q/pT, phi, cot_theta, dxy, dz) through the conversion,
- *   linearised around the solution by central differences in FP64.
+ *   linearised around the solution (forward-mode derivatives in FP64).
+ * Vertices (vertexing).  The event's KEPT tracks with a finite dz, sorted by dz: a track joins
+ *   the cluster of the one before it when their dz differ by at most vtx_gap; clusters of at
+ *   least vtx_min_tracks tracks are vertices (z = mean dz, its standard error, the track count,
+ *   sum pT^2), ordered by sum pT^2, largest first.  An event with more than 8192 kept tracks gets
+ *   no vertices and PXR_EOVERFLOW.
  */
 typedef struct pxr_params {
     uint32_t n_layers;                         /* <= PXR_MAX_LAYERS; hit layer ids < n_layers */
@@ -165,6 +170,9 @@ typedef struct pxr_params {
     uint32_t clean_shared;                     /* selection: 0 or 1 (shared-hit cleaning) */
     uint32_t fit_cov;                          /* 1: compute each track's covariance
                                                   (pxr_tracks.cov); 0: not computed */
+    uint32_t vertexing;                        /* 1: find primary vertices (pxr_tracks.vtx_*) */
+    uint32_t vtx_min_tracks;                   /* tracks a vertex needs, >= 2 */
+    double vtx_gap;                            /* cm, > 0: largest z gap inside a vertex */
 } pxr_params;
 
 /* Context configuration. */
@@ -197,6 +205,14 @@ typedef struct pxr_tracks {
     double *cov;                /* [capacity * 15] covariance of (q/pT [1/GeV], phi, cot_theta,
                                    dxy, dz), upper triangle row by row; NaN when fit_cov was 0
                                    or the fit failed */
+    int32_t *vertex;            /* [capacity] index of the track's vertex, -1 for none (always -1
+                                   without vertexing) */
+    uint32_t n_vertices;        /* out: vertices of the event (<= n_tracks / 2) */
+    double *vtx_z, *vtx_z_err;  /* [capacity] vertex z (cm, mean dz of its tracks) and the
+                                   standard error of that mean */
+    double *vtx_sum_pt2;        /* [capacity] sum of pT^2 of its tracks (GeV^2); vertices are
+                                   ordered by it, largest first */
+    uint32_t *vtx_n_tracks;     /* [capacity] */
 } pxr_tracks;
 
 typedef struct pxr_ctx pxr_ctx;
@@ -208,7 +224,8 @@ const char *pxr_version(void);
 /* Message of the last error on this thread (static thread-local storage). */
 const char *pxr_last_error(void);
 
-/* Fill *p with a preset (PXR_PRESET_*), cut mode FP64 and fit mode FP64. */
+/* Fill *p with a preset (PXR_PRESET_*), cut mode FP64 and fit mode FP64; no selection, no
+ * covariance, no vertexing (vtx_min_tracks 2 and vtx_gap 0.05 cm for when it is switched on). */
 int pxr_params_init(pxr_params *p, int preset);
 
 /* Validate *p without touching any device: PXR_OK or PXR_EINVAL with a message. */

@@ -774,6 +774,164 @@ void launch_keep(const DevBatch &b, const DevParams &p, uint32_t total, cudaStre
     k_keep<<<(unsigned)blocks, 256, 0, s>>>(b);
 }
 
+// ---- primary vertices ----
+constexpr int kVtxMax = 8192;      // kept tracks per event the vertex finder takes (more: flagged)
+constexpr int kVtxThreads = 512;
+
+// One CTA per event.  The kept tracks with a finite dz are gathered into shared memory and
+// sorted by (dz, output slot) with a bitonic network; a sorted track starts a new cluster when
+// its dz exceeds the previous one's by more than the gap.  Each cluster start counts its members;
+// clusters of at least vtx_min tracks become vertices (a block-wide scan gives their cluster-
+// order index).  Each vertex's start sums its members in sorted order (mean dz, the standard
+// error of the mean, sum pT^2), the records go to the event's vertex arrays, and each record is
+// then moved to its rank by (sum pT^2 descending, z ascending) and stamped on its tracks.
+__global__ void __launch_bounds__(kVtxThreads) k_vertices(DevBatch b, DevParams p)
+{
+    extern __shared__ unsigned char vsm[];
+    double *sz = reinterpret_cast<double *>(vsm);                 // [kVtxMax] dz
+    uint32_t *si = reinterpret_cast<uint32_t *>(sz + kVtxMax);    // [kVtxMax] output slot
+    __shared__ uint32_t s_m, s_wsum[kVtxThreads / 32];
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    for (uint32_t e = blockIdx.x; e < b.E; e += gridDim.x) {
+        const uint32_t a = b.out_evt[e], n = b.out_evt[e + 1] - a;
+        for (uint32_t t = tid; t < n; t += nt) b.o_vtx[a + t] = -1;
+        if (tid == 0) s_m = 0;
+        __syncthreads();
+        for (uint32_t t = tid; t < n; t += nt) {
+            const double dz = b.o_dz[a + t];
+            if ((b.o_ql[a + t] & kQKept) && isfinite(dz)) {
+                const uint32_t k = atomicAdd(&s_m, 1u);
+                if (k < (uint32_t)kVtxMax) { sz[k] = dz; si[k] = t; }
+            }
+        }
+        __syncthreads();
+        const uint32_t m = s_m;
+        if (m > (uint32_t)kVtxMax) {                   // uniform: too many tracks, no vertices
+            if (tid == 0) {
+                b.cnt[C_VERTS * b.E + e] = 0;
+                atomicOr(&b.cnt[C_FLAGS * b.E + e], F_VERTS);
+            }
+            __syncthreads();
+            continue;
+        }
+        uint32_t P2 = 1;
+        while (P2 < m) P2 <<= 1;
+        for (uint32_t k = m + tid; k < P2; k += nt) {
+            sz[k] = __longlong_as_double(0x7FF0000000000000LL);   // +inf after every track
+            si[k] = 0xFFFFFFFFu;
+        }
+        __syncthreads();
+        for (uint32_t size = 2; size <= P2; size <<= 1)
+            for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+                for (uint32_t i = tid; i < P2; i += nt) {
+                    const uint32_t j = i ^ stride;
+                    if (j > i) {
+                        const bool asc = (i & size) == 0;
+                        const bool jl = sz[j] < sz[i] || (sz[j] == sz[i] && si[j] < si[i]);
+                        if (asc == jl) {
+                            const double tz = sz[i]; sz[i] = sz[j]; sz[j] = tz;
+                            const uint32_t ti = si[i]; si[i] = si[j]; si[j] = ti;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        // each thread owns a run of consecutive sorted positions; a position is a vertex start
+        // when it starts a cluster of at least vtx_min tracks
+        const uint32_t per = (m + nt - 1) / nt;
+        const uint32_t k0 = min(m, tid * per), k1 = min(m, k0 + per);
+        auto starts = [&](uint32_t k) { return k == 0 || sz[k] - sz[k - 1] > p.vtx_gap; };
+        auto members = [&](uint32_t k) {
+            uint32_t c = 1;
+            while (k + c < m && !starts(k + c)) ++c;
+            return c;
+        };
+        uint32_t mine = 0;
+        for (uint32_t k = k0; k < k1; ++k)
+            if (starts(k) && members(k) >= p.vtx_min) ++mine;
+        // block-wide exclusive scan of the counts
+        const uint32_t lane = tid & 31u, wid = tid >> 5;
+        uint32_t incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= (uint32_t)o) incl += t;
+        }
+        if (lane == 31) s_wsum[wid] = incl;
+        __syncthreads();
+        uint32_t before = 0, nv = 0;
+        for (uint32_t w = 0; w < nt / 32; ++w) {
+            if (w < wid) before += s_wsum[w];
+            nv += s_wsum[w];
+        }
+        uint32_t vi = before + incl - mine;
+        // the vertex records, in cluster order, at the event's vertex arrays
+        for (uint32_t k = k0; k < k1; ++k) {
+            if (!starts(k)) continue;
+            const uint32_t c = members(k);
+            if (c < p.vtx_min) continue;
+            double sum = 0.0, pt2 = 0.0;
+            for (uint32_t q = 0; q < c; ++q) {
+                sum += sz[k + q];
+                const double pt = b.o_pt[a + si[k + q]];
+                pt2 += pt * pt;
+            }
+            const double z = sum / (double)c;
+            double ss = 0.0;
+            for (uint32_t q = 0; q < c; ++q) ss += (sz[k + q] - z) * (sz[k + q] - z);
+            b.v_z[a + vi] = z;
+            b.v_err[a + vi] = c > 1 ? sqrt(ss / ((double)c * (double)(c - 1))) : 0.0;
+            b.v_pt2[a + vi] = pt2;
+            b.v_n[a + vi] = k;                          // (the start, until the final pass)
+            ++vi;
+        }
+        __syncthreads();
+        // ranks: sum pT^2 descending, then z ascending (vertex records owned per thread)
+        constexpr int kOwn = kVtxMax / kVtxThreads;   // records per thread at most (vtx_min >= 2)
+        double oz[kOwn], oe[kOwn], op[kOwn];
+        uint32_t ok_[kOwn], orank[kOwn];
+        int own = 0;
+        for (uint32_t v = tid; v < nv && own < kOwn; v += nt, ++own) {
+            oz[own] = b.v_z[a + v];
+            oe[own] = b.v_err[a + v];
+            op[own] = b.v_pt2[a + v];
+            ok_[own] = b.v_n[a + v];
+            uint32_t r = 0;
+            for (uint32_t u = 0; u < nv; ++u) {
+                const double pu = b.v_pt2[a + u], zu = b.v_z[a + u];
+                r += pu > op[own] || (pu == op[own] && (zu < oz[own] || (zu == oz[own] && u < v)));
+            }
+            orank[own] = r;
+        }
+        __syncthreads();
+        for (int q = 0; q < own; ++q) {
+            const uint32_t r = orank[q], k = ok_[q];
+            const uint32_t c = members(k);
+            b.v_z[a + r] = oz[q];
+            b.v_err[a + r] = oe[q];
+            b.v_pt2[a + r] = op[q];
+            b.v_n[a + r] = c;
+            for (uint32_t t = 0; t < c; ++t) b.o_vtx[a + si[k + t]] = (int32_t)r;
+        }
+        if (tid == 0) b.cnt[C_VERTS * b.E + e] = nv;
+        __syncthreads();
+    }
+}
+
+cudaError_t init_fit_kernels()
+{
+    return cudaFuncSetAttribute(k_vertices, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kVtxMax * (int)(sizeof(double) + sizeof(uint32_t)));
+}
+
+void launch_vertices(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms)
+{
+    if (b.E == 0) return;
+    const size_t smem = (size_t)kVtxMax * (sizeof(double) + sizeof(uint32_t));
+    const uint32_t grid = b.E < (uint32_t)sms * 2 ? b.E : (uint32_t)sms * 2;
+    k_vertices<<<grid, kVtxThreads, smem, s>>>(b, p);
+}
+
 // Fit-only path: m ntuplets given directly.
 __global__ void __launch_bounds__(128) k_fit_batch(uint32_t m, const uint8_t *nh, const float *x,
                                                    const float *y, const float *z,

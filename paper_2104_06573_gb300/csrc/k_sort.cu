@@ -105,8 +105,10 @@ __global__ void __launch_bounds__(512) k_sort(DevBatch b, DevParams p)
 cudaError_t init_kernels()
 {
     // up to 16 layers x 2048 bins of 4-byte counters
-    return cudaFuncSetAttribute(k_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kMaxLayers * 2048 * (int)sizeof(uint32_t));
+    cudaError_t e = cudaFuncSetAttribute(k_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kMaxLayers * 2048 * (int)sizeof(uint32_t));
+    if (e != cudaSuccess) return e;
+    return init_fit_kernels();
 }
 
 void launch_sort(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms)

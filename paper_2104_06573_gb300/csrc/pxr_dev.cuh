@@ -26,8 +26,8 @@ constexpr uint32_t kHitChunk = 32;   // granularity of the hit -> event table
 // Per-event counters, laid out as kCounters consecutive arrays of E words.
 enum Counter : int {
     C_CELLS = 0, C_EDGES = 1, C_TUPLES = 2, C_FLAGS = 3, C_OUT = 4,   // reported per event
-    C_ROOTS = 5, C_SLOTS = 6, C_FRONT = 7,                             // internal
-    kCounters = 8
+    C_ROOTS = 5, C_SLOTS = 6, C_FRONT = 7, C_VERTS = 8,                // internal
+    kCounters = 9
 };
 constexpr int kReportedCounters = 5;
 
@@ -35,7 +35,7 @@ constexpr int kReportedCounters = 5;
 constexpr uint8_t kQGood = 1u, kQKept = 2u;
 
 // Per-event flags (C_FLAGS).
-enum Flag : uint32_t { F_CELLS = 1u, F_EDGES = 2u, F_TUPLES = 4u, F_LAYER = 8u };
+enum Flag : uint32_t { F_CELLS = 1u, F_EDGES = 2u, F_TUPLES = 4u, F_LAYER = 8u, F_VERTS = 16u };
 
 enum CutMode : uint32_t { CUT_FP64 = 0, CUT_FP32 = 1 };
 enum FitMode : uint32_t { FIT_FP64 = 0, FIT_MIXED = 1, FIT_FP32 = 2, FIT_RIEMANN = 3 };
@@ -72,6 +72,8 @@ struct DevParams {
     double pt_min, chi2_max;            // track selection (0: no cut)
     uint32_t clean;                     // shared-hit cleaning
     uint32_t cov;                       // fit covariance wanted
+    uint32_t vtx, vtx_min;              // primary vertices wanted; tracks a vertex needs
+    double vtx_gap;                     // largest z gap (cm) inside a vertex cluster
 };
 
 struct DevBatch {
@@ -129,6 +131,11 @@ struct DevBatch {
     int8_t *o_q, *o_status;
     uint8_t *o_ql;                      // quality bits (PXR_Q_*)
     double *o_cov;                      // [out_cap * 15] covariances (only with the cov option)
+    // primary vertices (only with the vertex option): per track its vertex (-1 none); per event
+    // the vertices at the event's output offset, ordered by sum pT^2 (C_VERTS of them)
+    int32_t *o_vtx;
+    double *v_z, *v_err, *v_pt2;
+    uint32_t *v_n;
     unsigned long long *best;           // [N] shared-hit cleaning: best rank key per hit (caller
                                         //   order, events back to back)
 };
@@ -157,6 +164,7 @@ __device__ __forceinline__ uint32_t find_event(const uint32_t *__restrict__ off,
 
 // One-time kernel attributes (large dynamic shared memory of the sort kernel).
 cudaError_t init_kernels();
+cudaError_t init_fit_kernels();     // (called by init_kernels)
 
 // Kernel launchers (defined in the .cu files).
 void launch_sort(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms);
@@ -177,6 +185,7 @@ void launch_fit(const DevBatch &b, const DevParams &p, uint32_t tup_total, cudaS
                 int sms);
 void launch_keep(const DevBatch &b, const DevParams &p, uint32_t tup_total, cudaStream_t s,
                  int sms);
+void launch_vertices(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms);
 void launch_fit_batch(uint32_t m, const uint8_t *nh, const float *x, const float *y,
                       const float *z, const uint16_t *layer, uint32_t stride, const DevParams &p,
                       double *pt, double *phi, double *cot, double *dxy, double *dz, double *chi2,

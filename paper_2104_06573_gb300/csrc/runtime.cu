@@ -55,6 +55,8 @@ extern "C" int pxr_params_init(pxr_params *p, int preset)
 {
     if (!p) return fail(PXR_EINVAL, "null params");
     std::memset(p, 0, sizeof(*p));
+    p->vtx_min_tracks = 2;                      // used when vertexing is switched on
+    p->vtx_gap = 0.05;
     if (preset == PXR_PRESET_BARREL) {
         p->n_layers = 4;
         const uint8_t pi[] = {0, 1, 2}, po[] = {1, 2, 3};
@@ -126,6 +128,9 @@ static int check_params(const pxr_params *p, DevParams *d)
         !std::isfinite(p->chi2_max) || p->clean_shared > 1)
         return fail(PXR_EINVAL, "pt_min and chi2_max must be finite and >= 0, clean_shared 0 or 1");
     if (p->fit_cov > 1) return fail(PXR_EINVAL, "fit_cov must be 0 or 1");
+    if (p->vertexing > 1 || (p->vertexing && (p->vtx_min_tracks < 2 || !(p->vtx_gap > 0.0) ||
+                                             !std::isfinite(p->vtx_gap))))
+        return fail(PXR_EINVAL, "vertexing needs vtx_min_tracks >= 2 and a finite vtx_gap > 0");
     if (!d) return PXR_OK;
     std::memset(d, 0, sizeof(*d));
     d->n_layers = p->n_layers;
@@ -169,6 +174,9 @@ static int check_params(const pxr_params *p, DevParams *d)
     d->chi2_max = p->chi2_max;
     d->clean = p->clean_shared;
     d->cov = p->fit_cov;
+    d->vtx = p->vertexing;
+    d->vtx_min = p->vtx_min_tracks;
+    d->vtx_gap = p->vtx_gap;
     // CA levels: a layer's level is 1 + the highest level of its pairs' inner layers (0 without
     // in-pairs); junction layers (in- and out-pairs) are processed level by level, so that every
     // cell has all its in-edges before its own out-edges are built
@@ -256,7 +264,8 @@ struct PlanOffsets {
     size_t cnt, bkt, hs, r64, hmeta, hphi, item, cell_in, cell_out,
         nbr_first,
         nbr_n, nbr, mindepth, root_list, live, front_list, front_snap, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, out_evt, o_nh,
-        o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status, o_ql, best, o_cov;
+        o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status, o_ql, best, o_cov, o_vtx,
+        v_z, v_err, v_pt2, v_n;
     size_t total;
 };
 
@@ -317,6 +326,11 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.o_ql = L.add(T);
     o.best = L.add(dp.clean ? 8 * N : 0);
     o.o_cov = L.add(dp.cov ? 8 * 15 * T : 0);
+    o.o_vtx = L.add(dp.vtx ? 4 * T : 0);
+    o.v_z = L.add(dp.vtx ? 8 * T : 0);
+    o.v_err = L.add(dp.vtx ? 8 * T : 0);
+    o.v_pt2 = L.add(dp.vtx ? 8 * T : 0);
+    o.v_n = L.add(dp.vtx ? 4 * T : 0);
     o.total = L.add(0);
     return o;
 }
@@ -509,6 +523,11 @@ static void plan_bind(pxr_plan *P)
     b.o_ql = (uint8_t *)(r + o.o_ql);
     b.best = (unsigned long long *)(r + o.best);
     b.o_cov = (double *)(r + o.o_cov);
+    b.o_vtx = (int32_t *)(r + o.o_vtx);
+    b.v_z = (double *)(r + o.v_z);
+    b.v_err = (double *)(r + o.v_err);
+    b.v_pt2 = (double *)(r + o.v_pt2);
+    b.v_n = (uint32_t *)(r + o.v_n);
 }
 
 // Fill the per-event capacity prefixes from per-layer counts (lcount: E x (kMaxLayers+1)).
@@ -612,6 +631,7 @@ static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
     if (p.clean) CK(cudaMemsetAsync(b.best, 0xFF, 8 * (size_t)P->N, s));
     launch_fit(b, p, (uint32_t)P->T, s, sms);
     if (p.clean) launch_keep(b, p, (uint32_t)P->T, s, sms);
+    if (p.vtx) launch_vertices(b, p, s, sms);
     if (t) CK(stage_mark(P->ev_stage[5], s, capturing));
     CK(cudaGetLastError());
     return PXR_OK;
@@ -619,7 +639,8 @@ static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
 
 static int plan_launches(const pxr_plan *P)
 {
-    int n = 6 + (P->dp.clean ? 1 : 0);          // sort, doublets, walk, select, scan, fit, keep
+    int n = 6 + (P->dp.clean ? 1 : 0) + (P->dp.vtx ? 1 : 0);   // sort, doublets, walk, select,
+                                                                 // scan, fit, keep, vertices
     for (uint32_t lv = 1; lv <= P->dp.n_levels; ++lv)
         n += (P->dp.level_dense[lv] ? 1 : 0) + (P->dp.level_sparse[lv] ? 1 : 0);
     return n;
@@ -810,12 +831,20 @@ struct HostTracks {
     std::vector<int8_t> q, st;
     std::vector<uint8_t> ql;
     std::vector<double> cov;             // 15 per track, or empty (covariance not computed)
+    std::vector<int32_t> vtx;            // vertex of each track, or empty (no vertex finding)
+    std::vector<double> vz, verr, vpt2;  // the event's vertices
+    std::vector<uint32_t> vn;
     size_t size() const { return nh.size(); }
-    void resize(size_t n, bool with_cov = false)
+    void resize(size_t n, bool with_cov = false, bool with_vtx = false)
     {
         nh.resize(n); hits.resize(n * kMaxHits); pt.resize(n); phi.resize(n); cot.resize(n);
         dxy.resize(n); dz.resize(n); chi2.resize(n); q.resize(n); st.resize(n); ql.resize(n);
         cov.resize(with_cov ? 15 * n : 0);
+        vtx.resize(with_vtx ? n : 0);
+    }
+    void resize_vertices(size_t nv)
+    {
+        vz.resize(nv); verr.resize(nv); vpt2.resize(nv); vn.resize(nv);
     }
 };
 
@@ -867,8 +896,17 @@ static int emit_tracks(const HostTracks &h, int32_t status, pxr_tracks *out, boo
 {
     const size_t n = h.size();
     out->n_tracks = (uint32_t)n;
+    out->n_vertices = (uint32_t)h.vz.size();
     out->status = status;
     if (n > out->capacity) return fail(PXR_ETRUNC, "track capacity too small");
+    // the vertices (ordered by sum pT^2, whatever the track order)
+    const size_t nv = h.vz.size();
+    if (nv) {
+        if (out->vtx_z) std::memcpy(out->vtx_z, h.vz.data(), 8 * nv);
+        if (out->vtx_z_err) std::memcpy(out->vtx_z_err, h.verr.data(), 8 * nv);
+        if (out->vtx_sum_pt2) std::memcpy(out->vtx_sum_pt2, h.vpt2.data(), 8 * nv);
+        if (out->vtx_n_tracks) std::memcpy(out->vtx_n_tracks, h.vn.data(), 4 * nv);
+    }
     if (in_order) {                          // already canonical: one copy per array
         auto cp = [n](void *dst, const void *src, size_t sz) {
             if (dst && n) std::memcpy(dst, src, sz * n);
@@ -887,6 +925,10 @@ static int emit_tracks(const HostTracks &h, int32_t status, pxr_tracks *out, boo
         if (out->cov) {
             if (h.cov.empty()) std::fill(out->cov, out->cov + 15 * n, NAN);
             else cp(out->cov, h.cov.data(), 15 * sizeof(double));
+        }
+        if (out->vertex) {
+            if (h.vtx.empty()) std::fill(out->vertex, out->vertex + n, -1);
+            else cp(out->vertex, h.vtx.data(), 4);
         }
         return PXR_OK;
     }
@@ -910,11 +952,12 @@ static int emit_tracks(const HostTracks &h, int32_t status, pxr_tracks *out, boo
             if (h.cov.empty()) std::fill(out->cov + 15 * k, out->cov + 15 * k + 15, NAN);
             else std::memcpy(out->cov + 15 * k, h.cov.data() + 15 * s, 15 * sizeof(double));
         }
+        if (out->vertex) out->vertex[k] = h.vtx.empty() ? -1 : h.vtx[s];
     }
     return PXR_OK;
 }
 
-static int32_t flags_status(uint32_t f) { return (f & (F_CELLS | F_EDGES | F_TUPLES)) ? PXR_EOVERFLOW : (f & F_LAYER) ? PXR_EINVAL : PXR_OK; }
+static int32_t flags_status(uint32_t f) { return (f & (F_CELLS | F_EDGES | F_TUPLES | F_VERTS)) ? PXR_EOVERFLOW : (f & F_LAYER) ? PXR_EINVAL : PXR_OK; }
 
 template <typename T>
 static int d2h(std::vector<T> &v, const void *src, size_t n)
@@ -944,6 +987,14 @@ extern "C" int pxr_plan_tracks(pxr_plan *P, uint32_t e, pxr_tracks *out)
         (rc = d2h(h.ql, P->db.o_ql + a, n)))
         return rc;
     if (P->dp.cov && (rc = d2h(h.cov, P->db.o_cov + 15 * a, 15 * n))) return rc;
+    if (P->dp.vtx) {
+        uint32_t nv = 0;
+        CK(cudaMemcpy(&nv, P->db.cnt + C_VERTS * P->E + e, 4, cudaMemcpyDeviceToHost));
+        if ((rc = d2h(h.vtx, P->db.o_vtx + a, n)) || (rc = d2h(h.vz, P->db.v_z + a, nv)) ||
+            (rc = d2h(h.verr, P->db.v_err + a, nv)) || (rc = d2h(h.vpt2, P->db.v_pt2 + a, nv)) ||
+            (rc = d2h(h.vn, P->db.v_n + a, nv)))
+            return rc;
+    }
     return emit_tracks(h, flags_status(flags), out);
 }
 
@@ -1102,7 +1153,8 @@ struct Batch {
     size_t reserved = 0;
     uint32_t total = 0;
     size_t o_nh = 0, o_hits = 0, o_pt = 0, o_phi = 0, o_cot = 0, o_dxy = 0, o_dz = 0,
-           o_chi2 = 0, o_q = 0, o_st = 0, o_ql = 0, o_cov = 0;
+           o_chi2 = 0, o_q = 0, o_st = 0, o_ql = 0, o_cov = 0, o_vtx = 0, v_z = 0, v_err = 0,
+           v_pt2 = 0, v_n = 0;
     ~Batch()
     {
         if (ev_counts) cudaEventDestroy(ev_counts);
@@ -1166,7 +1218,7 @@ static int launch_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
     P->own_inputs = true;
     if ((rc = plan_size(P, lcount.data(), true))) return rc;
     SlotBuffers &sb = *ctx->slot_buf[slot];
-    if (!sb.head.reserve(P->off.head_end) || !sb.evt.reserve(4 * (2 * (size_t)E + 1)))
+    if (!sb.head.reserve(P->off.head_end) || !sb.evt.reserve(4 * (3 * (size_t)E + 1)))
         return fail(PXR_ENOMEM, "pinned host allocation failed");
     CK(cudaEventCreateWithFlags(&B->ev_counts, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&B->ev_data, cudaEventDisableTiming));
@@ -1213,6 +1265,8 @@ static int launch_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
     uint32_t *hev = (uint32_t *)sb.evt.p;
     CK(cudaMemcpyAsync(hev, P->db.out_evt, e1, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(hev + E + 1, P->db.cnt + C_FLAGS * E, 4 * E, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hev + 2 * E + 1, P->db.cnt + C_VERTS * E, 4 * E, cudaMemcpyDeviceToHost,
+                       s));
     CK(cudaEventRecord(B->ev_counts, s));
     }
     B->state = 1;
@@ -1251,6 +1305,12 @@ static bool progress_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
         B.o_st = L.add(T);
         B.o_ql = L.add(T);
         B.o_cov = L.add(P->dp.cov ? 8 * 15 * (size_t)T : 0);
+        const size_t tv = P->dp.vtx ? (size_t)T : 0;
+        B.o_vtx = L.add(4 * tv);
+        B.v_z = L.add(8 * tv);
+        B.v_err = L.add(8 * tv);
+        B.v_pt2 = L.add(8 * tv);
+        B.v_n = L.add(4 * tv);
         bool ok = sb.out.reserve(L.add(0) + 256);
         const DevBatch &d = P->db;
         char *ho = sb.out.p;
@@ -1270,6 +1330,13 @@ static bool progress_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
             cp(B.o_st, d.o_status, T);
             cp(B.o_ql, d.o_ql, T);
             if (P->dp.cov) cp(B.o_cov, d.o_cov, 8 * 15 * (size_t)T);
+            if (P->dp.vtx) {
+                cp(B.o_vtx, d.o_vtx, 4 * (size_t)T);
+                cp(B.v_z, d.v_z, 8 * (size_t)T);
+                cp(B.v_err, d.v_err, 8 * (size_t)T);
+                cp(B.v_pt2, d.v_pt2, 8 * (size_t)T);
+                cp(B.v_n, d.v_n, 4 * (size_t)T);
+            }
         }
         ok &= cudaEventRecord(B.ev_data, s) == cudaSuccess;
         if (!ok) ctx->sched_error = "device-to-host copy failed";
@@ -1295,7 +1362,15 @@ static bool progress_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
             if (!ts[e]) continue;
             Ticket &t = *ts[e];
             const uint32_t a = hev[e], n = hev[e + 1] - a;
-            t.res.resize(n, P->dp.cov != 0);
+            t.res.resize(n, P->dp.cov != 0, P->dp.vtx != 0);
+            t.res.resize_vertices(P->dp.vtx ? hev[2 * E + 1 + e] : 0);
+            if (P->dp.vtx) {
+                const uint32_t nv = hev[2 * E + 1 + e];
+                std::memcpy(t.res.vz.data(), ho + B.v_z + 8 * (size_t)a, 8 * (size_t)nv);
+                std::memcpy(t.res.verr.data(), ho + B.v_err + 8 * (size_t)a, 8 * (size_t)nv);
+                std::memcpy(t.res.vpt2.data(), ho + B.v_pt2 + 8 * (size_t)a, 8 * (size_t)nv);
+                std::memcpy(t.res.vn.data(), ho + B.v_n + 4 * (size_t)a, 4 * (size_t)nv);
+            }
             if (n) {
                 // canonical order here, on the scheduler thread, so that a fetch only copies
                 auto hp = [&](size_t off) { return ho + off; };
@@ -1329,6 +1404,8 @@ static bool progress_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
                     if (P->dp.cov)
                         std::memcpy(&t.res.cov[15 * (size_t)k], cv + 15 * (size_t)s_,
                                     15 * sizeof(double));
+                    if (P->dp.vtx)
+                        t.res.vtx[k] = ((const int32_t *)(ho + B.o_vtx))[a + s_];
                 }
             }
         }

@@ -44,7 +44,8 @@ class pxr_params(C.Structure):
                 ("x_over_x0", C.c_double), ("n_phi_bins", C.c_uint32),
                 ("max_cells_per_event", C.c_uint32), ("max_tuples_per_event", C.c_uint32),
                 ("grid_per_sm", C.c_uint32 * 6), ("pt_min", C.c_double), ("chi2_max", C.c_double),
-                ("clean_shared", C.c_uint32), ("fit_cov", C.c_uint32)]
+                ("clean_shared", C.c_uint32), ("fit_cov", C.c_uint32),
+                ("vertexing", C.c_uint32), ("vtx_min_tracks", C.c_uint32), ("vtx_gap", C.c_double)]
 
 
 class pxr_config(C.Structure):
@@ -60,7 +61,10 @@ class pxr_tracks(C.Structure):
                 ("n_hits", C.c_void_p), ("hit_idx", C.c_void_p), ("pt", C.c_void_p),
                 ("phi", C.c_void_p), ("cot_theta", C.c_void_p), ("dxy", C.c_void_p),
                 ("dz", C.c_void_p), ("chi2", C.c_void_p), ("charge", C.c_void_p),
-                ("fit_status", C.c_void_p), ("quality", C.c_void_p), ("cov", C.c_void_p)]
+                ("fit_status", C.c_void_p), ("quality", C.c_void_p), ("cov", C.c_void_p),
+                ("vertex", C.c_void_p), ("n_vertices", C.c_uint32), ("vtx_z", C.c_void_p),
+                ("vtx_z_err", C.c_void_p), ("vtx_sum_pt2", C.c_void_p),
+                ("vtx_n_tracks", C.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -148,12 +152,14 @@ STAGES = ("sort", "doublets", "connect", "walk", "select", "fit")   # PXR_STAGE_
 
 def params_from(p, cut_mode=CUT_FP64, fit_mode=FIT_FP64, n_phi_bins=0, max_cells=0,
                 max_tuples=0, grid_per_sm=None, pt_min=0.0, chi2_max=0.0,
-                clean_shared=False, fit_cov=False) -> pxr_params:
+                clean_shared=False, fit_cov=False, vertexing=False, vtx_min_tracks=2,
+                vtx_gap=0.05) -> pxr_params:
     """Marshal any object with the workload fields (n_layers, layer_is_disk, pairs, root_mask,
     drop_suffixes, min_hits, max_hits, phi_window, cos_phi_window, cuts, field, errors).
     grid_per_sm: optional CTAs-per-SM caps per stage (STAGES order; 0 = built-in).
     pt_min, chi2_max, clean_shared: the track selection (0 / False: off); fit_cov: compute the
-    tracks' covariances (the fetched 'cov' field, [n, 15]; NaN otherwise)."""
+    tracks' covariances (the fetched 'cov' field, [n, 15]; NaN otherwise); vertexing,
+    vtx_min_tracks, vtx_gap: primary vertices from the kept tracks."""
     o = pxr_params()
     o.n_layers = p.n_layers
     for i, v in enumerate(p.layer_is_disk):
@@ -176,6 +182,8 @@ def params_from(p, cut_mode=CUT_FP64, fit_mode=FIT_FP64, n_phi_bins=0, max_cells
     o.pt_min, o.chi2_max = float(pt_min), float(chi2_max)
     o.clean_shared = 1 if clean_shared else 0
     o.fit_cov = 1 if fit_cov else 0
+    o.vertexing = 1 if vertexing else 0
+    o.vtx_min_tracks, o.vtx_gap = int(vtx_min_tracks), float(vtx_gap)
     return o
 
 
@@ -201,7 +209,10 @@ _TRACK_LAYOUT = (("n_hits", np.uint8, 1), ("hit_idx", np.uint32, MAX_HITS),
                  ("pt", np.float64, 1), ("phi", np.float64, 1), ("cot_theta", np.float64, 1),
                  ("dxy", np.float64, 1), ("dz", np.float64, 1), ("chi2", np.float64, 1),
                  ("charge", np.int8, 1), ("fit_status", np.int8, 1), ("quality", np.uint8, 1),
+                 ("vertex", np.int32, 1), ("vtx_z", np.float64, 1), ("vtx_z_err", np.float64, 1),
+                 ("vtx_sum_pt2", np.float64, 1), ("vtx_n_tracks", np.uint32, 1),
                  ("cov", np.float64, 15))
+_VERTEX_FIELDS = ("vtx_z", "vtx_z_err", "vtx_sum_pt2", "vtx_n_tracks")
 
 
 def _read_tracks(call, cov=False) -> dict:
@@ -216,7 +227,7 @@ def _read_tracks(call, cov=False) -> dict:
         _check(rc)
     n = t.n_tracks
     if rc == OK:                                        # no tracks: the call is complete
-        out = {"n": 0, "status": t.status}
+        out = {"n": 0, "status": t.status, "n_vertices": 0}
         for name, dt, k in layout:
             out[name] = np.zeros((0, k) if k > 1 else 0, dt)
         return out
@@ -234,10 +245,12 @@ def _read_tracks(call, cov=False) -> dict:
             n = t.n_tracks
             continue
         _check(rc)
-        out = {"n": n, "status": t.status}
+        out = {"n": n, "status": t.status, "n_vertices": t.n_vertices}
         for (name, dt, k), off in zip(layout, offs[:-1]):
             a = np.frombuffer(buf, dt, n * k, int(off))
             out[name] = a.reshape(n, k) if k > 1 else a
+        for name in _VERTEX_FIELDS:                      # the vertex arrays hold n_vertices
+            out[name] = out[name][:t.n_vertices]
         return out
 
 

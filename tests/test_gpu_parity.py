@@ -312,6 +312,41 @@ def test_covariance_matches_oracle(ctx, orc, fit):
     assert rel.max() < 1e-3
 
 
+def test_vertices_match_oracle(ctx, orc):
+    """Primary vertices (plan and serving paths) against the oracle's on a smeared event with 40
+    generated vertices, shared-hit cleaning on, FP64 fit: the same vertices in the same order
+    (track counts, sums of pT^2), z within 1e-9 cm, and the same vertex for every track."""
+    P = synth.params_barrel_quadruplets()
+    ev = synth.make_event(21, 2000, smear=True, n_vertices=40)
+    e = ev_tuple(ev)
+    sel = dict(clean_shared=True, vertexing=True, vtx_min_tracks=2, vtx_gap=0.05)
+    got = run_plan(ctx, [e], P, pxr.CUT_FP32, debug=False, **sel)[0]["tracks"]
+    ref = orc.reconstruct(*e, P)
+    q = orc.select_tracks(ref["tuples"], ref["tuple_n"], ref["fits"], clean_shared=True)
+    v, vid = orc.find_vertices(ref["fits"], q, gap=0.05, min_tracks=2)
+    # no kept pair of neighbours within round-off of the gap (else the test would be ambiguous)
+    dz = np.sort(ref["fits"]["dz"][(q & pxr.Q_KEPT) != 0])
+    assert np.min(np.abs(np.diff(dz) - 0.05)) > 1e-9
+    assert got["n_vertices"] == len(v["z"]) > 20
+    assert np.array_equal(got["vtx_n_tracks"], v["n_tracks"])
+    assert np.max(np.abs(got["vtx_z"] - v["z"])) < 1e-9
+    assert np.allclose(got["vtx_z_err"], v["z_err"], rtol=1e-6, atol=1e-12)
+    assert np.allclose(got["vtx_sum_pt2"], v["sum_pt2"], rtol=1e-9)
+    # the vertex of each track (tracks matched by their hit tuples)
+    tup = [tuple(int(h) for h in row[:n]) for row, n in zip(ref["tuples"], ref["tuple_n"])]
+    want = dict(zip(tup, vid.tolist()))
+    assert [want[t] for t in gpu_tuples(got)] == got["vertex"].tolist()
+    # the serving path gives the same vertices
+    p = pxr.params_from(P, cut_mode=pxr.CUT_FP32, fit_mode=pxr.FIT_FP64, **sel)
+    with pxr.Context(device=0, mem_budget_bytes=2 << 30) as sctx:
+        t = sctx.pxr_submit_event(*e, p)
+        while t not in sctx.pxr_poll(timeout_us=100000):
+            pass
+        served = sctx.pxr_fetch_tracks(t)
+    for k in ("vtx_z", "vtx_z_err", "vtx_sum_pt2", "vtx_n_tracks", "vertex"):
+        assert np.array_equal(served[k], got[k]), k
+
+
 def test_graph_equals_direct_and_bin_counts(ctx, orc):
     """Graph replay and direct launches agree; the result does not depend on the bin count."""
     P = synth.params_phase1()
