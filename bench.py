@@ -536,6 +536,59 @@ def _selection_study(pxr, synth, ctx, dev, stream, n_events=256, reps=10):
     return res
 
 
+def _vertex_study(pxr, synth, ctx, dev, stream, n_events=256, n_vertices=50, reps=10):
+    """Primary vertices on the batch workload made of events with n_vertices generated vertices
+    each (smeared hits, shared-hit cleaning on): the cost of the vertex kernel (fit+output stage
+    with and without it, L2 flushed between steps) and the vertices found against the generated
+    ones (those with at least 5 kept tracks)."""
+    import torch
+    counts = synth.batch_track_counts(n_events, 0)
+    evs = [synth.make_event(e, counts[e], smear=True, n_vertices=n_vertices)
+           for e in range(n_events)]
+    off = np.zeros(n_events + 1, np.uint32)
+    off[1:] = np.cumsum([e.n for e in evs])
+    cat = lambda k: np.concatenate([getattr(e, k) for e in evs])
+    x, y, z = (torch.from_numpy(cat(k)).to(dev) for k in "xyz")
+    layer = torch.from_numpy(cat("layer").view(np.int16)).to(dev)
+    P = synth.params_barrel_quadruplets()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    res = {"events": n_events, "vertices_per_event": n_vertices}
+    for name, vtx in (("off", False), ("on", True)):
+        prm = pxr.params_from(P, cut_mode=pxr.CUT_FP32, fit_mode=pxr.FIT_MIXED, n_phi_bins=1024,
+                              clean_shared=True, vertexing=vtx)
+        plan = pxr.Plan(ctx, off, x, y, z, layer, prm, use_graph=True)
+        st = np.zeros(5)
+        with torch.cuda.stream(stream):
+            for r in range(reps + 2):
+                flush.zero_()
+                plan.pxr_plan_run(stream)
+                stream.synchronize()
+                if r >= 2:
+                    st += np.array(plan.pxr_plan_stage_ms())
+        st /= reps
+        res["step_ms_" + name] = float(st.sum())
+        res["fit_output_ms_" + name] = float(st[4])
+        if vtx:
+            found, gen, dzs, n_reco = 0, 0, [], 0
+            for e, ev in enumerate(evs):
+                t = plan.pxr_plan_tracks(e)
+                n_reco += t["n_vertices"]
+                kept = (t["quality"] & pxr.Q_KEPT) != 0
+                tid = ev.track[t["hit_idx"][:, 0].astype(np.int64)]
+                zs, cnt = np.unique(ev.tracks.zv[tid[kept & (tid >= 0)]], return_counts=True)
+                for zt in zs[cnt >= 5]:
+                    gen += 1
+                    if t["n_vertices"]:
+                        d = np.min(np.abs(t["vtx_z"] - zt))
+                        dzs.append(d)
+                        found += d < 0.02
+            res.update({"vertices_found": n_reco, "generated_with_5_kept_tracks": gen,
+                        "generated_found_within_0.02cm": found / max(gen, 1),
+                        "median_abs_dz_cm": float(np.median(dzs)) if dzs else None})
+        plan.close()
+    return res
+
+
 def _oracle_rate(oracle, ev, P, min_s=1.0):
     n, t0 = 0, time.perf_counter()
     while True:
@@ -713,6 +766,8 @@ def study(args):
         out["C4_fit_precision"] = c4
         # next row N1: track selection (shared-hit cleaning) on the smeared batch
         out["N1_selection"] = _selection_study(pxr, synth, ctx, dev, stream)
+        # next row N3: primary vertices on a batch of events with 50 vertices each
+        out["N3_vertices"] = _vertex_study(pxr, synth, ctx, dev, stream)
     # C5: serving sweep, continuous batching vs one event per launch, 8 GB budget
     P = synth.params_barrel_quadruplets()
     prm = pxr.params_from(P, cut_mode=pxr.CUT_FP32, fit_mode=pxr.FIT_MIXED)

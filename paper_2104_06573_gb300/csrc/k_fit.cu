@@ -778,8 +778,8 @@ void launch_keep(const DevBatch &b, const DevParams &p, uint32_t total, cudaStre
 constexpr int kVtxMax = 8192;      // kept tracks per event the vertex finder takes (more: flagged)
 constexpr int kVtxThreads = 512;
 
-// One CTA per event.  The kept tracks with a finite dz are gathered into shared memory and
-// sorted by (dz, output slot) with a bitonic network; a sorted track starts a new cluster when
+// One CTA per event.  The kept tracks with a finite dz are gathered into shared memory (dz, pT^2,
+// output slot) and sorted by (dz, output slot) with a bitonic network; a sorted track starts a new cluster when
 // its dz exceeds the previous one's by more than the gap.  Each cluster start counts its members;
 // clusters of at least vtx_min tracks become vertices (a block-wide scan gives their cluster-
 // order index).  Each vertex's start sums its members in sorted order (mean dz, the standard
@@ -789,7 +789,8 @@ __global__ void __launch_bounds__(kVtxThreads) k_vertices(DevBatch b, DevParams 
 {
     extern __shared__ unsigned char vsm[];
     double *sz = reinterpret_cast<double *>(vsm);                 // [kVtxMax] dz
-    uint32_t *si = reinterpret_cast<uint32_t *>(sz + kVtxMax);    // [kVtxMax] output slot
+    double *sp = sz + kVtxMax;                                    // [kVtxMax] pT^2 (sorted along)
+    uint32_t *si = reinterpret_cast<uint32_t *>(sp + kVtxMax);    // [kVtxMax] output slot
     __shared__ uint32_t s_m, s_wsum[kVtxThreads / 32];
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
     for (uint32_t e = blockIdx.x; e < b.E; e += gridDim.x) {
@@ -801,7 +802,12 @@ __global__ void __launch_bounds__(kVtxThreads) k_vertices(DevBatch b, DevParams 
             const double dz = b.o_dz[a + t];
             if ((b.o_ql[a + t] & kQKept) && isfinite(dz)) {
                 const uint32_t k = atomicAdd(&s_m, 1u);
-                if (k < (uint32_t)kVtxMax) { sz[k] = dz; si[k] = t; }
+                if (k < (uint32_t)kVtxMax) {
+                    const double pt = b.o_pt[a + t];
+                    sz[k] = dz;
+                    sp[k] = pt * pt;
+                    si[k] = t;
+                }
             }
         }
         __syncthreads();
@@ -830,6 +836,7 @@ __global__ void __launch_bounds__(kVtxThreads) k_vertices(DevBatch b, DevParams 
                         const bool jl = sz[j] < sz[i] || (sz[j] == sz[i] && si[j] < si[i]);
                         if (asc == jl) {
                             const double tz = sz[i]; sz[i] = sz[j]; sz[j] = tz;
+                            const double tp = sp[i]; sp[i] = sp[j]; sp[j] = tp;
                             const uint32_t ti = si[i]; si[i] = si[j]; si[j] = ti;
                         }
                     }
@@ -873,8 +880,7 @@ __global__ void __launch_bounds__(kVtxThreads) k_vertices(DevBatch b, DevParams 
             double sum = 0.0, pt2 = 0.0;
             for (uint32_t q = 0; q < c; ++q) {
                 sum += sz[k + q];
-                const double pt = b.o_pt[a + si[k + q]];
-                pt2 += pt * pt;
+                pt2 += sp[k + q];
             }
             const double z = sum / (double)c;
             double ss = 0.0;
@@ -921,13 +927,13 @@ __global__ void __launch_bounds__(kVtxThreads) k_vertices(DevBatch b, DevParams 
 cudaError_t init_fit_kernels()
 {
     return cudaFuncSetAttribute(k_vertices, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kVtxMax * (int)(sizeof(double) + sizeof(uint32_t)));
+                                kVtxMax * (int)(2 * sizeof(double) + sizeof(uint32_t)));
 }
 
 void launch_vertices(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms)
 {
     if (b.E == 0) return;
-    const size_t smem = (size_t)kVtxMax * (sizeof(double) + sizeof(uint32_t));
+    const size_t smem = (size_t)kVtxMax * (2 * sizeof(double) + sizeof(uint32_t));
     const uint32_t grid = b.E < (uint32_t)sms * 2 ? b.E : (uint32_t)sms * 2;
     k_vertices<<<grid, kVtxThreads, smem, s>>>(b, p);
 }
