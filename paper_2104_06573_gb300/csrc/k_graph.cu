@@ -446,14 +446,25 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
     uint32_t *bin = s_bin[wid];
     const uint32_t nk = p.n_keys;
     const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t jj = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; jj < b.N;
+    const uint32_t n_junctions = b.jbase[b.E];
+    for (uint64_t jj = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; jj < n_junctions;
          jj += stride) {
-        const uint32_t j = (uint32_t)jj;
-        // independent loads first (hits past an event's valid range carry layer 0xFF)
+        // the jj-th junction hit: its event from the per-event junction prefix, its position
+        // from the event's layer ranges of the layers in layer_mask
+        const uint32_t g = (uint32_t)jj;
+        const uint32_t e = find_event(b.jbase, b.E, g);
+        uint32_t o = g - b.jbase[e];
+        const uint32_t *bke = b.bkt + (size_t)e * (nk + 1);
+        uint32_t j = 0;
+        for (uint32_t l = 0; l < p.n_layers; ++l) {
+            if (!((layer_mask >> l) & 1u)) continue;
+            const uint32_t lo = bke[l * p.nb], n_l = bke[(l + 1) * p.nb] - lo;
+            if (o < n_l) { j = lo + o; break; }
+            o -= n_l;
+        }
         const uint32_t meta = b.hmeta[j];
         const float4 hj = b.hs[j];
         const float phij = b.hphi[j];
-        const uint32_t e = hit_event(b, j);
         const uint4 it0 = b.item[(size_t)j * kMaxOut];
         uint32_t f0 = it0.x, nB = it0.y;
         const uint32_t Lj = meta >> kLocalBits;
@@ -698,9 +709,50 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
     }
 }
 
+// Per-event prefix of the hits on the layers of layer_mask (the junctions of a dense CA level):
+// jbase[e] = junctions of events before e, jbase[E] = all.  One CTA; each thread takes a run of
+// consecutive events.
+__global__ void __launch_bounds__(1024) k_jbase(DevBatch b, DevParams p, uint32_t layer_mask)
+{
+    __shared__ uint32_t s_w[32];
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t per = (b.E + nt - 1) / nt;
+    const uint32_t e0 = min(b.E, tid * per), e1 = min(b.E, e0 + per);
+    auto count = [&](uint32_t e) {
+        const uint32_t *bke = b.bkt + (size_t)e * (p.n_keys + 1);
+        uint32_t c = 0;
+        for (uint32_t l = 0; l < p.n_layers; ++l)
+            if ((layer_mask >> l) & 1u) c += bke[(l + 1) * p.nb] - bke[l * p.nb];
+        return c;
+    };
+    uint32_t mine = 0;
+    for (uint32_t e = e0; e < e1; ++e) mine += count(e);
+    const uint32_t lane = tid & 31u, wid = tid >> 5;
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= (uint32_t)o) incl += t;
+    }
+    if (lane == 31) s_w[wid] = incl;
+    __syncthreads();
+    uint32_t run = 0, tot = 0;
+    for (uint32_t w = 0; w < nt / 32; ++w) {
+        if (w < wid) run += s_w[w];
+        tot += s_w[w];
+    }
+    run += incl - mine;
+    for (uint32_t e = e0; e < e1; ++e) {
+        b.jbase[e] = run;
+        run += count(e);
+    }
+    if (tid == 0) b.jbase[b.E] = tot;
+}
+
 void launch_connect(const DevBatch &b, const DevParams &p, uint32_t layer_mask, cudaStream_t s,
                     int sms)
 {
+    k_jbase<<<1, 1024, 0, s>>>(b, p, layer_mask);
     uint64_t blocks = ((uint64_t)b.N + kConnWarps - 1) / kConnWarps;
     uint64_t cap = (uint64_t)sms * p.grid_per_sm[2];
     if (blocks > cap) blocks = cap;

@@ -113,6 +113,7 @@ struct DevBatch {
     uint32_t *front_list;               // [edges] per event: non-root cells with in-edges whose
                                         //   outer hit starts further pairs (the sparse CA input;
                                         //   kNone: a slot reserved for a cell already listed)
+    uint32_t *jbase;                    // [E + 1] junction prefix of a dense CA level
     uint32_t *front_snap;               // [E] frontier lengths when a sparse pass starts (the pass
                                         //   appends for later levels while it reads)
     // ntuplets

@@ -263,7 +263,7 @@ struct PlanOffsets {
         head_end;
     size_t cnt, bkt, hs, r64, hmeta, hphi, item, cell_in, cell_out,
         nbr_first,
-        nbr_n, nbr, mindepth, root_list, live, front_list, front_snap, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, out_evt, o_nh,
+        nbr_n, nbr, mindepth, root_list, live, front_list, front_snap, jbase, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, out_evt, o_nh,
         o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status, o_ql, best, o_cov, o_vtx,
         v_z, v_err, v_pt2, v_n;
     size_t total;
@@ -306,6 +306,7 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.live = L.add(4 * ((C + 31) / 32));
     o.front_list = L.add(4 * G);
     o.front_snap = L.add(4 * (size_t)E);
+    o.jbase = L.add(4 * ((size_t)E + 1));
     o.tup_hits = L.add(4 * T * kMaxHits);
     o.tup_n = L.add(T);
     o.tup_state = L.add(T);
@@ -502,6 +503,7 @@ static void plan_bind(pxr_plan *P)
     b.live = (uint32_t *)(r + o.live);
     b.front_list = (uint32_t *)(r + o.front_list);
     b.front_snap = (uint32_t *)(r + o.front_snap);
+    b.jbase = (uint32_t *)(r + o.jbase);
     b.tup_hits = (uint32_t *)(r + o.tup_hits);
     b.tup_n = (uint8_t *)(r + o.tup_n);
     b.tup_state = (uint8_t *)(r + o.tup_state);
@@ -642,7 +644,7 @@ static int plan_launches(const pxr_plan *P)
     int n = 6 + (P->dp.clean ? 1 : 0) + (P->dp.vtx ? 1 : 0);   // sort, doublets, walk, select,
                                                                  // scan, fit, keep, vertices
     for (uint32_t lv = 1; lv <= P->dp.n_levels; ++lv)
-        n += (P->dp.level_dense[lv] ? 1 : 0) + (P->dp.level_sparse[lv] ? 1 : 0);
+        n += (P->dp.level_dense[lv] ? 2 : 0) + (P->dp.level_sparse[lv] ? 1 : 0);
     return n;
 }
 
