@@ -61,7 +61,7 @@ __device__ uint32_t block_exclusive_scan(uint32_t *s, uint32_t n, uint32_t *warp
     return total;
 }
 
-__global__ void __launch_bounds__(512) k_sort(DevBatch b, DevParams p)
+__global__ void __launch_bounds__(1024) k_sort(DevBatch b, DevParams p)
 {
     extern __shared__ uint32_t s_cnt[];
     __shared__ uint32_t s_warp[32];
@@ -116,7 +116,7 @@ void launch_sort(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms)
     const uint32_t cap = (uint32_t)sms * p.grid_per_sm[0];
     const uint32_t grid = b.E < cap ? b.E : cap;
     if (grid == 0) return;
-    k_sort<<<grid, 512, p.n_keys * sizeof(uint32_t), s>>>(b, p);
+    k_sort<<<grid, 1024, p.n_keys * sizeof(uint32_t), s>>>(b, p);
 }
 
 // Per-event, per-layer hit counts (used once to size a plan's per-event capacities).
