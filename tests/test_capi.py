@@ -99,6 +99,20 @@ def test_params_validation(lib):
         q = pxr.params_from(synth.params_barrel_quadruplets())
         q.grid_per_sm[k] = v
         assert lib.pxr_params_check(C.byref(q)) == pxr.EINVAL
+    # the optional steps after the fit
+    for kw in (dict(pt_min=-1.0), dict(pt_min=float("nan")), dict(chi2_max=-0.5),
+               dict(chi2_max=float("inf")), dict(vertexing=True, vtx_min_tracks=1),
+               dict(vertexing=True, vtx_gap=0.0), dict(vertexing=True, vtx_gap=float("nan"))):
+        q = pxr.params_from(synth.params_barrel_quadruplets(), **kw)
+        assert lib.pxr_params_check(C.byref(q)) == pxr.EINVAL, kw
+    for field, val in (("clean_shared", 2), ("fit_cov", 2), ("vertexing", 3), ("fit_mode", 4)):
+        q = pxr.params_from(synth.params_barrel_quadruplets())
+        setattr(q, field, val)
+        assert lib.pxr_params_check(C.byref(q)) == pxr.EINVAL, field
+    for kw in (dict(pt_min=0.9, chi2_max=10.0, clean_shared=True), dict(fit_cov=True),
+               dict(vertexing=True), dict(fit_mode=pxr.FIT_RIEMANN)):
+        q = pxr.params_from(synth.params_barrel_quadruplets(), **kw)
+        assert lib.pxr_params_check(C.byref(q)) == pxr.OK, kw
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
