@@ -768,7 +768,7 @@ void launch_fit(const DevBatch &b, const DevParams &p, uint32_t total, cudaStrea
 void launch_keep(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
 {
     uint64_t blocks = ((uint64_t)total + 255) / 256;
-    const uint64_t cap = (uint64_t)sms * 8;
+    const uint64_t cap = (uint64_t)sms * p.grid_per_sm[5];     // the fit stage's cap
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
     k_keep<<<(unsigned)blocks, 256, 0, s>>>(b);
