@@ -6,10 +6,12 @@ the whole hot path (sort, doublets, CA connect, ntuplets, selection, fit) over t
 from a captured CUDA graph with the inputs already in device memory.  Between timed steps the L2
 is flushed by writing a 512 MB buffer (outside the timed events).
 
-Also reported: per-stage device times and the doublet kernel's fraction of the measured HBM
-bandwidth; the plain path (one event per launch sequence); end to end through the serving API
-with host buffers (H2D/D2H inside); p50/p99 latency of Poisson-arriving events; the FP64 oracle on
-the host cores (bounded sample).  `--impl reference` times the oracle alone.
+Also reported: per-stage device times; the fraction of the measured HBM bandwidth of the
+dominant stage (CA connect, `roofline`) and of the doublet kernel (`roofline_k4`); the plain path
+(one event per launch sequence); end to end through the serving API with host buffers (H2D/D2H
+inside); p50/p99 latency of Poisson-arriving events; the FP64 oracle on the host cores (bounded
+sample).  `--impl reference` times the oracle alone; `--study` measures every workload
+configuration and the optional steps (selection, covariance, Riemann fit, vertices).
 """
 from __future__ import annotations
 
