@@ -190,7 +190,9 @@ typedef struct pxr_config {
                                    pxr_fetch_debug (costs memory until the fetch) */
 } pxr_config;
 
-/* Caller-owned arrays receiving the tracks of one event. */
+/* Caller-owned arrays receiving the tracks of one event.  Any array pointer may be NULL: that
+ * field is not copied.  The vertex arrays are indexed by vertex (n_vertices of them), the others
+ * by track. */
 typedef struct pxr_tracks {
     uint32_t capacity;          /* in: slots in every array below */
     uint32_t n_tracks;          /* out: tracks of the event (may exceed capacity: PXR_ETRUNC) */
