@@ -233,14 +233,17 @@ def ca_traffic(cells, n_phi_bins):
         return None
 
 
-def doublet_algorithmic_bytes(layer_counts, pairs, n_cells):
-    """16 B per hit read per layer pair it takes part in, 8 B per inner hit and pair for the two
-    bucket offsets of its window, 8 B per cell written."""
+def doublet_algorithmic_bytes(layer_counts, pairs, n_cells, cell_bytes=4):
+    """Bytes the doublet stage must move: 16 B per hit read per layer pair it takes part in, 8 B
+    per inner hit and pair for the two bucket offsets of its window, the 16 B record of each
+    (inner hit, pair) that delimits its cells, and cell_bytes per cell written.  The cells are
+    stored grouped by inner hit (the record gives the group), so a cell is its outer hit, 4 B;
+    cell_bytes=8 gives the bytes of the (inner, outer) pair form instead."""
     b = 0
     for lc in layer_counts:
         for a, o in pairs:
-            b += 16 * (lc[a] + lc[o]) + 8 * lc[a]
-    return b + 8 * n_cells
+            b += 16 * (lc[a] + lc[o]) + 8 * lc[a] + 16 * lc[a]
+    return b + cell_bytes * n_cells
 
 
 def run_pxr(args, rank, world, local):
@@ -337,6 +340,7 @@ def run_pxr(args, rank, world, local):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     alg = doublet_algorithmic_bytes(layer_counts, P.pairs, cells)
+    alg_pairs = doublet_algorithmic_bytes(layer_counts, P.pairs, cells, cell_bytes=8)
     k4_ms = stage[1]
     achieved = alg / (k4_ms / 1e3) / 1e9
     # the dominant stage: CA connect (dense and sparse passes), 8 B per cell read + 8 B per edge
@@ -370,7 +374,12 @@ def run_pxr(args, rank, world, local):
                             "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                             "peak_source": peak_src,
                             "traffic": doublet_traffic(cells, params.n_phi_bins),
-                            "algorithmic_bytes": alg, "cells": cells},
+                            "traffic_note": "scaled by cells from a capture of a smaller "
+                                            "batch (an estimate; null when the kernel changed)",
+                            "algorithmic_bytes": alg, "cells": cells,
+                            "pair_form": {"algorithmic_bytes": alg_pairs,
+                                          "frac": alg_pairs / (k4_ms / 1e3) / 1e9 / hbm_peak,
+                                          "note": "8 B per cell, the (inner, outer) pair form"}},
             "clocks": clk, "tracks_per_step": n_tracks * world}
 
     if not args.no_extras and rank == 0:

@@ -220,26 +220,34 @@ typedef struct pxr_tracks {
 typedef struct pxr_ctx pxr_ctx;
 typedef struct pxr_plan pxr_plan;
 
-/* Library version string (static storage). */
+/* Library version string (static storage).
+ * Source: none (library plumbing; the paper defines no interface). */
 const char *pxr_version(void);
 
-/* Message of the last error on this thread (static thread-local storage). */
+/* Message of the last error on this thread (static thread-local storage).
+ * Source: none (library plumbing; the paper defines no interface). */
 const char *pxr_last_error(void);
 
 /* Fill *p with a preset (PXR_PRESET_*), cut mode FP64 and fit mode FP64; no selection, no
- * covariance, no vertexing (vtx_min_tracks 2 and vtx_gap 0.05 cm for when it is switched on). */
+ * covariance, no vertexing (vtx_min_tracks 2 and vtx_gap 0.05 cm for when it is switched on).
+ * Source: the paper names the Tracks module's steps (§2) without values; the presets are this
+ * library's synthetic geometries (barrel layers, Phase-1-like disks). */
 int pxr_params_init(pxr_params *p, int preset);
 
-/* Validate *p without touching any device: PXR_OK or PXR_EINVAL with a message. */
+/* Validate *p without touching any device: PXR_OK or PXR_EINVAL with a message.
+ * Source: none (library plumbing). */
 int pxr_params_check(const pxr_params *p);
 
 /* Create a context on cfg->device.  Allocates the arena (unless cfg->arena is given), pinned host
- * staging memory and the scheduler thread.  *out receives the context. */
+ * staging memory and the scheduler thread.  *out receives the context.
+ * Source: the paper's memory pool (§5, Table 2: allocation through a caching pool) is the
+ * context for the one arena allocated here. */
 int pxr_create(const pxr_config *cfg, pxr_ctx **out);
 
 /* Stop the scheduler, wait for work in flight, release everything the context allocated.
  * Unfetched results are discarded; plans of the context that are still alive are destroyed
- * (their handles become invalid). */
+ * (their handles become invalid).
+ * Source: none (library plumbing). */
 void pxr_destroy(pxr_ctx *ctx);
 
 /*
@@ -248,18 +256,22 @@ void pxr_destroy(pxr_ctx *ctx);
  * thread (continuous batching: a batch is launched as soon as a device slot is free).
  * *ticket identifies the event.  Errors: PXR_EINVAL (bad params or input), PXR_EAGAIN (budget
  * full now), PXR_ENOMEM (the event alone exceeds the budget).
+ * Source: the paper defines no serving interface; its throughput comes from events processed
+ * concurrently (§5, Table 2), which this entry point provides by continuous batching.
  */
 int pxr_submit_event(pxr_ctx *ctx, const float *x, const float *y, const float *z,
                      const uint16_t *layer, uint32_t n_hits, const pxr_params *params,
                      uint64_t *ticket);
 
 /* Return up to cap finished tickets in done[] (host array), *n_done = count.  Waits up to
- * timeout_us microseconds (0 = do not wait, < 0 = until at least one is done or none pending). */
+ * timeout_us microseconds (0 = do not wait, < 0 = until at least one is done or none pending).
+ * Source: the paper defines no serving interface (§5, Table 2 for concurrent events). */
 int pxr_poll(pxr_ctx *ctx, uint64_t *done, uint32_t cap, uint32_t *n_done, int timeout_us);
 
 /* Copy the tracks of a finished event into caller arrays (canonical order: lexicographic by hit
  * tuple).  On success the ticket is released.  PXR_ETRUNC: out->capacity too small, n_tracks set,
- * ticket kept.  PXR_EBUSY: not finished.  The event's own status (overflow) is in out->status. */
+ * ticket kept.  PXR_EBUSY: not finished.  The event's own status (overflow) is in out->status.
+ * Source: §2, the Tracks module's product (tracks with fitted parameters from hit n-tuplets). */
 int pxr_fetch_tracks(pxr_ctx *ctx, uint64_t ticket, pxr_tracks *out);
 
 /* Debug content of a finished event kept with cfg->keep_debug (before pxr_fetch_tracks):
@@ -268,7 +280,8 @@ int pxr_fetch_tracks(pxr_ctx *ctx, uint64_t ticket, pxr_tracks *out);
  *           lie on a root path (root cells and, transitively, their edges' targets: the edges
  *           of other cells cannot change a result and are not built);
  * what = 2: ntuplets before suffix removal as PXR_MAX_HITS words each (0xFFFFFFFF padded).
- * Writes at most cap words to buf (host), *n = number of items. */
+ * Writes at most cap words to buf (host), *n = number of items.
+ * Source: §2, the Tracks module's intermediate products (doublets, CA graph, n-tuplets). */
 int pxr_fetch_debug(pxr_ctx *ctx, uint64_t ticket, int what, uint32_t *buf, uint32_t cap,
                     uint32_t *n);
 
@@ -281,44 +294,54 @@ int pxr_fetch_debug(pxr_ctx *ctx, uint64_t ticket, int what, uint32_t *buf, uint
  * use_graph != 0 the launch sequence is captured once into a CUDA graph and replayed.
  * The caller keeps the input arrays alive and unchanged in shape for the plan's lifetime; their
  * contents may change between runs.
+ * Source: many events per launch, the batched form of the concurrency of §5 (Table 2).
  */
 int pxr_plan_create(pxr_ctx *ctx, uint32_t n_events, const uint32_t *hit_offsets,
                     const float *x, const float *y, const float *z, const uint16_t *layer,
                     const pxr_params *params, int use_graph, pxr_plan **out);
 
 /* Run the whole hot path for the plan's batch on stream (cudaStream_t; NULL = the context's).
- * Asynchronous: returns after enqueueing. */
+ * Asynchronous: returns after enqueueing.
+ * Source: §2, the Tracks module (doublets, cellular automaton, n-tuplets, broken-line fit). */
 int pxr_plan_run(pxr_plan *plan, void *stream);
 
 /* Wait for the plan's last run and copy event e's tracks to the caller (same layout and order
- * as pxr_fetch_tracks). */
+ * as pxr_fetch_tracks).
+ * Source: §2, the Tracks module's product. */
 int pxr_plan_tracks(pxr_plan *plan, uint32_t e, pxr_tracks *out);
 
-/* Debug content of event e after the last run (see pxr_fetch_debug for `what`). */
+/* Debug content of event e after the last run (see pxr_fetch_debug for `what`).
+ * Source: §2, the Tracks module's intermediate products. */
 int pxr_plan_debug(pxr_plan *plan, uint32_t e, int what, uint32_t *buf, uint32_t cap,
                    uint32_t *n);
 
-/* Number of kernel launches one pxr_plan_run performs (for launch accounting). */
+/* Number of kernel launches one pxr_plan_run performs (for launch accounting).
+ * Source: none (measurement plumbing). */
 int pxr_plan_launches(const pxr_plan *plan);
 
 /* Per-event counters of the last run, copied to the host array out[5 * n_events]: out[k*E + e]
  * for k = 0 cells, 1 CA edges, 2 ntuplets before selection, 3 flags (1 cells, 2 edges,
- * 4 ntuplets overflowed; 8 bad layer id), 4 tracks. */
+ * 4 ntuplets overflowed; 8 bad layer id), 4 tracks.
+ * Source: none (measurement plumbing). */
 int pxr_plan_counts(pxr_plan *plan, uint32_t *out);
 
 /* Device time in milliseconds of each stage of the last run, from CUDA events recorded between
  * the launches (event-record nodes when the plan replays a graph).  Stage order: hit sort,
- * doublets, CA connect, ntuplets + selection + output scan, fit; n = entries written (<= cap). */
+ * doublets, CA connect, ntuplets + selection + output scan, fit; n = entries written (<= cap).
+ * Source: none (measurement plumbing; the paper gives no per-kernel times, §5). */
 int pxr_plan_stage_ms(pxr_plan *plan, float *ms, int cap, int *n);
 
 /* Wait for the plan's last run and release it.  Call before pxr_destroy of its context (which
- * otherwise destroys it). */
+ * otherwise destroys it).
+ * Source: none (library plumbing). */
 void pxr_plan_destroy(pxr_plan *plan);
 
 /*
  * Fit-only path over device-resident ntuplets (the precision study): m ntuplets of nh[t] hits
  * (3..PXR_MAX_HITS), hit h of ntuplet t at x[t*stride + h] (device float arrays), layer ids
  * likewise.  Outputs are device arrays of m elements.  fit_mode selects the arithmetic.
+ * Source: §2, the Tracks module's fit of hit n-tuplets (the broken line, Blobel 2006, is this
+ * library's reading; the paper names no fit).
  */
 int pxr_fit_batch(pxr_ctx *ctx, uint32_t m, const uint8_t *nh, const float *x, const float *y,
                   const float *z, const uint16_t *layer, uint32_t stride,
@@ -339,14 +362,18 @@ int pxr_fit_batch(pxr_ctx *ctx, uint32_t m, const uint8_t *nh, const float *x, c
  * Inputs (device): x, y, z, layer of n_hits hits (n_hits <= 65536).  Outputs (device):
  * cells_inner[cap], cells_outer[cap] receive the cells as caller hit indices (cap <= 1048576),
  * *n_cells the number of cells found (may exceed cap: then only cap are written), *flags
- * (optional, may be NULL) the overflow flag word (1 = more cells than cap).  stream: cudaStream_t
- * or NULL.  Asynchronous: results are valid once the stream reaches them.
+ * (optional, may be NULL) the event's flag word: bit 1 = more cells than cap (the first cap
+ * cells found are written, in no particular order), bit 8 = at least one hit has a layer id
+ * >= params->n_layers (such hits are left out of every cell; the other hits' cells are
+ * unaffected); other bits are 0.  stream: cudaStream_t or NULL.  Asynchronous: results are valid
+ * once the stream reaches them.
  * The first call on each device resolves the scratch array's device address and sets kernel
  * attributes (with that device current); make that first call before any stream capture.
  * Every call shares the scratch array and it keeps the last call's contents: calls whose work
  * overlaps on the GPU race on it and must be ordered by the caller (one stream, or events).
  * Errors: PXR_EINVAL for sizes beyond the limits or bad parameters (nothing is launched),
- * PXR_ECUDA for a failed launch.
+ * PXR_ECUDA when a CUDA error was already pending before the call (nothing is launched; the
+ * error is left pending) or a launch failed (the message names the launch).
  */
 int pxr_doublets_noalloc(const float *x, const float *y, const float *z, const uint16_t *layer,
                          uint32_t n_hits, const pxr_params *params, uint32_t *cells_inner,

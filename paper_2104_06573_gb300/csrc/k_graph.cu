@@ -263,7 +263,6 @@ __global__ void __launch_bounds__(256) k_doublets(DevBatch b, DevParams p, uint3
             for (uint32_t c = lane; c < wk; c += 32) {
                 const uint32_t o = c < a1 ? a0 + c : a2 + (c - a1);
                 const bool pass = doublet_test<F64>(b, p, gk, hk, o, __ldg(&b.hs[o]));
-                b.cell_in[fk + c] = gk;
                 b.cell_out[fk + c] = pass ? o : kNone;
                 np += pass;
             }
@@ -402,7 +401,8 @@ __device__ __forceinline__ float funord(int i) { return __int_as_float(i >= 0 ? 
 // reads it; a later level writes the count if C gets out-edges) and, when C is `listed` (a
 // non-root cell whose outer hit starts further pairs), appends it to the event's frontier list,
 // the input of the sparse pass of C's outer layer.
-__device__ __forceinline__ void mark_reached(const DevBatch &b, uint32_t e, uint32_t C, bool listed)
+__device__ __forceinline__ void mark_reached(const DevBatch &b, uint32_t e, uint32_t C,
+                                             uint32_t c_in, bool listed)
 {
     const uint32_t bit = 1u << (C & 31u);
     if (!listed) {
@@ -416,8 +416,12 @@ __device__ __forceinline__ void mark_reached(const DevBatch &b, uint32_t e, uint
     b.nbr_n[C] = 0u;
     const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
     const uint32_t x = atomicAdd(&b.cnt[C_FRONT * b.E + e], 1u);
-    if (x < cap) b.front_list[b.edge_off[e] + x] = C;
-    else atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+    if (x < cap) {
+        b.front_list[b.edge_off[e] + x] = C;
+        b.front_in[b.edge_off[e] + x] = c_in;
+    } else {
+        atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+    }
 }
 
 // One warp per junction hit j.  For each out-layer slot, j's out-cells (j, k) are staged in
@@ -668,12 +672,20 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                     const bool fresh = ok && !(was & bit);
                     if (fresh) b.nbr_n[Bf] = 0u;
                     if (ok && front) {
-                        if (fbase < cap) b.front_list[b.edge_off[e] + fbase] = fresh ? Bf : kNone;
-                        else atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+                        if (fbase < cap) {
+                            b.front_list[b.edge_off[e] + fbase] = fresh ? Bf : kNone;
+                            b.front_in[b.edge_off[e] + fbase] = j;
+                        } else {
+                            atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+                        }
                     }
                     if (first_root) {
-                        if (rbase < cap) b.root_list[b.edge_off[e] + rbase] = A;
-                        else atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+                        if (rbase < cap) {
+                            b.root_list[b.edge_off[e] + rbase] = A;
+                            b.root_in[b.edge_off[e] + rbase] = i;
+                        } else {
+                            atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+                        }
                     }
                     if (ok) {
                         if (nw < need) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
@@ -696,7 +708,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                             }
                             if (triplet_test<F64>(b, p, i, j, B, hi.x, hi.y, hj, hk, a)) {
                                 b.nbr[first + wr++] = B;
-                                mark_reached(b, e, B, front);
+                                mark_reached(b, e, B, j, front);
                             }
                         }
                         b.nbr_first[A] = first;
@@ -797,10 +809,10 @@ __global__ void __launch_bounds__(256, 4) k_connect_front(DevBatch b, DevParams 
         bool valid = x - x0 < nf;
         if (valid) {
             B = b.front_list[x];
+            j = b.front_in[x];
             valid = B != kNone;                                    // slot of a cell reached twice
         }
         if (valid) {
-            j = b.cell_in[B];
             k = b.cell_out[B];
             hj = b.hs[j];
             hk = b.hs[k];
@@ -850,7 +862,7 @@ __global__ void __launch_bounds__(256, 4) k_connect_front(DevBatch b, DevParams 
                         if (pass) {
                             const uint32_t idx = start + cnt + __popc(pm & lt);
                             if (idx < (uint32_t)kFrontBuf) buf[idx] = C;
-                            mark_reached(b, e, C, front);
+                            mark_reached(b, e, C, kq, front);
                         }
                         cnt += __popc(pm);
                     }
@@ -944,7 +956,7 @@ void launch_connect_front(const DevBatch &b, const DevParams &p, uint32_t total,
 // Depth-first walk from one root cell A; emits every path that has max_hits hits or ends at a
 // cell without out-edges, if it has at least min_hits hits.
 __device__ __forceinline__ void walk_from(const DevBatch &b, const DevParams &p, uint32_t e,
-                                          uint32_t A)
+                                          uint32_t A, uint32_t a_in)
 {
     uint32_t cells[kMaxHits - 1];
     uint32_t next[kMaxHits - 1];
@@ -962,7 +974,7 @@ __device__ __forceinline__ void walk_from(const DevBatch &b, const DevParams &p,
                 if (slot < tcap) {
                     const uint32_t t = b.tup_off[e] + slot;
                     uint32_t *th = b.tup_hits + (size_t)t * kMaxHits;
-                    th[0] = b.cell_in[cells[0]];
+                    th[0] = a_in;
                     for (int q = 0; q <= d; ++q) th[q + 1] = b.cell_out[cells[q]];
                     for (int q = d + 2; q < kMaxHits; ++q) th[q] = kNone;
                     b.tup_n[t] = (uint8_t)nh;
@@ -1007,7 +1019,7 @@ __global__ void __launch_bounds__(256) k_ntuplets(DevBatch b, DevParams p)
             const uint4 its = s ? b.item[(size_t)g * kMaxOut + s] : it0;
             const uint32_t f = its.x, n = its.y;
             for (uint32_t c = lane; c < n; c += 32)
-                if (b.cell_out[f + c] != kNone) walk_from(b, p, e, f + c);
+                if (b.cell_out[f + c] != kNone) walk_from(b, p, e, f + c, g);
         }
     }
 }
@@ -1022,7 +1034,7 @@ __global__ void __launch_bounds__(256) k_walk_roots(DevBatch b, DevParams p, uin
         const uint32_t e = b.edge_chunk[ch];
         const uint32_t x0 = b.edge_off[e];
         const uint32_t n = min(b.cnt[C_ROOTS * b.E + e], b.edge_off[e + 1] - x0);
-        if (x - x0 < n) walk_from(b, p, e, b.root_list[x]);
+        if (x - x0 < n) walk_from(b, p, e, b.root_list[x], b.root_in[x]);
     }
 }
 

@@ -13,6 +13,7 @@
 // whose work overlaps on the GPU (different streams or threads without ordering) race on it.
 #include <cstring>
 #include <mutex>
+#include <string>
 
 #include "../../include/pxr.h"
 #include "pxr_dev.cuh"
@@ -84,6 +85,7 @@ __global__ void k_na_count(uint32_t *n_cells, uint32_t *flags)
 // Parameter derivation and error reporting shared with the other entry points.
 int dev_params(const pxr_params *p, DevParams *d);
 int set_error(int code, const char *msg);
+inline int set_error(int code, const std::string &msg) { return set_error(code, msg.c_str()); }
 
 }  // namespace pxr
 
@@ -153,12 +155,26 @@ extern "C" int pxr_doublets_noalloc(const float *x, const float *y, const float 
     b.hit_chunk = reinterpret_cast<const uint32_t *>(base + kNaHitChunk);
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // An error left pending by earlier work of the process is reported as such (and left in
+    // place for its owner), not blamed on the launches below.
+    cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess)
+        return set_error(PXR_ECUDA, std::string("CUDA error pending before the call: ") +
+                                        cudaGetErrorString(pending));
+    // Each launch is checked right after it is issued, so that the message names it.
+    auto check = [](const char *what) {
+        const cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) return PXR_OK;
+        return set_error(PXR_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    };
     k_na_init<<<1, 32, 0, s>>>(n_hits, cap);
+    if ((rc = check("launch of the scratch initialisation")) != PXR_OK) return rc;
     launch_sort(b, dp, s, sms);
+    if ((rc = check("launch of the hit sort")) != PXR_OK) return rc;
     launch_doublets_compact(b, dp, s, sms);
+    if ((rc = check("launch of the doublet kernel")) != PXR_OK) return rc;
     k_na_to_caller<<<sms * 4, 256, 0, s>>>(cells_inner, cells_outer, n_cells, cap);
+    if ((rc = check("launch of the index conversion")) != PXR_OK) return rc;
     k_na_count<<<1, 32, 0, s>>>(n_cells, flags);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return set_error(PXR_ECUDA, cudaGetErrorString(e));
-    return PXR_OK;
+    return check("launch of the count copy");
 }

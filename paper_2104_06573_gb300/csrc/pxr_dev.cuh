@@ -100,19 +100,24 @@ struct DevBatch {
     // cell_out = kNone where the doublet cut failed.  item[(i, slot)] = (first entry, entries,
     // r0, d2): the cell (i, o) sits at first + rank, rank = o - r0 for o >= r0 (window run 1)
     // and o + d2 otherwise (run 2; unsigned arithmetic, d2 = run-1 length - run-2 start).  The
-    // allocation-free entry point writes passing pairs only (z, w unused).
+    // inner hit of an entry is implied by the item whose run holds it (the plan path stores no
+    // per-entry inner hit: the CA lists carry it where a reader needs it).  The allocation-free
+    // entry point writes passing pairs only, with their inner hits (item z, w unused).
     uint4 *item;                        // [N * kMaxOut]
-    uint32_t *cell_in, *cell_out;       // [entries] sorted hit positions
+    uint32_t *cell_in;                  // [entries] inner hit (allocation-free entry point only)
+    uint32_t *cell_out;                 // [entries] outer hit, sorted position
     // CA graph: out-edges of each cell
     uint32_t *nbr_first;                // [cells]
     uint32_t *nbr_n;                    // [cells]
     uint32_t *nbr;                      // [edges] target cells
     uint32_t *mindepth;                 // [cells] fewest hits before the cell on a root path
     uint32_t *root_list;                // [edges] per event: root cells that have out-edges
+    uint32_t *root_in;                  // [edges] their inner hits
     uint32_t *live;                     // [entries / 32] bit per cell: has an in-edge
     uint32_t *front_list;               // [edges] per event: non-root cells with in-edges whose
                                         //   outer hit starts further pairs (the sparse CA input;
                                         //   kNone: a slot reserved for a cell already listed)
+    uint32_t *front_in;                 // [edges] the inner hits of the frontier cells
     uint32_t *jbase;                    // [E + 1] junction prefix of a dense CA level
     uint32_t *front_snap;               // [E] frontier lengths when a sparse pass starts (the pass
                                         //   appends for later levels while it reads)

@@ -261,9 +261,9 @@ struct PlanOffsets {
     size_t x, y, z, layer, hit_off, cell_off, edge_off, tup_off, cell_chunk, edge_chunk, tup_chunk,
         hit_chunk,
         head_end;
-    size_t cnt, bkt, hs, r64, hmeta, hphi, item, cell_in, cell_out,
+    size_t cnt, bkt, hs, r64, hmeta, hphi, item, cell_out,
         nbr_first,
-        nbr_n, nbr, mindepth, root_list, live, front_list, front_snap, jbase, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, out_evt, o_nh,
+        nbr_n, nbr, mindepth, root_list, root_in, live, front_list, front_in, front_snap, jbase, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, out_evt, o_nh,
         o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status, o_ql, best, o_cov, o_vtx,
         v_z, v_err, v_pt2, v_n;
     size_t total;
@@ -296,15 +296,16 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.hphi = L.add(4 * N);
 
     o.item = L.add(16 * N * kMaxOut);
-    o.cell_in = L.add(4 * C);
     o.cell_out = L.add(4 * C);
     o.nbr_first = L.add(4 * C);
     o.nbr_n = L.add(4 * C);
     o.nbr = L.add(4 * G);
     o.mindepth = L.add(4 * C);
     o.root_list = L.add(4 * G);
+    o.root_in = L.add(4 * G);
     o.live = L.add(4 * ((C + 31) / 32));
     o.front_list = L.add(4 * G);
+    o.front_in = L.add(4 * G);
     o.front_snap = L.add(4 * (size_t)E);
     o.jbase = L.add(4 * ((size_t)E + 1));
     o.tup_hits = L.add(4 * T * kMaxHits);
@@ -493,15 +494,17 @@ static void plan_bind(pxr_plan *P)
     b.hit_chunk = (const uint32_t *)(r + o.hit_chunk);
 
     b.item = (uint4 *)(r + o.item);
-    b.cell_in = (uint32_t *)(r + o.cell_in);
+    b.cell_in = nullptr;
     b.cell_out = (uint32_t *)(r + o.cell_out);
     b.nbr_first = (uint32_t *)(r + o.nbr_first);
     b.nbr_n = (uint32_t *)(r + o.nbr_n);
     b.nbr = (uint32_t *)(r + o.nbr);
     b.mindepth = (uint32_t *)(r + o.mindepth);
     b.root_list = (uint32_t *)(r + o.root_list);
+    b.root_in = (uint32_t *)(r + o.root_in);
     b.live = (uint32_t *)(r + o.live);
     b.front_list = (uint32_t *)(r + o.front_list);
+    b.front_in = (uint32_t *)(r + o.front_in);
     b.front_snap = (uint32_t *)(r + o.front_snap);
     b.jbase = (uint32_t *)(r + o.jbase);
     b.tup_hits = (uint32_t *)(r + o.tup_hits);
@@ -1018,11 +1021,22 @@ static int region_debug(pxr_plan *P, uint32_t e, int what, uint32_t *buf, uint32
     const uint32_t nc = std::min(cnt[C_SLOTS], P->cell_off[e + 1] - c0);   // slots, holes included
     std::vector<uint32_t> out;
     if (what == 0 || what == 1) {
-        std::vector<uint32_t> ci, co;
-        if ((rc = d2h(ci, b.cell_in + c0, nc)) || (rc = d2h(co, b.cell_out + c0, nc))) return rc;
+        std::vector<uint32_t> co, ci(nc, kNone);
+        if ((rc = d2h(co, b.cell_out + c0, nc))) return rc;
+        // the inner hit of each entry: the item (inner hit, pair slot) whose entry run holds it
+        std::vector<uint4> items;
+        if ((rc = d2h(items, b.item + (size_t)h0 * kMaxOut, (size_t)nh * kMaxOut))) return rc;
+        for (uint32_t h = 0; h < nh; ++h) {
+            const uint32_t L = meta[h] >> kLocalBits;
+            if (L >= P->dp.n_layers) continue;
+            for (uint32_t sl = 0; sl < P->dp.n_out[L]; ++sl) {
+                const uint4 it = items[(size_t)h * kMaxOut + sl];
+                for (uint32_t c = it.x - c0; c < it.x - c0 + it.y && c < nc; ++c) ci[c] = h0 + h;
+            }
+        }
         if (what == 0) {
             for (uint32_t c = 0; c < nc; ++c) {
-                if (co[c] == kNone) continue;                   // candidate that failed the cut
+                if (co[c] == kNone || ci[c] == kNone) continue;  // candidate that failed the cut
                 out.push_back(loc(ci[c]));
                 out.push_back(loc(co[c]));
             }
@@ -1039,7 +1053,8 @@ static int region_debug(pxr_plan *P, uint32_t e, int what, uint32_t *buf, uint32
             const uint32_t nr = std::min(cnt[C_ROOTS], P->edge_off[e + 1] - g0);
             if ((rc = d2h(roots, b.root_list + g0, nr))) return rc;
             std::vector<uint8_t> valid(nc, 0);
-            for (uint32_t c = 0; c < nc; ++c) valid[c] = (live[c / 32] >> (c % 32)) & 1u;
+            for (uint32_t c = 0; c < nc; ++c)
+                valid[c] = ci[c] != kNone && ((live[c / 32] >> (c % 32)) & 1u);
             for (uint32_t A : roots) valid[A - c0] = 1;
             for (uint32_t c = 0; c < nc; ++c)
                 for (uint32_t k = 0; valid[c] && k < nn[c]; ++k) {

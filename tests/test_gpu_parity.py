@@ -377,16 +377,29 @@ def test_overflow_is_flagged_not_written(ctx):
     assert {tuple(c) for c in got[1]["cells"].tolist()} <= {tuple(c) for c in full["cells"].tolist()}
 
 
-@pytest.mark.parametrize("cut", [pxr.CUT_FP64, pxr.CUT_FP32])
-def test_full_size_batch_sampled(ctx, orc, cut):
+# (cut mode, fit mode, phi bins, CTAs per SM per stage): the built-in launch shapes in both cut
+# modes, and the benchmark's timed configuration (FP32 cuts, the benchmark's fit mode, the bin
+# count and per-stage grid caps the tuner picks on this batch)
+FULL_SIZE_CONFIGS = [
+    (pxr.CUT_FP64, pxr.FIT_FP64, 0, [0] * 6),
+    (pxr.CUT_FP32, pxr.FIT_FP64, 0, [0] * 6),
+    (pxr.CUT_FP32, pxr.FIT_MIXED, 1024, [4, 32, 32, 32, 4, 0]),
+]
+
+
+@pytest.mark.parametrize("cut,fit,bins,grid", FULL_SIZE_CONFIGS)
+def test_full_size_batch_sampled(ctx, orc, cut, fit, bins, grid):
     """The 256-event batch (200-6000 tracks per event) in one graph launch, as timed by the
     benchmark.  Three sampled events (smallest, a middle one, the largest) are compared with the
-    oracle in full; every event passes the structural invariants."""
+    oracle in full (sets bit-exact, fits within the tolerances); every event passes the
+    structural invariants."""
+    from paper_2104_06573_gb300 import autotune
     P = synth.params_barrel_quadruplets()
     counts = synth.batch_track_counts(256)
     evs = [ev_tuple(synth.make_event(e, counts[e])) for e in range(256)]
     off, x, y, z, layer = to_dev(evs)
-    plan = pxr.Plan(ctx, off, x, y, z, layer, pxr.params_from(P, cut_mode=cut), use_graph=True)
+    params = autotune._with(pxr.params_from(P, cut_mode=cut, fit_mode=fit), bins, grid)
+    plan = pxr.Plan(ctx, off, x, y, z, layer, params, use_graph=True)
     plan.pxr_plan_run()
     order = np.argsort(counts)
     sample = [int(order[0]), int(order[128]), int(order[-1])]

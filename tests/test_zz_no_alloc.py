@@ -8,6 +8,8 @@ the cells the existing plan path reports for the same event (integer sets: bit-e
 call checks that nothing from the first call leaks through the shared array.  Size limits are
 rejected on the host before any launch.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -34,7 +36,8 @@ def _plan_cells(ctx, ev, params):
     return {tuple(c) for c in cells.tolist()}, len(cells)
 
 
-def _noalloc_cells(ev, params, cap):
+def _noalloc_call(ev, params, cap):
+    """One call; returns (written cells as a list of pairs, cell count, flag word)."""
     dev = torch.device("cuda:0")
     x, y, z, layer = _dev(ev)
     inner = torch.full((cap,), -1, dtype=torch.int32, device=dev)
@@ -44,10 +47,16 @@ def _noalloc_cells(ev, params, cap):
     pxr.pxr_doublets_noalloc(x, y, z, layer, ev.n, params, inner, outer, cap, n, flags)
     torch.cuda.synchronize()
     k = int(n.item())
-    assert int(flags.item()) == 0
-    got = np.stack([inner[:k].cpu().numpy().view(np.uint32),
-                    outer[:k].cpu().numpy().view(np.uint32)], 1)
-    return {tuple(c) for c in got.tolist()}, k
+    w = min(k, cap)
+    got = np.stack([inner[:w].cpu().numpy().view(np.uint32),
+                    outer[:w].cpu().numpy().view(np.uint32)], 1)
+    return [tuple(c) for c in got.tolist()], k, int(flags.item())
+
+
+def _noalloc_cells(ev, params, cap):
+    cells, k, flags = _noalloc_call(ev, params, cap)
+    assert flags == 0
+    return set(cells), k
 
 
 @pytest.fixture(scope="module")
@@ -82,3 +91,45 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
         pxr.pxr_doublets_noalloc(dummy, dummy, dummy, dummy, 10, P, dummy, dummy, (1 << 20) + 1,
                                  dummy)
     assert e2.value.code == pxr.EINVAL and "1048576" in str(e2.value)
+
+
+def test_noalloc_overflow_then_full_call():
+    """cap below the event's cell count: the full count is reported, flag bit 1 is set and the cap
+    written pairs are distinct cells of the event.  A following call with room for every cell
+    gives exactly the plan path's cells (nothing stale from the truncated call)."""
+    P = synth.params_barrel_quadruplets()
+    params = pxr.params_from(P, cut_mode=pxr.CUT_FP32)
+    ev = synth.event_barrel(11, 400)
+    c = pxr.Context(device=0, mem_budget_bytes=1 << 30)
+    try:
+        want, n_want = _plan_cells(c, ev, params)
+    finally:
+        c.close()
+    cap = n_want // 3
+    cells, k, flags = _noalloc_call(ev, params, cap)
+    assert k == n_want > cap > 0
+    assert flags & 1 and not flags & ~1
+    assert len(cells) == cap and len(set(cells)) == cap and set(cells) <= want
+    got, k2 = _noalloc_cells(ev, params, cap=1 << 20)
+    assert k2 == n_want and got == want
+
+
+def test_noalloc_bad_layer_id_flagged():
+    """A hit whose layer id is beyond the geometry is left out and flagged (bit 8); every other
+    cell is found exactly as the plan path finds it on the intact event."""
+    P = synth.params_barrel_quadruplets()
+    params = pxr.params_from(P, cut_mode=pxr.CUT_FP32)
+    ev = synth.event_barrel(12, 300)
+    c = pxr.Context(device=0, mem_budget_bytes=1 << 30)
+    try:
+        want, _ = _plan_cells(c, ev, params)
+    finally:
+        c.close()
+    bad = int(np.flatnonzero(ev.layer == 1)[0])        # a hit that takes part in cells
+    assert any(bad in cell for cell in want)
+    layer = ev.layer.copy()
+    layer[bad] = 200
+    ev_bad = dataclasses.replace(ev, layer=layer)
+    cells, k, flags = _noalloc_call(ev_bad, params, cap=1 << 20)
+    assert flags == 8
+    assert set(cells) == {cell for cell in want if bad not in cell} and k == len(cells)
