@@ -196,55 +196,83 @@ static int chol_solve(int m, const double *A, const double *b, double *x)
  *     beta_j = (x[j+1]-x[j])/ds_j - (x[j]-x[j-1])/ds_{j-1} + curv * (ds_{j-1}+ds_j)/2 * x[n]
  * with variance kvar[j].  The curvature term is written with a plus sign because an increase of
  * the curvature magnitude pulls the path towards the centre, i.e. the outward offset has second
- * derivative -x[n].  Minimises  sum w (meas - x)^2 + sum beta^2 / kvar  through the normal
- * equations.  Returns 0 on success and stores the minimum in *chi2.
+ * derivative -x[n].  The result is the minimiser of
+ *     chi2 = sum w (meas - x)^2 + sum beta^2 / kvar.
+ *
+ * The minimiser is computed in the parameters theta = (x[0], slope of the first segment,
+ * [x[n]], beta_1 .. beta_{n-2}), which describe the same paths one to one: the slope of segment
+ * m is slope_0 + sum_{j=1..m} (beta_j - curv (ds_{j-1}+ds_j)/2 x[n]), so
+ *     x[i] = x[0] + slope_0 (s_i - s_0) + sum_{1<=j<i} (beta_j - curv c_j x[n]) (s_i - s_j),
+ *     c_j = (s_{j+1} - s_{j-1}) / 2,
+ * and chi2 = |W^(1/2) (meas - J theta)|^2 + sum beta_j^2 / kvar_j.  Its normal matrix
+ * J^T W J + diag(0, .., 1/kvar_j) keeps the kink weights on the diagonal: with little material
+ * they reach 1e20 next to measurement weights of 1e6, and the normal equations written in the
+ * offsets x would mix the two in every entry, where their FP64 rounding leaves the straight-line
+ * part of the solution with errors of 1e-3; here they stay apart and the solve keeps FP64
+ * accuracy.  Dense Cholesky; x = J theta.  Ainv (optional) receives the inverse normal matrix in
+ * the offsets (x[0..n-1], x[n]): T N^-1 T^T with T the map from theta to them.
+ * Returns 0 on success and stores the minimum in *chi2.
  */
 static int bl_solve(int n, const double *s, const double *meas, const double *w,
                     const double *kvar, int curv, double *x, double *chi2, double *Ainv)
 {
-    int m = n + (curv ? 1 : 0);
-    double A[ORC_MAXM * ORC_MAXM];
-    double b[ORC_MAXM];
-    double g[ORC_MAXM];
+    const int g = curv ? 3 : 2;                 /* x[0], slope_0, [curvature correction] */
+    const int m = n + (curv ? 1 : 0);           /* = g + (n - 2) */
+    double J[ORC_MAXH][ORC_MAXM];               /* d x_i / d theta_k */
+    double N[ORC_MAXM * ORC_MAXM], b[ORC_MAXM], th[ORC_MAXM];
     if (n < 2 || n > ORC_MAXH) return -1;
-    memset(A, 0, sizeof(A));
-    memset(b, 0, sizeof(b));
+    memset(J, 0, sizeof(J));
     for (int i = 0; i < n; ++i) {
-        A[i * m + i] += w[i];
-        b[i] += w[i] * meas[i];
+        J[i][0] = 1.0;
+        J[i][1] = s[i] - s[0];
+        for (int j = 1; j < i && j + 1 < n; ++j) {
+            J[i][g + j - 1] = s[i] - s[j];
+            if (curv) J[i][2] -= 0.5 * (s[j + 1] - s[j - 1]) * (s[i] - s[j]);
+        }
     }
-    for (int j = 1; j + 1 < n; ++j) {
-        double ds0 = s[j] - s[j - 1];
-        double ds1 = s[j + 1] - s[j];
-        double wk = 1.0 / kvar[j];
-        memset(g, 0, sizeof(g));
-        g[j - 1] = 1.0 / ds0;
-        g[j] = -1.0 / ds0 - 1.0 / ds1;
-        g[j + 1] = 1.0 / ds1;
-        if (curv) g[n] = 0.5 * (ds0 + ds1);
-        for (int r = 0; r < m; ++r)
-            for (int c = 0; c < m; ++c) A[r * m + c] += wk * g[r] * g[c];
+    for (int r = 0; r < m; ++r) {
+        b[r] = 0.0;
+        for (int i = 0; i < n; ++i) b[r] += J[i][r] * w[i] * meas[i];
+        for (int c = 0; c < m; ++c) {
+            double a = 0.0;
+            for (int i = 0; i < n; ++i) a += J[i][r] * w[i] * J[i][c];
+            N[r * m + c] = a;
+        }
     }
-    if (chol_solve(m, A, b, x) != 0) return -1;
-    /* covariance of the unknowns: the inverse of the normal matrix, column by column */
+    for (int j = 1; j + 1 < n; ++j) N[(g + j - 1) * m + (g + j - 1)] += 1.0 / kvar[j];
+    if (chol_solve(m, N, b, th) != 0) return -1;
+    for (int i = 0; i < n; ++i) {
+        double v = 0.0;
+        for (int k = 0; k < m; ++k) v += J[i][k] * th[k];
+        x[i] = v;
+    }
+    if (curv) x[n] = th[2];
+    /* inverse normal matrix in the offsets: T N^-1 T^T, T's rows the J rows and, for the
+     * curvature correction, the unit row of theta_2 */
     if (Ainv) {
+        double Ninv[ORC_MAXM * ORC_MAXM], T[ORC_MAXM][ORC_MAXM];
         for (int k = 0; k < m; ++k) {
             double e[ORC_MAXM], col[ORC_MAXM];
             memset(e, 0, sizeof(e));
             e[k] = 1.0;
-            if (chol_solve(m, A, e, col) != 0) return -1;
-            for (int r = 0; r < m; ++r) Ainv[r * m + k] = col[r];
+            if (chol_solve(m, N, e, col) != 0) return -1;
+            for (int r = 0; r < m; ++r) Ninv[r * m + k] = col[r];
         }
+        memset(T, 0, sizeof(T));
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < m; ++k) T[i][k] = J[i][k];
+        if (curv) T[n][2] = 1.0;
+        for (int r = 0; r < m; ++r)
+            for (int c = 0; c < m; ++c) {
+                double a = 0.0;
+                for (int k = 0; k < m; ++k)
+                    for (int l = 0; l < m; ++l) a += T[r][k] * Ninv[k * m + l] * T[c][l];
+                Ainv[r * m + c] = a;
+            }
     }
     double c2 = 0.0;
     for (int i = 0; i < n; ++i) c2 += w[i] * (meas[i] - x[i]) * (meas[i] - x[i]);
-    for (int j = 1; j + 1 < n; ++j) {
-        double ds0 = s[j] - s[j - 1];
-        double ds1 = s[j + 1] - s[j];
-        double beta = (x[j + 1] - x[j]) / ds1 - (x[j] - x[j - 1]) / ds0;
-        if (curv) beta += 0.5 * (ds0 + ds1) * x[n];
-        c2 += beta * beta / kvar[j];
-    }
+    for (int j = 1; j + 1 < n; ++j) c2 += th[g + j - 1] * th[g + j - 1] / kvar[j];
     *chi2 = c2;
     return 0;
 }

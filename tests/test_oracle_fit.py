@@ -13,6 +13,7 @@
 6. Symmetries: rotation, mirror and z-reflection act on the parameters as geometry says.
 """
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -379,6 +380,61 @@ def test_normal_equations_equal_lstsq(orc, curv):
         scale = np.max(np.abs(ref)) + 1e-12
         assert np.max(np.abs(x - ref)) <= 1e-8 * scale
         assert chi2 == pytest.approx(float(np.sum((A @ ref - b) ** 2)), rel=1e-7, abs=1e-12)
+
+
+def _exact_minimiser(s, meas, w, kvar, curv):
+    """The broken line's chi2 minimiser in exact rational arithmetic: the normal equations in the
+    offsets (and the curvature correction), written from the definition of the kinks, solved by
+    Gaussian elimination on fractions (the inputs are doubles, so they are exact rationals)."""
+    n = len(s)
+    m = n + (1 if curv else 0)
+    s, meas, w, kvar = ([Fraction(float(v)) for v in a] for a in (s, meas, w, kvar))
+    A = [[Fraction(0)] * m for _ in range(m)]
+    b = [Fraction(0)] * m
+    for i in range(n):
+        A[i][i] += w[i]
+        b[i] += w[i] * meas[i]
+    for j in range(1, n - 1):
+        d0, d1 = s[j] - s[j - 1], s[j + 1] - s[j]
+        g = [Fraction(0)] * m
+        g[j - 1], g[j], g[j + 1] = 1 / d0, -1 / d0 - 1 / d1, 1 / d1
+        if curv:
+            g[n] = (d0 + d1) / 2
+        for r in range(m):
+            for c in range(m):
+                A[r][c] += g[r] * g[c] / kvar[j]
+    M = [A[r] + [b[r]] for r in range(m)]
+    for k in range(m):
+        for r in range(k + 1, m):
+            f = M[r][k] / M[k][k]
+            for c in range(k, m + 1):
+                M[r][c] -= f * M[k][c]
+    x = [Fraction(0)] * m
+    for k in reversed(range(m)):
+        x[k] = (M[k][m] - sum(M[k][c] * x[c] for c in range(k + 1, m))) / M[k][k]
+    return np.array([float(v) for v in x])
+
+
+@pytest.mark.parametrize("curv", [True, False])
+def test_broken_line_equals_exact_minimiser(orc, curv):
+    """From soft to extremely stiff kinks (kink variances 1e-4 .. 1e-22 against measurement
+    weights ~1e6, as nearly straight tracks with a large prefit momentum give), the solve equals
+    the exact minimiser of the chi2 to FP64 accuracy (the stiff limit is the weighted
+    least-squares line or parabola, which a solve of the offset normal equations in FP64 misses
+    by up to 1e-3)."""
+    rng = np.random.default_rng(29)
+    for t in range(80):
+        n = int(rng.integers(3, 7))
+        s = np.cumsum(rng.uniform(2, 6, n)) - 2.0
+        meas = rng.normal(0, 1e-3, n) + (0.3 * s if t % 2 else 0.0)
+        w = rng.uniform(0.5, 2, n) * 1e6
+        kvar = 10.0 ** rng.uniform(-22, -4) * rng.uniform(0.5, 2, n)
+        x, chi2 = orc.bl_solve(s, meas, w, kvar, curv)
+        ref = _exact_minimiser(s, meas, w, kvar, curv)
+        assert np.max(np.abs(x[:n] - ref[:n])) <= 1e-9 * (np.max(np.abs(ref[:n])) + 1e-6), t
+        if curv:     # the curvature correction, on the scale of the offsets' curvature
+            scale = abs(ref[n]) + np.max(np.abs(meas)) / (s[-1] - s[0]) ** 2
+            assert abs(x[n] - ref[n]) <= 1e-9 * scale, t
 
 
 def test_curvature_term_sign(orc):
