@@ -109,6 +109,11 @@ def lib():
             L.orc_reconstruct.argtypes = [C.c_uint32, C.POINTER(C.c_float), C.POINTER(C.c_float),
                                           C.POINTER(C.c_float), C.POINTER(C.c_uint16),
                                           C.POINTER(OrcParams), C.c_int]
+            L.orc_reconstruct_w.restype = C.POINTER(OrcResult)
+            L.orc_reconstruct_w.argtypes = [C.c_uint32, C.POINTER(C.c_float),
+                                            C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                            C.POINTER(C.c_uint16), C.POINTER(OrcParams), C.c_int,
+                                            C.c_int]
             L.orc_free.restype = None
             L.orc_free.argtypes = [C.POINTER(OrcResult)]
             _lib = L
@@ -271,8 +276,10 @@ def cov_matrix(c15):
 
 
 # -- whole event -----------------------------------------------------------------------------
-def reconstruct(x, y, z, layer, params, stage: int = 4) -> dict:
-    """Doublets, CA edges, ntuplets and fits of one event (caller hit order).
+def reconstruct(x, y, z, layer, params, stage: int = 4, windowed: bool = False) -> dict:
+    """Doublets, CA edges, ntuplets and fits of one event (caller hit order).  windowed: the
+    doublets by the azimuth-sorted windowed search (the same cells in the same order; the timed
+    CPU baseline uses it) instead of every hit pair.
 
     Returns a dict with 'cells' [nc, 2] (inner, outer hit), 'edges' [ne, 2] (cell A, cell B),
     'tuples' [nt, 8] (hits, 0xFFFFFFFF padded), 'tuple_n' [nt], 'fits' (structured [nt]).
@@ -283,8 +290,9 @@ def reconstruct(x, y, z, layer, params, stage: int = 4) -> dict:
     layer = np.ascontiguousarray(layer, np.uint16)
     P = make_params(params)
     L = lib()
-    rp = L.orc_reconstruct(len(x), _ptr(x, C.c_float), _ptr(y, C.c_float), _ptr(z, C.c_float),
-                           _ptr(layer, C.c_uint16), C.byref(P), stage)
+    rp = L.orc_reconstruct_w(len(x), _ptr(x, C.c_float), _ptr(y, C.c_float),
+                             _ptr(z, C.c_float), _ptr(layer, C.c_uint16), C.byref(P), stage,
+                             1 if windowed else 0)
     if not rp:
         raise ValueError("oracle rejected the input (layer id, limits) or ran out of memory")
     try:

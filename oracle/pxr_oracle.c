@@ -28,7 +28,8 @@
  * cos(w) is an input, computed once by the caller.
  *
  * The oracle is plain and slow on purpose: the doublet search tests every hit pair of every
- * allowed layer pair, and the cell graph is walked recursively.
+ * allowed layer pair, and the cell graph is walked recursively.  (A windowed doublet search,
+ * equal to the all-pairs one entry by entry, serves the timed CPU baseline.)
  */
 #include <math.h>
 #include <stdint.h>
@@ -721,10 +722,98 @@ void orc_free(orc_result *r)
     free(r);
 }
 
+/* Doublets by a windowed search (for the timed CPU baseline; the reference definition is the
+ * all-pairs search in orc_reconstruct): per layer pair, the outer layer's hits sorted by azimuth;
+ * for each inner hit the outer hits whose azimuth lies within phi_window of its own (a binary
+ * search at each end, the window wrapping at +-pi, widened by 1e-9 rad, far above the rounding of
+ * atan2 and of the cut) are tested with the same cut.  An inner hit's cells are emitted in
+ * increasing outer index, so the cell list equals the all-pairs list entry by entry. */
+typedef struct { double phi; uint32_t h; } orc_az;
+
+static int az_cmp(const void *pa, const void *pb)
+{
+    const orc_az *a = (const orc_az *)pa, *b = (const orc_az *)pb;
+    return a->phi < b->phi ? -1 : a->phi > b->phi ? 1 : (a->h < b->h ? -1 : a->h > b->h);
+}
+
+static int u32_cmp(const void *pa, const void *pb)
+{
+    uint32_t a = *(const uint32_t *)pa, b = *(const uint32_t *)pb;
+    return a < b ? -1 : a > b;
+}
+
+/* first index of az[0..m) with phi >= v */
+static uint32_t az_lower(const orc_az *az, uint32_t m, double v)
+{
+    uint32_t lo = 0, hi = m;
+    while (lo < hi) {
+        uint32_t mid = lo + (hi - lo) / 2;
+        if (az[mid].phi < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+static int doublets_windowed(uint32_t n, const double *x, const double *y, const uint16_t *layer,
+                             const orc_params *P, u32vec *ci, u32vec *co)
+{
+    const double pi = ORC_TWO_PI / 2.0;
+    const double W = acos(P->cos_phi_window) + 1e-9;
+    orc_az *az = (orc_az *)malloc((n + 1) * sizeof(orc_az));
+    uint32_t *cand = (uint32_t *)malloc((n + 1) * sizeof(uint32_t));
+    int rc = -1;
+    if (!az || !cand) goto out;
+    for (uint32_t p = 0; p < P->n_pairs; ++p) {
+        uint32_t Li = P->pair_inner[p], Lo = P->pair_outer[p], m = 0;
+        for (uint32_t o = 0; o < n; ++o)
+            if (layer[o] == Lo) { az[m].phi = atan2(y[o], x[o]); az[m].h = o; ++m; }
+        qsort(az, m, sizeof(orc_az), az_cmp);
+        for (uint32_t i = 0; i < n; ++i) {
+            if (layer[i] != Li) continue;
+            const double phi = atan2(y[i], x[i]);
+            double a = phi - W, b = phi + W;
+            uint32_t nc = 0;
+            /* one or two ranges of azimuth [a, b] (modulo 2 pi) */
+            double ra[2][2] = {{a, b}, {1.0, 0.0}};
+            if (a < -pi) { ra[0][0] = a + ORC_TWO_PI; ra[0][1] = pi; ra[1][0] = -pi; ra[1][1] = b; }
+            else if (b > pi) { ra[0][0] = a; ra[0][1] = pi; ra[1][0] = -pi; ra[1][1] = b - ORC_TWO_PI; }
+            if (b - a >= ORC_TWO_PI) { ra[0][0] = -pi - 1.0; ra[0][1] = pi + 1.0; ra[1][0] = 1.0; ra[1][1] = 0.0; }
+            for (int q = 0; q < 2; ++q) {
+                if (ra[q][0] > ra[q][1]) continue;
+                for (uint32_t t = az_lower(az, m, ra[q][0]); t < m && az[t].phi <= ra[q][1]; ++t)
+                    cand[nc++] = az[t].h;
+            }
+            qsort(cand, nc, sizeof(uint32_t), u32_cmp);
+            for (uint32_t t = 0; t < nc; ++t) {
+                const uint32_t o = cand[t];
+                if (t && o == cand[t - 1]) continue;          /* (overlapping ranges) */
+                if (orc_doublet_pass(x[i], y[i], x[o], y[o], P->cos_phi_window))
+                    if (push(ci, i) || push(co, o)) goto out;
+            }
+        }
+    }
+    rc = 0;
+out:
+    free(az);
+    free(cand);
+    return rc;
+}
+
 /* Returns NULL on allocation failure or invalid input.  stage: 1 = stop after doublets,
- * 2 = after edges, 3 = after ntuplets, 4 = with fits. */
+ * 2 = after edges, 3 = after ntuplets, 4 = with fits.  windowed: doublets by the windowed search
+ * (same cells, same order) instead of all pairs. */
+orc_result *orc_reconstruct_w(uint32_t n, const float *xf, const float *yf, const float *zf,
+                              const uint16_t *layer, const orc_params *P, int stage,
+                              int windowed);
+
 orc_result *orc_reconstruct(uint32_t n, const float *xf, const float *yf, const float *zf,
                             const uint16_t *layer, const orc_params *P, int stage)
+{
+    return orc_reconstruct_w(n, xf, yf, zf, layer, P, stage, 0);
+}
+
+orc_result *orc_reconstruct_w(uint32_t n, const float *xf, const float *yf, const float *zf,
+                              const uint16_t *layer, const orc_params *P, int stage,
+                              int windowed)
 {
     orc_result *R = (orc_result *)calloc(1, sizeof(orc_result));
     double *x = NULL, *y = NULL, *z = NULL, *r = NULL;
@@ -747,8 +836,10 @@ orc_result *orc_reconstruct(uint32_t n, const float *xf, const float *yf, const 
         r[h] = orc_radius(x[h], y[h]);
     }
 
-    /* doublets: all pairs of every allowed layer pair */
-    for (uint32_t p = 0; p < P->n_pairs; ++p) {
+    /* doublets: all pairs of every allowed layer pair (or the windowed search) */
+    if (windowed) {
+        if (doublets_windowed(n, x, y, layer, P, &ci, &co)) goto fail;
+    } else for (uint32_t p = 0; p < P->n_pairs; ++p) {
         uint32_t Li = P->pair_inner[p], Lo = P->pair_outer[p];
         for (uint32_t i = 0; i < n; ++i) {
             if (layer[i] != Li) continue;
