@@ -8,13 +8,15 @@
 //  3. Highland scattering angle from the reference momentum, kink variances projected by
 //     1 + cot^2 (transverse) and (1 + cot^2)^2 (line);
 //  4. transverse broken line (offsets u_i + curvature correction delta) and line broken line
-//     (z_i); the normal equations are a pentadiagonal block bordered (transverse) by the
-//     curvature row, solved by a banded Cholesky and the Schur complement of the border;
+//     (z_i), each the minimiser of its chi2, solved in the parameters (kinks, x_0, slope
+//     [, delta]): the kink block (kink weights on its diagonal) by Cholesky, bordered by the
+//     global unknowns, which its Schur complement gives;
 //  5. fitted circle at hit 0 and its point of closest approach to the z axis.
-// Precision modes: FP64 (all steps double), MIXED (arithmetic double, transcendentals float:
-// the normal matrices mix kink weights up to ~1e14 with measurement weights ~1e6, which float
-// assembly cannot hold), FP32 (all float).  The hit count is a template parameter, so every
-// array lives in registers.
+// Precision modes: FP64 (all steps double), MIXED (arithmetic double, transcendentals float),
+// FP32 (all float), SPLIT (steps 1-3 in float, on a chord frame whose differences are
+// error-free; the normal matrices, their Cholesky factorisation and the conversion in double;
+// tracks where the float reference circle would limit the accuracy are refitted in FP64).  The hit count is a template parameter, so
+// every array lives in registers.
 #include "pxr_dev.cuh"
 
 namespace pxr {
@@ -69,146 +71,203 @@ struct FitOut {
     int8_t q, status;
 };
 
-// Symmetric positive definite pentadiagonal matrix (diagonal d0, first and second
-// super-diagonals d1, d2) factored as L L^T in place: d1, d2 receive L's sub-diagonals and d0
-// the reciprocals of L's diagonal (so the solves multiply instead of divide).
-template <int N, typename T>
-__device__ __forceinline__ bool band_factor(T (&d0)[N], T (&d1)[N], T (&d2)[N])
+// In-place Cholesky factor L L^T of a small symmetric positive definite matrix (lower triangle
+// used); the diagonal receives the reciprocals of L's diagonal (the solves multiply).
+template <int K, typename T>
+__device__ __forceinline__ bool chol_factor(T (&A)[K][K])
 {
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        T s = d0[i];
-        if (i >= 1) s -= d1[i - 1] * d1[i - 1];
-        if (i >= 2) s -= d2[i - 2] * d2[i - 2];
-        if (!(s > T(0))) return false;
-        const T il = rsqrt_t(s);
-        d0[i] = il;
-        if (i + 1 < N) {
-            T t = d1[i];
-            if (i >= 1) t -= d2[i - 1] * d1[i - 1];
-            d1[i] = t * il;
+    for (int j = 0; j < K; ++j) {
+        T d = A[j][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
+        if (!(d > T(0))) return false;
+        const T il = rsqrt_t(d);
+        A[j][j] = il;
+#pragma unroll
+        for (int i = j + 1; i < K; ++i) {
+            T t = A[i][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t -= A[i][k] * A[j][k];
+            A[i][j] = t * il;
         }
-        if (i + 2 < N) d2[i] = d2[i] * il;
     }
     return true;
 }
 
-// Solve (L L^T) x = b with the factor of band_factor (il: reciprocal diagonal).
-template <int N, typename T>
-__device__ __forceinline__ void band_solve(const T (&il)[N], const T (&l1)[N], const T (&l2)[N],
-                                           const T (&b)[N], T (&x)[N])
+// y = L^-1 b and x = L^-T y with the factor of chol_factor.
+template <int K, typename T>
+__device__ __forceinline__ void chol_lower(const T (&L)[K][K], T (&b)[K])
 {
-    T y[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
+    for (int i = 0; i < K; ++i) {
         T t = b[i];
-        if (i >= 1) t -= l1[i - 1] * y[i - 1];
-        if (i >= 2) t -= l2[i - 2] * y[i - 2];
-        y[i] = t * il[i];
-    }
 #pragma unroll
-    for (int i = N - 1; i >= 0; --i) {
+        for (int k = 0; k < i; ++k) t -= L[i][k] * b[k];
+        b[i] = t * L[i][i];
+    }
+}
+template <int K, typename T>
+__device__ __forceinline__ void chol_upper(const T (&L)[K][K], T (&y)[K])
+{
+#pragma unroll
+    for (int i = K - 1; i >= 0; --i) {
         T t = y[i];
-        if (i + 1 < N) t -= l1[i] * x[i + 1];
-        if (i + 2 < N) t -= l2[i] * x[i + 2];
-        x[i] = t * il[i];
+#pragma unroll
+        for (int k = i + 1; k < K; ++k) t -= L[k][i] * y[k];
+        y[i] = t * L[i][i];
     }
 }
 
-// Broken line over N points: measurements meas (weights w), kinks at the inner points j with
-// weights wk[j] (reciprocal variances), and (CURV) one curvature unknown.  g[i] = 1/(s[i+1]-s[i])
-// and h[i] = s[i+1]-s[i].  Normal equations: a pentadiagonal block for the offsets (each kink
-// couples three neighbours) bordered by the curvature row; the border is eliminated through the
-// Schur complement.  Returns the offsets x, the curvature correction and the chi2 at the minimum;
-// with CV, also the covariance of (x_0, x_1[, delta]) (the corresponding block of the inverse
-// normal matrix: cv = c00, c01, c11 and, with CURV, c0d, c1d, cdd).
+// Broken line over N points (arc-length steps h[i] = s[i+1] - s[i]): measurements meas with
+// weights w, a kink at each inner point j with weight wk[j] (reciprocal variance), and (CURV) one
+// curvature correction delta.  Kink j = (x_{j+1} - x_j)/h_j - (x_j - x_{j-1})/h_{j-1}
+// + CURV (h_{j-1} + h_j)/2 delta; the fit minimises sum w (meas - x)^2 + sum wk kink^2.
+// It is solved in the parameters theta = (kinks, x_0, first slope, [delta]), which give the
+// paths one to one: x_i = x_0 + slope (s_i - s_0) + sum_{0<j<i} (kink_j - CURV c_j delta)
+// (s_i - s_j), c_j = (h_{j-1} + h_j)/2.  The normal matrix keeps the kink weights (up to ~1e20
+// for nearly straight tracks) on the diagonal of its kink block, apart from the measurement
+// weights (~1e6) that fill the rest: the kink block is factored (Cholesky), the border of the
+// global unknowns (x_0, slope[, delta]) eliminated through its Schur complement, factored in turn.
+// Returns the offsets x, the curvature correction and the chi2 at the minimum; with CV, also the
+// covariance of (x_0, x_1[, delta]) (the Schur complement's inverse carried to x_1 = x_0 + h_0
+// slope: cv = c00, c01, c11 and, with CURV, c0d, c1d, cdd).
 template <int N, bool CURV, typename T, bool CV = false>
-__device__ __forceinline__ bool broken_line_n(const T (&g)[N], const T (&h)[N], const T (&meas)[N],
+__device__ __forceinline__ bool broken_line_n(const T (&h)[N], const T (&meas)[N],
                                               const T (&w)[N], const T (&wk)[N], T (&x)[N],
                                               T &delta, T &chi2, T *cv = nullptr)
 {
-    T d0[N], d1[N], d2[N], c[N], b[N];
-    T dd = T(0);
+    constexpr int K = N - 2;                 // kinks
+    constexpr int G = CURV ? 3 : 2;          // x_0, slope, [delta]
+    T S[N], jd[N];                           // s_i - s_0; d x_i / d delta
+    S[0] = T(0);
+#pragma unroll
+    for (int i = 1; i < N; ++i) S[i] = S[i - 1] + h[i - 1];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        d0[i] = w[i];
-        d1[i] = T(0);
-        d2[i] = T(0);
-        c[i] = T(0);
-        b[i] = w[i] * meas[i];
-    }
+        T a = T(0);
 #pragma unroll
-    for (int j = 1; j + 1 < N; ++j) {
-        const T g0 = g[j - 1], g2 = g[j], g1 = -g0 - g2;
-        const T k = wk[j];
-        d0[j - 1] += k * g0 * g0;
-        d0[j] += k * g1 * g1;
-        d0[j + 1] += k * g2 * g2;
-        d1[j - 1] += k * g0 * g1;
-        d1[j] += k * g1 * g2;
-        d2[j - 1] += k * g0 * g2;
-        if (CURV) {
-            const T gd = T(0.5) * (h[j - 1] + h[j]);
-            c[j - 1] += k * g0 * gd;
-            c[j] += k * g1 * gd;
-            c[j + 1] += k * g2 * gd;
-            dd += k * gd * gd;
+        for (int j = 1; j < i && j + 1 < N; ++j) a -= T(0.5) * (h[j - 1] + h[j]) * (S[i] - S[j]);
+        jd[i] = a;
+    }
+    // d x_i / d theta: kink j -> (S_i - S_j)_+, x_0 -> 1, slope -> S_i, delta -> jd_i
+    auto jk = [&](int i, int j) { return i > j ? S[i] - S[j] : T(0); };   // j = 1..K
+    auto jg = [&](int i, int c) { return c == 0 ? T(1) : c == 1 ? S[i] : jd[i]; };
+    T A[K][K], B[K][G], Gm[G][G], rb[K], rg[G];
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+#pragma unroll
+        for (int b = 0; b <= a; ++b) {
+            T v = a == b ? wk[a + 1] : T(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) v += w[i] * jk(i, a + 1) * jk(i, b + 1);
+            A[a][b] = v;
         }
-    }
-    if (!band_factor<N, T>(d0, d1, d2)) return false;
-    band_solve<N, T>(d0, d1, d2, b, x);
-    delta = T(0);
-    T z[N], schur = T(1);
-    if (CURV) {
-        band_solve<N, T>(d0, d1, d2, c, z);
-        T cy = T(0), cz = T(0);
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-            cy += c[i] * x[i];
-            cz += c[i] * z[i];
+        for (int c = 0; c < G; ++c) {
+            T v = T(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) v += w[i] * jk(i, a + 1) * jg(i, c);
+            B[a][c] = v;
         }
-        schur = dd - cz;
-        if (!(schur > T(0))) return false;
-        delta = -cy / schur;
+        T v = T(0);
 #pragma unroll
-        for (int i = 0; i < N; ++i) x[i] -= z[i] * delta;
+        for (int i = 0; i < N; ++i) v += w[i] * jk(i, a + 1) * meas[i];
+        rb[a] = v;
     }
-    if constexpr (CV) {
-        // columns 0 and 1 of the inverse of the pentadiagonal block; the bordered inverse adds
-        // z z^T / S to it, with -z / S and 1 / S for the curvature (S the Schur complement)
-        T e[N], y0[N], y1[N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) e[i] = i == 0 ? T(1) : T(0);
-        band_solve<N, T>(d0, d1, d2, e, y0);
+    for (int c = 0; c < G; ++c) {
 #pragma unroll
-        for (int i = 0; i < N; ++i) e[i] = i == 1 ? T(1) : T(0);
-        band_solve<N, T>(d0, d1, d2, e, y1);
-        cv[0] = y0[0];
-        cv[1] = y0[1];
-        cv[2] = y1[1];
-        if (CURV) {
-            const T is = T(1) / schur;
-            cv[0] += z[0] * z[0] * is;
-            cv[1] += z[0] * z[1] * is;
-            cv[2] += z[1] * z[1] * is;
-            cv[3] = -z[0] * is;
-            cv[4] = -z[1] * is;
-            cv[5] = is;
+        for (int d = 0; d <= c; ++d) {
+            T v = T(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) v += w[i] * jg(i, c) * jg(i, d);
+            Gm[c][d] = v;
         }
+        T v = T(0);
+#pragma unroll
+        for (int i = 0; i < N; ++i) v += w[i] * jg(i, c) * meas[i];
+        rg[c] = v;
     }
+    // kink block: A = L L^T; Y = L^-1 B, y = L^-1 rb; Schur complement Gm - Y^T Y
+    if (!chol_factor<K, T>(A)) return false;
+    chol_lower<K, T>(A, rb);
+#pragma unroll
+    for (int c = 0; c < G; ++c) {
+        T col[K];
+#pragma unroll
+        for (int a = 0; a < K; ++a) col[a] = B[a][c];
+        chol_lower<K, T>(A, col);
+#pragma unroll
+        for (int a = 0; a < K; ++a) B[a][c] = col[a];
+    }
+#pragma unroll
+    for (int c = 0; c < G; ++c) {
+#pragma unroll
+        for (int d = 0; d <= c; ++d) {
+            T v = Gm[c][d];
+#pragma unroll
+            for (int a = 0; a < K; ++a) v -= B[a][c] * B[a][d];
+            Gm[c][d] = v;
+        }
+        T v = rg[c];
+#pragma unroll
+        for (int a = 0; a < K; ++a) v -= B[a][c] * rb[a];
+        rg[c] = v;
+    }
+    if (!chol_factor<G, T>(Gm)) return false;
+    T tg[G];
+#pragma unroll
+    for (int c = 0; c < G; ++c) tg[c] = rg[c];
+    chol_lower<G, T>(Gm, tg);
+    chol_upper<G, T>(Gm, tg);
+    // kinks: L^T beta = y - Y theta_g
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+        T v = rb[a];
+#pragma unroll
+        for (int c = 0; c < G; ++c) v -= B[a][c] * tg[c];
+        rb[a] = v;
+    }
+    chol_upper<K, T>(A, rb);
+    delta = CURV ? tg[G - 1] : T(0);
     T c2 = T(0);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        const T r = meas[i] - x[i];
+        T v = tg[0] + S[i] * tg[1];
+        if (CURV) v += jd[i] * tg[G - 1];
+#pragma unroll
+        for (int a = 0; a < K; ++a) v += jk(i, a + 1) * rb[a];
+        x[i] = v;
+        const T r = meas[i] - v;
         c2 += w[i] * r * r;
     }
 #pragma unroll
-    for (int j = 1; j + 1 < N; ++j) {
-        T beta = (x[j + 1] - x[j]) * g[j] - (x[j] - x[j - 1]) * g[j - 1];
-        if (CURV) beta += T(0.5) * (h[j - 1] + h[j]) * delta;
-        c2 += beta * beta * wk[j];
-    }
+    for (int a = 0; a < K; ++a) c2 += wk[a + 1] * rb[a] * rb[a];
     chi2 = c2;
+    if constexpr (CV) {
+        // the globals' covariance: the inverse of the Schur complement, columns by solves
+        T Ci[G][G];
+#pragma unroll
+        for (int c = 0; c < G; ++c) {
+            T e[G];
+#pragma unroll
+            for (int d = 0; d < G; ++d) e[d] = c == d ? T(1) : T(0);
+            chol_lower<G, T>(Gm, e);
+            chol_upper<G, T>(Gm, e);
+#pragma unroll
+            for (int d = 0; d < G; ++d) Ci[d][c] = e[d];
+        }
+        const T h0 = h[0];
+        cv[0] = Ci[0][0];
+        cv[1] = Ci[0][0] + h0 * Ci[0][1];
+        cv[2] = Ci[0][0] + T(2) * h0 * Ci[0][1] + h0 * h0 * Ci[1][1];
+        if (CURV) {
+            cv[3] = Ci[0][G - 1];
+            cv[4] = Ci[0][G - 1] + h0 * Ci[1][G - 1];
+            cv[5] = Ci[G - 1][G - 1];
+        }
+    }
     return true;
 }
 
@@ -332,14 +391,19 @@ __device__ __forceinline__ bool bl_convert(const ConvGeom<T> &G, T u0, T u1, T d
     return true;
 }
 
+template <typename T>
+__device__ __forceinline__ void bl_covariance(const ConvGeom<T> &G, T u0, T u1, T delta, T v0,
+                                              T v1, const T *cvT, const T *cvL, double *cov15);
+
 // TC: prefit + residuals + arc lengths; T: everything else (scattering, solves, conversion);
 // FT: float transcendentals (angles and logarithms need ~1e-7 relative, far inside the
 // tolerances).  Divisions and square roots are shared where the method allows (one reciprocal
 // per arc-length step, one scattering angle per surface type, reciprocal Cholesky pivots): they
 // are the costly operations of the double-precision path.
 template <int N, typename TC, typename T, bool FT, bool COV>
-__device__ void fit_n(const float *X, const float *Y, const float *Z, const uint8_t *L,
-                      const DevParams &p, FitOut &o, double *cov15)
+__device__ __noinline__ void fit_n(const float *X, const float *Y, const float *Z,
+                                   const uint8_t *L, const DevParams &p, FitOut &o,
+                                   double *cov15)
 {
     o = FitOut{0, 0, 0, 0, 0, 0, 0, 0};
     TC px[N], py[N];
@@ -426,8 +490,8 @@ __device__ void fit_n(const float *X, const float *Y, const float *Z, const uint
 
     T xT[N], xL[N], delta, dummy, chi2T, chi2L;
     T cvT[6], cvL[3];
-    if (!broken_line_n<N, true, T, COV>(g, h, yr, wT, wkT, xT, delta, chi2T, cvT) ||
-        !broken_line_n<N, false, T, COV>(g, h, z, wL, wkL, xL, dummy, chi2L, cvL)) {
+    if (!broken_line_n<N, true, T, COV>(h, yr, wT, wkT, xT, delta, chi2T, cvT) ||
+        !broken_line_n<N, false, T, COV>(h, z, wL, wkL, xL, dummy, chi2L, cvL)) {
         o.status = 3;
         return;
     }
@@ -440,10 +504,17 @@ __device__ void fit_n(const float *X, const float *Y, const float *Z, const uint
     if (!bl_convert<FT, T>(G, xT[0], xT[1], delta, xL[0], xL[1], o)) { o.status = 2; return; }
     o.chi2 = double(chi2T + chi2L);
     o.status = 0;
-    if constexpr (COV) {
-        // covariance of (q/pT, phi, cot, dxy, dz): the fitted values' covariance (the blocks of
-        // the inverse normal matrices; the two broken lines are independent) through the
-        // conversion's Jacobian (forward-mode derivatives in FP64)
+    if constexpr (COV) bl_covariance<T>(G, xT[0], xT[1], delta, xL[0], xL[1], cvT, cvL, cov15);
+}
+
+// Covariance of (q/pT, phi, cot, dxy, dz): the fitted values' covariance (the blocks of the
+// inverse normal matrices; the two broken lines are independent) through the conversion's
+// Jacobian (forward-mode derivatives in FP64).  v0, v1: the line values the conversion took.
+template <typename T>
+__device__ __forceinline__ void bl_covariance(const ConvGeom<T> &G, T u0, T u1, T delta, T v0,
+                                              T v1, const T *cvT, const T *cvL, double *cov15)
+{
+    {
         double C[5][5];
 #pragma unroll
         for (int a = 0; a < 5; ++a)
@@ -456,11 +527,11 @@ __device__ void fit_n(const float *X, const float *Y, const float *Z, const uint
                                   double(G.g0), double(G.ds0), double(G.X0), double(G.Y0),
                                   double(G.kB)};
         D5 q0[5];
-        q0[0] = D5(double(xT[0]));
-        q0[1] = D5(double(xT[1]));
+        q0[0] = D5(double(u0));
+        q0[1] = D5(double(u1));
         q0[2] = D5(double(delta));
-        q0[3] = D5(double(xL[0]));
-        q0[4] = D5(double(xL[1]));
+        q0[3] = D5(double(v0));
+        q0[4] = D5(double(v1));
 #pragma unroll
         for (int k = 0; k < 5; ++k) q0[k].d[k] = 1.0;
         D5 pt, phi, cot, dxy, dz;
@@ -502,6 +573,188 @@ __device__ __forceinline__ void fit_track(int n, const float *X, const float *Y,
     case 4: fit_n<4, TC, T, FT, COV>(X, Y, Z, L, p, o, cov15); break;
     case 5: fit_n<5, TC, T, FT, COV>(X, Y, Z, L, p, o, cov15); break;
     case 6: fit_n<6, TC, T, FT, COV>(X, Y, Z, L, p, o, cov15); break;
+    default: o = FitOut{0, 0, 0, 0, 0, 0, 0, 4};
+    }
+}
+
+// ---- SPLIT: float bulk, double normal equations, factorisation and conversion ----
+// Error-free transformations (Knuth's two-sum; the product's rounding error from a fused
+// multiply-add): a + b = s + e and a b = p + e exactly.  The _rn intrinsics are never contracted
+// or reassociated.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// The refit of the tracks the float front end does not take: the same fit in FP64 (out of
+// line; rare, so its cost does not matter, and a nearly straight fit from a bent reference
+// amplifies any float rounding, transcendentals included).
+template <int N, bool COV>
+__device__ __forceinline__ void fit_refit64(const float *X, const float *Y, const float *Z,
+                                            const uint8_t *L, const DevParams &p, FitOut &o,
+                                            double *cov15)
+{
+    fit_n<N, double, double, false, COV>(X, Y, Z, L, p, o, cov15);
+}
+
+// Float front end on the chord frame of hits 0 and n-1: every hit's offset from hit 0 is
+// carried exactly as two floats (two-sum), its components along the chord (a) and across it
+// (b) follow, b with the products' rounding errors added back (so b, the small coordinate the
+// curvature lives in, keeps float's relative accuracy however straight the track is).  The
+// reference circle through hits 0, n/2, n-1, the outward residuals (the cancellation-free form
+// (|q|^2 - 2 q.C) / (|q - C| + R0), exact for the circle of centre C through hit 0 whatever the
+// rounding of C), the arc lengths, the weights and the Highland kinks are float; the two normal
+// matrices are formed from these float values in double and factorised in double (the kink
+// block, then the Schur complement of the global unknowns: a float normal matrix holds the
+// measurement geometry of a nearly straight track too coarsely), and the conversion runs in
+// double on the reference centre turned back to the global frame.  The fitted curvature inherits float's
+// relative error of the reference curvature 1/R0 (a few 1e-7), so a track whose fitted
+// curvature is more than ten times smaller than 1/R0 (a nearly straight fit from a bent
+// reference) is refitted in FP64, as is any track the float front end cannot take (degenerate
+// geometry, a failed factorisation).
+template <int N, bool COV>
+__device__ __noinline__ void fit_split_n(const float *X, const float *Y, const float *Z,
+                                         const uint8_t *L, const DevParams &p, FitOut &o,
+                                         double *cov15)
+{
+    constexpr int ib = N / 2, ic = N - 1;
+    o = FitOut{0, 0, 0, 0, 0, 0, 0, 0};
+    // 1. exact offsets from hit 0, the chord frame
+    float dxh[N], dxl[N], dyh[N], dyl[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (i == 0) { dxh[0] = dxl[0] = dyh[0] = dyl[0] = 0.f; continue; }
+        two_sum(X[i], -X[0], dxh[i], dxl[i]);
+        two_sum(Y[i], -Y[0], dyh[i], dyl[i]);
+    }
+    const float l2 = __fmaf_rn(dxh[ic], dxh[ic], __fmul_rn(dyh[ic], dyh[ic]));
+    bool ok = l2 > 0.f && l2 < 1e30f;
+    const float il = rsqrtf(l2);
+    const float tx = dxh[ic] * il, ty = dyh[ic] * il;
+    float a[N], b[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (i == 0) { a[0] = b[0] = 0.f; continue; }
+        a[i] = __fmaf_rn(dxh[i], tx, __fmaf_rn(dyh[i], ty, __fmaf_rn(dxl[i], tx, dyl[i] * ty)));
+        const float p1 = __fmul_rn(dxh[i], -ty), e1 = __fmaf_rn(dxh[i], -ty, -p1);
+        const float p2 = __fmul_rn(dyh[i], tx), e2 = __fmaf_rn(dyh[i], tx, -p2);
+        float sm, e3;
+        two_sum(p1, p2, sm, e3);
+        const float corr = (e1 + e2) + (e3 + __fmaf_rn(dxl[i], -ty, dyl[i] * tx));
+        b[i] = __fadd_rn(sm, corr);
+    }
+    // 2. reference circle through hits 0, ib, ic (centre C in the chord frame)
+    const float D = 2.f * __fmaf_rn(a[ib], b[ic], -__fmul_rn(b[ib], a[ic]));
+    ok = ok && D != 0.f;
+    const float uu = __fmaf_rn(a[ib], a[ib], b[ib] * b[ib]);
+    const float vv = __fmaf_rn(a[ic], a[ic], b[ic] * b[ic]);
+    const float iD = 1.f / D;
+    const float Cx = (uu * b[ic] - vv * b[ib]) * iD, Cy = (vv * a[ib] - uu * a[ic]) * iD;
+    const float R0 = sqrtf(__fmaf_rn(Cx, Cx, Cy * Cy));
+    ok = ok && R0 < 1e7f;       // a nearly straight reference (pT above ~1e5 GeV): refitted
+    const float sgn = D > 0.f ? 1.f : -1.f;
+    // 3. outward residuals, arc lengths, z offsets from hit 0
+    float sa[N], yr[N], zr[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (i == 0) { sa[0] = yr[0] = zr[0] = 0.f; continue; }
+        const float dx = a[i] - Cx, dy = b[i] - Cy;
+        const float pw = __fmaf_rn(a[i], a[i] - 2.f * Cx, b[i] * (b[i] - 2.f * Cy));
+        yr[i] = __fdividef(pw, sqrtf(__fmaf_rn(dx, dx, dy * dy)) + R0);
+        const float cr = __fmaf_rn(Cy, a[i], -Cx * b[i]);                  // (-C) x (q - C)
+        const float dt = __fmaf_rn(R0, R0, -__fmaf_rn(Cx, a[i], Cy * b[i]));  // (-C) . (q - C)
+        sa[i] = R0 * arc_angle<true, float>(sgn * cr, dt);
+        zr[i] = __fsub_rn(Z[i], Z[0]);
+    }
+    // 4. multiple scattering (float): one Highland angle per surface type
+    const float cot0 = zr[ic] / sa[ic];
+    const float sec2 = __fmaf_rn(cot0, cot0, 1.f);
+    const float isec2 = 1.f / sec2;
+    const float sec = sqrtf(sec2);
+    const float a0 = 0.0136f / (float(kKpt * p.bfield) * R0 * sec);
+    auto inv_th2 = [&](float path) {
+        const float xx = float(p.x_over_x0) * path;
+        const float th0 = a0 * sqrtf(xx) * (1.f + 0.038f * logf(xx));
+        return 1.f / (th0 * th0);
+    };
+    bool any_disk = false;
+#pragma unroll
+    for (int i = 0; i < N; ++i) any_disk |= p.is_disk[L[i]] != 0;
+    const float ib2 = inv_th2(sec);
+    const float wz = float(1.0 / (p.sigma_z * p.sigma_z));
+    float id2 = ib2, wdisk = wz;
+    if (any_disk) {
+        const float icot = 1.f / fabsf(cot0);
+        id2 = inv_th2(sec * icot);
+        const float iz = float(1.0 / p.sigma_z) * icot;    // disk: sigma_r = sigma_z |cot|
+        wdisk = iz * iz;
+    }
+    // 5. rows of the normal equations (float values), matrices and solves in double
+    double h[N], g[N], y64[N], z64[N], wT[N], wL[N], wkT[N], wkL[N];
+    const double wrphi = 1.0 / (p.sigma_rphi * p.sigma_rphi);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const float hf = i + 1 < N ? sa[i + 1] - sa[i] : 1.f;
+        h[i] = hf;
+        g[i] = 1.f / hf;
+        y64[i] = yr[i];
+        z64[i] = zr[i];
+        const bool dk = p.is_disk[L[i]] != 0;
+        wT[i] = wrphi;
+        wL[i] = dk ? wdisk : wz;
+        const float it2 = dk ? id2 : ib2;
+        wkT[i] = it2 * isec2;                // kink variance th0^2 (1 + cot^2)
+        wkL[i] = it2 * isec2 * isec2;        // kink variance th0^2 (1 + cot^2)^2
+    }
+#pragma unroll
+    for (int j = 1; j + 1 < N; ++j)
+        ok = ok && isfinite(wkT[j]) && isfinite(wkL[j]) && wkT[j] > 0.0 && wkL[j] > 0.0;
+    double xT[N], xL[N], delta = 0.0, dummy, chi2T = 0.0, chi2L = 0.0;
+    double cvT[6], cvL[3];
+    ok = ok && broken_line_n<N, true, double, COV>(h, y64, wT, wkT, xT, delta, chi2T, cvT) &&
+         broken_line_n<N, false, double, COV>(h, z64, wL, wkL, xL, dummy, chi2L, cvL);
+    // 6. conversion in double: |C| and 1/|C| by two Newton steps from float (the fitted circle's
+    // distance from the beam line needs its centre and radius consistent to ~1e-16 relative at
+    // R0 ~ 1e7 cm), the chord direction to unit length, C turned back to the global frame
+    const double Cxd = Cx, Cyd = Cy, r2 = Cxd * Cxd + Cyd * Cyd;
+    double R0d = R0, iR0 = 1.f / R0;
+    R0d += (r2 - R0d * R0d) * (0.5 * iR0);
+    iR0 *= 2.0 - R0d * iR0;
+    R0d += (r2 - R0d * R0d) * (0.5 * iR0);
+    iR0 *= 2.0 - R0d * iR0;
+    const double kappa = iR0 + delta;
+    ok = ok && fabs(kappa) * 10.0 >= iR0;
+    if (ok) {
+        const double txd = tx, tyd = ty;
+        const double un = rsqrt(txd * txd + tyd * tyd);
+        const double ux = txd * un, uy = tyd * un;
+        const double z0 = Z[0];
+        const ConvGeom<double> G{iR0, Cxd * ux - Cyd * uy, Cxd * uy + Cyd * ux, double(sgn), g[0],
+                                 h[0], double(X[0]), double(Y[0]), kKpt * p.bfield};
+        ok = bl_convert<true, double>(G, xT[0], xT[1], delta, xL[0] + z0, xL[1] + z0, o);
+        if (ok) {
+            o.chi2 = chi2T + chi2L;
+            o.status = 0;
+            if constexpr (COV)
+                bl_covariance<double>(G, xT[0], xT[1], delta, xL[0] + z0, xL[1] + z0, cvT, cvL,
+                                      cov15);
+        }
+    }
+    if (!ok) fit_refit64<N, COV>(X, Y, Z, L, p, o, cov15);
+}
+
+template <bool COV>
+__device__ __forceinline__ void fit_track_split(int n, const float *X, const float *Y,
+                                                const float *Z, const uint8_t *L,
+                                                const DevParams &p, FitOut &o, double *cov15)
+{
+    switch (n) {
+    case 3: fit_split_n<3, COV>(X, Y, Z, L, p, o, cov15); break;
+    case 4: fit_split_n<4, COV>(X, Y, Z, L, p, o, cov15); break;
+    case 5: fit_split_n<5, COV>(X, Y, Z, L, p, o, cov15); break;
+    case 6: fit_split_n<6, COV>(X, Y, Z, L, p, o, cov15); break;
     default: o = FitOut{0, 0, 0, 0, 0, 0, 0, 4};
     }
 }
@@ -640,11 +893,15 @@ __device__ __noinline__ void riemann_fit(int n, const float *X, const float *Y, 
     o.status = 0;
 }
 
-template <bool COV>
+template <bool COV, bool SPLIT>
 __device__ __forceinline__ void fit_dispatch(int n, const float *X, const float *Y,
                                              const float *Z, const uint8_t *L,
                                              const DevParams &p, FitOut &o, double *cov15)
 {
+    if constexpr (SPLIT) {
+        fit_track_split<COV>(n, X, Y, Z, L, p, o, cov15);
+        return;
+    }
     if (p.fit_mode == FIT_RIEMANN) {
         riemann_fit(n, X, Y, Z, L, p, o);
         if constexpr (COV) {
@@ -676,7 +933,7 @@ __device__ __forceinline__ double chi2_ndof(double chi2, int n)
 // number of outputs is read on the device, so no thread is spent on unused capacity.  After the
 // fit, the selection cuts give the track's quality; with shared-hit cleaning a good track offers
 // its rank key to each of its hits (the smallest key of a hit wins, k_keep reads them).
-template <bool COV>
+template <bool COV, bool SPLIT>
 __global__ void __launch_bounds__(256, 2) k_fit(DevBatch b, DevParams p)
 {
     const uint32_t n_out = b.out_evt[b.E];
@@ -704,7 +961,7 @@ __global__ void __launch_bounds__(256, 2) k_fit(DevBatch b, DevParams p)
         }
         FitOut f;
         double cv[COV ? 15 : 1];
-        fit_dispatch<COV>(n, X, Y, Z, L, p, f, cv);
+        fit_dispatch<COV, SPLIT>(n, X, Y, Z, L, p, f, cv);
         if constexpr (COV) {
 #pragma unroll
             for (int k = 0; k < 15; ++k)
@@ -761,8 +1018,14 @@ void launch_fit(const DevBatch &b, const DevParams &p, uint32_t total, cudaStrea
     uint64_t cap = (uint64_t)sms * p.grid_per_sm[5] * (256 / tpb);
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
-    if (p.cov) k_fit<true><<<(unsigned)blocks, tpb, 0, s>>>(b, p);
-    else k_fit<false><<<(unsigned)blocks, tpb, 0, s>>>(b, p);
+    const bool split = p.fit_mode == FIT_SPLIT;
+    if (p.cov) {
+        if (split) k_fit<true, true><<<(unsigned)blocks, tpb, 0, s>>>(b, p);
+        else k_fit<true, false><<<(unsigned)blocks, tpb, 0, s>>>(b, p);
+    } else {
+        if (split) k_fit<false, true><<<(unsigned)blocks, tpb, 0, s>>>(b, p);
+        else k_fit<false, false><<<(unsigned)blocks, tpb, 0, s>>>(b, p);
+    }
 }
 
 void launch_keep(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
@@ -939,7 +1202,8 @@ void launch_vertices(const DevBatch &b, const DevParams &p, cudaStream_t s, int 
 }
 
 // Fit-only path: m ntuplets given directly.
-__global__ void __launch_bounds__(128) k_fit_batch(uint32_t m, const uint8_t *nh, const float *x,
+template <bool SPLIT>
+__global__ void __launch_bounds__(128, 4) k_fit_batch(uint32_t m, const uint8_t *nh, const float *x,
                                                    const float *y, const float *z,
                                                    const uint16_t *layer, uint32_t stride,
                                                    DevParams p, double *pt, double *phi,
@@ -962,7 +1226,7 @@ __global__ void __launch_bounds__(128) k_fit_batch(uint32_t m, const uint8_t *nh
             }
         }
         FitOut f;
-        fit_dispatch<false>(n <= (int)stride ? n : 0, X, Y, Z, L, p, f, nullptr);
+        fit_dispatch<false, SPLIT>(n <= (int)stride ? n : 0, X, Y, Z, L, p, f, nullptr);
         pt[t] = f.pt; phi[t] = f.phi; cot[t] = f.cot; dxy[t] = f.dxy; dz[t] = f.dz;
         chi2[t] = f.chi2; q[t] = f.q; status[t] = f.status;
     }
@@ -977,8 +1241,12 @@ void launch_fit_batch(uint32_t m, const uint8_t *nh, const float *x, const float
     uint64_t cap = (uint64_t)sms * 16;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
-    k_fit_batch<<<(unsigned)blocks, 128, 0, s>>>(m, nh, x, y, z, layer, stride, p, pt, phi, cot,
-                                                 dxy, dz, chi2, q, status);
+    if (p.fit_mode == FIT_SPLIT)
+        k_fit_batch<true><<<(unsigned)blocks, 128, 0, s>>>(m, nh, x, y, z, layer, stride, p, pt,
+                                                           phi, cot, dxy, dz, chi2, q, status);
+    else
+        k_fit_batch<false><<<(unsigned)blocks, 128, 0, s>>>(m, nh, x, y, z, layer, stride, p, pt,
+                                                            phi, cot, dxy, dz, chi2, q, status);
 }
 
 }  // namespace pxr

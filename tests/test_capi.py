@@ -105,7 +105,7 @@ def test_params_validation(lib):
                dict(vertexing=True, vtx_gap=0.0), dict(vertexing=True, vtx_gap=float("nan"))):
         q = pxr.params_from(synth.params_barrel_quadruplets(), **kw)
         assert lib.pxr_params_check(C.byref(q)) == pxr.EINVAL, kw
-    for field, val in (("clean_shared", 2), ("fit_cov", 2), ("vertexing", 3), ("fit_mode", 4)):
+    for field, val in (("clean_shared", 2), ("fit_cov", 2), ("vertexing", 3), ("fit_mode", 5)):
         q = pxr.params_from(synth.params_barrel_quadruplets())
         setattr(q, field, val)
         assert lib.pxr_params_check(C.byref(q)) == pxr.EINVAL, field

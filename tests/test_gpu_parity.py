@@ -384,6 +384,7 @@ FULL_SIZE_CONFIGS = [
     (pxr.CUT_FP64, pxr.FIT_FP64, 0, [0] * 6),
     (pxr.CUT_FP32, pxr.FIT_FP64, 0, [0] * 6),
     (pxr.CUT_FP32, pxr.FIT_MIXED, 1024, [4, 32, 32, 32, 4, 0]),
+    (pxr.CUT_FP32, pxr.FIT_SPLIT, 1024, [4, 32, 32, 32, 4, 0]),
 ]
 
 
@@ -457,7 +458,7 @@ def test_fit_batch_modes(ctx, orc):
     args = [torch.from_numpy(a).to(dev) for a in (tb.n_hits, tb.x, tb.y, tb.z,
                                                   tb.layer.view(np.int16))]
     res = {}
-    for mode in (pxr.FIT_FP64, pxr.FIT_MIXED, pxr.FIT_FP32):
+    for mode in (pxr.FIT_FP64, pxr.FIT_MIXED, pxr.FIT_FP32, pxr.FIT_SPLIT):
         out = {k: torch.zeros(m, dtype=torch.float64, device=dev) for k in pxr.TRACK_FIELDS}
         out["charge"] = torch.zeros(m, dtype=torch.int8, device=dev)
         out["fit_status"] = torch.zeros(m, dtype=torch.int8, device=dev)
@@ -475,8 +476,42 @@ def test_fit_batch_modes(ctx, orc):
     # still 1 % of the stated tolerance.
     for k, v in res[pxr.FIT_FP64].items():
         assert v < 0.01 * TOL[k], (k, v)
-    # MIXED (double arithmetic, float transcendentals) stays inside the stated tolerances
-    for k, v in res[pxr.FIT_MIXED].items():
+    # MIXED (double arithmetic, float transcendentals) and SPLIT (float bulk, double normal
+    # equations and conversion) stay inside the stated tolerances
+    for mode in (pxr.FIT_MIXED, pxr.FIT_SPLIT):
+        for k, v in res[mode].items():
+            assert v <= TOL[k], (mode, k, v)
+
+
+def _fit_only(ctx, tb, P, mode):
+    dev = torch.device("cuda:0")
+    m = len(tb.n_hits)
+    args = [torch.from_numpy(a).to(dev) for a in (tb.n_hits, tb.x, tb.y, tb.z,
+                                                  tb.layer.view(np.int16))]
+    out = {k: torch.zeros(m, dtype=torch.float64, device=dev) for k in pxr.TRACK_FIELDS}
+    out["charge"] = torch.zeros(m, dtype=torch.int8, device=dev)
+    out["fit_status"] = torch.zeros(m, dtype=torch.int8, device=dev)
+    ctx.pxr_fit_batch(m, *args, tb.x.shape[1], pxr.params_from(P, fit_mode=mode), out)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def test_split_fit_precision_set_within_tolerance(ctx, orc):
+    """The precision workload at full size: 1e6 smeared ntuplets (70 % quadruplets, 30 %
+    triplets, pT 0.5-100 GeV log-uniform).  The SPLIT fit (float bulk; double normal equations,
+    Cholesky and conversion; MIXED refit where the float reference would limit accuracy) has the
+    oracle's statuses and charges, and every parameter within the stated tolerances."""
+    P = synth.params_barrel_quadruplets()
+    tb = synth.fit_tuplets(1_000_000, seed=0)
+    ref = orc.fit_batch(tb.n_hits, tb.x.astype(np.float64), tb.y.astype(np.float64),
+                        tb.z.astype(np.float64), tb.layer, P)
+    h = _fit_only(ctx, tb, P, pxr.FIT_SPLIT)
+    assert np.all(h["fit_status"] == ref["status"])
+    ok = ref["status"] == 0
+    assert np.all(h["charge"][ok] == ref["charge"][ok])
+    err = fit_errors(h, ref, ok)
+    print("SPLIT fit errors vs FP64 oracle (1e6 ntuplets):", err)
+    for k, v in err.items():
         assert v <= TOL[k], (k, v)
 
 
@@ -527,13 +562,14 @@ def test_riemann_fit_matches_oracle(ctx, orc):
         assert v < 0.01 * TOL[k], (k, v)
 
 
-@pytest.mark.parametrize("cut", [pxr.CUT_FP32])
-def test_dense_event_mixed_fit_within_tolerance(ctx, orc, cut):
-    """The batch path with the MIXED fit (the benchmark's setting): sets bit-exact, fitted
-    parameters within the stated tolerances of the FP64 oracle."""
+@pytest.mark.parametrize("fit", [pxr.FIT_MIXED, pxr.FIT_SPLIT])
+def test_dense_event_reduced_precision_fit_within_tolerance(ctx, orc, fit):
+    """The batch path with the MIXED and SPLIT fits on the dense event with disks (3-5 hits,
+    smearing, noise): sets bit-exact, fitted parameters within the stated tolerances of the FP64
+    oracle."""
     P = synth.params_phase1()
     ev = ev_tuple(synth.event_phase1(4))
-    got = run_plan(ctx, [ev], P, cut, fit=pxr.FIT_MIXED)[0]
+    got = run_plan(ctx, [ev], P, pxr.CUT_FP32, fit=fit)[0]
     check_event(orc, ev, P, got, fit_tol=TOL)
 
 
