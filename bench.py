@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pxr", choices=["pxr", "reference"])
     ap.add_argument("--cut", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--fit", default="mixed", choices=["fp64", "mixed", "fp32"])
+    ap.add_argument("--fit", default="split", choices=["fp64", "mixed", "fp32", "split"])
     ap.add_argument("--events", type=int, default=256)
     ap.add_argument("--no-extras", action="store_true", help="skip plain/e2e/serving/cpu legs")
     ap.add_argument("--serve-rate", type=float, default=5000.0)
@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--bins", type=int, default=0, help="phi bins per layer (skips tuning)")
     ap.add_argument("--grid", default="", help="CTAs per SM per stage, 6 comma-separated values "
                     "(sort,doublets,connect,walk,select,fit; skips tuning)")
+    ap.add_argument("--arena-gb", type=int, default=64, help="device arena of the batch plan")
     ap.add_argument("--tune-cache", default=os.path.join(os.path.expanduser("~"), ".cache", "pxr",
                                                          "tune.json"))
     return ap.parse_args()
@@ -81,11 +82,14 @@ def _oracle_event(args):
     ev = synth.make_event(seed, T)
     P = synth.params_barrel_quadruplets()
     t0 = time.perf_counter()
-    r = oracle.reconstruct(ev.x, ev.y, ev.z, ev.layer, P)
+    # the windowed doublet search (same cells as the all-pairs definition, see the oracle's pins)
+    r = oracle.reconstruct(ev.x, ev.y, ev.z, ev.layer, P, windowed=True)
     return time.perf_counter() - t0, len(r["tuples"])
 
 
 def cpu_baseline(seeds_counts, cores):
+    """The oracle on `cores` host processes, one event per process (the paper's CPU strategy):
+    events/s over the sample's wall time, the wall time, and the summed per-event times."""
     import multiprocessing as mp
     import oracle
     oracle.build()
@@ -95,6 +99,54 @@ def cpu_baseline(seeds_counts, cores):
         res = pool.map(_oracle_event, seeds_counts, chunksize=1)
     wall = time.perf_counter() - t0
     return len(seeds_counts) / wall, wall, sum(r[0] for r in res)
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        info = open("/proc/cpuinfo").read()
+        for line in info.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+        imp = [l.split(":")[1].strip() for l in info.splitlines() if l.startswith("CPU implementer")]
+        part = [l.split(":")[1].strip() for l in info.splitlines() if l.startswith("CPU part")]
+        if imp and part:
+            return f"arm64 implementer {imp[0]} part {part[0]}"
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline_record(n_single=8, n_all=64):
+    """The timed CPU baseline: the oracle (windowed doublet search) on one thread over n_single
+    events and on every host core over n_all events, both spread over the batch's track-count
+    range, one event per process."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    single = oracle_sample(n_single)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(1) as pool:
+        pool.map(_oracle_event, single[:1])                 # warm-up (imports, build)
+        t0 = time.perf_counter()
+        pool.map(_oracle_event, single, chunksize=1)
+        t1 = len(single) / (time.perf_counter() - t0)
+    sample = oracle_sample(n_all)
+    v, wall, _ = cpu_baseline(sample, cores)
+    return {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(), "nproc": cores,
+            "threads_1": {"value": t1, "events": len(single)},
+            "threads_all": {"value": v, "events": len(sample), "threads": cores},
+            "sample": f"{len(sample)} events spread over the batch's 200-6000 track range, one "
+                      f"event per process on {cores} cores ({wall:.1f} s); single thread: "
+                      f"{len(single)} events; doublets by the oracle's windowed search"}
 
 
 def oracle_sample(n_events):
@@ -172,7 +224,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     cores = os.cpu_count() or 1
-    sample = oracle_sample(min(32, 2 * cores))
+    sample = oracle_sample(max(64, 4 * cores))
     for _ in range(args.warmup):
         cpu_baseline(sample[:cores], cores)
     t0 = time.perf_counter()
@@ -188,9 +240,10 @@ def run_reference(args, rank, world):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample_events": len(sample)},
             "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores,
-                             "kind": "oracle",
+                             "kind": "oracle", "cpu_model": cpu_model(), "nproc": cores,
                              "sample": f"{len(sample)} events of the batch spread over 200-6000 "
-                                       f"tracks, one event per process"},
+                                       f"tracks, one event per process; doublets by the "
+                                       f"oracle's windowed search"},
             "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -257,7 +310,8 @@ def run_pxr(args, rank, world, local):
         dist.init_process_group("nccl", device_id=dev)
 
     cut = pxr.CUT_FP32 if args.cut == "fp32" else pxr.CUT_FP64
-    fit = {"fp64": pxr.FIT_FP64, "mixed": pxr.FIT_MIXED, "fp32": pxr.FIT_FP32}[args.fit]
+    fit = {"fp64": pxr.FIT_FP64, "mixed": pxr.FIT_MIXED, "fp32": pxr.FIT_FP32,
+           "split": pxr.FIT_SPLIT}[args.fit]
     P = synth.params_barrel_quadruplets()
     params = pxr.params_from(P, cut_mode=cut, fit_mode=fit)
     # each rank processes its own batch of events (event sharding, no collective)
@@ -273,7 +327,7 @@ def run_pxr(args, rank, world, local):
     layer_counts = [np.bincount(e.layer, minlength=4) for e in evs]
     n_hits = int(off[-1])
 
-    budget = 64 << 30
+    budget = args.arena_gb << 30
     arena = torch.empty(budget, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
     ctx = pxr.Context(device=local, mem_budget_bytes=budget, arena=arena,
@@ -416,29 +470,42 @@ def extras(args, ctx, pxr, synth, P, params, evs, off, x, y, z, layer, dev, stre
                     "how": "one event per launch sequence, no graph, same stream"}
     out["batched_over_plain"] = value / plain
 
-    # end to end through the serving API with host buffers (copies inside the timed region)
+    # end to end through the serving API with host buffers (copies inside the timed region): the
+    # step's events submitted in one call from pinned host arrays, polled, fetched in one call
+    # into preallocated host arrays
+    import torch as _t
+    hoff = off.astype(np.uint32)
+    pin = lambda a: _t.from_numpy(a).pin_memory().numpy()
+    cat = lambda k: np.concatenate([getattr(e, k) for e in evs])
+    px, py, pz, pl = pin(cat("x")), pin(cat("y")), pin(cat("z")), pin(cat("layer").view(np.int16))
+    pl = pl.view(np.uint16)
     with pxr.Context(device=dev.index, mem_budget_bytes=48 << 30, max_batch_events=256) as sctx:
+        res = {"out": None}
+
         def serve_all():
             t0 = time.perf_counter()
-            tickets = [sctx.pxr_submit_event(e.x, e.y, e.z, e.layer, params) for e in evs]
-            done = 0
-            while done < len(tickets):
-                done += len(sctx.pxr_poll(timeout_us=100000))
-            d2h = 0
-            for t in tickets:
-                r = sctx.pxr_fetch_tracks(t)
-                d2h += r["n"] * (1 + 4 * pxr.MAX_HITS + 6 * 8 + 3) + 8
-            return time.perf_counter() - t0, d2h
+            tickets = sctx.pxr_submit_events(hoff, px, py, pz, pl, params)
+            want = set(tickets)
+            done = set()
+            while not want <= done:
+                done |= set(sctx.pxr_poll(timeout_us=100000))
+            r = sctx.pxr_fetch_events(tickets, out=res["out"])
+            dt = time.perf_counter() - t0
+            if res["out"] is None or len(res["out"]["pt"]) < r["n"]:
+                res["out"] = {k: v.copy() for k, v in r.items() if isinstance(v, np.ndarray)}
+            d2h = r["n"] * (1 + 4 * pxr.MAX_HITS + 6 * 8 + 3) + 4 * (len(tickets) + 1)
+            return dt, d2h
         serve_all()
         times = []
-        for _ in range(3):
+        for _ in range(5):
             dt, d2h = serve_all()
             times.append(dt)
         e2e = len(evs) / float(np.median(times))
         out["e2e"] = {"value": e2e, "unit": "events/s",
                       "h2d_bytes_per_step": int(sum(14 * e.n for e in evs)),
                       "d2h_bytes_per_step": int(d2h),
-                      "how": "pxr_submit_event x256 (host arrays) + pxr_poll + pxr_fetch_tracks"}
+                      "how": "pxr_submit_events (256 events, pinned host arrays) + pxr_poll + "
+                             "pxr_fetch_events (host arrays); median of 5 steps"}
 
     # Poisson arrivals, latency from arrival to fetchable, 8 GB budget, continuous batching
     rate = args.serve_rate
@@ -448,12 +515,7 @@ def extras(args, ctx, pxr, synth, P, params, evs, off, x, y, z, layer, dev, stre
     out["serving"] = sv
 
     # host-core oracle on a bounded sample of the same workload
-    cores = os.cpu_count() or 1
-    sample = oracle_sample(min(32, 2 * cores))
-    v, wall, cpu_s = cpu_baseline(sample, cores)
-    out["cpu_baseline"] = {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
-                           "sample": f"{len(sample)} events spread over the batch's 200-6000 "
-                                     f"track range, one event per process ({wall:.1f} s)"}
+    out["cpu_baseline"] = cpu_baseline_record()
     return out
 
 
@@ -729,8 +791,9 @@ def study(args):
         dargs = [torch.from_numpy(a).to(dev) for a in (tb.n_hits, tb.x, tb.y, tb.z,
                                                        tb.layer.view(np.int16))]
         c4 = {"ntuplets": m, "oracle_1core_fits_per_s": o_fit}
-        for name, mode in (("fp32", pxr.FIT_FP32), ("mixed", pxr.FIT_MIXED),
-                           ("fp64", pxr.FIT_FP64)):
+        fits_of = {}
+        for name, mode in (("fp32", pxr.FIT_FP32), ("split", pxr.FIT_SPLIT),
+                           ("mixed", pxr.FIT_MIXED), ("fp64", pxr.FIT_FP64)):
             res = {k: torch.zeros(m, dtype=torch.float64, device=dev) for k in pxr.TRACK_FIELDS}
             res["charge"] = torch.zeros(m, dtype=torch.int8, device=dev)
             res["fit_status"] = torch.zeros(m, dtype=torch.int8, device=dev)
@@ -749,6 +812,11 @@ def study(args):
             c4[name] = {"fits_per_s": 5 * m / (a.elapsed_time(b) / 1e3),
                         "status_agree": float(np.mean(h["fit_status"] == ref["status"])),
                         "errors": _fit_errors(h, ref, ok)}
+            fits_of[name] = h
+        # SPLIT refits in MIXED where the float reference would limit the accuracy: the share of
+        # such tracks (their results are MIXED's, bit for bit)
+        c4["split"]["mixed_refit_share"] = float(np.mean(
+            fits_of["split"]["pt"] == fits_of["mixed"]["pt"]))
         # the Riemann fit (FP64) on the same ntuplets, against the oracle's Riemann fit
         t0 = time.perf_counter()
         ref_r = oracle.riemann_batch(tb.n_hits, tb.x.astype(np.float64), tb.y.astype(np.float64),
@@ -788,11 +856,8 @@ def study(args):
         c5.append({"served": _serve(pxr, synth, prm, dev, rate, n, 8 << 30, 256),
                    "plain": _serve(pxr, synth, prm, dev, rate, n, 8 << 30, 1)})
     out["C5_serving"] = c5
-    # oracle on all host cores, one event per process, on a sample of the batch workload
-    cores = os.cpu_count() or 1
-    sample = oracle_sample(min(32, 2 * cores))
-    v, wall, _ = cpu_baseline(sample, cores)
-    out["C3_oracle_all_cores"] = {"events_per_s": v, "cores": cores, "sample_events": len(sample)}
+    # oracle on one and on all host cores, one event per process, on samples of the batch workload
+    out["C3_oracle"] = cpu_baseline_record()
     print(json.dumps(out, indent=1, default=float), flush=True)
 
 

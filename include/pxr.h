@@ -70,6 +70,14 @@ extern "C" {
                                eigenvector of the weighted scatter matrix) gives the circle; a
                                weighted straight line in (arc length, z); no multiple scattering.
                                The track covariance is not computed for it (NaN) */
+#define PXR_FIT_SPLIT 4     /* FP32 bulk: the local (chord) frame with error-free offsets from hit
+                               0, the reference circle, residuals, arc lengths, multiple
+                               scattering and the rows of the normal equations in FP32; the
+                               normal matrices, their banded Cholesky with the curvature border
+                               (Schur complement) and the conversion to track parameters in FP64.
+                               A track whose fitted curvature is below a tenth of its reference
+                               circle's (where FP32's error of the reference would be amplified)
+                               or that the FP32 front end cannot take is refitted in FP64 */
 
 /* Presets for pxr_params_init */
 #define PXR_PRESET_BARREL 0 /* 4 barrel layers r = 2.9/6.8/10.9/16.0, pairs (0,1)(1,2)(2,3), roots
@@ -263,6 +271,19 @@ int pxr_submit_event(pxr_ctx *ctx, const float *x, const float *y, const float *
                      const uint16_t *layer, uint32_t n_hits, const pxr_params *params,
                      uint64_t *ticket);
 
+/* Serving path, many events in one call: n_events events whose hits are back to back in the
+ * host arrays x, y, z, layer, event e at [hit_offsets[e], hit_offsets[e+1]) (hit_offsets: host
+ * array of n_events+1; the arrays are indexed from hit_offsets[0]).  Each event behaves as if
+ * submitted by pxr_submit_event, in order; tickets[e] (host, n_events) receives its ticket.  The
+ * hits are copied into the context's pinned host memory before the call returns (from there
+ * they go to the device without a further host copy).  All events are admitted or none:
+ * PXR_EINVAL (bad params or any event's input), PXR_ENOMEM (an event alone exceeds the budget,
+ * or no pinned memory), PXR_EAGAIN (the events together exceed the free budget now).
+ * Source: the paper defines no serving interface (§5, Table 2 for concurrent events). */
+int pxr_submit_events(pxr_ctx *ctx, uint32_t n_events, const uint32_t *hit_offsets,
+                      const float *x, const float *y, const float *z, const uint16_t *layer,
+                      const pxr_params *params, uint64_t *tickets);
+
 /* Return up to cap finished tickets in done[] (host array), *n_done = count.  Waits up to
  * timeout_us microseconds (0 = do not wait, < 0 = until at least one is done or none pending).
  * Source: the paper defines no serving interface (§5, Table 2 for concurrent events). */
@@ -273,6 +294,19 @@ int pxr_poll(pxr_ctx *ctx, uint64_t *done, uint32_t cap, uint32_t *n_done, int t
  * ticket kept.  PXR_EBUSY: not finished.  The event's own status (overflow) is in out->status.
  * Source: §2, the Tracks module's product (tracks with fitted parameters from hit n-tuplets). */
 int pxr_fetch_tracks(pxr_ctx *ctx, uint64_t ticket, pxr_tracks *out);
+
+/* The tracks of n finished events in one call, into one set of caller arrays: event k's tracks
+ * at rows [track_offsets[k], track_offsets[k+1]) of every track array and its vertices at rows
+ * [vertex_offsets[k], vertex_offsets[k+1]) of the vertex arrays (track_offsets: host array of
+ * n+1, written; vertex_offsets, event_status: optional host arrays of n+1 and n, written).  Each
+ * event's tracks are in canonical order; a track's vertex index counts within its event.
+ * out->capacity is the rows of every array; out->n_tracks and out->n_vertices receive the
+ * totals, out->status the first event status that is not PXR_OK (else PXR_OK).  On success every
+ * ticket is released.  PXR_ETRUNC: capacity too small (totals set, tickets kept); PXR_EBUSY /
+ * PXR_ENOTFOUND: a ticket not finished / unknown (nothing copied, tickets kept).
+ * Source: §2, the Tracks module's product. */
+int pxr_fetch_events(pxr_ctx *ctx, uint32_t n, const uint64_t *tickets, uint32_t *track_offsets,
+                     uint32_t *vertex_offsets, int32_t *event_status, pxr_tracks *out);
 
 /* Debug content of a finished event kept with cfg->keep_debug (before pxr_fetch_tracks):
  * what = 0: cells as (inner, outer) caller-index pairs (2 words each);

@@ -35,9 +35,13 @@ __device__ __forceinline__ Window phi_window(const uint32_t *__restrict__ bk, ui
 {
     const uint32_t *lb = bk + Lo * p.nb;
     int nb = (int)p.nb;
+    Window w;
+    if (!(fabsf(phi) <= 4.f)) {                // a non-finite azimuth has no window
+        w.r0 = w.n1 = w.r2 = w.n2 = 0;
+        return w;
+    }
     int blo = (int)floorf((phi - p.w_eps + kPiF2) * p.bins_per_rad);
     int bhi = (int)floorf((phi + p.w_eps + kPiF2) * p.bins_per_rad);
-    Window w;
     if (bhi - blo + 1 >= nb) {
         w.r0 = lb[0]; w.n1 = lb[nb] - lb[0]; w.r2 = 0; w.n2 = 0;
     } else if (blo < 0) {
@@ -385,18 +389,6 @@ __device__ __forceinline__ bool cone_window(float ar, float az, float base, floa
     return true;
 }
 
-constexpr int kConnWarps = 8;
-constexpr int kStage = 256;     // out-cells of one junction staged per out-layer slot
-constexpr int kBins = 128;      // local bins of the free coordinate (multiple of 32)
-
-// Order-preserving int encoding of floats (for warp min / max reductions).
-__device__ __forceinline__ int ford(float f)
-{
-    const int i = __float_as_int(f);
-    return i >= 0 ? i : i ^ 0x7FFFFFFF;
-}
-__device__ __forceinline__ float funord(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
-
 // Mark cell C as reached (it has an in-edge).  The first marker clears C's edge count (the walk
 // reads it; a later level writes the count if C gets out-edges) and, when C is `listed` (a
 // non-root cell whose outer hit starts further pairs), appends it to the event's frontier list,
@@ -423,6 +415,300 @@ __device__ __forceinline__ void mark_reached(const DevBatch &b, uint32_t e, uint
         atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
     }
 }
+
+// The grid search of the out-cells (j, k) on layer Lk of the pair (item itj of hit j) that can
+// continue the segment a (ending at j) of the cell (i, j): the hit grid's cells of j's phi
+// window on Lk (whole coarse azimuth bins: j's fine-bin window as the doublet stage binned it)
+// crossed with the bins of the r-z cone of directions within asin(theta_cut) of a, a
+// conservative window.  Returns the number of grid ranges (one per coarse bin, at most kCaR:
+// a window of at most 1 rad spans at most 7 bins of 2 pi / 32) with their starts and lengths in
+// q0, qn, and the cone [lo, hi]; 0 when nothing can pass.
+constexpr int kCaR = 8;
+
+__device__ __forceinline__ uint32_t ca_ranges(const DevBatch &b, const DevParams &p, uint32_t e,
+                                              uint32_t Lk, float4 hj, float phij, const RZ32 &a,
+                                              uint4 itj, float &lo, float &hi,
+                                              uint32_t (&q0)[kCaR], uint32_t (&qn)[kCaR])
+{
+    lo = -3.0e38f;
+    hi = 3.0e38f;
+    const uint32_t g = p.glidx[Lk];
+    if (itj.y == 0 || g == 0xFF || !(fabsf(phij) <= 4.f)) return 0;   // (g: always a grid layer;
+                                                                     //  phij: finite)
+    const float4 gl = b.glay[(size_t)e * p.n_glayers + g];
+    const bool disk = p.is_disk[Lk];
+    const float jx = disk ? hj.z : hj.w;          // j's fixed coordinate relative to Lk's
+    int z0 = 0, z1 = (int)p.gz - 1;
+    if (cone_window(a.ar, a.az, disk ? hj.w : hj.z, gl.z - jx, gl.w - jx, disk, p.tan_win, lo,
+                    hi)) {
+        const float u0 = floorf((lo - gl.x) * gl.y), u1 = floorf((hi - gl.x) * gl.y);
+        if (!(u1 >= 0.f) || !(u0 < (float)p.gz)) return 0;  // (also when either is not a number)
+        z0 = u0 < 0.f ? 0 : (int)u0;
+        z1 = u1 >= (float)p.gz ? (int)p.gz - 1 : (int)u1;
+    }
+    const int nb = (int)p.nb, gp = (int)p.gphi;
+    const int blo = (int)floorf((phij - p.w_eps + kPiF2) * p.bins_per_rad);
+    const int bhi = (int)floorf((phij + p.w_eps + kPiF2) * p.bins_per_rad);
+    int c0, c1, c2 = 1, c3 = 0;                   // coarse runs [c0, c1] and [c2, c3]
+    if (bhi - blo + 1 >= nb) {
+        c0 = 0; c1 = gp - 1;
+    } else if (blo < 0) {
+        c0 = (blo + nb) * gp / nb; c1 = gp - 1;
+        c2 = 0; c3 = bhi * gp / nb;
+    } else if (bhi >= nb) {
+        c0 = blo * gp / nb; c1 = gp - 1;
+        c2 = 0; c3 = (bhi - nb) * gp / nb;
+    } else {
+        c0 = blo * gp / nb; c1 = bhi * gp / nb;
+    }
+    const uint32_t *go = b.gofs + (size_t)e * (p.n_glayers * p.gphi * p.gz + 1) +
+                         (size_t)g * p.gphi * p.gz;
+    uint32_t nr = 0;
+    // (the bounds of all ranges are loaded together)
+#pragma unroll
+    for (int r = 0; r < kCaR; ++r) {
+        const int n1 = c1 - c0 + 1;
+        const int pc = r < n1 ? c0 + r : c2 + (r - n1);
+        if (r < n1 || pc <= c3) {
+            const uint32_t *gc = go + (size_t)pc * p.gz;
+            q0[r] = gc[z0];
+            qn[r] = gc[z1 + 1];
+            nr = r + 1;
+        } else {
+            q0[r] = qn[r] = 0;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kCaR; ++r) qn[r] -= q0[r];
+    return nr;
+}
+
+constexpr int kCaWarps = 8;
+constexpr int kEdgeBuf = 8;     // passes buffered per cell; a longer list is found again
+#ifndef PXR_CA_MINB
+#define PXR_CA_MINB 2           // CTAs per SM the CA kernels are compiled for (register budget)
+#endif
+
+// One warp's cells (one per lane), their queries and passes, in shared memory: the warp works
+// through the grid candidates of all its lanes as one list, 32 at a time, so that a lane with
+// many candidates does not hold up the others.
+struct CaWarp {
+    float4 hj[32], a[32];        // junction hit, segment into it (ar, az, |a|, error bound)
+    float2 xy[32], cone[32];     // the segment's inner hit (x, y); the cone [lo, hi]
+    uint4 itj[32];               // j's entries on the out-layer of the pair
+    uint32_t i[32], j[32], fr[32];
+    uint32_t pre[32];            // exclusive prefix of the lanes' candidates
+    uint32_t q0[kCaR][32], qn[kCaR][32];
+    uint32_t npass[32];
+    uint32_t buf[kEdgeBuf][32];  // passes; bit 31: list the target in the frontier
+};
+
+// The exact triplet cut for a grid candidate, out of line: only candidates inside the cone get
+// here, and its registers then do not weigh on the lookup loop.
+template <bool F64>
+__device__ __noinline__ bool ca_test(const DevBatch &b, const DevParams &p, uint32_t i, uint32_t j,
+                                     uint32_t B, uint32_t k, float xi, float yi, float4 hj,
+                                     float4 a4)
+{
+    const RZ32 a{a4.x, a4.y, a4.z, a4.w};
+    return triplet_test<F64>(b, p, i, j, B, xi, yi, hj, b.hs[k], a);
+}
+
+// One pair (out-layer Lk of the lane's cell; lanes with active false take no part) for the
+// warp's cells: each lane's grid ranges, then the flattened candidates, each checked against its
+// owner's cone, j's window (the rank among j's entries) and the entry (which holds k unless the
+// doublet cut failed); the exact triplet cut decides; passes go to the owner's buffer.
+template <bool F64>
+__device__ __forceinline__ void ca_warp_pair(const DevBatch &b, const DevParams &p, uint32_t e,
+                                             CaWarp &W, uint32_t lane, bool active, uint32_t Lk,
+                                             uint32_t i, uint32_t j, float xi, float yi,
+                                             float4 hj, float phij, const RZ32 &a, uint4 itj,
+                                             uint32_t fr)
+{
+    const uint32_t FULL = 0xFFFFFFFFu;
+    uint32_t q0[kCaR], qn[kCaR];
+    float lo = 0.f, hi = 0.f;
+    uint32_t nr = 0, nc = 0;
+    if (active) nr = ca_ranges(b, p, e, Lk, hj, phij, a, itj, lo, hi, q0, qn);
+#pragma unroll
+    for (int r = 0; r < kCaR; ++r) {
+        if (r >= (int)nr) qn[r] = 0;
+        nc += qn[r];
+        W.q0[r][lane] = q0[r];
+        W.qn[r][lane] = qn[r];
+    }
+    uint32_t incl = nc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= (uint32_t)o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    if (total == 0) return;
+    W.pre[lane] = incl - nc;
+    W.hj[lane] = hj;
+    W.a[lane] = make_float4(a.ar, a.az, a.na, a.Ea);
+    W.xy[lane] = make_float2(xi, yi);
+    W.cone[lane] = make_float2(lo, hi);
+    W.itj[lane] = itj;
+    W.i[lane] = i;
+    W.j[lane] = j;
+    W.fr[lane] = fr;
+    __syncwarp();
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t f = base + lane;
+        if (f < total) {
+            uint32_t o = 0;                       // the last lane whose candidates start <= f
+#pragma unroll
+            for (uint32_t step = 16; step; step >>= 1)
+                if (W.pre[o + step] <= f) o += step;
+            uint32_t off = f - W.pre[o], r = 0;
+            while (off >= W.qn[r][o]) off -= W.qn[r++][o];
+            const uint32_t q = W.q0[r][o] + off;
+            const float fz = b.gfree[q];
+            const float2 cone = W.cone[o];
+            if (fz >= cone.x && fz <= cone.y) {
+                const uint32_t k = b.gpos[q];
+                const uint4 it = W.itj[o];
+                const uint32_t rank = k >= it.z ? k - it.z : k + it.w;
+                if (rank < it.y) {
+                    const uint32_t B = it.x + rank;
+                    const float2 xy = W.xy[o];
+                    if (b.cell_out[B] == k &&
+                        ca_test<F64>(b, p, W.i[o], W.j[o], B, k, xy.x, xy.y, W.hj[o], W.a[o])) {
+                        const uint32_t sl = atomicAdd(&W.npass[o], 1u);
+                        if (sl < (uint32_t)kEdgeBuf) W.buf[sl][o] = B | W.fr[o];
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Edge lists of one cell per lane (all lanes in event e): npass passes of the lane's cell A,
+// buffered in W.buf when there are at most kEdgeBuf of them.  The warp's returning atomics are
+// issued together: the edge reservation, the root-list reservation (a root cell with edges is
+// listed), the frontier slots of the targets that start further pairs (taken before freshness
+// is known: a slot of a target already reached holds kNone) and the targets' reached marks.
+// Each lane writes its cell's list head and its buffered passes and clears the edge count of a
+// target it reached first.  Returns the lane's list start (absolute) and sets nw to the entries
+// that fit the region; a cell with more than kEdgeBuf passes is written by ca_rest.
+__device__ __forceinline__ uint32_t ca_append(const DevBatch &b, uint32_t e, bool root,
+                                              uint32_t A, uint32_t a_in, uint32_t a_out,
+                                              uint32_t npass, const CaWarp &W, uint32_t lane,
+                                              uint32_t &nw)
+{
+    const uint32_t FULL = 0xFFFFFFFFu;
+    nw = 0;
+    const uint32_t nbuf = npass <= (uint32_t)kEdgeBuf ? npass : 0u;
+    uint32_t nf = 0;
+    for (uint32_t t = 0; t < nbuf; ++t) nf += W.buf[t][lane] >> 31;
+    uint32_t incl = npass, finc = nf;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, incl, o);
+        const uint32_t u = __shfl_up_sync(FULL, finc, o);
+        if (lane >= (uint32_t)o) { incl += t; finc += u; }
+    }
+    const uint32_t tot = __shfl_sync(FULL, incl, 31), ftot = __shfl_sync(FULL, finc, 31);
+    if (tot == 0) return 0;
+    const uint32_t rm = root ? __ballot_sync(FULL, npass > 0) : 0u;
+    uint32_t base = 0, rbase = 0, fbase = 0;
+    if (lane == 0) {
+        base = atomicAdd(&b.cnt[C_EDGES * b.E + e], tot);
+        if (rm) rbase = atomicAdd(&b.cnt[C_ROOTS * b.E + e], __popc(rm));
+        if (ftot) fbase = atomicAdd(&b.cnt[C_FRONT * b.E + e], ftot);
+    }
+    uint32_t fresh = 0;                           // bit t: buffered target t reached first here
+    for (uint32_t t = 0; t < nbuf; ++t) {
+        const uint32_t B = W.buf[t][lane] & 0x7FFFFFFFu, bit = 1u << (B & 31u);
+        if (!(atomicOr(&b.live[B >> 5], bit) & bit)) fresh |= 1u << t;
+    }
+    base = __shfl_sync(FULL, base, 0);
+    rbase = __shfl_sync(FULL, rbase, 0) + __popc(rm & ((1u << lane) - 1u));
+    fbase = __shfl_sync(FULL, fbase, 0) + finc - nf;
+    if (npass == 0) return 0;
+    const uint32_t g0 = b.edge_off[e], cap = b.edge_off[e + 1] - g0;
+    const uint32_t my0 = base + incl - npass;
+    nw = my0 >= cap ? 0u : min(npass, cap - my0);
+    if (nw < npass) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+    if (root) {
+        if (rbase < cap) {
+            b.root_list[g0 + rbase] = A;
+            b.root_in[g0 + rbase] = a_in;
+        } else {
+            atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+        }
+    }
+    b.nbr_first[A] = g0 + my0;
+    b.nbr_n[A] = nw;
+    for (uint32_t t = 0; t < nbuf; ++t) {
+        const uint32_t Bf = W.buf[t][lane], B = Bf & 0x7FFFFFFFu;
+        const bool fr_t = (fresh >> t) & 1u;
+        if (t < nw) b.nbr[g0 + my0 + t] = B;
+        if (fr_t) b.nbr_n[B] = 0u;
+        if (Bf >> 31) {
+            if (fbase < cap) {
+                b.front_list[g0 + fbase] = fr_t ? B : kNone;
+                b.front_in[g0 + fbase] = a_out;
+            } else {
+                atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+            }
+            ++fbase;
+        }
+    }
+    return g0 + my0;
+}
+
+// Every pass of a cell with more than kEdgeBuf of them (rare), found again lane by lane in a
+// fixed order and written, the targets marked reached.  The cell is the segment a from hit i
+// (x, y = xi, yi) to its outer hit j (on layer Lj; hj, phij); its pairs start on Lj.
+template <bool F64>
+__device__ __noinline__ void ca_rest(const DevBatch &b, const DevParams &p, uint32_t e,
+                                     uint32_t i, uint32_t j, uint32_t Lj, float xi, float yi,
+                                     float4 hj, float phij, RZ32 a, uint32_t first, uint32_t nw)
+{
+    const bool j_root = (p.root_mask >> Lj) & 1u;
+    uint32_t t = 0;
+    for (uint32_t s = 0; s < p.n_out[Lj]; ++s) {
+        const uint32_t Lk = p.out_layer[Lj][s];
+        const bool fr = !j_root && p.n_out[Lk] > 0;
+        const uint4 itj = b.item[(size_t)j * kMaxOut + s];
+        uint32_t q0[kCaR], qn[kCaR];
+        float lo, hi;
+        const uint32_t nr = ca_ranges(b, p, e, Lk, hj, phij, a, itj, lo, hi, q0, qn);
+        for (uint32_t r = 0; r < nr; ++r)
+            for (uint32_t q = q0[r]; q < q0[r] + qn[r]; ++q) {
+                const float fz = b.gfree[q];
+                if (fz < lo || fz > hi) continue;
+                const uint32_t k = b.gpos[q];
+                const uint32_t rank = k >= itj.z ? k - itj.z : k + itj.w;
+                if (rank >= itj.y) continue;
+                const uint32_t B = itj.x + rank;
+                if (b.cell_out[B] != k ||
+                    !ca_test<F64>(b, p, i, j, B, k, xi, yi, hj,
+                                  make_float4(a.ar, a.az, a.na, a.Ea)))
+                    continue;
+                if (t < nw) b.nbr[first + t] = B;
+                mark_reached(b, e, B, j, fr);
+                ++t;
+            }
+    }
+}
+
+constexpr int kConnWarps = 8;
+constexpr int kStage = 256;     // out-cells of one junction staged per out-layer slot
+constexpr int kBins = 128;      // local bins of the free coordinate (multiple of 32)
+
+// Order-preserving int encoding of floats (for warp min / max reductions).
+__device__ __forceinline__ int ford(float f)
+{
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float funord(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
+
 
 // One warp per junction hit j.  For each out-layer slot, j's out-cells (j, k) are staged in
 // shared memory (k's coordinates) and counting-sorted by the free coordinate of k (z on barrel
@@ -573,6 +859,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                     // ---- one in-cell candidate per lane ----
                     const uint32_t c = c0 + lane;
                     uint32_t i = 0, q0 = 0, q1 = 0;
+                    float clo = -3.0e38f, chi = 3.0e38f;   // the cone (candidates outside skip)
                     uint4 itm = make_uint4(0u, 0u, 0u, 0u);
                     float4 hi = make_float4(0.f, 0.f, 0.f, 0.f);
                     RZ32 a{0.f, 0.f, 0.f, 0.f};
@@ -595,6 +882,8 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                                     b1 = b1 < 0 ? 0 : (b1 >= kBins ? kBins - 1 : b1);
                                     q0 = b0 ? bin[b0 - 1] : 0u;
                                     q1 = bin[b1];
+                                    clo = lo;
+                                    chi = hi_;
                                 }
                             }
                         }
@@ -617,6 +906,8 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                             const uint32_t t = sT[q];
                             B = f0 + t;
                             hk = sH[t];
+                            const float fc = disk ? hk.w : hk.z;
+                            if (fc < clo || fc > chi) continue;
                         } else {
                             B = f0 + q;
                             const uint32_t k = b.cell_out[B];
@@ -700,6 +991,8 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
                                 const uint32_t t = sT[q];
                                 B = f0 + t;
                                 hk = sH[t];
+                                const float fc = disk ? hk.w : hk.z;
+                                if (fc < clo || fc > chi) continue;
                             } else {
                                 B = f0 + q;
                                 const uint32_t k = b.cell_out[B];
@@ -721,8 +1014,9 @@ __global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevP
     }
 }
 
+
 // Per-event prefix of the hits on the layers of layer_mask (the junctions of a dense CA level):
-// jbase[e] = junctions of events before e, jbase[E] = all.  One CTA; each thread takes a run of
+// jbase[e] = those of events before e, jbase[E] = all.  One CTA; each thread takes a run of
 // consecutive events.
 __global__ void __launch_bounds__(1024) k_jbase(DevBatch b, DevParams p, uint32_t layer_mask)
 {
@@ -775,37 +1069,26 @@ void launch_connect(const DevBatch &b, const DevParams &p, uint32_t layer_mask, 
         k_connect<false><<<(unsigned)blocks, kConnWarps * 32, 0, s>>>(b, p, layer_mask);
 }
 
-// Sparse CA pass over the frontier: cells B = (j, k) that were reached (have an in-edge), are not
-// root cells, and whose outer hit k lies on a layer of layer_mask.  Their out-edges go to the
-// out-cells C = (k, l) of every pair starting on k's layer that pass the triplet cut.  Each warp
-// takes 32 consecutive frontier entries (one chunk of 256 entries per CTA, all of one event): the
-// lanes load their cells' hits together, then the warp tests the cells' out-entries one cell at
-// a time, 32 entries per step (failed candidates skipped), collecting the passes in shared
-// memory grouped by cell; one atomic reserves the edge lists of all 32 cells, which are
-// contiguous and in the same order, so the warp copies them with coalesced stores.  A cell whose
-// passes do not fit the buffer is redone on its own.  Reached out-cells join the frontier.
-constexpr int kFrontBuf = 256;
-constexpr int kFrontU = 3;      // entries per lane whose loads are issued together
-
+// Sparse CA pass of one level over the frontier: cells B = (j, k) that were reached (have an
+// in-edge), are not root cells, and whose outer hit k lies on a junction layer of the level.
+// One lane per frontier entry (chunks of 256 entries, all of one event per CTA): for every pair
+// starting on k's layer the warp looks up the out-cells (k, l) that pass the triplet cut
+// (ca_warp_pair), then appends the cells' edge lists; reached out-cells join the frontier.
 template <bool F64>
-__global__ void __launch_bounds__(256, 4) k_connect_front(DevBatch b, DevParams p, uint32_t total,
-                                                          uint32_t layer_mask)
+__global__ void __launch_bounds__(256, PXR_CA_MINB) k_ca_front(DevBatch b, DevParams p,
+                                                               uint32_t total, uint32_t layer_mask)
 {
-    __shared__ uint32_t s_pass[8][kFrontBuf];
-    const uint32_t FULL = 0xFFFFFFFFu;
-    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, lt = (1u << lane) - 1u;
-    uint32_t *buf = s_pass[wid];
+    __shared__ CaWarp s_w[8];
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    CaWarp &W = s_w[wid];
     const uint32_t n_chunks = total / kChunk;
     for (uint32_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
         const uint32_t e = b.edge_chunk[ch];
         const uint32_t x0 = b.edge_off[e];
         const uint32_t nf = min(b.front_snap[e], b.edge_off[e + 1] - x0);
         if (ch * kChunk - x0 >= nf) continue;                      // uniform over the CTA
-        // ---- this warp's 32 entries, one cell per lane ----
-        const uint32_t x = ch * kChunk + wid * 32u + lane;
-        uint32_t B = 0, j = 0, k = 0, Lk = 0;
-        float4 hj = make_float4(0.f, 0.f, 0.f, 0.f), hk = hj;
-        uint4 it0 = make_uint4(0u, 0u, 0u, 0u);                    // k's first pair's entries
+        const uint32_t x = ch * kChunk + threadIdx.x;
+        uint32_t B = kNone, j = 0, k = 0, Lk = 0;
         bool valid = x - x0 < nf;
         if (valid) {
             B = b.front_list[x];
@@ -814,125 +1097,37 @@ __global__ void __launch_bounds__(256, 4) k_connect_front(DevBatch b, DevParams 
         }
         if (valid) {
             k = b.cell_out[B];
-            hj = b.hs[j];
-            hk = b.hs[k];
-            it0 = b.item[(size_t)k * kMaxOut];
             Lk = b.hmeta[k] >> kLocalBits;
             valid = (layer_mask >> Lk) & 1u;
         }
-        uint32_t my_cnt = 0, redo = 0;
-        uint32_t nbuf = 0;                                         // warp-uniform
-        for (uint32_t m = __ballot_sync(FULL, valid); m; m &= m - 1) {
-            const int q = __ffs(m) - 1;
-            const uint32_t jq = __shfl_sync(FULL, j, q), kq = __shfl_sync(FULL, k, q);
-            const uint32_t Lq = __shfl_sync(FULL, Lk, q);
-            const float4 hjq = make_float4(__shfl_sync(FULL, hj.x, q), __shfl_sync(FULL, hj.y, q),
-                                           __shfl_sync(FULL, hj.z, q), __shfl_sync(FULL, hj.w, q));
-            const float4 hkq = make_float4(__shfl_sync(FULL, hk.x, q), __shfl_sync(FULL, hk.y, q),
-                                           __shfl_sync(FULL, hk.z, q), __shfl_sync(FULL, hk.w, q));
-            const RZ32 a = rz32(hjq, hkq);
-            const bool k_root = (p.root_mask >> Lq) & 1u;
-            const uint32_t start = nbuf;
-            uint32_t cnt = 0;
-            bool fits = true;
-            for (uint32_t s = 0; s < p.n_out[Lq]; ++s) {
-                const uint4 it = s ? b.item[(size_t)kq * kMaxOut + s]
-                                   : make_uint4(__shfl_sync(FULL, it0.x, q),
-                                                __shfl_sync(FULL, it0.y, q), 0u, 0u);
-                const bool front = !k_root && p.n_out[p.out_layer[Lq][s]] > 0;
-                for (uint32_t c0 = 0; c0 < it.y; c0 += 32u * kFrontU) {
-                    // all loads of the step first: entries, then their outer hits
-                    uint32_t l[kFrontU];
-                    float4 hl[kFrontU];
-#pragma unroll
-                    for (int u = 0; u < kFrontU; ++u) {
-                        const uint32_t c = c0 + 32u * u + lane;
-                        l[u] = c < it.y ? b.cell_out[it.x + c] : kNone;
-                    }
-#pragma unroll
-                    for (int u = 0; u < kFrontU; ++u)
-                        hl[u] = l[u] != kNone ? b.hs[l[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                    for (int u = 0; u < kFrontU; ++u) {
-                        if (c0 + 32u * u >= it.y) break;                   // uniform
-                        const uint32_t C = it.x + c0 + 32u * u + lane;
-                        const bool pass = l[u] != kNone &&
-                            triplet_test<F64>(b, p, jq, kq, C, hjq.x, hjq.y, hkq, hl[u], a);
-                        const uint32_t pm = __ballot_sync(FULL, pass);
-                        if (pass) {
-                            const uint32_t idx = start + cnt + __popc(pm & lt);
-                            if (idx < (uint32_t)kFrontBuf) buf[idx] = C;
-                            mark_reached(b, e, C, kq, front);
-                        }
-                        cnt += __popc(pm);
-                    }
-                }
-            }
-            if (start + cnt > (uint32_t)kFrontBuf) fits = false;
-            if (lane == (uint32_t)q) {
-                my_cnt = fits ? cnt : 0u;
-                redo = fits ? 0u : cnt;
-            }
-            if (fits) nbuf += cnt;
+        float4 hj = make_float4(0.f, 0.f, 0.f, 0.f), hk = hj;
+        float phik = 0.f;
+        RZ32 a{0.f, 0.f, 0.f, 0.f};
+        uint32_t nout = 0;
+        bool k_root = false;
+        if (valid) {
+            hj = b.hs[j];
+            hk = b.hs[k];
+            phik = b.hphi[k];
+            a = rz32(hj, hk);
+            nout = p.n_out[Lk];
+            k_root = (p.root_mask >> Lk) & 1u;
         }
-        // ---- one reservation for the buffered lists (in lane order = buffer order) ----
-        uint32_t incl = my_cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(FULL, incl, o);
-            if (lane >= (uint32_t)o) incl += t;
+        W.npass[lane] = 0;
+        const uint32_t nmax = __reduce_max_sync(0xFFFFFFFFu, nout);
+        for (uint32_t t = 0; t < nmax; ++t) {
+            const bool act = t < nout;
+            const uint32_t Ll = act ? p.out_layer[Lk][t] : 0u;
+            const uint32_t fr = act && !k_root && p.n_out[Ll] > 0 ? 0x80000000u : 0u;
+            const uint4 itk = act ? b.item[(size_t)k * kMaxOut + t] : make_uint4(0, 0, 0, 0);
+            ca_warp_pair<F64>(b, p, e, W, lane, act, Ll, j, k, hj.x, hj.y, hk, phik, a, itk, fr);
         }
-        uint32_t base = 0;
-        if (lane == 0 && nbuf) base = atomicAdd(&b.cnt[C_EDGES * b.E + e], nbuf);
-        base = __shfl_sync(FULL, base, 0);
-        const uint32_t cap = b.edge_off[e + 1] - x0;
-        const uint32_t nw = base >= cap ? 0u : min(nbuf, cap - base);
-        if (nw < nbuf && lane == 0) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
         __syncwarp();
-        for (uint32_t t = lane; t < nw; t += 32) b.nbr[x0 + base + t] = buf[t];
-        if (my_cnt) {
-            const uint32_t o = incl - my_cnt;                      // offset in the warp's range
-            b.nbr_first[B] = x0 + base + o;
-            b.nbr_n[B] = o >= nw ? 0u : min(my_cnt, nw - o);
-        }
-        // ---- cells whose passes did not fit: their own reservation and a second sweep ----
-        for (uint32_t m = __ballot_sync(FULL, redo > 0); m; m &= m - 1) {
-            const int q = __ffs(m) - 1;
-            const uint32_t Bq = __shfl_sync(FULL, B, q), n = __shfl_sync(FULL, redo, q);
-            const uint32_t jq = __shfl_sync(FULL, j, q), kq = __shfl_sync(FULL, k, q);
-            const uint32_t Lq = __shfl_sync(FULL, Lk, q);
-            const float4 hjq = make_float4(__shfl_sync(FULL, hj.x, q), __shfl_sync(FULL, hj.y, q),
-                                           __shfl_sync(FULL, hj.z, q), __shfl_sync(FULL, hj.w, q));
-            const float4 hkq = make_float4(__shfl_sync(FULL, hk.x, q), __shfl_sync(FULL, hk.y, q),
-                                           __shfl_sync(FULL, hk.z, q), __shfl_sync(FULL, hk.w, q));
-            const RZ32 a = rz32(hjq, hkq);
-            uint32_t rb = 0;
-            if (lane == 0) rb = atomicAdd(&b.cnt[C_EDGES * b.E + e], n);
-            rb = __shfl_sync(FULL, rb, 0);
-            const uint32_t rw = rb >= cap ? 0u : min(n, cap - rb);
-            if (lane == 0) {
-                if (rw < n) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
-                b.nbr_first[Bq] = x0 + rb;
-                b.nbr_n[Bq] = rw;
-            }
-            uint32_t run = 0;
-            for (uint32_t s = 0; s < p.n_out[Lq] && run < rw; ++s) {
-                const uint4 it = b.item[(size_t)kq * kMaxOut + s];
-                for (uint32_t c0 = 0; c0 < it.y && run < rw; c0 += 32) {
-                    const uint32_t C = it.x + c0 + lane;
-                    bool pass = false;
-                    if (c0 + lane < it.y) {
-                        const uint32_t l = b.cell_out[C];
-                        if (l != kNone)
-                            pass = triplet_test<F64>(b, p, jq, kq, C, hjq.x, hjq.y, hkq, b.hs[l], a);
-                    }
-                    const uint32_t pm = __ballot_sync(FULL, pass);
-                    const uint32_t idx = run + __popc(pm & lt);
-                    if (pass && idx < rw) b.nbr[x0 + rb + idx] = C;
-                    run += __popc(pm);
-                }
-            }
-        }
+        const uint32_t npass = W.npass[lane];
+        uint32_t nw;
+        const uint32_t first = ca_append(b, e, false, B, j, k, npass, W, lane, nw);
+        if (npass > (uint32_t)kEdgeBuf)
+            ca_rest<F64>(b, p, e, j, k, Lk, hj.x, hj.y, hk, phik, a, first, nw);
         __syncwarp();
     }
 }
@@ -945,9 +1140,9 @@ void launch_connect_front(const DevBatch &b, const DevParams &p, uint32_t total,
     if (chunks == 0) return;
     const uint32_t grid = chunks < cap ? chunks : cap;
     if (p.cut_mode == CUT_FP64)
-        k_connect_front<true><<<grid, 256, 0, s>>>(b, p, total, layer_mask);
+        k_ca_front<true><<<grid, 256, 0, s>>>(b, p, total, layer_mask);
     else
-        k_connect_front<false><<<grid, 256, 0, s>>>(b, p, total, layer_mask);
+        k_ca_front<false><<<grid, 256, 0, s>>>(b, p, total, layer_mask);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1128,6 +1323,72 @@ __global__ void k_out_scan(DevBatch b)
 void launch_out_scan(const DevBatch &b, cudaStream_t s)
 {
     k_out_scan<<<1, 1024, 0, s>>>(b);
+}
+
+// Caller index of slot q of ntuplet t, kNone past its hits (the padding of the canonical order).
+__device__ __forceinline__ uint32_t tup_caller(const DevBatch &b, uint32_t t, int q)
+{
+    return q < b.tup_n[t] ? b.hmeta[b.tup_hits[(size_t)t * kMaxHits + q]] & kLocalMask : kNone;
+}
+
+// Canonical order of each event's kept ntuplets: lexicographic by their hits' caller indices
+// (unused slots as kNone), so that a result does not depend on the batch or on the order in
+// which the walk found the ntuplets.  A counting sort by the first hit (per-hit counters of the
+// event), then each bucket (the ntuplets sharing a first hit: a few) by insertion on the
+// remaining hits; tup_list receives the order, in which the fit writes the tracks.  One CTA per
+// event.
+__global__ void __launch_bounds__(1024) k_canon(DevBatch b)
+{
+    __shared__ uint32_t s_warp[32];
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    for (uint32_t e = blockIdx.x; e < b.E; e += gridDim.x) {
+        const uint32_t h0 = b.hit_off[e], nh = b.hit_off[e + 1] - h0;
+        const uint32_t t0 = b.tup_off[e];
+        const uint32_t n = b.out_evt[e + 1] - b.out_evt[e];
+        if (n < 2) continue;                                       // uniform over the CTA
+        uint32_t *cnt = b.canon_cnt + h0;
+        uint32_t *tmp = b.tup_tmp + t0;
+        for (uint32_t c = tid; c < nh; c += nt) cnt[c] = 0;
+        __syncthreads();
+        for (uint32_t k = tid; k < n; k += nt) atomicAdd(&cnt[tup_caller(b, b.tup_list[t0 + k], 0)], 1u);
+        __syncthreads();
+        block_exclusive_scan(cnt, nh, s_warp);
+        for (uint32_t k = tid; k < n; k += nt) {
+            const uint32_t t = b.tup_list[t0 + k];
+            tmp[atomicAdd(&cnt[tup_caller(b, t, 0)], 1u)] = t;
+        }
+        __syncthreads();
+        // cnt[c] is now the end of bucket c
+        for (uint32_t c = tid; c < nh; c += nt) {
+            const uint32_t lo = c ? cnt[c - 1] : 0u, hi = cnt[c];
+            for (uint32_t x = lo + 1; x < hi; ++x) {
+                const uint32_t t = tmp[x];
+                uint32_t y = x;
+                while (y > lo) {
+                    const uint32_t u = tmp[y - 1];
+                    int cmp = 0;
+                    for (int q = 1; q < kMaxHits && cmp == 0; ++q) {
+                        const uint32_t a = tup_caller(b, u, q), v = tup_caller(b, t, q);
+                        cmp = a < v ? -1 : (a > v ? 1 : 0);
+                    }
+                    if (cmp <= 0) break;
+                    tmp[y] = u;
+                    --y;
+                }
+                tmp[y] = t;
+            }
+        }
+        __syncthreads();
+        for (uint32_t k = tid; k < n; k += nt) b.tup_list[t0 + k] = tmp[k];
+        __syncthreads();
+    }
+}
+
+void launch_canon(const DevBatch &b, cudaStream_t s, int sms)
+{
+    const uint32_t grid = b.E < (uint32_t)sms * 2 ? b.E : (uint32_t)sms * 2;
+    if (grid == 0) return;
+    k_canon<<<grid, 1024, 0, s>>>(b);
 }
 
 }  // namespace pxr

@@ -22,53 +22,45 @@ __device__ __forceinline__ uint32_t phi_bin(float phi, const DevParams &p)
     return (uint32_t)(b >= (int)p.nb ? (int)p.nb - 1 : b);
 }
 
-// Block-wide exclusive scan of s[0..n) in place; returns the total.  blockDim.x is a multiple
-// of 32 and at most 1024.
-__device__ uint32_t block_exclusive_scan(uint32_t *s, uint32_t n, uint32_t *warp_tot)
+// Order-preserving int encoding of floats (min / max by integer atomics).
+__device__ __forceinline__ int ford_s(float f)
 {
-    const uint32_t tid = threadIdx.x, nt = blockDim.x;
-    const uint32_t per = (n + nt - 1) / nt;
-    const uint32_t b0 = min(n, tid * per), b1 = min(n, b0 + per);
-    uint32_t local = 0;
-    for (uint32_t k = b0; k < b1; ++k) local += s[k];
-    // inclusive scan of `local` across the block
-    const uint32_t lane = tid & 31u, wid = tid >> 5;
-    uint32_t v = local;
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
-        if (lane >= (uint32_t)o) v += t;
-    }
-    if (lane == 31) warp_tot[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        uint32_t nw = nt >> 5;
-        uint32_t w = lane < nw ? warp_tot[lane] : 0u;
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t t = __shfl_up_sync(0xFFFFFFFFu, w, o);
-            if (lane >= (uint32_t)o) w += t;
-        }
-        if (lane < nw) warp_tot[lane] = w;     // inclusive warp prefix
-    }
-    __syncthreads();
-    uint32_t excl = v - local + (wid ? warp_tot[wid - 1] : 0u);
-    uint32_t total = warp_tot[(nt >> 5) - 1];
-    for (uint32_t k = b0; k < b1; ++k) {
-        uint32_t c = s[k];
-        s[k] = excl;
-        excl += c;
-    }
-    __syncthreads();
-    return total;
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float funord_s(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
+
+// Grid cell of a sorted hit: coarse azimuth bin (the fine bin scaled down, so a fine-bin window
+// maps onto whole coarse bins) and the bin of its free coordinate (z on a barrel layer, the
+// radius on a disk) over the layer's range in the event.
+__device__ __forceinline__ uint32_t grid_key(uint32_t g, uint32_t fine, float f, float4 gl,
+                                             const DevParams &p)
+{
+    const uint32_t pc = fine * p.gphi / p.nb;
+    int zc = (int)floorf((f - gl.x) * gl.y);
+    zc = zc < 0 ? 0 : (zc >= (int)p.gz ? (int)p.gz - 1 : zc);
+    return (g * p.gphi + pc) * p.gz + (uint32_t)zc;
 }
 
+// One CTA per event.  1) (layer, phi bin) histogram, 2) scan (bucket starts), 3) scatter of the
+// sorted hit records; then, when the batch carries a hit grid (the CA stage's lookup), 4) each
+// layer's range of the free coordinate (binning) and of the fixed one (the r-z cone), 5) grid
+// histogram, 6) scan, 7) scatter of the sorted positions and free coordinates by grid cell.
+// The shared counters of steps 1-3 are reused for steps 5-7.
 __global__ void __launch_bounds__(1024) k_sort(DevBatch b, DevParams p)
 {
     extern __shared__ uint32_t s_cnt[];
     __shared__ uint32_t s_warp[32];
+    __shared__ int s_lay[kMaxLayers][4];    // free min, free max, fixed min, fixed max (ordered)
     const uint32_t nk = p.n_keys;
+    const bool grid = b.gpos != nullptr;
     for (uint32_t e = blockIdx.x; e < b.E; e += gridDim.x) {
         const uint32_t h0 = b.hit_off[e], n = b.hit_off[e + 1] - h0;
         for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) s_cnt[k] = 0;
+        if (threadIdx.x < kMaxLayers * 4) {
+            const uint32_t l = threadIdx.x >> 2, q = threadIdx.x & 3u;
+            s_lay[l][q] = (q & 1u) ? ford_s(-3.0e38f) : ford_s(3.0e38f);
+        }
         __syncthreads();
         bool bad = false;
         for (uint32_t h = threadIdx.x; h < n; h += blockDim.x) {
@@ -99,12 +91,75 @@ __global__ void __launch_bounds__(1024) k_sort(DevBatch b, DevParams p)
             b.hphi[pos] = phi;
         }
         __syncthreads();
+        if (!grid) continue;
+        // ---- hit grid (the grid layers' hits, each layer contiguous in the sorted order) ----
+        for (uint32_t L = 0; L < p.n_layers; ++L) {
+            if (p.glidx[L] == 0xFF) continue;
+            const bool disk = p.is_disk[L];
+            int m0 = ford_s(3.0e38f), m1 = ford_s(-3.0e38f), m2 = m0, m3 = m1;
+            for (uint32_t t = bk[L * p.nb] + threadIdx.x; t < bk[(L + 1) * p.nb]; t += blockDim.x) {
+                const float4 h = b.hs[t];
+                const int fr = ford_s(disk ? h.w : h.z), fx = ford_s(disk ? h.z : h.w);
+                m0 = min(m0, fr);
+                m1 = max(m1, fr);
+                m2 = min(m2, fx);
+                m3 = max(m3, fx);
+            }
+            m0 = __reduce_min_sync(0xFFFFFFFFu, m0);
+            m1 = __reduce_max_sync(0xFFFFFFFFu, m1);
+            m2 = __reduce_min_sync(0xFFFFFFFFu, m2);
+            m3 = __reduce_max_sync(0xFFFFFFFFu, m3);
+            if ((threadIdx.x & 31u) == 0) {
+                atomicMin(&s_lay[L][0], m0);
+                atomicMax(&s_lay[L][1], m1);
+                atomicMin(&s_lay[L][2], m2);
+                atomicMax(&s_lay[L][3], m3);
+            }
+        }
+        __syncthreads();
+        const uint32_t gk = p.n_glayers * p.gphi * p.gz;
+        float4 *gl = b.glay + (size_t)e * p.n_glayers;
+        if (threadIdx.x < p.n_layers && p.glidx[threadIdx.x] != 0xFF) {
+            const uint32_t l = threadIdx.x;
+            const float f0 = funord_s(s_lay[l][0]), f1 = funord_s(s_lay[l][1]);
+            const float scale = f1 > f0 ? (float)p.gz / (f1 - f0) : 0.f;
+            gl[p.glidx[l]] = make_float4(f0, scale, funord_s(s_lay[l][2]), funord_s(s_lay[l][3]));
+        }
+        for (uint32_t k = threadIdx.x; k < gk; k += blockDim.x) s_cnt[k] = 0;
+        __syncthreads();
+        // the grid layers' hits, layer by layer (positions [bk[L nb], bk[(L + 1) nb]))
+        auto for_grid_hits = [&](auto &&fn) {
+            for (uint32_t L = 0; L < p.n_layers; ++L) {
+                const uint32_t g = p.glidx[L];
+                if (g == 0xFF) continue;
+                const float4 glg = gl[g];
+                for (uint32_t t = bk[L * p.nb] + threadIdx.x; t < bk[(L + 1) * p.nb];
+                     t += blockDim.x) {
+                    const float4 h = b.hs[t];
+                    const float f = p.is_disk[L] ? h.w : h.z;
+                    fn(t, f, grid_key(g, phi_bin(b.hphi[t], p), f, glg, p));
+                }
+            }
+        };
+        for_grid_hits([&](uint32_t, float, uint32_t key) { atomicAdd(&s_cnt[key], 1u); });
+        __syncthreads();
+        const uint32_t gtotal = block_exclusive_scan(s_cnt, gk, s_warp);
+        uint32_t *go = b.gofs + (size_t)e * (gk + 1);
+        for (uint32_t k = threadIdx.x; k < gk; k += blockDim.x) go[k] = h0 + s_cnt[k];
+        if (threadIdx.x == 0) go[gk] = h0 + gtotal;
+        __syncthreads();
+        for_grid_hits([&](uint32_t t, float f, uint32_t key) {
+            const uint32_t q = h0 + atomicAdd(&s_cnt[key], 1u);
+            b.gpos[q] = t;
+            b.gfree[q] = f;
+        });
+        __syncthreads();
     }
 }
 
 cudaError_t init_kernels()
 {
-    // up to 16 layers x 2048 bins of 4-byte counters
+    // up to 16 layers x 2048 bins of 4-byte counters (the hit grid's counters are fewer)
     cudaError_t e = cudaFuncSetAttribute(k_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kMaxLayers * 2048 * (int)sizeof(uint32_t));
     if (e != cudaSuccess) return e;
@@ -116,7 +171,9 @@ void launch_sort(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms)
     const uint32_t cap = (uint32_t)sms * p.grid_per_sm[0];
     const uint32_t grid = b.E < cap ? b.E : cap;
     if (grid == 0) return;
-    k_sort<<<grid, 1024, p.n_keys * sizeof(uint32_t), s>>>(b, p);
+    const uint32_t gk = b.gpos ? p.n_glayers * p.gphi * p.gz : 0u;
+    const size_t smem = (size_t)(p.n_keys > gk ? p.n_keys : gk) * sizeof(uint32_t);
+    k_sort<<<grid, 1024, smem, s>>>(b, p);
 }
 
 // Per-event, per-layer hit counts (used once to size a plan's per-event capacities).

@@ -38,7 +38,7 @@ constexpr uint8_t kQGood = 1u, kQKept = 2u;
 enum Flag : uint32_t { F_CELLS = 1u, F_EDGES = 2u, F_TUPLES = 4u, F_LAYER = 8u, F_VERTS = 16u };
 
 enum CutMode : uint32_t { CUT_FP64 = 0, CUT_FP32 = 1 };
-enum FitMode : uint32_t { FIT_FP64 = 0, FIT_MIXED = 1, FIT_FP32 = 2, FIT_RIEMANN = 3 };
+enum FitMode : uint32_t { FIT_FP64 = 0, FIT_MIXED = 1, FIT_FP32 = 2, FIT_RIEMANN = 3, FIT_SPLIT = 4 };
 
 struct DevParams {
     uint32_t n_layers;
@@ -61,6 +61,11 @@ struct DevParams {
     float dca32;                        // dca_cut rounded to float
     float tan_win;                      // tan(asin(theta_cut) + margin); inf when theta_cut >= 1
     uint32_t grid_per_sm[6];            // CTAs per SM at most, per stage (sort ... fit)
+    uint32_t gphi, gz;                  // hit grid: coarse azimuth bins (bin = fine bin * gphi
+                                        //   / nb) and bins of the free coordinate per layer
+    uint32_t n_glayers;                 // layers in the grid: the out-layers of the pairs that
+    uint8_t glidx[kMaxLayers];          //   start on a sparse CA junction layer; glidx = the
+                                        //   layer's index among them, 0xFF for the others
     // CA levels: junction layers (with in- and out-pairs) ordered so that every pair's inner
     // layer comes first; per level the junction layers whose in-cells include root cells (dense
     // pass) and those with in-cells from non-root layers (sparse pass over reached cells)
@@ -92,6 +97,15 @@ struct DevBatch {
     double *r64;                        // [N] sorted radii, FP64
     uint32_t *hmeta;                    // [N] layer << 24 | local caller index
     float *hphi;                        // [N] atan2f(y, x) of the sorted hits (the binned value)
+    // hit grid of the sparse CA pass: per event and grid layer (index g = glidx[layer]), coarse
+    // azimuth bins x bins of the free coordinate (z on barrel layers, r on disks);
+    // gofs[e][(g * gphi + pc) * gz + zc] is the start of the cell's hits in gpos / gfree
+    // (absolute, events back to back, one end entry per event); glay[e][g] = (free min, free
+    // bin scale, fixed min, fixed max)
+    uint32_t *gofs;                     // [E * (n_glayers * gphi * gz + 1)]
+    uint32_t *gpos;                     // [N] sorted hit positions of grid layers, by grid cell
+    float *gfree;                       // [N] their free coordinates
+    float4 *glay;                       // [E * n_glayers]
     // event of a work chunk: cells, edges and ntuplets by 256-entry chunk; hits by 32-hit chunk
     // (first event of the chunk, bit 31 set when the chunk holds the start of a later event)
     const uint32_t *cell_chunk, *edge_chunk, *tup_chunk, *hit_chunk;
@@ -128,6 +142,9 @@ struct DevBatch {
     uint32_t *tup_first;                // [tuples] root cell
     uint32_t *tup_rank;                 // [tuples] output slot within the event, kNone = dropped
     uint32_t *tup_list;                 // [tuples] per event: kept ntuplets in output order
+                                        //   (canonical: by their hits' caller indices)
+    uint32_t *tup_tmp;                  // [tuples] scratch of the canonical ordering
+    uint32_t *canon_cnt;                // [N] per-hit counters of the canonical ordering
     // compact output, events back to back
     uint32_t *out_evt;                  // [E+1]
     uint32_t out_cap;                   // output slots (= tuple capacity)
@@ -168,6 +185,45 @@ __device__ __forceinline__ uint32_t find_event(const uint32_t *__restrict__ off,
     return lo;
 }
 
+// Block-wide exclusive scan of s[0..n) in place; returns the total.  blockDim.x is a multiple
+// of 32 and at most 1024.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t *s, uint32_t n, uint32_t *warp_tot)
+{
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t per = (n + nt - 1) / nt;
+    const uint32_t b0 = min(n, tid * per), b1 = min(n, b0 + per);
+    uint32_t local = 0;
+    for (uint32_t k = b0; k < b1; ++k) local += s[k];
+    // inclusive scan of `local` across the block
+    const uint32_t lane = tid & 31u, wid = tid >> 5;
+    uint32_t v = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        if (lane >= (uint32_t)o) v += t;
+    }
+    if (lane == 31) warp_tot[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t nw = nt >> 5;
+        uint32_t w = lane < nw ? warp_tot[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xFFFFFFFFu, w, o);
+            if (lane >= (uint32_t)o) w += t;
+        }
+        if (lane < nw) warp_tot[lane] = w;     // inclusive warp prefix
+    }
+    __syncthreads();
+    uint32_t excl = v - local + (wid ? warp_tot[wid - 1] : 0u);
+    uint32_t total = warp_tot[(nt >> 5) - 1];
+    for (uint32_t k = b0; k < b1; ++k) {
+        uint32_t c = s[k];
+        s[k] = excl;
+        excl += c;
+    }
+    __syncthreads();
+    return total;
+}
+
 // One-time kernel attributes (large dynamic shared memory of the sort kernel).
 cudaError_t init_kernels();
 cudaError_t init_fit_kernels();     // (called by init_kernels)
@@ -187,6 +243,7 @@ void launch_ntuplets(const DevBatch &b, const DevParams &p, uint32_t edge_total,
 void launch_select(const DevBatch &b, const DevParams &p, uint32_t tup_total, cudaStream_t s,
                    int sms);
 void launch_out_scan(const DevBatch &b, cudaStream_t s);
+void launch_canon(const DevBatch &b, cudaStream_t s, int sms);
 void launch_fit(const DevBatch &b, const DevParams &p, uint32_t tup_total, cudaStream_t s,
                 int sms);
 void launch_keep(const DevBatch &b, const DevParams &p, uint32_t tup_total, cudaStream_t s,

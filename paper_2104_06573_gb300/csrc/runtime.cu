@@ -112,7 +112,7 @@ static int check_params(const pxr_params *p, DevParams *d)
     if (p->min_hits < 2 || p->max_hits > PXR_MAX_HITS || p->min_hits > p->max_hits)
         return fail(PXR_EINVAL, "need 2 <= min_hits <= max_hits <= 6");
     if (p->cut_mode > PXR_CUT_FP32) return fail(PXR_EINVAL, "bad cut_mode");
-    if (p->fit_mode > PXR_FIT_RIEMANN) return fail(PXR_EINVAL, "bad fit_mode");
+    if (p->fit_mode > PXR_FIT_SPLIT) return fail(PXR_EINVAL, "bad fit_mode");
     if (!(p->phi_window > 0.0 && p->phi_window <= 0.5)) return fail(PXR_EINVAL, "phi_window must be in (0, 0.5]");
     if (!(std::fabs(p->cos_phi_window - std::cos(p->phi_window)) < 1e-12))
         return fail(PXR_EINVAL, "cos_phi_window must equal cos(phi_window)");
@@ -200,6 +200,19 @@ static int check_params(const pxr_params *p, DevParams *d)
             else d->level_sparse[level[l]] |= 1u << l;
         }
     }
+    // hit grid of the sparse CA pass: the out-layers of the pairs that start on its junction
+    // layers; 32 coarse azimuth bins, free-coordinate bins up to 1024 per layer with at most
+    // 32768 cells per event (its counters share the sort's shared memory)
+    uint32_t gmask = 0;
+    for (uint32_t lv = 1; lv <= d->n_levels; ++lv)
+        for (uint32_t l = 0; l < p->n_layers; ++l)
+            if ((d->level_sparse[lv] >> l) & 1u)
+                for (uint32_t q = 0; q < d->n_out[l]; ++q) gmask |= 1u << d->out_layer[l][q];
+    for (uint32_t l = 0; l < kMaxLayers; ++l)
+        d->glidx[l] = (gmask >> l) & 1u ? (uint8_t)d->n_glayers++ : (uint8_t)0xFF;
+    d->gphi = 32;
+    d->gz = 1024;
+    while (d->gz > 8 && d->n_glayers * d->gphi * d->gz > 32768u) d->gz >>= 1;
     // launch shapes: CTAs per SM at most (the kernels stride over their work)
     static const uint32_t kGridDefault[PXR_STAGES] = {4, 16, 16, 8, 8, 8};
     for (int k = 0; k < PXR_STAGES; ++k)
@@ -261,9 +274,9 @@ struct PlanOffsets {
     size_t x, y, z, layer, hit_off, cell_off, edge_off, tup_off, cell_chunk, edge_chunk, tup_chunk,
         hit_chunk,
         head_end;
-    size_t cnt, bkt, hs, r64, hmeta, hphi, item, cell_out,
+    size_t cnt, bkt, hs, r64, hmeta, hphi, gofs, gpos, gfree, glay, item, cell_out,
         nbr_first,
-        nbr_n, nbr, mindepth, root_list, root_in, live, front_list, front_in, front_snap, jbase, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, out_evt, o_nh,
+        nbr_n, nbr, mindepth, root_list, root_in, live, front_list, front_in, front_snap, jbase, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, tup_tmp, canon_cnt, out_evt, o_nh,
         o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status, o_ql, best, o_cov, o_vtx,
         v_z, v_err, v_pt2, v_n;
     size_t total;
@@ -294,6 +307,10 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.r64 = L.add(8 * N);
     o.hmeta = L.add(4 * N);
     o.hphi = L.add(4 * N);
+    o.gofs = L.add(dp.n_glayers ? 4 * (size_t)E * ((size_t)dp.n_glayers * dp.gphi * dp.gz + 1) : 0);
+    o.gpos = L.add(dp.n_glayers ? 4 * N : 0);
+    o.gfree = L.add(dp.n_glayers ? 4 * N : 0);
+    o.glay = L.add(16 * (size_t)E * dp.n_glayers);
 
     o.item = L.add(16 * N * kMaxOut);
     o.cell_out = L.add(4 * C);
@@ -314,6 +331,8 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.tup_first = L.add(4 * T);
     o.tup_rank = L.add(4 * T);
     o.tup_list = L.add(4 * T);
+    o.tup_tmp = L.add(4 * T);
+    o.canon_cnt = L.add(4 * N);
     o.out_evt = L.add(4 * (E + 1));
     o.o_nh = L.add(T);
     o.o_hits = L.add(4 * T * kMaxHits);
@@ -416,6 +435,66 @@ struct Arena {
 // ------------------------------------------------------------------------------------------
 // context and plan
 // ------------------------------------------------------------------------------------------
+// Pinned host memory of the serving path: submissions' hits (copied from the caller once,
+// then sent to the device straight from here) and batches' results (received from the device
+// and read by the fetches in place).  Blocks are reused (pinned allocation is slow and
+// synchronising), kept by size class (powers of two from 64 KiB), freed with the context.
+struct PinnedPool {
+    std::mutex mu;
+    std::multimap<size_t, char *> free_;
+    std::vector<char *> all;
+    char *get(size_t bytes, size_t &got)
+    {
+        size_t c = size_t(1) << 16;
+        while (c < bytes) c <<= 1;
+        {
+            std::lock_guard<std::mutex> g(mu);
+            auto it = free_.lower_bound(c);
+            if (it != free_.end() && it->first == c) {
+                char *p = it->second;
+                free_.erase(it);
+                got = c;
+                return p;
+            }
+        }
+        char *p = nullptr;
+        if (cudaMallocHost((void **)&p, c) != cudaSuccess) return nullptr;
+        std::lock_guard<std::mutex> g(mu);
+        all.push_back(p);
+        got = c;
+        return p;
+    }
+    void put(char *p, size_t n)
+    {
+        std::lock_guard<std::mutex> g(mu);
+        free_.emplace(n, p);
+    }
+    ~PinnedPool()
+    {
+        for (char *p : all) cudaFreeHost(p);
+    }
+};
+
+// A block of the pool, returned to it when the last holder lets go.
+struct PinnedBlock {
+    PinnedPool *pool = nullptr;
+    char *p = nullptr;
+    size_t n = 0;
+    ~PinnedBlock()
+    {
+        if (p) pool->put(p, n);
+    }
+};
+
+static std::shared_ptr<PinnedBlock> pinned_block(PinnedPool &pool, size_t bytes)
+{
+    auto b = std::make_shared<PinnedBlock>();
+    b->pool = &pool;
+    b->p = pool.get(bytes, b->n);
+    if (!b->p) b.reset();
+    return b;
+}
+
 struct Batch;
 
 struct pxr_ctx {
@@ -430,6 +509,7 @@ struct pxr_ctx {
     std::mutex plans_mu;
     std::unordered_set<pxr_plan *> plans;   // live plans, destroyed with the context
     // serving
+    PinnedPool pool;                    // (outlives the tickets and batches holding its blocks)
     std::mutex mu;
     std::condition_variable cv_sched, cv_done;
     std::thread sched;
@@ -488,6 +568,10 @@ static void plan_bind(pxr_plan *P)
     b.r64 = (double *)(r + o.r64);
     b.hmeta = (uint32_t *)(r + o.hmeta);
     b.hphi = (float *)(r + o.hphi);
+    b.gofs = (uint32_t *)(r + o.gofs);
+    b.gpos = P->dp.n_glayers ? (uint32_t *)(r + o.gpos) : nullptr;     // (null: no grid)
+    b.gfree = (float *)(r + o.gfree);
+    b.glay = (float4 *)(r + o.glay);
     b.cell_chunk = (const uint32_t *)(r + o.cell_chunk);
     b.edge_chunk = (const uint32_t *)(r + o.edge_chunk);
     b.tup_chunk = (const uint32_t *)(r + o.tup_chunk);
@@ -513,6 +597,8 @@ static void plan_bind(pxr_plan *P)
     b.tup_first = (uint32_t *)(r + o.tup_first);
     b.tup_rank = (uint32_t *)(r + o.tup_rank);
     b.tup_list = (uint32_t *)(r + o.tup_list);
+    b.tup_tmp = (uint32_t *)(r + o.tup_tmp);
+    b.canon_cnt = (uint32_t *)(r + o.canon_cnt);
     b.out_evt = (uint32_t *)(r + o.out_evt);
     b.out_cap = (uint32_t)P->T;
     b.o_nh = (uint8_t *)(r + o.o_nh);
@@ -631,6 +717,7 @@ static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
     launch_ntuplets(b, p, (uint32_t)P->G, s, sms);
     launch_select(b, p, (uint32_t)P->T, s, sms);
     launch_out_scan(b, s);
+    launch_canon(b, s, sms);
     if (t) CK(stage_mark(P->ev_stage[4], s, capturing));
     // the selection's shared-hit ranks start at the largest key (no track)
     if (p.clean) CK(cudaMemsetAsync(b.best, 0xFF, 8 * (size_t)P->N, s));
@@ -644,8 +731,9 @@ static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
 
 static int plan_launches(const pxr_plan *P)
 {
-    int n = 6 + (P->dp.clean ? 1 : 0) + (P->dp.vtx ? 1 : 0);   // sort, doublets, walk, select,
-                                                                 // scan, fit, keep, vertices
+    int n = 7 + (P->dp.clean ? 1 : 0) + (P->dp.vtx ? 1 : 0);   // sort, doublets, walk, select,
+                                                                 // scan, order, fit, keep,
+                                                                 // vertices
     for (uint32_t lv = 1; lv <= P->dp.n_levels; ++lv)
         n += (P->dp.level_dense[lv] ? 2 : 0) + (P->dp.level_sparse[lv] ? 1 : 0);
     return n;
@@ -829,6 +917,23 @@ extern "C" void pxr_plan_destroy(pxr_plan *P)
 }
 
 // ---- readback -----------------------------------------------------------------------------
+// The tracks of one event (canonical order: the device writes them so) and its vertices, as
+// arrays somewhere in host memory.
+struct TrackSrc {
+    size_t n = 0, nv = 0;
+    const uint8_t *nh = nullptr;
+    const uint32_t *hits = nullptr;
+    const double *pt = nullptr, *phi = nullptr, *cot = nullptr, *dxy = nullptr, *dz = nullptr,
+                 *chi2 = nullptr;
+    const int8_t *q = nullptr, *st = nullptr;
+    const uint8_t *ql = nullptr;
+    const double *cov = nullptr;         // 15 per track, or null (covariance not computed)
+    const int32_t *vtx = nullptr;        // vertex of each track, or null (no vertex finding)
+    const double *vz = nullptr, *verr = nullptr, *vpt2 = nullptr;
+    const uint32_t *vn = nullptr;
+};
+
+// Host copies of one event's results (the plan path reads them back into these).
 struct HostTracks {
     std::vector<uint8_t> nh;
     std::vector<uint32_t> hits;
@@ -839,126 +944,63 @@ struct HostTracks {
     std::vector<int32_t> vtx;            // vertex of each track, or empty (no vertex finding)
     std::vector<double> vz, verr, vpt2;  // the event's vertices
     std::vector<uint32_t> vn;
-    size_t size() const { return nh.size(); }
-    void resize(size_t n, bool with_cov = false, bool with_vtx = false)
+    TrackSrc src() const
     {
-        nh.resize(n); hits.resize(n * kMaxHits); pt.resize(n); phi.resize(n); cot.resize(n);
-        dxy.resize(n); dz.resize(n); chi2.resize(n); q.resize(n); st.resize(n); ql.resize(n);
-        cov.resize(with_cov ? 15 * n : 0);
-        vtx.resize(with_vtx ? n : 0);
-    }
-    void resize_vertices(size_t nv)
-    {
-        vz.resize(nv); verr.resize(nv); vpt2.resize(nv); vn.resize(nv);
+        TrackSrc t;
+        t.n = nh.size();
+        t.nv = vz.size();
+        t.nh = nh.data(); t.hits = hits.data(); t.pt = pt.data(); t.phi = phi.data();
+        t.cot = cot.data(); t.dxy = dxy.data(); t.dz = dz.data(); t.chi2 = chi2.data();
+        t.q = q.data(); t.st = st.data(); t.ql = ql.data();
+        t.cov = cov.empty() ? nullptr : cov.data();
+        t.vtx = vtx.empty() ? nullptr : vtx.data();
+        t.vz = vz.data(); t.verr = verr.data(); t.vpt2 = vpt2.data(); t.vn = vn.data();
+        return t;
     }
 };
 
-// Canonical order of n tracks (lexicographic by their hit tuples): LSD radix sort on the packed
-// first two hit indices (caller indices are < 2^24, so the key has 48 bits), then the rare runs
-// of equal first two hits are ordered by the remaining hits.
-static void canonical_order(const uint32_t *hits, size_t n, std::vector<uint32_t> &ord)
+// Copy h into out's arrays at track row r0 and vertex row v0, one copy per array (no capacity
+// check).  A covariance that was not computed reads as NaN, a missing vertex index as -1.
+static void copy_tracks(const TrackSrc &h, pxr_tracks *out, size_t r0, size_t v0)
 {
-    std::vector<uint64_t> key(n), key2(n);
-    std::vector<uint32_t> tmp(n);
-    ord.resize(n);
-    for (size_t i = 0; i < n; ++i) {
-        const uint32_t *h = hits + i * kMaxHits;
-        key[i] = ((uint64_t)(h[0] & 0xFFFFFFu) << 24) | (uint64_t)(h[1] & 0xFFFFFFu);
-        ord[i] = (uint32_t)i;
+    const size_t n = h.n, nv = h.nv;
+    auto cp = [](void *dst, size_t row, const void *src, size_t sz, size_t cnt) {
+        if (dst && cnt) std::memcpy((char *)dst + sz * row, src, sz * cnt);
+    };
+    cp(out->vtx_z, v0, h.vz, 8, nv);
+    cp(out->vtx_z_err, v0, h.verr, 8, nv);
+    cp(out->vtx_sum_pt2, v0, h.vpt2, 8, nv);
+    cp(out->vtx_n_tracks, v0, h.vn, 4, nv);
+    cp(out->n_hits, r0, h.nh, 1, n);
+    cp(out->hit_idx, r0, h.hits, 4 * kMaxHits, n);
+    cp(out->pt, r0, h.pt, 8, n);
+    cp(out->phi, r0, h.phi, 8, n);
+    cp(out->cot_theta, r0, h.cot, 8, n);
+    cp(out->dxy, r0, h.dxy, 8, n);
+    cp(out->dz, r0, h.dz, 8, n);
+    cp(out->chi2, r0, h.chi2, 8, n);
+    cp(out->charge, r0, h.q, 1, n);
+    cp(out->fit_status, r0, h.st, 1, n);
+    cp(out->quality, r0, h.ql, 1, n);
+    if (out->cov) {
+        if (!h.cov) std::fill(out->cov + 15 * r0, out->cov + 15 * (r0 + n), NAN);
+        else cp(out->cov, r0, h.cov, 15 * sizeof(double), n);
     }
-    size_t count[256];
-    for (int pass = 0; pass < 6; ++pass) {
-        const int sh = 8 * pass;
-        std::fill(count, count + 256, 0);
-        for (size_t i = 0; i < n; ++i) ++count[(key[i] >> sh) & 0xFF];
-        size_t run = 0;
-        for (int b = 0; b < 256; ++b) { const size_t c = count[b]; count[b] = run; run += c; }
-        for (size_t i = 0; i < n; ++i) {
-            const size_t d = count[(key[i] >> sh) & 0xFF]++;
-            key2[d] = key[i];
-            tmp[d] = ord[i];
-        }
-        key.swap(key2);
-        ord.swap(tmp);
-    }
-    for (size_t a = 0; a < n;) {
-        size_t b = a + 1;
-        while (b < n && key[b] == key[a]) ++b;
-        if (b - a > 1)
-            std::sort(ord.begin() + a, ord.begin() + b, [&](uint32_t x, uint32_t y) {
-                return std::lexicographical_compare(hits + (size_t)x * kMaxHits,
-                                                    hits + (size_t)x * kMaxHits + kMaxHits,
-                                                    hits + (size_t)y * kMaxHits,
-                                                    hits + (size_t)y * kMaxHits + kMaxHits);
-            });
-        a = b;
+    if (out->vertex) {
+        if (!h.vtx) std::fill(out->vertex + r0, out->vertex + r0 + n, -1);
+        else cp(out->vertex, r0, h.vtx, 4, n);
     }
 }
 
-// Copy the tracks of h into out, in canonical order (in_order: h already is).  A covariance
-// that was not computed reads as NaN.
-static int emit_tracks(const HostTracks &h, int32_t status, pxr_tracks *out, bool in_order = false)
+// The tracks of one event into out (capacity checked).
+static int emit_tracks(const TrackSrc &h, int32_t status, pxr_tracks *out)
 {
-    const size_t n = h.size();
-    out->n_tracks = (uint32_t)n;
-    out->n_vertices = (uint32_t)h.vz.size();
+    out->n_tracks = (uint32_t)h.n;
+    out->n_vertices = (uint32_t)h.nv;
     out->status = status;
-    if (n > out->capacity) return fail(PXR_ETRUNC, "track capacity too small");
-    // the vertices (ordered by sum pT^2, whatever the track order)
-    const size_t nv = h.vz.size();
-    if (nv) {
-        if (out->vtx_z) std::memcpy(out->vtx_z, h.vz.data(), 8 * nv);
-        if (out->vtx_z_err) std::memcpy(out->vtx_z_err, h.verr.data(), 8 * nv);
-        if (out->vtx_sum_pt2) std::memcpy(out->vtx_sum_pt2, h.vpt2.data(), 8 * nv);
-        if (out->vtx_n_tracks) std::memcpy(out->vtx_n_tracks, h.vn.data(), 4 * nv);
-    }
-    if (in_order) {                          // already canonical: one copy per array
-        auto cp = [n](void *dst, const void *src, size_t sz) {
-            if (dst && n) std::memcpy(dst, src, sz * n);
-        };
-        cp(out->n_hits, h.nh.data(), 1);
-        cp(out->hit_idx, h.hits.data(), 4 * kMaxHits);
-        cp(out->pt, h.pt.data(), 8);
-        cp(out->phi, h.phi.data(), 8);
-        cp(out->cot_theta, h.cot.data(), 8);
-        cp(out->dxy, h.dxy.data(), 8);
-        cp(out->dz, h.dz.data(), 8);
-        cp(out->chi2, h.chi2.data(), 8);
-        cp(out->charge, h.q.data(), 1);
-        cp(out->fit_status, h.st.data(), 1);
-        cp(out->quality, h.ql.data(), 1);
-        if (out->cov) {
-            if (h.cov.empty()) std::fill(out->cov, out->cov + 15 * n, NAN);
-            else cp(out->cov, h.cov.data(), 15 * sizeof(double));
-        }
-        if (out->vertex) {
-            if (h.vtx.empty()) std::fill(out->vertex, out->vertex + n, -1);
-            else cp(out->vertex, h.vtx.data(), 4);
-        }
-        return PXR_OK;
-    }
-    std::vector<uint32_t> ord;
-    canonical_order(h.hits.data(), n, ord);
-    for (size_t k = 0; k < n; ++k) {
-        const size_t s = ord[k];
-        if (out->n_hits) out->n_hits[k] = h.nh[s];
-        if (out->hit_idx)
-            std::memcpy(out->hit_idx + k * kMaxHits, h.hits.data() + s * kMaxHits, 4 * kMaxHits);
-        if (out->pt) out->pt[k] = h.pt[s];
-        if (out->phi) out->phi[k] = h.phi[s];
-        if (out->cot_theta) out->cot_theta[k] = h.cot[s];
-        if (out->dxy) out->dxy[k] = h.dxy[s];
-        if (out->dz) out->dz[k] = h.dz[s];
-        if (out->chi2) out->chi2[k] = h.chi2[s];
-        if (out->charge) out->charge[k] = h.q[s];
-        if (out->fit_status) out->fit_status[k] = h.st[s];
-        if (out->quality) out->quality[k] = h.ql[s];
-        if (out->cov) {
-            if (h.cov.empty()) std::fill(out->cov + 15 * k, out->cov + 15 * k + 15, NAN);
-            else std::memcpy(out->cov + 15 * k, h.cov.data() + 15 * s, 15 * sizeof(double));
-        }
-        if (out->vertex) out->vertex[k] = h.vtx.empty() ? -1 : h.vtx[s];
-    }
+    if (h.n > out->capacity || h.nv > out->capacity)
+        return fail(PXR_ETRUNC, "track capacity too small");
+    copy_tracks(h, out, 0, 0);
     return PXR_OK;
 }
 
@@ -1000,7 +1042,7 @@ extern "C" int pxr_plan_tracks(pxr_plan *P, uint32_t e, pxr_tracks *out)
             (rc = d2h(h.vn, P->db.v_n + a, nv)))
             return rc;
     }
-    return emit_tracks(h, flags_status(flags), out);
+    return emit_tracks(h.src(), flags_status(flags), out);
 }
 
 // Debug content of one event of a plan region (also used by the serving path).
@@ -1121,21 +1163,27 @@ extern "C" int pxr_fit_batch(pxr_ctx *ctx, uint32_t m, const uint8_t *nh, const 
 struct Ticket {
     uint64_t id = 0;
     int state = 0;                       // 0 pending, 1 running, 2 done
-    // the event's hits, copied at submission: x, y, z (float) then layer (uint16), n of each
-    std::unique_ptr<uint8_t[]> hits;
+    // the event's hits in its submission's block: x, y, z (float) then layer (uint16), nt
+    // values of each for the whole submission, the event's nt from in_a
+    std::shared_ptr<PinnedBlock> in;
+    size_t in_nt = 0, in_a = 0;
     uint32_t n = 0;
-    const float *x() const { return reinterpret_cast<const float *>(hits.get()); }
-    const float *y() const { return x() + n; }
-    const float *z() const { return x() + 2 * (size_t)n; }
-    const uint16_t *layer() const { return reinterpret_cast<const uint16_t *>(x() + 3 * (size_t)n); }
+    const float *x() const { return reinterpret_cast<const float *>(in->p) + in_a; }
+    const float *y() const { return x() + in_nt; }
+    const float *z() const { return x() + 2 * in_nt; }
+    const uint16_t *layer() const
+    {
+        return reinterpret_cast<const uint16_t *>(reinterpret_cast<const float *>(in->p) +
+                                                  3 * in_nt) + in_a;
+    }
     uint32_t lcount[kMaxLayers + 1] = {};
     pxr_params params{};
     size_t bytes = 0;
     std::shared_ptr<Batch> batch;        // kept for pxr_fetch_debug
     uint32_t index = 0;
     int32_t status = PXR_OK;
-    HostTracks res;                      // results in canonical order (copied from the slot's
-                                         // pinned buffer by the scheduler thread)
+    std::shared_ptr<PinnedBlock> out;    // the batch's results, which res points into
+    TrackSrc res;
 };
 
 // Pinned host buffers of one in-flight slot, grown on demand and reused.
@@ -1169,6 +1217,8 @@ struct Batch {
     cudaEvent_t ev_counts = nullptr, ev_data = nullptr;
     size_t reserved = 0;
     uint32_t total = 0;
+    std::vector<std::shared_ptr<PinnedBlock>> inputs;   // until the hits are on the device
+    std::shared_ptr<PinnedBlock> results;               // the tracks, read by the fetches
     size_t o_nh = 0, o_hits = 0, o_pt = 0, o_phi = 0, o_cot = 0, o_dxy = 0, o_dz = 0,
            o_chi2 = 0, o_q = 0, o_st = 0, o_ql = 0, o_cov = 0, o_vtx = 0, v_z = 0, v_err = 0,
            v_pt2 = 0, v_n = 0;
@@ -1181,7 +1231,7 @@ struct Batch {
 };
 
 struct SlotBuffers {
-    Pinned head, evt, out;
+    Pinned head, evt;
 };
 
 static size_t event_bytes(const pxr_params &p, const DevParams &dp, const uint32_t *lcount,
@@ -1243,29 +1293,13 @@ static int launch_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
     P->region = ctx->arena.alloc(P->off.total);
     if (!P->region) return fail(PXR_EAGAIN, "arena fragmented");
     plan_bind(P);
-    // pinned staging of the head (inputs + small arrays), one H2D copy; the batch's tickets are
-    // out of the pending queue and reach no other thread before the batch is published
+    // the small arrays staged in the slot's pinned head, one H2D copy; the hits straight from
+    // the submissions' pinned blocks, one copy per array for each run of events contiguous in
+    // one block.  The batch's tickets are out of the pending queue and reach no other thread
+    // before the batch is published
     {
     Unlocked unlocked(lk);
     char *h = sb.head.p;
-    auto stage = [&](uint32_t e0, uint32_t step) {
-        for (uint32_t e = e0; e < E; e += step) {
-            size_t a = P->hit_off[e], n = items[e]->n;
-            std::memcpy(h + P->off.x + 4 * a, items[e]->x(), 4 * n);
-            std::memcpy(h + P->off.y + 4 * a, items[e]->y(), 4 * n);
-            std::memcpy(h + P->off.z + 4 * a, items[e]->z(), 4 * n);
-            std::memcpy(h + P->off.layer + 2 * a, items[e]->layer(), 2 * n);
-        }
-    };
-    {
-        // large batches are staged by a few host threads
-        const uint32_t nth = P->N > (1u << 20) ? std::min<uint32_t>(
-            E, std::max(1u, std::min(8u, std::thread::hardware_concurrency() / 2))) : 1u;
-        std::vector<std::thread> th;
-        for (uint32_t w = 1; w < nth; ++w) th.emplace_back(stage, w, nth);
-        stage(0, nth);
-        for (auto &x : th) x.join();
-    }
     const size_t e1 = 4 * (E + 1);
     std::memcpy(h + P->off.hit_off, P->hit_off.data(), e1);
     std::memcpy(h + P->off.cell_off, P->cell_off.data(), e1);
@@ -1274,7 +1308,24 @@ static int launch_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
     fill_chunks(P, h);
     cudaStream_t s = slot_stream(ctx, slot);
     B->stream = s;
-    CK(cudaMemcpyAsync(P->region, h, P->off.head_end, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(P->region + P->off.hit_off, h + P->off.hit_off,
+                       P->off.head_end - P->off.hit_off, cudaMemcpyHostToDevice, s));
+    for (uint32_t e = 0; e < E;) {
+        const Ticket &t = *items[e];
+        uint32_t f = e + 1;
+        while (f < E && items[f]->in == t.in && items[f]->in_a == items[f - 1]->in_a + items[f - 1]->n)
+            ++f;
+        const size_t a = P->hit_off[e], n = P->hit_off[f] - a;
+        if (n) {
+            CK(cudaMemcpyAsync(P->region + P->off.x + 4 * a, t.x(), 4 * n, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(P->region + P->off.y + 4 * a, t.y(), 4 * n, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(P->region + P->off.z + 4 * a, t.z(), 4 * n, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(P->region + P->off.layer + 2 * a, t.layer(), 2 * n,
+                               cudaMemcpyHostToDevice, s));
+        }
+        if (B->inputs.empty() || B->inputs.back() != t.in) B->inputs.push_back(t.in);
+        e = f;
+    }
     if ((rc = plan_enqueue(P, s))) return rc;
     CK(cudaEventRecord(P->ev_done, s));
     P->has_run = true;
@@ -1290,7 +1341,7 @@ static int launch_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
     for (uint32_t e = 0; e < E; ++e) {
         items[e]->state = 1;
         items[e]->index = e;
-        items[e]->hits.reset();
+        items[e]->in.reset();                   // (the batch holds the blocks until the copies)
     }
     out = B;
     return PXR_OK;
@@ -1328,9 +1379,15 @@ static bool progress_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
         B.v_err = L.add(8 * tv);
         B.v_pt2 = L.add(8 * tv);
         B.v_n = L.add(4 * tv);
-        bool ok = sb.out.reserve(L.add(0) + 256);
+        // the results' pinned block (the fetches read it in place); the hits' blocks are done
+        B.inputs.clear();
+        {
+            Unlocked unlocked(lk);
+            B.results = pinned_block(ctx->pool, L.add(0) + 256);
+        }
+        bool ok = B.results != nullptr;
         const DevBatch &d = P->db;
-        char *ho = sb.out.p;
+        char *ho = ok ? B.results->p : nullptr;
         if (ok && T) {
             auto cp = [&](size_t off, const void *src, size_t bytes) {
                 ok &= cudaMemcpyAsync(ho + off, src, bytes, cudaMemcpyDeviceToHost, s) == cudaSuccess;
@@ -1361,82 +1418,47 @@ static bool progress_batch(pxr_ctx *ctx, std::unique_lock<std::mutex> &lk,
         return true;
     }
     if (B.state == 2 && cudaEventQuery(B.ev_data) == cudaSuccess) {
-        const char *ho = sb.out.p;
+        // each event's results: a view of the batch's pinned block (tracks in canonical order)
+        const char *ho = B.results ? B.results->p : nullptr;
         std::vector<std::shared_ptr<Ticket>> ts(E);
         for (uint32_t e = 0; e < E; ++e) {
             auto it = ctx->tickets.find(B.ids[e]);
-            if (it != ctx->tickets.end()) ts[e] = it->second;
-        }
-        {
-        // the results reach no other thread before the tickets are marked done (below)
-        Unlocked unlocked(lk);
-        Range range("pxr.batch.order");
-        // events in parallel (a few host threads): the ordering is the heaviest host work of a
-        // batch
-        auto work = [&](uint32_t e0, uint32_t step) {
-        std::vector<uint32_t> ord;
-        for (uint32_t e = e0; e < E; e += step) {
-            if (!ts[e]) continue;
+            if (it == ctx->tickets.end()) continue;
+            ts[e] = it->second;
             Ticket &t = *ts[e];
-            const uint32_t a = hev[e], n = hev[e + 1] - a;
-            t.res.resize(n, P->dp.cov != 0, P->dp.vtx != 0);
-            t.res.resize_vertices(P->dp.vtx ? hev[2 * E + 1 + e] : 0);
-            if (P->dp.vtx) {
-                const uint32_t nv = hev[2 * E + 1 + e];
-                std::memcpy(t.res.vz.data(), ho + B.v_z + 8 * (size_t)a, 8 * (size_t)nv);
-                std::memcpy(t.res.verr.data(), ho + B.v_err + 8 * (size_t)a, 8 * (size_t)nv);
-                std::memcpy(t.res.vpt2.data(), ho + B.v_pt2 + 8 * (size_t)a, 8 * (size_t)nv);
-                std::memcpy(t.res.vn.data(), ho + B.v_n + 4 * (size_t)a, 4 * (size_t)nv);
+            const size_t a = hev[e];
+            TrackSrc &r = t.res;
+            r.n = hev[e + 1] - a;
+            r.nv = P->dp.vtx ? hev[2 * E + 1 + e] : 0;
+            if (ho) {
+                auto at = [&](size_t off, size_t sz) { return ho + off + sz * a; };
+                r.nh = (const uint8_t *)at(B.o_nh, 1);
+                r.hits = (const uint32_t *)at(B.o_hits, 4 * kMaxHits);
+                r.pt = (const double *)at(B.o_pt, 8);
+                r.phi = (const double *)at(B.o_phi, 8);
+                r.cot = (const double *)at(B.o_cot, 8);
+                r.dxy = (const double *)at(B.o_dxy, 8);
+                r.dz = (const double *)at(B.o_dz, 8);
+                r.chi2 = (const double *)at(B.o_chi2, 8);
+                r.q = (const int8_t *)at(B.o_q, 1);
+                r.st = (const int8_t *)at(B.o_st, 1);
+                r.ql = (const uint8_t *)at(B.o_ql, 1);
+                r.cov = P->dp.cov ? (const double *)at(B.o_cov, 15 * sizeof(double)) : nullptr;
+                r.vtx = P->dp.vtx ? (const int32_t *)at(B.o_vtx, 4) : nullptr;
+                r.vz = (const double *)at(B.v_z, 8);
+                r.verr = (const double *)at(B.v_err, 8);
+                r.vpt2 = (const double *)at(B.v_pt2, 8);
+                r.vn = (const uint32_t *)at(B.v_n, 4);
+            } else {
+                r.n = r.nv = 0;
             }
-            if (n) {
-                // canonical order here, on the scheduler thread, so that a fetch only copies
-                auto hp = [&](size_t off) { return ho + off; };
-                const uint32_t *hits = (const uint32_t *)hp(B.o_hits + 4 * (size_t)a * kMaxHits);
-                canonical_order(hits, n, ord);
-                const uint8_t *nh = (const uint8_t *)hp(B.o_nh + a);
-                const double *pt = (const double *)hp(B.o_pt + 8 * (size_t)a);
-                const double *phi = (const double *)hp(B.o_phi + 8 * (size_t)a);
-                const double *cot = (const double *)hp(B.o_cot + 8 * (size_t)a);
-                const double *dxy = (const double *)hp(B.o_dxy + 8 * (size_t)a);
-                const double *dz = (const double *)hp(B.o_dz + 8 * (size_t)a);
-                const double *chi2 = (const double *)hp(B.o_chi2 + 8 * (size_t)a);
-                const int8_t *q = (const int8_t *)hp(B.o_q + a);
-                const int8_t *st = (const int8_t *)hp(B.o_st + a);
-                const uint8_t *ql = (const uint8_t *)hp(B.o_ql + a);
-                const double *cv = (const double *)hp(B.o_cov + 8 * 15 * (size_t)a);
-                for (uint32_t k = 0; k < n; ++k) {
-                    const uint32_t s_ = ord[k];
-                    t.res.nh[k] = nh[s_];
-                    std::memcpy(&t.res.hits[(size_t)k * kMaxHits], hits + (size_t)s_ * kMaxHits,
-                                4 * kMaxHits);
-                    t.res.pt[k] = pt[s_];
-                    t.res.phi[k] = phi[s_];
-                    t.res.cot[k] = cot[s_];
-                    t.res.dxy[k] = dxy[s_];
-                    t.res.dz[k] = dz[s_];
-                    t.res.chi2[k] = chi2[s_];
-                    t.res.q[k] = q[s_];
-                    t.res.st[k] = st[s_];
-                    t.res.ql[k] = ql[s_];
-                    if (P->dp.cov)
-                        std::memcpy(&t.res.cov[15 * (size_t)k], cv + 15 * (size_t)s_,
-                                    15 * sizeof(double));
-                    if (P->dp.vtx)
-                        t.res.vtx[k] = ((const int32_t *)(ho + B.o_vtx))[a + s_];
-                }
-            }
-        }
-        };
-        const uint32_t nth = std::min<uint32_t>(E, std::max(1u, std::min(8u, std::thread::hardware_concurrency() / 2)));
-        std::vector<std::thread> th;
-        for (uint32_t w = 1; w < nth; ++w) th.emplace_back(work, w, nth);
-        work(0, nth);
-        for (auto &x : th) x.join();
+            t.out = B.results;
         }
         for (uint32_t e = 0; e < E; ++e) {
             if (!ts[e]) continue;
             Ticket &t = *ts[e];
             t.status = flags_status(hev[E + 1 + e]);
+            if (!B.results && hev[e + 1] > hev[e]) t.status = PXR_ENOMEM;   // (no pinned memory)
             t.state = 2;
             if (ctx->cfg.keep_debug) t.batch = Bp;
             ctx->done_q.push_back(t.id);
@@ -1578,54 +1600,124 @@ extern "C" void pxr_destroy(pxr_ctx *ctx)
     delete ctx;
 }
 
+// Host threads for a copy or check of `work` units (a few for large inputs).
+static uint32_t host_threads(size_t work, size_t per_thread)
+{
+    const uint32_t hw = std::max(1u, std::thread::hardware_concurrency() / 2);
+    return (uint32_t)std::max<size_t>(1, std::min<size_t>(std::min(8u, hw), work / per_thread));
+}
+
+// n_events events, hits back to back in the caller's arrays (event e: [off[e], off[e+1])): one
+// pinned block receives all of them (x, y, z, layer), the events are checked and counted per
+// layer, and admitted together (all or none).
+static int submit_many(pxr_ctx *ctx, uint32_t n_events, const uint32_t *off, const float *x,
+                       const float *y, const float *z, const uint16_t *layer,
+                       const pxr_params *params, uint64_t *tickets)
+{
+    DevParams dp;
+    int rc = check_params(params, &dp);
+    if (rc) return rc;
+    if (n_events == 0) return PXR_OK;
+    const size_t nt = off[n_events] - off[0];
+    for (uint32_t e = 0; e < n_events; ++e) {
+        if (off[e + 1] < off[e]) return fail(PXR_EINVAL, "hit offsets must not decrease");
+        if (off[e + 1] - off[e] > kLocalMask) return fail(PXR_EINVAL, "too many hits in one event");
+    }
+    auto blk = pinned_block(ctx->pool, 14 * nt + 64);
+    if (!blk) return fail(PXR_ENOMEM, "pinned host allocation failed");
+    float *bx = reinterpret_cast<float *>(blk->p);
+    uint16_t *bl = reinterpret_cast<uint16_t *>(bx + 3 * nt);
+    const float *sx = x + off[0], *sy = y + off[0], *sz = z + off[0];
+    const uint16_t *sl = layer + off[0];
+    std::vector<std::shared_ptr<Ticket>> ts(n_events);
+    std::atomic<int> bad{0};
+    // the copy and the checks, split over a few host threads by events
+    auto work = [&](uint32_t w, uint32_t nw) {
+        const uint32_t e0 = (uint32_t)((uint64_t)n_events * w / nw);
+        const uint32_t e1 = (uint32_t)((uint64_t)n_events * (w + 1) / nw);
+        if (e0 == e1) return;
+        const size_t a = off[e0] - off[0], n = off[e1] - off[e0];
+        std::memcpy(bx + a, sx + a, 4 * n);
+        std::memcpy(bx + nt + a, sy + a, 4 * n);
+        std::memcpy(bx + 2 * nt + a, sz + a, 4 * n);
+        std::memcpy(bl + a, sl + a, 2 * n);
+        for (uint32_t e = e0; e < e1; ++e) {
+            auto t = std::make_shared<Ticket>();
+            t->in = blk;
+            t->in_nt = nt;
+            t->in_a = off[e] - off[0];
+            t->n = off[e + 1] - off[e];
+            bool finite = true;
+            uint32_t bad_layer = 0;
+            uint32_t lc[4][kMaxLayers + 1] = {};
+            const float *ex = t->x(), *ey = t->y(), *ez = t->z();
+            const uint16_t *el = t->layer();
+            for (uint32_t h = 0; h < t->n; ++h) {
+                finite &= std::isfinite(ex[h]) & std::isfinite(ey[h]) & std::isfinite(ez[h]);
+                const uint16_t l = el[h];
+                bad_layer |= l >= params->n_layers;
+                lc[h & 3][l < kMaxLayers ? l : kMaxLayers]++;
+            }
+            if (!finite) { bad |= 1; continue; }
+            if (bad_layer) { bad |= 2; continue; }
+            for (int l = 0; l <= kMaxLayers; ++l)
+                t->lcount[l] = lc[0][l] + lc[1][l] + lc[2][l] + lc[3][l];
+            t->params = *params;
+            t->bytes = event_bytes(*params, dp, t->lcount, t->n);
+            if (t->bytes > ctx->arena.size) bad |= 4;
+            ts[e] = t;
+        }
+    };
+    {
+        const uint32_t nth = host_threads(nt, 1u << 18);
+        std::vector<std::thread> th;
+        for (uint32_t w = 1; w < nth; ++w) th.emplace_back(work, w, nth);
+        work(0, nth);
+        for (auto &t : th) t.join();
+    }
+    if (bad & 1) return fail(PXR_EINVAL, "non-finite hit coordinate");
+    if (bad & 2) return fail(PXR_EINVAL, "hit layer id >= n_layers");
+    if (bad & 4) return fail(PXR_ENOMEM, "event exceeds the memory budget");
+    size_t bytes = 0;
+    for (auto &t : ts) bytes += t->bytes;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (!ctx->sched_error.empty() && ctx->inflight.empty() && ctx->pending.empty()) {
+        // a failed batch is reported through its tickets; the context stays usable
+        ctx->sched_error.clear();
+    }
+    if (ctx->reserved + bytes > ctx->arena.size) return fail(PXR_EAGAIN, "memory budget full");
+    for (uint32_t e = 0; e < n_events; ++e) {
+        auto &t = ts[e];
+        t->id = ctx->next_ticket++;
+        ctx->tickets[t->id] = t;
+        ctx->pending.push_back(t->id);
+        tickets[e] = t->id;
+    }
+    ctx->reserved += bytes;
+    ctx->cv_sched.notify_all();
+    return PXR_OK;
+}
+
 extern "C" int pxr_submit_event(pxr_ctx *ctx, const float *x, const float *y, const float *z,
                                 const uint16_t *layer, uint32_t n_hits, const pxr_params *params,
                                 uint64_t *ticket)
 {
     if (!ctx || !ticket || (n_hits && (!x || !y || !z || !layer)))
         return fail(PXR_EINVAL, "null argument");
-    DevParams dp;
-    int rc = check_params(params, &dp);
-    if (rc) return rc;
-    if (n_hits > kLocalMask) return fail(PXR_EINVAL, "too many hits in one event");
-    auto t = std::make_shared<Ticket>();
-    // copy the hits into the ticket (uninitialised storage), then check them and count them per
-    // layer (four interleaved counter sets keep the increments independent)
-    t->n = n_hits;
-    t->hits.reset(new uint8_t[14 * (size_t)n_hits + 16]);
-    float *tx = const_cast<float *>(t->x());
-    std::memcpy(tx, x, 4 * (size_t)n_hits);
-    std::memcpy(tx + n_hits, y, 4 * (size_t)n_hits);
-    std::memcpy(tx + 2 * (size_t)n_hits, z, 4 * (size_t)n_hits);
-    std::memcpy(const_cast<uint16_t *>(t->layer()), layer, 2 * (size_t)n_hits);
-    bool finite = true;
-    uint32_t bad_layer = 0;
-    uint32_t lc[4][kMaxLayers + 1] = {};
-    for (uint32_t h = 0; h < n_hits; ++h) {
-        finite &= std::isfinite(x[h]) & std::isfinite(y[h]) & std::isfinite(z[h]);
-        const uint16_t l = layer[h];
-        bad_layer |= l >= params->n_layers;
-        lc[h & 3][l < kMaxLayers ? l : kMaxLayers]++;
-    }
-    if (!finite) return fail(PXR_EINVAL, "non-finite hit coordinate");
-    if (bad_layer) return fail(PXR_EINVAL, "hit layer id >= n_layers");
-    for (int l = 0; l <= kMaxLayers; ++l) t->lcount[l] = lc[0][l] + lc[1][l] + lc[2][l] + lc[3][l];
-    t->params = *params;
-    t->bytes = event_bytes(*params, dp, t->lcount, n_hits);
-    if (t->bytes > ctx->arena.size) return fail(PXR_ENOMEM, "event exceeds the memory budget");
-    std::lock_guard<std::mutex> g(ctx->mu);
-    if (!ctx->sched_error.empty() && ctx->inflight.empty() && ctx->pending.empty()) {
-        // a failed batch is reported through its tickets; the context stays usable
-        ctx->sched_error.clear();
-    }
-    if (ctx->reserved + t->bytes > ctx->arena.size) return fail(PXR_EAGAIN, "memory budget full");
-    t->id = ctx->next_ticket++;
-    ctx->reserved += t->bytes;
-    ctx->tickets[t->id] = t;
-    ctx->pending.push_back(t->id);
-    ctx->cv_sched.notify_all();
-    *ticket = t->id;
-    return PXR_OK;
+    const uint32_t off[2] = {0, n_hits};
+    return submit_many(ctx, 1, off, x, y, z, layer, params, ticket);
+}
+
+extern "C" int pxr_submit_events(pxr_ctx *ctx, uint32_t n_events, const uint32_t *hit_offsets,
+                                 const float *x, const float *y, const float *z,
+                                 const uint16_t *layer, const pxr_params *params,
+                                 uint64_t *tickets)
+{
+    if (!ctx || (n_events && (!hit_offsets || !tickets)))
+        return fail(PXR_EINVAL, "null argument");
+    if (n_events && hit_offsets[n_events] > hit_offsets[0] && (!x || !y || !z || !layer))
+        return fail(PXR_EINVAL, "null argument");
+    return submit_many(ctx, n_events, hit_offsets, x, y, z, layer, params, tickets);
 }
 
 extern "C" int pxr_poll(pxr_ctx *ctx, uint64_t *done, uint32_t cap, uint32_t *n_done,
@@ -1659,11 +1751,57 @@ extern "C" int pxr_fetch_tracks(pxr_ctx *ctx, uint64_t ticket, pxr_tracks *out)
         t = it->second;
         if (t->state != 2) return fail(PXR_EBUSY, "event not finished");
     }
-    const HostTracks &r = t->res;
-    int rc = emit_tracks(r, t->status, out, true);
+    int rc = emit_tracks(t->res, t->status, out);
     if (rc) return rc;
     std::lock_guard<std::mutex> g(ctx->mu);
     ctx->tickets.erase(ticket);
+    return PXR_OK;
+}
+
+extern "C" int pxr_fetch_events(pxr_ctx *ctx, uint32_t n, const uint64_t *tickets,
+                                uint32_t *track_offsets, uint32_t *vertex_offsets,
+                                int32_t *event_status, pxr_tracks *out)
+{
+    if (!ctx || !out || (n && (!tickets || !track_offsets))) return fail(PXR_EINVAL, "null argument");
+    std::vector<std::shared_ptr<Ticket>> ts(n);
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        for (uint32_t k = 0; k < n; ++k) {
+            auto it = ctx->tickets.find(tickets[k]);
+            if (it == ctx->tickets.end()) return fail(PXR_ENOTFOUND, "unknown ticket");
+            if (it->second->state != 2) return fail(PXR_EBUSY, "event not finished");
+            ts[k] = it->second;
+        }
+    }
+    std::vector<uint32_t> voff(n + 1, 0);
+    track_offsets[0] = 0;
+    int32_t worst = PXR_OK;
+    for (uint32_t k = 0; k < n; ++k) {
+        track_offsets[k + 1] = track_offsets[k] + (uint32_t)ts[k]->res.n;
+        voff[k + 1] = voff[k] + (uint32_t)ts[k]->res.nv;
+        if (event_status) event_status[k] = ts[k]->status;
+        if (worst == PXR_OK) worst = ts[k]->status;
+    }
+    if (vertex_offsets) std::memcpy(vertex_offsets, voff.data(), 4 * (size_t)(n + 1));
+    out->n_tracks = n ? track_offsets[n] : 0;
+    out->n_vertices = voff[n];
+    out->status = worst;
+    if (out->n_tracks > out->capacity || out->n_vertices > out->capacity)
+        return fail(PXR_ETRUNC, "track capacity too small");
+    // one copy per array and event, split over a few host threads by events
+    auto work = [&](uint32_t w, uint32_t nw) {
+        for (uint32_t k = (uint32_t)((uint64_t)n * w / nw); k < (uint64_t)n * (w + 1) / nw; ++k)
+            copy_tracks(ts[k]->res, out, track_offsets[k], voff[k]);
+    };
+    {
+        const uint32_t nth = host_threads(out->n_tracks, 1u << 15);
+        std::vector<std::thread> th;
+        for (uint32_t w = 1; w < nth; ++w) th.emplace_back(work, w, nth);
+        work(0, nth);
+        for (auto &t : th) t.join();
+    }
+    std::lock_guard<std::mutex> g(ctx->mu);
+    for (uint32_t k = 0; k < n; ++k) ctx->tickets.erase(tickets[k]);
     return PXR_OK;
 }
 

@@ -21,7 +21,7 @@ MAX_LAYERS, MAX_PAIRS, MAX_HITS = 16, 32, 6
 OK, EINVAL, EAGAIN, ENOMEM, EOVERFLOW, ETIMEDOUT, ECUDA, ETRUNC, ENOTFOUND, EBUSY = (
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9)
 CUT_FP64, CUT_FP32 = 0, 1
-FIT_FP64, FIT_MIXED, FIT_FP32, FIT_RIEMANN = 0, 1, 2, 3
+FIT_FP64, FIT_MIXED, FIT_FP32, FIT_RIEMANN, FIT_SPLIT = 0, 1, 2, 3, 4
 PRESET_BARREL, PRESET_PHASE1 = 0, 1
 NONE = 0xFFFFFFFF
 
@@ -100,7 +100,9 @@ def load(build_if_missing: bool = False):
             "pxr_create": (i32, [P(pxr_config), P(vp)]),
             "pxr_destroy": (None, [vp]),
             "pxr_submit_event": (i32, [vp, vp, vp, vp, vp, u32, P(pxr_params), P(C.c_uint64)]),
+            "pxr_submit_events": (i32, [vp, u32, vp, vp, vp, vp, vp, P(pxr_params), vp]),
             "pxr_poll": (i32, [vp, P(C.c_uint64), u32, P(u32), i32]),
+            "pxr_fetch_events": (i32, [vp, u32, vp, vp, vp, vp, P(pxr_tracks)]),
             "pxr_fetch_tracks": (i32, [vp, C.c_uint64, P(pxr_tracks)]),
             "pxr_fetch_debug": (i32, [vp, C.c_uint64, i32, P(u32), u32, P(u32)]),
             "pxr_plan_create": (i32, [vp, u32, P(u32), vp, vp, vp, vp, P(pxr_params), i32,
@@ -325,6 +327,67 @@ class Context:
             if e.code == EAGAIN:
                 return None
             raise
+
+    def pxr_submit_events(self, hit_offsets, x, y, z, layer, params: pxr_params) -> list:
+        """Many events in one call (hits back to back, event e at [hit_offsets[e],
+        hit_offsets[e+1])); returns their tickets."""
+        off = np.ascontiguousarray(hit_offsets, np.uint32)
+        x = np.ascontiguousarray(x, np.float32)
+        y = np.ascontiguousarray(y, np.float32)
+        z = np.ascontiguousarray(z, np.float32)
+        layer = np.ascontiguousarray(layer, np.uint16)
+        n = len(off) - 1
+        t = np.zeros(max(n, 1), np.uint64)
+        _check(load().pxr_submit_events(self.h, n, off.ctypes.data, x.ctypes.data,
+                                        y.ctypes.data, z.ctypes.data, layer.ctypes.data,
+                                        C.byref(params), t.ctypes.data))
+        return [int(v) for v in t[:n]]
+
+    def pxr_fetch_events(self, tickets, cov: bool = False, out=None) -> dict:
+        """Tracks of finished events in one set of arrays: 'track_offsets' [n+1] delimit each
+        event's rows, 'vertex_offsets' [n+1] its vertices, 'event_status' [n] its status.
+        out: optional dict of preallocated arrays (as returned), reused when large enough."""
+        tk = np.ascontiguousarray(tickets, np.uint64)
+        n = len(tk)
+        toff = np.zeros(n + 1, np.uint32)
+        voff = np.zeros(n + 1, np.uint32)
+        st = np.zeros(max(n, 1), np.int32)
+        layout = _TRACK_LAYOUT if cov else _TRACK_LAYOUT[:-1]
+
+        def call(t):
+            return load().pxr_fetch_events(self.h, n, tk.ctypes.data, toff.ctypes.data,
+                                           voff.ctypes.data, st.ctypes.data, C.byref(t))
+        cap = 0
+        if out is not None:
+            cap = min(len(out[name]) for name, _, _ in layout)
+        while True:
+            if out is None or cap == 0:
+                t = pxr_tracks()
+                t.capacity = 0
+                rc = call(t)
+                if rc not in (OK, ETRUNC):
+                    _check(rc)
+                if rc == OK:
+                    res = {name: np.zeros((0, k) if k > 1 else 0, dt) for name, dt, k in layout}
+                    break
+                cap = t.n_tracks
+                out = {name: np.empty((cap, k) if k > 1 else cap, dt) for name, dt, k in layout}
+            t = pxr_tracks()
+            t.capacity = cap
+            for name, _, _ in layout:
+                setattr(t, name, out[name].ctypes.data)
+            rc = call(t)
+            if rc == ETRUNC:
+                out, cap = None, 0
+                continue
+            _check(rc)
+            res = {name: out[name][:t.n_tracks] for name, _, _ in layout}
+            for name in _VERTEX_FIELDS:
+                res[name] = out[name][:t.n_vertices]
+            break
+        res.update(track_offsets=toff, vertex_offsets=voff, event_status=st[:n],
+                   n=int(toff[-1]), status=int(st[:n].min()) if n else OK)
+        return res
 
     def pxr_poll(self, cap=4096, timeout_us=0) -> list:
         done = (C.c_uint64 * cap)()
