@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--bins", type=int, default=0, help="phi bins per layer (skips tuning)")
     ap.add_argument("--grid", default="", help="CTAs per SM per stage, 6 comma-separated values "
                     "(sort,doublets,connect,walk,select,fit; skips tuning)")
+    ap.add_argument("--block", default="", help="threads per CTA per stage, 6 comma-separated "
+                    "values (0 = built-in; skips tuning)")
     ap.add_argument("--arena-gb", type=int, default=64, help="device arena of the batch plan")
     ap.add_argument("--tune-cache", default=os.path.join(os.path.expanduser("~"), ".cache", "pxr",
                                                          "tune.json"))
@@ -286,6 +288,26 @@ def ca_traffic(cells, n_phi_bins):
         return None
 
 
+# FP32 operations of one CA candidate test as the method defines it (each add, subtract,
+# multiply, divide, square root, absolute value and compare counted once): the r-z alignment
+# test, 19, and the transverse distance of the circle through the three hits from the origin, 44
+CA_OPS_PER_CANDIDATE = 19 + 44
+
+
+def ca_candidates(plan, n_events):
+    """Candidate pairs of the CA stage by definition: every cell (i, j) with every cell (j, k)
+    that starts on its outer hit j (the pairs the brute-force connection would test)."""
+    total = 0
+    for e in range(n_events):
+        c = plan.pxr_plan_debug(e, 0)
+        if len(c) == 0:
+            continue
+        m = int(c.max()) + 1
+        total += int(np.dot(np.bincount(c[:, 1], minlength=m).astype(np.int64),
+                            np.bincount(c[:, 0], minlength=m).astype(np.int64)))
+    return total
+
+
 def doublet_algorithmic_bytes(layer_counts, pairs, n_cells, cell_bytes=4):
     """Bytes the doublet stage must move: 16 B per hit read per layer pair it takes part in, 8 B
     per inner hit and pair for the two bucket offsets of its window, the 16 B record of each
@@ -334,11 +356,12 @@ def run_pxr(args, rank, world, local):
                       stream=stream.cuda_stream)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     tuning = None
-    if args.bins or args.grid:
+    if args.bins or args.grid or args.block:
         grid = [int(v) for v in args.grid.split(",")] if args.grid else [0] * 6
+        block = [int(v) for v in args.block.split(",")] if args.block else [0] * 6
         from paper_2104_06573_gb300 import autotune
-        params = autotune._with(params, args.bins or 0, grid)
-        tuning = {"n_phi_bins": args.bins, "grid_per_sm": grid}
+        params = autotune._with(params, args.bins or 0, grid, block)
+        tuning = {"n_phi_bins": args.bins, "grid_per_sm": grid, "block_threads": block}
     elif not args.no_tune:
         # phi-bin count and per-stage grid sizes picked on this batch (outside the timed region)
         from paper_2104_06573_gb300 import autotune
@@ -402,6 +425,11 @@ def run_pxr(args, rank, world, local):
     ca_alg = 8 * cells + 8 * edges
     ca_ms = stage[2]
     ca_achieved = ca_alg / (ca_ms / 1e3) / 1e9
+    # the same stage against the FP32 pipe: candidate tests x operations per test
+    cand = ca_candidates(plan, args.events)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * 2070e6 / 1e12          # nominal: lanes x FMA x max SM clock
+    ca_tflops = cand * CA_OPS_PER_CANDIDATE / (ca_ms / 1e3) / 1e12
 
     rates = args.events * world / (step_ms / 1e3)      # per-step spread (rank-local)
     line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
@@ -413,7 +441,8 @@ def run_pxr(args, rank, world, local):
             "config": {"workload": WORKLOAD, "events_per_step": args.events * world,
                        "hits_per_step": n_hits * world, "l2": "flushed (512 MB write) between steps",
                        "launch": "captured CUDA graph, inputs resident",
-                       "tuning": tuning and {k: tuning[k] for k in ("n_phi_bins", "grid_per_sm")}},
+                       "tuning": tuning and {k: tuning[k] for k in ("n_phi_bins", "grid_per_sm",
+                                                                   "block_threads")}},
             "gpu_launches": plan.pxr_plan_launches() * args.steps,
             "stage_ms": dict(zip(["sort", "doublets", "connect", "ntuplets+select",
                                   "fit+output"], [round(v, 4) for v in stage])),
@@ -424,6 +453,17 @@ def run_pxr(args, rank, world, local):
                          "algorithmic_bytes": ca_alg, "cells": cells, "edges": edges,
                          "note": "latency- and issue-bound (L2-resident gathers, returning "
                                  "atomics); the HBM fraction is low by construction"},
+            "roofline_ca_alu": {"kernel": "k_connect + k_connect_front (CA stage)",
+                                "bound": "alu", "achieved": ca_tflops, "peak": fp32_peak,
+                                "unit": "TFLOP/s", "frac": ca_tflops / fp32_peak,
+                                "peak_source": f"nominal FP32: {sms} SMs x 128 lanes x 2 "
+                                               "(FMA) x 2070 MHz",
+                                "candidates": cand, "ops_per_candidate": CA_OPS_PER_CANDIDATE,
+                                "traffic": None,
+                                "note": "algorithmic: every in-cell x out-cell pair of a "
+                                        "junction hit tested; the kernels skip pairs outside "
+                                        "the r-z cone and the phi window, so this counts "
+                                        "work the definition asks for, not work done"},
             "roofline_k4": {"kernel": "k_doublets", "bound": "hbm", "achieved": achieved,
                             "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                             "peak_source": peak_src,

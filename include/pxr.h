@@ -172,6 +172,15 @@ typedef struct pxr_params {
                                                   stage's grid (PXR_STAGE_*), 1..64; 0 = the
                                                   built-in value.  Results do not depend on it;
                                                   pxr's autotuner picks it with the bin count */
+    uint32_t block_threads[PXR_STAGES];        /* launch shape: threads per CTA of the stage's
+                                                  main kernel; 0 = the built-in value.  Sort:
+                                                  256, 512 or 1024 (built-in 1024); doublets:
+                                                  64, 128 or 256 (built-in 256); fit: 32, 64,
+                                                  128 or 256 (built-in: from the track count).
+                                                  Connect, walk and select take 0 only (their
+                                                  CTAs own fixed chunks of work and shared
+                                                  staging).  Other values: PXR_EINVAL.  Results
+                                                  do not depend on it; pxr's autotuner picks it */
     double pt_min;                             /* selection: GeV, >= 0; 0 = no cut */
     double chi2_max;                           /* selection: chi2 per degree of freedom, >= 0;
                                                   0 = no cut */

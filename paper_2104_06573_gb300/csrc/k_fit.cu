@@ -1012,8 +1012,11 @@ void launch_fit(const DevBatch &b, const DevParams &p, uint32_t total, cudaStrea
 {
     // a few hundred fits are bound by the FP64 pipe of the SMs they run on: small batches take
     // smaller blocks, so that their tracks spread over more SMs
-    uint32_t tpb = 32;
-    while (tpb < 256 && (uint64_t)tpb * sms < total) tpb *= 2;
+    uint32_t tpb = p.block_threads[5];
+    if (tpb == 0) {
+        tpb = 32;
+        while (tpb < 256 && (uint64_t)tpb * sms < total) tpb *= 2;
+    }
     uint64_t blocks = ((uint64_t)total + tpb - 1) / tpb;
     uint64_t cap = (uint64_t)sms * p.grid_per_sm[5] * (256 / tpb);
     if (blocks > cap) blocks = cap;

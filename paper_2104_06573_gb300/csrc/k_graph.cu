@@ -283,14 +283,15 @@ void launch_doublets(const DevBatch &b, const DevParams &p, cudaStream_t s, int 
     uint32_t slots = 1;
     for (uint32_t l = 0; l < p.n_layers; ++l) slots = p.n_out[l] > slots ? p.n_out[l] : slots;
     const uint64_t warps = ((uint64_t)b.N * slots + 31) / 32;     // one warp per 32 items
-    uint64_t blocks = (warps + 7) / 8;
+    const uint32_t tpb = p.block_threads[1];
+    uint64_t blocks = (warps + tpb / 32 - 1) / (tpb / 32);
     const uint64_t cap = (uint64_t)sms * p.grid_per_sm[1];
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
     if (p.cut_mode == CUT_FP64)
-        k_doublets<true><<<(unsigned)blocks, 256, 0, s>>>(b, p, slots);
+        k_doublets<true><<<(unsigned)blocks, tpb, 0, s>>>(b, p, slots);
     else
-        k_doublets<false><<<(unsigned)blocks, 256, 0, s>>>(b, p, slots);
+        k_doublets<false><<<(unsigned)blocks, tpb, 0, s>>>(b, p, slots);
 }
 
 void launch_doublets_compact(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms)
@@ -483,7 +484,6 @@ __device__ __forceinline__ uint32_t ca_ranges(const DevBatch &b, const DevParams
     return nr;
 }
 
-constexpr int kCaWarps = 8;
 constexpr int kEdgeBuf = 8;     // passes buffered per cell; a longer list is found again
 #ifndef PXR_CA_MINB
 #define PXR_CA_MINB 2           // CTAs per SM the CA kernels are compiled for (register budget)

@@ -173,7 +173,7 @@ void launch_sort(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms)
     if (grid == 0) return;
     const uint32_t gk = b.gpos ? p.n_glayers * p.gphi * p.gz : 0u;
     const size_t smem = (size_t)(p.n_keys > gk ? p.n_keys : gk) * sizeof(uint32_t);
-    k_sort<<<grid, 1024, smem, s>>>(b, p);
+    k_sort<<<grid, p.block_threads[0], smem, s>>>(b, p);
 }
 
 // Per-event, per-layer hit counts (used once to size a plan's per-event capacities).

@@ -61,6 +61,7 @@ struct DevParams {
     float dca32;                        // dca_cut rounded to float
     float tan_win;                      // tan(asin(theta_cut) + margin); inf when theta_cut >= 1
     uint32_t grid_per_sm[6];            // CTAs per SM at most, per stage (sort ... fit)
+    uint32_t block_threads[6];          // threads per CTA per stage (fit: 0 = from the track count)
     uint32_t gphi, gz;                  // hit grid: coarse azimuth bins (bin = fine bin * gphi
                                         //   / nb) and bins of the free coordinate per layer
     uint32_t n_glayers;                 // layers in the grid: the out-layers of the pairs that

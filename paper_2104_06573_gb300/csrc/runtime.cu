@@ -124,6 +124,19 @@ static int check_params(const pxr_params *p, DevParams *d)
         return fail(PXR_EINVAL, "n_phi_bins must be 0 or in [64, 2048]");
     for (int k = 0; k < PXR_STAGES; ++k)
         if (p->grid_per_sm[k] > 64) return fail(PXR_EINVAL, "grid_per_sm must be in [0, 64]");
+    {
+        // threads per CTA each stage's kernels accept (0 = built-in; a zero row: 0 only)
+        static const uint32_t kBlockOk[PXR_STAGES][4] = {
+            {256, 512, 1024, 0}, {64, 128, 256, 0}, {0}, {0}, {0}, {32, 64, 128, 256}};
+        for (int k = 0; k < PXR_STAGES; ++k) {
+            const uint32_t t = p->block_threads[k];
+            bool ok = t == 0;
+            for (int i = 0; i < 4 && !ok; ++i) ok = kBlockOk[k][i] == t;
+            if (!ok)
+                return fail(PXR_EINVAL, "block_threads: sort 256/512/1024, doublets 64/128/256, "
+                                        "fit 32/64/128/256, connect/walk/select 0 only");
+        }
+    }
     if (!(p->pt_min >= 0.0) || !(p->chi2_max >= 0.0) || !std::isfinite(p->pt_min) ||
         !std::isfinite(p->chi2_max) || p->clean_shared > 1)
         return fail(PXR_EINVAL, "pt_min and chi2_max must be finite and >= 0, clean_shared 0 or 1");
@@ -217,6 +230,9 @@ static int check_params(const pxr_params *p, DevParams *d)
     static const uint32_t kGridDefault[PXR_STAGES] = {4, 16, 16, 8, 8, 8};
     for (int k = 0; k < PXR_STAGES; ++k)
         d->grid_per_sm[k] = p->grid_per_sm[k] ? p->grid_per_sm[k] : kGridDefault[k];
+    static const uint32_t kBlockDefault[PXR_STAGES] = {1024, 256, 0, 0, 0, 0};
+    for (int k = 0; k < PXR_STAGES; ++k)
+        d->block_threads[k] = p->block_threads[k] ? p->block_threads[k] : kBlockDefault[k];
     return PXR_OK;
 }
 

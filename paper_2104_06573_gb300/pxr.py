@@ -43,7 +43,8 @@ class pxr_params(C.Structure):
                 ("sigma_rphi", C.c_double), ("sigma_z", C.c_double),
                 ("x_over_x0", C.c_double), ("n_phi_bins", C.c_uint32),
                 ("max_cells_per_event", C.c_uint32), ("max_tuples_per_event", C.c_uint32),
-                ("grid_per_sm", C.c_uint32 * 6), ("pt_min", C.c_double), ("chi2_max", C.c_double),
+                ("grid_per_sm", C.c_uint32 * 6), ("block_threads", C.c_uint32 * 6),
+                ("pt_min", C.c_double), ("chi2_max", C.c_double),
                 ("clean_shared", C.c_uint32), ("fit_cov", C.c_uint32),
                 ("vertexing", C.c_uint32), ("vtx_min_tracks", C.c_uint32), ("vtx_gap", C.c_double)]
 
