@@ -174,7 +174,7 @@ typedef struct pxr_params {
                                                   pxr's autotuner picks it with the bin count */
     uint32_t block_threads[PXR_STAGES];        /* launch shape: threads per CTA of the stage's
                                                   main kernel; 0 = the built-in value.  Sort:
-                                                  256, 512 or 1024 (built-in 1024); doublets:
+                                                  256, 512 or 1024 (built-in 512); doublets:
                                                   64, 128 or 256 (built-in 256); fit: 32, 64,
                                                   128 or 256 (built-in: from the track count).
                                                   Connect, walk and select take 0 only (their
@@ -361,6 +361,14 @@ int pxr_plan_debug(pxr_plan *plan, uint32_t e, int what, uint32_t *buf, uint32_t
 /* Number of kernel launches one pxr_plan_run performs (for launch accounting).
  * Source: none (measurement plumbing). */
 int pxr_plan_launches(const pxr_plan *plan);
+
+/* Run the plan once like pxr_plan_run, but without its graph and with the CA stage counting its
+ * work, wait for it, and write to counts[2]: the candidate triplets whose r-z alignment test
+ * was evaluated, and of them the ones whose transverse-DCA test was evaluated.  The results of
+ * the run equal those of pxr_plan_run (the counting costs time; the run is not meant to be
+ * timed).  Errors: PXR_EINVAL for a null argument, PXR_ECUDA.
+ * Source: §2 (the CA's triplet tests); the counts size the CA stage's arithmetic roofline. */
+int pxr_plan_count_ca_tests(pxr_plan *plan, void *stream, uint64_t *counts);
 
 /* Per-event counters of the last run, copied to the host array out[5 * n_events]: out[k*E + e]
  * for k = 0 cells, 1 CA edges, 2 ntuplets before selection, 3 flags (1 cells, 2 edges,

@@ -332,6 +332,13 @@ __device__ __noinline__ bool triplet_exact(const double *r64, const uint32_t *ce
                  (double)hk.y) <= dca;
 }
 
+// Warp-aggregated count of the calling lanes into *c.
+__device__ __forceinline__ void count_lanes(unsigned long long *c)
+{
+    const uint32_t m = __activemask();
+    if ((threadIdx.x & 31u) == (uint32_t)(__ffs(m) - 1)) atomicAdd(c, (unsigned long long)__popc(m));
+}
+
 // Exact decision for the triplet (i, j, k), k the outer hit of the out-cell B = (j, k):
 // r-z alignment, then DCA.  FP32 mode decides in float when outside the guard bands and takes
 // the FP64 formulas otherwise (FP64 mode always).
@@ -340,6 +347,7 @@ __device__ __forceinline__ bool triplet_test(const DevBatch &b, const DevParams 
                                              uint32_t j, uint32_t B, float xi, float yi,
                                              float4 hj, float4 hk, const RZ32 &a)
 {
+    if (b.ca_tests) count_lanes(b.ca_tests);
     if constexpr (F64) {
         if (theta32(a, rz32(hj, hk), p.theta32) == 0) return false;
         const uint32_t k = b.cell_out[B];
@@ -348,12 +356,14 @@ __device__ __forceinline__ bool triplet_test(const DevBatch &b, const DevParams 
         if (!theta64(ri, zi, rj, zj, rk, zk, seglen64(ri, zi, rj, zj), seglen64(rj, zj, rk, zk),
                      p.theta))
             return false;
+        if (b.ca_tests) count_lanes(b.ca_tests + 1);
         if (dca32(xi, yi, hj.x, hj.y, hk.x, hk.y, p.dca32) == 0) return false;
         return dca64((double)xi, (double)yi, (double)hj.x, (double)hj.y, (double)hk.x,
                      (double)hk.y) <= p.dca;
     } else {
         const int th = theta32(a, rz32(hj, hk), p.theta32);
         if (th == 0) return false;
+        if (b.ca_tests) count_lanes(b.ca_tests + 1);
         const int dc = dca32(xi, yi, hj.x, hj.y, hk.x, hk.y, p.dca32);
         if (th == 1 && dc >= 0) return dc == 1;
         return triplet_exact(b.r64, b.cell_out, b.hs, i, j, B, xi, yi, hj, hk, th < 0, dc,

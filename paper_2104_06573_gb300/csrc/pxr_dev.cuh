@@ -134,6 +134,9 @@ struct DevBatch {
                                         //   kNone: a slot reserved for a cell already listed)
     uint32_t *front_in;                 // [edges] the inner hits of the frontier cells
     uint32_t *jbase;                    // [E + 1] junction prefix of a dense CA level
+    unsigned long long *ca_tests;       // [2] or null: CA candidate tests evaluated (r-z test) and
+                                        //   of them the ones whose DCA was evaluated (counted
+                                        //   only when non-null)
     uint32_t *front_snap;               // [E] frontier lengths when a sparse pass starts (the pass
                                         //   appends for later levels while it reads)
     // ntuplets

@@ -230,7 +230,7 @@ static int check_params(const pxr_params *p, DevParams *d)
     static const uint32_t kGridDefault[PXR_STAGES] = {4, 16, 16, 8, 8, 8};
     for (int k = 0; k < PXR_STAGES; ++k)
         d->grid_per_sm[k] = p->grid_per_sm[k] ? p->grid_per_sm[k] : kGridDefault[k];
-    static const uint32_t kBlockDefault[PXR_STAGES] = {1024, 256, 0, 0, 0, 0};
+    static const uint32_t kBlockDefault[PXR_STAGES] = {512, 256, 0, 0, 0, 0};
     for (int k = 0; k < PXR_STAGES; ++k)
         d->block_threads[k] = p->block_threads[k] ? p->block_threads[k] : kBlockDefault[k];
     return PXR_OK;
@@ -292,7 +292,7 @@ struct PlanOffsets {
         head_end;
     size_t cnt, bkt, hs, r64, hmeta, hphi, gofs, gpos, gfree, glay, item, cell_out,
         nbr_first,
-        nbr_n, nbr, mindepth, root_list, root_in, live, front_list, front_in, front_snap, jbase, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, tup_tmp, canon_cnt, out_evt, o_nh,
+        nbr_n, nbr, mindepth, root_list, root_in, live, front_list, front_in, front_snap, jbase, ca_tests, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, tup_tmp, canon_cnt, out_evt, o_nh,
         o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status, o_ql, best, o_cov, o_vtx,
         v_z, v_err, v_pt2, v_n;
     size_t total;
@@ -341,6 +341,7 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.front_in = L.add(4 * G);
     o.front_snap = L.add(4 * (size_t)E);
     o.jbase = L.add(4 * ((size_t)E + 1));
+    o.ca_tests = L.add(16);
     o.tup_hits = L.add(4 * T * kMaxHits);
     o.tup_n = L.add(T);
     o.tup_state = L.add(T);
@@ -699,10 +700,11 @@ static void fill_chunks(const pxr_plan *P, char *head)
     std::memcpy(head + P->off.hit_chunk, P->hit_chunk.data(), 4 * P->hit_chunk.size());
 }
 
-static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false)
+static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false,
+                        const DevBatch *db = nullptr)
 {
     Range range("pxr.enqueue");
-    const DevBatch &b = P->db;
+    const DevBatch &b = db ? *db : P->db;
     const DevParams &p = P->dp;
     int sms = P->ctx->sms;
     char *r = P->region;
@@ -894,6 +896,24 @@ extern "C" int pxr_plan_run(pxr_plan *P, void *stream)
 }
 
 extern "C" int pxr_plan_launches(const pxr_plan *P) { return P ? plan_launches(P) : 0; }
+
+extern "C" int pxr_plan_count_ca_tests(pxr_plan *P, void *stream, uint64_t *counts)
+{
+    if (!P || !counts) return fail(PXR_EINVAL, "null argument");
+    int rc = set_device(P->ctx);
+    if (rc) return rc;
+    cudaStream_t s = stream ? (cudaStream_t)stream : P->ctx->stream;
+    DevBatch b = P->db;
+    b.ca_tests = (unsigned long long *)(P->region + P->off.ca_tests);
+    CK(cudaMemsetAsync(b.ca_tests, 0, 16, s));
+    if ((rc = plan_enqueue(P, s, false, &b))) return rc;
+    CK(cudaMemcpyAsync(counts, b.ca_tests, 16, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaEventRecord(P->ev_done, s));
+    P->last_stream = s;
+    P->has_run = true;
+    return PXR_OK;
+}
 
 extern "C" int pxr_plan_counts(pxr_plan *P, uint32_t *out)
 {

@@ -112,6 +112,7 @@ def load(build_if_missing: bool = False):
             "pxr_plan_tracks": (i32, [vp, u32, P(pxr_tracks)]),
             "pxr_plan_debug": (i32, [vp, u32, i32, P(u32), u32, P(u32)]),
             "pxr_plan_launches": (i32, [vp]),
+            "pxr_plan_count_ca_tests": (i32, [vp, vp, P(C.c_uint64)]),
             "pxr_plan_counts": (i32, [vp, P(u32)]),
             "pxr_plan_stage_ms": (i32, [vp, P(C.c_float), i32, P(i32)]),
             "pxr_plan_destroy": (None, [vp]),
@@ -446,6 +447,12 @@ class Plan:
 
     def pxr_plan_launches(self) -> int:
         return load().pxr_plan_launches(self.h)
+
+    def pxr_plan_count_ca_tests(self, stream=None) -> tuple:
+        """One untimed run with the CA stage counting its work: (r-z tests, DCA tests)."""
+        out = (C.c_uint64 * 2)()
+        _check(load().pxr_plan_count_ca_tests(self.h, ptr(stream), out))
+        return int(out[0]), int(out[1])
 
     def pxr_plan_counts(self) -> dict:
         """Per-event counters of the last run: cells, edges, tuples, flags, tracks."""

@@ -361,6 +361,35 @@ def test_graph_equals_direct_and_bin_counts(ctx, orc):
     check_event(orc, ev, P, ref)
 
 
+@pytest.mark.parametrize("cut", [pxr.CUT_FP64, pxr.CUT_FP32])
+def test_counted_run_equals_plain_run(ctx, cut):
+    """The run that counts the CA's tests gives the plain run's results, and its counts are
+    consistent: every edge passed both tests, the DCA test runs only after a passed r-z test, and
+    no more r-z tests run than candidate pairs exist (every cell into a hit with every cell out
+    of it)."""
+    P = synth.params_phase1()
+    evs = [ev_tuple(synth.make_event(40 + k, n, with_disks=True, pt_mode="power3", pt_lo=0.5,
+                                     eta_max=2.5, smear=True, noise_frac=0.2))
+           for k, n in enumerate([300, 900])]
+    off, x, y, z, layer = to_dev(evs)
+    plan = pxr.Plan(ctx, off, x, y, z, layer, pxr.params_from(P, cut_mode=cut), use_graph=True)
+    plan.pxr_plan_run()
+    want = [plan.pxr_plan_tracks(e) for e in range(len(evs))]
+    n_rz, n_dca = plan.pxr_plan_count_ca_tests()
+    got = [plan.pxr_plan_tracks(e) for e in range(len(evs))]
+    for a, b in zip(want, got):
+        for k in pxr.TRACK_FIELDS:
+            assert np.array_equal(a[k], b[k]), k
+    edges = int(plan.pxr_plan_counts()["edges"].sum())
+    cand = 0
+    for e in range(len(evs)):
+        c = plan.pxr_plan_debug(e, 0).astype(np.int64)
+        m = int(c.max()) + 1
+        cand += int(np.dot(np.bincount(c[:, 1], minlength=m), np.bincount(c[:, 0], minlength=m)))
+    plan.close()
+    assert 0 < edges <= n_dca <= n_rz <= cand
+
+
 def test_overflow_is_flagged_not_written(ctx):
     P = synth.params_barrel_quadruplets()
     ev = ev_tuple(synth.event_barrel(0))
