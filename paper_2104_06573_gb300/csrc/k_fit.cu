@@ -271,6 +271,178 @@ __device__ __forceinline__ bool broken_line_n(const T (&h)[N], const T (&meas)[N
     return true;
 }
 
+// Elimination of one view's normal equations in the kink parametrisation, the steps of
+// broken_line_n: the kink block A (K x K, lower part) factored, the border B (K x G) and the
+// right-hand side rb carried through it, the globals' Schur complement Gm - Y^T Y (G x G) factored
+// and solved, then the kinks.  On return tg holds the globals and rb the kinks.
+template <int K, int G, typename T>
+__device__ __forceinline__ bool bl_eliminate(T (&A)[K][K], T (&B)[K][G], T (&Gm)[G][G],
+                                             T (&rb)[K], T (&rg)[G], T (&tg)[G])
+{
+    if (!chol_factor<K, T>(A)) return false;
+    chol_lower<K, T>(A, rb);
+#pragma unroll
+    for (int c = 0; c < G; ++c) {
+        T col[K];
+#pragma unroll
+        for (int a = 0; a < K; ++a) col[a] = B[a][c];
+        chol_lower<K, T>(A, col);
+#pragma unroll
+        for (int a = 0; a < K; ++a) B[a][c] = col[a];
+    }
+#pragma unroll
+    for (int c = 0; c < G; ++c) {
+#pragma unroll
+        for (int d = 0; d <= c; ++d) {
+            T v = Gm[c][d];
+#pragma unroll
+            for (int a = 0; a < K; ++a) v -= B[a][c] * B[a][d];
+            Gm[c][d] = v;
+        }
+        T v = rg[c];
+#pragma unroll
+        for (int a = 0; a < K; ++a) v -= B[a][c] * rb[a];
+        rg[c] = v;
+    }
+    if (!chol_factor<G, T>(Gm)) return false;
+#pragma unroll
+    for (int c = 0; c < G; ++c) tg[c] = rg[c];
+    chol_lower<G, T>(Gm, tg);
+    chol_upper<G, T>(Gm, tg);
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+        T v = rb[a];
+#pragma unroll
+        for (int c = 0; c < G; ++c) v -= B[a][c] * tg[c];
+        rb[a] = v;
+    }
+    chol_upper<K, T>(A, rb);
+    return true;
+}
+
+// Both views of a track whose hits share one measurement weight per view (wT, wL) and one kink
+// weight per view (every hit on a barrel layer): the minimisers of broken_line_n for the two
+// views.  Divided by its measurement weight, a view's normal matrix is J^T J with
+// lam = kink weight / measurement weight added on the kink diagonal, where J (d x_i / d theta) is
+// the same arc-length geometry in both views; the transverse view has the extra curvature
+// column.  J^T J is therefore built once, with no weights in it, and each view adds its lam and
+// right-hand side.  Returns both views' fitted points, delta, and the summed chi2 of both views
+// (the measurement weights put back).
+template <int N, typename T>
+__device__ __forceinline__ bool broken_line_pair(const T (&h)[N], const T (&mT)[N],
+                                                 const T (&mL)[N], T wT, T wL, T lamT, T lamL,
+                                                 T (&xT)[N], T (&xL)[N], T &delta, T &chi2)
+{
+    constexpr int K = N - 2;                 // kinks
+    T S[N], jd[N];                           // s_i - s_0; d x_i / d delta
+    S[0] = T(0);
+#pragma unroll
+    for (int i = 1; i < N; ++i) S[i] = S[i - 1] + h[i - 1];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        T a = T(0);
+#pragma unroll
+        for (int j = 1; j < i && j + 1 < N; ++j) a -= T(0.5) * (h[j - 1] + h[j]) * (S[i] - S[j]);
+        jd[i] = a;
+    }
+    auto jk = [&](int i, int j) { return i > j ? S[i] - S[j] : T(0); };   // j = 1..K
+    auto jg = [&](int i, int c) { return c == 0 ? T(1) : c == 1 ? S[i] : jd[i]; };
+    // the shared geometry J^T J: kink block, border, globals (x_0, slope, delta)
+    T A[K][K], B[K][3], Gm[3][3], rbT[K], rbL[K], rgT[3], rgL[2];
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+#pragma unroll
+        for (int b = 0; b <= a; ++b) {
+            T v = T(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) v += jk(i, a + 1) * jk(i, b + 1);
+            A[a][b] = v;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            T v = T(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) v += jk(i, a + 1) * jg(i, c);
+            B[a][c] = v;
+        }
+        T vT = T(0), vL = T(0);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            vT += jk(i, a + 1) * mT[i];
+            vL += jk(i, a + 1) * mL[i];
+        }
+        rbT[a] = vT;
+        rbL[a] = vL;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int d = 0; d <= c; ++d) {
+            T v = T(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) v += jg(i, c) * jg(i, d);
+            Gm[c][d] = v;
+        }
+        T vT = T(0), vL = T(0);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            vT += jg(i, c) * mT[i];
+            vL += jg(i, c) * mL[i];
+        }
+        rgT[c] = vT;
+        if (c < 2) rgL[c] = vL;
+    }
+    // each view: its kink weight ratio on the diagonal, then the elimination
+    T AT[K][K], AL[K][K], BT[K][3], BL[K][2], GT[3][3], GL[2][2], tgT[3], tgL[2];
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+#pragma unroll
+        for (int b = 0; b <= a; ++b) {
+            AT[a][b] = a == b ? A[a][b] + lamT : A[a][b];
+            AL[a][b] = a == b ? A[a][b] + lamL : A[a][b];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            BT[a][c] = B[a][c];
+            if (c < 2) BL[a][c] = B[a][c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d <= c; ++d) {
+            GT[c][d] = Gm[c][d];
+            if (c < 2) GL[c][d] = Gm[c][d];
+        }
+    if (!bl_eliminate<K, 3, T>(AT, BT, GT, rbT, rgT, tgT)) return false;
+    if (!bl_eliminate<K, 2, T>(AL, BL, GL, rbL, rgL, tgL)) return false;
+    delta = tgT[2];
+    T c2T = T(0), c2L = T(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        T vT = tgT[0] + S[i] * tgT[1] + jd[i] * tgT[2];
+        T vL = tgL[0] + S[i] * tgL[1];
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+            vT += jk(i, a + 1) * rbT[a];
+            vL += jk(i, a + 1) * rbL[a];
+        }
+        xT[i] = vT;
+        xL[i] = vL;
+        const T rT = mT[i] - vT, rL = mL[i] - vL;
+        c2T += rT * rT;
+        c2L += rL * rL;
+    }
+    T kT = T(0), kL = T(0);
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+        kT += rbT[a] * rbT[a];
+        kL += rbL[a] * rbL[a];
+    }
+    chi2 = wT * (c2T + lamT * kT) + wL * (c2L + lamL * kL);
+    return true;
+}
+
 // Geometry of the conversion: the reference circle (reciprocal radius, centre, orientation) in
 // the frame of hit 0, the first arc-length step (and its reciprocal), hit 0, and K B.
 template <typename T>
@@ -713,8 +885,18 @@ __device__ __noinline__ void fit_split_n(const float *X, const float *Y, const f
         ok = ok && isfinite(wkT[j]) && isfinite(wkL[j]) && wkT[j] > 0.0 && wkL[j] > 0.0;
     double xT[N], xL[N], delta = 0.0, dummy, chi2T = 0.0, chi2L = 0.0;
     double cvT[6], cvL[3];
-    ok = ok && broken_line_n<N, true, double, COV>(h, y64, wT, wkT, xT, delta, chi2T, cvT) &&
-         broken_line_n<N, false, double, COV>(h, z64, wL, wkL, xL, dummy, chi2L, cvL);
+    if (!COV && !any_disk) {
+        // every hit on a barrel layer: one measurement and one kink weight per view, the
+        // geometry shared (the kink weights over the measurement weights; 1 / wz is sigma_z^2
+        // to float rounding, far below the kink weights' own float rounding)
+        const double lamT = wkT[1] * (p.sigma_rphi * p.sigma_rphi);
+        const double lamL = wkL[1] * (p.sigma_z * p.sigma_z);
+        ok = ok && broken_line_pair<N, double>(h, y64, z64, wrphi, wL[0], lamT, lamL, xT, xL,
+                                               delta, chi2T);
+    } else {
+        ok = ok && broken_line_n<N, true, double, COV>(h, y64, wT, wkT, xT, delta, chi2T, cvT) &&
+             broken_line_n<N, false, double, COV>(h, z64, wL, wkL, xL, dummy, chi2L, cvL);
+    }
     // 6. conversion in double: |C| and 1/|C| by two Newton steps from float (the fitted circle's
     // distance from the beam line needs its centre and radius consistent to ~1e-16 relative at
     // R0 ~ 1e7 cm), the chord direction to unit length, C turned back to the global frame
