@@ -14,8 +14,12 @@
 // passes compute their cell's index from j's rank in i's window and append their edge lists
 // through one atomic per warp.  Ntuplets: one warp per root hit walks the out-edges of its
 // cells depth first.  Selection removes suffix paths and assigns output slots.
+#include <cooperative_groups.h>
+
 #include "pxr_dev.cuh"
 #include "pxr_cuts.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pxr {
 
@@ -496,7 +500,10 @@ __device__ __forceinline__ uint32_t ca_ranges(const DevBatch &b, const DevParams
 
 constexpr int kEdgeBuf = 8;     // passes buffered per cell; a longer list is found again
 #ifndef PXR_CA_MINB
-#define PXR_CA_MINB 2           // CTAs per SM the CA kernels are compiled for (register budget)
+#define PXR_CA_MINB 4           // CTAs per SM the sparse CA kernel is compiled for (registers)
+#endif
+#ifndef PXR_CONN_MINB
+#define PXR_CONN_MINB 4         // CTAs per SM the dense CA kernel is compiled for (registers)
 #endif
 
 // One warp's cells (one per lane), their queries and passes, in shared memory: the warp works
@@ -734,7 +741,7 @@ __device__ __forceinline__ float funord(int i) { return __int_as_float(i >= 0 ? 
 // junction's own records, its first out-cell list and inner window) so that a junction waits on
 // few memory round trips.
 template <bool F64>
-__global__ void __launch_bounds__(kConnWarps * 32, 4) k_connect(DevBatch b, DevParams p,
+__global__ void __launch_bounds__(kConnWarps * 32, PXR_CONN_MINB) k_connect(DevBatch b, DevParams p,
                                                                 uint32_t layer_mask)
 {
     __shared__ float4 s_h[kConnWarps][kStage];      // staged out-cells' outer hits (list order)
@@ -1159,7 +1166,8 @@ void launch_connect_front(const DevBatch &b, const DevParams &p, uint32_t total,
 // Ntuplets: depth-first walk from every root cell
 // ------------------------------------------------------------------------------------------
 // Depth-first walk from one root cell A; emits every path that has max_hits hits or ends at a
-// cell without out-edges, if it has at least min_hits hits.
+// cell without out-edges, if it has at least min_hits hits.  All lanes of a calling warp walk
+// in the same event e.
 __device__ __forceinline__ void walk_from(const DevBatch &b, const DevParams &p, uint32_t e,
                                           uint32_t A, uint32_t a_in)
 {
@@ -1175,7 +1183,11 @@ __device__ __forceinline__ void walk_from(const DevBatch &b, const DevParams &p,
         const uint32_t ne = b.nbr_n[c];
         if (next[d] == 0 && (nh >= p.max_hits || ne == 0)) {
             if (nh >= p.min_hits) {
-                const uint32_t slot = atomicAdd(&b.cnt[C_TUPLES * b.E + e], 1u);
+                // one reservation for the lanes that emit together (a warp's walks share e)
+                const cg::coalesced_group g = cg::coalesced_threads();
+                uint32_t base = 0;
+                if (g.thread_rank() == 0) base = atomicAdd(&b.cnt[C_TUPLES * b.E + e], g.size());
+                const uint32_t slot = g.shfl(base, 0) + g.thread_rank();
                 if (slot < tcap) {
                     const uint32_t t = b.tup_off[e] + slot;
                     uint32_t *th = b.tup_hits + (size_t)t * kMaxHits;
@@ -1341,14 +1353,17 @@ __device__ __forceinline__ uint32_t tup_caller(const DevBatch &b, uint32_t t, in
     return q < b.tup_n[t] ? b.hmeta[b.tup_hits[(size_t)t * kMaxHits + q]] & kLocalMask : kNone;
 }
 
+constexpr uint32_t kCanonSmem = 32768;     // events with more hits count in global memory
+
 // Canonical order of each event's kept ntuplets: lexicographic by their hits' caller indices
 // (unused slots as kNone), so that a result does not depend on the batch or on the order in
 // which the walk found the ntuplets.  A counting sort by the first hit (per-hit counters of the
-// event), then each bucket (the ntuplets sharing a first hit: a few) by insertion on the
-// remaining hits; tup_list receives the order, in which the fit writes the tracks.  One CTA per
-// event.
+// event, in shared memory up to kCanonSmem hits), then each bucket (the ntuplets sharing a first
+// hit: a few) by insertion on the remaining hits; tup_list receives the order, in which the fit
+// writes the tracks.  One CTA per event.
 __global__ void __launch_bounds__(1024) k_canon(DevBatch b)
 {
+    extern __shared__ uint32_t s_cnt[];        // the bucket counters of events up to kCanonSmem hits
     __shared__ uint32_t s_warp[32];
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
     for (uint32_t e = blockIdx.x; e < b.E; e += gridDim.x) {
@@ -1356,7 +1371,7 @@ __global__ void __launch_bounds__(1024) k_canon(DevBatch b)
         const uint32_t t0 = b.tup_off[e];
         const uint32_t n = b.out_evt[e + 1] - b.out_evt[e];
         if (n < 2) continue;                                       // uniform over the CTA
-        uint32_t *cnt = b.canon_cnt + h0;
+        uint32_t *cnt = nh <= kCanonSmem ? s_cnt : b.canon_cnt + h0;   // uniform over the CTA
         uint32_t *tmp = b.tup_tmp + t0;
         for (uint32_t c = tid; c < nh; c += nt) cnt[c] = 0;
         __syncthreads();
@@ -1398,7 +1413,13 @@ void launch_canon(const DevBatch &b, cudaStream_t s, int sms)
 {
     const uint32_t grid = b.E < (uint32_t)sms * 2 ? b.E : (uint32_t)sms * 2;
     if (grid == 0) return;
-    k_canon<<<grid, 1024, 0, s>>>(b);
+    k_canon<<<grid, 1024, kCanonSmem * sizeof(uint32_t), s>>>(b);
+}
+
+cudaError_t init_graph_kernels()
+{
+    return cudaFuncSetAttribute(k_canon, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kCanonSmem * (int)sizeof(uint32_t));
 }
 
 }  // namespace pxr

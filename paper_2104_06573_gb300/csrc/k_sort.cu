@@ -219,6 +219,7 @@ cudaError_t init_kernels()
     cudaError_t e = cudaFuncSetAttribute(k_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kMaxLayers * 2048 * (int)sizeof(uint32_t));
     if (e != cudaSuccess) return e;
+    if ((e = init_graph_kernels()) != cudaSuccess) return e;
     return init_fit_kernels();
 }
 

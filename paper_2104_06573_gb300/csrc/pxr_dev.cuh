@@ -231,6 +231,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t *s, uint32_t n
 // One-time kernel attributes (large dynamic shared memory of the sort kernel).
 cudaError_t init_kernels();
 cudaError_t init_fit_kernels();     // (called by init_kernels)
+cudaError_t init_graph_kernels();   // (called by init_kernels)
 
 // Kernel launchers (defined in the .cu files).
 void launch_sort(const DevBatch &b, const DevParams &p, cudaStream_t s, int sms);
