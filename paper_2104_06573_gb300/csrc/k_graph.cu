@@ -416,11 +416,11 @@ __device__ __forceinline__ void mark_reached(const DevBatch &b, uint32_t e, uint
         // nothing to append: the mark needs no answer, and clearing the count again is harmless
         // (C's own edges are written by a later launch)
         atomicOr(&b.live[C >> 5], bit);
-        b.nbr_n[C] = 0u;
+        b.nbr_head[C].y = 0u;
         return;
     }
     if (atomicOr(&b.live[C >> 5], bit) & bit) return;
-    b.nbr_n[C] = 0u;
+    b.nbr_head[C].y = 0u;
     const uint32_t cap = b.edge_off[e + 1] - b.edge_off[e];
     const uint32_t x = atomicAdd(&b.cnt[C_FRONT * b.E + e], 1u);
     if (x < cap) {
@@ -658,13 +658,12 @@ __device__ __forceinline__ uint32_t ca_append(const DevBatch &b, uint32_t e, boo
             atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
         }
     }
-    b.nbr_first[A] = g0 + my0;
-    b.nbr_n[A] = nw;
+    b.nbr_head[A] = make_uint2(g0 + my0, nw);
     for (uint32_t t = 0; t < nbuf; ++t) {
         const uint32_t Bf = W.buf[t][lane], B = Bf & 0x7FFFFFFFu;
         const bool fr_t = (fresh >> t) & 1u;
         if (t < nw) b.nbr[g0 + my0 + t] = B;
-        if (fr_t) b.nbr_n[B] = 0u;
+        if (fr_t) b.nbr_head[B].y = 0u;
         if (Bf >> 31) {
             if (fbase < cap) {
                 b.front_list[g0 + fbase] = fr_t ? B : kNone;
@@ -716,7 +715,10 @@ __device__ __noinline__ void ca_rest(const DevBatch &b, const DevParams &p, uint
 
 constexpr int kConnWarps = 8;
 constexpr int kStage = 256;     // out-cells of one junction staged per out-layer slot
-constexpr int kBins = 128;      // local bins of the free coordinate (multiple of 32)
+#ifndef PXR_CONN_BINS
+#define PXR_CONN_BINS 128
+#endif
+constexpr int kBins = PXR_CONN_BINS;   // local bins of the free coordinate (multiple of 32)
 
 // Order-preserving int encoding of floats (for warp min / max reductions).
 __device__ __forceinline__ int ford(float f)
@@ -945,7 +947,11 @@ __global__ void __launch_bounds__(kConnWarps * 32, PXR_CONN_MINB) k_connect(DevB
                     // ---- append the edges: one atomic per warp reserves all lanes' lists ----
                     const bool ok = npass && A != kNone;   // kNone: the cell was dropped (overflow)
                     uint32_t have = 0, old = 0;
-                    if (ok && s > 0) { have = b.nbr_n[A]; old = b.nbr_first[A]; }
+                    if (ok && s > 0) {
+                        const uint2 hd = b.nbr_head[A];
+                        have = hd.y;
+                        old = hd.x;
+                    }
                     const uint32_t need = ok ? have + npass : 0u;
                     uint32_t incl = need;
 #pragma unroll
@@ -978,7 +984,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, PXR_CONN_MINB) k_connect(DevB
                     // a cell reached for the first time: its edge count cleared and, if its outer
                     // hit starts further pairs, the frontier entry (one reservation per warp)
                     const bool fresh = ok && !(was & bit);
-                    if (fresh) b.nbr_n[Bf] = 0u;
+                    if (fresh) b.nbr_head[Bf].y = 0u;
                     if (ok && front) {
                         if (fbase < cap) {
                             b.front_list[b.edge_off[e] + fbase] = fresh ? Bf : kNone;
@@ -1021,8 +1027,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, PXR_CONN_MINB) k_connect(DevB
                                 mark_reached(b, e, B, j, front);
                             }
                         }
-                        b.nbr_first[A] = first;
-                        b.nbr_n[A] = wr;
+                        b.nbr_head[A] = make_uint2(first, wr);
                     }
                 }
             }
@@ -1180,7 +1185,8 @@ __device__ __forceinline__ void walk_from(const DevBatch &b, const DevParams &p,
     while (d >= 0) {
         const uint32_t c = cells[d];
         const uint32_t nh = (uint32_t)d + 2u;
-        const uint32_t ne = b.nbr_n[c];
+        const uint2 hd = b.nbr_head[c];
+        const uint32_t ne = hd.y;
         if (next[d] == 0 && (nh >= p.max_hits || ne == 0)) {
             if (nh >= p.min_hits) {
                 // one reservation for the lanes that emit together (a warp's walks share e)
@@ -1205,7 +1211,7 @@ __device__ __forceinline__ void walk_from(const DevBatch &b, const DevParams &p,
             continue;
         }
         if (next[d] < ne) {
-            const uint32_t nxt = b.nbr[b.nbr_first[c] + next[d]];
+            const uint32_t nxt = b.nbr[hd.x + next[d]];
             ++next[d];
             ++d;
             cells[d] = nxt;

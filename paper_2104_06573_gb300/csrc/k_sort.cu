@@ -223,13 +223,16 @@ cudaError_t init_kernels()
     return init_fit_kernels();
 }
 
-// Cluster size: about 4096 hits per CTA on the batch's mean event, a power of two up to 8 (the
-// portable cluster size limit).
+// Cluster size: about PXR_SORT_HITS hits per CTA on the batch's mean event, a power of two up to
+// 8 (the portable cluster size limit).
+#ifndef PXR_SORT_HITS
+#define PXR_SORT_HITS 4096
+#endif
 static uint32_t sort_cluster(const DevBatch &b)
 {
     const uint64_t mean = b.E ? (uint64_t)b.N / b.E : 0;
     uint32_t C = 1;
-    while (C < 8 && (uint64_t)C * 4096 < mean) C <<= 1;
+    while (C < 8 && (uint64_t)C * PXR_SORT_HITS < mean) C <<= 1;
     return C;
 }
 

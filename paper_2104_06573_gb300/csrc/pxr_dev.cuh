@@ -122,8 +122,7 @@ struct DevBatch {
     uint32_t *cell_in;                  // [entries] inner hit (allocation-free entry point only)
     uint32_t *cell_out;                 // [entries] outer hit, sorted position
     // CA graph: out-edges of each cell
-    uint32_t *nbr_first;                // [cells]
-    uint32_t *nbr_n;                    // [cells]
+    uint2 *nbr_head;                    // [cells] the cell's edge list: x first (absolute), y count
     uint32_t *nbr;                      // [edges] target cells
     uint32_t *mindepth;                 // [cells] fewest hits before the cell on a root path
     uint32_t *root_list;                // [edges] per event: root cells that have out-edges

@@ -291,8 +291,7 @@ struct PlanOffsets {
         hit_chunk,
         head_end;
     size_t cnt, bkt, hs, r64, hmeta, hphi, gofs, gpos, gfree, glay, item, cell_out,
-        nbr_first,
-        nbr_n, nbr, mindepth, root_list, root_in, live, front_list, front_in, front_snap, jbase, ca_tests, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, tup_tmp, canon_cnt, out_evt, o_nh,
+        nbr_head, nbr, mindepth, root_list, root_in, live, front_list, front_in, front_snap, jbase, ca_tests, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, tup_tmp, canon_cnt, out_evt, o_nh,
         o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status, o_ql, best, o_cov, o_vtx,
         v_z, v_err, v_pt2, v_n;
     size_t total;
@@ -330,8 +329,7 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
 
     o.item = L.add(16 * N * kMaxOut);
     o.cell_out = L.add(4 * C);
-    o.nbr_first = L.add(4 * C);
-    o.nbr_n = L.add(4 * C);
+    o.nbr_head = L.add(8 * C);
     o.nbr = L.add(4 * G);
     o.mindepth = L.add(4 * C);
     o.root_list = L.add(4 * G);
@@ -597,8 +595,7 @@ static void plan_bind(pxr_plan *P)
     b.item = (uint4 *)(r + o.item);
     b.cell_in = nullptr;
     b.cell_out = (uint32_t *)(r + o.cell_out);
-    b.nbr_first = (uint32_t *)(r + o.nbr_first);
-    b.nbr_n = (uint32_t *)(r + o.nbr_n);
+    b.nbr_head = (uint2 *)(r + o.nbr_head);
     b.nbr = (uint32_t *)(r + o.nbr);
     b.mindepth = (uint32_t *)(r + o.mindepth);
     b.root_list = (uint32_t *)(r + o.root_list);
@@ -717,7 +714,7 @@ static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false,
     // 2-hit paths count) and a junction with several out-layers appending to an in-cell's list
     bool multi_out = false;
     for (uint32_t l = 0; l < p.n_layers; ++l) multi_out |= p.n_out[l] > 1;
-    if (p.min_hits <= 2 || multi_out) CK(cudaMemsetAsync(r + P->off.nbr_n, 0, 4 * P->C, s));
+    if (p.min_hits <= 2 || multi_out) CK(cudaMemsetAsync(r + P->off.nbr_head, 0, 8 * P->C, s));
     CK(cudaMemsetAsync(r + P->off.live, 0, 4 * ((P->C + 31) / 32), s));
     launch_sort(b, p, s, sms);
     if (t) CK(stage_mark(P->ev_stage[1], s, capturing));
@@ -1119,8 +1116,9 @@ static int region_debug(pxr_plan *P, uint32_t e, int what, uint32_t *buf, uint32
                 out.push_back(loc(co[c]));
             }
         } else {
-            std::vector<uint32_t> nf, nn, live, roots;
-            if ((rc = d2h(nf, b.nbr_first + c0, nc)) || (rc = d2h(nn, b.nbr_n + c0, nc))) return rc;
+            std::vector<uint32_t> live, roots;
+            std::vector<uint2> hd;
+            if ((rc = d2h(hd, b.nbr_head + c0, nc))) return rc;
             const uint32_t g0 = P->edge_off[e];
             const uint32_t ng = std::min(cnt[C_EDGES], P->edge_off[e + 1] - g0);
             std::vector<uint32_t> nb;
@@ -1135,8 +1133,8 @@ static int region_debug(pxr_plan *P, uint32_t e, int what, uint32_t *buf, uint32
                 valid[c] = ci[c] != kNone && ((live[c / 32] >> (c % 32)) & 1u);
             for (uint32_t A : roots) valid[A - c0] = 1;
             for (uint32_t c = 0; c < nc; ++c)
-                for (uint32_t k = 0; valid[c] && k < nn[c]; ++k) {
-                    uint32_t B = nb[nf[c] - g0 + k] - c0;
+                for (uint32_t k = 0; valid[c] && k < hd[c].y; ++k) {
+                    uint32_t B = nb[hd[c].x - g0 + k] - c0;
                     out.push_back(loc(ci[c]));
                     out.push_back(loc(co[c]));
                     out.push_back(loc(co[B]));
