@@ -320,11 +320,11 @@ void launch_doublets_compact(const DevBatch &b, const DevParams &p, cudaStream_t
 // need_theta, then the DCA, decided by the FP32 result dc (1 pass, 0 fail) or else in FP64.
 __device__ __noinline__ bool triplet_exact(const double *r64, const uint32_t *cell_out,
                                            const float4 *hs, uint32_t i, uint32_t j, uint32_t B,
-                                           float xi, float yi, float4 hj, float4 hk,
+                                           uint32_t k, float xi, float yi, float4 hj, float4 hk,
                                            bool need_theta, int dc, double theta, double dca)
 {
     if (need_theta) {
-        const uint32_t k = cell_out[B];
+        if (k == kNone) k = cell_out[B];
         const double zi = (double)hs[i].z, zj = (double)hj.z, zk = (double)hk.z;
         const double ri = r64[i], rj = r64[j], rk = r64[k];
         const double nA = seglen64(ri, zi, rj, zj);
@@ -343,18 +343,18 @@ __device__ __forceinline__ void count_lanes(unsigned long long *c)
     if ((threadIdx.x & 31u) == (uint32_t)(__ffs(m) - 1)) atomicAdd(c, (unsigned long long)__popc(m));
 }
 
-// Exact decision for the triplet (i, j, k), k the outer hit of the out-cell B = (j, k):
-// r-z alignment, then DCA.  FP32 mode decides in float when outside the guard bands and takes
-// the FP64 formulas otherwise (FP64 mode always).
+// Exact decision for the triplet (i, j, k), k the outer hit of the out-cell B = (j, k) (kNone:
+// read from B's entry): r-z alignment, then DCA.  FP32 mode decides in float when outside the
+// guard bands and takes the FP64 formulas otherwise (FP64 mode always).
 template <bool F64>
 __device__ __forceinline__ bool triplet_test(const DevBatch &b, const DevParams &p, uint32_t i,
-                                             uint32_t j, uint32_t B, float xi, float yi,
-                                             float4 hj, float4 hk, const RZ32 &a)
+                                             uint32_t j, uint32_t B, uint32_t k, float xi,
+                                             float yi, float4 hj, float4 hk, const RZ32 &a)
 {
     if (b.ca_tests) count_lanes(b.ca_tests);
     if constexpr (F64) {
         if (theta32(a, rz32(hj, hk), p.theta32) == 0) return false;
-        const uint32_t k = b.cell_out[B];
+        if (k == kNone) k = b.cell_out[B];
         const double zi = (double)b.hs[i].z, zj = (double)hj.z, zk = (double)hk.z;
         const double ri = b.r64[i], rj = b.r64[j], rk = b.r64[k];
         if (!theta64(ri, zi, rj, zj, rk, zk, seglen64(ri, zi, rj, zj), seglen64(rj, zj, rk, zk),
@@ -370,7 +370,7 @@ __device__ __forceinline__ bool triplet_test(const DevBatch &b, const DevParams 
         if (b.ca_tests) count_lanes(b.ca_tests + 1);
         const int dc = dca32(xi, yi, hj.x, hj.y, hk.x, hk.y, p.dca32);
         if (th == 1 && dc >= 0) return dc == 1;
-        return triplet_exact(b.r64, b.cell_out, b.hs, i, j, B, xi, yi, hj, hk, th < 0, dc,
+        return triplet_exact(b.r64, b.cell_out, b.hs, i, j, B, k, xi, yi, hj, hk, th < 0, dc,
                              p.theta, p.dca);
     }
 }
@@ -502,9 +502,6 @@ constexpr int kEdgeBuf = 8;     // passes buffered per cell; a longer list is fo
 #ifndef PXR_CA_MINB
 #define PXR_CA_MINB 4           // CTAs per SM the sparse CA kernel is compiled for (registers)
 #endif
-#ifndef PXR_CONN_MINB
-#define PXR_CONN_MINB 4         // CTAs per SM the dense CA kernel is compiled for (registers)
-#endif
 
 // One warp's cells (one per lane), their queries and passes, in shared memory: the warp works
 // through the grid candidates of all its lanes as one list, 32 at a time, so that a lane with
@@ -528,7 +525,7 @@ __device__ __noinline__ bool ca_test(const DevBatch &b, const DevParams &p, uint
                                      float4 a4)
 {
     const RZ32 a{a4.x, a4.y, a4.z, a4.w};
-    return triplet_test<F64>(b, p, i, j, B, xi, yi, hj, b.hs[k], a);
+    return triplet_test<F64>(b, p, i, j, B, k, xi, yi, hj, b.hs[k], a);
 }
 
 // One pair (out-layer Lk of the lane's cell; lanes with active false take no part) for the
@@ -713,7 +710,6 @@ __device__ __noinline__ void ca_rest(const DevBatch &b, const DevParams &p, uint
     }
 }
 
-constexpr int kConnWarps = 8;
 constexpr int kStage = 256;     // out-cells of one junction staged per out-layer slot
 #ifndef PXR_CONN_BINS
 #define PXR_CONN_BINS 128
@@ -729,57 +725,35 @@ __device__ __forceinline__ int ford(float f)
 __device__ __forceinline__ float funord(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
 
 
-// One warp per junction hit j.  For each out-layer slot, j's out-cells (j, k) are staged in
-// shared memory (k's coordinates) and counting-sorted by the free coordinate of k (z on barrel
-// layers, r on disks) into local bins over the staged range.  The in-cells (i, j) are found 32
-// at a time, one per lane, by scanning i over j's phi window on the inner layer with the doublet
-// cut; each lane computes the cone of r-z directions that can pass the alignment cut, the bins it
-// reaches (a conservative window: the exact cuts decide) and tests those out-cells itself (j's
-// entries of failed candidates are skipped).  The in-cell's index is j's rank in i's window
-// (loaded alongside the tests).  Lanes with passes append their edges: the round's returning
-// atomics (edge and root-list reservations, frontier slots, reached marks) are issued together,
-// so a round waits on one atomic round trip.  A slot with more than kStage entries is tested
-// from global memory.  Loads that do not depend on one another are issued together (the
-// junction's own records, its first out-cell list and inner window) so that a junction waits on
-// few memory round trips.
+// One junction hit j (on a layer of layer_mask, in event e), one warp.  For each out-layer
+// slot, j's out-cells (j, k) are staged in shared memory (k's coordinates) and counting-sorted
+// by the free coordinate of k (z on barrel layers, r on disks) into local bins over the staged
+// range.  The in-cells (i, j) are found 32 at a time, one per lane, by scanning i over j's phi
+// window on the inner layer with the doublet cut; each lane computes the cone of r-z directions
+// that can pass the alignment cut, the bins it reaches (a conservative window: the exact cuts
+// decide) and tests those out-cells itself (j's entries of failed candidates are skipped).  The
+// in-cell's index is j's rank in i's window.  Lanes with passes append their edges: the round's
+// returning atomics (edge and root-list reservations, frontier slots, reached marks) are issued
+// together.  A slot with more than kStage entries is tested from global memory.  This is the
+// dense pass's path for the junctions of a tile whose window unions exceed the tile's staging
+// (k_connect_tiles); sH, sT and bin are the calling warp's staging arrays.
 template <bool F64>
-__global__ void __launch_bounds__(kConnWarps * 32, PXR_CONN_MINB) k_connect(DevBatch b, DevParams p,
-                                                                uint32_t layer_mask)
+__device__ __noinline__ void connect_junction(const DevBatch &b, const DevParams &p, uint32_t e,
+                                              uint32_t j, uint32_t layer_mask, float4 *sH,
+                                              uint16_t *sT, uint32_t *bin)
 {
-    __shared__ float4 s_h[kConnWarps][kStage];      // staged out-cells' outer hits (list order)
-    __shared__ uint16_t s_t[kConnWarps][kStage];    // list positions sorted by local bin
-    __shared__ uint32_t s_bin[kConnWarps][kBins];   // bin ends after the scan
-    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-    float4 *sH = s_h[wid];
-    uint16_t *sT = s_t[wid];
-    uint32_t *bin = s_bin[wid];
+    const uint32_t lane = threadIdx.x & 31u;
     const uint32_t nk = p.n_keys;
-    const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint32_t n_junctions = b.jbase[b.E];
-    for (uint64_t jj = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; jj < n_junctions;
-         jj += stride) {
-        // the jj-th junction hit: its event from the per-event junction prefix, its position
-        // from the event's layer ranges of the layers in layer_mask
-        const uint32_t g = (uint32_t)jj;
-        const uint32_t e = find_event(b.jbase, b.E, g);
-        uint32_t o = g - b.jbase[e];
-        const uint32_t *bke = b.bkt + (size_t)e * (nk + 1);
-        uint32_t j = 0;
-        for (uint32_t l = 0; l < p.n_layers; ++l) {
-            if (!((layer_mask >> l) & 1u)) continue;
-            const uint32_t lo = bke[l * p.nb], n_l = bke[(l + 1) * p.nb] - lo;
-            if (o < n_l) { j = lo + o; break; }
-            o -= n_l;
-        }
+    {
         const uint32_t meta = b.hmeta[j];
         const float4 hj = b.hs[j];
         const float phij = b.hphi[j];
         const uint4 it0 = b.item[(size_t)j * kMaxOut];
         uint32_t f0 = it0.x, nB = it0.y;
         const uint32_t Lj = meta >> kLocalBits;
-        if (Lj >= p.n_layers || !((layer_mask >> Lj) & 1u)) continue;
+        if (Lj >= p.n_layers || !((layer_mask >> Lj) & 1u)) return;
         const uint32_t nin = p.n_in[Lj], nout = p.n_out[Lj];
-        if (nin == 0 || nout == 0) continue;
+        if (nin == 0 || nout == 0) return;
         const uint32_t *bk = b.bkt + (size_t)e * (nk + 1);
         const Window w0 = phi_window(bk, p.in_layer[Lj][0], phij, p);
         // out-cells that start further pairs from a non-root inner layer go to the frontier
@@ -933,7 +907,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, PXR_CONN_MINB) k_connect(DevB
                             if (k == kNone) continue;
                             hk = b.hs[k];
                         }
-                        if (triplet_test<F64>(b, p, i, j, B, hi.x, hi.y, hj, hk, a)) {
+                        if (triplet_test<F64>(b, p, i, j, B, kNone, hi.x, hi.y, hj, hk, a)) {
                             if (npass == 0) { qf = q; Bf = B; }
                             ++npass;
                         }
@@ -1022,7 +996,7 @@ __global__ void __launch_bounds__(kConnWarps * 32, PXR_CONN_MINB) k_connect(DevB
                                 if (k == kNone) continue;
                                 hk = b.hs[k];
                             }
-                            if (triplet_test<F64>(b, p, i, j, B, hi.x, hi.y, hj, hk, a)) {
+                            if (triplet_test<F64>(b, p, i, j, B, kNone, hi.x, hi.y, hj, hk, a)) {
                                 b.nbr[first + wr++] = B;
                                 mark_reached(b, e, B, j, front);
                             }
@@ -1037,10 +1011,602 @@ __global__ void __launch_bounds__(kConnWarps * 32, PXR_CONN_MINB) k_connect(DevB
 }
 
 
-// Per-event prefix of the hits on the layers of layer_mask (the junctions of a dense CA level):
-// jbase[e] = those of events before e, jbase[E] = all.  One CTA; each thread takes a run of
-// consecutive events.
-__global__ void __launch_bounds__(1024) k_jbase(DevBatch b, DevParams p, uint32_t layer_mask)
+// ------------------------------------------------------------------------------------------
+// Dense CA pass on junction tiles
+// ------------------------------------------------------------------------------------------
+// A tile is a run of up to 32 consecutive junction hits of one event and layer (in (layer, phi
+// bin) order), one per lane of a warp.  Their phi windows on an inner (outer) layer overlap
+// almost entirely, so the warp stages the union of the windows once, in shared memory, instead
+// of once per junction.  The lanes then walk their junctions' inner windows in step: for the
+// inner hit i of its step a lane computes the r-z cone of the segment (i, j) and looks up the
+// staged outer hits inside it (counting-sorted by the free coordinate).  The few that fall
+// inside the cone are queued, and the warp tests them 32 at a time with all lanes busy: a cell
+// (j, k) (rank in j's window, entry holding the hit), the exact triplet cut, and the in-cell
+// (i, j) itself, read from i's entry (the doublet stage decided it).  Passes are buffered in
+// queue order, so the passes of one in-cell are adjacent, and appended together: one edge,
+// root-list and frontier reservation per flush, each in-cell's edges a contiguous run.
+constexpr uint32_t kTileJ = 32;       // junction hits per tile (one per lane)
+constexpr int kTileW = 4;             // warps per CTA
+constexpr uint32_t kTileQ = 128;      // queued candidates per warp (a ring)
+constexpr uint32_t kTileCand = 2;     // queued candidates per lane and step; more: lane alone
+constexpr uint32_t kTilePass = 64;    // buffered passes per warp
+#ifndef PXR_TILE_MINB
+#define PXR_TILE_MINB 4               // CTAs per SM the tile kernel is compiled for (registers;
+                                      //   its shared memory allows four)
+#endif
+
+struct TileWarp {
+    float4 hin[kStage];               // inner-layer window union, staging order
+    float4 hout[kStage];              // outer-layer window union, staging order
+    uint16_t sT[kStage];              // hout indices in free-coordinate bin order
+    uint32_t bin[kBins];              // bin ends after the scan
+    float4 jh[32];                    // the junctions' hits
+    uint4 jit[32];                    // their entries on the current out-layer
+    uint32_t jpos[32];                // their sorted positions
+    uint32_t q[kTileQ];               // candidates: junction lane << 16 | inner << 8 | outer
+    uint32_t pA[kTilePass], pB[kTilePass], pI[kTilePass], pK[kTilePass];   // passes: in-cell,
+                                      //   out-cell, inner hit, junction lane << 8 | inner index
+    uint32_t pHave[kTilePass];        // a run's edges from an earlier out-layer (run start)
+};
+
+// Hit positions of an event's layer taken as periodic in azimuth: the first hit of the
+// unwrapped phi bin bb (in [-nb, 2 nb): bins below 0 and from nb on are the neighbouring turns)
+// relative to the layer's first hit, tot hits per turn.
+__device__ __forceinline__ int tile_v(const uint32_t *lb, int nb, int tot, int bb)
+{
+    if (bb < 0) return (int)(lb[bb + nb] - lb[0]) - tot;
+    if (bb >= nb) return (int)(lb[bb - nb] - lb[0]) + tot;
+    return (int)(lb[bb] - lb[0]);
+}
+
+// The union of the tile's windows on one layer (lb: the layer's bucket starts): staging index s
+// is the hit at periodic position v0 + s; n hits (the whole layer, in natural order, when the
+// union spans every bin).
+struct TileSpan {
+    int v0;
+    uint32_t n, lb0, tot;
+};
+
+// Sorted position of staging index s.
+__device__ __forceinline__ uint32_t tile_pos(const TileSpan &t, uint32_t s)
+{
+    int v = t.v0 + (int)s;
+    if (v < 0) v += (int)t.tot;
+    else if (v >= (int)t.tot) v -= (int)t.tot;
+    return t.lb0 + (uint32_t)v;
+}
+
+// The union of the lanes' windows [blo, bhi] (unwrapped bins; ok false: the lane has none) and
+// each lane's window as staging indices [ws, ws + wn) (modulo n when the union is the whole
+// layer).  Warp-collective.
+__device__ __forceinline__ TileSpan tile_span(const uint32_t *lb, int nb, bool ok, int blo,
+                                              int bhi, uint32_t &ws, uint32_t &wn)
+{
+    TileSpan t;
+    t.lb0 = lb[0];
+    t.tot = lb[nb] - t.lb0;
+    t.v0 = 0;
+    t.n = 0;
+    ws = wn = 0;
+    const int ulo = __reduce_min_sync(0xFFFFFFFFu, ok ? blo : 0x7FFFFFFF);
+    const int uhi = __reduce_max_sync(0xFFFFFFFFu, ok ? bhi : -0x7FFFFFFF);
+    if (ulo > uhi || t.tot == 0) return t;
+    const int tot = (int)t.tot;
+    if (uhi - ulo + 1 >= nb) {
+        t.n = t.tot;
+        if (ok) {
+            if (bhi - blo + 1 >= nb) {
+                wn = t.tot;
+            } else {
+                int a = tile_v(lb, nb, tot, blo);
+                wn = (uint32_t)(tile_v(lb, nb, tot, bhi + 1) - a);
+                if (a < 0) a += tot;
+                else if (a >= tot) a -= tot;
+                ws = (uint32_t)a;
+            }
+        }
+    } else {
+        t.v0 = tile_v(lb, nb, tot, ulo);
+        t.n = (uint32_t)(tile_v(lb, nb, tot, uhi + 1) - t.v0);
+        if (ok) {
+            const int a = tile_v(lb, nb, tot, blo);
+            ws = (uint32_t)(a - t.v0);
+            wn = (uint32_t)(tile_v(lb, nb, tot, bhi + 1) - a);
+        }
+    }
+    return t;
+}
+
+// The out-cell B of j for the staged outer hit kt, and the triplet (i, j, k): kNone unless
+// (j, k) is a cell (rank in j's window, entry holding k) and the exact triplet cut passes.
+template <bool F64>
+__device__ __forceinline__ uint32_t tile_test(const DevBatch &b, const DevParams &p,
+                                              const TileSpan &tk, uint32_t kt, float4 hk,
+                                              uint32_t i, float4 hi, uint32_t j, float4 hj,
+                                              const RZ32 &a, uint4 itj)
+{
+    const uint32_t k = tile_pos(tk, kt);
+    const uint32_t rank = k >= itj.z ? k - itj.z : k + itj.w;
+    if (rank >= itj.y) return kNone;
+    const uint32_t B = itj.x + rank;
+    if (!triplet_test<F64>(b, p, i, j, B, k, hi.x, hi.y, hj, hk, a)) return kNone;
+    return b.cell_out[B] == k ? B : kNone;          // (j, k) failed the doublet cut: kNone
+}
+
+// The in-cell (i, j) for the pair slot slot_i of i: i's entry of rank(j) in its window, kNone
+// when the doublet stage did not keep it.
+__device__ __forceinline__ uint32_t tile_incell(const DevBatch &b, uint32_t i, uint32_t slot_i,
+                                                uint32_t j)
+{
+    const uint4 iti = b.item[(size_t)i * kMaxOut + slot_i];
+    const uint32_t rank = j >= iti.z ? j - iti.z : j + iti.w;
+    if (rank >= iti.y) return kNone;
+    const uint32_t A = iti.x + rank;
+    return b.cell_out[A] == j ? A : kNone;
+}
+
+// Every pass of one in-cell (i, j) written straight to global memory, for a lane whose cone
+// held more than kTileCand candidates (rare): the candidates [q0, q1) of the bin order tested
+// one by one.  more: an earlier out-layer of j may have given the in-cell edges already (copied
+// first).
+template <bool F64>
+__device__ __noinline__ void tile_direct(const DevBatch &b, const DevParams &p, uint32_t e,
+                                         const TileWarp &S, const TileSpan &tk, uint32_t q0,
+                                         uint32_t q1, float lo, float hi_, bool disk,
+                                         uint32_t slot_i, uint32_t i, float4 hi, uint32_t j,
+                                         float4 hj, RZ32 a, uint4 itj, bool more, bool front)
+{
+    uint32_t np = 0;
+    for (uint32_t q = q0; q < q1; ++q) {
+        const uint32_t kt = S.sT[q];
+        const float4 hk = S.hout[kt];
+        const float fc = disk ? hk.w : hk.z;
+        if (fc >= lo && fc <= hi_ && tile_test<F64>(b, p, tk, kt, hk, i, hi, j, hj, a, itj) != kNone)
+            ++np;
+    }
+    if (np == 0) return;
+    const uint32_t A = tile_incell(b, i, slot_i, j);
+    if (A == kNone) return;
+    uint32_t have = 0, old = 0;
+    if (more) {
+        const uint2 hd = b.nbr_head[A];
+        have = hd.y;
+        old = hd.x;
+    }
+    const uint32_t need = have + np;
+    const uint32_t g0 = b.edge_off[e], cap = b.edge_off[e + 1] - g0;
+    const uint32_t my0 = atomicAdd(&b.cnt[C_EDGES * b.E + e], need);
+    const uint32_t nw = my0 >= cap ? 0u : min(need, cap - my0);
+    if (nw < need) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+    if (have == 0) {
+        const uint32_t r = atomicAdd(&b.cnt[C_ROOTS * b.E + e], 1u);
+        if (r < cap) {
+            b.root_list[g0 + r] = A;
+            b.root_in[g0 + r] = i;
+        } else {
+            atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+        }
+    }
+    uint32_t wr = 0;
+    for (uint32_t t = 0; t < have && wr < nw; ++t) b.nbr[g0 + my0 + wr++] = b.nbr[old + t];
+    for (uint32_t q = q0; q < q1; ++q) {
+        const uint32_t kt = S.sT[q];
+        const float4 hk = S.hout[kt];
+        const float fc = disk ? hk.w : hk.z;
+        if (!(fc >= lo && fc <= hi_)) continue;
+        const uint32_t B = tile_test<F64>(b, p, tk, kt, hk, i, hi, j, hj, a, itj);
+        if (B == kNone) continue;
+        if (wr < nw) b.nbr[g0 + my0 + wr++] = B;
+        mark_reached(b, e, B, j, front);
+    }
+    b.nbr_head[A] = make_uint2(g0 + my0, wr);
+}
+
+// Append the first n buffered passes (runs of equal in-cell, each complete).  A run whose in-cell
+// has no edges yet (every run when more is false) takes its place in one contiguous block of
+// edges reserved for the flush and is listed as a root cell; a run whose in-cell got edges from
+// an earlier out-layer is written by its first lane with the old edges copied in front.  Every
+// pass marks its target reached and, when front, takes a frontier slot (taken before the target
+// is known to be fresh: kNone if it is not).  Warp-collective.
+__device__ __forceinline__ void tile_flush(const DevBatch &b, uint32_t e, TileWarp &S, uint32_t n,
+                                           bool more, bool front, uint32_t lane)
+{
+    const uint32_t FULL = 0xFFFFFFFFu;
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t g0 = b.edge_off[e], cap = b.edge_off[e + 1] - g0;
+    __syncwarp();
+    // run starts: the earlier edges of their in-cells; counts of the block and the new roots
+    uint32_t nfast = 0, nroot = 0;
+    for (uint32_t r0 = 0; r0 < n; r0 += 32) {
+        const uint32_t x = r0 + lane;
+        bool fast = false, root = false;
+        if (x < n) {
+            const uint32_t A = S.pA[x];
+            const bool start = x == 0 || S.pA[x - 1] != A;
+            uint32_t have = 0;
+            if (start) {
+                if (more) have = b.nbr_head[A].y;
+                S.pHave[x] = have;
+                root = have == 0;
+            }
+        }
+        __syncwarp();
+        if (x < n) {
+            uint32_t s0 = x;
+            while (s0 > 0 && S.pA[s0 - 1] == S.pA[x]) --s0;
+            fast = S.pHave[s0] == 0;
+        }
+        nfast += __popc(__ballot_sync(FULL, fast));
+        nroot += __popc(__ballot_sync(FULL, root));
+    }
+    uint32_t ebase = 0, rbase = 0, fbase = 0;
+    if (lane == 0) {
+        if (nfast) ebase = atomicAdd(&b.cnt[C_EDGES * b.E + e], nfast);
+        if (nroot) rbase = atomicAdd(&b.cnt[C_ROOTS * b.E + e], nroot);
+        if (front && n) fbase = atomicAdd(&b.cnt[C_FRONT * b.E + e], n);
+    }
+    ebase = __shfl_sync(FULL, ebase, 0);
+    rbase = __shfl_sync(FULL, rbase, 0);
+    fbase = __shfl_sync(FULL, fbase, 0);
+    if (ebase + nfast > cap && nfast) {
+        if (lane == 0) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+    }
+    for (uint32_t r0 = 0; r0 < n; r0 += 32) {
+        const uint32_t x = r0 + lane;
+        const bool v = x < n;
+        uint32_t A = 0, B = 0, s0 = x;
+        bool start = false, fast = false;
+        if (v) {
+            A = S.pA[x];
+            B = S.pB[x];
+            start = x == 0 || S.pA[x - 1] != A;
+            while (s0 > 0 && S.pA[s0 - 1] == A) --s0;
+            fast = S.pHave[s0] == 0;
+        }
+        const uint32_t fm = __ballot_sync(FULL, fast), rm = __ballot_sync(FULL, start && fast);
+        const uint32_t epos = ebase + __popc(fm & lt), rpos = rbase + __popc(rm & lt);
+        ebase += __popc(fm);
+        rbase += __popc(rm);
+        if (!v) continue;
+        if (fast) {
+            if (epos < cap) b.nbr[g0 + epos] = B;
+            if (start) {
+                // the run's length and the edges that fit the region
+                uint32_t len = 1;
+                while (x + len < n && S.pA[x + len] == A) ++len;
+                const uint32_t nw = epos >= cap ? 0u : min(len, cap - epos);
+                b.nbr_head[A] = make_uint2(g0 + epos, nw);
+                if (rpos < cap) {
+                    b.root_list[g0 + rpos] = A;
+                    b.root_in[g0 + rpos] = S.pI[x];
+                } else {
+                    atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+                }
+            }
+        } else if (start) {
+            // an in-cell with edges from an earlier out-layer: old edges, then this run
+            uint32_t len = 1;
+            while (x + len < n && S.pA[x + len] == A) ++len;
+            const uint2 hd = b.nbr_head[A];
+            const uint32_t need = hd.y + len;
+            const uint32_t my0 = atomicAdd(&b.cnt[C_EDGES * b.E + e], need);
+            const uint32_t nw = my0 >= cap ? 0u : min(need, cap - my0);
+            if (nw < need) atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+            uint32_t wr = 0;
+            for (uint32_t t = 0; t < hd.y && wr < nw; ++t) b.nbr[g0 + my0 + wr++] = b.nbr[hd.x + t];
+            for (uint32_t t = 0; t < len && wr < nw; ++t) b.nbr[g0 + my0 + wr++] = S.pB[x + t];
+            b.nbr_head[A] = make_uint2(g0 + my0, wr);
+        }
+        // the target reached; its frontier slot
+        const uint32_t bit = 1u << (B & 31u);
+        const bool fresh = !(atomicOr(&b.live[B >> 5], bit) & bit);
+        if (fresh) b.nbr_head[B].y = 0u;
+        if (front) {
+            const uint32_t fpos = fbase + x;
+            if (fpos < cap) {
+                b.front_list[g0 + fpos] = fresh ? B : kNone;
+                b.front_in[g0 + fpos] = S.jpos[S.pK[x] >> 8];
+            } else {
+                atomicOr(&b.cnt[C_FLAGS * b.E + e], F_EDGES);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Stage the hits of a union (n <= kStage) into dst, four loads in flight per lane.
+__device__ __forceinline__ void tile_stage(const DevBatch &b, const TileSpan &t, float4 *dst,
+                                           uint32_t lane)
+{
+    for (uint32_t q0 = 0; q0 < t.n; q0 += 128) {
+        float4 h[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t q = q0 + 32u * u + lane;
+            if (q < t.n) h[u] = b.hs[tile_pos(t, q)];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t q = q0 + 32u * u + lane;
+            if (q < t.n) dst[q] = h[u];
+        }
+    }
+}
+
+template <bool F64>
+__global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(DevBatch b,
+                                                                             DevParams p,
+                                                                             uint32_t layer_mask)
+{
+    __shared__ TileWarp s_w[kTileW];
+    const uint32_t FULL = 0xFFFFFFFFu;
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    TileWarp &S = s_w[wid];
+    const uint32_t nk = p.n_keys;
+    const int nb = (int)p.nb;
+    const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t n_tiles = b.jbase[b.E];
+    for (uint64_t tt = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tt < n_tiles;
+         tt += stride) {
+        // the tile: its event from the per-event tile prefix, its junctions from the event's
+        // layer ranges of the layers in layer_mask
+        const uint32_t e = find_event(b.jbase, b.E, (uint32_t)tt);
+        uint32_t o = (uint32_t)tt - b.jbase[e];
+        const uint32_t *bk = b.bkt + (size_t)e * (nk + 1);
+        uint32_t Lj = 0, J0 = 0, nJ = 0;
+        for (uint32_t l = 0; l < p.n_layers; ++l) {
+            if (!((layer_mask >> l) & 1u)) continue;
+            const uint32_t lo = bk[l * p.nb], n_l = bk[(l + 1) * p.nb] - lo;
+            const uint32_t nt = (n_l + kTileJ - 1) / kTileJ;
+            if (o < nt) {
+                Lj = l;
+                J0 = lo + o * kTileJ;
+                nJ = min(kTileJ, n_l - o * kTileJ);
+                break;
+            }
+            o -= nt;
+        }
+        const uint32_t nin = p.n_in[Lj], nout = p.n_out[Lj];
+        if (nJ == 0 || nin == 0 || nout == 0) continue;
+        const bool jv = lane < nJ;
+        const uint32_t j = J0 + (jv ? lane : 0u);
+        const float4 hj = b.hs[j];
+        const float phij = b.hphi[j];
+        const bool ok = jv && fabsf(phij) <= 4.f;    // (a non-finite azimuth has no window)
+        const int blo = ok ? (int)floorf((phij - p.w_eps + kPiF2) * p.bins_per_rad) : 0;
+        const int bhi = ok ? (int)floorf((phij + p.w_eps + kPiF2) * p.bins_per_rad) : 0;
+        // every union must fit the staging; otherwise the tile's junctions go one by one
+        bool fits = true;
+        for (uint32_t si = 0; si < nin && fits; ++si) {
+            const uint32_t Li = p.in_layer[Lj][si];
+            if (!((p.root_mask >> Li) & 1u)) continue;
+            uint32_t ws, wn;
+            fits = tile_span(bk + Li * p.nb, nb, ok, blo, bhi, ws, wn).n <= (uint32_t)kStage;
+        }
+        for (uint32_t s = 0; s < nout && fits; ++s) {
+            uint32_t ws, wn;
+            fits = tile_span(bk + p.out_layer[Lj][s] * p.nb, nb, ok, blo, bhi, ws, wn).n <=
+                   (uint32_t)kStage;
+        }
+        if (!fits) {
+            for (uint32_t t = 0; t < nJ; ++t)
+                connect_junction<F64>(b, p, e, J0 + t, layer_mask, S.hout, S.sT, S.bin);
+            continue;
+        }
+        const bool j_root = (p.root_mask >> Lj) & 1u;
+        __syncwarp();
+        S.jh[lane] = hj;
+        S.jpos[lane] = j;
+        for (uint32_t si = 0; si < nin; ++si) {
+            const uint32_t Li = p.in_layer[Lj][si];
+            // this pass takes the root in-cells; reached non-root ones go to the sparse pass
+            if (!((p.root_mask >> Li) & 1u)) continue;
+            const uint32_t slot_i = p.in_slot[Lj][si];
+            uint32_t ws, wn;
+            const TileSpan ti = tile_span(bk + Li * p.nb, nb, ok, blo, bhi, ws, wn);
+            if (ti.n == 0) continue;
+            __syncwarp();
+            tile_stage(b, ti, S.hin, lane);
+            for (uint32_t s = 0; s < nout; ++s) {
+                const uint32_t Lk = p.out_layer[Lj][s];
+                const bool disk = p.is_disk[Lk];
+                const bool front = !j_root && p.n_out[Lk] > 0;
+                const bool more = s > 0;
+                const uint4 itj = ok ? b.item[(size_t)j * kMaxOut + s] : make_uint4(0u, 0u, 0u, 0u);
+                uint32_t os, on;
+                const TileSpan tk = tile_span(bk + Lk * p.nb, nb, ok, blo, bhi, os, on);
+                if (tk.n == 0) continue;
+                __syncwarp();
+                S.jit[lane] = itj;
+                tile_stage(b, tk, S.hout, lane);
+                __syncwarp();
+                // range of the free (z barrel, r disk) and fixed coordinates of the staged hits
+                int m0 = ford(3.0e38f), m1 = ford(-3.0e38f), m2 = m0, m3 = m1;
+                for (uint32_t q = lane; q < tk.n; q += 32) {
+                    const float4 hk = S.hout[q];
+                    const float fc = disk ? hk.w : hk.z, xc = disk ? hk.z : hk.w;
+                    m0 = min(m0, ford(fc));
+                    m1 = max(m1, ford(fc));
+                    m2 = min(m2, ford(xc));
+                    m3 = max(m3, ford(xc));
+                }
+                const float flo = funord(__reduce_min_sync(FULL, m0));
+                const float fhi = funord(__reduce_max_sync(FULL, m1));
+                const float jfix = disk ? hj.z : hj.w, jfree = disk ? hj.w : hj.z;
+                const float dlo = funord(__reduce_min_sync(FULL, m2)) - jfix;
+                const float dhi = funord(__reduce_max_sync(FULL, m3)) - jfix;
+                const float scale = fhi > flo ? (float)kBins / (fhi - flo) : 0.f;
+                auto local_bin = [&](float fc) {
+                    const int bb = (int)floorf((fc - flo) * scale);
+                    return bb < 0 ? 0u : (bb >= kBins ? (uint32_t)kBins - 1u : (uint32_t)bb);
+                };
+                // counting sort of the staged hits by bin: histogram, scan, scatter
+#pragma unroll
+                for (int q = 0; q < kBins / 32; ++q) S.bin[lane + 32 * q] = 0;
+                __syncwarp();
+                for (uint32_t q = lane; q < tk.n; q += 32) {
+                    const float4 hk = S.hout[q];
+                    atomicAdd(&S.bin[local_bin(disk ? hk.w : hk.z)], 1u);
+                }
+                __syncwarp();
+                {
+                    constexpr int per = kBins / 32;
+                    uint32_t v[per], sum = 0;
+#pragma unroll
+                    for (int q = 0; q < per; ++q) { v[q] = S.bin[lane * per + q]; sum += v[q]; }
+                    uint32_t incl = sum;
+#pragma unroll
+                    for (int w = 1; w < 32; w <<= 1) {
+                        const uint32_t t = __shfl_up_sync(FULL, incl, w);
+                        if (lane >= (uint32_t)w) incl += t;
+                    }
+                    uint32_t run = incl - sum;
+                    __syncwarp();
+#pragma unroll
+                    for (int q = 0; q < per; ++q) { S.bin[lane * per + q] = run; run += v[q]; }
+                    __syncwarp();
+                }
+                for (uint32_t q = lane; q < tk.n; q += 32) {
+                    const float4 hk = S.hout[q];
+                    S.sT[atomicAdd(&S.bin[local_bin(disk ? hk.w : hk.z)], 1u)] = (uint16_t)q;
+                }
+                __syncwarp();
+                // S.bin[t] is now the end of bin t.  The lanes step through their junctions'
+                // inner windows together; candidates in a cone are queued (ring of kTileQ,
+                // positions head..tail) and tested 32 at a time; passes buffered (np of them).
+                const uint32_t wme = itj.y ? wn : 0u;      // j without cells on Lk: nothing
+                const uint32_t wmax = __reduce_max_sync(FULL, wme);
+                uint32_t head = 0, tail = 0, np = 0;
+                // test the n <= 32 candidates at the queue head, passes appended in queue order
+                auto batch = [&](uint32_t n) {
+                    const bool v = lane < n;
+                    const uint32_t ent = v ? S.q[(head + lane) % kTileQ] : 0u;
+                    head += n;
+                    uint32_t A = kNone, B = kNone, pi = 0;
+                    const uint32_t t = ent >> 16, sx = (ent >> 8) & 0xFFu, kt = ent & 0xFFu;
+                    if (v) {
+                        const float4 hi = S.hin[sx], hjt = S.jh[t];
+                        pi = tile_pos(ti, sx);
+                        B = tile_test<F64>(b, p, tk, kt, S.hout[kt], pi, hi, S.jpos[t], hjt,
+                                           rz32(hi, hjt), S.jit[t]);
+                        if (B != kNone) A = tile_incell(b, pi, slot_i, S.jpos[t]);
+                    }
+                    const uint32_t pm = __ballot_sync(FULL, A != kNone);
+                    if (A != kNone) {
+                        const uint32_t x = np + __popc(pm & lt);
+                        S.pA[x] = A;
+                        S.pB[x] = B;
+                        S.pI[x] = pi;
+                        S.pK[x] = t << 8 | sx;
+                    }
+                    np += __popc(pm);
+                };
+                // append the buffered passes whose runs are complete: all but the last run when
+                // the queue head belongs to the same in-cell (moved to the buffer's front)
+                auto flush_complete = [&]() {
+                    uint32_t keep = 0;
+                    if (np && tail != head &&
+                        S.pK[np - 1] == ((S.q[head % kTileQ] >> 8) & 0x1FFFu)) {
+                        const uint32_t Al = S.pA[np - 1];
+                        while (keep < np && S.pA[np - 1 - keep] == Al) ++keep;
+                    }
+                    tile_flush(b, e, S, np - keep, more, front, lane);
+                    uint32_t a0 = 0, b0 = 0, i0 = 0, k0 = 0;
+                    if (lane < keep) {
+                        const uint32_t src = np - keep + lane;
+                        a0 = S.pA[src];
+                        b0 = S.pB[src];
+                        i0 = S.pI[src];
+                        k0 = S.pK[src];
+                    }
+                    __syncwarp();
+                    if (lane < keep) {
+                        S.pA[lane] = a0;
+                        S.pB[lane] = b0;
+                        S.pI[lane] = i0;
+                        S.pK[lane] = k0;
+                    }
+                    __syncwarp();
+                    np = keep;
+                };
+                for (uint32_t c = 0; c < wmax; ++c) {
+                    // ---- this step's inner hit per lane: cone, bins, candidates inside ----
+                    uint32_t nq = 0, k0 = 0, k1 = 0, sx = 0, q0 = 0, q1 = 0;
+                    float lo = -3.0e38f, hi_ = 3.0e38f;
+                    float4 hi = make_float4(0.f, 0.f, 0.f, 0.f);
+                    RZ32 a{0.f, 0.f, 0.f, 0.f};
+                    if (c < wme) {
+                        sx = ws + c;
+                        if (sx >= ti.n) sx -= ti.n;
+                        hi = S.hin[sx];
+                        a = rz32(hi, hj);
+                        q1 = tk.n;
+                        if (cone_window(a.ar, a.az, jfree, dlo, dhi, disk, p.tan_win, lo, hi_)) {
+                            if (hi_ < flo || lo > fhi) {
+                                q1 = 0;
+                            } else {
+                                int b0 = (int)floorf((lo - flo) * scale);
+                                int b1 = (int)floorf((hi_ - flo) * scale);
+                                b0 = b0 < 0 ? 0 : (b0 >= kBins ? kBins - 1 : b0);
+                                b1 = b1 < 0 ? 0 : (b1 >= kBins ? kBins - 1 : b1);
+                                q0 = b0 ? S.bin[b0 - 1] : 0u;
+                                q1 = S.bin[b1];
+                            }
+                        }
+                        for (uint32_t q = q0; q < q1; ++q) {
+                            const uint32_t kt = S.sT[q];
+                            const float fc = disk ? S.hout[kt].w : S.hout[kt].z;
+                            if (fc < lo || fc > hi_) continue;
+                            if (nq == 0) k0 = kt;
+                            else if (nq == 1) k1 = kt;
+                            ++nq;
+                        }
+                    }
+                    // a cone with many candidates is taken by its lane alone (rare)
+                    const bool alone = nq > kTileCand;
+                    if (alone)
+                        tile_direct<F64>(b, p, e, S, tk, q0, q1, lo, hi_, disk, slot_i,
+                                         tile_pos(ti, sx), hi, j, hj, a, itj, more, front);
+                    // ---- queue the others' candidates: a lane's entries are adjacent ----
+                    const uint32_t m = alone ? 0u : nq;
+                    uint32_t incl = m;
+#pragma unroll
+                    for (int w = 1; w < 32; w <<= 1) {
+                        const uint32_t t = __shfl_up_sync(FULL, incl, w);
+                        if (lane >= (uint32_t)w) incl += t;
+                    }
+                    const uint32_t tot = __shfl_sync(FULL, incl, 31);
+                    const uint32_t me = lane << 16 | sx << 8;
+                    if (m > 0) S.q[(tail + incl - m) % kTileQ] = me | k0;
+                    if (m > 1) S.q[(tail + incl - m + 1) % kTileQ] = me | k1;
+                    tail += tot;
+                    __syncwarp();
+                    // ---- full batches; a flush keeps a run that may continue in the queue ----
+                    while (tail - head >= 32) {
+                        if (np + 32 > kTilePass) flush_complete();
+                        batch(32);
+                        __syncwarp();
+                    }
+                }
+                // drain the queue and append everything
+                while (tail != head) {
+                    if (np + 32 > kTilePass) flush_complete();
+                    batch(min(32u, tail - head));
+                    __syncwarp();
+                }
+                tile_flush(b, e, S, np, more, front, lane);
+            }
+        }
+    }
+}
+
+
+// Per-event prefix of the junction tiles of a dense CA level (per layer of layer_mask, its hits
+// in runs of `per`): jbase[e] = those of events before e, jbase[E] = all.  One CTA; each thread
+// takes a run of consecutive events.
+__global__ void __launch_bounds__(1024) k_jbase(DevBatch b, DevParams p, uint32_t layer_mask,
+                                                uint32_t per_tile)
 {
     __shared__ uint32_t s_w[32];
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
@@ -1050,7 +1616,8 @@ __global__ void __launch_bounds__(1024) k_jbase(DevBatch b, DevParams p, uint32_
         const uint32_t *bke = b.bkt + (size_t)e * (p.n_keys + 1);
         uint32_t c = 0;
         for (uint32_t l = 0; l < p.n_layers; ++l)
-            if ((layer_mask >> l) & 1u) c += bke[(l + 1) * p.nb] - bke[l * p.nb];
+            if ((layer_mask >> l) & 1u)
+                c += (bke[(l + 1) * p.nb] - bke[l * p.nb] + per_tile - 1) / per_tile;
         return c;
     };
     uint32_t mine = 0;
@@ -1080,15 +1647,16 @@ __global__ void __launch_bounds__(1024) k_jbase(DevBatch b, DevParams p, uint32_
 void launch_connect(const DevBatch &b, const DevParams &p, uint32_t layer_mask, cudaStream_t s,
                     int sms)
 {
-    k_jbase<<<1, 1024, 0, s>>>(b, p, layer_mask);
-    uint64_t blocks = ((uint64_t)b.N + kConnWarps - 1) / kConnWarps;
+    k_jbase<<<1, 1024, 0, s>>>(b, p, layer_mask, kTileJ);
+    // tiles: at most one per kTileJ hits plus one per event and layer
+    uint64_t blocks = ((uint64_t)b.N / kTileJ + (uint64_t)b.E * p.n_layers + kTileW - 1) / kTileW;
     uint64_t cap = (uint64_t)sms * p.grid_per_sm[2];
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
     if (p.cut_mode == CUT_FP64)
-        k_connect<true><<<(unsigned)blocks, kConnWarps * 32, 0, s>>>(b, p, layer_mask);
+        k_connect_tiles<true><<<(unsigned)blocks, kTileW * 32, 0, s>>>(b, p, layer_mask);
     else
-        k_connect<false><<<(unsigned)blocks, kConnWarps * 32, 0, s>>>(b, p, layer_mask);
+        k_connect_tiles<false><<<(unsigned)blocks, kTileW * 32, 0, s>>>(b, p, layer_mask);
 }
 
 // Sparse CA pass of one level over the frontier: cells B = (j, k) that were reached (have an
