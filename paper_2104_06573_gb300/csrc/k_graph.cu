@@ -1025,11 +1025,12 @@ __device__ __noinline__ void connect_junction(const DevBatch &b, const DevParams
 // (i, j) itself, read from i's entry (the doublet stage decided it).  Passes are buffered in
 // queue order, so the passes of one in-cell are adjacent, and appended together: one edge,
 // root-list and frontier reservation per flush, each in-cell's edges a contiguous run.
-constexpr uint32_t kTileJ = 32;       // junction hits per tile (one per lane)
+constexpr uint32_t kTileJ = kCaTile;  // junction hits per tile (one per lane)
 constexpr int kTileW = 4;             // warps per CTA
 constexpr uint32_t kTileQ = 128;      // queued candidates per warp (a ring)
 constexpr uint32_t kTileCand = 2;     // queued candidates per lane and step; more: lane alone
 constexpr uint32_t kTilePass = 64;    // buffered passes per warp
+constexpr uint32_t kTileAlone = 64;   // in-cells with many candidates, handled after the steps
 #ifndef PXR_TILE_MINB
 #define PXR_TILE_MINB 4               // CTAs per SM the tile kernel is compiled for (registers;
                                       //   its shared memory allows four)
@@ -1047,7 +1048,12 @@ struct TileWarp {
     uint32_t pA[kTilePass], pB[kTilePass], pI[kTilePass], pK[kTilePass];   // passes: in-cell,
                                       //   out-cell, inner hit, junction lane << 8 | inner index
     uint32_t pHave[kTilePass];        // a run's edges from an earlier out-layer (run start)
+    uint32_t alone[kTileAlone];       // in-cells (junction lane << 8 | inner index) whose cone
+                                      //   held more than kTileCand candidates
+    float fix[2];                     // fixed-coordinate range of the staged outer hits
 };
+
+constexpr int kTileSmem = kTileW * (int)sizeof(TileWarp);   // dynamic shared memory per CTA
 
 // Hit positions of an event's layer taken as periodic in azimuth: the first hit of the
 // unwrapped phi bin bb (in [-nb, 2 nb): bins below 0 and from nb on are the neighbouring turns)
@@ -1154,8 +1160,9 @@ __device__ __noinline__ void tile_direct(const DevBatch &b, const DevParams &p, 
                                          const TileWarp &S, const TileSpan &tk, uint32_t q0,
                                          uint32_t q1, float lo, float hi_, bool disk,
                                          uint32_t slot_i, uint32_t i, float4 hi, uint32_t j,
-                                         float4 hj, RZ32 a, uint4 itj, bool more, bool front)
+                                         float4 hj, uint4 itj, bool more, bool front)
 {
+    const RZ32 a = rz32(hi, hj);
     uint32_t np = 0;
     for (uint32_t q = q0; q < q1; ++q) {
         const uint32_t kt = S.sT[q];
@@ -1200,6 +1207,35 @@ __device__ __noinline__ void tile_direct(const DevBatch &b, const DevParams &p, 
         mark_reached(b, e, B, j, front);
     }
     b.nbr_head[A] = make_uint2(g0 + my0, wr);
+}
+
+// One listed in-cell (key: junction lane << 8 | inner staging index) written by tile_direct:
+// its cone recomputed from the staged hits (flo, fhi, scale: the outer union's free-coordinate
+// range and bin scale).
+template <bool F64>
+__device__ __noinline__ void tile_alone(const DevBatch &b, const DevParams &p, uint32_t e,
+                                        const TileWarp &S, TileSpan ti, TileSpan tk, uint32_t key,
+                                        float flo, float fhi, float scale, bool disk,
+                                        uint32_t slot_i, bool more, bool front)
+{
+    const uint32_t t = key >> 8, sx = key & 0xFFu;
+    const float4 hi = S.hin[sx], hj = S.jh[t];
+    const float jfix = disk ? hj.z : hj.w, jfree = disk ? hj.w : hj.z;
+    const float dlo = S.fix[0] - jfix, dhi = S.fix[1] - jfix;
+    uint32_t q0 = 0, q1 = tk.n;
+    float lo = -3.0e38f, hi_ = 3.0e38f;
+    if (cone_window(__fsub_rn(hj.w, hi.w), __fsub_rn(hj.z, hi.z), jfree, dlo, dhi, disk,
+                    p.tan_win, lo, hi_)) {
+        if (hi_ < flo || lo > fhi) return;
+        int b0 = (int)floorf((lo - flo) * scale);
+        int b1 = (int)floorf((hi_ - flo) * scale);
+        b0 = b0 < 0 ? 0 : (b0 >= kBins ? kBins - 1 : b0);
+        b1 = b1 < 0 ? 0 : (b1 >= kBins ? kBins - 1 : b1);
+        q0 = b0 ? S.bin[b0 - 1] : 0u;
+        q1 = S.bin[b1];
+    }
+    tile_direct<F64>(b, p, e, S, tk, q0, q1, lo, hi_, disk, slot_i, tile_pos(ti, sx), hi,
+                     S.jpos[t], hj, S.jit[t], more, front);
 }
 
 // Append the first n buffered passes (runs of equal in-cell, each complete).  A run whose in-cell
@@ -1338,35 +1374,21 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
                                                                              DevParams p,
                                                                              uint32_t layer_mask)
 {
-    __shared__ TileWarp s_w[kTileW];
+    extern __shared__ __align__(16) unsigned char s_tile[];   // kTileW x TileWarp
     const uint32_t FULL = 0xFFFFFFFFu;
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
-    TileWarp &S = s_w[wid];
+    TileWarp &S = reinterpret_cast<TileWarp *>(s_tile)[wid];
     const uint32_t nk = p.n_keys;
     const int nb = (int)p.nb;
     const uint64_t stride = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t n_tiles = b.jbase[b.E];
     for (uint64_t tt = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tt < n_tiles;
          tt += stride) {
-        // the tile: its event from the per-event tile prefix, its junctions from the event's
-        // layer ranges of the layers in layer_mask
-        const uint32_t e = find_event(b.jbase, b.E, (uint32_t)tt);
-        uint32_t o = (uint32_t)tt - b.jbase[e];
+        // the tile: (event, junction layer, first junction hit, junction hits)
+        const uint4 tr = b.tiles[tt];
+        const uint32_t e = tr.x, Lj = tr.y, J0 = tr.z, nJ = tr.w;
         const uint32_t *bk = b.bkt + (size_t)e * (nk + 1);
-        uint32_t Lj = 0, J0 = 0, nJ = 0;
-        for (uint32_t l = 0; l < p.n_layers; ++l) {
-            if (!((layer_mask >> l) & 1u)) continue;
-            const uint32_t lo = bk[l * p.nb], n_l = bk[(l + 1) * p.nb] - lo;
-            const uint32_t nt = (n_l + kTileJ - 1) / kTileJ;
-            if (o < nt) {
-                Lj = l;
-                J0 = lo + o * kTileJ;
-                nJ = min(kTileJ, n_l - o * kTileJ);
-                break;
-            }
-            o -= nt;
-        }
         const uint32_t nin = p.n_in[Lj], nout = p.n_out[Lj];
         if (nJ == 0 || nin == 0 || nout == 0) continue;
         const bool jv = lane < nJ;
@@ -1376,15 +1398,23 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
         const bool ok = jv && fabsf(phij) <= 4.f;    // (a non-finite azimuth has no window)
         const int blo = ok ? (int)floorf((phij - p.w_eps + kPiF2) * p.bins_per_rad) : 0;
         const int bhi = ok ? (int)floorf((phij + p.w_eps + kPiF2) * p.bins_per_rad) : 0;
-        // every union must fit the staging; otherwise the tile's junctions go one by one
-        bool fits = true;
-        for (uint32_t si = 0; si < nin && fits; ++si) {
+        const uint4 itj0 = ok ? b.item[(size_t)j * kMaxOut] : make_uint4(0u, 0u, 0u, 0u);
+        // the unions on the first root in-layer and the first out-layer (kept for the passes
+        // below); every union must fit the staging, otherwise the tile's junctions go one by one
+        uint32_t si0 = 0;
+        while (si0 < nin && !((p.root_mask >> p.in_layer[Lj][si0]) & 1u)) ++si0;
+        if (si0 == nin) continue;
+        uint32_t ws0, wn0, os, on;
+        const TileSpan ti0 = tile_span(bk + p.in_layer[Lj][si0] * p.nb, nb, ok, blo, bhi, ws0, wn0);
+        const TileSpan tk0 = tile_span(bk + p.out_layer[Lj][0] * p.nb, nb, ok, blo, bhi, os, on);
+        bool fits = ti0.n <= (uint32_t)kStage && tk0.n <= (uint32_t)kStage;
+        for (uint32_t si = si0 + 1; si < nin && fits; ++si) {
             const uint32_t Li = p.in_layer[Lj][si];
             if (!((p.root_mask >> Li) & 1u)) continue;
             uint32_t ws, wn;
             fits = tile_span(bk + Li * p.nb, nb, ok, blo, bhi, ws, wn).n <= (uint32_t)kStage;
         }
-        for (uint32_t s = 0; s < nout && fits; ++s) {
+        for (uint32_t s = 1; s < nout && fits; ++s) {
             uint32_t ws, wn;
             fits = tile_span(bk + p.out_layer[Lj][s] * p.nb, nb, ok, blo, bhi, ws, wn).n <=
                    (uint32_t)kStage;
@@ -1403,8 +1433,8 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
             // this pass takes the root in-cells; reached non-root ones go to the sparse pass
             if (!((p.root_mask >> Li) & 1u)) continue;
             const uint32_t slot_i = p.in_slot[Lj][si];
-            uint32_t ws, wn;
-            const TileSpan ti = tile_span(bk + Li * p.nb, nb, ok, blo, bhi, ws, wn);
+            uint32_t ws = ws0, wn = wn0;
+            const TileSpan ti = si == si0 ? ti0 : tile_span(bk + Li * p.nb, nb, ok, blo, bhi, ws, wn);
             if (ti.n == 0) continue;
             __syncwarp();
             tile_stage(b, ti, S.hin, lane);
@@ -1413,9 +1443,9 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
                 const bool disk = p.is_disk[Lk];
                 const bool front = !j_root && p.n_out[Lk] > 0;
                 const bool more = s > 0;
-                const uint4 itj = ok ? b.item[(size_t)j * kMaxOut + s] : make_uint4(0u, 0u, 0u, 0u);
-                uint32_t os, on;
-                const TileSpan tk = tile_span(bk + Lk * p.nb, nb, ok, blo, bhi, os, on);
+                const uint4 itj = s == 0 ? itj0 : (ok ? b.item[(size_t)j * kMaxOut + s]
+                                                      : make_uint4(0u, 0u, 0u, 0u));
+                const TileSpan tk = s == 0 ? tk0 : tile_span(bk + Lk * p.nb, nb, ok, blo, bhi, os, on);
                 if (tk.n == 0) continue;
                 __syncwarp();
                 S.jit[lane] = itj;
@@ -1434,8 +1464,13 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
                 const float flo = funord(__reduce_min_sync(FULL, m0));
                 const float fhi = funord(__reduce_max_sync(FULL, m1));
                 const float jfix = disk ? hj.z : hj.w, jfree = disk ? hj.w : hj.z;
-                const float dlo = funord(__reduce_min_sync(FULL, m2)) - jfix;
-                const float dhi = funord(__reduce_max_sync(FULL, m3)) - jfix;
+                const float xmin = funord(__reduce_min_sync(FULL, m2));
+                const float xmax = funord(__reduce_max_sync(FULL, m3));
+                if (lane == 0) {
+                    S.fix[0] = xmin;
+                    S.fix[1] = xmax;
+                }
+                const float dlo = xmin - jfix, dhi = xmax - jfix;
                 const float scale = fhi > flo ? (float)kBins / (fhi - flo) : 0.f;
                 auto local_bin = [&](float fc) {
                     const int bb = (int)floorf((fc - flo) * scale);
@@ -1530,64 +1565,78 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
                     __syncwarp();
                     np = keep;
                 };
-                for (uint32_t c = 0; c < wmax; ++c) {
-                    // ---- this step's inner hit per lane: cone, bins, candidates inside ----
-                    uint32_t nq = 0, k0 = 0, k1 = 0, sx = 0, q0 = 0, q1 = 0;
-                    float lo = -3.0e38f, hi_ = 3.0e38f;
-                    float4 hi = make_float4(0.f, 0.f, 0.f, 0.f);
-                    RZ32 a{0.f, 0.f, 0.f, 0.f};
-                    if (c < wme) {
-                        sx = ws + c;
-                        if (sx >= ti.n) sx -= ti.n;
-                        hi = S.hin[sx];
-                        a = rz32(hi, hj);
-                        q1 = tk.n;
-                        if (cone_window(a.ar, a.az, jfree, dlo, dhi, disk, p.tan_win, lo, hi_)) {
-                            if (hi_ < flo || lo > fhi) {
-                                q1 = 0;
-                            } else {
-                                int b0 = (int)floorf((lo - flo) * scale);
-                                int b1 = (int)floorf((hi_ - flo) * scale);
-                                b0 = b0 < 0 ? 0 : (b0 >= kBins ? kBins - 1 : b0);
-                                b1 = b1 < 0 ? 0 : (b1 >= kBins ? kBins - 1 : b1);
-                                q0 = b0 ? S.bin[b0 - 1] : 0u;
-                                q1 = S.bin[b1];
+                // the steps; in-cells whose cone holds more than kTileCand candidates are listed
+                // and written by their lanes alone between runs of steps (rare: kept out of the
+                // step loop, whose registers a call would constrain)
+                uint32_t nalone = 0;
+                for (uint32_t c = 0; c < wmax;) {
+                    for (; c < wmax; ++c) {
+                        // ---- this step's inner hit per lane: cone, bins, candidates inside ----
+                        uint32_t nq = 0, k0 = 0, k1 = 0, sx = 0;
+                        if (c < wme) {
+                            sx = ws + c;
+                            if (sx >= ti.n) sx -= ti.n;
+                            const float4 hi = S.hin[sx];
+                            // the segment (i, j) in r-z (norm and error bound only where tested)
+                            const float ar = __fsub_rn(hj.w, hi.w), az = __fsub_rn(hj.z, hi.z);
+                            uint32_t q0 = 0, q1 = tk.n;
+                            float lo = -3.0e38f, hi_ = 3.0e38f;
+                            if (cone_window(ar, az, jfree, dlo, dhi, disk, p.tan_win, lo, hi_)) {
+                                if (hi_ < flo || lo > fhi) {
+                                    q1 = 0;
+                                } else {
+                                    int b0 = (int)floorf((lo - flo) * scale);
+                                    int b1 = (int)floorf((hi_ - flo) * scale);
+                                    b0 = b0 < 0 ? 0 : (b0 >= kBins ? kBins - 1 : b0);
+                                    b1 = b1 < 0 ? 0 : (b1 >= kBins ? kBins - 1 : b1);
+                                    q0 = b0 ? S.bin[b0 - 1] : 0u;
+                                    q1 = S.bin[b1];
+                                }
+                            }
+                            for (uint32_t q = q0; q < q1; ++q) {
+                                const uint32_t kt = S.sT[q];
+                                const float fc = disk ? S.hout[kt].w : S.hout[kt].z;
+                                if (fc < lo || fc > hi_) continue;
+                                if (nq == 0) k0 = kt;
+                                else if (nq == 1) k1 = kt;
+                                ++nq;
                             }
                         }
-                        for (uint32_t q = q0; q < q1; ++q) {
-                            const uint32_t kt = S.sT[q];
-                            const float fc = disk ? S.hout[kt].w : S.hout[kt].z;
-                            if (fc < lo || fc > hi_) continue;
-                            if (nq == 0) k0 = kt;
-                            else if (nq == 1) k1 = kt;
-                            ++nq;
+                        const uint32_t me = lane << 16 | sx << 8;
+                        const bool alone = nq > kTileCand;
+                        const uint32_t am = __ballot_sync(FULL, alone);
+                        if (alone) S.alone[nalone + __popc(am & lt)] = me >> 8;
+                        nalone += __popc(am);
+                        // ---- queue the others' candidates (0 to 2 per lane, adjacent) ----
+                        const uint32_t m = alone ? 0u : nq;
+                        const uint32_t m1 = __ballot_sync(FULL, m & 1u), m2 = __ballot_sync(FULL, m & 2u);
+                        if (m1 | m2) {
+                            const uint32_t x = tail + __popc(m1 & lt) + 2u * __popc(m2 & lt);
+                            if (m > 0) S.q[x % kTileQ] = me | k0;
+                            if (m > 1) S.q[(x + 1) % kTileQ] = me | k1;
+                            tail += __popc(m1) + 2u * __popc(m2);
+                            __syncwarp();
+                        }
+                        // ---- full batches; a flush keeps a run that may continue in the queue
+                        while (tail - head >= 32) {
+                            if (np + 32 > kTilePass) flush_complete();
+                            batch(32);
+                            __syncwarp();
+                        }
+                        if (nalone > kTileAlone - 32) {
+                            ++c;
+                            break;
                         }
                     }
-                    // a cone with many candidates is taken by its lane alone (rare)
-                    const bool alone = nq > kTileCand;
-                    if (alone)
-                        tile_direct<F64>(b, p, e, S, tk, q0, q1, lo, hi_, disk, slot_i,
-                                         tile_pos(ti, sx), hi, j, hj, a, itj, more, front);
-                    // ---- queue the others' candidates: a lane's entries are adjacent ----
-                    const uint32_t m = alone ? 0u : nq;
-                    uint32_t incl = m;
-#pragma unroll
-                    for (int w = 1; w < 32; w <<= 1) {
-                        const uint32_t t = __shfl_up_sync(FULL, incl, w);
-                        if (lane >= (uint32_t)w) incl += t;
-                    }
-                    const uint32_t tot = __shfl_sync(FULL, incl, 31);
-                    const uint32_t me = lane << 16 | sx << 8;
-                    if (m > 0) S.q[(tail + incl - m) % kTileQ] = me | k0;
-                    if (m > 1) S.q[(tail + incl - m + 1) % kTileQ] = me | k1;
-                    tail += tot;
                     __syncwarp();
-                    // ---- full batches; a flush keeps a run that may continue in the queue ----
-                    while (tail - head >= 32) {
-                        if (np + 32 > kTilePass) flush_complete();
-                        batch(32);
-                        __syncwarp();
-                    }
+                    if (lane < nalone)
+                        tile_alone<F64>(b, p, e, S, ti, tk, S.alone[lane], flo, fhi, scale, disk,
+                                        slot_i, more, front);
+                    if (nalone > 32 && lane < nalone - 32)
+                        tile_alone<F64>(b, p, e, S, ti, tk, S.alone[32 + lane], flo, fhi, scale,
+                                        disk, slot_i, more, front);
+                    nalone = 0;
+                    __syncwarp();
                 }
                 // drain the queue and append everything
                 while (tail != head) {
@@ -1602,9 +1651,9 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
 }
 
 
-// Per-event prefix of the junction tiles of a dense CA level (per layer of layer_mask, its hits
-// in runs of `per`): jbase[e] = those of events before e, jbase[E] = all.  One CTA; each thread
-// takes a run of consecutive events.
+// The tiles of a dense CA level: per event and layer of layer_mask, its hits in runs of
+// per_tile.  jbase[e] = the tiles of events before e, jbase[E] = all; tiles[] = each tile's
+// (event, layer, first hit, hits).  One CTA; each thread takes a run of consecutive events.
 __global__ void __launch_bounds__(1024) k_jbase(DevBatch b, DevParams p, uint32_t layer_mask,
                                                 uint32_t per_tile)
 {
@@ -1639,7 +1688,13 @@ __global__ void __launch_bounds__(1024) k_jbase(DevBatch b, DevParams p, uint32_
     run += incl - mine;
     for (uint32_t e = e0; e < e1; ++e) {
         b.jbase[e] = run;
-        run += count(e);
+        const uint32_t *bke = b.bkt + (size_t)e * (p.n_keys + 1);
+        for (uint32_t l = 0; l < p.n_layers; ++l) {
+            if (!((layer_mask >> l) & 1u)) continue;
+            const uint32_t lo = bke[l * p.nb], n_l = bke[(l + 1) * p.nb] - lo;
+            for (uint32_t k = 0; k < n_l; k += per_tile)
+                b.tiles[run++] = make_uint4(e, l, lo + k, min(per_tile, n_l - k));
+        }
     }
     if (tid == 0) b.jbase[b.E] = tot;
 }
@@ -1654,9 +1709,9 @@ void launch_connect(const DevBatch &b, const DevParams &p, uint32_t layer_mask, 
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
     if (p.cut_mode == CUT_FP64)
-        k_connect_tiles<true><<<(unsigned)blocks, kTileW * 32, 0, s>>>(b, p, layer_mask);
+        k_connect_tiles<true><<<(unsigned)blocks, kTileW * 32, kTileSmem, s>>>(b, p, layer_mask);
     else
-        k_connect_tiles<false><<<(unsigned)blocks, kTileW * 32, 0, s>>>(b, p, layer_mask);
+        k_connect_tiles<false><<<(unsigned)blocks, kTileW * 32, kTileSmem, s>>>(b, p, layer_mask);
 }
 
 // Sparse CA pass of one level over the frontier: cells B = (j, k) that were reached (have an
@@ -1992,8 +2047,15 @@ void launch_canon(const DevBatch &b, cudaStream_t s, int sms)
 
 cudaError_t init_graph_kernels()
 {
-    return cudaFuncSetAttribute(k_canon, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kCanonSmem * (int)sizeof(uint32_t));
+    cudaError_t r = cudaFuncSetAttribute(k_canon, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kCanonSmem * (int)sizeof(uint32_t));
+    if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(k_connect_tiles<false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmem);
+    if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(k_connect_tiles<true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmem);
+    return r;
 }
 
 }  // namespace pxr

@@ -22,6 +22,7 @@ constexpr int kLocalBits = 24;   // hmeta = layer << 24 | index of the hit insid
 constexpr uint32_t kLocalMask = (1u << kLocalBits) - 1u;
 constexpr uint32_t kChunk = 256;     // per-event cell / ntuplet capacities are multiples of this
 constexpr uint32_t kHitChunk = 32;   // granularity of the hit -> event table
+constexpr uint32_t kCaTile = 32;     // junction hits per tile of the dense CA pass
 
 // Per-event counters, laid out as kCounters consecutive arrays of E words.
 enum Counter : int {
@@ -132,7 +133,9 @@ struct DevBatch {
                                         //   outer hit starts further pairs (the sparse CA input;
                                         //   kNone: a slot reserved for a cell already listed)
     uint32_t *front_in;                 // [edges] the inner hits of the frontier cells
-    uint32_t *jbase;                    // [E + 1] junction prefix of a dense CA level
+    uint32_t *jbase;                    // [E + 1] per-event prefix of the tiles of a dense CA level
+    uint4 *tiles;                       // [N / kCaTile + E * n_layers + 1] the tiles of a dense CA
+                                        //   level: (event, layer, first junction hit, hits)
     unsigned long long *ca_tests;       // [2] or null: CA candidate tests evaluated (r-z test) and
                                         //   of them the ones whose DCA was evaluated (counted
                                         //   only when non-null)

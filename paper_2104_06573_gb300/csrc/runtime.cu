@@ -291,7 +291,7 @@ struct PlanOffsets {
         hit_chunk,
         head_end;
     size_t cnt, bkt, hs, r64, hmeta, hphi, gofs, gpos, gfree, glay, item, cell_out,
-        nbr_head, nbr, mindepth, root_list, root_in, live, front_list, front_in, front_snap, jbase, ca_tests, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, tup_tmp, canon_cnt, out_evt, o_nh,
+        nbr_head, nbr, mindepth, root_list, root_in, live, front_list, front_in, front_snap, jbase, tiles, ca_tests, tup_hits, tup_n, tup_state, tup_first, tup_rank, tup_list, tup_tmp, canon_cnt, out_evt, o_nh,
         o_hits, o_pt, o_phi, o_cot, o_dxy, o_dz, o_chi2, o_q, o_status, o_ql, best, o_cov, o_vtx,
         v_z, v_err, v_pt2, v_n;
     size_t total;
@@ -339,6 +339,7 @@ static PlanOffsets plan_layout(uint32_t E, uint64_t N, uint64_t C, uint64_t G, u
     o.front_in = L.add(4 * G);
     o.front_snap = L.add(4 * (size_t)E);
     o.jbase = L.add(4 * ((size_t)E + 1));
+    o.tiles = L.add(16 * (N / kCaTile + (size_t)E * dp.n_layers + 1));
     o.ca_tests = L.add(16);
     o.tup_hits = L.add(4 * T * kMaxHits);
     o.tup_n = L.add(T);
@@ -605,6 +606,7 @@ static void plan_bind(pxr_plan *P)
     b.front_in = (uint32_t *)(r + o.front_in);
     b.front_snap = (uint32_t *)(r + o.front_snap);
     b.jbase = (uint32_t *)(r + o.jbase);
+    b.tiles = (uint4 *)(r + o.tiles);
     b.tup_hits = (uint32_t *)(r + o.tup_hits);
     b.tup_n = (uint8_t *)(r + o.tup_n);
     b.tup_state = (uint8_t *)(r + o.tup_state);
