@@ -1036,11 +1036,31 @@ constexpr uint32_t kTileAlone = 64;   // in-cells with many candidates, handled 
                                       //   its shared memory allows four)
 #endif
 
+constexpr uint32_t kZBins = 512;      // bins of the outer union's free coordinate
+
+// The staged unions of the tile path: the inner hits' (z, r), the outer hits' free coordinate
+// in staging order and in bin order with their staging indices, the bin ends (16 bits each, two
+// per word; a union holds at most kStage hits).  The step loop reads nothing else.
+struct TileStage {
+    float2 hin[kStage];
+    float zs[kStage];
+    float zo[kStage];
+    uint16_t sT[kStage];
+    uint32_t zb[kZBins / 2];
+};
+
+// The staging of connect_junction (the tile's junctions one by one).
+struct TileFallback {
+    float4 sH[kStage];
+    uint16_t sT[kStage];
+    uint32_t bin[kBins];
+};
+
 struct TileWarp {
-    float4 hin[kStage];               // inner-layer window union, staging order
-    float4 hout[kStage];              // outer-layer window union, staging order
-    uint16_t sT[kStage];              // hout indices in free-coordinate bin order
-    uint32_t bin[kBins];              // bin ends after the scan
+    union {
+        TileStage t;
+        TileFallback f;
+    } u;
     float4 jh[32];                    // the junctions' hits
     uint4 jit[32];                    // their entries on the current out-layer
     uint32_t jpos[32];                // their sorted positions
@@ -1052,6 +1072,12 @@ struct TileWarp {
                                       //   held more than kTileCand candidates
     float fix[2];                     // fixed-coordinate range of the staged outer hits
 };
+
+// End of bin x of the packed bin ends.
+__device__ __forceinline__ uint32_t zbin_end(const uint32_t *zb, uint32_t x)
+{
+    return (zb[x >> 1] >> (16u * (x & 1u))) & 0xFFFFu;
+}
 
 constexpr int kTileSmem = kTileW * (int)sizeof(TileWarp);   // dynamic shared memory per CTA
 
@@ -1127,14 +1153,15 @@ __device__ __forceinline__ TileSpan tile_span(const uint32_t *lb, int nb, bool o
 // (j, k) is a cell (rank in j's window, entry holding k) and the exact triplet cut passes.
 template <bool F64>
 __device__ __forceinline__ uint32_t tile_test(const DevBatch &b, const DevParams &p,
-                                              const TileSpan &tk, uint32_t kt, float4 hk,
-                                              uint32_t i, float4 hi, uint32_t j, float4 hj,
-                                              const RZ32 &a, uint4 itj)
+                                              const TileSpan &tk, uint32_t kt, uint32_t i,
+                                              float4 hi, uint32_t j, float4 hj, const RZ32 &a,
+                                              uint4 itj)
 {
     const uint32_t k = tile_pos(tk, kt);
     const uint32_t rank = k >= itj.z ? k - itj.z : k + itj.w;
     if (rank >= itj.y) return kNone;
     const uint32_t B = itj.x + rank;
+    const float4 hk = b.hs[k];
     if (!triplet_test<F64>(b, p, i, j, B, k, hi.x, hi.y, hj, hk, a)) return kNone;
     return b.cell_out[B] == k ? B : kNone;          // (j, k) failed the doublet cut: kNone
 }
@@ -1165,10 +1192,9 @@ __device__ __noinline__ void tile_direct(const DevBatch &b, const DevParams &p, 
     const RZ32 a = rz32(hi, hj);
     uint32_t np = 0;
     for (uint32_t q = q0; q < q1; ++q) {
-        const uint32_t kt = S.sT[q];
-        const float4 hk = S.hout[kt];
-        const float fc = disk ? hk.w : hk.z;
-        if (fc >= lo && fc <= hi_ && tile_test<F64>(b, p, tk, kt, hk, i, hi, j, hj, a, itj) != kNone)
+        const float fc = S.u.t.zo[q];
+        if (fc >= lo && fc <= hi_ &&
+            tile_test<F64>(b, p, tk, S.u.t.sT[q], i, hi, j, hj, a, itj) != kNone)
             ++np;
     }
     if (np == 0) return;
@@ -1197,11 +1223,9 @@ __device__ __noinline__ void tile_direct(const DevBatch &b, const DevParams &p, 
     uint32_t wr = 0;
     for (uint32_t t = 0; t < have && wr < nw; ++t) b.nbr[g0 + my0 + wr++] = b.nbr[old + t];
     for (uint32_t q = q0; q < q1; ++q) {
-        const uint32_t kt = S.sT[q];
-        const float4 hk = S.hout[kt];
-        const float fc = disk ? hk.w : hk.z;
+        const float fc = S.u.t.zo[q];
         if (!(fc >= lo && fc <= hi_)) continue;
-        const uint32_t B = tile_test<F64>(b, p, tk, kt, hk, i, hi, j, hj, a, itj);
+        const uint32_t B = tile_test<F64>(b, p, tk, S.u.t.sT[q], i, hi, j, hj, a, itj);
         if (B == kNone) continue;
         if (wr < nw) b.nbr[g0 + my0 + wr++] = B;
         mark_reached(b, e, B, j, front);
@@ -1219,7 +1243,7 @@ __device__ __noinline__ void tile_alone(const DevBatch &b, const DevParams &p, u
                                         uint32_t slot_i, bool more, bool front)
 {
     const uint32_t t = key >> 8, sx = key & 0xFFu;
-    const float4 hi = S.hin[sx], hj = S.jh[t];
+    const float4 hi = b.hs[tile_pos(ti, sx)], hj = S.jh[t];
     const float jfix = disk ? hj.z : hj.w, jfree = disk ? hj.w : hj.z;
     const float dlo = S.fix[0] - jfix, dhi = S.fix[1] - jfix;
     uint32_t q0 = 0, q1 = tk.n;
@@ -1229,10 +1253,10 @@ __device__ __noinline__ void tile_alone(const DevBatch &b, const DevParams &p, u
         if (hi_ < flo || lo > fhi) return;
         int b0 = (int)floorf((lo - flo) * scale);
         int b1 = (int)floorf((hi_ - flo) * scale);
-        b0 = b0 < 0 ? 0 : (b0 >= kBins ? kBins - 1 : b0);
-        b1 = b1 < 0 ? 0 : (b1 >= kBins ? kBins - 1 : b1);
-        q0 = b0 ? S.bin[b0 - 1] : 0u;
-        q1 = S.bin[b1];
+        b0 = b0 < 0 ? 0 : (b0 >= (int)kZBins ? (int)kZBins - 1 : b0);
+        b1 = b1 < 0 ? 0 : (b1 >= (int)kZBins ? (int)kZBins - 1 : b1);
+        q0 = b0 ? zbin_end(S.u.t.zb, b0 - 1) : 0u;
+        q1 = zbin_end(S.u.t.zb, b1);
     }
     tile_direct<F64>(b, p, e, S, tk, q0, q1, lo, hi_, disk, slot_i, tile_pos(ti, sx), hi,
                      S.jpos[t], hj, S.jit[t], more, front);
@@ -1350,8 +1374,8 @@ __device__ __forceinline__ void tile_flush(const DevBatch &b, uint32_t e, TileWa
     __syncwarp();
 }
 
-// Stage the hits of a union (n <= kStage) into dst, four loads in flight per lane.
-__device__ __forceinline__ void tile_stage(const DevBatch &b, const TileSpan &t, float4 *dst,
+// Stage the (z, r) of a union's hits (n <= kStage) into dst, four loads in flight per lane.
+__device__ __forceinline__ void tile_stage(const DevBatch &b, const TileSpan &t, float2 *dst,
                                            uint32_t lane)
 {
     for (uint32_t q0 = 0; q0 < t.n; q0 += 128) {
@@ -1364,7 +1388,7 @@ __device__ __forceinline__ void tile_stage(const DevBatch &b, const TileSpan &t,
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const uint32_t q = q0 + 32u * u + lane;
-            if (q < t.n) dst[q] = h[u];
+            if (q < t.n) dst[q] = make_float2(h[u].z, h[u].w);
         }
     }
 }
@@ -1421,7 +1445,7 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
         }
         if (!fits) {
             for (uint32_t t = 0; t < nJ; ++t)
-                connect_junction<F64>(b, p, e, J0 + t, layer_mask, S.hout, S.sT, S.bin);
+                connect_junction<F64>(b, p, e, J0 + t, layer_mask, S.u.f.sH, S.u.f.sT, S.u.f.bin);
             continue;
         }
         const bool j_root = (p.root_mask >> Lj) & 1u;
@@ -1437,7 +1461,7 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
             const TileSpan ti = si == si0 ? ti0 : tile_span(bk + Li * p.nb, nb, ok, blo, bhi, ws, wn);
             if (ti.n == 0) continue;
             __syncwarp();
-            tile_stage(b, ti, S.hin, lane);
+            tile_stage(b, ti, S.u.t.hin, lane);
             for (uint32_t s = 0; s < nout; ++s) {
                 const uint32_t Lk = p.out_layer[Lj][s];
                 const bool disk = p.is_disk[Lk];
@@ -1449,17 +1473,28 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
                 if (tk.n == 0) continue;
                 __syncwarp();
                 S.jit[lane] = itj;
-                tile_stage(b, tk, S.hout, lane);
-                __syncwarp();
-                // range of the free (z barrel, r disk) and fixed coordinates of the staged hits
+                // the outer union's free (z barrel, r disk) coordinates and their range, the
+                // range of the fixed coordinate
                 int m0 = ford(3.0e38f), m1 = ford(-3.0e38f), m2 = m0, m3 = m1;
-                for (uint32_t q = lane; q < tk.n; q += 32) {
-                    const float4 hk = S.hout[q];
-                    const float fc = disk ? hk.w : hk.z, xc = disk ? hk.z : hk.w;
-                    m0 = min(m0, ford(fc));
-                    m1 = max(m1, ford(fc));
-                    m2 = min(m2, ford(xc));
-                    m3 = max(m3, ford(xc));
+                for (uint32_t q0 = 0; q0 < tk.n; q0 += 128) {
+                    float4 h[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t q = q0 + 32u * u + lane;
+                        if (q < tk.n) h[u] = b.hs[tile_pos(tk, q)];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t q = q0 + 32u * u + lane;
+                        if (q < tk.n) {
+                            const float fc = disk ? h[u].w : h[u].z, xc = disk ? h[u].z : h[u].w;
+                            S.u.t.zs[q] = fc;
+                            m0 = min(m0, ford(fc));
+                            m1 = max(m1, ford(fc));
+                            m2 = min(m2, ford(xc));
+                            m3 = max(m3, ford(xc));
+                        }
+                    }
                 }
                 const float flo = funord(__reduce_min_sync(FULL, m0));
                 const float fhi = funord(__reduce_max_sync(FULL, m1));
@@ -1471,25 +1506,30 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
                     S.fix[1] = xmax;
                 }
                 const float dlo = xmin - jfix, dhi = xmax - jfix;
-                const float scale = fhi > flo ? (float)kBins / (fhi - flo) : 0.f;
+                const float scale = fhi > flo ? (float)kZBins / (fhi - flo) : 0.f;
                 auto local_bin = [&](float fc) {
                     const int bb = (int)floorf((fc - flo) * scale);
-                    return bb < 0 ? 0u : (bb >= kBins ? (uint32_t)kBins - 1u : (uint32_t)bb);
+                    return bb < 0 ? 0u : (bb >= (int)kZBins ? kZBins - 1u : (uint32_t)bb);
                 };
-                // counting sort of the staged hits by bin: histogram, scan, scatter
+                // counting sort of the staged hits by bin (16-bit counters, two per word):
+                // histogram, scan, scatter
+                uint32_t *zb = S.u.t.zb;
 #pragma unroll
-                for (int q = 0; q < kBins / 32; ++q) S.bin[lane + 32 * q] = 0;
+                for (uint32_t q = 0; q < kZBins / 2; q += 32) zb[q + lane] = 0;
                 __syncwarp();
                 for (uint32_t q = lane; q < tk.n; q += 32) {
-                    const float4 hk = S.hout[q];
-                    atomicAdd(&S.bin[local_bin(disk ? hk.w : hk.z)], 1u);
+                    const uint32_t x = local_bin(S.u.t.zs[q]);
+                    atomicAdd(&zb[x >> 1], 1u << (16u * (x & 1u)));
                 }
                 __syncwarp();
                 {
-                    constexpr int per = kBins / 32;
+                    constexpr uint32_t per = kZBins / 64;      // words per lane
                     uint32_t v[per], sum = 0;
 #pragma unroll
-                    for (int q = 0; q < per; ++q) { v[q] = S.bin[lane * per + q]; sum += v[q]; }
+                    for (uint32_t q = 0; q < per; ++q) {
+                        v[q] = zb[lane * per + q];
+                        sum += (v[q] & 0xFFFFu) + (v[q] >> 16);
+                    }
                     uint32_t incl = sum;
 #pragma unroll
                     for (int w = 1; w < 32; w <<= 1) {
@@ -1499,15 +1539,22 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
                     uint32_t run = incl - sum;
                     __syncwarp();
 #pragma unroll
-                    for (int q = 0; q < per; ++q) { S.bin[lane * per + q] = run; run += v[q]; }
+                    for (uint32_t q = 0; q < per; ++q) {
+                        const uint32_t lo16 = run, hi16 = run + (v[q] & 0xFFFFu);
+                        zb[lane * per + q] = lo16 | hi16 << 16;
+                        run = hi16 + (v[q] >> 16);
+                    }
                     __syncwarp();
                 }
                 for (uint32_t q = lane; q < tk.n; q += 32) {
-                    const float4 hk = S.hout[q];
-                    S.sT[atomicAdd(&S.bin[local_bin(disk ? hk.w : hk.z)], 1u)] = (uint16_t)q;
+                    const float fc = S.u.t.zs[q];
+                    const uint32_t x = local_bin(fc), sh = 16u * (x & 1u);
+                    const uint32_t pos = (atomicAdd(&zb[x >> 1], 1u << sh) >> sh) & 0xFFFFu;
+                    S.u.t.zo[pos] = fc;
+                    S.u.t.sT[pos] = (uint16_t)q;
                 }
                 __syncwarp();
-                // S.bin[t] is now the end of bin t.  The lanes step through their junctions'
+                // zb now holds the end of each bin.  The lanes step through their junctions'
                 // inner windows together; candidates in a cone are queued (ring of kTileQ,
                 // positions head..tail) and tested 32 at a time; passes buffered (np of them).
                 const uint32_t wme = itj.y ? wn : 0u;      // j without cells on Lk: nothing
@@ -1521,10 +1568,10 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
                     uint32_t A = kNone, B = kNone, pi = 0;
                     const uint32_t t = ent >> 16, sx = (ent >> 8) & 0xFFu, kt = ent & 0xFFu;
                     if (v) {
-                        const float4 hi = S.hin[sx], hjt = S.jh[t];
                         pi = tile_pos(ti, sx);
-                        B = tile_test<F64>(b, p, tk, kt, S.hout[kt], pi, hi, S.jpos[t], hjt,
-                                           rz32(hi, hjt), S.jit[t]);
+                        const float4 hi = b.hs[pi], hjt = S.jh[t];
+                        B = tile_test<F64>(b, p, tk, kt, pi, hi, S.jpos[t], hjt, rz32(hi, hjt),
+                                           S.jit[t]);
                         if (B != kNone) A = tile_incell(b, pi, slot_i, S.jpos[t]);
                     }
                     const uint32_t pm = __ballot_sync(FULL, A != kNone);
@@ -1576,9 +1623,9 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
                         if (c < wme) {
                             sx = ws + c;
                             if (sx >= ti.n) sx -= ti.n;
-                            const float4 hi = S.hin[sx];
+                            const float2 hi = S.u.t.hin[sx];     // (z, r)
                             // the segment (i, j) in r-z (norm and error bound only where tested)
-                            const float ar = __fsub_rn(hj.w, hi.w), az = __fsub_rn(hj.z, hi.z);
+                            const float ar = __fsub_rn(hj.w, hi.y), az = __fsub_rn(hj.z, hi.x);
                             uint32_t q0 = 0, q1 = tk.n;
                             float lo = -3.0e38f, hi_ = 3.0e38f;
                             if (cone_window(ar, az, jfree, dlo, dhi, disk, p.tan_win, lo, hi_)) {
@@ -1587,16 +1634,16 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
                                 } else {
                                     int b0 = (int)floorf((lo - flo) * scale);
                                     int b1 = (int)floorf((hi_ - flo) * scale);
-                                    b0 = b0 < 0 ? 0 : (b0 >= kBins ? kBins - 1 : b0);
-                                    b1 = b1 < 0 ? 0 : (b1 >= kBins ? kBins - 1 : b1);
-                                    q0 = b0 ? S.bin[b0 - 1] : 0u;
-                                    q1 = S.bin[b1];
+                                    b0 = b0 < 0 ? 0 : (b0 >= (int)kZBins ? (int)kZBins - 1 : b0);
+                                    b1 = b1 < 0 ? 0 : (b1 >= (int)kZBins ? (int)kZBins - 1 : b1);
+                                    q0 = b0 ? zbin_end(zb, b0 - 1) : 0u;
+                                    q1 = zbin_end(zb, b1);
                                 }
                             }
                             for (uint32_t q = q0; q < q1; ++q) {
-                                const uint32_t kt = S.sT[q];
-                                const float fc = disk ? S.hout[kt].w : S.hout[kt].z;
+                                const float fc = S.u.t.zo[q];
                                 if (fc < lo || fc > hi_) continue;
+                                const uint32_t kt = S.u.t.sT[q];
                                 if (nq == 0) k0 = kt;
                                 else if (nq == 1) k1 = kt;
                                 ++nq;
