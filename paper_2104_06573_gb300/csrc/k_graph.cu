@@ -1568,11 +1568,29 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
                     uint32_t A = kNone, B = kNone, pi = 0;
                     const uint32_t t = ent >> 16, sx = (ent >> 8) & 0xFFu, kt = ent & 0xFFu;
                     if (v) {
+                        // the out-cell (j, k) by k's rank in j's window; the hits and i's entries
+                        // record loaded together, then both cell entries together
                         pi = tile_pos(ti, sx);
-                        const float4 hi = b.hs[pi], hjt = S.jh[t];
-                        B = tile_test<F64>(b, p, tk, kt, pi, hi, S.jpos[t], hjt, rz32(hi, hjt),
-                                           S.jit[t]);
-                        if (B != kNone) A = tile_incell(b, pi, slot_i, S.jpos[t]);
+                        const uint32_t k = tile_pos(tk, kt), jq = S.jpos[t];
+                        const uint4 itq = S.jit[t];
+                        const uint32_t rk = k >= itq.z ? k - itq.z : k + itq.w;
+                        if (rk < itq.y) {
+                            const float4 hi = b.hs[pi], hk = b.hs[k], hjt = S.jh[t];
+                            const uint4 iti = b.item[(size_t)pi * kMaxOut + slot_i];
+                            if (triplet_test<F64>(b, p, pi, jq, itq.x + rk, k, hi.x, hi.y, hjt,
+                                                  hk, rz32(hi, hjt))) {
+                                const uint32_t ri = jq >= iti.z ? jq - iti.z : jq + iti.w;
+                                if (ri < iti.y) {
+                                    const uint32_t Bc = itq.x + rk, Ac = iti.x + ri;
+                                    const uint32_t ob = b.cell_out[Bc], oa = b.cell_out[Ac];
+                                    // (j, k) and (i, j) cells: the doublet stage kept both
+                                    if (ob == k && oa == jq) {
+                                        A = Ac;
+                                        B = Bc;
+                                    }
+                                }
+                            }
+                        }
                     }
                     const uint32_t pm = __ballot_sync(FULL, A != kNone);
                     if (A != kNone) {
