@@ -450,14 +450,14 @@ def run_pxr(args, rank, world, local):
             "gpu_launches": plan.pxr_plan_launches() * args.steps,
             "stage_ms": dict(zip(["sort", "doublets", "connect", "ntuplets+select",
                                   "fit+output"], [round(v, 4) for v in stage])),
-            "roofline": {"kernel": "k_connect + k_connect_front (CA stage)", "bound": "hbm",
+            "roofline": {"kernel": "k_connect_tiles + k_ca_front (CA stage)", "bound": "hbm",
                          "achieved": ca_achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": ca_achieved / hbm_peak, "peak_source": peak_src,
                          "traffic": ca_traffic(cells, params.n_phi_bins),
                          "algorithmic_bytes": ca_alg, "cells": cells, "edges": edges,
                          "note": "latency- and issue-bound (L2-resident gathers, returning "
                                  "atomics); the HBM fraction is low by construction"},
-            "roofline_ca_alu": {"kernel": "k_connect + k_connect_front (CA stage)",
+            "roofline_ca_alu": {"kernel": "k_connect_tiles + k_ca_front (CA stage)",
                                 "bound": "alu", "achieved": ca_tflops, "peak": fp32_peak,
                                 "unit": "TFLOP/s", "frac": ca_tflops / fp32_peak,
                                 "peak_source": f"nominal FP32: {sms} SMs x 128 lanes x 2 "
