@@ -404,6 +404,32 @@ __device__ __forceinline__ bool cone_window(float ar, float az, float base, floa
     return true;
 }
 
+// The cone window of cone_window for the tile pass, with a division-free slope interval: the
+// exact interval [(m - T)/(1 + mT), (m + T)/(1 - mT)] deviates from m by T(1 + m^2)/(1 -+ mT),
+// and 1/(1 - x) <= 1 + 2|x| for |x| <= 1/2, so [m - d, m + d] with d = T(1 + m^2)(1 + 2|m|T)
+// contains it (a wider cone only admits candidates the exact cut then rejects).  dlo, dhi come
+// adjusted by the caller (the same widening cone_window applies), dmx = 1e-5 max(|dlo|, |dhi|).
+// Returns false when the whole free range must be scanned (|mT| > 1/2 included).
+__device__ __forceinline__ bool cone_tile(float ar, float az, float base, float dlo, float dhi,
+                                          float dmx, bool disk, float T, float &lo, float &hi)
+{
+    const float u = disk ? az : ar, v = disk ? ar : az;
+    if (!(fabsf(u) > 1e-20f)) return false;
+    const float m = __fdividef(v, u);
+    const float mt = fabsf(m) * T;
+    if (!(mt <= 0.5f)) return false;
+    const float d = T * __fmaf_rn(m, m, 1.f) * __fmaf_rn(2.f, mt, 1.f);
+    const float sl = m - d, sh = m + d;
+    const float c1 = dlo * sl, c2 = dlo * sh, c3 = dhi * sl, c4 = dhi * sh;
+    lo = base + fminf(fminf(c1, c2), fminf(c3, c4));
+    hi = base + fmaxf(fmaxf(c1, c2), fmaxf(c3, c4));
+    const float smax = fabsf(m) + d;
+    const float margin = 2e-3f + 1e-4f * (fabsf(lo) + fabsf(hi)) + dmx * __fmaf_rn(smax, smax, 1.f);
+    lo -= margin;
+    hi += margin;
+    return true;
+}
+
 // Mark cell C as reached (it has an in-edge).  The first marker clears C's edge count (the walk
 // reads it; a later level writes the count if C gets out-edges) and, when C is `listed` (a
 // non-root cell whose outer hit starts further pairs), appends it to the event's frontier list,
@@ -1245,11 +1271,14 @@ __device__ __noinline__ void tile_alone(const DevBatch &b, const DevParams &p, u
     const uint32_t t = key >> 8, sx = key & 0xFFu;
     const float4 hi = b.hs[tile_pos(ti, sx)], hj = S.jh[t];
     const float jfix = disk ? hj.z : hj.w, jfree = disk ? hj.w : hj.z;
-    const float dlo = S.fix[0] - jfix, dhi = S.fix[1] - jfix;
+    float dlo = S.fix[0] - jfix, dhi = S.fix[1] - jfix;
+    dlo -= 1e-4f + 1e-5f * fabsf(dlo);
+    dhi += 1e-4f + 1e-5f * fabsf(dhi);
+    const float dmx = 1e-5f * fmaxf(fabsf(dlo), fabsf(dhi));
     uint32_t q0 = 0, q1 = tk.n;
     float lo = -3.0e38f, hi_ = 3.0e38f;
-    if (cone_window(__fsub_rn(hj.w, hi.w), __fsub_rn(hj.z, hi.z), jfree, dlo, dhi, disk,
-                    p.tan_win, lo, hi_)) {
+    if (cone_tile(__fsub_rn(hj.w, hi.w), __fsub_rn(hj.z, hi.z), jfree, dlo, dhi, dmx, disk,
+                  p.tan_win, lo, hi_)) {
         if (hi_ < flo || lo > fhi) return;
         int b0 = (int)floorf((lo - flo) * scale);
         int b1 = (int)floorf((hi_ - flo) * scale);
@@ -1505,7 +1534,10 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
                     S.fix[0] = xmin;
                     S.fix[1] = xmax;
                 }
-                const float dlo = xmin - jfix, dhi = xmax - jfix;
+                float dlo = xmin - jfix, dhi = xmax - jfix;
+                dlo -= 1e-4f + 1e-5f * fabsf(dlo);
+                dhi += 1e-4f + 1e-5f * fabsf(dhi);
+                const float dmx = 1e-5f * fmaxf(fabsf(dlo), fabsf(dhi));
                 const float scale = fhi > flo ? (float)kZBins / (fhi - flo) : 0.f;
                 auto local_bin = [&](float fc) {
                     const int bb = (int)floorf((fc - flo) * scale);
@@ -1646,7 +1678,7 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
                             const float ar = __fsub_rn(hj.w, hi.y), az = __fsub_rn(hj.z, hi.x);
                             uint32_t q0 = 0, q1 = tk.n;
                             float lo = -3.0e38f, hi_ = 3.0e38f;
-                            if (cone_window(ar, az, jfree, dlo, dhi, disk, p.tan_win, lo, hi_)) {
+                            if (cone_tile(ar, az, jfree, dlo, dhi, dmx, disk, p.tan_win, lo, hi_)) {
                                 if (hi_ < flo || lo > fhi) {
                                     q1 = 0;
                                 } else {
