@@ -1785,15 +1785,23 @@ __global__ void __launch_bounds__(1024) k_jbase(DevBatch b, DevParams p, uint32_
     run += incl - mine;
     for (uint32_t e = e0; e < e1; ++e) {
         b.jbase[e] = run;
+        run += count(e);
+    }
+    if (tid == 0) b.jbase[b.E] = tot;
+    __syncthreads();
+    // the records: one warp per event, its tiles over the lanes
+    for (uint32_t e = wid; e < b.E; e += nt / 32) {
+        uint32_t r = b.jbase[e];
         const uint32_t *bke = b.bkt + (size_t)e * (p.n_keys + 1);
         for (uint32_t l = 0; l < p.n_layers; ++l) {
             if (!((layer_mask >> l) & 1u)) continue;
             const uint32_t lo = bke[l * p.nb], n_l = bke[(l + 1) * p.nb] - lo;
-            for (uint32_t k = 0; k < n_l; k += per_tile)
-                b.tiles[run++] = make_uint4(e, l, lo + k, min(per_tile, n_l - k));
+            const uint32_t ntl = (n_l + per_tile - 1) / per_tile;
+            for (uint32_t k = lane; k < ntl; k += 32)
+                b.tiles[r + k] = make_uint4(e, l, lo + k * per_tile, min(per_tile, n_l - k * per_tile));
+            r += ntl;
         }
     }
-    if (tid == 0) b.jbase[b.E] = tot;
 }
 
 void launch_connect(const DevBatch &b, const DevParams &p, uint32_t layer_mask, cudaStream_t s,
@@ -1905,7 +1913,8 @@ __device__ __forceinline__ void walk_from(const DevBatch &b, const DevParams &p,
     while (d >= 0) {
         const uint32_t c = cells[d];
         const uint32_t nh = (uint32_t)d + 2u;
-        const uint2 hd = b.nbr_head[c];
+        // (a path at the hit cap ends here whatever c's edges: they are not read)
+        const uint2 hd = nh < p.max_hits ? b.nbr_head[c] : make_uint2(0u, 0u);
         const uint32_t ne = hd.y;
         if (next[d] == 0 && (nh >= p.max_hits || ne == 0)) {
             if (nh >= p.min_hits) {
