@@ -51,6 +51,9 @@ extern "C" {
 #define PXR_ETRUNC (-7)     /* caller buffer too small; the required count is returned */
 #define PXR_ENOTFOUND (-8)  /* unknown or already fetched ticket */
 #define PXR_EBUSY (-9)      /* the ticket's event is not finished yet */
+#define PXR_EBOUNDS (-10)   /* libpxr_checked.so only: a device-side bounds check found an index
+                               outside its array (the access was skipped; the event's results
+                               are not to be trusted).  The normal library never returns it */
 
 /* Arithmetic of the three cuts. */
 #define PXR_CUT_FP64 0      /* every cut quantity evaluated in FP64, in the fixed operation

@@ -1129,7 +1129,7 @@ __global__ void __launch_bounds__(256, 2) k_fit(DevBatch b, DevParams p)
 #pragma unroll
         for (int h = 0; h < kMaxHits; ++h) {
             const uint32_t pos = b.tup_hits[(size_t)t * kMaxHits + h];
-            if (h < n) {
+            if (h < n && PXR_IN(b, e, pos, b.N)) {
                 const float4 v = b.hs[pos];
                 const uint32_t meta = b.hmeta[pos];
                 X[h] = v.x; Y[h] = v.y; Z[h] = v.z;

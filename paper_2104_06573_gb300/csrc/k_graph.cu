@@ -1178,7 +1178,7 @@ __device__ __forceinline__ TileSpan tile_span(const uint32_t *lb, int nb, bool o
 // The out-cell B of j for the staged outer hit kt, and the triplet (i, j, k): kNone unless
 // (j, k) is a cell (rank in j's window, entry holding k) and the exact triplet cut passes.
 template <bool F64>
-__device__ __forceinline__ uint32_t tile_test(const DevBatch &b, const DevParams &p,
+__device__ __forceinline__ uint32_t tile_test(const DevBatch &b, const DevParams &p, uint32_t ev,
                                               const TileSpan &tk, uint32_t kt, uint32_t i,
                                               float4 hi, uint32_t j, float4 hj, const RZ32 &a,
                                               uint4 itj)
@@ -1187,6 +1187,7 @@ __device__ __forceinline__ uint32_t tile_test(const DevBatch &b, const DevParams
     const uint32_t rank = k >= itj.z ? k - itj.z : k + itj.w;
     if (rank >= itj.y) return kNone;
     const uint32_t B = itj.x + rank;
+    if (!PXR_IN(b, ev, B, b.C)) return kNone;
     const float4 hk = b.hs[k];
     if (!triplet_test<F64>(b, p, i, j, B, k, hi.x, hi.y, hj, hk, a)) return kNone;
     return b.cell_out[B] == k ? B : kNone;          // (j, k) failed the doublet cut: kNone
@@ -1194,13 +1195,14 @@ __device__ __forceinline__ uint32_t tile_test(const DevBatch &b, const DevParams
 
 // The in-cell (i, j) for the pair slot slot_i of i: i's entry of rank(j) in its window, kNone
 // when the doublet stage did not keep it.
-__device__ __forceinline__ uint32_t tile_incell(const DevBatch &b, uint32_t i, uint32_t slot_i,
-                                                uint32_t j)
+__device__ __forceinline__ uint32_t tile_incell(const DevBatch &b, uint32_t ev, uint32_t i,
+                                                uint32_t slot_i, uint32_t j)
 {
     const uint4 iti = b.item[(size_t)i * kMaxOut + slot_i];
     const uint32_t rank = j >= iti.z ? j - iti.z : j + iti.w;
     if (rank >= iti.y) return kNone;
     const uint32_t A = iti.x + rank;
+    if (!PXR_IN(b, ev, A, b.C)) return kNone;
     return b.cell_out[A] == j ? A : kNone;
 }
 
@@ -1220,11 +1222,11 @@ __device__ __noinline__ void tile_direct(const DevBatch &b, const DevParams &p, 
     for (uint32_t q = q0; q < q1; ++q) {
         const float fc = S.u.t.zo[q];
         if (fc >= lo && fc <= hi_ &&
-            tile_test<F64>(b, p, tk, S.u.t.sT[q], i, hi, j, hj, a, itj) != kNone)
+            tile_test<F64>(b, p, e, tk, S.u.t.sT[q], i, hi, j, hj, a, itj) != kNone)
             ++np;
     }
     if (np == 0) return;
-    const uint32_t A = tile_incell(b, i, slot_i, j);
+    const uint32_t A = tile_incell(b, e, i, slot_i, j);
     if (A == kNone) return;
     uint32_t have = 0, old = 0;
     if (more) {
@@ -1251,7 +1253,7 @@ __device__ __noinline__ void tile_direct(const DevBatch &b, const DevParams &p, 
     for (uint32_t q = q0; q < q1; ++q) {
         const float fc = S.u.t.zo[q];
         if (!(fc >= lo && fc <= hi_)) continue;
-        const uint32_t B = tile_test<F64>(b, p, tk, S.u.t.sT[q], i, hi, j, hj, a, itj);
+        const uint32_t B = tile_test<F64>(b, p, e, tk, S.u.t.sT[q], i, hi, j, hj, a, itj);
         if (B == kNone) continue;
         if (wr < nw) b.nbr[g0 + my0 + wr++] = B;
         mark_reached(b, e, B, j, front);
@@ -1614,7 +1616,9 @@ __global__ void __launch_bounds__(kTileW * 32, PXR_TILE_MINB) k_connect_tiles(De
                                 const uint32_t ri = jq >= iti.z ? jq - iti.z : jq + iti.w;
                                 if (ri < iti.y) {
                                     const uint32_t Bc = itq.x + rk, Ac = iti.x + ri;
-                                    const uint32_t ob = b.cell_out[Bc], oa = b.cell_out[Ac];
+                                    const bool in = PXR_IN(b, e, Bc, b.C) && PXR_IN(b, e, Ac, b.C);
+                                    const uint32_t ob = in ? b.cell_out[Bc] : kNone;
+                                    const uint32_t oa = in ? b.cell_out[Ac] : kNone;
                                     // (j, k) and (i, j) cells: the doublet stage kept both
                                     if (ob == k && oa == jq) {
                                         A = Ac;
@@ -1844,9 +1848,13 @@ __global__ void __launch_bounds__(256, PXR_CA_MINB) k_ca_front(DevBatch b, DevPa
             B = b.front_list[x];
             j = b.front_in[x];
             valid = B != kNone;                                    // slot of a cell reached twice
+            valid = valid && PXR_IN(b, e, B, b.C) && PXR_IN(b, e, j, b.N);
         }
         if (valid) {
             k = b.cell_out[B];
+            valid = PXR_IN(b, e, k, b.N);
+        }
+        if (valid) {
             Lk = b.hmeta[k] >> kLocalBits;
             valid = (layer_mask >> Lk) & 1u;
         }
@@ -1913,6 +1921,10 @@ __device__ __forceinline__ void walk_from(const DevBatch &b, const DevParams &p,
     while (d >= 0) {
         const uint32_t c = cells[d];
         const uint32_t nh = (uint32_t)d + 2u;
+        if (!PXR_IN(b, e, c, b.C)) {
+            --d;
+            continue;
+        }
         // (a path at the hit cap ends here whatever c's edges: they are not read)
         const uint2 hd = nh < p.max_hits ? b.nbr_head[c] : make_uint2(0u, 0u);
         const uint32_t ne = hd.y;
@@ -1940,6 +1952,10 @@ __device__ __forceinline__ void walk_from(const DevBatch &b, const DevParams &p,
             continue;
         }
         if (next[d] < ne) {
+            if (!PXR_IN(b, e, (uint64_t)hd.x + next[d], b.G)) {
+                --d;
+                continue;
+            }
             const uint32_t nxt = b.nbr[hd.x + next[d]];
             ++next[d];
             ++d;
@@ -2021,7 +2037,7 @@ __global__ void __launch_bounds__(256) k_select(DevBatch b, DevParams p, uint32_
         const uint32_t nt = min(b.cnt[C_TUPLES * b.E + e], b.tup_off[e + 1] - t0);
         if (t - t0 >= nt) continue;
         bool keep = true;
-        if (p.drop_suffixes && b.tup_state[t] == 2) {
+        if (p.drop_suffixes && b.tup_state[t] == 2 && PXR_IN(b, e, b.tup_first[t], b.C)) {
             const uint32_t md = b.mindepth[b.tup_first[t]];
             if (md != kNone && md + b.tup_n[t] <= p.max_hits) keep = false;
         }
@@ -2083,9 +2099,11 @@ void launch_out_scan(const DevBatch &b, cudaStream_t s)
 }
 
 // Caller index of slot q of ntuplet t, kNone past its hits (the padding of the canonical order).
-__device__ __forceinline__ uint32_t tup_caller(const DevBatch &b, uint32_t t, int q)
+__device__ __forceinline__ uint32_t tup_caller(const DevBatch &b, uint32_t e, uint32_t t, int q)
 {
-    return q < b.tup_n[t] ? b.hmeta[b.tup_hits[(size_t)t * kMaxHits + q]] & kLocalMask : kNone;
+    if (q >= b.tup_n[t]) return kNone;
+    const uint32_t h = b.tup_hits[(size_t)t * kMaxHits + q];
+    return PXR_IN(b, e, h, b.N) ? b.hmeta[h] & kLocalMask : kNone;
 }
 
 constexpr uint32_t kCanonSmem = 32768;     // events with more hits count in global memory
@@ -2110,12 +2128,12 @@ __global__ void __launch_bounds__(1024) k_canon(DevBatch b)
         uint32_t *tmp = b.tup_tmp + t0;
         for (uint32_t c = tid; c < nh; c += nt) cnt[c] = 0;
         __syncthreads();
-        for (uint32_t k = tid; k < n; k += nt) atomicAdd(&cnt[tup_caller(b, b.tup_list[t0 + k], 0)], 1u);
+        for (uint32_t k = tid; k < n; k += nt) atomicAdd(&cnt[tup_caller(b, e, b.tup_list[t0 + k], 0)], 1u);
         __syncthreads();
         block_exclusive_scan(cnt, nh, s_warp);
         for (uint32_t k = tid; k < n; k += nt) {
             const uint32_t t = b.tup_list[t0 + k];
-            tmp[atomicAdd(&cnt[tup_caller(b, t, 0)], 1u)] = t;
+            tmp[atomicAdd(&cnt[tup_caller(b, e, t, 0)], 1u)] = t;
         }
         __syncthreads();
         // cnt[c] is now the end of bucket c
@@ -2128,7 +2146,7 @@ __global__ void __launch_bounds__(1024) k_canon(DevBatch b)
                     const uint32_t u = tmp[y - 1];
                     int cmp = 0;
                     for (int q = 1; q < kMaxHits && cmp == 0; ++q) {
-                        const uint32_t a = tup_caller(b, u, q), v = tup_caller(b, t, q);
+                        const uint32_t a = tup_caller(b, e, u, q), v = tup_caller(b, e, t, q);
                         cmp = a < v ? -1 : (a > v ? 1 : 0);
                     }
                     if (cmp <= 0) break;

@@ -137,6 +137,7 @@ extern "C" int pxr_doublets_noalloc(const float *x, const float *y, const float 
     std::memset(&b, 0, sizeof b);
     b.E = 1;
     b.N = n_hits;
+    b.C = cap;
     b.x = x;
     b.y = y;
     b.z = z;

@@ -36,7 +36,10 @@ constexpr int kReportedCounters = 5;
 constexpr uint8_t kQGood = 1u, kQKept = 2u;
 
 // Per-event flags (C_FLAGS).
-enum Flag : uint32_t { F_CELLS = 1u, F_EDGES = 2u, F_TUPLES = 4u, F_LAYER = 8u, F_VERTS = 16u };
+enum Flag : uint32_t {
+    F_CELLS = 1u, F_EDGES = 2u, F_TUPLES = 4u, F_LAYER = 8u, F_VERTS = 16u,
+    F_BOUNDS = 32u   // (checked build) an index outside its array; the access was skipped
+};
 
 enum CutMode : uint32_t { CUT_FP64 = 0, CUT_FP32 = 1 };
 enum FitMode : uint32_t { FIT_FP64 = 0, FIT_MIXED = 1, FIT_FP32 = 2, FIT_RIEMANN = 3, FIT_SPLIT = 4 };
@@ -86,6 +89,8 @@ struct DevParams {
 struct DevBatch {
     uint32_t E;                         // events
     uint32_t N;                         // hits of all events
+    uint32_t C, G, T;                   // cell entries, edge entries and ntuple slots of the
+                                        //   batch (the extents the checked build tests against)
     // inputs (device, caller order, events back to back)
     const float *x, *y, *z;
     const uint16_t *layer;
@@ -168,6 +173,23 @@ struct DevBatch {
     unsigned long long *best;           // [N] shared-hit cleaning: best rank key per hit (caller
                                         //   order, events back to back)
 };
+
+// Bounds checks of the checked build (compiled with PXR_CHECKED): an index that a kernel reads
+// from another kernel's output, or computes from it, is compared with the extent of the array it
+// addresses before the access; outside it, the event's F_BOUNDS flag is set and the access
+// skipped (no trap: the context stays usable and the host reports PXR_EBOUNDS).  The normal
+// build compiles every check to true.
+#ifdef PXR_CHECKED
+__device__ __forceinline__ bool bound_ok(const DevBatch &b, uint32_t e, uint64_t i, uint64_t n)
+{
+    if (i < n) return true;
+    atomicOr(&b.cnt[3 * b.E + e], 32u);         // C_FLAGS, F_BOUNDS
+    return false;
+}
+#define PXR_IN(b, e, i, n) ::pxr::bound_ok((b), (e), (uint64_t)(i), (uint64_t)(n))
+#else
+#define PXR_IN(b, e, i, n) true
+#endif
 
 // Event of hit g: the chunk table gives the event of the chunk's first hit.
 __device__ __forceinline__ uint32_t hit_event(const DevBatch &b, uint32_t g)

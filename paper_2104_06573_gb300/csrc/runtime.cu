@@ -568,6 +568,9 @@ static void plan_bind(pxr_plan *P)
     DevBatch &b = P->db;
     b.E = P->E;
     b.N = (uint32_t)P->N;
+    b.C = (uint32_t)P->C;
+    b.G = (uint32_t)P->G;
+    b.T = (uint32_t)P->T;
     if (P->own_inputs) {
         b.x = (const float *)(r + o.x);
         b.y = (const float *)(r + o.y);
@@ -1039,7 +1042,13 @@ static int emit_tracks(const TrackSrc &h, int32_t status, pxr_tracks *out)
     return PXR_OK;
 }
 
-static int32_t flags_status(uint32_t f) { return (f & (F_CELLS | F_EDGES | F_TUPLES | F_VERTS)) ? PXR_EOVERFLOW : (f & F_LAYER) ? PXR_EINVAL : PXR_OK; }
+static int32_t flags_status(uint32_t f)
+{
+    if (f & F_BOUNDS) return PXR_EBOUNDS;
+    return (f & (F_CELLS | F_EDGES | F_TUPLES | F_VERTS)) ? PXR_EOVERFLOW
+           : (f & F_LAYER)                                 ? PXR_EINVAL
+                                                           : PXR_OK;
+}
 
 template <typename T>
 static int d2h(std::vector<T> &v, const void *src, size_t n)

@@ -1,6 +1,8 @@
 """ctypes binding of the pxr C ABI (include/pxr.h): argument marshalling only.
 
-Every step of the reconstruction runs in the CUDA library paper_2104_06573_gb300/_build/libpxr.so.
+Every step of the reconstruction runs in the CUDA library paper_2104_06573_gb300/_build/libpxr.so
+(with PXR_CHECKED=1 in the environment: libpxr_checked.so, the same library with device-side
+bounds checks that report PXR_EBOUNDS instead of touching memory outside an array).
 There is no CPU fallback: if the library is missing or no GB300 is present, the calls raise.
 Device pointers may be passed as integers or as torch tensors (their data_ptr() is used).
 """
@@ -14,12 +16,13 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libpxr.so")
+LIB_PATH = os.path.join(HERE, "_build", "libpxr_checked.so" if os.environ.get("PXR_CHECKED") == "1"
+                        else "libpxr.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "pxr.h")
 
 MAX_LAYERS, MAX_PAIRS, MAX_HITS = 16, 32, 6
-OK, EINVAL, EAGAIN, ENOMEM, EOVERFLOW, ETIMEDOUT, ECUDA, ETRUNC, ENOTFOUND, EBUSY = (
-    0, -1, -2, -3, -4, -5, -6, -7, -8, -9)
+OK, EINVAL, EAGAIN, ENOMEM, EOVERFLOW, ETIMEDOUT, ECUDA, ETRUNC, ENOTFOUND, EBUSY, EBOUNDS = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10)
 CUT_FP64, CUT_FP32 = 0, 1
 FIT_FP64, FIT_MIXED, FIT_FP32, FIT_RIEMANN, FIT_SPLIT = 0, 1, 2, 3, 4
 PRESET_BARREL, PRESET_PHASE1 = 0, 1
