@@ -760,6 +760,62 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// ---- double-float arithmetic (a value as the unevaluated sum hi + lo of two floats) ----
+// The error-free transformations of Knuth (sum) and Dekker (product, here with a fused
+// multiply-add) give the rounding error of one float operation as another float; carrying it
+// gives about 48 significant bits at float speed, where GB300's FP64 pipe runs at 1/64 of its
+// FP32 rate.  Every operation is written with explicit round-to-nearest intrinsics, so that no
+// step is contracted or reassociated.  Renormalised results (|lo| <= half an ulp of hi).
+struct df64 {
+    float hi, lo;
+    __device__ df64() : hi(0.f), lo(0.f) {}
+    __device__ df64(float h, float l) : hi(h), lo(l) {}
+    __device__ df64(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+    __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ df64 df_fast(float s, float e)        // |s| >= |e|
+{
+    const float t = __fadd_rn(s, e);
+    return df64(t, __fsub_rn(e, __fsub_rn(t, s)));
+}
+__device__ __forceinline__ df64 operator+(const df64 &a, const df64 &b)
+{
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    float t, f;
+    two_sum(a.lo, b.lo, t, f);
+    e = __fadd_rn(e, t);
+    const df64 u = df_fast(s, e);
+    return df_fast(u.hi, __fadd_rn(u.lo, f));
+}
+__device__ __forceinline__ df64 operator-(const df64 &a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(const df64 &a, const df64 &b) { return a + (-b); }
+__device__ __forceinline__ df64 operator*(const df64 &a, const df64 &b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_fast(p, e);
+}
+__device__ __forceinline__ df64 &operator+=(df64 &a, const df64 &b) { return a = a + b; }
+__device__ __forceinline__ df64 &operator-=(df64 &a, const df64 &b) { return a = a - b; }
+__device__ __forceinline__ bool operator>(const df64 &a, const df64 &b)
+{
+    return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
+}
+__device__ __forceinline__ bool isfinite(const df64 &a) { return ::isfinite(a.hi); }
+// 1 / sqrt(a): the float estimate, then one Newton step y + y (1 - a y^2) / 2 in double-float
+// (the estimate's ~23 bits doubled)
+template <>
+__device__ __forceinline__ df64 rsqrt_t<df64>(df64 a)
+{
+    const df64 y(rsqrtf(a.hi), 0.f);
+    const df64 r = df64(1.0) - a * (y * y);
+    return y + y * (r * df64(0.5f, 0.f));
+}
+
 // The refit of the tracks the float front end does not take: the same fit in FP64 (out of
 // line; rare, so its cost does not matter, and a nearly straight fit from a bent reference
 // amplifies any float rounding, transcendentals included).
@@ -855,17 +911,17 @@ __device__ __noinline__ void fit_split_n(const float *X, const float *Y, const f
 #pragma unroll
     for (int i = 0; i < N; ++i) any_disk |= p.is_disk[L[i]] != 0;
     const float ib2 = inv_th2(sec);
-    const float wz = float(1.0 / (p.sigma_z * p.sigma_z));
+    const float wz = float(p.w_z);
     float id2 = ib2, wdisk = wz;
     if (any_disk) {
         const float icot = 1.f / fabsf(cot0);
         id2 = inv_th2(sec * icot);
-        const float iz = float(1.0 / p.sigma_z) * icot;    // disk: sigma_r = sigma_z |cot|
+        const float iz = float(p.i_sz) * icot;             // disk: sigma_r = sigma_z |cot|
         wdisk = iz * iz;
     }
     // 5. rows of the normal equations (float values), matrices and solves in double
     double h[N], g[N], y64[N], z64[N], wT[N], wL[N], wkT[N], wkL[N];
-    const double wrphi = 1.0 / (p.sigma_rphi * p.sigma_rphi);
+    const double wrphi = p.w_rphi;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         const float hf = i + 1 < N ? sa[i + 1] - sa[i] : 1.f;
@@ -889,10 +945,25 @@ __device__ __noinline__ void fit_split_n(const float *X, const float *Y, const f
         // every hit on a barrel layer: one measurement and one kink weight per view, the
         // geometry shared (the kink weights over the measurement weights; 1 / wz is sigma_z^2
         // to float rounding, far below the kink weights' own float rounding)
-        const double lamT = wkT[1] * (p.sigma_rphi * p.sigma_rphi);
-        const double lamL = wkL[1] * (p.sigma_z * p.sigma_z);
-        ok = ok && broken_line_pair<N, double>(h, y64, z64, wrphi, wL[0], lamT, lamL, xT, xL,
-                                               delta, chi2T);
+        const double lamT = wkT[1] * p.s2_rphi;
+        const double lamL = wkL[1] * p.s2_z;
+        // (the solve in double-float arithmetic)
+        df64 hd[N], yd[N], zd[N], xTd[N], xLd[N], deltad, chi2d;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            hd[i] = df64(h[i]);
+            yd[i] = df64(y64[i]);
+            zd[i] = df64(z64[i]);
+        }
+        ok = ok && broken_line_pair<N, df64>(hd, yd, zd, df64(wrphi), df64(wL[0]), df64(lamT),
+                                             df64(lamL), xTd, xLd, deltad, chi2d);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            xT[i] = double(xTd[i]);
+            xL[i] = double(xLd[i]);
+        }
+        delta = double(deltad);
+        chi2T = double(chi2d);
     } else {
         ok = ok && broken_line_n<N, true, double, COV>(h, y64, wT, wkT, xT, delta, chi2T, cvT) &&
              broken_line_n<N, false, double, COV>(h, z64, wL, wkL, xL, dummy, chi2L, cvL);

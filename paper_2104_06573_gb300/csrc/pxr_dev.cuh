@@ -79,6 +79,8 @@ struct DevParams {
     double cw;                          // cos(w) as given by the caller
     double theta, dca;
     double bfield, sigma_rphi, sigma_z, x_over_x0;
+    double w_rphi, w_z, s2_rphi, s2_z, i_sz;   // 1/sigma_rphi^2, 1/sigma_z^2, sigma_rphi^2,
+                                               //   sigma_z^2, 1/sigma_z (host-computed)
     double pt_min, chi2_max;            // track selection (0: no cut)
     uint32_t clean;                     // shared-hit cleaning
     uint32_t cov;                       // fit covariance wanted

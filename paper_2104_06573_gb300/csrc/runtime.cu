@@ -182,6 +182,11 @@ static int check_params(const pxr_params *p, DevParams *d)
     d->bfield = p->bfield;
     d->sigma_rphi = p->sigma_rphi;
     d->sigma_z = p->sigma_z;
+    d->s2_rphi = p->sigma_rphi * p->sigma_rphi;
+    d->s2_z = p->sigma_z * p->sigma_z;
+    d->w_rphi = 1.0 / d->s2_rphi;
+    d->w_z = 1.0 / d->s2_z;
+    d->i_sz = 1.0 / p->sigma_z;
     d->x_over_x0 = p->x_over_x0;
     d->pt_min = p->pt_min;
     d->chi2_max = p->chi2_max;
