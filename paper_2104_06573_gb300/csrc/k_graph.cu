@@ -1992,17 +1992,56 @@ __global__ void __launch_bounds__(256) k_ntuplets(DevBatch b, DevParams p)
     }
 }
 
-// Walk from the root cells that have out-edges (listed per event by the CA stage): one thread
-// per listed cell.  Enough when paths need at least 3 hits.
-__global__ void __launch_bounds__(256) k_walk_roots(DevBatch b, DevParams p, uint32_t total)
+// The chunks of listed root cells (kChunk cells of one event each): per-event prefix in jbase
+// (free once the CA stage has ended; jbase[E] = all chunks), so that the walk visits the listed
+// cells only and not the whole edge capacity.  One CTA; each thread takes a run of consecutive
+// events.
+__global__ void __launch_bounds__(1024) k_root_chunks(DevBatch b)
 {
-    const uint32_t n_chunks = total / kChunk;
-    for (uint32_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
-        const uint32_t x = ch * kChunk + threadIdx.x;
-        const uint32_t e = b.edge_chunk[ch];
+    __shared__ uint32_t s_w[32];
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t per = (b.E + nt - 1) / nt;
+    const uint32_t e0 = min(b.E, tid * per), e1 = min(b.E, e0 + per);
+    auto count = [&](uint32_t e) {
+        const uint32_t n = min(b.cnt[C_ROOTS * b.E + e], b.edge_off[e + 1] - b.edge_off[e]);
+        return (n + kChunk - 1) / kChunk;
+    };
+    uint32_t mine = 0;
+    for (uint32_t e = e0; e < e1; ++e) mine += count(e);
+    const uint32_t lane = tid & 31u, wid = tid >> 5;
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= (uint32_t)o) incl += t;
+    }
+    if (lane == 31) s_w[wid] = incl;
+    __syncthreads();
+    uint32_t run = 0, tot = 0;
+    for (uint32_t w = 0; w < nt / 32; ++w) {
+        if (w < wid) run += s_w[w];
+        tot += s_w[w];
+    }
+    run += incl - mine;
+    for (uint32_t e = e0; e < e1; ++e) {
+        b.jbase[e] = run;
+        run += count(e);
+    }
+    if (tid == 0) b.jbase[b.E] = tot;
+}
+
+// Walk from the root cells that have out-edges (listed per event by the CA stage): one CTA per
+// chunk of an event's listed cells (k_root_chunks), one thread per cell.  Enough when paths need
+// at least 3 hits.
+__global__ void __launch_bounds__(256) k_walk_roots(DevBatch b, DevParams p)
+{
+    const uint32_t total = b.jbase[b.E];
+    for (uint32_t v = blockIdx.x; v < total; v += gridDim.x) {
+        const uint32_t e = find_event(b.jbase, b.E, v);
         const uint32_t x0 = b.edge_off[e];
         const uint32_t n = min(b.cnt[C_ROOTS * b.E + e], b.edge_off[e + 1] - x0);
-        if (x - x0 < n) walk_from(b, p, e, b.root_list[x], b.root_in[x]);
+        const uint32_t x = (v - b.jbase[e]) * kChunk + threadIdx.x;
+        if (x < n) walk_from(b, p, e, b.root_list[x0 + x], b.root_in[x0 + x]);
     }
 }
 
@@ -2013,7 +2052,9 @@ void launch_ntuplets(const DevBatch &b, const DevParams &p, uint32_t edge_total,
         const uint32_t chunks = edge_total / kChunk;
         const uint32_t cap = (uint32_t)sms * p.grid_per_sm[3];
         if (chunks == 0) return;
-        k_walk_roots<<<chunks < cap ? chunks : cap, kChunk, 0, s>>>(b, p, edge_total);
+        // (the edge capacity bounds the listed root cells, hence their chunks)
+        k_root_chunks<<<1, 1024, 0, s>>>(b);
+        k_walk_roots<<<chunks < cap ? chunks : cap, kChunk, 0, s>>>(b, p);
         return;
     }
     uint64_t blocks = ((uint64_t)b.N + 7) / 8;
