@@ -1992,18 +1992,21 @@ __global__ void __launch_bounds__(256) k_ntuplets(DevBatch b, DevParams p)
     }
 }
 
-// The chunks of listed root cells (kChunk cells of one event each): per-event prefix in jbase
-// (free once the CA stage has ended; jbase[E] = all chunks), so that the walk visits the listed
-// cells only and not the whole edge capacity.  One CTA; each thread takes a run of consecutive
-// events.
-__global__ void __launch_bounds__(1024) k_root_chunks(DevBatch b)
+// The chunks (kChunk entries of one event each) of the filled part of a per-event region: the
+// region of event e starts at off[e], counter `which` says how much of it was filled.  Per-event
+// prefix in jbase (free once the CA stage has ended; jbase[E] = all chunks), so that the walk
+// visits the listed root cells (C_ROOTS of the edge regions) and the selection the emitted
+// ntuplets (C_TUPLES of the ntuplet regions) without a pass over the whole capacity.  One CTA;
+// each thread takes a run of consecutive events.
+__global__ void __launch_bounds__(1024) k_chunks(DevBatch b, uint32_t which,
+                                                 const uint32_t *__restrict__ off)
 {
     __shared__ uint32_t s_w[32];
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
     const uint32_t per = (b.E + nt - 1) / nt;
     const uint32_t e0 = min(b.E, tid * per), e1 = min(b.E, e0 + per);
     auto count = [&](uint32_t e) {
-        const uint32_t n = min(b.cnt[C_ROOTS * b.E + e], b.edge_off[e + 1] - b.edge_off[e]);
+        const uint32_t n = min(b.cnt[which * b.E + e], off[e + 1] - off[e]);
         return (n + kChunk - 1) / kChunk;
     };
     uint32_t mine = 0;
@@ -2031,7 +2034,7 @@ __global__ void __launch_bounds__(1024) k_root_chunks(DevBatch b)
 }
 
 // Walk from the root cells that have out-edges (listed per event by the CA stage): one CTA per
-// chunk of an event's listed cells (k_root_chunks), one thread per cell.  Enough when paths need
+// chunk of an event's listed cells (k_chunks), one thread per cell.  Enough when paths need
 // at least 3 hits.
 __global__ void __launch_bounds__(256) k_walk_roots(DevBatch b, DevParams p)
 {
@@ -2053,7 +2056,7 @@ void launch_ntuplets(const DevBatch &b, const DevParams &p, uint32_t edge_total,
         const uint32_t cap = (uint32_t)sms * p.grid_per_sm[3];
         if (chunks == 0) return;
         // (the edge capacity bounds the listed root cells, hence their chunks)
-        k_root_chunks<<<1, 1024, 0, s>>>(b);
+        k_chunks<<<1, 1024, 0, s>>>(b, C_ROOTS, b.edge_off);
         k_walk_roots<<<chunks < cap ? chunks : cap, kChunk, 0, s>>>(b, p);
         return;
     }
@@ -2068,15 +2071,16 @@ void launch_ntuplets(const DevBatch &b, const DevParams &p, uint32_t edge_total,
 // Selection: a path that ended without an out-edge is a strict suffix of another emitted path
 // exactly when a root path of m hits enters its first cell and m + (its hits) <= max_hits.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_select(DevBatch b, DevParams p, uint32_t total)
+__global__ void __launch_bounds__(256) k_select(DevBatch b, DevParams p)
 {
-    const uint32_t n_chunks = total / kChunk;
-    for (uint32_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
-        const uint32_t t = ch * kChunk + threadIdx.x;
-        const uint32_t e = b.tup_chunk[ch];
+    const uint32_t total = b.jbase[b.E];      // chunks of emitted ntuplets (k_chunks)
+    for (uint32_t v = blockIdx.x; v < total; v += gridDim.x) {
+        const uint32_t e = find_event(b.jbase, b.E, v);
         const uint32_t t0 = b.tup_off[e];
         const uint32_t nt = min(b.cnt[C_TUPLES * b.E + e], b.tup_off[e + 1] - t0);
-        if (t - t0 >= nt) continue;
+        const uint32_t x = (v - b.jbase[e]) * kChunk + threadIdx.x;
+        if (x >= nt) continue;
+        const uint32_t t = t0 + x;
         bool keep = true;
         if (p.drop_suffixes && b.tup_state[t] == 2 && PXR_IN(b, e, b.tup_first[t], b.C)) {
             const uint32_t md = b.mindepth[b.tup_first[t]];
@@ -2090,11 +2094,12 @@ __global__ void __launch_bounds__(256) k_select(DevBatch b, DevParams p, uint32_
 
 void launch_select(const DevBatch &b, const DevParams &p, uint32_t total, cudaStream_t s, int sms)
 {
-    uint64_t blocks = total / kChunk;
+    uint64_t blocks = total / kChunk;              // (bounds the chunks of emitted ntuplets)
     uint64_t cap = (uint64_t)sms * 2 * p.grid_per_sm[4];
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
-    k_select<<<(unsigned)blocks, 256, 0, s>>>(b, p, total);
+    k_chunks<<<1, 1024, 0, s>>>(b, C_TUPLES, b.tup_off);
+    k_select<<<(unsigned)blocks, 256, 0, s>>>(b, p);
 }
 
 // Exclusive prefix of the per-event output counts (one CTA).

@@ -756,9 +756,9 @@ static int plan_enqueue(pxr_plan *P, cudaStream_t s, bool capturing = false,
 
 static int plan_launches(const pxr_plan *P)
 {
-    // sort, doublets, walk (with its root-chunk prefix when paths need 3 hits), select, scan,
-    // order, fit, keep, vertices
-    int n = 7 + (P->dp.min_hits > 2 ? 1 : 0) + (P->dp.clean ? 1 : 0) + (P->dp.vtx ? 1 : 0);
+    // sort, doublets, walk (with its root-chunk prefix when paths need 3 hits), select (with
+    // its ntuplet-chunk prefix), scan, order, fit, keep, vertices
+    int n = 8 + (P->dp.min_hits > 2 ? 1 : 0) + (P->dp.clean ? 1 : 0) + (P->dp.vtx ? 1 : 0);
     for (uint32_t lv = 1; lv <= P->dp.n_levels; ++lv)
         n += (P->dp.level_dense[lv] ? 2 : 0) + (P->dp.level_sparse[lv] ? 1 : 0);
     return n;
