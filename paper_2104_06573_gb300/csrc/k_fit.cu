@@ -14,9 +14,10 @@
 //  5. fitted circle at hit 0 and its point of closest approach to the z axis.
 // Precision modes: FP64 (all steps double), MIXED (arithmetic double, transcendentals float),
 // FP32 (all float), SPLIT (steps 1-3 in float, on a chord frame whose differences are
-// error-free; the normal matrices, their Cholesky factorisation and the conversion in double;
-// tracks where the float reference circle would limit the accuracy are refitted in FP64).  The hit count is a template parameter, so
-// every array lives in registers.
+// error-free; the normal matrices and their Cholesky factorisation in double-float arithmetic
+// when every hit is on a barrel layer, in double otherwise; the conversion in double; tracks
+// where the float reference circle would limit the accuracy are refitted in FP64).  The hit
+// count is a template parameter, so every array lives in registers.
 #include "pxr_dev.cuh"
 
 namespace pxr {
