@@ -554,10 +554,15 @@ def extras(args, ctx, pxr, synth, P, params, evs, off, x, y, z, layer, dev, stre
         # copies and inputs) before step k is waited for and fetched, so each step's host work
         # overlaps the device work of its neighbour; every step's copies are inside the timed
         # region (total time of K steps)
+        # (a poll reports each finished ticket once: completions of the step in flight that a
+        # wait for the previous step sees are kept for the next wait)
+        finished = set()
+
         def wait_fetch(tickets):
-            want, done = set(tickets), set()
-            while not want <= done:
-                done |= set(sctx.pxr_poll(timeout_us=100000))
+            want = set(tickets)
+            while not want <= finished:
+                finished.update(sctx.pxr_poll(timeout_us=100000))
+            finished.difference_update(want)
             return sctx.pxr_fetch_events(tickets, out=res["out"])
 
         K = 10

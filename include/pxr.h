@@ -205,7 +205,8 @@ typedef struct pxr_config {
                                    creates its own streams */
     uint32_t max_batch_events;  /* dynamic batching cap (events per launch); 0 = 256 */
     uint32_t max_batch_hits;    /* dynamic batching cap (hits per launch); 0 = 4M */
-    uint32_t max_inflight;      /* batches on the device at once, 1 or 2; 0 = 2 */
+    uint32_t max_inflight;      /* batches on the device at once, 1 to 4 (each on its own
+                                   stream); 0 = 2 */
     uint32_t keep_debug;        /* keep cells/edges/ntuplets of served events for
                                    pxr_fetch_debug (costs memory until the fetch) */
 } pxr_config;

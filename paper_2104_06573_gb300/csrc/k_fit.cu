@@ -321,6 +321,19 @@ __device__ __forceinline__ bool bl_eliminate(T (&A)[K][K], T (&B)[K][G], T (&Gm)
     return true;
 }
 
+// Add t to the running sum v, or start the sum with it (the unrolled loops below decide at
+// compile time which terms exist, so no sum starts from a literal zero).
+template <typename T>
+__device__ __forceinline__ void acc(T &v, bool &started, const T &t)
+{
+    if (started) {
+        v += t;
+    } else {
+        v = t;
+        started = true;
+    }
+}
+
 // Both views of a track whose hits share one measurement weight per view (wT, wL) and one kink
 // weight per view (every hit on a barrel layer): the minimisers of broken_line_n for the two
 // views.  Divided by its measurement weight, a view's normal matrix is J^T J with
@@ -335,42 +348,58 @@ __device__ __forceinline__ bool broken_line_pair(const T (&h)[N], const T (&mT)[
                                                  T (&xT)[N], T (&xL)[N], T &delta, T &chi2)
 {
     constexpr int K = N - 2;                 // kinks
+    // J's structural zeros and ones are left out of every product and sum: d x_i / d kink j is
+    // zero up to hit j + 1, d x_i / d slope (S_i = s_i - s_0) is zero at hit 0, d x_i / d delta
+    // (jd_i) at hits 0 and 1, d x_i / d x_0 is one.  (A product with a literal zero cannot be
+    // folded away in IEEE arithmetic; the results are the same bit for bit.)
     T S[N], jd[N];                           // s_i - s_0; d x_i / d delta
     S[0] = T(0);
+    S[1] = h[0];
 #pragma unroll
-    for (int i = 1; i < N; ++i) S[i] = S[i - 1] + h[i - 1];
+    for (int i = 2; i < N; ++i) S[i] = S[i - 1] + h[i - 1];
+    jd[0] = jd[1] = T(0);
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        T a = T(0);
+    for (int i = 2; i < N; ++i) {
+        T a = -(T(0.5) * (h[0] + h[1]) * (S[i] - S[1]));
 #pragma unroll
-        for (int j = 1; j < i && j + 1 < N; ++j) a -= T(0.5) * (h[j - 1] + h[j]) * (S[i] - S[j]);
+        for (int j = 2; j < i && j + 1 < N; ++j) a -= T(0.5) * (h[j - 1] + h[j]) * (S[i] - S[j]);
         jd[i] = a;
     }
-    auto jk = [&](int i, int j) { return i > j ? S[i] - S[j] : T(0); };   // j = 1..K
-    auto jg = [&](int i, int c) { return c == 0 ? T(1) : c == 1 ? S[i] : jd[i]; };
+    // D[a][i] = d x_i / d kink (a + 1) for i > a + 1
+    T D[K][N];
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+        for (int i = a + 2; i < N; ++i) D[a][i] = S[i] - S[a + 1];
+    auto gnz = [](int i, int c) { return c == 0 || i >= c; };             // (x_0, slope, delta)
+    auto gv = [&](int i, int c) { return c == 1 ? S[i] : jd[i]; };        // (c > 0)
     // the shared geometry J^T J: kink block, border, globals (x_0, slope, delta)
     T A[K][K], B[K][3], Gm[3][3], rbT[K], rbL[K], rgT[3], rgL[2];
 #pragma unroll
     for (int a = 0; a < K; ++a) {
 #pragma unroll
         for (int b = 0; b <= a; ++b) {
-            T v = T(0);
+            T v;
+            bool st = false;
 #pragma unroll
-            for (int i = 0; i < N; ++i) v += jk(i, a + 1) * jk(i, b + 1);
+            for (int i = a + 2; i < N; ++i) acc(v, st, D[a][i] * D[b][i]);
             A[a][b] = v;
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            T v = T(0);
+            T v;
+            bool st = false;
 #pragma unroll
-            for (int i = 0; i < N; ++i) v += jk(i, a + 1) * jg(i, c);
+            for (int i = a + 2; i < N; ++i)
+                if (gnz(i, c)) acc(v, st, c == 0 ? D[a][i] : D[a][i] * gv(i, c));
             B[a][c] = v;
         }
-        T vT = T(0), vL = T(0);
+        T vT, vL;
+        bool st = false, sl = false;
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-            vT += jk(i, a + 1) * mT[i];
-            vL += jk(i, a + 1) * mL[i];
+        for (int i = a + 2; i < N; ++i) {
+            acc(vT, st, D[a][i] * mT[i]);
+            acc(vL, sl, D[a][i] * mL[i]);
         }
         rbT[a] = vT;
         rbL[a] = vL;
@@ -379,16 +408,24 @@ __device__ __forceinline__ bool broken_line_pair(const T (&h)[N], const T (&mT)[
     for (int c = 0; c < 3; ++c) {
 #pragma unroll
         for (int d = 0; d <= c; ++d) {
-            T v = T(0);
+            T v;
+            bool st = false;
 #pragma unroll
-            for (int i = 0; i < N; ++i) v += jg(i, c) * jg(i, d);
+            for (int i = 0; i < N; ++i) {
+                if (!gnz(i, c) || !gnz(i, d)) continue;
+                if (c == 0) acc(v, st, T(1));
+                else if (d == 0) acc(v, st, gv(i, c));
+                else acc(v, st, gv(i, c) * gv(i, d));
+            }
             Gm[c][d] = v;
         }
-        T vT = T(0), vL = T(0);
+        T vT, vL;
+        bool st = false, sl = false;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            vT += jg(i, c) * mT[i];
-            vL += jg(i, c) * mL[i];
+            if (!gnz(i, c)) continue;
+            acc(vT, st, c == 0 ? mT[i] : gv(i, c) * mT[i]);
+            if (c < 2) acc(vL, sl, c == 0 ? mL[i] : gv(i, c) * mL[i]);
         }
         rgT[c] = vT;
         if (c < 2) rgL[c] = vL;
@@ -421,12 +458,17 @@ __device__ __forceinline__ bool broken_line_pair(const T (&h)[N], const T (&mT)[
     T c2T = T(0), c2L = T(0);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        T vT = tgT[0] + S[i] * tgT[1] + jd[i] * tgT[2];
-        T vL = tgL[0] + S[i] * tgL[1];
+        T vT = tgT[0], vL = tgL[0];
+        if (i >= 1) {
+            vT += S[i] * tgT[1];
+            vL += S[i] * tgL[1];
+        }
+        if (i >= 2) vT += jd[i] * tgT[2];
 #pragma unroll
         for (int a = 0; a < K; ++a) {
-            vT += jk(i, a + 1) * rbT[a];
-            vL += jk(i, a + 1) * rbL[a];
+            if (i < a + 2) continue;
+            vT += D[a][i] * rbT[a];
+            vL += D[a][i] * rbL[a];
         }
         xT[i] = vT;
         xL[i] = vL;

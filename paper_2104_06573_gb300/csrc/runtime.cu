@@ -518,12 +518,14 @@ static std::shared_ptr<PinnedBlock> pinned_block(PinnedPool &pool, size_t bytes)
 
 struct Batch;
 
+constexpr int kMaxSlots = 4;           // batches in flight at most (one stream and staging each)
+
 struct pxr_ctx {
     pxr_config cfg{};
     int sms = 152;
     cudaStream_t stream = nullptr;      // default stream of the context
     bool own_stream = false;
-    cudaStream_t slot_stream[2] = {nullptr, nullptr};
+    cudaStream_t slot_stream[kMaxSlots] = {};
     bool own_arena = false;
     Arena arena;
     std::mutex api_mu;                  // serialises plan API calls
@@ -541,7 +543,7 @@ struct pxr_ctx {
     std::deque<uint64_t> done_q;
     std::unordered_map<uint64_t, std::shared_ptr<struct Ticket>> tickets;
     std::vector<std::shared_ptr<Batch>> inflight;
-    std::unique_ptr<struct SlotBuffers> slot_buf[2];
+    std::unique_ptr<struct SlotBuffers> slot_buf[kMaxSlots];
     std::string sched_error;
 };
 
@@ -1550,9 +1552,12 @@ static void scheduler(pxr_ctx *ctx)
                 items.push_back(t);
                 ctx->pending.pop_front();
             }
+            // the lowest slot (stream and pinned staging buffers) no batch in flight holds
             int slot = 0;
-            for (auto &b : ctx->inflight)
-                if (b->slot == 0) slot = 1;
+            for (bool taken = true; taken; slot += taken) {
+                taken = false;
+                for (auto &b : ctx->inflight) taken |= b->slot == slot;
+            }
             std::shared_ptr<Batch> B;
             int rc = launch_batch(ctx, lk, items, slot, B);
             if (rc == PXR_EAGAIN && !ctx->inflight.empty()) {
@@ -1593,7 +1598,8 @@ extern "C" int pxr_create(const pxr_config *cfg, pxr_ctx **out)
     if (!ctx->cfg.mem_budget_bytes) ctx->cfg.mem_budget_bytes = size_t(2) << 30;
     if (!ctx->cfg.max_batch_events) ctx->cfg.max_batch_events = 256;
     if (!ctx->cfg.max_batch_hits) ctx->cfg.max_batch_hits = 4u << 20;
-    if (!ctx->cfg.max_inflight || ctx->cfg.max_inflight > 2) ctx->cfg.max_inflight = 2;
+    if (!ctx->cfg.max_inflight) ctx->cfg.max_inflight = 2;
+    if (ctx->cfg.max_inflight > kMaxSlots) ctx->cfg.max_inflight = kMaxSlots;
     CK(cudaSetDevice(ctx->cfg.device));
     CK(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->cfg.device));
     int major = 0, minor = 0;

@@ -7,6 +7,8 @@ with the oracle's FP64 fit within the tolerances stated for the method (pT and c
 relative, phi 1e-5 rad, dxy 1e-5 cm, dz 1e-4 relative with a 1e-5 cm floor); in practice they
 agree to ~1e-10 because only library math functions differ.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -450,18 +452,22 @@ def test_full_size_batch_sampled(ctx, orc, cut, fit, bins, grid):
     plan.close()
 
 
-def test_serving_results_equal_alone_and_in_mix(ctx, orc):
-    """Continuous batching: events submitted while others run are batched with them; each
-    result equals the result of the same event run alone (bit-exact sets and fits)."""
+@pytest.mark.parametrize("inflight", [2, 4])
+def test_serving_results_equal_alone_and_in_mix(ctx, orc, inflight):
+    """Continuous batching: events submitted while others run are batched with them (two or
+    four batches in flight, each on its own stream); each result equals the result of the same
+    event run alone (bit-exact sets and fits)."""
     P = synth.params_barrel_quadruplets()
     p = pxr.params_from(P, cut_mode=pxr.CUT_FP32)
     evs = [ev_tuple(synth.event_serving(100 + k, n))
            for k, n in enumerate([50, 3000, 10, 800, 1, 5000, 200, 0, 1500])]
-    with pxr.Context(device=0, mem_budget_bytes=8 << 30, max_batch_events=4) as sctx:
+    with pxr.Context(device=0, mem_budget_bytes=8 << 30, max_batch_events=2,
+                     max_inflight=inflight) as sctx:
         tickets = [sctx.pxr_submit_event(*ev, p) for ev in evs]
-        done = set()
+        done, t0 = set(), time.time()
         while len(done) < len(tickets):
             done |= set(sctx.pxr_poll(timeout_us=200000))
+            assert time.time() - t0 < 60.0, "served events did not finish"
         mixed = [sctx.pxr_fetch_tracks(t) for t in tickets]
     for ev, m in zip(evs, mixed):
         alone = run_plan(ctx, [ev], P, pxr.CUT_FP32, debug=False)[0]["tracks"]
